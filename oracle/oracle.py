@@ -1,0 +1,260 @@
+"""ctypes front-end of the C oracle plus two independent NumPy routes.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Nothing in the CUDA
+library imports this module.
+
+* ``rotate_dense``      -- C loops: T = (O (x) I_d) U, then O' = U^T T
+                           (Sec. 2 step 5; Sec. 3.2 order of the two products).
+* ``rotate_dense_kron`` -- second route: materialise kron(O, I_d) (the blocking
+                           step of Sec. 2) and multiply, for small sizes.
+* ``rotate_blocked``    -- C per-sector loops (Sec. 3.1 Eq. (hache) labels).
+* ``rotate_blocked_assembled`` -- second route: assemble the dense U and O
+                           from their blocks, rotate densely, cut the blocks.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dmrg_oracle.c")
+_BUILD_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_f64p = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (-O2, OpenMP).  Portable C only."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-Wall",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        lib.oracle_rotate_dense.argtypes = [_f64p, _f64p, _f64p, ctypes.c_int64, ctypes.c_int,
+                                            ctypes.c_int64, ctypes.c_int64, ctypes.c_int]
+        lib.oracle_rotate_dense.restype = ctypes.c_int
+        lib.oracle_orthonormality_error.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int64]
+        lib.oracle_orthonormality_error.restype = ctypes.c_double
+        lib.oracle_correlations.argtypes = [_f64p, _f64p, _f64p, ctypes.c_int64, ctypes.c_int64]
+        lib.oracle_correlations.restype = ctypes.c_int
+        lib.oracle_rotate_backward.argtypes = [_f64p, _f64p, _f64p, _f64p, _f64p, ctypes.c_int64,
+                                               ctypes.c_int, ctypes.c_int64, ctypes.c_int64]
+        lib.oracle_rotate_backward.restype = ctypes.c_int
+        lib.oracle_rotate_blocked.argtypes = [
+            ctypes.c_int, _i32p, _i32p, _i64p, ctypes.c_int, _i32p, _i32p,
+            ctypes.c_int, _i32p, _i32p, _i64p, ctypes.c_int64, _i32p, _i32p,
+            _f64p, _f64p, _f64p]
+        lib.oracle_rotate_blocked.restype = ctypes.c_int
+        lib.oracle_num_threads.argtypes = []
+        lib.oracle_num_threads.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _p(a, ptype):
+    return a.ctypes.data_as(ptype)
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def rotate_dense(U, O, d: int, nthreads: int = 0) -> np.ndarray:
+    """O'_k = U^T (O_k (x) I_d) U for every k (Sec. 2 step 5), FP64.
+
+    U: (m*d) x m'; O: K x m x m (or m x m).  Returns K x m' x m'."""
+    U = _c(U, np.float64)
+    O = _c(O, np.float64)
+    squeeze = O.ndim == 2
+    if squeeze:
+        O = O[None]
+    K, m, m2 = O.shape
+    assert m == m2 and U.shape[0] == m * d, "shape mismatch"
+    mp = U.shape[1]
+    out = np.empty((K, mp, mp), dtype=np.float64)
+    if K:
+        rc = _load().oracle_rotate_dense(_p(U, _f64p), _p(O, _f64p), _p(out, _f64p),
+                                         m, d, mp, K, int(nthreads))
+        if rc:
+            raise RuntimeError("oracle_rotate_dense failed")
+    return out[0] if squeeze else out
+
+
+def rotate_dense_kron(U, O, d: int) -> np.ndarray:
+    """Second route: build kron(O_k, I_d) explicitly (the blocking step) and
+    form U^T Z U with library matmuls.  Small sizes only."""
+    U = np.asarray(U, dtype=np.float64)
+    O = np.asarray(O, dtype=np.float64)
+    squeeze = O.ndim == 2
+    if squeeze:
+        O = O[None]
+    eye = np.eye(d)
+    out = np.stack([U.T @ (np.kron(Ok, eye) @ U) for Ok in O]) if len(O) else \
+        np.zeros((0, U.shape[1], U.shape[1]))
+    return out[0] if squeeze else out
+
+
+def orthonormality_error(U) -> float:
+    """||U^T U - I||_F in FP64."""
+    U = _c(U, np.float64)
+    return float(_load().oracle_orthonormality_error(_p(U, _f64p), U.shape[0], U.shape[1]))
+
+
+def correlations(Op, psi) -> np.ndarray:
+    """C[i, j] = <psi| O'_i O'_j |psi> for real data (Sec. 3.2)."""
+    Op = _c(Op, np.float64)
+    psi = _c(psi, np.float64)
+    K, mp, _ = Op.shape
+    C = np.empty((K, K), dtype=np.float64)
+    if _load().oracle_correlations(_p(Op, _f64p), _p(psi, _f64p), _p(C, _f64p), K, mp):
+        raise RuntimeError("oracle_correlations failed")
+    return C
+
+
+def rotate_backward(U, O, G, d: int, want_dU: bool = True):
+    """Adjoint of the rotation for L = sum_k <G_k, O'_k>.  Returns (dO, dU)."""
+    U = _c(U, np.float64)
+    O = _c(O, np.float64)
+    G = _c(G, np.float64)
+    K, m, _ = O.shape
+    mp = U.shape[1]
+    dO = np.empty_like(O)
+    dU = np.empty_like(U) if want_dU else None
+    rc = _load().oracle_rotate_backward(_p(U, _f64p), _p(O, _f64p), _p(G, _f64p), _p(dO, _f64p),
+                                        _p(dU, _f64p) if want_dU else None, m, d, mp, K)
+    if rc:
+        raise RuntimeError("oracle_rotate_backward failed")
+    return dO, dU
+
+
+# ----------------------------------------------------------------------------
+# Block-sparse U(1) x U(1) rotation.
+# ----------------------------------------------------------------------------
+
+def rotate_blocked(block_sectors, site_shifts, kept_sectors, op_shifts, U_blocks, O_blocks,
+                   out_size: int) -> np.ndarray:
+    """Per-sector C loops.  ``block_sectors`` / ``kept_sectors``: sequences of
+    (N_up, N_dn, dim); ``site_shifts``: d pairs; ``op_shifts``: K pairs;
+    ``U_blocks`` / ``O_blocks``: flat FP64 arrays in the library's canonical
+    block order.  Returns the flat output of ``out_size`` doubles."""
+    bs = np.asarray(block_sectors, dtype=np.int64).reshape(-1, 3)
+    ks = np.asarray(kept_sectors, dtype=np.int64).reshape(-1, 3)
+    ss = np.asarray(site_shifts, dtype=np.int64).reshape(-1, 2)
+    os_ = np.asarray(op_shifts, dtype=np.int64).reshape(-1, 2)
+    bu, bd, bm = (_c(bs[:, 0], np.int32), _c(bs[:, 1], np.int32), _c(bs[:, 2], np.int64))
+    ku, kd, km = (_c(ks[:, 0], np.int32), _c(ks[:, 1], np.int32), _c(ks[:, 2], np.int64))
+    su, sd = _c(ss[:, 0], np.int32), _c(ss[:, 1], np.int32)
+    ou, od = _c(os_[:, 0], np.int32), _c(os_[:, 1], np.int32)
+    Ub = _c(U_blocks, np.float64)
+    Ob = _c(O_blocks, np.float64)
+    out = np.zeros(max(int(out_size), 1), dtype=np.float64)
+    rc = _load().oracle_rotate_blocked(
+        len(bs), _p(bu, _i32p), _p(bd, _i32p), _p(bm, _i64p), len(ss), _p(su, _i32p), _p(sd, _i32p),
+        len(ks), _p(ku, _i32p), _p(kd, _i32p), _p(km, _i64p), len(os_), _p(ou, _i32p), _p(od, _i32p),
+        _p(Ub, _f64p), _p(Ob, _f64p), _p(out, _f64p))
+    if rc:
+        raise RuntimeError("oracle_rotate_blocked failed")
+    return out[:int(out_size)]
+
+
+def blocked_dense_assembly(block_sectors, site_shifts, kept_sectors, op_shifts, U_blocks, O_blocks):
+    """Assemble dense U ((m*d) x m') and O_k (m x m) from the block storage.
+
+    Dense block basis: block sectors in order, states in order inside each.
+    Dense [B a] row of (block state i, site state s) is i*d + s.  Dense kept
+    column: kept sectors in order.  Returns (U, O, index) where ``index``
+    holds the block positions needed to cut blocks back out."""
+    bs = [tuple(int(v) for v in x) for x in block_sectors]
+    ks = [tuple(int(v) for v in x) for x in kept_sectors]
+    ss = [tuple(int(v) for v in x) for x in site_shifts]
+    shifts = [tuple(int(v) for v in x) for x in op_shifts]
+    d = len(ss)
+    boff, m = {}, 0
+    for (u, dn, n) in bs:
+        boff[(u, dn)] = (m, n)
+        m += n
+    koff, mp = {}, 0
+    for (u, dn, n) in ks:
+        koff[(u, dn)] = (mp, n)
+        mp += n
+    U = np.zeros((m * d, mp))
+    pos = 0
+    Ub = np.asarray(U_blocks, dtype=np.float64)
+    for (u, dn, n) in ks:
+        c0 = koff[(u, dn)][0]
+        rows = []
+        for s, (du, dd) in enumerate(ss):
+            src = (u - du, dn - dd)
+            if src in boff:
+                o, nb = boff[src]
+                rows += [(o + x) * d + s for x in range(nb)]
+        blk = Ub[pos:pos + len(rows) * n].reshape(len(rows), n)
+        pos += len(rows) * n
+        for x, r in enumerate(rows):
+            U[r, c0:c0 + n] = blk[x]
+    assert pos == Ub.size, "U block storage size mismatch"
+    Obf = np.asarray(O_blocks, dtype=np.float64)
+    O = np.zeros((len(shifts), m, m))
+    pos = 0
+    for k, (du, dd) in enumerate(shifts):
+        for (u, dn, n) in bs:
+            dst = (u + du, dn + dd)
+            if dst in boff:
+                r0, nr = boff[dst]
+                c0, _ = boff[(u, dn)]
+                O[k, r0:r0 + nr, c0:c0 + n] = Obf[pos:pos + nr * n].reshape(nr, n)
+                pos += nr * n
+    assert pos == Obf.size, "O block storage size mismatch"
+    return U, O, {"koff": koff, "kept": ks, "shifts": shifts, "d": d}
+
+
+def rotate_blocked_assembled(block_sectors, site_shifts, kept_sectors, op_shifts, U_blocks,
+                             O_blocks):
+    """Second route: dense assembly, dense oracle rotation, blocks cut out.
+    Returns (flat_output, dense_rotated) so callers can also check that every
+    entry outside the allowed sector pairs is exactly zero."""
+    U, O, idx = blocked_dense_assembly(block_sectors, site_shifts, kept_sectors, op_shifts,
+                                       U_blocks, O_blocks)
+    Op = rotate_dense(U, O, idx["d"]) if len(O) else np.zeros((0, U.shape[1], U.shape[1]))
+    out = []
+    koff = idx["koff"]
+    for k, (du, dd) in enumerate(idx["shifts"]):
+        for (u, dn, n) in idx["kept"]:
+            dst = (u + du, dn + dd)
+            if dst in koff:
+                r0, nr = koff[dst]
+                c0, _ = koff[(u, dn)]
+                out.append(Op[k, r0:r0 + nr, c0:c0 + n].ravel())
+    flat = np.concatenate(out) if out else np.zeros(0)
+    return flat, Op
