@@ -1,0 +1,244 @@
+/*
+ * dmrg_rotate.h -- C ABI of the GB300 (sm_103a) DMRG operator-rotation library.
+ *
+ * The library performs the density-matrix rotation and decimation step of
+ * the DMRG (Rincon, Garcia, Hallberg, "Improved parallelization techniques
+ * for the density matrix renormalization group", Sec. 2, algorithm step 5,
+ * and the paragraph after it):
+ *
+ *     O'_k = U^T (O_k (x) I_d) U,        k = 0 .. K-1,
+ *
+ * where O_k is an m x m block operator, I_d the identity of the added site
+ * (the "blocking" Z_[B a] <- Z_[B (+) a]), and U = R^+ the (m*d) x m'
+ * matrix of kept density-matrix eigenvectors (step 4; real data, so
+ * R^+ = R^T).  Sec. 3.2 identifies the two matrix products Z R^+ and
+ * R (Z R^+) over the K stored Z_i and Z_i Z_j operators as the most
+ * expensive part of a DMRG run that measures correlation functions.
+ *
+ * Conventions shared by every entry point
+ *   - Index convention of [B a]: row r = i*d + s (block state i, site state
+ *     s), i.e. the blocked operator is kron(O, I_d).  All matrices row-major.
+ *   - Every data pointer is a DEVICE pointer owned by the caller.  The
+ *     library never keeps a reference to caller memory after a call returns.
+ *   - Calls are asynchronous on `stream` (NULL = legacy default stream).
+ *     Argument and shape errors are returned synchronously, before anything
+ *     is launched.  A kernel that gives up waiting (bounded spin on an
+ *     mbarrier) records DMRG_ERR_TIMEOUT in a device status word owned by
+ *     the handle; dmrg_sync_status() reads and clears it.
+ *   - The hot-path calls allocate nothing: scratch memory is the caller's
+ *     workspace `ws` of at least the size returned by the matching
+ *     *_workspace query.  Workspace pointers must be 256-byte aligned.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef DMRG_ROTATE_H
+#define DMRG_ROTATE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DMRG_API __attribute__((visibility("default")))
+#else
+#define DMRG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st* dmrg_stream_t;
+
+typedef enum {
+    DMRG_OK = 0,
+    DMRG_ERR_INVALID_ARG = 1,      /* null pointer, bad enum, misaligned pointer        */
+    DMRG_ERR_SHAPE = 2,            /* inconsistent or unsupported sizes                  */
+    DMRG_ERR_NOT_ORTHONORMAL = 3,  /* ||U^T U - I||_F above the checked tolerance       */
+    DMRG_ERR_WORKSPACE = 4,        /* workspace missing or smaller than the query says   */
+    DMRG_ERR_CUDA = 5,             /* a CUDA runtime/driver call failed                  */
+    DMRG_ERR_TIMEOUT = 6,          /* a device-side bounded wait expired                 */
+    DMRG_ERR_UNSUPPORTED = 7       /* combination not implemented (e.g. GPU too old)     */
+} dmrg_status;
+
+/* Arithmetic of the two products.
+ *   FP64   : plain FP64 FMA on the GPU (reference path).
+ *   FP32   : plain FP32 FMA.
+ *   TF32   : tcgen05 tensor cores, kind::tf32, FP32 accumulate.
+ *   BF16X3 : tcgen05 tensor cores, kind::f16 with every operand split into a
+ *            BF16 pair x = hi + lo and hi*hi + hi*lo + lo*hi accumulated in FP32. */
+typedef enum {
+    DMRG_PREC_FP64 = 0,
+    DMRG_PREC_FP32 = 1,
+    DMRG_PREC_TF32 = 2,
+    DMRG_PREC_BF16X3 = 3
+} dmrg_precision;
+
+typedef struct dmrg_handle_s* dmrg_handle;
+
+/* Creates a handle bound to the current CUDA device.  It owns a small device
+ * status word, the autotuner's cache and any captured CUDA graphs. */
+DMRG_API dmrg_status dmrg_create(dmrg_handle* handle);
+DMRG_API dmrg_status dmrg_destroy(dmrg_handle handle);
+DMRG_API const char* dmrg_status_string(dmrg_status status);
+/* Human-readable detail of the last error returned on this handle ("" if none). */
+DMRG_API const char* dmrg_last_error(dmrg_handle handle);
+/* Synchronises `stream`, then reads and clears the device status word:
+ * DMRG_ERR_TIMEOUT if a kernel gave up on a bounded wait since the last check. */
+DMRG_API dmrg_status dmrg_sync_status(dmrg_handle handle, dmrg_stream_t stream);
+
+/* Options (value is a double for uniformity).
+ *   DMRG_OPT_GRAPH           : 1 = capture each distinct call (pointers + sizes)
+ *                              in a CUDA graph on first use and replay it after.
+ *   DMRG_OPT_KERNEL_TIMING   : 1 = record CUDA events around every kernel the
+ *                              library launches (read with dmrg_kernel_timing).
+ *   DMRG_OPT_WAIT_TIMEOUT_MS : device-side bounded-wait limit (default 2000 ms).
+ *   DMRG_OPT_CHECK_ORTHO     : tolerance > 0 makes dmrg_rotate_ops verify
+ *                              ||U^T U - I||_F <= tol first (synchronises the
+ *                              stream); 0 = off (default). */
+typedef enum {
+    DMRG_OPT_GRAPH = 1,
+    DMRG_OPT_KERNEL_TIMING = 2,
+    DMRG_OPT_WAIT_TIMEOUT_MS = 3,
+    DMRG_OPT_CHECK_ORTHO = 4
+} dmrg_option;
+DMRG_API dmrg_status dmrg_set_option(dmrg_handle handle, dmrg_option option, double value);
+
+/* Writes a JSON array [{"kernel": name, "launches": n, "total_ms": t}, ...]
+ * of the events recorded since the last reset into buf (synchronises the
+ * recorded events).  reset != 0 clears the record afterwards. */
+DMRG_API dmrg_status dmrg_kernel_timing(dmrg_handle handle, char* buf, size_t buf_len, int reset);
+
+/* ------------------------------------------------------------------------
+ * Dense rotation (Sec. 2 step 5; Sec. 3.2 two-product order).
+ *
+ *   U    : (m*d) x mp, FP64, orthonormal columns, row-major.
+ *   O    : K x m x m, FP64 if in_is_fp64 else FP32.  The FP64 precision needs
+ *          FP64 input.
+ *   Oout : K x mp x mp; FP64 for DMRG_PREC_FP64, FP32 for every other
+ *          precision.  Must not overlap O, U or ws.
+ *   Requires m >= 1, d >= 1, 1 <= mp <= m*d, K >= 0 (K = 0 is a no-op),
+ *   and (tensor-core precisions) m*d <= 2^31 - 1 and K*max(m, mp) <= 2^31 - 1.
+ *
+ * Implementation: the blocking is never materialised.  With U viewed as the
+ * m x (d*mp) matrix U_r[j][s*mp + b] = U[j*d + s][b], the first product is
+ * T_k = O_k U_r (= (O_k (x) I_d) U), the second O'_k = U^T T_k.  Tensor-core
+ * precisions stack all K operators into one GEMM per product.
+ * ------------------------------------------------------------------------ */
+DMRG_API dmrg_status dmrg_rotate_ops_workspace(dmrg_handle handle, int64_t K, int64_t m, int d, int64_t mp,
+                                      dmrg_precision precision, size_t* bytes);
+DMRG_API dmrg_status dmrg_rotate_ops(dmrg_handle handle, const double* U, int64_t m, int d, int64_t mp,
+                            const void* O, int in_is_fp64, int64_t K, void* Oout,
+                            dmrg_precision precision, void* ws, size_t ws_bytes,
+                            dmrg_stream_t stream);
+
+/* Runs every candidate tiling of the tensor-core kernels on these buffers,
+ * times them with CUDA events and caches the fastest for this shape in the
+ * handle (and in the JSON file named by $DMRG_AUTOTUNE_CACHE, if set).
+ * Overwrites Oout and ws.  Synchronous.  FP64/FP32 precisions: no-op. */
+DMRG_API dmrg_status dmrg_autotune_rotate_ops(dmrg_handle handle, const double* U, int64_t m, int d,
+                                     int64_t mp, const void* O, int in_is_fp64, int64_t K,
+                                     void* Oout, dmrg_precision precision, void* ws,
+                                     size_t ws_bytes, dmrg_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Adjoint of the dense rotation for a loss L with dL/dO'_k = G_k:
+ *   dO_k = Tr_d(U G_k U^T)        i.e. dO_k[i][j] = sum_s (U G_k U^T)[i*d+s][j*d+s]
+ *   dU   = sum_k (O_k (x) I_d) U G_k^T + (O_k (x) I_d)^T U G_k
+ * (chain rule of the rotation of Sec. 2 step 5; the paper has no gradient).
+ * Nothing from the forward pass is stored; only U and O are read again.
+ *   G (dOout) : K x mp x mp and O : K x m x m, both FP64 if in_is_fp64 else FP32
+ *               (FP64 precision needs FP64).
+ *   dO        : K x m x m, FP64 for DMRG_PREC_FP64 else FP32.  May be NULL.
+ *   dU        : (m*d) x mp FP64, overwritten.  May be NULL.
+ * ------------------------------------------------------------------------ */
+DMRG_API dmrg_status dmrg_rotate_ops_backward_workspace(dmrg_handle handle, int64_t K, int64_t m, int d,
+                                               int64_t mp, dmrg_precision precision, size_t* bytes);
+DMRG_API dmrg_status dmrg_rotate_ops_backward(dmrg_handle handle, const double* U, int64_t m, int d,
+                                     int64_t mp, const void* O, const void* dOout, int in_is_fp64,
+                                     int64_t K, void* dO, double* dU, dmrg_precision precision,
+                                     void* ws, size_t ws_bytes, dmrg_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * FP64 checks and measurements (kept in FP64 whatever the rotation used).
+ * ------------------------------------------------------------------------ */
+/* out_fro (device, 1 double) = ||U^T U - I_mp||_F for U (rows x mp).  The
+ * kept |w_alpha> must be orthonormal for the rotation to be a projection
+ * (Sec. 2: the block basis is only approximately complete). */
+DMRG_API dmrg_status dmrg_orthonormality_error(dmrg_handle handle, const double* U, int64_t rows,
+                                      int64_t mp, double* out_fro, void* ws, size_t ws_bytes,
+                                      dmrg_stream_t stream);
+DMRG_API dmrg_status dmrg_orthonormality_error_workspace(dmrg_handle handle, int64_t rows, int64_t mp,
+                                                size_t* bytes);
+
+/* Two-point functions of Sec. 3.2, C[i][j] = <psi| O'_i O'_j |psi>, computed in
+ * FP64 as (O'_i^T psi) . (O'_j psi) (real data).  Op: K x mp x mp (FP64 if
+ * in_is_fp64 else FP32); psi: mp FP64; C: K x K FP64 (device). */
+DMRG_API dmrg_status dmrg_correlations_workspace(dmrg_handle handle, int64_t K, int64_t mp, size_t* bytes);
+DMRG_API dmrg_status dmrg_correlations(dmrg_handle handle, const void* Op, int in_is_fp64,
+                              const double* psi, int64_t K, int64_t mp, double* C, void* ws,
+                              size_t ws_bytes, dmrg_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Block-sparse U(1) x U(1) rotation (operators labelled by quantum numbers,
+ * Sec. 3.1 Eq. (hache); the paper did not distribute these sub-blocks
+ * "because of their dissimilar dimensions" -- here they all go into one
+ * grouped launch per product).
+ *
+ * Canonical storage (all row-major, FP64 U, operators FP64/FP32):
+ *   block sectors q (given order): label (n_up, n_dn), size m_q;
+ *   site states s = 0..d-1 with label shifts delta_s;
+ *   kept sectors Q (given order): label, size m'_Q (0 < m'_Q <= D_Q).
+ *   [B a] sector of kept Q: for s = 0..d-1 in order, the states of block
+ *     sector (Q - delta_s) if present; D_Q = number of such states.
+ *   U blocks : kept sector after kept sector, U_Q of D_Q x m'_Q.
+ *   O blocks : operator after operator; operator k (label shift delta_k)
+ *     stores, for every block sector q in order with q + delta_k present,
+ *     the m_{q+delta_k} x m_q block O_k[q + delta_k, q].
+ *   Output   : operator after operator; operator k stores, for every kept
+ *     sector Q in order with Q + delta_k kept, the m'_{Q+delta_k} x m'_Q block
+ *     O'_k[Q + delta_k, Q] = sum_s U_{Q+delta_k}[seg s]^T
+ *                            O_k[Q + delta_k - delta_s, Q - delta_s] U_Q[seg s].
+ * Labels must be distinct within each list.  The plan precomputes the
+ * grouped problem lists (device tables; allocated at plan creation, not on
+ * the hot path) and is tied to the handle's device.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t n_up;
+    int32_t n_dn;
+    int64_t dim;
+} dmrg_qn_sector;
+
+typedef struct {
+    int32_t d_up;
+    int32_t d_dn;
+} dmrg_qn_shift;
+
+typedef struct dmrg_blocked_plan_s* dmrg_blocked_plan;
+
+DMRG_API dmrg_status dmrg_blocked_plan_create(dmrg_handle handle, const dmrg_qn_sector* block_sectors,
+                                     int32_t n_block_sectors, const dmrg_qn_shift* site_shifts,
+                                     int32_t d, const dmrg_qn_sector* kept_sectors, int32_t n_kept,
+                                     const dmrg_qn_shift* op_shifts, int64_t K,
+                                     dmrg_blocked_plan* plan);
+DMRG_API dmrg_status dmrg_blocked_plan_destroy(dmrg_blocked_plan plan);
+/* Element counts of the three storages and the workspace bytes for `precision`
+ * (DMRG_PREC_FP64, DMRG_PREC_FP32 or DMRG_PREC_BF16X3). */
+DMRG_API dmrg_status dmrg_blocked_plan_sizes(dmrg_blocked_plan plan, dmrg_precision precision,
+                                    int64_t* u_elems, int64_t* in_elems, int64_t* out_elems,
+                                    size_t* ws_bytes);
+/* Realised problem statistics: number of grouped GEMM problems of each
+ * product, and the logical flops of one call. */
+DMRG_API dmrg_status dmrg_blocked_plan_stats(dmrg_blocked_plan plan, int64_t* n_problems_first,
+                                    int64_t* n_problems_second, double* flops);
+/* Oout_blocks: FP64 for DMRG_PREC_FP64, else FP32. */
+DMRG_API dmrg_status dmrg_rotate_ops_blocked(dmrg_handle handle, dmrg_blocked_plan plan,
+                                    const double* U_blocks, const void* O_blocks, int in_is_fp64,
+                                    void* Oout_blocks, dmrg_precision precision, void* ws,
+                                    size_t ws_bytes, dmrg_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DMRG_ROTATE_H */

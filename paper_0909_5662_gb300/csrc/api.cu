@@ -1,0 +1,568 @@
+// api.cu -- C ABI of the library (declared in include/dmrg_rotate.h): handle,
+// argument checks, workspace layout and the dense forward rotation
+//   O'_k = U^T (O_k (x) I_d) U        (Sec. 2 step 5; two products of Sec. 3.2).
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "api_common.h"
+#include "internal.h"
+
+using namespace dmrg;
+
+namespace dmrg {
+
+dmrg_status fail(dmrg_handle h, dmrg_status st, const std::string& msg) {
+    if (h) h->last_error = msg;
+    return st;
+}
+
+dmrg_status cuda_fail(dmrg_handle h, cudaError_t e, const char* where) {
+    if (e == cudaSuccess) return DMRG_OK;
+    return fail(h, DMRG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+cudaEvent_t pooled_event(dmrg_handle h) {
+    if (!h->event_pool.empty()) {
+        cudaEvent_t e = h->event_pool.back();
+        h->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+cudaError_t timed_launch(dmrg_handle h, const char* name, cudaStream_t s,
+                         const std::function<cudaError_t()>& f) {
+    if (!h->timing || h->capturing) return f();
+    cudaEvent_t a = pooled_event(h), b = pooled_event(h);
+    cudaEventRecord(a, s);
+    cudaError_t e = f();
+    cudaEventRecord(b, s);
+    h->pending.push_back({name, a, b});
+    return e;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+void WsLayout::add(const char* name, size_t bytes) {
+    (void)name;
+    offsets.push_back(total);
+    total = align_up(total + align_up(bytes, 256), 256);
+}
+
+bool tc_supported(dmrg_handle h) { return h->cc_major == 10 && h->cc_minor == 3; }
+
+uint64_t timeout_ns(dmrg_handle h) {
+    double ms = h->wait_timeout_ms;
+    if (!(ms > 0)) ms = 2000.0;
+    return uint64_t(ms * 1e6);
+}
+
+// Runs `body` directly, or (graph mode) captures it once per key into a CUDA
+// graph on the handle's private stream and replays the graph on `stream`.
+dmrg_status run_maybe_graph(dmrg_handle h, const std::string& key, cudaStream_t stream,
+                            const std::function<dmrg_status(cudaStream_t)>& body) {
+    if (!h->graph_mode) return body(stream);
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+        if (!h->capture_stream) {
+            cudaError_t e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamCreate");
+        }
+        cudaError_t e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamBeginCapture");
+        h->capturing = true;
+        dmrg_status st = body(h->capture_stream);
+        h->capturing = false;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(h->capture_stream, &g);
+        if (st != DMRG_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+        it = h->graphs.emplace(key, ex).first;
+    }
+    return cuda_fail(h, cudaGraphLaunch(it->second, stream), "cudaGraphLaunch");
+}
+
+// ------------------------------------------------------------------ dense layout
+DenseDims dense_dims(int64_t K, int64_t m, int d, int64_t mp, dmrg_precision p) {
+    DenseDims D;
+    D.K = K; D.m = m; D.d = d; D.mp = mp; D.md = m * d;
+    const int64_t align = (p == DMRG_PREC_TF32) ? 4 : 8;
+    D.ld1 = (m + align - 1) / align * align;
+    D.ld2 = (D.md + align - 1) / align * align;
+    const size_t es = (p == DMRG_PREC_TF32) ? 4 : 2;
+    WsLayout& W = D.ws;
+    if (p == DMRG_PREC_FP64) {
+        W.add("T", size_t(K) * D.md * mp * 8);
+    } else if (p == DMRG_PREC_FP32) {
+        W.add("O32", size_t(K) * m * m * 4);
+        W.add("U32", size_t(D.md) * mp * 4);
+        W.add("T", size_t(K) * D.md * mp * 4);
+    } else {
+        const int nsplit = (p == DMRG_PREC_BF16X3) ? 2 : 1;
+        for (int s = 0; s < nsplit; ++s) W.add("Op", size_t(K) * m * D.ld1 * es);
+        for (int s = 0; s < nsplit; ++s) W.add("B1", size_t(d) * mp * D.ld1 * es);
+        for (int s = 0; s < nsplit; ++s) W.add("B2", size_t(mp) * D.ld2 * es);
+        for (int s = 0; s < nsplit; ++s) W.add("T", size_t(K) * mp * D.ld2 * es);
+    }
+    return D;
+}
+
+dmrg_status check_dense_args(dmrg_handle h, int64_t K, int64_t m, int d, int64_t mp,
+                             dmrg_precision p) {
+    if (!h) return DMRG_ERR_INVALID_ARG;
+    if (p < DMRG_PREC_FP64 || p > DMRG_PREC_BF16X3)
+        return fail(h, DMRG_ERR_INVALID_ARG, "unknown precision");
+    if (m < 1 || d < 1 || mp < 1 || K < 0)
+        return fail(h, DMRG_ERR_SHAPE, "need m >= 1, d >= 1, mp >= 1, K >= 0");
+    if (mp > m * d) return fail(h, DMRG_ERR_SHAPE, "mp must not exceed m*d");
+    if (p == DMRG_PREC_TF32 || p == DMRG_PREC_BF16X3) {
+        const int64_t lim = 0x7fffffffLL;
+        if (m * d > lim || K * std::max(m, mp) > lim || int64_t(d) * mp > lim)
+            return fail(h, DMRG_ERR_SHAPE, "sizes exceed the 32-bit tile index range");
+    }
+    return DMRG_OK;
+}
+
+TcConfig tuned_config(dmrg_handle h, const std::string& key, TcMode mode) {
+    auto it = h->tune_cache.find(key);
+    if (it != h->tune_cache.end()) return it->second;
+    TcConfig c;
+    c.tile_n_max = 256;
+    c.stages = tc_max_stages(mode, 256);
+    c.grid = 0;
+    return c;
+}
+
+std::string shape_key(const char* tag, int64_t K, int64_t m, int d, int64_t mp, dmrg_precision p) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "%s:K%lld:m%lld:d%d:mp%lld:p%d", tag, (long long)K, (long long)m, d,
+             (long long)mp, int(p));
+    return buf;
+}
+
+// Dense tensor-core forward with explicit tilings (the autotuner calls this directly).
+dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
+                             const void* O, int in_is_fp64, int64_t K, void* Oout,
+                             dmrg_precision p, void* ws, const TcConfig& c1, const TcConfig& c2,
+                             cudaStream_t s) {
+    const DenseDims D = dense_dims(K, m, d, mp, p);
+    const bool split = (p == DMRG_PREC_BF16X3);
+    const TcMode mode = split ? TC_BF16X3 : TC_TF32;
+    const int pmode = split ? 0 : 1;
+    char* base = static_cast<char*>(ws);
+    int si = 0;
+    void* Op[2] = {nullptr, nullptr};
+    void* B1[2] = {nullptr, nullptr};
+    void* B2[2] = {nullptr, nullptr};
+    void* Tt[2] = {nullptr, nullptr};
+    const int ns = split ? 2 : 1;
+    for (int i = 0; i < ns; ++i) Op[i] = base + D.ws.offsets[si++];
+    for (int i = 0; i < ns; ++i) B1[i] = base + D.ws.offsets[si++];
+    for (int i = 0; i < ns; ++i) B2[i] = base + D.ws.offsets[si++];
+    for (int i = 0; i < ns; ++i) Tt[i] = base + D.ws.offsets[si++];
+
+    // ---- operand packing: O (stacked K*m x m), U_r' (rows b*d + s, cols j), U^T.
+    PackJob jobs[3] = {};
+    PackJob& jo = jobs[0];
+    jo.src = O; jo.src_f64 = in_is_fp64; jo.mode = pmode;
+    jo.rows = K * m; jo.cols = m; jo.rows_per_op = K * m; jo.s_op = 0; jo.op_off = nullptr;
+    jo.rdiv = 1; jo.s_r_hi = m; jo.s_r_lo = 0; jo.s_c = 1;
+    jo.dst0 = Op[0]; jo.dst1 = Op[1]; jo.ld = D.ld1;
+    PackJob& j1 = jobs[1];
+    j1.src = U; j1.src_f64 = 1; j1.mode = pmode;
+    j1.rows = int64_t(d) * mp; j1.cols = m; j1.rows_per_op = j1.rows;
+    j1.rdiv = d; j1.s_r_hi = 1; j1.s_r_lo = mp; j1.s_c = int64_t(d) * mp;
+    j1.dst0 = B1[0]; j1.dst1 = B1[1]; j1.ld = D.ld1;
+    PackJob& j2 = jobs[2];
+    j2.src = U; j2.src_f64 = 1; j2.mode = pmode;
+    j2.rows = mp; j2.cols = D.md; j2.rows_per_op = mp;
+    j2.rdiv = 1; j2.s_r_hi = 1; j2.s_r_lo = 0; j2.s_c = mp;
+    j2.dst0 = B2[0]; j2.dst1 = B2[1]; j2.ld = D.ld2;
+    cudaError_t e = timed_launch(h, "pack_operands", s, [&] { return pack_launch(jobs, 3, nullptr, s); });
+    if (e != cudaSuccess) return cuda_fail(h, e, "pack");
+
+    const bool f32 = !split;
+    // ---- first product: T = O U_r, written straight into the second product's
+    //      K-major operand layout: T_all[k*mp + b][i*d + s].
+    TcLaunch L1{};
+    TcProblem& P1 = L1.inline_prob;
+    const int tn1 = choose_tile_n(int64_t(d) * mp, c1.tile_n_max);
+    for (int i = 0; i < ns; ++i) {
+        if (!encode_operand_map(&P1.tmA[i], Op[i], f32, K * m, m, D.ld1, 128) ||
+            !encode_operand_map(&P1.tmB[i], B1[i], f32, int64_t(d) * mp, m, D.ld1, tn1))
+            return fail(h, DMRG_ERR_CUDA, "cuTensorMapEncodeTiled failed (first product)");
+    }
+    if (!split) { P1.tmA[1] = P1.tmA[0]; P1.tmB[1] = P1.tmB[0]; }
+    finish_problem(P1, K * m, int64_t(d) * mp, m, tn1, 1, mode);
+    P1.tile_start = 0;
+    P1.rows_per_op = int32_t(m);
+    P1.s_op = mp * D.ld2;
+    P1.s_row = d;
+    P1.col_div = d;
+    P1.s_col_hi = D.ld2;
+    P1.s_col_lo = 1;
+    P1.out_off = 0;
+    P1.op_off = nullptr;
+    L1.table = nullptr;
+    L1.nprob = 1;
+    L1.total_tiles = P1.m_tiles * P1.n_tiles * P1.k_splits;
+    L1.out0 = Tt[0];
+    L1.out1 = Tt[1];
+    L1.status = h->d_status;
+    L1.timeout_ns = timeout_ns(h);
+    const int grid1 = c1.grid > 0 ? c1.grid : h->num_sms;
+    e = timed_launch(h, "tc_gemm_first_product", s, [&] {
+        return tc_gemm_launch(mode, split ? EPI_SPLIT_BF16 : EPI_TF32, L1, c1.stages, grid1, s);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "first product");
+
+    // ---- second product: O'_k^T rows = T_all rows (k*mp + b), columns a: O'_k[a][b].
+    TcLaunch L2{};
+    TcProblem& P2 = L2.inline_prob;
+    const int tn2 = choose_tile_n(mp, c2.tile_n_max);
+    for (int i = 0; i < ns; ++i) {
+        if (!encode_operand_map(&P2.tmA[i], Tt[i], f32, K * mp, D.md, D.ld2, 128) ||
+            !encode_operand_map(&P2.tmB[i], B2[i], f32, mp, D.md, D.ld2, tn2))
+            return fail(h, DMRG_ERR_CUDA, "cuTensorMapEncodeTiled failed (second product)");
+    }
+    if (!split) { P2.tmA[1] = P2.tmA[0]; P2.tmB[1] = P2.tmB[0]; }
+    finish_problem(P2, K * mp, mp, D.md, tn2, 1, mode);
+    P2.tile_start = 0;
+    P2.rows_per_op = int32_t(mp);
+    P2.s_op = mp * mp;
+    P2.s_row = 1;
+    P2.col_div = 1;
+    P2.s_col_hi = mp;
+    P2.s_col_lo = 0;
+    P2.out_off = 0;
+    P2.op_off = nullptr;
+    L2.table = nullptr;
+    L2.nprob = 1;
+    L2.total_tiles = P2.m_tiles * P2.n_tiles * P2.k_splits;
+    L2.out0 = Oout;
+    L2.out1 = nullptr;
+    L2.status = h->d_status;
+    L2.timeout_ns = timeout_ns(h);
+    const int grid2 = c2.grid > 0 ? c2.grid : h->num_sms;
+    e = timed_launch(h, "tc_gemm_second_product", s, [&] {
+        return tc_gemm_launch(mode, EPI_F32, L2, c2.stages, grid2, s);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "second product");
+    return DMRG_OK;
+}
+
+dmrg_status dense_simt_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
+                               const void* O, int in_is_fp64, int64_t K, void* Oout,
+                               dmrg_precision p, void* ws, cudaStream_t s) {
+    const DenseDims D = dense_dims(K, m, d, mp, p);
+    char* base = static_cast<char*>(ws);
+    const bool f64 = (p == DMRG_PREC_FP64);
+    const void* Ouse = O;
+    const void* Uuse = U;
+    void* T = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (f64) {
+        T = base + D.ws.offsets[0];
+    } else {
+        float* O32 = reinterpret_cast<float*>(base + D.ws.offsets[0]);
+        float* U32 = reinterpret_cast<float*>(base + D.ws.offsets[1]);
+        T = base + D.ws.offsets[2];
+        PackJob jobs[2] = {};
+        int nj = 0;
+        if (in_is_fp64) {
+            PackJob& j = jobs[nj++];
+            j.src = O; j.src_f64 = 1; j.mode = 2; j.rows = K * m; j.cols = m; j.rows_per_op = K * m;
+            j.rdiv = 1; j.s_r_hi = m; j.s_c = 1; j.dst0 = O32; j.ld = m;
+            Ouse = O32;
+        }
+        PackJob& j = jobs[nj++];
+        j.src = U; j.src_f64 = 1; j.mode = 2; j.rows = D.md; j.cols = mp; j.rows_per_op = D.md;
+        j.rdiv = 1; j.s_r_hi = mp; j.s_c = 1; j.dst0 = U32; j.ld = mp;
+        Uuse = U32;
+        e = timed_launch(h, "convert_fp32", s, [&] { return pack_launch(jobs, nj, nullptr, s); });
+        if (e != cudaSuccess) return cuda_fail(h, e, "convert");
+    }
+    const Real rt = f64 ? Real::F64 : Real::F32;
+    // First product: T_k (m x d*mp) = O_k (m x m) * U_r (m x d*mp).
+    SimtGemm g1{};
+    g1.A = Ouse; g1.B = Uuse; g1.C = T;
+    g1.M = m; g1.N = int64_t(d) * mp; g1.K = m;
+    g1.sAb = m * m; g1.sAi = m; g1.sAk = 1;
+    g1.sBb = 0; g1.sBk = int64_t(d) * mp; g1.sBj = 1;
+    g1.sCb = D.md * mp; g1.sCi = int64_t(d) * mp; g1.sCj = 1;
+    g1.batch = int32_t(K);
+    e = timed_launch(h, "simt_gemm_first_product", s, [&] { return simt_gemm_launch(rt, g1, s); });
+    if (e != cudaSuccess) return cuda_fail(h, e, "first product");
+    // Second product: O'_k (mp x mp) = U^T (mp x md) * T_k (md x mp).
+    SimtGemm g2{};
+    g2.A = Uuse; g2.B = T; g2.C = Oout;
+    g2.M = mp; g2.N = mp; g2.K = D.md;
+    g2.sAb = 0; g2.sAi = 1; g2.sAk = mp;
+    g2.sBb = D.md * mp; g2.sBk = mp; g2.sBj = 1;
+    g2.sCb = mp * mp; g2.sCi = mp; g2.sCj = 1;
+    g2.batch = int32_t(K);
+    e = timed_launch(h, "simt_gemm_second_product", s, [&] { return simt_gemm_launch(rt, g2, s); });
+    if (e != cudaSuccess) return cuda_fail(h, e, "second product");
+    return DMRG_OK;
+}
+
+dmrg_status check_ws(dmrg_handle h, const void* ws, size_t have, size_t need) {
+    if (need == 0) return DMRG_OK;
+    if (!ws || have < need) {
+        char b[128];
+        snprintf(b, sizeof b, "workspace too small: need %zu bytes, got %zu", need, have);
+        return fail(h, DMRG_ERR_WORKSPACE, b);
+    }
+    if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0)
+        return fail(h, DMRG_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    return DMRG_OK;
+}
+
+}  // namespace dmrg
+
+// =================================================================== C ABI
+extern "C" {
+
+const char* dmrg_status_string(dmrg_status s) {
+    switch (s) {
+        case DMRG_OK: return "DMRG_OK";
+        case DMRG_ERR_INVALID_ARG: return "DMRG_ERR_INVALID_ARG";
+        case DMRG_ERR_SHAPE: return "DMRG_ERR_SHAPE";
+        case DMRG_ERR_NOT_ORTHONORMAL: return "DMRG_ERR_NOT_ORTHONORMAL";
+        case DMRG_ERR_WORKSPACE: return "DMRG_ERR_WORKSPACE";
+        case DMRG_ERR_CUDA: return "DMRG_ERR_CUDA";
+        case DMRG_ERR_TIMEOUT: return "DMRG_ERR_TIMEOUT";
+        case DMRG_ERR_UNSUPPORTED: return "DMRG_ERR_UNSUPPORTED";
+    }
+    return "DMRG_ERR_UNKNOWN";
+}
+
+const char* dmrg_last_error(dmrg_handle h) { return h ? h->last_error.c_str() : ""; }
+
+dmrg_status dmrg_create(dmrg_handle* out) {
+    if (!out) return DMRG_ERR_INVALID_ARG;
+    *out = nullptr;
+    dmrg_handle h = new dmrg_handle_s();
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->cc_major, cudaDevAttrComputeCapabilityMajor, h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->cc_minor, cudaDevAttrComputeCapabilityMinor, h->device);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&h->d_status), 256);
+    if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, 256);
+    if (e != cudaSuccess) {
+        if (h->d_status) cudaFree(h->d_status);
+        delete h;
+        return DMRG_ERR_CUDA;
+    }
+    h->d_scratch = reinterpret_cast<double*>(reinterpret_cast<char*>(h->d_status) + 64);
+    *out = h;
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_destroy(dmrg_handle h) {
+    if (!h) return DMRG_ERR_INVALID_ARG;
+    for (auto& t : h->pending) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (auto ev : h->event_pool) cudaEventDestroy(ev);
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    if (h->d_status) cudaFree(h->d_status);
+    delete h;
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_set_option(dmrg_handle h, dmrg_option o, double v) {
+    if (!h) return DMRG_ERR_INVALID_ARG;
+    switch (o) {
+        case DMRG_OPT_GRAPH: h->graph_mode = v != 0; return DMRG_OK;
+        case DMRG_OPT_KERNEL_TIMING: h->timing = v != 0; return DMRG_OK;
+        case DMRG_OPT_WAIT_TIMEOUT_MS:
+            if (!(v > 0)) return fail(h, DMRG_ERR_INVALID_ARG, "timeout must be > 0");
+            h->wait_timeout_ms = v;
+            return DMRG_OK;
+        case DMRG_OPT_CHECK_ORTHO:
+            if (v < 0) return fail(h, DMRG_ERR_INVALID_ARG, "tolerance must be >= 0");
+            h->check_ortho_tol = v;
+            return DMRG_OK;
+    }
+    return fail(h, DMRG_ERR_INVALID_ARG, "unknown option");
+}
+
+dmrg_status dmrg_sync_status(dmrg_handle h, dmrg_stream_t stream) {
+    if (!h) return DMRG_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    unsigned st = 0;
+    e = cudaMemcpy(&st, h->d_status, sizeof st, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+    if (st != 0) {
+        cudaMemset(h->d_status, 0, sizeof st);
+        return fail(h, DMRG_ERR_TIMEOUT, "a device-side bounded wait expired");
+    }
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_kernel_timing(dmrg_handle h, char* buf, size_t len, int reset) {
+    if (!h || !buf || len == 0) return DMRG_ERR_INVALID_ARG;
+    for (auto& t : h->pending) {
+        cudaEventSynchronize(t.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t.a, t.b);
+        auto& acc = h->timing_acc[t.name];
+        acc.first += 1;
+        acc.second += ms;
+        h->event_pool.push_back(t.a);
+        h->event_pool.push_back(t.b);
+    }
+    h->pending.clear();
+    std::string js = "[";
+    bool first = true;
+    for (auto& kv : h->timing_acc) {
+        char b[256];
+        snprintf(b, sizeof b, "%s{\"kernel\": \"%s\", \"launches\": %ld, \"total_ms\": %.6f}",
+                 first ? "" : ", ", kv.first.c_str(), kv.second.first, kv.second.second);
+        js += b;
+        first = false;
+    }
+    js += "]";
+    if (reset) h->timing_acc.clear();
+    if (js.size() + 1 > len) return fail(h, DMRG_ERR_INVALID_ARG, "timing buffer too small");
+    memcpy(buf, js.c_str(), js.size() + 1);
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_rotate_ops_workspace(dmrg_handle h, int64_t K, int64_t m, int d, int64_t mp,
+                                      dmrg_precision p, size_t* bytes) {
+    if (!bytes) return fail(h, DMRG_ERR_INVALID_ARG, "bytes is NULL");
+    dmrg_status st = check_dense_args(h, K, m, d, mp, p);
+    if (st != DMRG_OK) return st;
+    *bytes = dense_dims(K, m, d, mp, p).ws.total;
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_rotate_ops(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
+                            const void* O, int in_is_fp64, int64_t K, void* Oout,
+                            dmrg_precision p, void* ws, size_t ws_bytes, dmrg_stream_t stream) {
+    dmrg_status st = check_dense_args(h, K, m, d, mp, p);
+    if (st != DMRG_OK) return st;
+    if (K == 0) return DMRG_OK;
+    if (!U || !O || !Oout) return fail(h, DMRG_ERR_INVALID_ARG, "null data pointer");
+    if (p == DMRG_PREC_FP64 && !in_is_fp64)
+        return fail(h, DMRG_ERR_INVALID_ARG, "the FP64 precision needs FP64 operators");
+    const DenseDims D = dense_dims(K, m, d, mp, p);
+    st = check_ws(h, ws, ws_bytes, D.ws.total);
+    if (st != DMRG_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const bool tc = (p == DMRG_PREC_TF32 || p == DMRG_PREC_BF16X3);
+    if (tc && !tc_supported(h))
+        return fail(h, DMRG_ERR_UNSUPPORTED, "tensor-core precisions need an sm_103 GPU");
+    if (h->check_ortho_tol > 0) {
+        cudaError_t e = ortho_error_launch(U, D.md, mp, h->d_scratch, h->d_scratch + 1, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "orthonormality check");
+        double err = 0;
+        e = cudaMemcpyAsync(&err, h->d_scratch + 1, sizeof err, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "orthonormality check");
+        if (!(err <= h->check_ortho_tol)) {
+            char b[128];
+            snprintf(b, sizeof b, "||U^T U - I||_F = %.3e exceeds %.3e", err, h->check_ortho_tol);
+            return fail(h, DMRG_ERR_NOT_ORTHONORMAL, b);
+        }
+    }
+    char key[256];
+    snprintf(key, sizeof key, "dense:%p:%p:%p:%p:%p:%lld:%lld:%d:%lld:%d:%d", (const void*)U, O,
+             Oout, ws, (void*)s, (long long)K, (long long)m, d, (long long)mp, int(p), in_is_fp64);
+    return run_maybe_graph(h, key, s, [&](cudaStream_t cs) -> dmrg_status {
+        if (!tc) return dense_simt_forward(h, U, m, d, mp, O, in_is_fp64, K, Oout, p, ws, cs);
+        const TcMode mode = (p == DMRG_PREC_BF16X3) ? TC_BF16X3 : TC_TF32;
+        const TcConfig c1 = tuned_config(h, shape_key("g1", K, m, d, mp, p), mode);
+        const TcConfig c2 = tuned_config(h, shape_key("g2", K, m, d, mp, p), mode);
+        return dense_tc_forward(h, U, m, d, mp, O, in_is_fp64, K, Oout, p, ws, c1, c2, cs);
+    });
+}
+
+dmrg_status dmrg_orthonormality_error_workspace(dmrg_handle h, int64_t rows, int64_t mp,
+                                                size_t* bytes) {
+    if (!h || !bytes) return DMRG_ERR_INVALID_ARG;
+    if (rows < 1 || mp < 1) return fail(h, DMRG_ERR_SHAPE, "need rows >= 1 and mp >= 1");
+    *bytes = 256;
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_orthonormality_error(dmrg_handle h, const double* U, int64_t rows, int64_t mp,
+                                      double* out, void* ws, size_t ws_bytes,
+                                      dmrg_stream_t stream) {
+    if (!h) return DMRG_ERR_INVALID_ARG;
+    if (rows < 1 || mp < 1) return fail(h, DMRG_ERR_SHAPE, "need rows >= 1 and mp >= 1");
+    if (!U || !out) return fail(h, DMRG_ERR_INVALID_ARG, "null pointer");
+    dmrg_status st = check_ws(h, ws, ws_bytes, 256);
+    if (st != DMRG_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    double* acc = static_cast<double*>(ws);
+    cudaError_t e = timed_launch(h, "ortho_error", s,
+                                 [&] { return ortho_error_launch(U, rows, mp, acc, out, s); });
+    return cuda_fail(h, e, "orthonormality error");
+}
+
+dmrg_status dmrg_correlations_workspace(dmrg_handle h, int64_t K, int64_t mp, size_t* bytes) {
+    if (!h || !bytes) return DMRG_ERR_INVALID_ARG;
+    if (K < 0 || mp < 1) return fail(h, DMRG_ERR_SHAPE, "need K >= 0 and mp >= 1");
+    WsLayout W;
+    W.add("x", size_t(K) * mp * 8);
+    W.add("y", size_t(K) * mp * 8);
+    *bytes = W.total;
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_correlations(dmrg_handle h, const void* Op, int in_is_fp64, const double* psi,
+                              int64_t K, int64_t mp, double* C, void* ws, size_t ws_bytes,
+                              dmrg_stream_t stream) {
+    if (!h) return DMRG_ERR_INVALID_ARG;
+    if (K < 0 || mp < 1) return fail(h, DMRG_ERR_SHAPE, "need K >= 0 and mp >= 1");
+    if (K == 0) return DMRG_OK;
+    if (!Op || !psi || !C) return fail(h, DMRG_ERR_INVALID_ARG, "null pointer");
+    WsLayout W;
+    W.add("x", size_t(K) * mp * 8);
+    W.add("y", size_t(K) * mp * 8);
+    dmrg_status st = check_ws(h, ws, ws_bytes, W.total);
+    if (st != DMRG_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    double* x = reinterpret_cast<double*>(static_cast<char*>(ws) + W.offsets[0]);
+    double* y = reinterpret_cast<double*>(static_cast<char*>(ws) + W.offsets[1]);
+    cudaError_t e = timed_launch(h, "corr_matvec", s, [&] {
+        return corr_matvec_launch(Op, in_is_fp64 != 0, psi, K, mp, x, y, s);
+    });
+    if (e != cudaSuccess) return cuda_fail(h, e, "correlation mat-vecs");
+    // C = X Y^T: C[i][j] = sum_g x[i][g] y[j][g]
+    SimtGemm g{};
+    g.A = x; g.B = y; g.C = C;
+    g.M = K; g.N = K; g.K = mp;
+    g.sAi = mp; g.sAk = 1;
+    g.sBk = 1; g.sBj = mp;
+    g.sCi = K; g.sCj = 1;
+    g.batch = 1;
+    e = timed_launch(h, "corr_gemm", s, [&] { return simt_gemm_launch(Real::F64, g, s); });
+    return cuda_fail(h, e, "correlation contraction");
+}
+
+}  // extern "C"

@@ -1,0 +1,47 @@
+// api_common.h -- helpers shared by the host translation units of the C ABI.
+#pragma once
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace dmrg {
+
+// Sections of a caller workspace, each 256-byte aligned.
+struct WsLayout {
+    std::vector<size_t> offsets;
+    size_t total = 0;
+    void add(const char* name, size_t bytes);
+};
+
+struct DenseDims {
+    int64_t K, m, mp, md, ld1, ld2;
+    int d;
+    WsLayout ws;
+};
+
+dmrg_status fail(dmrg_handle h, dmrg_status st, const std::string& msg);
+dmrg_status cuda_fail(dmrg_handle h, cudaError_t e, const char* where);
+cudaError_t timed_launch(dmrg_handle h, const char* name, cudaStream_t s,
+                         const std::function<cudaError_t()>& f);
+size_t align_up(size_t x, size_t a);
+bool tc_supported(dmrg_handle h);
+uint64_t timeout_ns(dmrg_handle h);
+dmrg_status run_maybe_graph(dmrg_handle h, const std::string& key, cudaStream_t stream,
+                            const std::function<dmrg_status(cudaStream_t)>& body);
+DenseDims dense_dims(int64_t K, int64_t m, int d, int64_t mp, dmrg_precision p);
+dmrg_status check_dense_args(dmrg_handle h, int64_t K, int64_t m, int d, int64_t mp,
+                             dmrg_precision p);
+dmrg_status check_ws(dmrg_handle h, const void* ws, size_t have, size_t need);
+TcConfig tuned_config(dmrg_handle h, const std::string& key, TcMode mode);
+std::string shape_key(const char* tag, int64_t K, int64_t m, int d, int64_t mp, dmrg_precision p);
+dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
+                             const void* O, int in_is_fp64, int64_t K, void* Oout,
+                             dmrg_precision p, void* ws, const TcConfig& c1, const TcConfig& c2,
+                             cudaStream_t s);
+
+cudaError_t tc_gemm_launch_grouped(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
+                                   int bn_smem, cudaStream_t s);
+
+}  // namespace dmrg

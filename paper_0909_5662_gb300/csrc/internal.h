@@ -1,0 +1,171 @@
+// internal.h -- host-side structures shared by the translation units of the library.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/dmrg_rotate.h"
+
+namespace dmrg {
+
+// ---------------------------------------------------------------- SIMT GEMM
+// C[b](i, j) (+)= sum_k A[b](i, k) * B[b](k, j) with arbitrary element strides.
+// Used by the FP64 and FP32 paths (plain FMA, no tensor cores).
+struct SimtGemm {
+    const void* A;
+    const void* B;
+    void* C;
+    int64_t M, N, K;
+    int64_t sAb, sAi, sAk;
+    int64_t sBb, sBk, sBj;
+    int64_t sCb, sCi, sCj;
+    int32_t accumulate;   // 1: C += A B, 0: C = A B
+    int32_t tile_start;   // first tile (grouped launches)
+    int32_t tiles_m, tiles_n;
+    int32_t batch;
+};
+
+enum class Real { F64, F32 };
+
+// Launches one batched GEMM (or a grouped list already in device memory).
+cudaError_t simt_gemm_launch(Real t, const SimtGemm& g, cudaStream_t s);
+cudaError_t simt_gemm_grouped_launch(Real t, const SimtGemm* d_problems, int nprob,
+                                     int total_tiles, cudaStream_t s);
+int simt_tile_m();
+int simt_tile_n();
+
+// Fused ||U^T U - I||_F: G = U^T U tile-wise, squares of (G - I) reduced into
+// *acc (device double, zeroed inside), then sqrt into *out.
+cudaError_t ortho_error_launch(const double* U, int64_t rows, int64_t mp, double* acc, double* out,
+                               cudaStream_t s);
+// x_k = O'_k^T psi and y_k = O'_k psi (FP64 results) for every k.
+cudaError_t corr_matvec_launch(const void* Op, bool f64, const double* psi, int64_t K, int64_t mp,
+                               double* x, double* y, cudaStream_t s);
+// dO-style partial trace helper etc. live in the api translation unit.
+cudaError_t convert_f32_to_f64_launch(const float* src, double* dst, int64_t n, cudaStream_t s);
+cudaError_t fill_zero_launch(void* p, size_t bytes, cudaStream_t s);
+
+// ---------------------------------------------------------------- tensor-core GEMM
+// One grouped GEMM problem for the tcgen05 kernel: D (M x N) = A (M x Kred) B (N x Kred)^T,
+// both operands K-major, stored as BF16 hi/lo pairs (BF16X3) or FP32 (TF32).
+// The epilogue scatters element (row R, col n) to
+//   out + out_off + (op_off ? op_off[R / rows_per_op] : (R / rows_per_op) * s_op)
+//       + (R % rows_per_op) * s_row + (n / col_div) * s_col_hi + (n % col_div) * s_col_lo.
+struct TcProblem {  // 64-byte aligned through its CUtensorMap members
+    CUtensorMap tmA[2];  // hi, lo (lo unused for TF32)
+    CUtensorMap tmB[2];
+    int32_t M, N, Kred;
+    int32_t tile_n;      // N tile width (multiple of 16, <= 256)
+    int32_t m_tiles, n_tiles, k_splits, kb_per_split;
+    int32_t tile_start;  // first global tile of this problem
+    int32_t rows_per_op;
+    int32_t col_div;
+    int32_t pad0;
+    int64_t out_off;
+    int64_t s_op, s_row, s_col_hi, s_col_lo;
+    const int64_t* op_off;
+};
+
+enum TcMode : int { TC_BF16X3 = 0, TC_TF32 = 1, TC_BF16 = 2 };
+enum TcEpi : int { EPI_SPLIT_BF16 = 0, EPI_TF32 = 1, EPI_F32 = 2, EPI_F32_ATOMIC = 3 };
+
+struct TcConfig {
+    int tile_n_max = 256;   // upper bound on the N tile (the split picks <= this)
+    int stages = 3;
+    int grid = 0;           // 0 = number of SMs
+    bool operator==(const TcConfig& o) const {
+        return tile_n_max == o.tile_n_max && stages == o.stages && grid == o.grid;
+    }
+};
+
+struct TcLaunch {
+    TcProblem inline_prob;        // used when table == nullptr
+    const TcProblem* table;       // grouped problems in device memory
+    int32_t nprob;
+    int32_t total_tiles;
+    void* out0;                   // FP32 output / BF16 hi output / TF32 output
+    void* out1;                   // BF16 lo output
+    unsigned* status;
+    uint64_t timeout_ns;
+};
+
+cudaError_t tc_gemm_launch(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
+                           cudaStream_t s);
+int tc_max_stages(TcMode mode, int tile_n_max);
+
+// Encodes a 2-D K-major operand map: rows x cols (cols = reduction, contiguous),
+// row stride ld elements, box = box_rows x (128 bytes of cols), 128-byte swizzle.
+bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t rows, int64_t cols,
+                        int64_t ld, int box_rows);
+// Chooses an N tile (multiple of 16, <= tile_n_max) that splits N evenly.
+int choose_tile_n(int64_t N, int tile_n_max);
+// Fills the tiling fields of a problem (tile counts, splits) for a reduction.
+void finish_problem(TcProblem& p, int64_t M, int64_t N, int64_t Kred, int tile_n, int k_splits,
+                    TcMode mode);
+
+// ---------------------------------------------------------------- packer
+// Gathers and converts a strided source matrix into K-major tensor-core
+// operands: dst row r, column c  <-  src[base + op_part(r) + (r % rdiv') ...].
+// For row r: g = r / rows_per_op (operand group), rr = r % rows_per_op;
+//   src index = src_off + (op_off ? op_off[g] : g * s_op) + (rr / rdiv) * s_r_hi
+//               + (rr % rdiv) * s_r_lo + c * s_c.
+struct PackJob {
+    const void* src;
+    int32_t src_f64;
+    int32_t mode;          // 0: BF16 hi/lo pair, 1: FP32 rounded to TF32
+    int64_t rows, cols;
+    int64_t src_off;
+    int64_t rows_per_op;
+    int64_t s_op;
+    const int64_t* op_off;
+    int64_t rdiv, s_r_hi, s_r_lo, s_c;
+    void* dst0;            // hi (BF16) or TF32 (FP32)
+    void* dst1;            // lo (BF16)
+    int64_t ld;            // dst row stride in elements
+    int64_t block_start;   // first CUDA block of this job (grouped launch)
+};
+cudaError_t pack_launch(const PackJob* jobs_host, int njobs, PackJob* jobs_dev_or_null,
+                        cudaStream_t s);
+int64_t pack_blocks_for(const PackJob& j);
+cudaError_t pack_grouped_launch(const PackJob* jobs_dev, int njobs, int64_t total_blocks,
+                                cudaStream_t s);
+
+// ---------------------------------------------------------------- backward helpers
+cudaError_t f32_to_f64_strided_launch(const float* src, double* dst, int64_t n, cudaStream_t s);
+
+}  // namespace dmrg
+
+// ---------------------------------------------------------------- handle
+struct dmrg_handle_s {
+    int device = 0;
+    int num_sms = 0;
+    int cc_major = 0, cc_minor = 0;
+    unsigned* d_status = nullptr;   // device status word (+ scratch doubles after it)
+    double* d_scratch = nullptr;    // 8 doubles of scratch for reductions
+    std::string last_error;
+    bool graph_mode = false;
+    bool timing = false;
+    double wait_timeout_ms = 2000.0;
+    double check_ortho_tol = 0.0;
+
+    struct Timed {
+        std::string name;
+        cudaEvent_t a, b;
+    };
+    std::vector<Timed> pending;
+    std::vector<cudaEvent_t> event_pool;
+    std::map<std::string, std::pair<long, double>> timing_acc;
+
+    std::map<std::string, dmrg::TcConfig> tune_cache;
+    bool tune_cache_loaded = false;
+
+    std::map<std::string, cudaGraphExec_t> graphs;
+    cudaStream_t capture_stream = nullptr;
+    bool capturing = false;
+};
+
+struct dmrg_blocked_plan_s;

@@ -1,0 +1,540 @@
+// tc.cu -- tcgen05 tensor-core GEMM pipeline and operand packer (sm_103a).
+//
+// Both products of the rotation (Sec. 3.2: Z R^+ then R (Z R^+)) run through one
+// persistent, warp-specialised kernel:
+//   warp 0   : TMA producer  -- 128-byte-swizzled K-major tiles of A and B into a
+//              ring of shared-memory stages (cp.async.bulk.tensor, mbarrier tx count);
+//   warp 1   : MMA issuer    -- one thread issues tcgen05.mma (M = 128, N <= 256)
+//              into one of two TMEM accumulators, tcgen05.commit frees the stage;
+//   warps 2-5: epilogue      -- tcgen05.ld of the finished accumulator, conversion
+//              (FP32 / TF32 / BF16 hi-lo split) and a strided scatter to global memory,
+//              overlapping the next tile's main loop.
+// Precision forms: BF16x3 (A = Ah + Al, B = Bh + Bl, D += Al Bh + Ah Bl + Ah Bh with
+// FP32 accumulation), TF32 (kind::tf32) and plain BF16 (one product, for comparison).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace dmrg {
+namespace {
+
+constexpr int kThreads = 192;        // 6 warps
+constexpr int kBM = 128;             // rows per tile (TMEM lanes)
+constexpr int kRowBytes = 128;       // one swizzle row: 64 BF16 or 32 FP32 of the reduction
+constexpr uint32_t kTmemCols = 512;  // two accumulators of up to 256 FP32 columns
+constexpr uint32_t kAccStride = 256;
+
+struct Decoded {
+    const TcProblem* P;
+    int mt, nt, kb_begin, kb_end;
+};
+
+__device__ __forceinline__ Decoded decode_tile(const TcLaunch& L, int t, int elems_per_row) {
+    const TcProblem* P = &L.inline_prob;
+    if (L.table != nullptr) {
+        int lo = 0, hi = L.nprob - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (L.table[mid].tile_start <= t) lo = mid; else hi = mid - 1;
+        }
+        P = &L.table[lo];
+    }
+    Decoded d;
+    d.P = P;
+    const int local = t - P->tile_start;
+    const int per_split = P->m_tiles * P->n_tiles;
+    const int ks = local / per_split;
+    const int rem = local - ks * per_split;
+    d.mt = rem / P->n_tiles;
+    d.nt = rem - d.mt * P->n_tiles;
+    const int kb_total = (P->Kred + elems_per_row - 1) / elems_per_row;
+    d.kb_begin = ks * P->kb_per_split;
+    d.kb_end = min(kb_total, d.kb_begin + P->kb_per_split);
+    return d;
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+template <int MODE, int EPI>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ TcLaunch L, int stages, int bn_smem) {
+    constexpr bool kSplit = (MODE == TC_BF16X3);
+    constexpr int kElem = (MODE == TC_TF32) ? 4 : 2;
+    constexpr int kElemsPerRow = kRowBytes / kElem;      // reduction elements per k-block
+    constexpr int kUmmaK = 32 / kElem;                   // reduction elements per MMA
+    constexpr int kStepsPerBlock = kElemsPerRow / kUmmaK;  // 4
+    constexpr uint32_t kFmt = (MODE == TC_TF32) ? 2u : 1u;
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t a_bytes = kBM * kRowBytes;
+    const uint32_t b_bytes = uint32_t(bn_smem) * kRowBytes;
+    const uint32_t stage_bytes = (a_bytes + b_bytes) * (kSplit ? 2 : 1);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + size_t(stages) * stage_bytes);
+    uint64_t* empty = full + stages;
+    uint64_t* tfull = empty + stages;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* drain = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 4);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) tmem_alloc<kTmemCols>(tmem_slot);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    volatile int* vabort = abort_flag;
+    const uint64_t tmo = L.timeout_ns;
+
+    auto stage_a = [&](int s, int half) -> uint8_t* {
+        return smem + size_t(s) * stage_bytes + size_t(half) * (a_bytes + b_bytes);
+    };
+    auto stage_b = [&](int s, int half) -> uint8_t* { return stage_a(s, half) + a_bytes; };
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            if (L.table == nullptr) {
+                tma_prefetch_desc(&L.inline_prob.tmA[0]);
+                tma_prefetch_desc(&L.inline_prob.tmB[0]);
+                if (kSplit) {
+                    tma_prefetch_desc(&L.inline_prob.tmA[1]);
+                    tma_prefetch_desc(&L.inline_prob.tmB[1]);
+                }
+            }
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t armed = 0;  // bit s: stage s holds an issued, unconfirmed load
+            uint32_t armed_parity = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < L.total_tiles && ok; t += gridDim.x) {
+                const Decoded dt = decode_tile(L, t, kElemsPerRow);
+                const TcProblem* P = dt.P;
+                const uint32_t bytes =
+                    (a_bytes + uint32_t(P->tile_n) * kRowBytes) * (kSplit ? 2u : 1u);
+                const int ya = dt.mt * kBM;
+                const int yb = dt.nt * P->tile_n;
+                for (int kb = dt.kb_begin; kb < dt.kb_end; ++kb) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, tmo, L.status, vabort)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[stage], bytes);
+                    const int x = kb * kElemsPerRow;
+                    tma_load_2d(stage_a(stage, 0), &P->tmA[0], &full[stage], x, ya);
+                    tma_load_2d(stage_b(stage, 0), &P->tmB[0], &full[stage], x, yb);
+                    if (kSplit) {
+                        tma_load_2d(stage_a(stage, 1), &P->tmA[1], &full[stage], x, ya);
+                        tma_load_2d(stage_b(stage, 1), &P->tmB[1], &full[stage], x, yb);
+                    }
+                    armed |= 1u << stage;
+                    armed_parity = (armed_parity & ~(1u << stage)) | (phase << stage);
+                    if (++stage == stages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            // Never leave the CTA with bulk copies still landing in shared memory.
+            for (int s = 0; s < stages; ++s)
+                if (armed & (1u << s)) {
+                    volatile int never = 0;
+                    mbar_wait(&full[s], (armed_parity >> s) & 1u, tmo, L.status,
+                              reinterpret_cast<volatile int*>(&never));
+                }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < L.total_tiles && ok; t += gridDim.x, ++it) {
+                const Decoded dt = decode_tile(L, t, kElemsPerRow);
+                const TcProblem* P = dt.P;
+                const int acc = it & 1;
+                const uint32_t acc_parity = uint32_t(it >> 1) & 1u;
+                if (!mbar_wait(&tempty[acc], acc_parity ^ 1u, tmo, L.status, vabort)) break;
+                tc_fence_after();
+                const uint32_t tmem_d = tmem_base + uint32_t(acc) * kAccStride;
+                int n_eff = min(P->tile_n, P->N - dt.nt * P->tile_n);
+                n_eff = (n_eff + 15) & ~15;
+                const uint32_t idesc = make_idesc(kFmt, uint32_t(n_eff));
+                for (int kb = dt.kb_begin; kb < dt.kb_end; ++kb) {
+                    if (!mbar_wait(&full[stage], phase, tmo, L.status, vabort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const int rem = P->Kred - kb * kElemsPerRow;
+                    const int steps = min(kStepsPerBlock, (rem + kUmmaK - 1) / kUmmaK);
+                    const uint64_t ah = smem_desc_sw128(smem_u32(stage_a(stage, 0)));
+                    const uint64_t bh = smem_desc_sw128(smem_u32(stage_b(stage, 0)));
+                    const uint64_t al = kSplit ? smem_desc_sw128(smem_u32(stage_a(stage, 1))) : 0;
+                    const uint64_t bl = kSplit ? smem_desc_sw128(smem_u32(stage_b(stage, 1))) : 0;
+                    for (int k = 0; k < steps; ++k) {
+                        const uint64_t off = uint64_t(k) * 2;  // 32 bytes in 16-byte units
+                        const uint32_t accum = (kb > dt.kb_begin || k > 0) ? 1u : 0u;
+                        if (MODE == TC_BF16X3) {
+                            mma_bf16(tmem_d, al + off, bh + off, idesc, accum);
+                            mma_bf16(tmem_d, ah + off, bl + off, idesc, 1u);
+                            mma_bf16(tmem_d, ah + off, bh + off, idesc, 1u);
+                        } else if (MODE == TC_TF32) {
+                            mma_tf32(tmem_d, ah + off, bh + off, idesc, accum);
+                        } else {
+                            mma_bf16(tmem_d, ah + off, bh + off, idesc, accum);
+                        }
+                    }
+                    mma_commit(&empty[stage]);
+                    if (++stage == stages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(&tfull[acc]);
+            }
+            // Every issued MMA has finished before TMEM is released.
+            mma_commit(drain);
+            volatile int never = 0;
+            mbar_wait(drain, 0, tmo, L.status, reinterpret_cast<volatile int*>(&never));
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue (warps 2..5)
+        const int quad = warp & 3;  // TMEM lanes [32*quad, 32*quad + 32)
+        int it = 0;
+        for (int t = blockIdx.x; t < L.total_tiles; t += gridDim.x, ++it) {
+            const Decoded dt = decode_tile(L, t, kElemsPerRow);
+            const TcProblem* P = dt.P;
+            const int acc = it & 1;
+            const uint32_t acc_parity = uint32_t(it >> 1) & 1u;
+            if (!mbar_wait(&tfull[acc], acc_parity, tmo, L.status, vabort)) break;
+            tc_fence_after();
+            const int row = dt.mt * kBM + quad * 32 + lane;
+            const bool row_ok = row < P->M;
+            int64_t row_base = 0;
+            if (row_ok) {
+                const int g = row / P->rows_per_op;
+                const int rr = row - g * P->rows_per_op;
+                row_base = P->out_off + (P->op_off ? P->op_off[g] : int64_t(g) * P->s_op) +
+                           int64_t(rr) * P->s_row;
+            }
+            const int n0 = dt.nt * P->tile_n;
+            const int ncols = min(P->tile_n, P->N - n0);
+            const int cdiv = P->col_div;
+            const int64_t sch = P->s_col_hi, scl = P->s_col_lo;
+            const bool vec4 = (EPI == EPI_SPLIT_BF16) && cdiv == 4 && scl == 1 &&
+                              ((row_base & 3) == 0) && ((sch & 3) == 0);
+            for (int c = 0; c < ncols; c += 32) {
+                uint32_t r[32];
+                tmem_ld_32x32b_x32(tmem_base + uint32_t(acc) * kAccStride +
+                                       (uint32_t(quad * 32) << 16) + uint32_t(c),
+                                   r);
+                tmem_ld_wait();
+                if (!row_ok) continue;
+                const int cmax = min(32, ncols - c);
+                if (EPI == EPI_SPLIT_BF16) {
+                    __nv_bfloat16* hi = static_cast<__nv_bfloat16*>(L.out0);
+                    __nv_bfloat16* lo = static_cast<__nv_bfloat16*>(L.out1);
+                    if (vec4 && cmax == 32) {
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4) {
+                            const int n = n0 + c + j;
+                            const int64_t idx = row_base + int64_t(n >> 2) * sch;
+                            __nv_bfloat16 h[4], l[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const float v = __uint_as_float(r[j + e]);
+                                h[e] = __float2bfloat16_rn(v);
+                                l[e] = __float2bfloat16_rn(v - __bfloat162float(h[e]));
+                            }
+                            uint2 hv, lv;
+                            hv.x = uint32_t(__bfloat16_as_ushort(h[0])) |
+                                   (uint32_t(__bfloat16_as_ushort(h[1])) << 16);
+                            hv.y = uint32_t(__bfloat16_as_ushort(h[2])) |
+                                   (uint32_t(__bfloat16_as_ushort(h[3])) << 16);
+                            lv.x = uint32_t(__bfloat16_as_ushort(l[0])) |
+                                   (uint32_t(__bfloat16_as_ushort(l[1])) << 16);
+                            lv.y = uint32_t(__bfloat16_as_ushort(l[2])) |
+                                   (uint32_t(__bfloat16_as_ushort(l[3])) << 16);
+                            *reinterpret_cast<uint2*>(hi + idx) = hv;
+                            *reinterpret_cast<uint2*>(lo + idx) = lv;
+                        }
+                    } else {
+                        for (int j = 0; j < cmax; ++j) {
+                            const int n = n0 + c + j;
+                            const int64_t idx = row_base + int64_t(n / cdiv) * sch +
+                                                int64_t(n % cdiv) * scl;
+                            const float v = __uint_as_float(r[j]);
+                            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                            hi[idx] = h;
+                            lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+                        }
+                    }
+                } else {
+                    float* out = static_cast<float*>(L.out0);
+#pragma unroll 4
+                    for (int j = 0; j < cmax; ++j) {
+                        const int n = n0 + c + j;
+                        const int64_t idx =
+                            row_base + int64_t(n / cdiv) * sch + int64_t(n % cdiv) * scl;
+                        const float v = __uint_as_float(r[j]);
+                        if (EPI == EPI_F32) out[idx] = v;
+                        else if (EPI == EPI_TF32) out[idx] = tf32_round(v);
+                        else atomicAdd(out + idx, v);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc<kTmemCols>(tmem_base);
+    }
+}
+
+// ---------------------------------------------------------------- packer
+struct PackLaunch {
+    PackJob inline_jobs[4];
+    const PackJob* table;
+    int njobs;
+};
+
+constexpr int kPackThreads = 256;
+constexpr int kPackElems = 4;  // elements per thread
+
+__device__ __forceinline__ void pack_store(const PackJob& j, int64_t dst, double x) {
+    if (j.mode == 0) {
+        const __nv_bfloat16 h = __double2bfloat16(x);
+        const __nv_bfloat16 l = __double2bfloat16(x - double(__bfloat162float(h)));
+        static_cast<__nv_bfloat16*>(j.dst0)[dst] = h;
+        static_cast<__nv_bfloat16*>(j.dst1)[dst] = l;
+    } else if (j.mode == 1) {
+        static_cast<float*>(j.dst0)[dst] = tf32_round(float(x));
+    } else {
+        static_cast<float*>(j.dst0)[dst] = float(x);
+    }
+}
+
+__global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constant__ PackLaunch L) {
+    const int b = blockIdx.x;
+    const PackJob* J = nullptr;
+    if (L.table == nullptr) {
+        int k = 0;
+        for (int i = 1; i < L.njobs; ++i)
+            if (L.inline_jobs[i].block_start <= b) k = i;
+        J = &L.inline_jobs[k];
+    } else {
+        int lo = 0, hi = L.njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (L.table[mid].block_start <= b) lo = mid; else hi = mid - 1;
+        }
+        J = &L.table[lo];
+    }
+    const PackJob& j = *J;
+    const int64_t total = j.rows * j.cols;
+    const int64_t e0 = (int64_t(b - j.block_start) * kPackThreads + threadIdx.x) * kPackElems;
+#pragma unroll
+    for (int q = 0; q < kPackElems; ++q) {
+        const int64_t e = e0 + q;
+        if (e >= total) break;
+        const int64_t r = e / j.cols;
+        const int64_t c = e - r * j.cols;
+        const int64_t g = r / j.rows_per_op;
+        const int64_t rr = r - g * j.rows_per_op;
+        const int64_t src = j.src_off + (j.op_off ? j.op_off[g] : g * j.s_op) +
+                            (rr / j.rdiv) * j.s_r_hi + (rr % j.rdiv) * j.s_r_lo + c * j.s_c;
+        const double x = j.src_f64 ? static_cast<const double*>(j.src)[src]
+                                   : double(static_cast<const float*>(j.src)[src]);
+        pack_store(j, r * j.ld + c, x);
+    }
+}
+
+template <int MODE, int EPI>
+cudaError_t launch_one(const TcLaunch& L, int stages, int grid, int bn_smem, size_t smem,
+                       cudaStream_t s) {
+    auto k = tc_gemm_kernel<MODE, EPI>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    k<<<grid, kThreads, smem, s>>>(L, stages, bn_smem);
+    return cudaGetLastError();
+}
+
+size_t tc_smem_bytes(TcMode mode, int stages, int bn) {
+    const size_t a = size_t(kBM) * kRowBytes, b = size_t(bn) * kRowBytes;
+    const size_t stage = (a + b) * (mode == TC_BF16X3 ? 2 : 1);
+    return 1024 + stage * stages + 8 * (2 * size_t(stages) + 5) + 16;
+}
+
+}  // namespace
+
+int tc_max_stages(TcMode mode, int tile_n_max) {
+    int s = 1;
+    while (s < 8 && tc_smem_bytes(mode, s + 1, tile_n_max) <= 232448) ++s;
+    return s;
+}
+
+cudaError_t tc_gemm_launch(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
+                           cudaStream_t s) {
+    if (L.total_tiles <= 0) return cudaSuccess;
+    int bn = 16;
+    if (L.table == nullptr) {
+        bn = L.inline_prob.tile_n;
+    } else {
+        return cudaErrorInvalidValue;  // grouped launches go through tc_gemm_launch_bn
+    }
+    const size_t smem = tc_smem_bytes(mode, stages, bn);
+    if (smem > 232448) return cudaErrorInvalidConfiguration;
+    grid = std::max(1, std::min(grid, L.total_tiles));
+#define DMRG_TC_CASE(M, E) \
+    if (mode == M && epi == E) return launch_one<M, E>(L, stages, grid, bn, smem, s);
+    DMRG_TC_CASE(TC_BF16X3, EPI_SPLIT_BF16)
+    DMRG_TC_CASE(TC_BF16X3, EPI_F32)
+    DMRG_TC_CASE(TC_BF16X3, EPI_F32_ATOMIC)
+    DMRG_TC_CASE(TC_TF32, EPI_TF32)
+    DMRG_TC_CASE(TC_TF32, EPI_F32)
+    DMRG_TC_CASE(TC_TF32, EPI_F32_ATOMIC)
+    DMRG_TC_CASE(TC_BF16, EPI_F32)
+#undef DMRG_TC_CASE
+    return cudaErrorNotSupported;
+}
+
+cudaError_t tc_gemm_launch_grouped(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
+                                   int bn_smem, cudaStream_t s) {
+    if (L.total_tiles <= 0) return cudaSuccess;
+    const size_t smem = tc_smem_bytes(mode, stages, bn_smem);
+    if (smem > 232448) return cudaErrorInvalidConfiguration;
+    grid = std::max(1, std::min(grid, L.total_tiles));
+#define DMRG_TC_CASE(M, E) \
+    if (mode == M && epi == E) return launch_one<M, E>(L, stages, grid, bn_smem, smem, s);
+    DMRG_TC_CASE(TC_BF16X3, EPI_SPLIT_BF16)
+    DMRG_TC_CASE(TC_BF16X3, EPI_F32)
+    DMRG_TC_CASE(TC_BF16X3, EPI_F32_ATOMIC)
+#undef DMRG_TC_CASE
+    return cudaErrorNotSupported;
+}
+
+int64_t pack_blocks_for(const PackJob& j) {
+    const int64_t per = int64_t(kPackThreads) * kPackElems;
+    return (j.rows * j.cols + per - 1) / per;
+}
+
+cudaError_t pack_launch(const PackJob* jobs, int njobs, PackJob* /*unused*/, cudaStream_t s) {
+    if (njobs <= 0) return cudaSuccess;
+    if (njobs > 4) return cudaErrorInvalidValue;
+    PackLaunch L{};
+    int64_t blocks = 0;
+    for (int i = 0; i < njobs; ++i) {
+        L.inline_jobs[i] = jobs[i];
+        L.inline_jobs[i].block_start = blocks;
+        blocks += pack_blocks_for(jobs[i]);
+    }
+    L.table = nullptr;
+    L.njobs = njobs;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    pack_kernel<<<unsigned(blocks), kPackThreads, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t pack_grouped_launch(const PackJob* jobs_dev, int njobs, int64_t total_blocks,
+                                cudaStream_t s) {
+    if (njobs <= 0 || total_blocks <= 0) return cudaSuccess;
+    PackLaunch L{};
+    L.table = jobs_dev;
+    L.njobs = njobs;
+    pack_kernel<<<unsigned(total_blocks), kPackThreads, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- host helpers
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+}
+
+bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t rows, int64_t cols,
+                        int64_t ld, int box_rows) {
+    if (g_encode == nullptr) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || fn == nullptr)
+            return false;
+        g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const int esize = fp32 ? 4 : 2;
+    cuuint64_t gdim[2] = {cuuint64_t(cols), cuuint64_t(rows)};
+    cuuint64_t gstride[1] = {cuuint64_t(ld) * esize};
+    cuuint32_t box[2] = {cuuint32_t(kRowBytes / esize), cuuint32_t(box_rows)};
+    cuuint32_t estride[2] = {1, 1};
+    CUresult r = g_encode(map, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                          2, const_cast<void*>(base), gdim, gstride, box, estride,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int choose_tile_n(int64_t N, int tile_n_max) {
+    const int64_t ntiles = (N + tile_n_max - 1) / tile_n_max;
+    int64_t t = (N + ntiles - 1) / ntiles;
+    t = (t + 15) / 16 * 16;
+    if (t > tile_n_max) t = tile_n_max;
+    if (t < 16) t = 16;
+    return int(t);
+}
+
+void finish_problem(TcProblem& p, int64_t M, int64_t N, int64_t Kred, int tile_n, int k_splits,
+                    TcMode mode) {
+    const int elems = (mode == TC_TF32) ? 32 : 64;
+    p.M = int32_t(M);
+    p.N = int32_t(N);
+    p.Kred = int32_t(Kred);
+    p.tile_n = tile_n;
+    p.m_tiles = int32_t((M + kBM - 1) / kBM);
+    p.n_tiles = int32_t((N + tile_n - 1) / tile_n);
+    const int kb_total = int((Kred + elems - 1) / elems);
+    if (k_splits < 1) k_splits = 1;
+    if (k_splits > kb_total) k_splits = kb_total;
+    p.kb_per_split = (kb_total + k_splits - 1) / k_splits;
+    p.k_splits = (kb_total + p.kb_per_split - 1) / p.kb_per_split;
+}
+
+}  // namespace dmrg
