@@ -1,0 +1,392 @@
+#!/usr/bin/env python3
+"""Benchmark of the DMRG operator rotation O'_k = U^T (O_k (x) I_d) U on GB300.
+
+Workload (one "step" = one rotation of the whole operator batch): the dense
+Hubbard-shaped step d = 4, m = 400 -> m*d = 1600 -> m' = 400, K = 150
+operators per GPU (50 sites x {n_up-like, two dense}), seeded synthetic
+inputs resident in HBM, L2 flushed (512 MiB write) between timed steps.
+The headline precision is BF16x3; TF32 and the plain FP64 GPU path are timed
+on the same inputs and reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank rotates its uniform-matrix-distribution slice of
+K*N operators (no collective on the data path); value = all operators / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rotated operators/s and eff. TFLOP/s (BF16×3, TF32 vs FP64 path) at m=400,K=150"
+UNIT = "rotated operators/s"
+WORKLOAD = "dense_m400_k150"
+D, M, MP, K_PER_GPU = 4, 400, 400, 150
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+KERNEL_SOURCES = ["paper_0909_5662_gb300/csrc/tc.cu", "paper_0909_5662_gb300/csrc/ptx.cuh",
+                  "paper_0909_5662_gb300/csrc/internal.h"]
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        loaded = [s for s, p in zip(sm, power) if p > 300] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def traffic_for(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None
+    if absent or taken on a different version of the kernel sources."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if data.get("source_hash") != kernel_source_hash():
+        return None
+    ent = data.get("kernels", {}).get(kernel)
+    return None if ent is None else ent.get("bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------- CPU oracle leg
+def cpu_oracle_sample(w, budget_s: float = 12.0, max_ops: int = 150):
+    """The FP64 CPU oracle as it stands, on host cores, on a bounded sample of the
+    same workload: operators 0.. of the batch until about budget_s of work."""
+    import oracle
+    oracle.build()
+    cores = oracle.num_threads()
+    n = min(max_ops, max(cores, 8))
+    t0 = time.perf_counter()
+    oracle.rotate_dense(w.U, w.O[:n], w.d)
+    dt = time.perf_counter() - t0
+    done, total_t = n, dt
+    while total_t < budget_s and done < 4 * max_ops:
+        n2 = min(max_ops, max(cores, int(n * max(1.0, (budget_s - total_t) / max(dt, 1e-3)))))
+        t0 = time.perf_counter()
+        oracle.rotate_dense(w.U, w.O[:n2], w.d)
+        dt = time.perf_counter() - t0
+        done += n2
+        total_t += dt
+        n = n2
+    return {"value": done / total_t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d rotations of the first operators of %s (FP64 loops, UMD split over "
+                      "%d OpenMP threads), %.1f s" % (done, WORKLOAD, cores, total_t)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from workloads import dense_config
+    w = dense_config(WORKLOAD)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; keep the arm's shape
+    res = cpu_oracle_sample(w, budget_s=max(10.0, 3.0 * args.steps), max_ops=K_PER_GPU)
+    v = res["value"]
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": K_PER_GPU / v * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "%s (d=4, m=400, m'=400, K=150)" % WORKLOAD,
+                       "arm": "FP64 CPU oracle (the reference arm of this project)"},
+            "cpu_baseline": res,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------- GPU leg
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only the BF16x3 step: warm-up then --steps steps (for ncu captures)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import paper_0909_5662_gb300 as P
+    from paper_0909_5662_gb300 import umd_partition
+    from workloads import dense_workload, SEED_BASE
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    # Weak scaling: the job holds K_PER_GPU * ws operators, UMD-partitioned.
+    K_total = K_PER_GPU * ws
+    lo, hi = umd_partition(K_total, ws, rank)
+    # every rank's slice has the same shape and statistics; ranks > 0 shift the seed
+    w = dense_workload(WORKLOAD, SEED_BASE + 2 + 1000 * rank, D, M, MP, hi - lo, hubbard_mix=True)
+    K = w.K
+    U = torch.from_numpy(w.U).to(dev)
+    O32 = torch.from_numpy(w.O).to(dev, torch.float32)
+    O64 = torch.from_numpy(w.O).to(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    h = P.default_handle()
+    flops_logical = 2.0 * K * D * M * MP * (M + MP)
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    def time_steps(prec, O, steps, warmup, timing=False):
+        out = P.dmrg_rotate_ops(U, O, D, prec)
+        for _ in range(warmup):
+            P.dmrg_rotate_ops(U, O, D, prec, out=out)
+        barrier()
+        if timing:
+            P.dmrg_kernel_timing(reset=True)
+            P.dmrg_set_option("kernel_timing", 1)
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            P.dmrg_rotate_ops(U, O, D, prec, out=out)
+            b.record()
+            evs.append((a, b))
+        barrier()
+        if timing:
+            P.dmrg_set_option("kernel_timing", 0)
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        kt = P.dmrg_kernel_timing(reset=True) if timing else []
+        P.dmrg_sync_status()
+        return ms, kt, out
+
+    if args.profile:
+        out = P.dmrg_rotate_ops(U, O32, D, "bf16x3")
+        for _ in range(args.warmup + args.steps):
+            P.dmrg_rotate_ops(U, O32, D, "bf16x3", out=out)
+        torch.cuda.synchronize()
+        P.dmrg_sync_status()
+        print(json.dumps({"profile": WORKLOAD, "steps": args.steps, "warmup": args.warmup}))
+        return 0
+
+    def max_over_ranks(x):
+        if pg is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- headline: BF16x3, clocks sampled during the timed region
+    sampler = ClockSampler(local if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    P.dmrg_rotate_ops(U, O32, D, "bf16x3")
+    torch.cuda.synchronize()
+    sampler.start()
+    ms_total, kt, out_bf = time_steps("bf16x3", O32, args.steps, args.warmup, timing=True)
+    clocks = sampler.stop()
+    ms_step = max_over_ranks(ms_total / args.steps)
+    value = K_total / (ms_step * 1e-3)
+    launches_per_step = sum(k["launches"] for k in kt) / max(args.steps, 1)
+
+    # ---- dominant kernel roofline (issued BF16 MMA flops: 3 per logical multiply-add pair)
+    peaks, peak_src = measured_peaks()
+    per_kernel = {k["kernel"]: k["total_ms"] / k["launches"] for k in kt}
+    dom = max(per_kernel, key=per_kernel.get)
+    issued = {"tc_gemm_first_product": 3 * 2.0 * K * M * (D * MP) * M,
+              "tc_gemm_second_product": 3 * 2.0 * K * MP * MP * (M * D)}
+    if dom in issued:
+        achieved = issued[dom] / (per_kernel[dom] * 1e-3) / 1e12
+        peak = peaks["bf16_tflops"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic_for(dom), "kernel": dom,
+                "peak_source": "%s bf16_tflops (burst)" % peak_src,
+                "flops_per_launch": issued[dom], "ms_per_launch": per_kernel[dom]}
+    else:
+        byt = {"pack_O": K * M * M * (4 + 4)}
+        achieved = byt.get(dom, 0) / (per_kernel[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic_for(dom), "kernel": dom}
+
+    # ---- the same inputs in TF32 and through the plain FP64 GPU path
+    ms_tf, kt_tf, out_tf = time_steps("tf32", O32, args.steps, args.warmup, timing=True)
+    fp64_steps = 2
+    ms_64, _, out_64 = time_steps("fp64", O64, fp64_steps, 1)
+    ms_tf = max_over_ranks(ms_tf / args.steps)
+    ms_64 = max_over_ranks(ms_64 / fp64_steps)
+
+    # ---- accuracy of the reduced paths against the FP64 GPU path (oracle-checked in tests)
+    def rel(a, b):
+        num = torch.linalg.vector_norm((a.double() - b).reshape(K, -1), dim=1)
+        den = torch.linalg.vector_norm(b.reshape(K, -1), dim=1)
+        return float((num / den).max())
+    err_bf = rel(out_bf, out_64)
+    err_tf = rel(out_tf, out_64)
+
+    # ---- end to end through the public API with host buffers (pinned), copies timed
+    Oh = torch.from_numpy(w.O.astype(np.float32)).pin_memory()
+    Uh = torch.from_numpy(w.U).pin_memory()
+    Ob = torch.empty_like(O32)
+    Ub = torch.empty_like(U)
+    outh = torch.empty((K, MP, MP), dtype=torch.float32).pin_memory()
+    outd = torch.empty((K, MP, MP), dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        Ob.copy_(Oh, non_blocking=True)
+        Ub.copy_(Uh, non_blocking=True)
+        P.dmrg_rotate_ops(Ub, Ob, D, "bf16x3", out=outd)
+        outh.copy_(outd, non_blocking=True)
+    barrier()
+    e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        Ob.copy_(Oh, non_blocking=True)
+        Ub.copy_(Uh, non_blocking=True)
+        P.dmrg_rotate_ops(Ub, Ob, D, "bf16x3", out=outd)
+        outh.copy_(outd, non_blocking=True)
+        b.record()
+        b.synchronize()
+        e_ms += a.elapsed_time(b)
+    e_ms = max_over_ranks(e_ms / args.steps)
+    h2d = Oh.numel() * 4 + Uh.numel() * 8
+    d2h = outh.numel() * 4
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(w)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3", "data": "synthetic",
+            "config": {
+                "workload": "%s (d=4, m=400 -> m*d=1600 -> m'=400, K=150 per GPU)" % WORKLOAD,
+                "precision": "BF16x3 (bf16 hi/lo operands, fp32 accumulate), output fp32",
+                "operators_total": K_total, "partition": "UMD contiguous slices, no collective",
+                "l2": "flushed between timed steps (512 MiB write, not timed)",
+                "inputs": "resident in HBM (operators fp32, U fp64)"},
+            "eff_tflops": flops_logical / (ms_step * 1e-3) / 1e12 * 1.0,
+            "issued_bf16_tflops": 3 * flops_logical / (ms_step * 1e-3) / 1e12,
+            "precisions": {
+                "bf16x3": {"ms_per_step": ms_step, "ops_per_s": K_total / (ms_step * 1e-3),
+                           "eff_tflops": flops_logical / (ms_step * 1e-3) / 1e12,
+                           "max_rel_fro_err_vs_fp64": err_bf},
+                "tf32": {"ms_per_step": ms_tf, "ops_per_s": K_total / (ms_tf * 1e-3),
+                         "eff_tflops": flops_logical / (ms_tf * 1e-3) / 1e12,
+                         "max_rel_fro_err_vs_fp64": err_tf},
+                "fp64": {"ms_per_step": ms_64, "ops_per_s": K_total / (ms_64 * 1e-3),
+                         "eff_tflops": flops_logical / (ms_64 * 1e-3) / 1e12}},
+            "kernels_ms_per_launch": per_kernel,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": K_total / (e_ms * 1e-3), "unit": UNIT, "ms_per_step": e_ms,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

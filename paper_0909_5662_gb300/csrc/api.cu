@@ -196,7 +196,9 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     j2.rows = mp; j2.cols = D.md; j2.rows_per_op = mp;
     j2.rdiv = 1; j2.s_r_hi = 1; j2.s_r_lo = 0; j2.s_c = mp;
     j2.dst0 = B2[0]; j2.dst1 = B2[1]; j2.ld = D.ld2;
-    cudaError_t e = timed_launch(h, "pack_operands", s, [&] { return pack_launch(jobs, 3, nullptr, s); });
+    cudaError_t e = timed_launch(h, "pack_O", s, [&] { return pack_launch(jobs, 1, nullptr, s); });
+    if (e == cudaSuccess)
+        e = timed_launch(h, "pack_U", s, [&] { return pack_launch(jobs + 1, 2, nullptr, s); });
     if (e != cudaSuccess) return cuda_fail(h, e, "pack");
 
     const bool f32 = !split;

@@ -339,10 +339,23 @@ struct PackLaunch {
 constexpr int kPackThreads = 256;
 constexpr int kPackElems = 4;  // elements per thread
 
-__device__ __forceinline__ void pack_store(const PackJob& j, int64_t dst, double x) {
+// BF16 pair of x: hi = bf16(x), lo = bf16(x - hi).  For an FP32 source the residual
+// x - hi is exact in FP32; for an FP64 source it is formed in FP64 (one subtraction)
+// and then rounded, so FP64 arithmetic stays off the per-element path otherwise.
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& h, __nv_bfloat16& l) {
+    h = __float2bfloat16_rn(x);
+    l = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+__device__ __forceinline__ void split_bf16(double x, __nv_bfloat16& h, __nv_bfloat16& l) {
+    h = __float2bfloat16_rn(__double2float_rn(x));
+    l = __float2bfloat16_rn(__double2float_rn(x - double(__bfloat162float(h))));
+}
+
+template <typename S>
+__device__ __forceinline__ void pack_store(const PackJob& j, int64_t dst, S x) {
     if (j.mode == 0) {
-        const __nv_bfloat16 h = __double2bfloat16(x);
-        const __nv_bfloat16 l = __double2bfloat16(x - double(__bfloat162float(h)));
+        __nv_bfloat16 h, l;
+        split_bf16(x, h, l);
         static_cast<__nv_bfloat16*>(j.dst0)[dst] = h;
         static_cast<__nv_bfloat16*>(j.dst1)[dst] = l;
     } else if (j.mode == 1) {
@@ -381,10 +394,79 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constan
         const int64_t rr = r - g * j.rows_per_op;
         const int64_t src = j.src_off + (j.op_off ? j.op_off[g] : g * j.s_op) +
                             (rr / j.rdiv) * j.s_r_hi + (rr % j.rdiv) * j.s_r_lo + c * j.s_c;
-        const double x = j.src_f64 ? static_cast<const double*>(j.src)[src]
-                                   : double(static_cast<const float*>(j.src)[src]);
-        pack_store(j, r * j.ld + c, x);
+        if (j.src_f64)
+            pack_store(j, r * j.ld + c, static_cast<const double*>(j.src)[src]);
+        else
+            pack_store(j, r * j.ld + c, static_cast<const float*>(j.src)[src]);
     }
+}
+
+// Contiguous fast path: source rows of `cols` elements at stride s_r_hi, 8
+// elements per thread with 16/32-byte loads and 16-byte stores (BF16 hi and lo)
+// or 2 x 16-byte stores (TF32 / FP32).
+template <typename S>
+__global__ void __launch_bounds__(kPackThreads) pack_rows_vec8_kernel(const __grid_constant__ PackJob j) {
+    const int64_t per_row = j.cols >> 3;
+    const int64_t total = j.rows * per_row;
+    const S* src = static_cast<const S*>(j.src) + j.src_off;
+    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < total;
+         v += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t r = v / per_row;
+        const int64_t c = (v - r * per_row) << 3;
+        const S* sp = src + r * j.s_r_hi + c;
+        S x[8];
+        if (sizeof(S) == 4) {
+            const float4 a = reinterpret_cast<const float4*>(sp)[0];
+            const float4 b = reinterpret_cast<const float4*>(sp)[1];
+            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+            x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const double2 a = reinterpret_cast<const double2*>(sp)[q];
+                x[2 * q] = S(a.x);
+                x[2 * q + 1] = S(a.y);
+            }
+        }
+        const int64_t dst = r * j.ld + c;
+        if (j.mode == 0) {
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t hh[2], ll[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    __nv_bfloat16 h, l;
+                    split_bf16(x[2 * q + e], h, l);
+                    hh[e] = __bfloat16_as_ushort(h);
+                    ll[e] = __bfloat16_as_ushort(l);
+                }
+                hw[q] = hh[0] | (hh[1] << 16);
+                lw[q] = ll[0] | (ll[1] << 16);
+            }
+            *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(j.dst0) + dst) =
+                make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(j.dst1) + dst) =
+                make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        } else {
+            float y[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) y[e] = (j.mode == 1) ? tf32_round(float(x[e])) : float(x[e]);
+            float4* d4 = reinterpret_cast<float4*>(static_cast<float*>(j.dst0) + dst);
+            d4[0] = make_float4(y[0], y[1], y[2], y[3]);
+            d4[1] = make_float4(y[4], y[5], y[6], y[7]);
+        }
+    }
+}
+
+bool pack_vec8_ok(const PackJob& j) {
+    const size_t es = j.src_f64 ? 8 : 4;
+    const bool single_group = (j.rows_per_op >= j.rows) && j.op_off == nullptr;
+    return single_group && j.rdiv == 1 && j.s_c == 1 && (j.cols % 8) == 0 && (j.s_r_hi % 8) == 0 &&
+           (j.ld % 8) == 0 && (j.src_off % 8) == 0 &&
+           (reinterpret_cast<uintptr_t>(j.src) % (8 * es)) == 0 &&
+           (reinterpret_cast<uintptr_t>(j.dst0) % 32) == 0 &&
+           (j.dst1 == nullptr || (reinterpret_cast<uintptr_t>(j.dst1) % 16) == 0);
 }
 
 template <int MODE, int EPI>
@@ -461,13 +543,28 @@ cudaError_t pack_launch(const PackJob* jobs, int njobs, PackJob* /*unused*/, cud
     if (njobs > 4) return cudaErrorInvalidValue;
     PackLaunch L{};
     int64_t blocks = 0;
+    int n = 0;
     for (int i = 0; i < njobs; ++i) {
-        L.inline_jobs[i] = jobs[i];
-        L.inline_jobs[i].block_start = blocks;
+        if (jobs[i].rows * jobs[i].cols == 0) continue;
+        if (pack_vec8_ok(jobs[i])) {
+            const int64_t vecs = jobs[i].rows * (jobs[i].cols / 8);
+            const int64_t nb = std::min<int64_t>((vecs + kPackThreads - 1) / kPackThreads, 152 * 16);
+            if (jobs[i].src_f64)
+                pack_rows_vec8_kernel<double><<<unsigned(nb), kPackThreads, 0, s>>>(jobs[i]);
+            else
+                pack_rows_vec8_kernel<float><<<unsigned(nb), kPackThreads, 0, s>>>(jobs[i]);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            continue;
+        }
+        L.inline_jobs[n] = jobs[i];
+        L.inline_jobs[n].block_start = blocks;
         blocks += pack_blocks_for(jobs[i]);
+        ++n;
     }
+    if (n == 0) return cudaSuccess;
     L.table = nullptr;
-    L.njobs = njobs;
+    L.njobs = n;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     pack_kernel<<<unsigned(blocks), kPackThreads, 0, s>>>(L);
