@@ -237,6 +237,29 @@ DMRG_API dmrg_status dmrg_rotate_ops_blocked(dmrg_handle handle, dmrg_blocked_pl
                                     void* Oout_blocks, dmrg_precision precision, void* ws,
                                     size_t ws_bytes, dmrg_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Dense rotation without any allocation (the paper has no counterpart; this
+ * entry point exists for callers of the library, not for the method).
+ *
+ * For callers that cannot call cudaMalloc -- a plug-in inside a host program
+ * whose device memory is fully reserved by that program's own pool, code
+ * under a fixed per-client memory limit, or a latency-critical loop where an
+ * allocation would synchronise the device.  Same arguments and result as
+ * dmrg_rotate_ops(), but no handle and no workspace: the scratch lives in a
+ * static device array of 32 MiB that every GPU loading the library holds
+ * until the process exits.  Problems whose dmrg_rotate_ops_workspace() size
+ * exceeds 32 MiB are rejected with DMRG_ERR_WORKSPACE before any launch.
+ * The first call on each device (with that device current) looks up the
+ * array's device address; make that first call before any stream capture.
+ * All calls share the array, so calls that overlap on the GPU race on it:
+ * serialise them (one stream, one host thread at a time).  A device-side
+ * bounded-wait timeout cannot be reported by this entry point (there is no
+ * handle to read it from); the kernels still return.
+ * ------------------------------------------------------------------------ */
+DMRG_API dmrg_status dmrg_rotate_ops_noalloc(const double* U, int64_t m, int d, int64_t mp,
+                                             const void* O, int in_is_fp64, int64_t K, void* Oout,
+                                             dmrg_precision precision, dmrg_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,6 +12,7 @@ from .api import (  # noqa: F401
     default_handle,
     dmrg_rotate_ops,
     dmrg_rotate_ops_workspace,
+    dmrg_rotate_ops_noalloc,
     dmrg_autotune_rotate_ops,
     dmrg_rotate_ops_backward,
     dmrg_orthonormality_error,

@@ -62,6 +62,7 @@ SIGNATURES = {
     "dmrg_blocked_plan_stats": [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                 ctypes.POINTER(_dbl)],
     "dmrg_rotate_ops_blocked": [_p, _p, _p, _p, _int, _p, _int, _p, _sz, _p],
+    "dmrg_rotate_ops_noalloc": [_p, _i64, _int, _i64, _p, _int, _i64, _p, _int, _p],
 }
 STRING_RETURN = {"dmrg_status_string": [_int], "dmrg_last_error": [_p]}
 

@@ -143,6 +143,22 @@ def dmrg_rotate_ops(U: torch.Tensor, O: torch.Tensor, d: int, precision="bf16x3"
     return out
 
 
+def dmrg_rotate_ops_noalloc(U: torch.Tensor, O: torch.Tensor, d: int, precision="bf16x3",
+                            out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """The dense rotation with no handle and no workspace: scratch is the
+    library's fixed 32 MiB static device array (small problems only)."""
+    lib = _capi.load()
+    K, m, mp, p = _dense_args(U, O, d, precision)
+    odt = torch.float64 if p == 0 else torch.float32
+    if out is None:
+        out = torch.empty((K, mp, mp), dtype=odt, device=O.device)
+    _need(out, "out", (odt,), 3)
+    _capi.check(lib.dmrg_rotate_ops_noalloc(_ptr(U), m, d, mp, _ptr(O), int(O.dtype == torch.float64),
+                                            K, _ptr(out), p, _stream(stream)),
+                None, "dmrg_rotate_ops_noalloc")
+    return out
+
+
 def dmrg_autotune_rotate_ops(U, O, d, precision="bf16x3", out=None, handle=None, stream=None):
     return dmrg_rotate_ops(U, O, d, precision, out, handle, stream, _entry="dmrg_autotune_rotate_ops")
 

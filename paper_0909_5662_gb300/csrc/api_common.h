@@ -41,6 +41,10 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
                              dmrg_precision p, void* ws, const TcConfig& c1, const TcConfig& c2,
                              cudaStream_t s);
 
+dmrg_status dense_simt_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
+                               const void* O, int in_is_fp64, int64_t K, void* Oout,
+                               dmrg_precision p, void* ws, cudaStream_t s);
+
 cudaError_t tc_gemm_launch_grouped(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
                                    int bn_smem, cudaStream_t s);
 
