@@ -95,12 +95,20 @@ DMRG_API dmrg_status dmrg_sync_status(dmrg_handle handle, dmrg_stream_t stream);
  *   DMRG_OPT_WAIT_TIMEOUT_MS : device-side bounded-wait limit (default 2000 ms).
  *   DMRG_OPT_CHECK_ORTHO     : tolerance > 0 makes dmrg_rotate_ops verify
  *                              ||U^T U - I||_F <= tol first (synchronises the
- *                              stream); 0 = off (default). */
+ *                              stream); 0 = off (default).
+ *   DMRG_OPT_TEST_WITHHOLD_ARRIVAL : test hook for failure detection.  1 makes
+ *                              the next dense tensor-core launch withhold one
+ *                              shared-memory stage release in its first CTA, so
+ *                              a bounded wait expires: the kernel winds down
+ *                              (waiting, with a fixed limit, for copies and MMAs
+ *                              already issued) and dmrg_sync_status() returns
+ *                              DMRG_ERR_TIMEOUT.  No fault, trap or hang. */
 typedef enum {
     DMRG_OPT_GRAPH = 1,
     DMRG_OPT_KERNEL_TIMING = 2,
     DMRG_OPT_WAIT_TIMEOUT_MS = 3,
-    DMRG_OPT_CHECK_ORTHO = 4
+    DMRG_OPT_CHECK_ORTHO = 4,
+    DMRG_OPT_TEST_WITHHOLD_ARRIVAL = 5
 } dmrg_option;
 DMRG_API dmrg_status dmrg_set_option(dmrg_handle handle, dmrg_option option, double value);
 

@@ -26,3 +26,4 @@ from .api import (  # noqa: F401
     PRECISIONS,
 )
 from .partition import umd_partition  # noqa: F401
+from .autograd import DmrgRotate, rotate  # noqa: F401

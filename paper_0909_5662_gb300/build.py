@@ -62,7 +62,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if jobs:
         with concurrent.futures.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
             list(ex.map(compile_one, jobs))
-    if jobs or not os.path.exists(LIB):
+    stale = (not os.path.exists(LIB)) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs)
+    if jobs or stale:
         tmp = LIB + ".tmp.%d" % os.getpid()
         cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -68,6 +68,12 @@ uint64_t timeout_ns(dmrg_handle h) {
     return uint64_t(ms * 1e6);
 }
 
+int take_drop_arrival(dmrg_handle h) {
+    const int v = h->drop_arrival_next;
+    h->drop_arrival_next = 0;
+    return v;
+}
+
 // Runs `body` directly, or (graph mode) captures it once per key into a CUDA
 // graph on the handle's private stream and replays the graph on `stream`.
 dmrg_status run_maybe_graph(dmrg_handle h, const std::string& key, cudaStream_t stream,
@@ -142,6 +148,7 @@ dmrg_status check_dense_args(dmrg_handle h, int64_t K, int64_t m, int d, int64_t
 }
 
 TcConfig tuned_config(dmrg_handle h, const std::string& key, TcMode mode) {
+    load_tune_file(h);
     auto it = h->tune_cache.find(key);
     if (it != h->tune_cache.end()) return it->second;
     TcConfig c;
@@ -201,35 +208,31 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
         e = timed_launch(h, "pack_U", s, [&] { return pack_launch(jobs + 1, 2, nullptr, s); });
     if (e != cudaSuccess) return cuda_fail(h, e, "pack");
 
-    const bool f32 = !split;
     // ---- first product: T = O U_r, written straight into the second product's
     //      K-major operand layout: T_all[k*mp + b][i*d + s].
     TcLaunch L1{};
-    TcProblem& P1 = L1.inline_prob;
-    const int tn1 = choose_tile_n(int64_t(d) * mp, c1.tile_n_max);
-    for (int i = 0; i < ns; ++i) {
-        if (!encode_operand_map(&P1.tmA[i], Op[i], f32, K * m, m, D.ld1, 128) ||
-            !encode_operand_map(&P1.tmB[i], B1[i], f32, int64_t(d) * mp, m, D.ld1, tn1))
+    TcProblem& P1 = L1.inline_prob[0];
+    {
+        TcOperand A{Op[0], Op[1], K * m, m, D.ld1};
+        TcOperand B{B1[0], B1[1], int64_t(d) * mp, m, D.ld1};
+        if (!make_problem(P1, mode, A, B, c1.tile_n_max, 1))
             return fail(h, DMRG_ERR_CUDA, "cuTensorMapEncodeTiled failed (first product)");
     }
-    if (!split) { P1.tmA[1] = P1.tmA[0]; P1.tmB[1] = P1.tmB[0]; }
-    finish_problem(P1, K * m, int64_t(d) * mp, m, tn1, 1, mode);
-    P1.tile_start = 0;
-    P1.rows_per_op = int32_t(m);
-    P1.s_op = mp * D.ld2;
-    P1.s_row = d;
-    P1.col_div = d;
-    P1.s_col_hi = D.ld2;
-    P1.s_col_lo = 1;
-    P1.out_off = 0;
-    P1.op_off = nullptr;
+    TcScatter& S1 = P1.sc[0];
+    S1.rows_per_op = int32_t(m);
+    S1.s_op = mp * D.ld2;
+    S1.s_row = d;
+    S1.col_div = d;
+    S1.s_col_hi = D.ld2;
+    S1.s_col_lo = 1;
     L1.table = nullptr;
     L1.nprob = 1;
     L1.total_tiles = P1.m_tiles * P1.n_tiles * P1.k_splits;
-    L1.out0 = Tt[0];
-    L1.out1 = Tt[1];
+    L1.out[0][0] = Tt[0];
+    L1.out[0][1] = Tt[1];
     L1.status = h->d_status;
     L1.timeout_ns = timeout_ns(h);
+    L1.drop_arrival = take_drop_arrival(h);
     const int grid1 = c1.grid > 0 ? c1.grid : h->num_sms;
     e = timed_launch(h, "tc_gemm_first_product", s, [&] {
         return tc_gemm_launch(mode, split ? EPI_SPLIT_BF16 : EPI_TF32, L1, c1.stages, grid1, s);
@@ -238,29 +241,24 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
 
     // ---- second product: O'_k^T rows = T_all rows (k*mp + b), columns a: O'_k[a][b].
     TcLaunch L2{};
-    TcProblem& P2 = L2.inline_prob;
-    const int tn2 = choose_tile_n(mp, c2.tile_n_max);
-    for (int i = 0; i < ns; ++i) {
-        if (!encode_operand_map(&P2.tmA[i], Tt[i], f32, K * mp, D.md, D.ld2, 128) ||
-            !encode_operand_map(&P2.tmB[i], B2[i], f32, mp, D.md, D.ld2, tn2))
+    TcProblem& P2 = L2.inline_prob[0];
+    {
+        TcOperand A{Tt[0], Tt[1], K * mp, D.md, D.ld2};
+        TcOperand B{B2[0], B2[1], mp, D.md, D.ld2};
+        if (!make_problem(P2, mode, A, B, c2.tile_n_max, 1))
             return fail(h, DMRG_ERR_CUDA, "cuTensorMapEncodeTiled failed (second product)");
     }
-    if (!split) { P2.tmA[1] = P2.tmA[0]; P2.tmB[1] = P2.tmB[0]; }
-    finish_problem(P2, K * mp, mp, D.md, tn2, 1, mode);
-    P2.tile_start = 0;
-    P2.rows_per_op = int32_t(mp);
-    P2.s_op = mp * mp;
-    P2.s_row = 1;
-    P2.col_div = 1;
-    P2.s_col_hi = mp;
-    P2.s_col_lo = 0;
-    P2.out_off = 0;
-    P2.op_off = nullptr;
+    TcScatter& S2 = P2.sc[0];
+    S2.rows_per_op = int32_t(mp);
+    S2.s_op = mp * mp;
+    S2.s_row = 1;
+    S2.col_div = 1;
+    S2.s_col_hi = mp;
+    S2.s_col_lo = 0;
     L2.table = nullptr;
     L2.nprob = 1;
     L2.total_tiles = P2.m_tiles * P2.n_tiles * P2.k_splits;
-    L2.out0 = Oout;
-    L2.out1 = nullptr;
+    L2.out[0][0] = Oout;
     L2.status = h->d_status;
     L2.timeout_ns = timeout_ns(h);
     const int grid2 = c2.grid > 0 ? c2.grid : h->num_sms;
@@ -405,6 +403,9 @@ dmrg_status dmrg_set_option(dmrg_handle h, dmrg_option o, double v) {
         case DMRG_OPT_CHECK_ORTHO:
             if (v < 0) return fail(h, DMRG_ERR_INVALID_ARG, "tolerance must be >= 0");
             h->check_ortho_tol = v;
+            return DMRG_OK;
+        case DMRG_OPT_TEST_WITHHOLD_ARRIVAL:
+            h->drop_arrival_next = v != 0;
             return DMRG_OK;
     }
     return fail(h, DMRG_ERR_INVALID_ARG, "unknown option");

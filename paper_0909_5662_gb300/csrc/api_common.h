@@ -28,6 +28,7 @@ cudaError_t timed_launch(dmrg_handle h, const char* name, cudaStream_t s,
 size_t align_up(size_t x, size_t a);
 bool tc_supported(dmrg_handle h);
 uint64_t timeout_ns(dmrg_handle h);
+int take_drop_arrival(dmrg_handle h);
 dmrg_status run_maybe_graph(dmrg_handle h, const std::string& key, cudaStream_t stream,
                             const std::function<dmrg_status(cudaStream_t)>& body);
 DenseDims dense_dims(int64_t K, int64_t m, int d, int64_t mp, dmrg_precision p);
@@ -35,6 +36,8 @@ dmrg_status check_dense_args(dmrg_handle h, int64_t K, int64_t m, int d, int64_t
                              dmrg_precision p);
 dmrg_status check_ws(dmrg_handle h, const void* ws, size_t have, size_t need);
 TcConfig tuned_config(dmrg_handle h, const std::string& key, TcMode mode);
+void load_tune_file(dmrg_handle h);
+void save_tune_file(dmrg_handle h);
 std::string shape_key(const char* tag, int64_t K, int64_t m, int d, int64_t mp, dmrg_precision p);
 dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
                              const void* O, int in_is_fp64, int64_t K, void* Oout,

@@ -1,0 +1,152 @@
+// autotune.cu -- in-house autotuner for the tensor-core tilings of the dense rotation.
+//
+// For each of the two products it times every candidate (N tile, pipeline depth)
+// with CUDA events on the caller's buffers, keeps the fastest per shape key in the
+// handle and, when $DMRG_AUTOTUNE_CACHE names a file, persists the choices there as
+// a small JSON object {"key": [tile_n_max, stages, grid], ...} so that later
+// processes start tuned.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "api_common.h"
+
+using namespace dmrg;
+
+namespace dmrg {
+
+void load_tune_file(dmrg_handle h) {
+    if (h->tune_cache_loaded) return;
+    h->tune_cache_loaded = true;
+    const char* path = std::getenv("DMRG_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    std::ifstream f(path);
+    if (!f) return;
+    std::stringstream ss;
+    ss << f.rdbuf();
+    const std::string text = ss.str();
+    size_t pos = 0;
+    while ((pos = text.find('"', pos)) != std::string::npos) {
+        const size_t end = text.find('"', pos + 1);
+        if (end == std::string::npos) break;
+        const std::string key = text.substr(pos + 1, end - pos - 1);
+        const size_t lb = text.find('[', end), rb = text.find(']', end);
+        if (lb == std::string::npos || rb == std::string::npos || rb < lb) break;
+        TcConfig c;
+        if (sscanf(text.c_str() + lb + 1, "%d , %d , %d", &c.tile_n_max, &c.stages, &c.grid) == 3 &&
+            c.tile_n_max >= 16 && c.tile_n_max <= 256 && c.stages >= 1 && c.stages <= 8 && c.grid >= 0)
+            h->tune_cache[key] = c;
+        pos = rb + 1;
+    }
+}
+
+void save_tune_file(dmrg_handle h) {
+    const char* path = std::getenv("DMRG_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    std::ofstream f(path);
+    if (!f) return;
+    f << "{\n";
+    size_t i = 0;
+    for (auto& kv : h->tune_cache) {
+        f << "  \"" << kv.first << "\": [" << kv.second.tile_n_max << ", " << kv.second.stages << ", "
+          << kv.second.grid << "]" << (++i < h->tune_cache.size() ? ",\n" : "\n");
+    }
+    f << "}\n";
+}
+
+}  // namespace dmrg
+
+namespace {
+
+std::vector<TcConfig> candidates(TcMode mode, int64_t N, int num_sms) {
+    std::vector<TcConfig> out;
+    std::vector<int> seen;
+    for (int tn : {256, 224, 192, 160, 128, 96, 64}) {
+        const int t = choose_tile_n(N, tn);
+        if (std::find(seen.begin(), seen.end(), t) != seen.end()) continue;
+        seen.push_back(t);
+        const int smax = tc_max_stages(mode, t);
+        for (int st = smax; st >= std::max(2, smax - 1); --st) {
+            TcConfig c;
+            c.tile_n_max = t;
+            c.stages = st;
+            c.grid = num_sms;
+            out.push_back(c);
+        }
+    }
+    return out;
+}
+
+}  // namespace
+
+extern "C" dmrg_status dmrg_autotune_rotate_ops(dmrg_handle h, const double* U, int64_t m, int d,
+                                                int64_t mp, const void* O, int in_is_fp64,
+                                                int64_t K, void* Oout, dmrg_precision p, void* ws,
+                                                size_t ws_bytes, dmrg_stream_t stream) {
+    dmrg_status st = check_dense_args(h, K, m, d, mp, p);
+    if (st != DMRG_OK) return st;
+    if (p != DMRG_PREC_TF32 && p != DMRG_PREC_BF16X3) return DMRG_OK;
+    if (K == 0) return DMRG_OK;
+    if (!U || !O || !Oout) return fail(h, DMRG_ERR_INVALID_ARG, "null data pointer");
+    if (!tc_supported(h)) return fail(h, DMRG_ERR_UNSUPPORTED, "tensor cores need sm_103");
+    const DenseDims D = dense_dims(K, m, d, mp, p);
+    st = check_ws(h, ws, ws_bytes, D.ws.total);
+    if (st != DMRG_OK) return st;
+    load_tune_file(h);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const TcMode mode = (p == DMRG_PREC_BF16X3) ? TC_BF16X3 : TC_TF32;
+    const bool timing = h->timing;
+    h->timing = false;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    auto time_cfg = [&](const TcConfig& c1, const TcConfig& c2, float& best) -> dmrg_status {
+        best = 1e30f;
+        for (int r = 0; r < 4; ++r) {
+            cudaEventRecord(a, s);
+            dmrg_status rs = dense_tc_forward(h, U, m, d, mp, O, in_is_fp64, K, Oout, p, ws, c1, c2, s);
+            cudaEventRecord(b, s);
+            if (rs != DMRG_OK) return rs;
+            if (cudaEventSynchronize(b) != cudaSuccess) return DMRG_ERR_CUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (r > 0) best = std::min(best, ms);  // first run warms up
+        }
+        return DMRG_OK;
+    };
+    const std::string k1 = shape_key("g1", K, m, d, mp, p), k2 = shape_key("g2", K, m, d, mp, p);
+    TcConfig best1 = tuned_config(h, k1, mode), best2 = tuned_config(h, k2, mode);
+    float tbest = 1e30f;
+    for (const TcConfig& c : candidates(mode, int64_t(d) * mp, h->num_sms)) {
+        float t = 0;
+        if ((st = time_cfg(c, best2, t)) != DMRG_OK) break;
+        if (t < tbest) { tbest = t; best1 = c; }
+    }
+    if (st == DMRG_OK) {
+        tbest = 1e30f;
+        for (const TcConfig& c : candidates(mode, mp, h->num_sms)) {
+            float t = 0;
+            if ((st = time_cfg(best1, c, t)) != DMRG_OK) break;
+            if (t < tbest) { tbest = t; best2 = c; }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    h->timing = timing;
+    if (st != DMRG_OK) return st;
+    h->tune_cache[k1] = best1;
+    h->tune_cache[k2] = best2;
+    save_tune_file(h);
+    // graphs captured before tuning hold the old tilings
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
+    h->graphs.clear();
+    // leave the caller's output computed with the chosen tilings
+    return dense_tc_forward(h, U, m, d, mp, O, in_is_fp64, K, Oout, p, ws, best1, best2, s);
+}

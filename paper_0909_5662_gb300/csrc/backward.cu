@@ -1,0 +1,364 @@
+// backward.cu -- adjoint of the dense rotation (dmrg_rotate_ops_backward).
+//
+// For a loss L with dL/dO'_k = G_k and O'_k = U^T (O_k (x) I_d) U (Sec. 2, step 5),
+// the chain rule gives
+//   dO_k = Tr_d(U G_k U^T) = sum_s U_s G_k U_s^T          (U_s: rows j*d + s of U)
+//   dU   = sum_k (O_k (x) I) U G_k^T + (O_k (x) I)^T U G_k.
+// Nothing from the forward pass is kept: only U, O and G are read.
+//
+// Tensor-core schedule (BF16x3 or TF32), with W_k = U G_k and W'_k = U G_k^T:
+//   1. W'_k  = (G_k U^T)^T : M = K*m' rows (k, a), N = m*d, written row-major per op;
+//   2. dO_k[i][j] = sum_(s,a) W'_k[j*d+s][a] U[i*d+s][a] : M = K*m rows (k, j), N = m;
+//   3. W_k and W'_k again, one problem per site state s, rows = block states j, written
+//      transposed (WT_k[s*m'+b][j]) so the next reduction over (k, j) is K-major;
+//   4. dU_r[i][n] = sum_(k,j) O_k[i][j] WT'_k[n][j] + O_k[j][i] WT_k[n][j] : one launch of
+//      two problems over 3-D operand maps, split over (k, j) and accumulated in FP32;
+//   5. dU (FP64) = dU_r (dU and dU_r share the row-major layout).
+// Plain FMA schedule (FP64, FP32): the same formulas as strided batched GEMMs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "api_common.h"
+
+using namespace dmrg;
+
+namespace {
+
+struct BwdDims {
+    int64_t K, m, mp, md, dmp;
+    int d;
+    int64_t ld_u, ld_n, ld_j;  // packed leading dimensions (elements)
+    WsLayout ws;
+    // section indices
+    int i_U, i_Ur, i_G, i_GT, i_O, i_OT, i_Wp, i_WT, i_WTp, i_dU, i_conv;
+};
+
+BwdDims bwd_dims(int64_t K, int64_t m, int d, int64_t mp, dmrg_precision p) {
+    BwdDims B{};
+    B.K = K; B.m = m; B.d = d; B.mp = mp; B.md = m * d; B.dmp = int64_t(d) * mp;
+    WsLayout& W = B.ws;
+    if (p == DMRG_PREC_FP64 || p == DMRG_PREC_FP32) {
+        const size_t es = (p == DMRG_PREC_FP64) ? 8 : 4;
+        B.i_Wp = int(W.offsets.size()); W.add("W", size_t(K) * B.md * mp * es);
+        B.i_WT = int(W.offsets.size()); W.add("Wp", size_t(K) * B.md * mp * es);
+        B.i_dU = int(W.offsets.size()); W.add("dU", size_t(B.md) * mp * es);
+        B.i_conv = int(W.offsets.size());
+        if (p == DMRG_PREC_FP32) {  // FP32 copies of U, O and G
+            W.add("U32", size_t(B.md) * mp * 4);
+            W.add("O32", size_t(K) * m * m * 4);
+            W.add("G32", size_t(K) * mp * mp * 4);
+        }
+        return B;
+    }
+    const bool split = (p == DMRG_PREC_BF16X3);
+    const int64_t al = split ? 8 : 4;
+    const size_t es = split ? 2 : 4;
+    const int ns = split ? 2 : 1;
+    auto ld = [&](int64_t x) { return (x + al - 1) / al * al; };
+    B.ld_u = ld(mp);
+    B.ld_n = ld(B.dmp);
+    B.ld_j = ld(m);
+    auto add = [&](int& idx, size_t elems) {
+        idx = int(W.offsets.size());
+        for (int i = 0; i < ns; ++i) W.add("x", elems * es);
+    };
+    add(B.i_U, size_t(B.md) * B.ld_u);
+    add(B.i_Ur, size_t(m) * B.ld_n);
+    add(B.i_G, size_t(K) * mp * B.ld_u);
+    add(B.i_GT, size_t(K) * mp * B.ld_u);
+    add(B.i_O, size_t(K) * m * B.ld_j);
+    add(B.i_OT, size_t(K) * m * B.ld_j);
+    add(B.i_Wp, size_t(K) * m * B.ld_n);
+    add(B.i_WT, size_t(K) * B.dmp * B.ld_j);
+    add(B.i_WTp, size_t(K) * B.dmp * B.ld_j);
+    B.i_dU = int(W.offsets.size());
+    W.add("dU32", size_t(B.md) * mp * 4);
+    return B;
+}
+
+dmrg_status bwd_simt(dmrg_handle h, const double* U, const void* O, const void* G, int in_is_fp64,
+                     void* dO, double* dU, const BwdDims& B, dmrg_precision p, void* ws,
+                     cudaStream_t s) {
+    const bool f64 = (p == DMRG_PREC_FP64);
+    const Real rt = f64 ? Real::F64 : Real::F32;
+    char* base = static_cast<char*>(ws);
+    void* W = base + B.ws.offsets[B.i_Wp];
+    void* Wp = base + B.ws.offsets[B.i_WT];
+    void* dUr = base + B.ws.offsets[B.i_dU];
+    const void* Uu = U;
+    const void* Ou = O;
+    const void* Gu = G;
+    const int64_t K = B.K, m = B.m, mp = B.mp, md = B.md, dmp = B.dmp;
+    cudaError_t e = cudaSuccess;
+    if (!f64) {
+        float* U32 = reinterpret_cast<float*>(base + B.ws.offsets[B.i_conv]);
+        float* O32 = reinterpret_cast<float*>(base + B.ws.offsets[B.i_conv + 1]);
+        float* G32 = reinterpret_cast<float*>(base + B.ws.offsets[B.i_conv + 2]);
+        PackJob jobs[3] = {};
+        int nj = 0;
+        auto conv = [&](const void* src, float* dst, int64_t rows, int64_t cols) {
+            PackJob& j = jobs[nj++];
+            j.src = src; j.src_f64 = 1; j.mode = 2; j.rows = rows; j.cols = cols;
+            j.rows_per_op = rows; j.rdiv = 1; j.s_r_hi = cols; j.s_c = 1; j.dst0 = dst; j.ld = cols;
+        };
+        conv(U, U32, md, mp);
+        Uu = U32;
+        if (in_is_fp64) {
+            conv(O, O32, K * m, m);
+            conv(G, G32, K * mp, mp);
+            Ou = O32;
+            Gu = G32;
+        }
+        e = timed_launch(h, "bwd_convert_fp32", s, [&] { return pack_launch(jobs, nj, nullptr, s); });
+        if (e != cudaSuccess) return cuda_fail(h, e, "convert");
+    }
+    // W_k = U G_k and W'_k = U G_k^T (md x mp each)
+    SimtGemm g{};
+    g.A = Uu; g.M = md; g.N = mp; g.K = mp;
+    g.sAb = 0; g.sAi = mp; g.sAk = 1;
+    g.B = Gu; g.sBb = mp * mp; g.sBk = mp; g.sBj = 1;
+    g.C = W; g.sCb = md * mp; g.sCi = mp; g.sCj = 1;
+    g.batch = int32_t(K);
+    e = timed_launch(h, "bwd_simt_W", s, [&] { return simt_gemm_launch(rt, g, s); });
+    if (e != cudaSuccess) return cuda_fail(h, e, "W");
+    g.sBk = 1; g.sBj = mp; g.C = Wp;
+    e = timed_launch(h, "bwd_simt_Wp", s, [&] { return simt_gemm_launch(rt, g, s); });
+    if (e != cudaSuccess) return cuda_fail(h, e, "W'");
+    if (dO) {
+        // dO_k[i][j] = sum_n (W_k)_r[i][n] U_r[j][n]
+        SimtGemm q{};
+        q.A = W; q.M = m; q.N = m; q.K = dmp;
+        q.sAb = md * mp; q.sAi = dmp; q.sAk = 1;
+        q.B = Uu; q.sBb = 0; q.sBk = 1; q.sBj = dmp;
+        q.C = dO; q.sCb = m * m; q.sCi = m; q.sCj = 1;
+        q.batch = int32_t(K);
+        e = timed_launch(h, "bwd_simt_dO", s, [&] { return simt_gemm_launch(rt, q, s); });
+        if (e != cudaSuccess) return cuda_fail(h, e, "dO");
+    }
+    if (dU) {
+        void* target = f64 ? static_cast<void*>(dU) : dUr;
+        // dU_r = sum_k O_k (W'_k)_r   then   += sum_k O_k^T (W_k)_r
+        SimtGemm q{};
+        q.A = Ou; q.M = m; q.N = dmp; q.K = m;
+        q.sAb = m * m; q.sAi = m; q.sAk = 1;
+        q.B = Wp; q.sBb = md * mp; q.sBk = dmp; q.sBj = 1;
+        q.C = target; q.sCb = 0; q.sCi = dmp; q.sCj = 1;
+        q.batch = int32_t(K);
+        q.reduce_batch = 1;
+        e = timed_launch(h, "bwd_simt_dU", s, [&] { return simt_gemm_launch(rt, q, s); });
+        if (e != cudaSuccess) return cuda_fail(h, e, "dU");
+        q.sAi = 1; q.sAk = m; q.B = W; q.accumulate = 1;
+        e = timed_launch(h, "bwd_simt_dU", s, [&] { return simt_gemm_launch(rt, q, s); });
+        if (e != cudaSuccess) return cuda_fail(h, e, "dU");
+        if (!f64) {
+            e = timed_launch(h, "bwd_dU_to_fp64", s, [&] {
+                return convert_f32_to_f64_launch(static_cast<const float*>(dUr), dU, md * mp, s);
+            });
+            if (e != cudaSuccess) return cuda_fail(h, e, "dU convert");
+        }
+    }
+    return DMRG_OK;
+}
+
+dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G, int in_is_fp64,
+                   void* dO, double* dU, const BwdDims& B, dmrg_precision p, void* ws,
+                   cudaStream_t s) {
+    const bool split = (p == DMRG_PREC_BF16X3);
+    const TcMode mode = split ? TC_BF16X3 : TC_TF32;
+    const int pmode = split ? 0 : 1;
+    const TcEpi epi_op = split ? EPI_SPLIT_BF16 : EPI_TF32;
+    const int64_t K = B.K, m = B.m, mp = B.mp, md = B.md, dmp = B.dmp;
+    const int d = B.d;
+    char* base = static_cast<char*>(ws);
+    auto sec = [&](int idx, int half) -> void* {
+        return base + B.ws.offsets[idx + (split ? half : 0)];
+    };
+    auto lo = [&](int idx) -> void* { return split ? sec(idx, 1) : sec(idx, 0); };
+    cudaError_t e;
+    // ---- packs
+    {
+        PackJob jobs[4] = {};
+        PackJob& ju = jobs[0];   // U: rows r, cols a
+        ju.src = U; ju.src_f64 = 1; ju.mode = pmode; ju.rows = md; ju.cols = mp; ju.rows_per_op = md;
+        ju.rdiv = 1; ju.s_r_hi = mp; ju.s_c = 1; ju.dst0 = sec(B.i_U, 0); ju.dst1 = lo(B.i_U); ju.ld = B.ld_u;
+        PackJob& jr = jobs[1];   // U_r: rows j, cols (s, a)
+        jr.src = U; jr.src_f64 = 1; jr.mode = pmode; jr.rows = m; jr.cols = dmp; jr.rows_per_op = m;
+        jr.rdiv = 1; jr.s_r_hi = dmp; jr.s_c = 1; jr.dst0 = sec(B.i_Ur, 0); jr.dst1 = lo(B.i_Ur); jr.ld = B.ld_n;
+        PackJob& jg = jobs[2];   // G: rows (k, a), cols b = G_k[a][b]
+        jg.src = G; jg.src_f64 = in_is_fp64; jg.mode = pmode; jg.rows = K * mp; jg.cols = mp;
+        jg.rows_per_op = K * mp; jg.rdiv = 1; jg.s_r_hi = mp; jg.s_c = 1;
+        jg.dst0 = sec(B.i_G, 0); jg.dst1 = lo(B.i_G); jg.ld = B.ld_u;
+        PackJob& jt = jobs[3];   // G^T: rows (k, b), cols a = G_k[a][b]
+        jt.src = G; jt.src_f64 = in_is_fp64; jt.mode = pmode; jt.rows = K * mp; jt.cols = mp;
+        jt.rows_per_op = mp; jt.s_op = mp * mp; jt.rdiv = 1; jt.s_r_hi = 1; jt.s_c = mp;
+        jt.dst0 = sec(B.i_GT, 0); jt.dst1 = lo(B.i_GT); jt.ld = B.ld_u;
+        e = timed_launch(h, "bwd_pack_UG", s, [&] { return pack_launch(jobs, 4, nullptr, s); });
+        if (e != cudaSuccess) return cuda_fail(h, e, "pack U/G");
+    }
+    if (dU) {
+        PackJob jobs[2] = {};
+        PackJob& jo = jobs[0];   // O: rows (k, i), cols j
+        jo.src = O; jo.src_f64 = in_is_fp64; jo.mode = pmode; jo.rows = K * m; jo.cols = m;
+        jo.rows_per_op = K * m; jo.rdiv = 1; jo.s_r_hi = m; jo.s_c = 1;
+        jo.dst0 = sec(B.i_O, 0); jo.dst1 = lo(B.i_O); jo.ld = B.ld_j;
+        PackJob& jt = jobs[1];   // O^T: rows (k, i), cols j = O_k[j][i]
+        jt.src = O; jt.src_f64 = in_is_fp64; jt.mode = pmode; jt.rows = K * m; jt.cols = m;
+        jt.rows_per_op = m; jt.s_op = m * m; jt.rdiv = 1; jt.s_r_hi = 1; jt.s_c = m;
+        jt.dst0 = sec(B.i_OT, 0); jt.dst1 = lo(B.i_OT); jt.ld = B.ld_j;
+        e = timed_launch(h, "bwd_pack_O", s, [&] { return pack_launch(jobs, 2, nullptr, s); });
+        if (e != cudaSuccess) return cuda_fail(h, e, "pack O");
+    }
+    const TcConfig cfg = tuned_config(h, shape_key("bwd", K, m, d, mp, p), mode);
+    const int grid = cfg.grid > 0 ? cfg.grid : h->num_sms;
+    auto launch = [&](const char* name, TcLaunch& L, TcEpi epi) -> dmrg_status {
+        L.table = nullptr;
+        int tiles = 0;
+        for (int i = 0; i < L.nprob; ++i) {
+            L.inline_prob[i].tile_start = tiles;
+            tiles += L.inline_prob[i].m_tiles * L.inline_prob[i].n_tiles * L.inline_prob[i].k_splits;
+        }
+        L.total_tiles = tiles;
+        L.status = h->d_status;
+        L.timeout_ns = timeout_ns(h);
+        cudaError_t ee = timed_launch(h, name, s, [&] {
+            return tc_gemm_launch(mode, epi, L, cfg.stages, grid, s);
+        });
+        return cuda_fail(h, ee, name);
+    };
+    dmrg_status st;
+    if (dO) {
+        // 1. W'_k[r][a] = sum_b G_k[a][b] U[r][b], rows (k, a), written as W'_k row-major.
+        TcLaunch L{};
+        TcProblem& P = L.inline_prob[0];
+        TcOperand A{sec(B.i_G, 0), lo(B.i_G), K * mp, mp, B.ld_u};
+        TcOperand Bo{sec(B.i_U, 0), lo(B.i_U), md, mp, B.ld_u};
+        if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, 1)) return fail(h, DMRG_ERR_CUDA, "tensor map");
+        TcScatter& S = P.sc[0];
+        S.rows_per_op = int32_t(mp); S.s_op = m * B.ld_n; S.s_row = 1;
+        S.col_div = d; S.s_col_hi = B.ld_n; S.s_col_lo = mp;
+        L.nprob = 1;
+        L.out[0][0] = sec(B.i_Wp, 0);
+        L.out[0][1] = lo(B.i_Wp);
+        if ((st = launch("bwd_tc_Wp_rows", L, epi_op)) != DMRG_OK) return st;
+        // 2. dO_k[i][j] = sum_(s,a) W'_k[j*d+s][a] U[i*d+s][a], rows (k, j), cols i.
+        TcLaunch L2{};
+        TcProblem& P2 = L2.inline_prob[0];
+        TcOperand A2{sec(B.i_Wp, 0), lo(B.i_Wp), K * m, dmp, B.ld_n};
+        TcOperand B2{sec(B.i_Ur, 0), lo(B.i_Ur), m, dmp, B.ld_n};
+        if (!make_problem(P2, mode, A2, B2, cfg.tile_n_max, 1)) return fail(h, DMRG_ERR_CUDA, "tensor map");
+        TcScatter& S2 = P2.sc[0];
+        S2.rows_per_op = int32_t(m); S2.s_op = m * m; S2.s_row = 1;
+        S2.col_div = 1; S2.s_col_hi = m; S2.s_col_lo = 0;
+        L2.nprob = 1;
+        L2.out[0][0] = dO;
+        if ((st = launch("bwd_tc_dO", L2, EPI_F32)) != DMRG_OK) return st;
+    }
+    if (dU) {
+        // 3. WT_k[s*mp + b][j] = W_k[j*d+s][b] and WT'_k likewise: one problem per s,
+        //    rows j (so stores run along j), columns (k, b).
+        for (int which = 0; which < 2; ++which) {
+            const int gsec = which == 0 ? B.i_GT : B.i_G;   // W = U G (B^T rows = G^T), W' = U G^T
+            const int osec = which == 0 ? B.i_WT : B.i_WTp;
+            for (int s0 = 0; s0 < d; s0 += kMaxInlineProblems) {
+                TcLaunch L{};
+                L.nprob = std::min(kMaxInlineProblems, d - s0);
+                for (int q = 0; q < L.nprob; ++q) {
+                    const int sidx = s0 + q;
+                    TcProblem& P = L.inline_prob[q];
+                    const int esz = split ? 2 : 4;
+                    TcOperand A{static_cast<char*>(sec(B.i_U, 0)) + size_t(sidx) * B.ld_u * esz,
+                                static_cast<char*>(lo(B.i_U)) + size_t(sidx) * B.ld_u * esz,
+                                m, mp, int64_t(d) * B.ld_u};
+                    TcOperand Bo{sec(gsec, 0), lo(gsec), K * mp, mp, B.ld_u};
+                    if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, 1))
+                        return fail(h, DMRG_ERR_CUDA, "tensor map");
+                    TcScatter& S = P.sc[0];
+                    S.rows_per_op = 1 << 30; S.s_op = 0; S.s_row = 1;
+                    S.col_div = int32_t(mp); S.s_col_hi = dmp * B.ld_j; S.s_col_lo = B.ld_j;
+                    S.out_off = int64_t(sidx) * mp * B.ld_j;
+                }
+                L.out[0][0] = sec(osec, 0);
+                L.out[0][1] = lo(osec);
+                if ((st = launch(which == 0 ? "bwd_tc_WT" : "bwd_tc_WTp", L, epi_op)) != DMRG_OK)
+                    return st;
+            }
+        }
+        // 4. dU_r[i][n] = sum_(k,j) O_k[i][j] WT'_k[n][j] + O_k[j][i] WT_k[n][j]
+        float* dUr = reinterpret_cast<float*>(base + B.ws.offsets[B.i_dU]);
+        e = cudaMemsetAsync(dUr, 0, size_t(md) * mp * 4, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "memset");
+        TcLaunch L{};
+        L.nprob = 2;
+        // The reduction runs over K*m terms.  Each split accumulates at most 16 k-blocks
+        // in the tensor core's FP32 accumulator (a chain no longer than the forward
+        // products'); the splits are then summed with FP32 atomics (round to nearest).
+        const int64_t kb = int64_t((m + (split ? 63 : 31)) / (split ? 64 : 32)) * K;
+        const int ksplit = int(std::max<int64_t>(1, (kb + 15) / 16));
+        for (int q = 0; q < 2; ++q) {
+            TcProblem& P = L.inline_prob[q];
+            const int asec = q == 0 ? B.i_O : B.i_OT;
+            const int bsec = q == 0 ? B.i_WTp : B.i_WT;
+            TcOperand A{sec(asec, 0), lo(asec), m, m, B.ld_j, K, m * B.ld_j};
+            TcOperand Bo{sec(bsec, 0), lo(bsec), dmp, m, B.ld_j, K, dmp * B.ld_j};
+            if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, ksplit))
+                return fail(h, DMRG_ERR_CUDA, "tensor map");
+            P.sc[0] = scatter_rowmajor(dmp);
+        }
+        L.out[0][0] = dUr;
+        if ((st = launch("bwd_tc_dU", L, EPI_F32_ATOMIC)) != DMRG_OK) return st;
+        e = timed_launch(h, "bwd_dU_to_fp64", s,
+                         [&] { return convert_f32_to_f64_launch(dUr, dU, md * mp, s); });
+        if (e != cudaSuccess) return cuda_fail(h, e, "dU convert");
+    }
+    return DMRG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dmrg_status dmrg_rotate_ops_backward_workspace(dmrg_handle h, int64_t K, int64_t m, int d,
+                                               int64_t mp, dmrg_precision p, size_t* bytes) {
+    if (!bytes) return fail(h, DMRG_ERR_INVALID_ARG, "bytes is NULL");
+    dmrg_status st = check_dense_args(h, K, m, d, mp, p);
+    if (st != DMRG_OK) return st;
+    *bytes = bwd_dims(K, m, d, mp, p).ws.total;
+    return DMRG_OK;
+}
+
+dmrg_status dmrg_rotate_ops_backward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
+                                     const void* O, const void* G, int in_is_fp64, int64_t K,
+                                     void* dO, double* dU, dmrg_precision p, void* ws,
+                                     size_t ws_bytes, dmrg_stream_t stream) {
+    dmrg_status st = check_dense_args(h, K, m, d, mp, p);
+    if (st != DMRG_OK) return st;
+    if (!U || !O || !G) return fail(h, DMRG_ERR_INVALID_ARG, "null data pointer");
+    if (p == DMRG_PREC_FP64 && !in_is_fp64)
+        return fail(h, DMRG_ERR_INVALID_ARG, "the FP64 precision needs FP64 operators");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (K == 0) {
+        if (dU) {
+            cudaError_t e = cudaMemsetAsync(dU, 0, size_t(m) * d * mp * sizeof(double), s);
+            return cuda_fail(h, e, "memset");
+        }
+        return DMRG_OK;
+    }
+    const BwdDims B = bwd_dims(K, m, d, mp, p);
+    st = check_ws(h, ws, ws_bytes, B.ws.total);
+    if (st != DMRG_OK) return st;
+    const bool tc = (p == DMRG_PREC_TF32 || p == DMRG_PREC_BF16X3);
+    if (tc && !tc_supported(h))
+        return fail(h, DMRG_ERR_UNSUPPORTED, "tensor-core precisions need an sm_103 GPU");
+    char key[256];
+    snprintf(key, sizeof key, "bwd:%p:%p:%p:%p:%p:%p:%p:%lld:%lld:%d:%lld:%d:%d", (const void*)U, O,
+             G, dO, (void*)dU, ws, (void*)s, (long long)K, (long long)m, d, (long long)mp, int(p),
+             in_is_fp64);
+    return run_maybe_graph(h, key, s, [&](cudaStream_t cs) -> dmrg_status {
+        if (tc) return bwd_tc(h, U, O, G, in_is_fp64, dO, dU, B, p, ws, cs);
+        return bwd_simt(h, U, O, G, in_is_fp64, dO, dU, B, p, ws, cs);
+    });
+}
+
+}  // extern "C"

@@ -27,6 +27,13 @@ struct SimtGemm {
     int32_t tile_start;   // first tile (grouped launches)
     int32_t tiles_m, tiles_n;
     int32_t batch;
+    int32_t reduce_batch; // 1: C = sum_b A[b] B[b] (one output, batch folded into the reduction)
+    // Grouped launches: A, B and C hold element offsets from bases[a_sel / b_sel / c_sel]
+    // of the launch (sel < 0: absolute pointers); a_boff / c_boff, when set, give the
+    // element offset of each batch entry instead of b * sAb / b * sCb.
+    int32_t a_sel, b_sel, c_sel, pad;
+    const int64_t* a_boff;
+    const int64_t* c_boff;
 };
 
 enum class Real { F64, F32 };
@@ -34,7 +41,7 @@ enum class Real { F64, F32 };
 // Launches one batched GEMM (or a grouped list already in device memory).
 cudaError_t simt_gemm_launch(Real t, const SimtGemm& g, cudaStream_t s);
 cudaError_t simt_gemm_grouped_launch(Real t, const SimtGemm* d_problems, int nprob,
-                                     int total_tiles, cudaStream_t s);
+                                     int total_tiles, const void* const bases[4], cudaStream_t s);
 int simt_tile_m();
 int simt_tile_n();
 
@@ -50,24 +57,30 @@ cudaError_t convert_f32_to_f64_launch(const float* src, double* dst, int64_t n, 
 cudaError_t fill_zero_launch(void* p, size_t bytes, cudaStream_t s);
 
 // ---------------------------------------------------------------- tensor-core GEMM
-// One grouped GEMM problem for the tcgen05 kernel: D (M x N) = A (M x Kred) B (N x Kred)^T,
-// both operands K-major, stored as BF16 hi/lo pairs (BF16X3) or FP32 (TF32).
-// The epilogue scatters element (row R, col n) to
-//   out + out_off + (op_off ? op_off[R / rows_per_op] : (R / rows_per_op) * s_op)
-//       + (R % rows_per_op) * s_row + (n / col_div) * s_col_hi + (n % col_div) * s_col_lo.
+// One grouped GEMM problem for the tcgen05 kernel:
+//   D (M x N) = sum_{z < nbatch} A_z (M x Kred) B_z (N x Kred)^T,
+// both operands K-major and stored as BF16 hi/lo pairs (BF16X3) or FP32 (TF32),
+// seen through 3-D tensor maps (reduction, rows, z).  The epilogue writes D through
+// up to two scatter maps; scatter c sends element (row R, col n) to
+//   out_c + out_off + (op_off ? op_off[R / rows_per_op] : (R / rows_per_op) * s_op)
+//         + (R % rows_per_op) * s_row + (n / col_div) * s_col_hi + (n % col_div) * s_col_lo.
+struct TcScatter {
+    int64_t out_off, s_op, s_row, s_col_hi, s_col_lo;
+    const int64_t* op_off;
+    int32_t rows_per_op, col_div;
+};
+
 struct TcProblem {  // 64-byte aligned through its CUtensorMap members
     CUtensorMap tmA[2];  // hi, lo (lo unused for TF32)
     CUtensorMap tmB[2];
-    int32_t M, N, Kred;
+    int32_t M, N, Kred;  // Kred: reduction length of one z slice
+    int32_t nbatch;      // reduction also runs over z = 0 .. nbatch-1
     int32_t tile_n;      // N tile width (multiple of 16, <= 256)
     int32_t m_tiles, n_tiles, k_splits, kb_per_split;
     int32_t tile_start;  // first global tile of this problem
-    int32_t rows_per_op;
-    int32_t col_div;
+    int32_t nscatter;    // 1 or 2
     int32_t pad0;
-    int64_t out_off;
-    int64_t s_op, s_row, s_col_hi, s_col_lo;
-    const int64_t* op_off;
+    TcScatter sc[2];
 };
 
 enum TcMode : int { TC_BF16X3 = 0, TC_TF32 = 1, TC_BF16 = 2 };
@@ -82,30 +95,43 @@ struct TcConfig {
     }
 };
 
+constexpr int kMaxInlineProblems = 4;
+
 struct TcLaunch {
-    TcProblem inline_prob;        // used when table == nullptr
+    TcProblem inline_prob[kMaxInlineProblems];  // used when table == nullptr
     const TcProblem* table;       // grouped problems in device memory
     int32_t nprob;
     int32_t total_tiles;
-    void* out0;                   // FP32 output / BF16 hi output / TF32 output
-    void* out1;                   // BF16 lo output
+    void* out[2][2];              // [scatter][hi, lo]: FP32/TF32 output in [c][0]
     unsigned* status;
     uint64_t timeout_ns;
+    int32_t drop_arrival;   // test hook: CTA 0 withholds its first stage release
+};
+
+// One operand seen by the kernel: `nbatch` slices of rows x cols (cols = the
+// reduction, contiguous), row stride ld elements, slice stride in elements.
+struct TcOperand {
+    const void* hi;
+    const void* lo;
+    int64_t rows, cols, ld;
+    int64_t nbatch = 1;
+    int64_t batch_stride = 0;
 };
 
 cudaError_t tc_gemm_launch(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
                            cudaStream_t s);
 int tc_max_stages(TcMode mode, int tile_n_max);
 
-// Encodes a 2-D K-major operand map: rows x cols (cols = reduction, contiguous),
-// row stride ld elements, box = box_rows x (128 bytes of cols), 128-byte swizzle.
+// Encodes a K-major operand map (3-D: cols, rows, batch), box = box_rows x 128 bytes.
 bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t rows, int64_t cols,
-                        int64_t ld, int box_rows);
+                        int64_t ld, int box_rows, int64_t nbatch = 1, int64_t batch_stride = 0);
 // Chooses an N tile (multiple of 16, <= tile_n_max) that splits N evenly.
 int choose_tile_n(int64_t N, int tile_n_max);
-// Fills the tiling fields of a problem (tile counts, splits) for a reduction.
-void finish_problem(TcProblem& p, int64_t M, int64_t N, int64_t Kred, int tile_n, int k_splits,
-                    TcMode mode);
+// Fills operand maps and tiling fields of a problem: D (M x N) += A B^T over Kred x nbatch.
+bool make_problem(TcProblem& p, TcMode mode, const TcOperand& A, const TcOperand& B,
+                  int tile_n_max, int k_splits);
+// Scatter for a plain row-major (rows x cols, leading dimension ld) destination.
+TcScatter scatter_rowmajor(int64_t ld);
 
 // ---------------------------------------------------------------- packer
 // Gathers and converts a strided source matrix into K-major tensor-core
@@ -127,11 +153,16 @@ struct PackJob {
     void* dst1;            // lo (BF16)
     int64_t ld;            // dst row stride in elements
     int64_t block_start;   // first CUDA block of this job (grouped launch)
+    // Grouped launches from a device table: src holds an element offset from
+    // srcs[src_sel] of the launch and dst0 / dst1 hold byte offsets from its
+    // workspace base (rel = 1); rel = 0 means absolute pointers.
+    int32_t rel, src_sel;
 };
 cudaError_t pack_launch(const PackJob* jobs_host, int njobs, PackJob* jobs_dev_or_null,
                         cudaStream_t s);
 int64_t pack_blocks_for(const PackJob& j);
 cudaError_t pack_grouped_launch(const PackJob* jobs_dev, int njobs, int64_t total_blocks,
+                                const void* const srcs[2], void* ws_base, int src1_f64,
                                 cudaStream_t s);
 
 // ---------------------------------------------------------------- backward helpers
@@ -151,6 +182,7 @@ struct dmrg_handle_s {
     bool timing = false;
     double wait_timeout_ms = 2000.0;
     double check_ortho_tol = 0.0;
+    int drop_arrival_next = 0;      // test hook, consumed by the next tensor-core launch
 
     struct Timed {
         std::string name;

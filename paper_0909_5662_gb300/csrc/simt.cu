@@ -25,8 +25,6 @@ __device__ __forceinline__ void simt_gemm_tile(const SimtGemm& g, int64_t b, int
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
     const int64_t i0 = int64_t(tm) * BM, j0 = int64_t(tn) * BN;
-    const T* A = static_cast<const T*>(g.A) + b * g.sAb;
-    const T* B = static_cast<const T*>(g.B) + b * g.sBb;
     T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -35,7 +33,12 @@ __device__ __forceinline__ void simt_gemm_tile(const SimtGemm& g, int64_t b, int
 
     const bool a_kfast = (g.sAk == 1);
     const bool b_jfast = (g.sBj == 1);
+    const int64_t bb0 = g.reduce_batch ? 0 : b;
+    const int64_t bb1 = g.reduce_batch ? g.batch : b + 1;
+    for (int64_t bb = bb0; bb < bb1; ++bb)
     for (int64_t k0 = 0; k0 < g.K; k0 += BK) {
+        const T* A = static_cast<const T*>(g.A) + (g.a_boff ? g.a_boff[bb] : bb * g.sAb);
+        const T* B = static_cast<const T*>(g.B) + bb * g.sBb;
 #pragma unroll
         for (int q = 0; q < (BM * BK) / NT; ++q) {
             const int e = tid + q * NT;
@@ -68,7 +71,7 @@ __device__ __forceinline__ void simt_gemm_tile(const SimtGemm& g, int64_t b, int
         __syncthreads();
     }
     if (EPI == SE_STORE) {
-        T* C = static_cast<T*>(g.C) + b * g.sCb;
+        T* C = static_cast<T*>(g.C) + (g.c_boff ? g.c_boff[b] : b * g.sCb);
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             const int64_t gi = i0 + ty + 16 * a;
@@ -117,16 +120,27 @@ __global__ void __launch_bounds__(NT) simt_gemm_kernel(const SimtGemm g, double*
     simt_gemm_tile<T, EPI>(g, b, int(r / g.tiles_n), int(r % g.tiles_n), ortho_acc);
 }
 
+struct SimtBases {
+    const void* p[4];
+};
+
 template <typename T>
 __global__ void __launch_bounds__(NT) simt_gemm_grouped_kernel(const SimtGemm* __restrict__ probs,
-                                                               int nprob) {
+                                                               int nprob, const SimtBases bases) {
     const int t = blockIdx.x;
     int lo = 0, hi = nprob - 1;
     while (lo < hi) {  // last problem with tile_start <= t
         const int mid = (lo + hi + 1) >> 1;
         if (probs[mid].tile_start <= t) lo = mid; else hi = mid - 1;
     }
-    const SimtGemm g = probs[lo];
+    SimtGemm g = probs[lo];
+    auto rebase = [&](const void* off, int sel) -> const void* {
+        if (sel < 0) return off;
+        return static_cast<const T*>(bases.p[sel]) + reinterpret_cast<intptr_t>(off);
+    };
+    g.A = rebase(g.A, g.a_sel);
+    g.B = rebase(g.B, g.b_sel);
+    g.C = const_cast<void*>(rebase(g.C, g.c_sel));
     const int64_t local = t - g.tile_start;
     const int64_t per_b = int64_t(g.tiles_m) * g.tiles_n;
     const int64_t b = local / per_b;
@@ -181,7 +195,7 @@ cudaError_t simt_gemm_launch(Real t, const SimtGemm& g0, cudaStream_t s) {
     if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return cudaSuccess;
     g.tiles_m = int((g.M + BM - 1) / BM);
     g.tiles_n = int((g.N + BN - 1) / BN);
-    const int64_t blocks = int64_t(g.tiles_m) * g.tiles_n * g.batch;
+    const int64_t blocks = int64_t(g.tiles_m) * g.tiles_n * (g.reduce_batch ? 1 : g.batch);
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     if (t == Real::F64)
         simt_gemm_kernel<double, SE_STORE><<<unsigned(blocks), NT, 0, s>>>(g, nullptr);
@@ -191,12 +205,14 @@ cudaError_t simt_gemm_launch(Real t, const SimtGemm& g0, cudaStream_t s) {
 }
 
 cudaError_t simt_gemm_grouped_launch(Real t, const SimtGemm* d_problems, int nprob,
-                                     int total_tiles, cudaStream_t s) {
+                                     int total_tiles, const void* const bases[4], cudaStream_t s) {
     if (nprob <= 0 || total_tiles <= 0) return cudaSuccess;
+    SimtBases b;
+    for (int i = 0; i < 4; ++i) b.p[i] = bases[i];
     if (t == Real::F64)
-        simt_gemm_grouped_kernel<double><<<total_tiles, NT, 0, s>>>(d_problems, nprob);
+        simt_gemm_grouped_kernel<double><<<total_tiles, NT, 0, s>>>(d_problems, nprob, b);
     else
-        simt_gemm_grouped_kernel<float><<<total_tiles, NT, 0, s>>>(d_problems, nprob);
+        simt_gemm_grouped_kernel<float><<<total_tiles, NT, 0, s>>>(d_problems, nprob, b);
     return cudaGetLastError();
 }
 

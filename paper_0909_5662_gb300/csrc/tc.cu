@@ -31,14 +31,17 @@ constexpr int kBM = 128;             // rows per tile (TMEM lanes)
 constexpr int kRowBytes = 128;       // one swizzle row: 64 BF16 or 32 FP32 of the reduction
 constexpr uint32_t kTmemCols = 512;  // two accumulators of up to 256 FP32 columns
 constexpr uint32_t kAccStride = 256;
+// Winding down after an expired wait: copies and MMAs already issued are waited for
+// with this fixed limit, whatever limit the caller chose for the main waits.
+constexpr uint64_t kDrainTimeoutNs = 2000000000ull;
 
 struct Decoded {
     const TcProblem* P;
-    int mt, nt, kb_begin, kb_end;
+    int mt, nt, kb_begin, kb_end, kb_per_batch;
 };
 
 __device__ __forceinline__ Decoded decode_tile(const TcLaunch& L, int t, int elems_per_row) {
-    const TcProblem* P = &L.inline_prob;
+    const TcProblem* P = &L.inline_prob[0];
     if (L.table != nullptr) {
         int lo = 0, hi = L.nprob - 1;
         while (lo < hi) {
@@ -46,6 +49,9 @@ __device__ __forceinline__ Decoded decode_tile(const TcLaunch& L, int t, int ele
             if (L.table[mid].tile_start <= t) lo = mid; else hi = mid - 1;
         }
         P = &L.table[lo];
+    } else {
+        for (int i = 1; i < L.nprob; ++i)
+            if (L.inline_prob[i].tile_start <= t) P = &L.inline_prob[i];
     }
     Decoded d;
     d.P = P;
@@ -55,7 +61,8 @@ __device__ __forceinline__ Decoded decode_tile(const TcLaunch& L, int t, int ele
     const int rem = local - ks * per_split;
     d.mt = rem / P->n_tiles;
     d.nt = rem - d.mt * P->n_tiles;
-    const int kb_total = (P->Kred + elems_per_row - 1) / elems_per_row;
+    d.kb_per_batch = (P->Kred + elems_per_row - 1) / elems_per_row;
+    const int kb_total = d.kb_per_batch * P->nbatch;
     d.kb_begin = ks * P->kb_per_split;
     d.kb_end = min(kb_total, d.kb_begin + P->kb_per_split);
     return d;
@@ -124,11 +131,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ------------------------------------------------------------ TMA producer
         if (lane == 0) {
             if (L.table == nullptr) {
-                tma_prefetch_desc(&L.inline_prob.tmA[0]);
-                tma_prefetch_desc(&L.inline_prob.tmB[0]);
-                if (kSplit) {
-                    tma_prefetch_desc(&L.inline_prob.tmA[1]);
-                    tma_prefetch_desc(&L.inline_prob.tmB[1]);
+                for (int i = 0; i < L.nprob; ++i) {
+                    tma_prefetch_desc(&L.inline_prob[i].tmA[0]);
+                    tma_prefetch_desc(&L.inline_prob[i].tmB[0]);
+                    if (kSplit) {
+                        tma_prefetch_desc(&L.inline_prob[i].tmA[1]);
+                        tma_prefetch_desc(&L.inline_prob[i].tmB[1]);
+                    }
                 }
             }
             int stage = 0;
@@ -149,12 +158,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     mbar_arrive_expect_tx(&full[stage], bytes);
-                    const int x = kb * kElemsPerRow;
-                    tma_load_2d(stage_a(stage, 0), &P->tmA[0], &full[stage], x, ya);
-                    tma_load_2d(stage_b(stage, 0), &P->tmB[0], &full[stage], x, yb);
+                    const int z = kb / dt.kb_per_batch;
+                    const int x = (kb - z * dt.kb_per_batch) * kElemsPerRow;
+                    tma_load_3d(stage_a(stage, 0), &P->tmA[0], &full[stage], x, ya, z);
+                    tma_load_3d(stage_b(stage, 0), &P->tmB[0], &full[stage], x, yb, z);
                     if (kSplit) {
-                        tma_load_2d(stage_a(stage, 1), &P->tmA[1], &full[stage], x, ya);
-                        tma_load_2d(stage_b(stage, 1), &P->tmB[1], &full[stage], x, yb);
+                        tma_load_3d(stage_a(stage, 1), &P->tmA[1], &full[stage], x, ya, z);
+                        tma_load_3d(stage_b(stage, 1), &P->tmB[1], &full[stage], x, yb, z);
                     }
                     armed |= 1u << stage;
                     armed_parity = (armed_parity & ~(1u << stage)) | (phase << stage);
@@ -168,7 +178,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int s = 0; s < stages; ++s)
                 if (armed & (1u << s)) {
                     volatile int never = 0;
-                    mbar_wait(&full[s], (armed_parity >> s) & 1u, tmo, L.status,
+                    mbar_wait(&full[s], (armed_parity >> s) & 1u, kDrainTimeoutNs, L.status,
                               reinterpret_cast<volatile int*>(&never));
                 }
         }
@@ -196,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     tc_fence_after();
-                    const int rem = P->Kred - kb * kElemsPerRow;
+                    const int rem = P->Kred - (kb % dt.kb_per_batch) * kElemsPerRow;
                     const int steps = min(kStepsPerBlock, (rem + kUmmaK - 1) / kUmmaK);
                     const uint64_t ah = smem_desc_sw128(smem_u32(stage_a(stage, 0)));
                     const uint64_t bh = smem_desc_sw128(smem_u32(stage_b(stage, 0)));
@@ -215,7 +225,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                             mma_bf16(tmem_d, ah + off, bh + off, idesc, accum);
                         }
                     }
-                    mma_commit(&empty[stage]);
+                    // Test hook: withhold one release so that the producer's bounded wait on
+                    // this stage expires (a barrier that nothing arrives on).
+                    const bool withhold = L.drop_arrival && blockIdx.x == 0 && it == 0 &&
+                                          kb == dt.kb_begin;
+                    if (!withhold) mma_commit(&empty[stage]);
                     if (++stage == stages) {
                         stage = 0;
                         phase ^= 1u;
@@ -227,7 +241,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // Every issued MMA has finished before TMEM is released.
             mma_commit(drain);
             volatile int never = 0;
-            mbar_wait(drain, 0, tmo, L.status, reinterpret_cast<volatile int*>(&never));
+            mbar_wait(drain, 0, kDrainTimeoutNs, L.status, reinterpret_cast<volatile int*>(&never));
         }
     } else {
         // ------------------------------------------------------------ epilogue (warps 2..5)
@@ -238,23 +252,26 @@ __global__ void __launch_bounds__(kThreads, 1)
             const TcProblem* P = dt.P;
             const int acc = it & 1;
             const uint32_t acc_parity = uint32_t(it >> 1) & 1u;
-            if (!mbar_wait(&tfull[acc], acc_parity, tmo, L.status, vabort)) break;
+            // One lane waits and the warp follows its verdict, so the warp-collective
+            // tcgen05.ld below is always executed by all 32 lanes or by none.
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(&tfull[acc], acc_parity, tmo, L.status, vabort) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
             tc_fence_after();
             const int row = dt.mt * kBM + quad * 32 + lane;
             const bool row_ok = row < P->M;
-            int64_t row_base = 0;
-            if (row_ok) {
-                const int g = row / P->rows_per_op;
-                const int rr = row - g * P->rows_per_op;
-                row_base = P->out_off + (P->op_off ? P->op_off[g] : int64_t(g) * P->s_op) +
-                           int64_t(rr) * P->s_row;
-            }
             const int n0 = dt.nt * P->tile_n;
             const int ncols = min(P->tile_n, P->N - n0);
-            const int cdiv = P->col_div;
-            const int64_t sch = P->s_col_hi, scl = P->s_col_lo;
-            const bool vec4 = (EPI == EPI_SPLIT_BF16) && cdiv == 4 && scl == 1 &&
-                              ((row_base & 3) == 0) && ((sch & 3) == 0);
+            int64_t rbase[2] = {0, 0};
+            for (int sci = 0; sci < P->nscatter; ++sci) {
+                const TcScatter& S = P->sc[sci];
+                const int g = row / S.rows_per_op;
+                const int rr = row - g * S.rows_per_op;
+                if (row_ok)
+                    rbase[sci] = S.out_off + (S.op_off ? S.op_off[g] : int64_t(g) * S.s_op) +
+                                 int64_t(rr) * S.s_row;
+            }
             for (int c = 0; c < ncols; c += 32) {
                 uint32_t r[32];
                 tmem_ld_32x32b_x32(tmem_base + uint32_t(acc) * kAccStride +
@@ -263,55 +280,82 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tmem_ld_wait();
                 if (!row_ok) continue;
                 const int cmax = min(32, ncols - c);
-                if (EPI == EPI_SPLIT_BF16) {
-                    __nv_bfloat16* hi = static_cast<__nv_bfloat16*>(L.out0);
-                    __nv_bfloat16* lo = static_cast<__nv_bfloat16*>(L.out1);
-                    if (vec4 && cmax == 32) {
+                for (int sci = 0; sci < P->nscatter; ++sci) {
+                    const TcScatter& S = P->sc[sci];
+                    const int64_t row_base = rbase[sci];
+                    const int cdiv = S.col_div;
+                    const int64_t sch = S.s_col_hi, scl = S.s_col_lo;
+                    if (EPI == EPI_SPLIT_BF16) {
+                        __nv_bfloat16* hi = static_cast<__nv_bfloat16*>(L.out[sci][0]);
+                        __nv_bfloat16* lo = static_cast<__nv_bfloat16*>(L.out[sci][1]);
+                        const bool vec4 = cdiv == 4 && scl == 1 && ((row_base & 3) == 0) &&
+                                          ((sch & 3) == 0) && cmax == 32;
+                        if (vec4) {
 #pragma unroll
-                        for (int j = 0; j < 32; j += 4) {
-                            const int n = n0 + c + j;
-                            const int64_t idx = row_base + int64_t(n >> 2) * sch;
-                            __nv_bfloat16 h[4], l[4];
+                            for (int j = 0; j < 32; j += 4) {
+                                const int n = n0 + c + j;
+                                const int64_t idx = row_base + int64_t(n >> 2) * sch;
+                                __nv_bfloat16 h[4], l[4];
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const float v = __uint_as_float(r[j + e]);
-                                h[e] = __float2bfloat16_rn(v);
-                                l[e] = __float2bfloat16_rn(v - __bfloat162float(h[e]));
+                                for (int e = 0; e < 4; ++e) {
+                                    const float v = __uint_as_float(r[j + e]);
+                                    h[e] = __float2bfloat16_rn(v);
+                                    l[e] = __float2bfloat16_rn(v - __bfloat162float(h[e]));
+                                }
+                                uint2 hv, lv;
+                                hv.x = uint32_t(__bfloat16_as_ushort(h[0])) |
+                                       (uint32_t(__bfloat16_as_ushort(h[1])) << 16);
+                                hv.y = uint32_t(__bfloat16_as_ushort(h[2])) |
+                                       (uint32_t(__bfloat16_as_ushort(h[3])) << 16);
+                                lv.x = uint32_t(__bfloat16_as_ushort(l[0])) |
+                                       (uint32_t(__bfloat16_as_ushort(l[1])) << 16);
+                                lv.y = uint32_t(__bfloat16_as_ushort(l[2])) |
+                                       (uint32_t(__bfloat16_as_ushort(l[3])) << 16);
+                                *reinterpret_cast<uint2*>(hi + idx) = hv;
+                                *reinterpret_cast<uint2*>(lo + idx) = lv;
                             }
-                            uint2 hv, lv;
-                            hv.x = uint32_t(__bfloat16_as_ushort(h[0])) |
-                                   (uint32_t(__bfloat16_as_ushort(h[1])) << 16);
-                            hv.y = uint32_t(__bfloat16_as_ushort(h[2])) |
-                                   (uint32_t(__bfloat16_as_ushort(h[3])) << 16);
-                            lv.x = uint32_t(__bfloat16_as_ushort(l[0])) |
-                                   (uint32_t(__bfloat16_as_ushort(l[1])) << 16);
-                            lv.y = uint32_t(__bfloat16_as_ushort(l[2])) |
-                                   (uint32_t(__bfloat16_as_ushort(l[3])) << 16);
-                            *reinterpret_cast<uint2*>(hi + idx) = hv;
-                            *reinterpret_cast<uint2*>(lo + idx) = lv;
+                        } else {
+                            for (int j = 0; j < cmax; ++j) {
+                                const int n = n0 + c + j;
+                                const int64_t idx = row_base + int64_t(n / cdiv) * sch +
+                                                    int64_t(n % cdiv) * scl;
+                                const float v = __uint_as_float(r[j]);
+                                const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                                hi[idx] = h;
+                                lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+                            }
                         }
                     } else {
-                        for (int j = 0; j < cmax; ++j) {
-                            const int n = n0 + c + j;
-                            const int64_t idx = row_base + int64_t(n / cdiv) * sch +
-                                                int64_t(n % cdiv) * scl;
-                            const float v = __uint_as_float(r[j]);
-                            const __nv_bfloat16 h = __float2bfloat16_rn(v);
-                            hi[idx] = h;
-                            lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
-                        }
-                    }
-                } else {
-                    float* out = static_cast<float*>(L.out0);
+                        float* out = static_cast<float*>(L.out[sci][0]);
+                        const bool contiguous = (cdiv == 1 && sch == 1);
+                        if (EPI != EPI_F32_ATOMIC && contiguous && cmax == 32 &&
+                            (((row_base + n0 + c) & 3) == 0)) {
+                            float4* o4 = reinterpret_cast<float4*>(out + row_base + n0 + c);
+#pragma unroll
+                            for (int j = 0; j < 32; j += 4) {
+                                float4 v;
+                                v.x = __uint_as_float(r[j]);
+                                v.y = __uint_as_float(r[j + 1]);
+                                v.z = __uint_as_float(r[j + 2]);
+                                v.w = __uint_as_float(r[j + 3]);
+                                if (EPI == EPI_TF32) {
+                                    v.x = tf32_round(v.x); v.y = tf32_round(v.y);
+                                    v.z = tf32_round(v.z); v.w = tf32_round(v.w);
+                                }
+                                o4[j >> 2] = v;
+                            }
+                        } else {
 #pragma unroll 4
-                    for (int j = 0; j < cmax; ++j) {
-                        const int n = n0 + c + j;
-                        const int64_t idx =
-                            row_base + int64_t(n / cdiv) * sch + int64_t(n % cdiv) * scl;
-                        const float v = __uint_as_float(r[j]);
-                        if (EPI == EPI_F32) out[idx] = v;
-                        else if (EPI == EPI_TF32) out[idx] = tf32_round(v);
-                        else atomicAdd(out + idx, v);
+                            for (int j = 0; j < cmax; ++j) {
+                                const int n = n0 + c + j;
+                                const int64_t idx =
+                                    row_base + int64_t(n / cdiv) * sch + int64_t(n % cdiv) * scl;
+                                const float v = __uint_as_float(r[j]);
+                                if (EPI == EPI_F32) out[idx] = v;
+                                else if (EPI == EPI_TF32) out[idx] = tf32_round(v);
+                                else atomicAdd(out + idx, v);
+                            }
+                        }
                     }
                 }
             }
@@ -334,6 +378,9 @@ struct PackLaunch {
     PackJob inline_jobs[4];
     const PackJob* table;
     int njobs;
+    const void* srcs[2];
+    char* ws_base;
+    int src1_f64;  // precision of srcs[1] for relative jobs
 };
 
 constexpr int kPackThreads = 256;
@@ -381,7 +428,14 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constan
         }
         J = &L.table[lo];
     }
-    const PackJob& j = *J;
+    PackJob j = *J;
+    if (j.rel) {
+        if (j.src_sel == 1) j.src_f64 = L.src1_f64;
+        const size_t es = j.src_f64 ? 8 : 4;
+        j.src = static_cast<const char*>(L.srcs[j.src_sel]) + reinterpret_cast<intptr_t>(j.src) * es;
+        j.dst0 = L.ws_base + reinterpret_cast<intptr_t>(j.dst0);
+        j.dst1 = j.dst1 ? L.ws_base + reinterpret_cast<intptr_t>(j.dst1) : nullptr;
+    }
     const int64_t total = j.rows * j.cols;
     const int64_t e0 = (int64_t(b - j.block_start) * kPackThreads + threadIdx.x) * kPackElems;
 #pragma unroll
@@ -497,10 +551,10 @@ cudaError_t tc_gemm_launch(TcMode mode, TcEpi epi, const TcLaunch& L, int stages
                            cudaStream_t s) {
     if (L.total_tiles <= 0) return cudaSuccess;
     int bn = 16;
-    if (L.table == nullptr) {
-        bn = L.inline_prob.tile_n;
+    if (L.table == nullptr && L.nprob >= 1 && L.nprob <= kMaxInlineProblems) {
+        for (int i = 0; i < L.nprob; ++i) bn = std::max(bn, L.inline_prob[i].tile_n);
     } else {
-        return cudaErrorInvalidValue;  // grouped launches go through tc_gemm_launch_bn
+        return cudaErrorInvalidValue;  // device-table launches go through tc_gemm_launch_grouped
     }
     const size_t smem = tc_smem_bytes(mode, stages, bn);
     if (smem > 232448) return cudaErrorInvalidConfiguration;
@@ -529,6 +583,9 @@ cudaError_t tc_gemm_launch_grouped(TcMode mode, TcEpi epi, const TcLaunch& L, in
     DMRG_TC_CASE(TC_BF16X3, EPI_SPLIT_BF16)
     DMRG_TC_CASE(TC_BF16X3, EPI_F32)
     DMRG_TC_CASE(TC_BF16X3, EPI_F32_ATOMIC)
+    DMRG_TC_CASE(TC_TF32, EPI_TF32)
+    DMRG_TC_CASE(TC_TF32, EPI_F32)
+    DMRG_TC_CASE(TC_TF32, EPI_F32_ATOMIC)
 #undef DMRG_TC_CASE
     return cudaErrorNotSupported;
 }
@@ -572,11 +629,17 @@ cudaError_t pack_launch(const PackJob* jobs, int njobs, PackJob* /*unused*/, cud
 }
 
 cudaError_t pack_grouped_launch(const PackJob* jobs_dev, int njobs, int64_t total_blocks,
+                                const void* const srcs[2], void* ws_base, int src1_f64,
                                 cudaStream_t s) {
     if (njobs <= 0 || total_blocks <= 0) return cudaSuccess;
+    if (total_blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     PackLaunch L{};
     L.table = jobs_dev;
     L.njobs = njobs;
+    L.srcs[0] = srcs[0];
+    L.srcs[1] = srcs[1];
+    L.ws_base = static_cast<char*>(ws_base);
+    L.src1_f64 = src1_f64;
     pack_kernel<<<unsigned(total_blocks), kPackThreads, 0, s>>>(L);
     return cudaGetLastError();
 }
@@ -587,7 +650,7 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 }
 
 bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t rows, int64_t cols,
-                        int64_t ld, int box_rows) {
+                        int64_t ld, int box_rows, int64_t nbatch, int64_t batch_stride) {
     if (g_encode == nullptr) {
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q;
@@ -598,12 +661,15 @@ bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t r
         g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
     const int esize = fp32 ? 4 : 2;
-    cuuint64_t gdim[2] = {cuuint64_t(cols), cuuint64_t(rows)};
-    cuuint64_t gstride[1] = {cuuint64_t(ld) * esize};
-    cuuint32_t box[2] = {cuuint32_t(kRowBytes / esize), cuuint32_t(box_rows)};
-    cuuint32_t estride[2] = {1, 1};
+    if (nbatch < 1) nbatch = 1;
+    if (nbatch == 1) batch_stride = rows * ld;
+    cuuint64_t gdim[3] = {cuuint64_t(cols), cuuint64_t(rows), cuuint64_t(nbatch)};
+    cuuint64_t gstride[2] = {cuuint64_t(ld) * esize, cuuint64_t(std::max<int64_t>(batch_stride, 1)) * esize};
+    if (nbatch == 1) gstride[1] = (gstride[1] + 15) / 16 * 16;
+    cuuint32_t box[3] = {cuuint32_t(kRowBytes / esize), cuuint32_t(box_rows), 1};
+    cuuint32_t estride[3] = {1, 1, 1};
     CUresult r = g_encode(map, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
-                          2, const_cast<void*>(base), gdim, gstride, box, estride,
+                          3, const_cast<void*>(base), gdim, gstride, box, estride,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -618,20 +684,54 @@ int choose_tile_n(int64_t N, int tile_n_max) {
     return int(t);
 }
 
-void finish_problem(TcProblem& p, int64_t M, int64_t N, int64_t Kred, int tile_n, int k_splits,
-                    TcMode mode) {
-    const int elems = (mode == TC_TF32) ? 32 : 64;
-    p.M = int32_t(M);
-    p.N = int32_t(N);
-    p.Kred = int32_t(Kred);
+bool make_problem(TcProblem& p, TcMode mode, const TcOperand& A, const TcOperand& B,
+                  int tile_n_max, int k_splits) {
+    const bool f32 = (mode == TC_TF32);
+    const bool split = (mode == TC_BF16X3);
+    const int elems = f32 ? 32 : 64;
+    if (A.cols != B.cols || A.nbatch != B.nbatch) return false;
+    const int tile_n = choose_tile_n(B.rows, tile_n_max);
+    for (int i = 0; i < (split ? 2 : 1); ++i) {
+        const void* a = i ? A.lo : A.hi;
+        const void* b = i ? B.lo : B.hi;
+        if (!encode_operand_map(&p.tmA[i], a, f32, A.rows, A.cols, A.ld, 128, A.nbatch, A.batch_stride) ||
+            !encode_operand_map(&p.tmB[i], b, f32, B.rows, B.cols, B.ld, tile_n, B.nbatch, B.batch_stride))
+            return false;
+    }
+    if (!split) {
+        p.tmA[1] = p.tmA[0];
+        p.tmB[1] = p.tmB[0];
+    }
+    p.M = int32_t(A.rows);
+    p.N = int32_t(B.rows);
+    p.Kred = int32_t(A.cols);
+    p.nbatch = int32_t(A.nbatch);
     p.tile_n = tile_n;
-    p.m_tiles = int32_t((M + kBM - 1) / kBM);
-    p.n_tiles = int32_t((N + tile_n - 1) / tile_n);
-    const int kb_total = int((Kred + elems - 1) / elems);
+    p.m_tiles = int32_t((A.rows + kBM - 1) / kBM);
+    p.n_tiles = int32_t((B.rows + tile_n - 1) / tile_n);
+    const int kb_total = int((A.cols + elems - 1) / elems) * int(A.nbatch);
     if (k_splits < 1) k_splits = 1;
     if (k_splits > kb_total) k_splits = kb_total;
     p.kb_per_split = (kb_total + k_splits - 1) / k_splits;
     p.k_splits = (kb_total + p.kb_per_split - 1) / p.kb_per_split;
+    p.tile_start = 0;
+    p.nscatter = 1;
+    p.sc[0] = scatter_rowmajor(B.rows);
+    p.sc[1] = p.sc[0];
+    return true;
+}
+
+TcScatter scatter_rowmajor(int64_t ld) {
+    TcScatter sc{};
+    sc.out_off = 0;
+    sc.rows_per_op = 1 << 30;
+    sc.s_op = 0;
+    sc.s_row = ld;
+    sc.col_div = 1;
+    sc.s_col_hi = 1;
+    sc.s_col_lo = 0;
+    sc.op_off = nullptr;
+    return sc;
 }
 
 }  // namespace dmrg

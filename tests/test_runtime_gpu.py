@@ -1,0 +1,134 @@
+"""Runtime features around the rotation kernels: CUDA-graph replay, per-kernel
+event timing, the autotuner and its cache file, the orthonormality check option,
+and the device-side bounded waits (failure detection without a GPU fault)."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from workloads import dense_workload, orthonormal_columns
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_0909_5662_gb300 as P
+    return P
+
+
+def _inputs(seed=9, m=96, d=4, mp=80, K=12):
+    w = dense_workload("rt", seed, d, m, mp, K)
+    dev = torch.device("cuda")
+    return w, torch.from_numpy(w.U).to(dev), torch.from_numpy(w.O).to(dev, torch.float32)
+
+
+def test_graph_replay_matches_eager(P):
+    w, U, O = _inputs()
+    h = P.Handle()
+    try:
+        eager = P.dmrg_rotate_ops(U, O, 4, "bf16x3", handle=h).clone()
+        P.dmrg_set_option("graph", 1, handle=h)
+        out = torch.empty_like(eager)
+        for _ in range(3):  # first call captures, the others replay
+            out.zero_()
+            P.dmrg_rotate_ops(U, O, 4, "bf16x3", out=out, handle=h)
+            torch.cuda.synchronize()
+            assert torch.equal(out, eager)
+        # the graph reads the inputs at replay time
+        O2 = O * 2
+        P.dmrg_rotate_ops(U, O2, 4, "fp32", handle=h)
+        torch.cuda.synchronize()
+        O.mul_(2)
+        P.dmrg_rotate_ops(U, O, 4, "bf16x3", out=out, handle=h)
+        torch.cuda.synchronize()
+        assert torch.allclose(out, 2 * eager, rtol=1e-5, atol=1e-5)
+        P.dmrg_sync_status(handle=h)
+    finally:
+        h.close()
+
+
+def test_kernel_timing_report(P):
+    w, U, O = _inputs()
+    h = P.Handle()
+    try:
+        P.dmrg_set_option("kernel_timing", 1, handle=h)
+        for _ in range(2):
+            P.dmrg_rotate_ops(U, O, 4, "bf16x3", handle=h)
+        rep = P.dmrg_kernel_timing(reset=True, handle=h)
+        names = {r["kernel"]: r for r in rep}
+        for k in ("pack_O", "pack_U", "tc_gemm_first_product", "tc_gemm_second_product"):
+            assert names[k]["launches"] == 2 and names[k]["total_ms"] > 0
+        assert P.dmrg_kernel_timing(reset=True, handle=h) == []
+    finally:
+        h.close()
+
+
+def test_autotuner_and_cache_file(P, tmp_path):
+    path = tmp_path / "tune.json"
+    os.environ["DMRG_AUTOTUNE_CACHE"] = str(path)
+    try:
+        w, U, O = _inputs(m=128, mp=128, K=20)
+        ref = oracle.rotate_dense(w.U, w.O.astype(np.float32).astype(np.float64), 4)
+        h = P.Handle()
+        out = P.dmrg_autotune_rotate_ops(U, O, 4, "bf16x3", handle=h)
+        torch.cuda.synchronize()
+        got = out.double().cpu().numpy()
+        err = np.linalg.norm((got - ref).reshape(20, -1), axis=1) / np.linalg.norm(ref.reshape(20, -1), axis=1)
+        assert err.max() <= 1e-5
+        data = json.loads(path.read_text())
+        assert any(k.startswith("g1:") for k in data) and any(k.startswith("g2:") for k in data)
+        h.close()
+        # a new handle starts from the cached choice and still computes the same result
+        h2 = P.Handle()
+        out2 = P.dmrg_rotate_ops(U, O, 4, "bf16x3", handle=h2)
+        torch.cuda.synchronize()
+        assert torch.equal(out, out2)
+        h2.close()
+    finally:
+        del os.environ["DMRG_AUTOTUNE_CACHE"]
+
+
+def test_orthonormality_check_option(P):
+    from paper_0909_5662_gb300 import _capi
+    w, U, O = _inputs()
+    h = P.Handle()
+    try:
+        P.dmrg_set_option("check_ortho", 1e-10, handle=h)
+        P.dmrg_rotate_ops(U, O, 4, "bf16x3", handle=h)           # orthonormal: accepted
+        with pytest.raises(_capi.DmrgError) as ei:
+            P.dmrg_rotate_ops(U * 1.01, O, 4, "bf16x3", handle=h)  # not orthonormal: refused
+        assert ei.value.status == 3
+    finally:
+        h.close()
+
+
+def test_bounded_wait_expiry_is_reported(P):
+    # Failure detection without a GPU fault: the test hook makes the first CTA of the
+    # next tensor-core launch withhold one stage release, so the producer's bounded
+    # wait (limit 50 ms here) runs out on a barrier that nothing arrives on.  The
+    # kernel winds down, the handle reports DMRG_ERR_TIMEOUT, and the context stays
+    # usable: the next call is correct and reports no error.
+    from paper_0909_5662_gb300 import _capi
+    w, U, O = _inputs(m=400, mp=400, K=40)
+    h = P.Handle()
+    try:
+        P.dmrg_set_option("wait_timeout_ms", 50, handle=h)
+        P.dmrg_set_option("test_withhold_arrival", 1, handle=h)
+        P.dmrg_rotate_ops(U, O, 4, "bf16x3", handle=h)
+        with pytest.raises(_capi.DmrgError) as ei:
+            P.dmrg_sync_status(handle=h)
+        assert ei.value.status == 6
+        P.dmrg_set_option("wait_timeout_ms", 2000, handle=h)
+        out = P.dmrg_rotate_ops(U, O, 4, "bf16x3", handle=h)
+        P.dmrg_sync_status(handle=h)   # cleared and clean
+        ref = oracle.rotate_dense(w.U, w.O[:4].astype(np.float32).astype(np.float64), 4)
+        got = out[:4].double().cpu().numpy()
+        err = np.linalg.norm((got - ref).reshape(len(ref), -1), axis=1) / \
+            np.linalg.norm(ref.reshape(len(ref), -1), axis=1)
+        assert err.max() <= 1e-5
+    finally:
+        h.close()
