@@ -184,6 +184,83 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------- GPU leg
+# ---------------------------------------------------------------------------- chained sweep
+def run_chained(args):
+    """50 consecutive block-growth steps at d = 4, m = m' = 1200, K = 300: the rotated
+    operators of step s are the inputs of step s + 1, with a fresh seeded orthonormal U
+    per step.  BF16x3 and TF32 carry all 300 operators; the FP64 GPU path carries a
+    tracked subset (operators are independent given U) as the drift reference, and its
+    first step is checked against the FP64 CPU oracle.  At the end the FP64 two-point
+    functions <psi|O'_i O'_j|psi> of the tracked operators are compared."""
+    import numpy as np
+    import torch
+    import paper_0909_5662_gb300 as P
+    from workloads import chained_inputs, SEED_BASE
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    d, m, K = 4, 1200, 300
+    steps = args.sweep_steps
+    track = list(range(0, K, K // 16))[:16]
+    g = torch.Generator(device=dev)
+    g.manual_seed(SEED_BASE + 5)
+    O0 = torch.randn(K, m, m, generator=g, dtype=torch.float64, device=dev)
+    psi = torch.randn(m, generator=g, dtype=torch.float64, device=dev)
+    psi /= torch.linalg.vector_norm(psi)
+    cur = {"bf16x3": O0.float(), "tf32": O0.float()}
+    ref = O0[track].clone()
+    outs = {p: torch.empty_like(cur[p]) for p in cur}
+    ref_out = torch.empty_like(ref)
+    drift = {p: [] for p in cur}
+    ms = {p: 0.0 for p in cur}
+    oracle_step1 = None
+    for step in range(steps):
+        U = chained_inputs(step, m * d, m, dev)
+        for p in cur:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            P.dmrg_rotate_ops(U, cur[p], d, p, out=outs[p])
+            b.record()
+            b.synchronize()
+            ms[p] += a.elapsed_time(b)
+            cur[p], outs[p] = outs[p], cur[p]
+        P.dmrg_rotate_ops(U, ref, d, "fp64", out=ref_out)
+        ref, ref_out = ref_out, ref
+        P.dmrg_sync_status()
+        if step == 0 and not args.no_cpu_baseline:
+            import oracle
+            sub = [0, 1]
+            r0 = oracle.rotate_dense(U.cpu().numpy(), O0[[track[i] for i in sub]].cpu().numpy(), d)
+            num = np.linalg.norm((ref[sub].cpu().numpy() - r0).reshape(len(sub), -1), axis=1)
+            oracle_step1 = float((num / np.linalg.norm(r0.reshape(len(sub), -1), axis=1)).max())
+        for p in cur:
+            x = cur[p][track].double()
+            num = torch.linalg.vector_norm((x - ref).reshape(len(track), -1), dim=1)
+            den = torch.linalg.vector_norm(ref.reshape(len(track), -1), dim=1)
+            drift[p].append(float((num / den).max()))
+    C_ref = P.dmrg_correlations(ref, psi)
+    corr = {}
+    for p in cur:
+        C = P.dmrg_correlations(cur[p][track].contiguous(), psi)
+        corr[p] = float((torch.linalg.vector_norm(C - C_ref) / torch.linalg.vector_norm(C_ref)).item())
+    flops_step = 2.0 * K * d * m * m * (m + m)
+    line = {"workload": "chained_m1200_k300 (d=4, m=m'=1200, K=300, %d steps)" % steps,
+            "metric": "chained sweep: rotated operators/s per precision, accumulated drift",
+            "unit": UNIT, "steps": steps,
+            "precisions": {p: {"ms_per_step": ms[p] / steps,
+                               "ops_per_s": K / (ms[p] / steps * 1e-3),
+                               "eff_tflops": flops_step / (ms[p] / steps * 1e-3) / 1e12,
+                               "max_rel_fro_drift_first": drift[p][0],
+                               "max_rel_fro_drift_last": drift[p][-1],
+                               "drift_per_step": drift[p],
+                               "correlation_rel_err": corr[p]} for p in cur},
+            "fp64_reference": {"tracked_operators": track, "oracle_step1_rel_err": oracle_step1},
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -191,6 +268,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="dense", choices=["dense", "chained"],
+                    help="dense: the benchmark line; chained: the 50-step sweep report")
+    ap.add_argument("--sweep-steps", type=int, default=50)
     ap.add_argument("--profile", action="store_true",
                     help="only the BF16x3 step: warm-up then --steps steps (for ncu captures)")
     args = ap.parse_args()
@@ -198,6 +278,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "chained":
+        return run_chained(args)
 
     import numpy as np
     import torch
@@ -317,18 +399,14 @@ def main():
     err_bf = rel(out_bf, out_64)
     err_tf = rel(out_tf, out_64)
 
-    # ---- end to end through the public API with host buffers (pinned), copies timed
+    # ---- end to end through the public API with host buffers (pinned): one
+    #      dmrg_rotate_ops_host call per step copies the operators in, rotates them
+    #      and copies the result out, overlapping the three in chunks.
     Oh = torch.from_numpy(w.O.astype(np.float32)).pin_memory()
     Uh = torch.from_numpy(w.U).pin_memory()
-    Ob = torch.empty_like(O32)
-    Ub = torch.empty_like(U)
     outh = torch.empty((K, MP, MP), dtype=torch.float32).pin_memory()
-    outd = torch.empty((K, MP, MP), dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
-        Ob.copy_(Oh, non_blocking=True)
-        Ub.copy_(Uh, non_blocking=True)
-        P.dmrg_rotate_ops(Ub, Ob, D, "bf16x3", out=outd)
-        outh.copy_(outd, non_blocking=True)
+        P.dmrg_rotate_ops_host(Uh, Oh, D, "bf16x3", out=outh, synchronize=False)
     barrier()
     e_ms = 0.0
     for _ in range(args.steps):
@@ -336,17 +414,14 @@ def main():
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record()
-        Ob.copy_(Oh, non_blocking=True)
-        Ub.copy_(Uh, non_blocking=True)
-        P.dmrg_rotate_ops(Ub, Ob, D, "bf16x3", out=outd)
-        outh.copy_(outd, non_blocking=True)
+        P.dmrg_rotate_ops_host(Uh, Oh, D, "bf16x3", out=outh, synchronize=False)
         b.record()
         b.synchronize()
         e_ms += a.elapsed_time(b)
     e_ms = max_over_ranks(e_ms / args.steps)
     h2d = Oh.numel() * 4 + Uh.numel() * 8
     d2h = outh.numel() * 4
-
+    e2e_err = rel(outh.to(dev), out_64)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(w)
@@ -377,7 +452,9 @@ def main():
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": K_total / (e_ms * 1e-3), "unit": UNIT, "ms_per_step": e_ms,
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "api": "dmrg_rotate_ops_host (pinned host buffers, chunked copy/compute overlap)",
+                    "max_rel_fro_err_vs_fp64": e2e_err},
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": clocks,
         }

@@ -140,6 +140,23 @@ DMRG_API dmrg_status dmrg_rotate_ops(dmrg_handle handle, const double* U, int64_
                             dmrg_precision precision, void* ws, size_t ws_bytes,
                             dmrg_stream_t stream);
 
+/* The same rotation with U, O and Oout in HOST memory (page-locked for the copies
+ * to overlap the computation; pageable memory works but serialises).  The batch is
+ * processed in chunks of `chunk` consecutive operators (0 = about K/6): while chunk
+ * c is rotated on `stream`, chunk c+1 is copied in and chunk c-1 copied out on two
+ * streams owned by the handle, so host-to-device copies, kernels and
+ * device-to-host copies overlap.  Operators are independent given U, which is what
+ * makes the split exact (the paper's UMD distribution rests on the same fact,
+ * Sec. 3.2).  ws: device workspace of dmrg_rotate_ops_host_workspace() bytes.
+ * Asynchronous on `stream`: Oout is complete once `stream` is. */
+DMRG_API dmrg_status dmrg_rotate_ops_host_workspace(dmrg_handle handle, int64_t K, int64_t m, int d,
+                                                    int64_t mp, dmrg_precision precision,
+                                                    int in_is_fp64, int64_t chunk, size_t* bytes);
+DMRG_API dmrg_status dmrg_rotate_ops_host(dmrg_handle handle, const double* U, int64_t m, int d,
+                                          int64_t mp, const void* O, int in_is_fp64, int64_t K,
+                                          void* Oout, dmrg_precision precision, int64_t chunk,
+                                          void* ws, size_t ws_bytes, dmrg_stream_t stream);
+
 /* Runs every candidate tiling of the tensor-core kernels on these buffers,
  * times them with CUDA events and caches the fastest for this shape in the
  * handle (and in the JSON file named by $DMRG_AUTOTUNE_CACHE, if set).

@@ -13,6 +13,7 @@ from .api import (  # noqa: F401
     dmrg_rotate_ops,
     dmrg_rotate_ops_workspace,
     dmrg_rotate_ops_noalloc,
+    dmrg_rotate_ops_host,
     dmrg_autotune_rotate_ops,
     dmrg_rotate_ops_backward,
     dmrg_orthonormality_error,

@@ -143,6 +143,48 @@ def dmrg_rotate_ops(U: torch.Tensor, O: torch.Tensor, d: int, precision="bf16x3"
     return out
 
 
+def _need_host(t: torch.Tensor, name: str, dtypes, dims=None):
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise ValueError("%s must be a host (CPU) tensor" % name)
+    if t.dtype not in dtypes:
+        raise TypeError("%s must have dtype in %s, got %s" % (name, dtypes, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if dims is not None and t.dim() != dims:
+        raise ValueError("%s must have %d dimensions" % (name, dims))
+
+
+def dmrg_rotate_ops_host(U: torch.Tensor, O: torch.Tensor, d: int, precision="bf16x3",
+                         out: Optional[torch.Tensor] = None, chunk: int = 0,
+                         handle: Optional[Handle] = None, stream=None,
+                         synchronize: bool = True) -> torch.Tensor:
+    """The rotation with U, O and the result in host memory (pin them with
+    ``tensor.pin_memory()`` for copies that overlap the kernels)."""
+    h = handle or default_handle()
+    _need_host(U, "U", (torch.float64,), 2)
+    _need_host(O, "O", (torch.float64, torch.float32), 3)
+    K, m, m2 = O.shape
+    if m != m2 or U.shape[0] != m * d:
+        raise ValueError("shape mismatch")
+    mp = U.shape[1]
+    p = _prec(precision)
+    odt = torch.float64 if p == 0 else torch.float32
+    if out is None:
+        out = torch.empty((K, mp, mp), dtype=odt, pin_memory=True)
+    _need_host(out, "out", (odt,), 3)
+    f64 = int(O.dtype == torch.float64)
+    n = ctypes.c_size_t()
+    _capi.check(h.lib.dmrg_rotate_ops_host_workspace(h.h, K, m, d, mp, p, f64, chunk, ctypes.byref(n)),
+                h.h, "dmrg_rotate_ops_host_workspace")
+    ws = h.workspace(n.value)
+    st = _stream(stream)
+    _capi.check(h.lib.dmrg_rotate_ops_host(h.h, _ptr(U), m, d, mp, _ptr(O), f64, K, _ptr(out), p, chunk,
+                                           _ptr(ws), ws.numel(), st), h.h, "dmrg_rotate_ops_host")
+    if synchronize:
+        (torch.cuda.current_stream() if stream is None else stream).synchronize()
+    return out
+
+
 def dmrg_rotate_ops_noalloc(U: torch.Tensor, O: torch.Tensor, d: int, precision="bf16x3",
                             out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     """The dense rotation with no handle and no workspace: scratch is the

@@ -115,17 +115,19 @@ DenseDims dense_dims(int64_t K, int64_t m, int d, int64_t mp, dmrg_precision p) 
     D.ld2 = (D.md + align - 1) / align * align;
     const size_t es = (p == DMRG_PREC_TF32) ? 4 : 2;
     WsLayout& W = D.ws;
+    // Sections that depend only on U come first, so that calls on slices of one
+    // operator batch (the host-buffer pipeline) can share them.
     if (p == DMRG_PREC_FP64) {
         W.add("T", size_t(K) * D.md * mp * 8);
     } else if (p == DMRG_PREC_FP32) {
-        W.add("O32", size_t(K) * m * m * 4);
         W.add("U32", size_t(D.md) * mp * 4);
+        W.add("O32", size_t(K) * m * m * 4);
         W.add("T", size_t(K) * D.md * mp * 4);
     } else {
         const int nsplit = (p == DMRG_PREC_BF16X3) ? 2 : 1;
-        for (int s = 0; s < nsplit; ++s) W.add("Op", size_t(K) * m * D.ld1 * es);
         for (int s = 0; s < nsplit; ++s) W.add("B1", size_t(d) * mp * D.ld1 * es);
         for (int s = 0; s < nsplit; ++s) W.add("B2", size_t(mp) * D.ld2 * es);
+        for (int s = 0; s < nsplit; ++s) W.add("Op", size_t(K) * m * D.ld1 * es);
         for (int s = 0; s < nsplit; ++s) W.add("T", size_t(K) * mp * D.ld2 * es);
     }
     return D;
@@ -153,7 +155,8 @@ TcConfig tuned_config(dmrg_handle h, const std::string& key, TcMode mode) {
     if (it != h->tune_cache.end()) return it->second;
     TcConfig c;
     c.tile_n_max = 256;
-    c.stages = tc_max_stages(mode, 256);
+    c.row_bytes = 128;
+    c.stages = tc_max_stages(mode, 256, c.row_bytes);
     c.grid = 0;
     return c;
 }
@@ -169,7 +172,7 @@ std::string shape_key(const char* tag, int64_t K, int64_t m, int d, int64_t mp, 
 dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
                              const void* O, int in_is_fp64, int64_t K, void* Oout,
                              dmrg_precision p, void* ws, const TcConfig& c1, const TcConfig& c2,
-                             cudaStream_t s) {
+                             cudaStream_t s, bool pack_u) {
     const DenseDims D = dense_dims(K, m, d, mp, p);
     const bool split = (p == DMRG_PREC_BF16X3);
     const TcMode mode = split ? TC_BF16X3 : TC_TF32;
@@ -181,9 +184,9 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     void* B2[2] = {nullptr, nullptr};
     void* Tt[2] = {nullptr, nullptr};
     const int ns = split ? 2 : 1;
-    for (int i = 0; i < ns; ++i) Op[i] = base + D.ws.offsets[si++];
     for (int i = 0; i < ns; ++i) B1[i] = base + D.ws.offsets[si++];
     for (int i = 0; i < ns; ++i) B2[i] = base + D.ws.offsets[si++];
+    for (int i = 0; i < ns; ++i) Op[i] = base + D.ws.offsets[si++];
     for (int i = 0; i < ns; ++i) Tt[i] = base + D.ws.offsets[si++];
 
     // ---- operand packing: O (stacked K*m x m), U_r' (rows b*d + s, cols j), U^T.
@@ -204,7 +207,7 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     j2.rdiv = 1; j2.s_r_hi = 1; j2.s_r_lo = 0; j2.s_c = mp;
     j2.dst0 = B2[0]; j2.dst1 = B2[1]; j2.ld = D.ld2;
     cudaError_t e = timed_launch(h, "pack_O", s, [&] { return pack_launch(jobs, 1, nullptr, s); });
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && pack_u)
         e = timed_launch(h, "pack_U", s, [&] { return pack_launch(jobs + 1, 2, nullptr, s); });
     if (e != cudaSuccess) return cuda_fail(h, e, "pack");
 
@@ -215,7 +218,7 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     {
         TcOperand A{Op[0], Op[1], K * m, m, D.ld1};
         TcOperand B{B1[0], B1[1], int64_t(d) * mp, m, D.ld1};
-        if (!make_problem(P1, mode, A, B, c1.tile_n_max, 1))
+        if (!make_problem(P1, mode, A, B, c1.tile_n_max, 1, c1.row_bytes))
             return fail(h, DMRG_ERR_CUDA, "cuTensorMapEncodeTiled failed (first product)");
     }
     TcScatter& S1 = P1.sc[0];
@@ -233,6 +236,7 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     L1.status = h->d_status;
     L1.timeout_ns = timeout_ns(h);
     L1.drop_arrival = take_drop_arrival(h);
+    L1.row_bytes = c1.row_bytes;
     const int grid1 = c1.grid > 0 ? c1.grid : h->num_sms;
     e = timed_launch(h, "tc_gemm_first_product", s, [&] {
         return tc_gemm_launch(mode, split ? EPI_SPLIT_BF16 : EPI_TF32, L1, c1.stages, grid1, s);
@@ -245,7 +249,7 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     {
         TcOperand A{Tt[0], Tt[1], K * mp, D.md, D.ld2};
         TcOperand B{B2[0], B2[1], mp, D.md, D.ld2};
-        if (!make_problem(P2, mode, A, B, c2.tile_n_max, 1))
+        if (!make_problem(P2, mode, A, B, c2.tile_n_max, 1, c2.row_bytes))
             return fail(h, DMRG_ERR_CUDA, "cuTensorMapEncodeTiled failed (second product)");
     }
     TcScatter& S2 = P2.sc[0];
@@ -261,6 +265,7 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     L2.out[0][0] = Oout;
     L2.status = h->d_status;
     L2.timeout_ns = timeout_ns(h);
+    L2.row_bytes = c2.row_bytes;
     const int grid2 = c2.grid > 0 ? c2.grid : h->num_sms;
     e = timed_launch(h, "tc_gemm_second_product", s, [&] {
         return tc_gemm_launch(mode, EPI_F32, L2, c2.stages, grid2, s);
@@ -271,7 +276,7 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
 
 dmrg_status dense_simt_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
                                const void* O, int in_is_fp64, int64_t K, void* Oout,
-                               dmrg_precision p, void* ws, cudaStream_t s) {
+                               dmrg_precision p, void* ws, cudaStream_t s, bool pack_u) {
     const DenseDims D = dense_dims(K, m, d, mp, p);
     char* base = static_cast<char*>(ws);
     const bool f64 = (p == DMRG_PREC_FP64);
@@ -282,8 +287,8 @@ dmrg_status dense_simt_forward(dmrg_handle h, const double* U, int64_t m, int d,
     if (f64) {
         T = base + D.ws.offsets[0];
     } else {
-        float* O32 = reinterpret_cast<float*>(base + D.ws.offsets[0]);
-        float* U32 = reinterpret_cast<float*>(base + D.ws.offsets[1]);
+        float* U32 = reinterpret_cast<float*>(base + D.ws.offsets[0]);
+        float* O32 = reinterpret_cast<float*>(base + D.ws.offsets[1]);
         T = base + D.ws.offsets[2];
         PackJob jobs[2] = {};
         int nj = 0;
@@ -293,12 +298,16 @@ dmrg_status dense_simt_forward(dmrg_handle h, const double* U, int64_t m, int d,
             j.rdiv = 1; j.s_r_hi = m; j.s_c = 1; j.dst0 = O32; j.ld = m;
             Ouse = O32;
         }
-        PackJob& j = jobs[nj++];
-        j.src = U; j.src_f64 = 1; j.mode = 2; j.rows = D.md; j.cols = mp; j.rows_per_op = D.md;
-        j.rdiv = 1; j.s_r_hi = mp; j.s_c = 1; j.dst0 = U32; j.ld = mp;
+        if (pack_u) {
+            PackJob& j = jobs[nj++];
+            j.src = U; j.src_f64 = 1; j.mode = 2; j.rows = D.md; j.cols = mp; j.rows_per_op = D.md;
+            j.rdiv = 1; j.s_r_hi = mp; j.s_c = 1; j.dst0 = U32; j.ld = mp;
+        }
         Uuse = U32;
-        e = timed_launch(h, "convert_fp32", s, [&] { return pack_launch(jobs, nj, nullptr, s); });
-        if (e != cudaSuccess) return cuda_fail(h, e, "convert");
+        if (nj > 0) {
+            e = timed_launch(h, "convert_fp32", s, [&] { return pack_launch(jobs, nj, nullptr, s); });
+            if (e != cudaSuccess) return cuda_fail(h, e, "convert");
+        }
     }
     const Real rt = f64 ? Real::F64 : Real::F32;
     // First product: T_k (m x d*mp) = O_k (m x m) * U_r (m x d*mp).
@@ -386,6 +395,11 @@ dmrg_status dmrg_destroy(dmrg_handle h) {
     for (auto ev : h->event_pool) cudaEventDestroy(ev);
     for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    if (h->copy_in) cudaStreamDestroy(h->copy_in);
+    if (h->copy_out) cudaStreamDestroy(h->copy_out);
+    for (cudaEvent_t ev : {h->ev_start, h->ev_u, h->ev_in[0], h->ev_in[1], h->ev_comp[0],
+                           h->ev_comp[1], h->ev_out[0], h->ev_out[1]})
+        if (ev) cudaEventDestroy(ev);
     if (h->d_status) cudaFree(h->d_status);
     delete h;
     return DMRG_OK;
@@ -496,11 +510,11 @@ dmrg_status dmrg_rotate_ops(dmrg_handle h, const double* U, int64_t m, int d, in
     snprintf(key, sizeof key, "dense:%p:%p:%p:%p:%p:%lld:%lld:%d:%lld:%d:%d", (const void*)U, O,
              Oout, ws, (void*)s, (long long)K, (long long)m, d, (long long)mp, int(p), in_is_fp64);
     return run_maybe_graph(h, key, s, [&](cudaStream_t cs) -> dmrg_status {
-        if (!tc) return dense_simt_forward(h, U, m, d, mp, O, in_is_fp64, K, Oout, p, ws, cs);
+        if (!tc) return dense_simt_forward(h, U, m, d, mp, O, in_is_fp64, K, Oout, p, ws, cs, true);
         const TcMode mode = (p == DMRG_PREC_BF16X3) ? TC_BF16X3 : TC_TF32;
         const TcConfig c1 = tuned_config(h, shape_key("g1", K, m, d, mp, p), mode);
         const TcConfig c2 = tuned_config(h, shape_key("g2", K, m, d, mp, p), mode);
-        return dense_tc_forward(h, U, m, d, mp, O, in_is_fp64, K, Oout, p, ws, c1, c2, cs);
+        return dense_tc_forward(h, U, m, d, mp, O, in_is_fp64, K, Oout, p, ws, c1, c2, cs, true);
     });
 }
 

@@ -42,11 +42,11 @@ std::string shape_key(const char* tag, int64_t K, int64_t m, int d, int64_t mp, 
 dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
                              const void* O, int in_is_fp64, int64_t K, void* Oout,
                              dmrg_precision p, void* ws, const TcConfig& c1, const TcConfig& c2,
-                             cudaStream_t s);
+                             cudaStream_t s, bool pack_u = true);
 
 dmrg_status dense_simt_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
                                const void* O, int in_is_fp64, int64_t K, void* Oout,
-                               dmrg_precision p, void* ws, cudaStream_t s);
+                               dmrg_precision p, void* ws, cudaStream_t s, bool pack_u = true);
 
 cudaError_t tc_gemm_launch_grouped(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
                                    int bn_smem, cudaStream_t s);

@@ -40,8 +40,11 @@ void load_tune_file(dmrg_handle h) {
         const size_t lb = text.find('[', end), rb = text.find(']', end);
         if (lb == std::string::npos || rb == std::string::npos || rb < lb) break;
         TcConfig c;
-        if (sscanf(text.c_str() + lb + 1, "%d , %d , %d", &c.tile_n_max, &c.stages, &c.grid) == 3 &&
-            c.tile_n_max >= 16 && c.tile_n_max <= 256 && c.stages >= 1 && c.stages <= 8 && c.grid >= 0)
+        const int n = sscanf(text.c_str() + lb + 1, "%d , %d , %d , %d", &c.tile_n_max, &c.stages,
+                             &c.grid, &c.row_bytes);
+        if (n == 3) c.row_bytes = 128;
+        if (n >= 3 && c.tile_n_max >= 16 && c.tile_n_max <= 256 && c.stages >= 1 && c.stages <= 8 &&
+            c.grid >= 0 && (c.row_bytes == 64 || c.row_bytes == 128))
             h->tune_cache[key] = c;
         pos = rb + 1;
     }
@@ -56,7 +59,8 @@ void save_tune_file(dmrg_handle h) {
     size_t i = 0;
     for (auto& kv : h->tune_cache) {
         f << "  \"" << kv.first << "\": [" << kv.second.tile_n_max << ", " << kv.second.stages << ", "
-          << kv.second.grid << "]" << (++i < h->tune_cache.size() ? ",\n" : "\n");
+          << kv.second.grid << ", " << kv.second.row_bytes << "]"
+          << (++i < h->tune_cache.size() ? ",\n" : "\n");
     }
     f << "}\n";
 }
@@ -72,13 +76,16 @@ std::vector<TcConfig> candidates(TcMode mode, int64_t N, int num_sms) {
         const int t = choose_tile_n(N, tn);
         if (std::find(seen.begin(), seen.end(), t) != seen.end()) continue;
         seen.push_back(t);
-        const int smax = tc_max_stages(mode, t);
-        for (int st = smax; st >= std::max(2, smax - 1); --st) {
-            TcConfig c;
-            c.tile_n_max = t;
-            c.stages = st;
-            c.grid = num_sms;
-            out.push_back(c);
+        for (int rb : {128, 64}) {
+            const int smax = tc_max_stages(mode, t, rb);
+            for (int st = smax; st >= std::max(2, smax - 1); --st) {
+                TcConfig c;
+                c.tile_n_max = t;
+                c.stages = st;
+                c.grid = num_sms;
+                c.row_bytes = rb;
+                out.push_back(c);
+            }
         }
     }
     return out;

@@ -222,6 +222,7 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
         L.total_tiles = tiles;
         L.status = h->d_status;
         L.timeout_ns = timeout_ns(h);
+        L.row_bytes = cfg.row_bytes;
         cudaError_t ee = timed_launch(h, name, s, [&] {
             return tc_gemm_launch(mode, epi, L, cfg.stages, grid, s);
         });
@@ -234,7 +235,7 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
         TcProblem& P = L.inline_prob[0];
         TcOperand A{sec(B.i_G, 0), lo(B.i_G), K * mp, mp, B.ld_u};
         TcOperand Bo{sec(B.i_U, 0), lo(B.i_U), md, mp, B.ld_u};
-        if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, 1)) return fail(h, DMRG_ERR_CUDA, "tensor map");
+        if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, 1, cfg.row_bytes)) return fail(h, DMRG_ERR_CUDA, "tensor map");
         TcScatter& S = P.sc[0];
         S.rows_per_op = int32_t(mp); S.s_op = m * B.ld_n; S.s_row = 1;
         S.col_div = d; S.s_col_hi = B.ld_n; S.s_col_lo = mp;
@@ -247,7 +248,7 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
         TcProblem& P2 = L2.inline_prob[0];
         TcOperand A2{sec(B.i_Wp, 0), lo(B.i_Wp), K * m, dmp, B.ld_n};
         TcOperand B2{sec(B.i_Ur, 0), lo(B.i_Ur), m, dmp, B.ld_n};
-        if (!make_problem(P2, mode, A2, B2, cfg.tile_n_max, 1)) return fail(h, DMRG_ERR_CUDA, "tensor map");
+        if (!make_problem(P2, mode, A2, B2, cfg.tile_n_max, 1, cfg.row_bytes)) return fail(h, DMRG_ERR_CUDA, "tensor map");
         TcScatter& S2 = P2.sc[0];
         S2.rows_per_op = int32_t(m); S2.s_op = m * m; S2.s_row = 1;
         S2.col_div = 1; S2.s_col_hi = m; S2.s_col_lo = 0;
@@ -272,7 +273,7 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
                                 static_cast<char*>(lo(B.i_U)) + size_t(sidx) * B.ld_u * esz,
                                 m, mp, int64_t(d) * B.ld_u};
                     TcOperand Bo{sec(gsec, 0), lo(gsec), K * mp, mp, B.ld_u};
-                    if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, 1))
+                    if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, 1, cfg.row_bytes))
                         return fail(h, DMRG_ERR_CUDA, "tensor map");
                     TcScatter& S = P.sc[0];
                     S.rows_per_op = 1 << 30; S.s_op = 0; S.s_row = 1;
@@ -294,7 +295,8 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
         // The reduction runs over K*m terms.  Each split accumulates at most 16 k-blocks
         // in the tensor core's FP32 accumulator (a chain no longer than the forward
         // products'); the splits are then summed with FP32 atomics (round to nearest).
-        const int64_t kb = int64_t((m + (split ? 63 : 31)) / (split ? 64 : 32)) * K;
+        const int64_t epr = cfg.row_bytes / (split ? 2 : 4);   // reduction elements per k-block
+        const int64_t kb = (m + epr - 1) / epr * K;
         const int ksplit = int(std::max<int64_t>(1, (kb + 15) / 16));
         for (int q = 0; q < 2; ++q) {
             TcProblem& P = L.inline_prob[q];
@@ -302,7 +304,7 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
             const int bsec = q == 0 ? B.i_WTp : B.i_WT;
             TcOperand A{sec(asec, 0), lo(asec), m, m, B.ld_j, K, m * B.ld_j};
             TcOperand Bo{sec(bsec, 0), lo(bsec), dmp, m, B.ld_j, K, dmp * B.ld_j};
-            if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, ksplit))
+            if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, ksplit, cfg.row_bytes))
                 return fail(h, DMRG_ERR_CUDA, "tensor map");
             P.sc[0] = scatter_rowmajor(dmp);
         }

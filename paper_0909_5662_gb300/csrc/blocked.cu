@@ -694,6 +694,7 @@ dmrg_status dmrg_rotate_ops_blocked(dmrg_handle h, dmrg_blocked_plan pl, const d
         L1.out[0][1] = lo;
         L1.status = h->d_status;
         L1.timeout_ns = timeout_ns(h);
+        L1.row_bytes = 128;
         const int st1 = tc_max_stages(mode, T->bn_first);
         e = timed_launch(h, "blk_tc_first_product", cs, [&] {
             return tc_gemm_launch_grouped(mode, tf32 ? EPI_TF32 : EPI_SPLIT_BF16, L1, std::min(st1, 4),
@@ -707,6 +708,7 @@ dmrg_status dmrg_rotate_ops_blocked(dmrg_handle h, dmrg_blocked_plan pl, const d
         L2.out[0][0] = Oout;
         L2.status = h->d_status;
         L2.timeout_ns = timeout_ns(h);
+        L2.row_bytes = 128;
         const int st2 = tc_max_stages(mode, T->bn_second);
         e = timed_launch(h, "blk_tc_second_product", cs, [&] {
             return tc_gemm_launch_grouped(mode, EPI_F32, L2, std::min(st2, 4), h->num_sms,

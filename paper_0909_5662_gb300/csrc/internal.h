@@ -61,9 +61,9 @@ cudaError_t fill_zero_launch(void* p, size_t bytes, cudaStream_t s);
 //   D (M x N) = sum_{z < nbatch} A_z (M x Kred) B_z (N x Kred)^T,
 // both operands K-major and stored as BF16 hi/lo pairs (BF16X3) or FP32 (TF32),
 // seen through 3-D tensor maps (reduction, rows, z).  The epilogue writes D through
-// up to two scatter maps; scatter c sends element (row R, col n) to
-//   out_c + out_off + (op_off ? op_off[R / rows_per_op] : (R / rows_per_op) * s_op)
-//         + (R % rows_per_op) * s_row + (n / col_div) * s_col_hi + (n % col_div) * s_col_lo.
+// the scatter map sc[0], which sends element (row R, col n) to
+//   out + out_off + (op_off ? op_off[R / rows_per_op] : (R / rows_per_op) * s_op)
+//       + (R % rows_per_op) * s_row + (n / col_div) * s_col_hi + (n % col_div) * s_col_lo.
 struct TcScatter {
     int64_t out_off, s_op, s_row, s_col_hi, s_col_lo;
     const int64_t* op_off;
@@ -78,9 +78,8 @@ struct TcProblem {  // 64-byte aligned through its CUtensorMap members
     int32_t tile_n;      // N tile width (multiple of 16, <= 256)
     int32_t m_tiles, n_tiles, k_splits, kb_per_split;
     int32_t tile_start;  // first global tile of this problem
-    int32_t nscatter;    // 1 or 2
-    int32_t pad0;
-    TcScatter sc[2];
+    int32_t pad0, pad1;
+    TcScatter sc[1];
 };
 
 enum TcMode : int { TC_BF16X3 = 0, TC_TF32 = 1, TC_BF16 = 2 };
@@ -90,8 +89,10 @@ struct TcConfig {
     int tile_n_max = 256;   // upper bound on the N tile (the split picks <= this)
     int stages = 3;
     int grid = 0;           // 0 = number of SMs
+    int row_bytes = 128;    // 128: 128-byte swizzle; 64: 64-byte swizzle, half-depth k-blocks
     bool operator==(const TcConfig& o) const {
-        return tile_n_max == o.tile_n_max && stages == o.stages && grid == o.grid;
+        return tile_n_max == o.tile_n_max && stages == o.stages && grid == o.grid &&
+               row_bytes == o.row_bytes;
     }
 };
 
@@ -102,10 +103,11 @@ struct TcLaunch {
     const TcProblem* table;       // grouped problems in device memory
     int32_t nprob;
     int32_t total_tiles;
-    void* out[2][2];              // [scatter][hi, lo]: FP32/TF32 output in [c][0]
+    void* out[1][2];              // [scatter][hi, lo]: FP32/TF32 output in [0][0]
     unsigned* status;
     uint64_t timeout_ns;
     int32_t drop_arrival;   // test hook: CTA 0 withholds its first stage release
+    int32_t row_bytes;      // 128 or 64: must match the problems' tensor maps
 };
 
 // One operand seen by the kernel: `nbatch` slices of rows x cols (cols = the
@@ -120,16 +122,17 @@ struct TcOperand {
 
 cudaError_t tc_gemm_launch(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
                            cudaStream_t s);
-int tc_max_stages(TcMode mode, int tile_n_max);
+int tc_max_stages(TcMode mode, int tile_n_max, int row_bytes = 128);
 
 // Encodes a K-major operand map (3-D: cols, rows, batch), box = box_rows x 128 bytes.
 bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t rows, int64_t cols,
-                        int64_t ld, int box_rows, int64_t nbatch = 1, int64_t batch_stride = 0);
+                        int64_t ld, int box_rows, int64_t nbatch = 1, int64_t batch_stride = 0,
+                        int row_bytes = 128);
 // Chooses an N tile (multiple of 16, <= tile_n_max) that splits N evenly.
 int choose_tile_n(int64_t N, int tile_n_max);
 // Fills operand maps and tiling fields of a problem: D (M x N) += A B^T over Kred x nbatch.
 bool make_problem(TcProblem& p, TcMode mode, const TcOperand& A, const TcOperand& B,
-                  int tile_n_max, int k_splits);
+                  int tile_n_max, int k_splits, int row_bytes = 128);
 // Scatter for a plain row-major (rows x cols, leading dimension ld) destination.
 TcScatter scatter_rowmajor(int64_t ld);
 
@@ -198,6 +201,12 @@ struct dmrg_handle_s {
     std::map<std::string, cudaGraphExec_t> graphs;
     cudaStream_t capture_stream = nullptr;
     bool capturing = false;
+
+    // host-buffer pipeline: copy-in and copy-out streams and their events
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_u = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
+                ev_out[2] = {nullptr, nullptr};
 };
 
 struct dmrg_blocked_plan_s;

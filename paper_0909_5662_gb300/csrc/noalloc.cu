@@ -92,7 +92,8 @@ extern "C" DMRG_API dmrg_status dmrg_rotate_ops_noalloc(const double* U, int64_t
     const dmrg::TcMode mode = (precision == DMRG_PREC_BF16X3) ? dmrg::TC_BF16X3 : dmrg::TC_TF32;
     dmrg::TcConfig cfg;
     cfg.tile_n_max = 256;
-    cfg.stages = dmrg::tc_max_stages(mode, 256);
+    cfg.row_bytes = 128;
+    cfg.stages = dmrg::tc_max_stages(mode, 256, cfg.row_bytes);
     return dmrg::dense_tc_forward(h, U, m, d, mp, O, in_is_fp64, K, Oout, precision, c->ws, cfg,
                                   cfg, s);
 }

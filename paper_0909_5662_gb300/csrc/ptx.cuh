@@ -175,15 +175,18 @@ __device__ __forceinline__ void tmem_ld_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor (tcgen05 format): K-major operand tile whose
-// rows are 128 bytes, 128-byte swizzled, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+// Shared-memory matrix descriptor (tcgen05 format) of a K-major operand tile whose
+// rows are RB bytes long and RB-byte swizzled (RB = 128 or 64), 8-row groups RB*8 bytes
+// apart.
+template <int RB>
+__device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t saddr) {
+    static_assert(RB == 128 || RB == 64, "row bytes");
     uint64_t d = 0;
-    d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);  // start address
-    d |= static_cast<uint64_t>(1) << 16;                   // leading byte offset (unused, 16 B)
-    d |= static_cast<uint64_t>(1024 >> 4) << 32;           // stride byte offset: 8 rows x 128 B
-    d |= static_cast<uint64_t>(1) << 46;                   // descriptor version
-    d |= static_cast<uint64_t>(2) << 61;                   // 128-byte swizzle
+    d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);   // start address
+    d |= static_cast<uint64_t>(1) << 16;                    // leading byte offset (unused, 16 B)
+    d |= static_cast<uint64_t>((RB * 8) >> 4) << 32;        // stride byte offset: 8 rows
+    d |= static_cast<uint64_t>(1) << 46;                    // descriptor version
+    d |= static_cast<uint64_t>(RB == 128 ? 2 : 4) << 61;    // 128- or 64-byte swizzle
     return d;
 }
 

@@ -28,7 +28,6 @@ namespace {
 
 constexpr int kThreads = 192;        // 6 warps
 constexpr int kBM = 128;             // rows per tile (TMEM lanes)
-constexpr int kRowBytes = 128;       // one swizzle row: 64 BF16 or 32 FP32 of the reduction
 constexpr uint32_t kTmemCols = 512;  // two accumulators of up to 256 FP32 columns
 constexpr uint32_t kAccStride = 256;
 // Winding down after an expired wait: copies and MMAs already issued are waited for
@@ -74,9 +73,12 @@ __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float(r);
 }
 
-template <int MODE, int EPI>
+// RB: bytes of reduction per shared-memory row and k-block (128 -> 128-byte swizzle,
+// 64 -> 64-byte swizzle with half-depth k-blocks and twice the pipeline stages).
+template <int MODE, int EPI, int RB>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ TcLaunch L, int stages, int bn_smem) {
+    constexpr int kRowBytes = RB;
     constexpr bool kSplit = (MODE == TC_BF16X3);
     constexpr int kElem = (MODE == TC_TF32) ? 4 : 2;
     constexpr int kElemsPerRow = kRowBytes / kElem;      // reduction elements per k-block
@@ -208,10 +210,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_after();
                     const int rem = P->Kred - (kb % dt.kb_per_batch) * kElemsPerRow;
                     const int steps = min(kStepsPerBlock, (rem + kUmmaK - 1) / kUmmaK);
-                    const uint64_t ah = smem_desc_sw128(smem_u32(stage_a(stage, 0)));
-                    const uint64_t bh = smem_desc_sw128(smem_u32(stage_b(stage, 0)));
-                    const uint64_t al = kSplit ? smem_desc_sw128(smem_u32(stage_a(stage, 1))) : 0;
-                    const uint64_t bl = kSplit ? smem_desc_sw128(smem_u32(stage_b(stage, 1))) : 0;
+                    const uint64_t ah = smem_desc_kmajor<RB>(smem_u32(stage_a(stage, 0)));
+                    const uint64_t bh = smem_desc_kmajor<RB>(smem_u32(stage_b(stage, 0)));
+                    const uint64_t al = kSplit ? smem_desc_kmajor<RB>(smem_u32(stage_a(stage, 1))) : 0;
+                    const uint64_t bl = kSplit ? smem_desc_kmajor<RB>(smem_u32(stage_b(stage, 1))) : 0;
                     for (int k = 0; k < steps; ++k) {
                         const uint64_t off = uint64_t(k) * 2;  // 32 bytes in 16-byte units
                         const uint32_t accum = (kb > dt.kb_begin || k > 0) ? 1u : 0u;
@@ -263,15 +265,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             const bool row_ok = row < P->M;
             const int n0 = dt.nt * P->tile_n;
             const int ncols = min(P->tile_n, P->N - n0);
-            int64_t rbase[2] = {0, 0};
-            for (int sci = 0; sci < P->nscatter; ++sci) {
-                const TcScatter& S = P->sc[sci];
+            const TcScatter& S = P->sc[0];
+            int64_t row_base = 0;
+            if (row_ok) {
                 const int g = row / S.rows_per_op;
                 const int rr = row - g * S.rows_per_op;
-                if (row_ok)
-                    rbase[sci] = S.out_off + (S.op_off ? S.op_off[g] : int64_t(g) * S.s_op) +
-                                 int64_t(rr) * S.s_row;
+                row_base = S.out_off + (S.op_off ? S.op_off[g] : int64_t(g) * S.s_op) +
+                           int64_t(rr) * S.s_row;
             }
+            const int cdiv = S.col_div;
+            const int64_t sch = S.s_col_hi, scl = S.s_col_lo;
             for (int c = 0; c < ncols; c += 32) {
                 uint32_t r[32];
                 tmem_ld_32x32b_x32(tmem_base + uint32_t(acc) * kAccStride +
@@ -280,14 +283,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tmem_ld_wait();
                 if (!row_ok) continue;
                 const int cmax = min(32, ncols - c);
-                for (int sci = 0; sci < P->nscatter; ++sci) {
-                    const TcScatter& S = P->sc[sci];
-                    const int64_t row_base = rbase[sci];
-                    const int cdiv = S.col_div;
-                    const int64_t sch = S.s_col_hi, scl = S.s_col_lo;
+                {
                     if (EPI == EPI_SPLIT_BF16) {
-                        __nv_bfloat16* hi = static_cast<__nv_bfloat16*>(L.out[sci][0]);
-                        __nv_bfloat16* lo = static_cast<__nv_bfloat16*>(L.out[sci][1]);
+                        __nv_bfloat16* hi = static_cast<__nv_bfloat16*>(L.out[0][0]);
+                        __nv_bfloat16* lo = static_cast<__nv_bfloat16*>(L.out[0][1]);
                         const bool vec4 = cdiv == 4 && scl == 1 && ((row_base & 3) == 0) &&
                                           ((sch & 3) == 0) && cmax == 32;
                         if (vec4) {
@@ -326,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                         }
                     } else {
-                        float* out = static_cast<float*>(L.out[sci][0]);
+                        float* out = static_cast<float*>(L.out[0][0]);
                         const bool contiguous = (cdiv == 1 && sch == 1);
                         if (EPI != EPI_F32_ATOMIC && contiguous && cmax == 32 &&
                             (((row_base + n0 + c) & 3) == 0)) {
@@ -526,24 +525,24 @@ bool pack_vec8_ok(const PackJob& j) {
 template <int MODE, int EPI>
 cudaError_t launch_one(const TcLaunch& L, int stages, int grid, int bn_smem, size_t smem,
                        cudaStream_t s) {
-    auto k = tc_gemm_kernel<MODE, EPI>;
+    auto k = L.row_bytes == 64 ? tc_gemm_kernel<MODE, EPI, 64> : tc_gemm_kernel<MODE, EPI, 128>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     k<<<grid, kThreads, smem, s>>>(L, stages, bn_smem);
     return cudaGetLastError();
 }
 
-size_t tc_smem_bytes(TcMode mode, int stages, int bn) {
-    const size_t a = size_t(kBM) * kRowBytes, b = size_t(bn) * kRowBytes;
+size_t tc_smem_bytes(TcMode mode, int stages, int bn, int rb) {
+    const size_t a = size_t(kBM) * rb, b = size_t(bn) * rb;
     const size_t stage = (a + b) * (mode == TC_BF16X3 ? 2 : 1);
     return 1024 + stage * stages + 8 * (2 * size_t(stages) + 5) + 16;
 }
 
 }  // namespace
 
-int tc_max_stages(TcMode mode, int tile_n_max) {
+int tc_max_stages(TcMode mode, int tile_n_max, int row_bytes) {
     int s = 1;
-    while (s < 8 && tc_smem_bytes(mode, s + 1, tile_n_max) <= 232448) ++s;
+    while (s < 8 && tc_smem_bytes(mode, s + 1, tile_n_max, row_bytes) <= 232448) ++s;
     return s;
 }
 
@@ -556,7 +555,7 @@ cudaError_t tc_gemm_launch(TcMode mode, TcEpi epi, const TcLaunch& L, int stages
     } else {
         return cudaErrorInvalidValue;  // device-table launches go through tc_gemm_launch_grouped
     }
-    const size_t smem = tc_smem_bytes(mode, stages, bn);
+    const size_t smem = tc_smem_bytes(mode, stages, bn, L.row_bytes);
     if (smem > 232448) return cudaErrorInvalidConfiguration;
     grid = std::max(1, std::min(grid, L.total_tiles));
 #define DMRG_TC_CASE(M, E) \
@@ -575,7 +574,7 @@ cudaError_t tc_gemm_launch(TcMode mode, TcEpi epi, const TcLaunch& L, int stages
 cudaError_t tc_gemm_launch_grouped(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
                                    int bn_smem, cudaStream_t s) {
     if (L.total_tiles <= 0) return cudaSuccess;
-    const size_t smem = tc_smem_bytes(mode, stages, bn_smem);
+    const size_t smem = tc_smem_bytes(mode, stages, bn_smem, L.row_bytes);
     if (smem > 232448) return cudaErrorInvalidConfiguration;
     grid = std::max(1, std::min(grid, L.total_tiles));
 #define DMRG_TC_CASE(M, E) \
@@ -650,7 +649,8 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 }
 
 bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t rows, int64_t cols,
-                        int64_t ld, int box_rows, int64_t nbatch, int64_t batch_stride) {
+                        int64_t ld, int box_rows, int64_t nbatch, int64_t batch_stride,
+                        int row_bytes) {
     if (g_encode == nullptr) {
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q;
@@ -666,11 +666,12 @@ bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t r
     cuuint64_t gdim[3] = {cuuint64_t(cols), cuuint64_t(rows), cuuint64_t(nbatch)};
     cuuint64_t gstride[2] = {cuuint64_t(ld) * esize, cuuint64_t(std::max<int64_t>(batch_stride, 1)) * esize};
     if (nbatch == 1) gstride[1] = (gstride[1] + 15) / 16 * 16;
-    cuuint32_t box[3] = {cuuint32_t(kRowBytes / esize), cuuint32_t(box_rows), 1};
+    cuuint32_t box[3] = {cuuint32_t(row_bytes / esize), cuuint32_t(box_rows), 1};
     cuuint32_t estride[3] = {1, 1, 1};
     CUresult r = g_encode(map, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                           3, const_cast<void*>(base), gdim, gstride, box, estride,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -685,17 +686,20 @@ int choose_tile_n(int64_t N, int tile_n_max) {
 }
 
 bool make_problem(TcProblem& p, TcMode mode, const TcOperand& A, const TcOperand& B,
-                  int tile_n_max, int k_splits) {
+                  int tile_n_max, int k_splits, int row_bytes) {
     const bool f32 = (mode == TC_TF32);
     const bool split = (mode == TC_BF16X3);
-    const int elems = f32 ? 32 : 64;
+    if (row_bytes != 64) row_bytes = 128;
+    const int elems = row_bytes / (f32 ? 4 : 2);
     if (A.cols != B.cols || A.nbatch != B.nbatch) return false;
     const int tile_n = choose_tile_n(B.rows, tile_n_max);
     for (int i = 0; i < (split ? 2 : 1); ++i) {
         const void* a = i ? A.lo : A.hi;
         const void* b = i ? B.lo : B.hi;
-        if (!encode_operand_map(&p.tmA[i], a, f32, A.rows, A.cols, A.ld, 128, A.nbatch, A.batch_stride) ||
-            !encode_operand_map(&p.tmB[i], b, f32, B.rows, B.cols, B.ld, tile_n, B.nbatch, B.batch_stride))
+        if (!encode_operand_map(&p.tmA[i], a, f32, A.rows, A.cols, A.ld, 128, A.nbatch, A.batch_stride,
+                                row_bytes) ||
+            !encode_operand_map(&p.tmB[i], b, f32, B.rows, B.cols, B.ld, tile_n, B.nbatch,
+                                B.batch_stride, row_bytes))
             return false;
     }
     if (!split) {
@@ -715,9 +719,7 @@ bool make_problem(TcProblem& p, TcMode mode, const TcOperand& A, const TcOperand
     p.kb_per_split = (kb_total + k_splits - 1) / k_splits;
     p.k_splits = (kb_total + p.kb_per_split - 1) / p.kb_per_split;
     p.tile_start = 0;
-    p.nscatter = 1;
     p.sc[0] = scatter_rowmajor(B.rows);
-    p.sc[1] = p.sc[0];
     return true;
 }
 

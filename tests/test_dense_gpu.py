@@ -171,3 +171,20 @@ def test_full_size_m400_sampled(lib):
     out = lib.dmrg_rotate_ops(U, O64, 4, "fp64")
     got = out[torch.from_numpy(sample).to(dev)].cpu().numpy()
     assert rel_err(got, oracle.rotate_dense(w.U, w.O[sample], 4)).max() <= TOL["fp64"]
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32", "fp64", "fp32"])
+@pytest.mark.parametrize("chunk", [0, 1, 7, 100])
+def test_host_buffer_pipeline(lib, prec, chunk):
+    # dmrg_rotate_ops_host: host buffers in and out, chunked copy/compute overlap;
+    # identical to the device-buffer entry point on the same inputs.
+    w = dense_workload("host", 31, 4, 72, 64, 19)
+    dt = torch.float64 if prec in ("fp64",) else torch.float32
+    Uh = torch.from_numpy(w.U).pin_memory()
+    Oh = torch.from_numpy(w.O).to(dt).pin_memory()
+    out = lib.dmrg_rotate_ops_host(Uh, Oh, 4, prec, chunk=chunk)
+    ref_dev = lib.dmrg_rotate_ops(Uh.cuda(), Oh.cuda(), 4, prec).cpu()
+    lib.dmrg_sync_status()
+    assert torch.equal(out, ref_dev)
+    ref = oracle.rotate_dense(w.U, Oh.double().numpy(), 4)
+    assert rel_err(out.double().numpy(), ref).max() <= TOL[prec]

@@ -132,3 +132,31 @@ def test_bounded_wait_expiry_is_reported(P):
         assert err.max() <= 1e-5
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("shape", [(37, 3, 50, 5), (400, 4, 400, 6), (130, 2, 200, 3)])
+@pytest.mark.parametrize("prec,pcode,tol", [("bf16x3", 3, 1e-5), ("tf32", 2, 3e-3)])
+@pytest.mark.parametrize("rb", [64, 128])
+def test_tilings_from_cache_file(P, tmp_path, shape, prec, pcode, tol, rb):
+    # Every tiling the autotuner may pick (N tile, stage count, 64- or 128-byte swizzle)
+    # gives the oracle's result; the cache file forces one.
+    m, d, mp, K = shape
+    path = tmp_path / "tune.json"
+    key = lambda g: "%s:K%d:m%d:d%d:mp%d:p%d" % (g, K, m, d, mp, pcode)
+    stages = 4 if rb == 64 else 2
+    path.write_text(json.dumps({key("g1"): [160, stages, 0, rb], key("g2"): [96, stages, 0, rb]}))
+    os.environ["DMRG_AUTOTUNE_CACHE"] = str(path)
+    try:
+        rng = np.random.default_rng(m + mp)
+        U = orthonormal_columns(rng, m * d, mp)
+        O = rng.standard_normal((K, m, m))
+        ref = oracle.rotate_dense(U, O, d)
+        h = P.Handle()
+        out = P.dmrg_rotate_ops(torch.from_numpy(U).cuda(), torch.from_numpy(O).cuda(), d, prec, handle=h)
+        P.dmrg_sync_status(handle=h)
+        got = out.double().cpu().numpy()
+        err = np.linalg.norm((got - ref).reshape(K, -1), axis=1) / np.linalg.norm(ref.reshape(K, -1), axis=1)
+        assert err.max() <= tol
+        h.close()
+    finally:
+        del os.environ["DMRG_AUTOTUNE_CACHE"]
