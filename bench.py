@@ -379,7 +379,7 @@ def main():
                 "peak_source": "%s bf16_tflops (burst)" % peak_src,
                 "flops_per_launch": issued[dom], "ms_per_launch": per_kernel[dom]}
     else:
-        byt = {"pack_O": K * M * M * (4 + 4)}
+        byt = {"pack_operands": K * M * M * (4 + 4)}
         achieved = byt.get(dom, 0) / (per_kernel[dom] * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic_for(dom), "kernel": dom}

@@ -96,6 +96,12 @@ DMRG_API dmrg_status dmrg_sync_status(dmrg_handle handle, dmrg_stream_t stream);
  *   DMRG_OPT_CHECK_ORTHO     : tolerance > 0 makes dmrg_rotate_ops verify
  *                              ||U^T U - I||_F <= tol first (synchronises the
  *                              stream); 0 = off (default).
+ *   DMRG_OPT_DETERMINISTIC   : 1 = bit-reproducible results.  By default the
+ *                              tiles left over after the last full wave of the
+ *                              second product are split along the reduction and
+ *                              accumulated with FP32 atomics, so the last few
+ *                              operators' rounding order may differ between runs
+ *                              (within the precision's tolerance).
  *   DMRG_OPT_TEST_WITHHOLD_ARRIVAL : test hook for failure detection.  1 makes
  *                              the next dense tensor-core launch withhold one
  *                              shared-memory stage release in its first CTA, so
@@ -108,7 +114,8 @@ typedef enum {
     DMRG_OPT_KERNEL_TIMING = 2,
     DMRG_OPT_WAIT_TIMEOUT_MS = 3,
     DMRG_OPT_CHECK_ORTHO = 4,
-    DMRG_OPT_TEST_WITHHOLD_ARRIVAL = 5
+    DMRG_OPT_TEST_WITHHOLD_ARRIVAL = 5,
+    DMRG_OPT_DETERMINISTIC = 6
 } dmrg_option;
 DMRG_API dmrg_status dmrg_set_option(dmrg_handle handle, dmrg_option option, double value);
 
@@ -142,10 +149,11 @@ DMRG_API dmrg_status dmrg_rotate_ops(dmrg_handle handle, const double* U, int64_
 
 /* The same rotation with U, O and Oout in HOST memory (page-locked for the copies
  * to overlap the computation; pageable memory works but serialises).  The batch is
- * processed in chunks of `chunk` consecutive operators (0 = about K/6): while chunk
- * c is rotated on `stream`, chunk c+1 is copied in and chunk c-1 copied out on two
- * streams owned by the handle, so host-to-device copies, kernels and
- * device-to-host copies overlap.  Operators are independent given U, which is what
+ * processed in chunks of `chunk` consecutive operators (0 = about K/5): while chunk
+ * c is rotated, chunk c+1 is copied in and chunk c-1 copied out on two streams
+ * owned by the handle, and rotations alternate between `stream` and a third
+ * handle stream, so host-to-device copies, kernels and device-to-host copies
+ * overlap.  Operators are independent given U, which is what
  * makes the split exact (the paper's UMD distribution rests on the same fact,
  * Sec. 3.2).  ws: device workspace of dmrg_rotate_ops_host_workspace() bytes.
  * Asynchronous on `stream`: Oout is complete once `stream` is. */

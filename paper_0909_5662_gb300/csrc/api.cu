@@ -206,9 +206,9 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     j2.rows = mp; j2.cols = D.md; j2.rows_per_op = mp;
     j2.rdiv = 1; j2.s_r_hi = 1; j2.s_r_lo = 0; j2.s_c = mp;
     j2.dst0 = B2[0]; j2.dst1 = B2[1]; j2.ld = D.ld2;
-    cudaError_t e = timed_launch(h, "pack_O", s, [&] { return pack_launch(jobs, 1, nullptr, s); });
-    if (e == cudaSuccess && pack_u)
-        e = timed_launch(h, "pack_U", s, [&] { return pack_launch(jobs + 1, 2, nullptr, s); });
+    // one launch: the two small U gathers run alongside the bandwidth-bound O stream
+    cudaError_t e = timed_launch(h, "pack_operands", s,
+                                 [&] { return pack_launch(jobs, pack_u ? 3 : 1, nullptr, s); });
     if (e != cudaSuccess) return cuda_fail(h, e, "pack");
 
     // ---- first product: T = O U_r, written straight into the second product's
@@ -263,10 +263,38 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     L2.nprob = 1;
     L2.total_tiles = P2.m_tiles * P2.n_tiles * P2.k_splits;
     L2.out[0][0] = Oout;
+    const int grid2 = c2.grid > 0 ? c2.grid : h->num_sms;
+    // Tail wave: the tiles left after the last full wave over the persistent CTAs are
+    // whole M tiles whose reduction is split so the last round is short.  Their parts
+    // accumulate with atomics into outputs cleared first.
+    {
+        const int tiles = P2.m_tiles * P2.n_tiles;
+        const int full_mt = (tiles / grid2) * grid2 / P2.n_tiles;
+        const int tail_mt = P2.m_tiles - full_mt;
+        const int64_t epr = c2.row_bytes / (split ? 2 : 4);   // reduction elements per k-block
+        const int kb = int((D.md + epr - 1) / epr);
+        const int parts = tail_mt > 0 ? std::min(kb, grid2 / (tail_mt * P2.n_tiles)) : 0;
+        if (!h->deterministic && full_mt > 0 && tail_mt > 0 && parts >= 2) {
+            TcProblem& T2 = L2.inline_prob[1];
+            T2 = P2;
+            P2.m_tiles = full_mt;
+            T2.m_tile0 = full_mt;
+            T2.m_tiles = tail_mt;
+            T2.kb_per_split = (kb + parts - 1) / parts;
+            T2.k_splits = (kb + T2.kb_per_split - 1) / T2.kb_per_split;
+            T2.atomic = 1;
+            T2.tile_start = P2.m_tiles * P2.n_tiles;
+            L2.nprob = 2;
+            L2.total_tiles = T2.tile_start + T2.m_tiles * T2.n_tiles * T2.k_splits;
+            const int64_t k_first = int64_t(full_mt) * 128 / mp;
+            e = cudaMemsetAsync(static_cast<float*>(Oout) + k_first * mp * mp, 0,
+                                size_t(K - k_first) * mp * mp * sizeof(float), s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "clear tail outputs");
+        }
+    }
     L2.status = h->d_status;
     L2.timeout_ns = timeout_ns(h);
     L2.row_bytes = c2.row_bytes;
-    const int grid2 = c2.grid > 0 ? c2.grid : h->num_sms;
     e = timed_launch(h, "tc_gemm_second_product", s, [&] {
         return tc_gemm_launch(mode, EPI_F32, L2, c2.stages, grid2, s);
     });
@@ -397,6 +425,7 @@ dmrg_status dmrg_destroy(dmrg_handle h) {
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     if (h->copy_in) cudaStreamDestroy(h->copy_in);
     if (h->copy_out) cudaStreamDestroy(h->copy_out);
+    if (h->compute2) cudaStreamDestroy(h->compute2);
     for (cudaEvent_t ev : {h->ev_start, h->ev_u, h->ev_in[0], h->ev_in[1], h->ev_comp[0],
                            h->ev_comp[1], h->ev_out[0], h->ev_out[1]})
         if (ev) cudaEventDestroy(ev);
@@ -417,6 +446,9 @@ dmrg_status dmrg_set_option(dmrg_handle h, dmrg_option o, double v) {
         case DMRG_OPT_CHECK_ORTHO:
             if (v < 0) return fail(h, DMRG_ERR_INVALID_ARG, "tolerance must be >= 0");
             h->check_ortho_tol = v;
+            return DMRG_OK;
+        case DMRG_OPT_DETERMINISTIC:
+            h->deterministic = v != 0;
             return DMRG_OK;
         case DMRG_OPT_TEST_WITHHOLD_ARRIVAL:
             h->drop_arrival_next = v != 0;

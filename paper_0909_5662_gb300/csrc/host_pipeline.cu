@@ -2,10 +2,12 @@
 //
 // The operator batch is split into chunks of consecutive operators (operators are
 // independent given U, the property the paper's UMD split relies on, Sec. 3.2).
-// Three streams overlap the work: chunk c+1 is copied in on the copy-in stream
-// while chunk c is rotated on the caller's stream and chunk c-1 is copied out on
-// the copy-out stream.  Device staging is double buffered; events order every
-// reuse of a buffer.  U is copied and packed once per call.
+// Four streams overlap the work: chunk c+1 is copied in on the copy-in stream
+// while chunk c is rotated and chunk c-1 is copied out on the copy-out stream.
+// Rotations alternate between the caller's stream and a second compute stream
+// (each with its own workspace), so the last, partly filled wave of one chunk's
+// kernels overlaps the next chunk's.  Device staging is double buffered; events
+// order every reuse of a buffer.  U is copied once and packed once per workspace.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,7 +27,7 @@ struct HostDims {
 HostDims host_dims(int64_t K, int64_t m, int d, int64_t mp, dmrg_precision p, int in_is_fp64,
                    int64_t chunk) {
     HostDims H;
-    if (chunk <= 0) chunk = std::max<int64_t>(1, (K + 5) / 6);
+    if (chunk <= 0) chunk = std::max<int64_t>(1, (K + 4) / 5);
     H.chunk = std::min<int64_t>(chunk, std::max<int64_t>(K, 1));
     H.nchunks = K > 0 ? (K + H.chunk - 1) / H.chunk : 0;
     H.es_in = in_is_fp64 ? 8 : 4;
@@ -35,7 +37,8 @@ HostDims host_dims(int64_t K, int64_t m, int d, int64_t mp, dmrg_precision p, in
     H.ws.add("O1", size_t(H.chunk) * m * m * H.es_in);
     H.ws.add("R0", size_t(H.chunk) * mp * mp * H.es_out);
     H.ws.add("R1", size_t(H.chunk) * mp * mp * H.es_out);
-    H.ws.add("rot", dense_dims(H.chunk, m, d, mp, p).ws.total);
+    H.ws.add("rot0", dense_dims(H.chunk, m, d, mp, p).ws.total);
+    H.ws.add("rot1", dense_dims(H.chunk, m, d, mp, p).ws.total);
     return H;
 }
 
@@ -43,6 +46,7 @@ cudaError_t ensure_pipeline(dmrg_handle h) {
     cudaError_t e = cudaSuccess;
     if (!h->copy_in) e = cudaStreamCreateWithFlags(&h->copy_in, cudaStreamNonBlocking);
     if (e == cudaSuccess && !h->copy_out) e = cudaStreamCreateWithFlags(&h->copy_out, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !h->compute2) e = cudaStreamCreateWithFlags(&h->compute2, cudaStreamNonBlocking);
     cudaEvent_t* evs[8] = {&h->ev_start, &h->ev_u, &h->ev_in[0], &h->ev_in[1],
                            &h->ev_comp[0], &h->ev_comp[1], &h->ev_out[0], &h->ev_out[1]};
     for (cudaEvent_t* ev : evs)
@@ -86,7 +90,8 @@ dmrg_status dmrg_rotate_ops_host(dmrg_handle h, const double* U, int64_t m, int 
     double* Ud = reinterpret_cast<double*>(base + H.ws.offsets[0]);
     void* Od[2] = {base + H.ws.offsets[1], base + H.ws.offsets[2]};
     void* Rd[2] = {base + H.ws.offsets[3], base + H.ws.offsets[4]};
-    void* rot = base + H.ws.offsets[5];
+    void* rot[2] = {base + H.ws.offsets[5], base + H.ws.offsets[6]};
+    cudaStream_t cs[2] = {s, h->compute2};
     const size_t op_in = size_t(m) * m * H.es_in, op_out = size_t(mp) * mp * H.es_out;
     const TcMode mode = (p == DMRG_PREC_BF16X3) ? TC_BF16X3 : TC_TF32;
     const TcConfig c1 = tuned_config(h, shape_key("g1", H.chunk, m, d, mp, p), mode);
@@ -95,11 +100,13 @@ dmrg_status dmrg_rotate_ops_host(dmrg_handle h, const double* U, int64_t m, int 
     // everything the caller queued before this call happens first
     if ((e = cudaEventRecord(h->ev_start, s)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(h->copy_in, h->ev_start, 0)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(h->copy_out, h->ev_start, 0)) != cudaSuccess)
+        (e = cudaStreamWaitEvent(h->copy_out, h->ev_start, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(h->compute2, h->ev_start, 0)) != cudaSuccess)
         return cuda_fail(h, e, "ordering");
     e = cudaMemcpyAsync(Ud, U, size_t(m) * d * mp * 8, cudaMemcpyHostToDevice, h->copy_in);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_u, h->copy_in);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_u, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->compute2, h->ev_u, 0);
     if (e != cudaSuccess) return cuda_fail(h, e, "copy U");
     for (int64_t c = 0; c < H.nchunks; ++c) {
         const int b = int(c & 1);
@@ -111,15 +118,17 @@ dmrg_status dmrg_rotate_ops_host(dmrg_handle h, const double* U, int64_t m, int 
                             cudaMemcpyHostToDevice, h->copy_in);
         if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[b], h->copy_in);
         if (e != cudaSuccess) return cuda_fail(h, e, "copy in");
-        // rotate: inputs landed, and the output buffer was copied out (chunk c-2)
-        if ((e = cudaStreamWaitEvent(s, h->ev_in[b], 0)) != cudaSuccess) return cuda_fail(h, e, "ordering");
-        if (c >= 2 && (e = cudaStreamWaitEvent(s, h->ev_out[b], 0)) != cudaSuccess)
+        // rotate on compute stream b: inputs landed, and the output buffer was copied out
+        // (chunk c-2, which ran on the same stream)
+        cudaStream_t x = cs[b];
+        if ((e = cudaStreamWaitEvent(x, h->ev_in[b], 0)) != cudaSuccess) return cuda_fail(h, e, "ordering");
+        if (c >= 2 && (e = cudaStreamWaitEvent(x, h->ev_out[b], 0)) != cudaSuccess)
             return cuda_fail(h, e, "ordering");
-        st = tc ? dense_tc_forward(h, Ud, m, d, mp, Od[b], in_is_fp64, kc, Rd[b], p, rot, c1, c2, s,
-                                   c == 0)
-                : dense_simt_forward(h, Ud, m, d, mp, Od[b], in_is_fp64, kc, Rd[b], p, rot, s, c == 0);
+        st = tc ? dense_tc_forward(h, Ud, m, d, mp, Od[b], in_is_fp64, kc, Rd[b], p, rot[b], c1, c2, x,
+                                   c < 2)
+                : dense_simt_forward(h, Ud, m, d, mp, Od[b], in_is_fp64, kc, Rd[b], p, rot[b], x, c < 2);
         if (st != DMRG_OK) return st;
-        if ((e = cudaEventRecord(h->ev_comp[b], s)) != cudaSuccess) return cuda_fail(h, e, "ordering");
+        if ((e = cudaEventRecord(h->ev_comp[b], x)) != cudaSuccess) return cuda_fail(h, e, "ordering");
         // copy out
         if ((e = cudaStreamWaitEvent(h->copy_out, h->ev_comp[b], 0)) != cudaSuccess)
             return cuda_fail(h, e, "ordering");

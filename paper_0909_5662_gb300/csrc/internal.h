@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/dmrg_rotate.h"
+#include "dmrg_rotate.h"
 
 namespace dmrg {
 
@@ -78,7 +78,8 @@ struct TcProblem {  // 64-byte aligned through its CUtensorMap members
     int32_t tile_n;      // N tile width (multiple of 16, <= 256)
     int32_t m_tiles, n_tiles, k_splits, kb_per_split;
     int32_t tile_start;  // first global tile of this problem
-    int32_t pad0, pad1;
+    int32_t m_tile0;     // first M tile (the problem covers M tiles m_tile0 .. m_tile0 + m_tiles - 1)
+    int32_t atomic;      // FP32 epilogues: accumulate with atomics (split-K parts of a tile)
     TcScatter sc[1];
 };
 
@@ -160,6 +161,7 @@ struct PackJob {
     // srcs[src_sel] of the launch and dst0 / dst1 hold byte offsets from its
     // workspace base (rel = 1); rel = 0 means absolute pointers.
     int32_t rel, src_sel;
+    int32_t vec8, pad;     // set by the launcher: contiguous rows, 8 elements per thread
 };
 cudaError_t pack_launch(const PackJob* jobs_host, int njobs, PackJob* jobs_dev_or_null,
                         cudaStream_t s);
@@ -186,6 +188,7 @@ struct dmrg_handle_s {
     double wait_timeout_ms = 2000.0;
     double check_ortho_tol = 0.0;
     int drop_arrival_next = 0;      // test hook, consumed by the next tensor-core launch
+    bool deterministic = false;     // no atomically accumulated split tiles
 
     struct Timed {
         std::string name;
@@ -203,7 +206,7 @@ struct dmrg_handle_s {
     bool capturing = false;
 
     // host-buffer pipeline: copy-in and copy-out streams and their events
-    cudaStream_t copy_in = nullptr, copy_out = nullptr;
+    cudaStream_t copy_in = nullptr, copy_out = nullptr, compute2 = nullptr;
     cudaEvent_t ev_start = nullptr, ev_u = nullptr;
     cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
                 ev_out[2] = {nullptr, nullptr};

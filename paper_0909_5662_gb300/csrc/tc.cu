@@ -6,9 +6,10 @@
 //              ring of shared-memory stages (cp.async.bulk.tensor, mbarrier tx count);
 //   warp 1   : MMA issuer    -- one thread issues tcgen05.mma (M = 128, N <= 256)
 //              into one of two TMEM accumulators, tcgen05.commit frees the stage;
-//   warps 2-5: epilogue      -- tcgen05.ld of the finished accumulator, conversion
+//   warps 2-9: epilogue      -- tcgen05.ld of the finished accumulator, conversion
 //              (FP32 / TF32 / BF16 hi-lo split) and a strided scatter to global memory,
-//              overlapping the next tile's main loop.
+//              overlapping the next tile's main loop (two warps per TMEM lane quadrant,
+//              alternate 32-column chunks).
 // Precision forms: BF16x3 (A = Ah + Al, B = Bh + Bl, D += Al Bh + Ah Bl + Ah Bh with
 // FP32 accumulation), TF32 (kind::tf32) and plain BF16 (one product, for comparison).
 #include <cuda.h>
@@ -26,7 +27,8 @@
 namespace dmrg {
 namespace {
 
-constexpr int kThreads = 192;        // 6 warps
+constexpr int kThreads = 320;        // 10 warps: producer, MMA issuer, 8 epilogue warps
+constexpr int kEpiWarps = 8;         // two per TMEM lane quadrant, alternate 32-column chunks
 constexpr int kBM = 128;             // rows per tile (TMEM lanes)
 constexpr uint32_t kTmemCols = 512;  // two accumulators of up to 256 FP32 columns
 constexpr uint32_t kAccStride = 256;
@@ -60,6 +62,7 @@ __device__ __forceinline__ Decoded decode_tile(const TcLaunch& L, int t, int ele
     const int rem = local - ks * per_split;
     d.mt = rem / P->n_tiles;
     d.nt = rem - d.mt * P->n_tiles;
+    d.mt += P->m_tile0;
     d.kb_per_batch = (P->Kred + elems_per_row - 1) / elems_per_row;
     const int kb_total = d.kb_per_batch * P->nbatch;
     d.kb_begin = ks * P->kb_per_split;
@@ -99,6 +102,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* drain = tempty + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+    int* zero_flag = abort_flag + 1;  // never raised: drain waits ignore the abort flag
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -110,10 +114,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
-            mbar_init(&tempty[a], 4);
+            mbar_init(&tempty[a], kEpiWarps);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
+        *zero_flag = 0;
         fence_mbar_init();
     }
     if (warp == 1) tmem_alloc<kTmemCols>(tmem_slot);
@@ -178,11 +183,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             // Never leave the CTA with bulk copies still landing in shared memory.
             for (int s = 0; s < stages; ++s)
-                if (armed & (1u << s)) {
-                    volatile int never = 0;
+                if (armed & (1u << s))
                     mbar_wait(&full[s], (armed_parity >> s) & 1u, kDrainTimeoutNs, L.status,
-                              reinterpret_cast<volatile int*>(&never));
-                }
+                              zero_flag);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
@@ -242,12 +245,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             // Every issued MMA has finished before TMEM is released.
             mma_commit(drain);
-            volatile int never = 0;
-            mbar_wait(drain, 0, kDrainTimeoutNs, L.status, reinterpret_cast<volatile int*>(&never));
+            mbar_wait(drain, 0, kDrainTimeoutNs, L.status, zero_flag);
         }
     } else {
-        // ------------------------------------------------------------ epilogue (warps 2..5)
-        const int quad = warp & 3;  // TMEM lanes [32*quad, 32*quad + 32)
+        // ------------------------------------------------------------ epilogue (warps 2..9)
+        const int quad = warp & 3;            // TMEM lanes [32*quad, 32*quad + 32)
+        const int half = (warp - 2) >> 2;     // 0: even 32-column chunks, 1: odd ones
         int it = 0;
         for (int t = blockIdx.x; t < L.total_tiles; t += gridDim.x, ++it) {
             const Decoded dt = decode_tile(L, t, kElemsPerRow);
@@ -262,7 +265,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!ok) break;
             tc_fence_after();
             const int row = dt.mt * kBM + quad * 32 + lane;
-            const bool row_ok = row < P->M;
+            // a tile whose reduction range is empty has an uninitialised accumulator
+            const bool row_ok = row < P->M && dt.kb_begin < dt.kb_end;
             const int n0 = dt.nt * P->tile_n;
             const int ncols = min(P->tile_n, P->N - n0);
             const TcScatter& S = P->sc[0];
@@ -275,7 +279,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const int cdiv = S.col_div;
             const int64_t sch = S.s_col_hi, scl = S.s_col_lo;
-            for (int c = 0; c < ncols; c += 32) {
+            const bool tile_atomic = P->atomic != 0;
+            for (int c = half * 32; c < ncols; c += 64) {
                 uint32_t r[32];
                 tmem_ld_32x32b_x32(tmem_base + uint32_t(acc) * kAccStride +
                                        (uint32_t(quad * 32) << 16) + uint32_t(c),
@@ -290,45 +295,69 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const bool vec4 = cdiv == 4 && scl == 1 && ((row_base & 3) == 0) &&
                                           ((sch & 3) == 0) && cmax == 32;
                         if (vec4) {
+                            // four consecutive columns (b, s = 0..3) -> four consecutive
+                            // elements; pairs are split with packed bf16x2 conversions
+                            const int64_t base = row_base + int64_t((n0 + c) >> 2) * sch;
+                            uint2* ph = reinterpret_cast<uint2*>(hi + base);
+                            uint2* pl = reinterpret_cast<uint2*>(lo + base);
+                            const int64_t step = sch >> 2;  // in uint2 units
 #pragma unroll
                             for (int j = 0; j < 32; j += 4) {
-                                const int n = n0 + c + j;
-                                const int64_t idx = row_base + int64_t(n >> 2) * sch;
-                                __nv_bfloat16 h[4], l[4];
+                                uint32_t hw[2], lw[2];
 #pragma unroll
-                                for (int e = 0; e < 4; ++e) {
-                                    const float v = __uint_as_float(r[j + e]);
-                                    h[e] = __float2bfloat16_rn(v);
-                                    l[e] = __float2bfloat16_rn(v - __bfloat162float(h[e]));
+                                for (int q = 0; q < 2; ++q) {
+                                    const float2 v = make_float2(__uint_as_float(r[j + 2 * q]),
+                                                                 __uint_as_float(r[j + 2 * q + 1]));
+                                    const __nv_bfloat162 h2 = __float22bfloat162_rn(v);
+                                    const float2 hf = __bfloat1622float2(h2);
+                                    const __nv_bfloat162 l2 =
+                                        __float22bfloat162_rn(make_float2(v.x - hf.x, v.y - hf.y));
+                                    hw[q] = *reinterpret_cast<const uint32_t*>(&h2);
+                                    lw[q] = *reinterpret_cast<const uint32_t*>(&l2);
                                 }
-                                uint2 hv, lv;
-                                hv.x = uint32_t(__bfloat16_as_ushort(h[0])) |
-                                       (uint32_t(__bfloat16_as_ushort(h[1])) << 16);
-                                hv.y = uint32_t(__bfloat16_as_ushort(h[2])) |
-                                       (uint32_t(__bfloat16_as_ushort(h[3])) << 16);
-                                lv.x = uint32_t(__bfloat16_as_ushort(l[0])) |
-                                       (uint32_t(__bfloat16_as_ushort(l[1])) << 16);
-                                lv.y = uint32_t(__bfloat16_as_ushort(l[2])) |
-                                       (uint32_t(__bfloat16_as_ushort(l[3])) << 16);
-                                *reinterpret_cast<uint2*>(hi + idx) = hv;
-                                *reinterpret_cast<uint2*>(lo + idx) = lv;
+                                ph[(j >> 2) * step] = make_uint2(hw[0], hw[1]);
+                                pl[(j >> 2) * step] = make_uint2(lw[0], lw[1]);
                             }
                         } else {
-                            for (int j = 0; j < cmax; ++j) {
-                                const int n = n0 + c + j;
-                                const int64_t idx = row_base + int64_t(n / cdiv) * sch +
-                                                    int64_t(n % cdiv) * scl;
-                                const float v = __uint_as_float(r[j]);
-                                const __nv_bfloat16 h = __float2bfloat16_rn(v);
-                                hi[idx] = h;
-                                lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+                            // r[] is indexed with constants only (full unroll), so it stays
+                            // in registers
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                if (j < cmax) {
+                                    const int n = n0 + c + j;
+                                    const int64_t idx = row_base + int64_t(n / cdiv) * sch +
+                                                        int64_t(n % cdiv) * scl;
+                                    const float v = __uint_as_float(r[j]);
+                                    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                                    hi[idx] = h;
+                                    lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+                                }
                             }
                         }
                     } else {
                         float* out = static_cast<float*>(L.out[0][0]);
-                        const bool contiguous = (cdiv == 1 && sch == 1);
-                        if (EPI != EPI_F32_ATOMIC && contiguous && cmax == 32 &&
-                            (((row_base + n0 + c) & 3) == 0)) {
+                        const bool atom = (EPI == EPI_F32_ATOMIC) || tile_atomic;
+                        if (!atom && cdiv == 4 && scl == 1 && cmax == 32 && ((row_base & 3) == 0) &&
+                            ((sch & 3) == 0)) {
+                            // groups of four columns (b, s = 0..3) land on four consecutive words
+                            float4* p4 = reinterpret_cast<float4*>(out + row_base +
+                                                                   int64_t((n0 + c) >> 2) * sch);
+                            const int64_t step = sch >> 2;  // in float4 units
+#pragma unroll
+                            for (int j = 0; j < 32; j += 4) {
+                                float4 v;
+                                v.x = __uint_as_float(r[j]);
+                                v.y = __uint_as_float(r[j + 1]);
+                                v.z = __uint_as_float(r[j + 2]);
+                                v.w = __uint_as_float(r[j + 3]);
+                                if (EPI == EPI_TF32) {
+                                    v.x = tf32_round(v.x); v.y = tf32_round(v.y);
+                                    v.z = tf32_round(v.z); v.w = tf32_round(v.w);
+                                }
+                                p4[(j >> 2) * step] = v;
+                            }
+                        } else if (!atom && cdiv == 1 && sch == 1 && cmax == 32 &&
+                                   (((row_base + n0 + c) & 3) == 0)) {
                             float4* o4 = reinterpret_cast<float4*>(out + row_base + n0 + c);
 #pragma unroll
                             for (int j = 0; j < 32; j += 4) {
@@ -343,16 +372,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 }
                                 o4[j >> 2] = v;
                             }
+                        } else if (cdiv == 1) {
+                            // one stride per column (the transposed store of the second product):
+                            // lanes hold consecutive rows, so each store instruction is coalesced
+                            float* p = out + row_base + int64_t(n0 + c) * sch;
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                if (j < cmax) {
+                                    const float v = __uint_as_float(r[j]);
+                                    if (atom) atomicAdd(p + j * sch, v);
+                                    else p[j * sch] = (EPI == EPI_TF32) ? tf32_round(v) : v;
+                                }
+                            }
                         } else {
-#pragma unroll 4
-                            for (int j = 0; j < cmax; ++j) {
-                                const int n = n0 + c + j;
-                                const int64_t idx =
-                                    row_base + int64_t(n / cdiv) * sch + int64_t(n % cdiv) * scl;
-                                const float v = __uint_as_float(r[j]);
-                                if (EPI == EPI_F32) out[idx] = v;
-                                else if (EPI == EPI_TF32) out[idx] = tf32_round(v);
-                                else atomicAdd(out + idx, v);
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                if (j < cmax) {
+                                    const int n = n0 + c + j;
+                                    const int64_t idx = row_base + int64_t(n / cdiv) * sch +
+                                                        int64_t(n % cdiv) * scl;
+                                    const float v = __uint_as_float(r[j]);
+                                    if (atom) atomicAdd(out + idx, v);
+                                    else if (EPI == EPI_TF32) out[idx] = tf32_round(v);
+                                    else out[idx] = v;
+                                }
                             }
                         }
                     }
@@ -512,6 +555,92 @@ __global__ void __launch_bounds__(kPackThreads) pack_rows_vec8_kernel(const __gr
     }
 }
 
+// One 8-element unit v of a contiguous job (see pack_rows_vec8_kernel).
+template <typename S>
+__device__ __forceinline__ void pack_vec8_unit(const PackJob& j, int64_t v) {
+    const int64_t per_row = j.cols >> 3;
+    const int64_t r = v / per_row;
+    const int64_t c = (v - r * per_row) << 3;
+    const S* sp = static_cast<const S*>(j.src) + j.src_off + r * j.s_r_hi + c;
+    S x[8];
+    if (sizeof(S) == 4) {
+        const float4 a = reinterpret_cast<const float4*>(sp)[0];
+        const float4 b = reinterpret_cast<const float4*>(sp)[1];
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+        x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double2 a = reinterpret_cast<const double2*>(sp)[q];
+            x[2 * q] = S(a.x);
+            x[2 * q + 1] = S(a.y);
+        }
+    }
+    const int64_t dst = r * j.ld + c;
+    if (j.mode == 0) {
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t hh[2], ll[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                __nv_bfloat16 h, l;
+                split_bf16(x[2 * q + e], h, l);
+                hh[e] = __bfloat16_as_ushort(h);
+                ll[e] = __bfloat16_as_ushort(l);
+            }
+            hw[q] = hh[0] | (hh[1] << 16);
+            lw[q] = ll[0] | (ll[1] << 16);
+        }
+        *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(j.dst0) + dst) =
+            make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(j.dst1) + dst) =
+            make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    } else {
+        float y[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) y[e] = (j.mode == 1) ? tf32_round(float(x[e])) : float(x[e]);
+        float4* d4 = reinterpret_cast<float4*>(static_cast<float*>(j.dst0) + dst);
+        d4[0] = make_float4(y[0], y[1], y[2], y[3]);
+        d4[1] = make_float4(y[4], y[5], y[6], y[7]);
+    }
+}
+
+// Several jobs in one launch: block ranges per job; contiguous jobs take the 8-wide
+// path, the others the general gather.  Small gathers placed first run alongside
+// the bandwidth-bound contiguous job instead of after it.
+__global__ void __launch_bounds__(kPackThreads) pack_mixed_kernel(const __grid_constant__ PackLaunch L) {
+    const int b = blockIdx.x;
+    int k = 0;
+    for (int i = 1; i < L.njobs; ++i)
+        if (L.inline_jobs[i].block_start <= b) k = i;
+    const PackJob& j = L.inline_jobs[k];
+    if (j.vec8) {
+        const int64_t v = int64_t(b - j.block_start) * kPackThreads + threadIdx.x;
+        if (v >= j.rows * (j.cols >> 3)) return;
+        if (j.src_f64) pack_vec8_unit<double>(j, v);
+        else pack_vec8_unit<float>(j, v);
+        return;
+    }
+    const int64_t total = j.rows * j.cols;
+    const int64_t e0 = (int64_t(b - j.block_start) * kPackThreads + threadIdx.x) * kPackElems;
+#pragma unroll
+    for (int q = 0; q < kPackElems; ++q) {
+        const int64_t e = e0 + q;
+        if (e >= total) break;
+        const int64_t r = e / j.cols;
+        const int64_t c = e - r * j.cols;
+        const int64_t g = r / j.rows_per_op;
+        const int64_t rr = r - g * j.rows_per_op;
+        const int64_t src = j.src_off + (j.op_off ? j.op_off[g] : g * j.s_op) +
+                            (rr / j.rdiv) * j.s_r_hi + (rr % j.rdiv) * j.s_r_lo + c * j.s_c;
+        if (j.src_f64)
+            pack_store(j, r * j.ld + c, static_cast<const double*>(j.src)[src]);
+        else
+            pack_store(j, r * j.ld + c, static_cast<const float*>(j.src)[src]);
+    }
+}
+
 bool pack_vec8_ok(const PackJob& j) {
     const size_t es = j.src_f64 ? 8 : 4;
     const bool single_group = (j.rows_per_op >= j.rows) && j.op_off == nullptr;
@@ -535,7 +664,7 @@ cudaError_t launch_one(const TcLaunch& L, int stages, int grid, int bn_smem, siz
 size_t tc_smem_bytes(TcMode mode, int stages, int bn, int rb) {
     const size_t a = size_t(kBM) * rb, b = size_t(bn) * rb;
     const size_t stage = (a + b) * (mode == TC_BF16X3 ? 2 : 1);
-    return 1024 + stage * stages + 8 * (2 * size_t(stages) + 5) + 16;
+    return 1024 + stage * stages + 8 * (2 * size_t(stages) + 5) + 32;
 }
 
 }  // namespace
@@ -600,30 +729,23 @@ cudaError_t pack_launch(const PackJob* jobs, int njobs, PackJob* /*unused*/, cud
     PackLaunch L{};
     int64_t blocks = 0;
     int n = 0;
-    for (int i = 0; i < njobs; ++i) {
-        if (jobs[i].rows * jobs[i].cols == 0) continue;
-        if (pack_vec8_ok(jobs[i])) {
-            const int64_t vecs = jobs[i].rows * (jobs[i].cols / 8);
-            const int64_t nb = std::min<int64_t>((vecs + kPackThreads - 1) / kPackThreads, 152 * 16);
-            if (jobs[i].src_f64)
-                pack_rows_vec8_kernel<double><<<unsigned(nb), kPackThreads, 0, s>>>(jobs[i]);
-            else
-                pack_rows_vec8_kernel<float><<<unsigned(nb), kPackThreads, 0, s>>>(jobs[i]);
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) return e;
-            continue;
+    // general gathers first, contiguous jobs after them
+    for (int pass = 0; pass < 2; ++pass)
+        for (int i = 0; i < njobs; ++i) {
+            if (jobs[i].rows * jobs[i].cols == 0) continue;
+            const bool v8 = pack_vec8_ok(jobs[i]);
+            if (v8 != (pass == 1)) continue;
+            PackJob& j = L.inline_jobs[n++];
+            j = jobs[i];
+            j.vec8 = v8 ? 1 : 0;
+            j.block_start = blocks;
+            blocks += v8 ? (j.rows * (j.cols / 8) + kPackThreads - 1) / kPackThreads : pack_blocks_for(j);
         }
-        L.inline_jobs[n] = jobs[i];
-        L.inline_jobs[n].block_start = blocks;
-        blocks += pack_blocks_for(jobs[i]);
-        ++n;
-    }
-    if (n == 0) return cudaSuccess;
+    if (n == 0 || blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     L.table = nullptr;
     L.njobs = n;
-    if (blocks <= 0) return cudaSuccess;
-    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    pack_kernel<<<unsigned(blocks), kPackThreads, 0, s>>>(L);
+    pack_mixed_kernel<<<unsigned(blocks), kPackThreads, 0, s>>>(L);
     return cudaGetLastError();
 }
 
@@ -719,6 +841,8 @@ bool make_problem(TcProblem& p, TcMode mode, const TcOperand& A, const TcOperand
     p.kb_per_split = (kb_total + k_splits - 1) / k_splits;
     p.k_splits = (kb_total + p.kb_per_split - 1) / p.kb_per_split;
     p.tile_start = 0;
+    p.m_tile0 = 0;
+    p.atomic = 0;
     p.sc[0] = scatter_rowmajor(B.rows);
     return true;
 }

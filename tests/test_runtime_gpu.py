@@ -60,7 +60,7 @@ def test_kernel_timing_report(P):
             P.dmrg_rotate_ops(U, O, 4, "bf16x3", handle=h)
         rep = P.dmrg_kernel_timing(reset=True, handle=h)
         names = {r["kernel"]: r for r in rep}
-        for k in ("pack_O", "pack_U", "tc_gemm_first_product", "tc_gemm_second_product"):
+        for k in ("pack_operands", "tc_gemm_first_product", "tc_gemm_second_product"):
             assert names[k]["launches"] == 2 and names[k]["total_ms"] > 0
         assert P.dmrg_kernel_timing(reset=True, handle=h) == []
     finally:
@@ -160,3 +160,32 @@ def test_tilings_from_cache_file(P, tmp_path, shape, prec, pcode, tol, rb):
         h.close()
     finally:
         del os.environ["DMRG_AUTOTUNE_CACHE"]
+
+
+def test_deterministic_option_and_tail_split(P):
+    # m = 400, K = 150: the second product's last wave is split along the reduction
+    # (atomic accumulation) unless DMRG_OPT_DETERMINISTIC is set; both stay within the
+    # BF16x3 tolerance and the deterministic mode is bit-reproducible.
+    from workloads import dense_config
+    w = dense_config("dense_m400_k150")
+    dev = torch.device("cuda")
+    U = torch.from_numpy(w.U).to(dev)
+    O = torch.from_numpy(w.O).to(dev, torch.float32)
+    tail = [140, 145, 146, 147, 148, 149]
+    ref = oracle.rotate_dense(w.U, w.O[tail].astype(np.float32).astype(np.float64), 4)
+    h = P.Handle()
+    try:
+        a = P.dmrg_rotate_ops(U, O, 4, "bf16x3", handle=h)
+        P.dmrg_set_option("deterministic", 1, handle=h)
+        b = P.dmrg_rotate_ops(U, O, 4, "bf16x3", handle=h).clone()
+        c = P.dmrg_rotate_ops(U, O, 4, "bf16x3", handle=h)
+        P.dmrg_sync_status(handle=h)
+        assert torch.equal(b, c)
+        for out in (a, b):
+            got = out[tail].double().cpu().numpy()
+            err = np.linalg.norm((got - ref).reshape(len(tail), -1), axis=1) / \
+                np.linalg.norm(ref.reshape(len(tail), -1), axis=1)
+            assert err.max() <= 1e-5
+        assert torch.equal(a[:140], b[:140])   # tiles outside the last wave are untouched
+    finally:
+        h.close()
