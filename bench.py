@@ -33,7 +33,8 @@ UNIT = "rotated operators/s"
 WORKLOAD = "dense_m400_k150"
 D, M, MP, K_PER_GPU = 4, 400, 400, 150
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
-KERNEL_SOURCES = ["paper_0909_5662_gb300/csrc/tc.cu", "paper_0909_5662_gb300/csrc/ptx.cuh",
+KERNEL_SOURCES = ["paper_0909_5662_gb300/csrc/tc.cu", "paper_0909_5662_gb300/csrc/tc_pair.cu",
+                  "paper_0909_5662_gb300/csrc/tc_common.cuh", "paper_0909_5662_gb300/csrc/ptx.cuh",
                   "paper_0909_5662_gb300/csrc/internal.h"]
 
 

@@ -152,11 +152,18 @@ dmrg_status check_dense_args(dmrg_handle h, int64_t K, int64_t m, int d, int64_t
 TcConfig tuned_config(dmrg_handle h, const std::string& key, TcMode mode) {
     load_tune_file(h);
     auto it = h->tune_cache.find(key);
-    if (it != h->tune_cache.end()) return it->second;
+    if (it != h->tune_cache.end()) {
+        TcConfig c = it->second;  // a cached depth that no longer fits is reduced
+        c.stages = std::min(c.stages, tc_stages_for(mode, c));
+        return c;
+    }
+    // Untuned default: 128-byte rows, N tiles up to 256, the deepest pipeline that
+    // fits; the two dense products run on CTA pairs (half of B staged per SM).
     TcConfig c;
     c.tile_n_max = 256;
     c.row_bytes = 128;
-    c.stages = tc_max_stages(mode, 256, c.row_bytes);
+    c.pair = (key.compare(0, 3, "g1:") == 0 || key.compare(0, 3, "g2:") == 0) ? 1 : 0;
+    c.stages = tc_stages_for(mode, c);
     c.grid = 0;
     return c;
 }
@@ -218,7 +225,7 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     {
         TcOperand A{Op[0], Op[1], K * m, m, D.ld1};
         TcOperand B{B1[0], B1[1], int64_t(d) * mp, m, D.ld1};
-        if (!make_problem(P1, mode, A, B, c1.tile_n_max, 1, c1.row_bytes))
+        if (!make_problem(P1, mode, A, B, c1.tile_n_max, 1, c1.row_bytes, c1.pair != 0))
             return fail(h, DMRG_ERR_CUDA, "cuTensorMapEncodeTiled failed (first product)");
     }
     TcScatter& S1 = P1.sc[0];
@@ -239,7 +246,9 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     L1.row_bytes = c1.row_bytes;
     const int grid1 = c1.grid > 0 ? c1.grid : h->num_sms;
     e = timed_launch(h, "tc_gemm_first_product", s, [&] {
-        return tc_gemm_launch(mode, split ? EPI_SPLIT_BF16 : EPI_TF32, L1, c1.stages, grid1, s);
+        const TcEpi epi = split ? EPI_SPLIT_BF16 : EPI_TF32;
+        return c1.pair ? tc_gemm_launch_pair(mode, epi, L1, c1.stages, grid1, s)
+                       : tc_gemm_launch(mode, epi, L1, c1.stages, grid1, s);
     });
     if (e != cudaSuccess) return cuda_fail(h, e, "first product");
 
@@ -249,7 +258,7 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     {
         TcOperand A{Tt[0], Tt[1], K * mp, D.md, D.ld2};
         TcOperand B{B2[0], B2[1], mp, D.md, D.ld2};
-        if (!make_problem(P2, mode, A, B, c2.tile_n_max, 1, c2.row_bytes))
+        if (!make_problem(P2, mode, A, B, c2.tile_n_max, 1, c2.row_bytes, c2.pair != 0))
             return fail(h, DMRG_ERR_CUDA, "cuTensorMapEncodeTiled failed (second product)");
     }
     TcScatter& S2 = P2.sc[0];
@@ -264,16 +273,18 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     L2.total_tiles = P2.m_tiles * P2.n_tiles * P2.k_splits;
     L2.out[0][0] = Oout;
     const int grid2 = c2.grid > 0 ? c2.grid : h->num_sms;
-    // Tail wave: the tiles left after the last full wave over the persistent CTAs are
-    // whole M tiles whose reduction is split so the last round is short.  Their parts
-    // accumulate with atomics into outputs cleared first.
+    // Tail wave: the tiles left after the last full wave over the persistent CTAs (or
+    // CTA pairs) are whole M tiles whose reduction is split so the last round is short.
+    // Their parts accumulate with atomics into outputs cleared first.
     {
+        const int slots = c2.pair ? grid2 / 2 : grid2;
+        const int bm = c2.pair ? 256 : 128;
         const int tiles = P2.m_tiles * P2.n_tiles;
-        const int full_mt = (tiles / grid2) * grid2 / P2.n_tiles;
+        const int full_mt = (tiles / slots) * slots / P2.n_tiles;
         const int tail_mt = P2.m_tiles - full_mt;
         const int64_t epr = c2.row_bytes / (split ? 2 : 4);   // reduction elements per k-block
         const int kb = int((D.md + epr - 1) / epr);
-        const int parts = tail_mt > 0 ? std::min(kb, grid2 / (tail_mt * P2.n_tiles)) : 0;
+        const int parts = tail_mt > 0 ? std::min(kb, slots / (tail_mt * P2.n_tiles)) : 0;
         if (!h->deterministic && full_mt > 0 && tail_mt > 0 && parts >= 2) {
             TcProblem& T2 = L2.inline_prob[1];
             T2 = P2;
@@ -286,7 +297,7 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
             T2.tile_start = P2.m_tiles * P2.n_tiles;
             L2.nprob = 2;
             L2.total_tiles = T2.tile_start + T2.m_tiles * T2.n_tiles * T2.k_splits;
-            const int64_t k_first = int64_t(full_mt) * 128 / mp;
+            const int64_t k_first = int64_t(full_mt) * bm / mp;
             e = cudaMemsetAsync(static_cast<float*>(Oout) + k_first * mp * mp, 0,
                                 size_t(K - k_first) * mp * mp * sizeof(float), s);
             if (e != cudaSuccess) return cuda_fail(h, e, "clear tail outputs");
@@ -296,7 +307,8 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     L2.timeout_ns = timeout_ns(h);
     L2.row_bytes = c2.row_bytes;
     e = timed_launch(h, "tc_gemm_second_product", s, [&] {
-        return tc_gemm_launch(mode, EPI_F32, L2, c2.stages, grid2, s);
+        return c2.pair ? tc_gemm_launch_pair(mode, EPI_F32, L2, c2.stages, grid2, s)
+                       : tc_gemm_launch(mode, EPI_F32, L2, c2.stages, grid2, s);
     });
     if (e != cudaSuccess) return cuda_fail(h, e, "second product");
     return DMRG_OK;

@@ -3,8 +3,8 @@
 // For each of the two products it times every candidate (N tile, pipeline depth)
 // with CUDA events on the caller's buffers, keeps the fastest per shape key in the
 // handle and, when $DMRG_AUTOTUNE_CACHE names a file, persists the choices there as
-// a small JSON object {"key": [tile_n_max, stages, grid], ...} so that later
-// processes start tuned.
+// a small JSON object {"key": [tile_n_max, stages, grid, row_bytes, pair], ...} so
+// that later processes start tuned (pair = 1: the CTA-pair kernel).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,11 +40,12 @@ void load_tune_file(dmrg_handle h) {
         const size_t lb = text.find('[', end), rb = text.find(']', end);
         if (lb == std::string::npos || rb == std::string::npos || rb < lb) break;
         TcConfig c;
-        const int n = sscanf(text.c_str() + lb + 1, "%d , %d , %d , %d", &c.tile_n_max, &c.stages,
-                             &c.grid, &c.row_bytes);
+        const int n = sscanf(text.c_str() + lb + 1, "%d , %d , %d , %d , %d", &c.tile_n_max,
+                             &c.stages, &c.grid, &c.row_bytes, &c.pair);
         if (n == 3) c.row_bytes = 128;
+        if (n <= 4) c.pair = 0;
         if (n >= 3 && c.tile_n_max >= 16 && c.tile_n_max <= 256 && c.stages >= 1 && c.stages <= 8 &&
-            c.grid >= 0 && (c.row_bytes == 64 || c.row_bytes == 128))
+            c.grid >= 0 && (c.row_bytes == 64 || c.row_bytes == 128) && (c.pair == 0 || c.pair == 1))
             h->tune_cache[key] = c;
         pos = rb + 1;
     }
@@ -59,7 +60,7 @@ void save_tune_file(dmrg_handle h) {
     size_t i = 0;
     for (auto& kv : h->tune_cache) {
         f << "  \"" << kv.first << "\": [" << kv.second.tile_n_max << ", " << kv.second.stages << ", "
-          << kv.second.grid << ", " << kv.second.row_bytes << "]"
+          << kv.second.grid << ", " << kv.second.row_bytes << ", " << kv.second.pair << "]"
           << (++i < h->tune_cache.size() ? ",\n" : "\n");
     }
     f << "}\n";
@@ -76,15 +77,18 @@ std::vector<TcConfig> candidates(TcMode mode, int64_t N, int num_sms) {
         const int t = choose_tile_n(N, tn);
         if (std::find(seen.begin(), seen.end(), t) != seen.end()) continue;
         seen.push_back(t);
-        for (int rb : {128, 64}) {
-            const int smax = tc_max_stages(mode, t, rb);
-            for (int st = smax; st >= std::max(2, smax - 1); --st) {
+        for (int pair : {0, 1}) {
+            for (int rb : {128, 64}) {
                 TcConfig c;
                 c.tile_n_max = t;
-                c.stages = st;
                 c.grid = num_sms;
                 c.row_bytes = rb;
-                out.push_back(c);
+                c.pair = pair;
+                const int smax = tc_stages_for(mode, c);
+                for (int st = smax; st >= std::max(2, smax - 1); --st) {
+                    c.stages = st;
+                    out.push_back(c);
+                }
             }
         }
     }

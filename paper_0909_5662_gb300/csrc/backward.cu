@@ -210,7 +210,9 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
         e = timed_launch(h, "bwd_pack_O", s, [&] { return pack_launch(jobs, 2, nullptr, s); });
         if (e != cudaSuccess) return cuda_fail(h, e, "pack O");
     }
-    const TcConfig cfg = tuned_config(h, shape_key("bwd", K, m, d, mp, p), mode);
+    TcConfig cfg = tuned_config(h, shape_key("bwd", K, m, d, mp, p), mode);
+    cfg.pair = 0;  // the adjoint's grouped products run on the one-CTA kernel
+    cfg.stages = std::min(cfg.stages, tc_max_stages(mode, cfg.tile_n_max, cfg.row_bytes));
     const int grid = cfg.grid > 0 ? cfg.grid : h->num_sms;
     auto launch = [&](const char* name, TcLaunch& L, TcEpi epi) -> dmrg_status {
         L.table = nullptr;

@@ -91,9 +91,10 @@ struct TcConfig {
     int stages = 3;
     int grid = 0;           // 0 = number of SMs
     int row_bytes = 128;    // 128: 128-byte swizzle; 64: 64-byte swizzle, half-depth k-blocks
+    int pair = 0;           // 1: CTA-pair kernel (256-row tiles on two SMs, cta_group::2)
     bool operator==(const TcConfig& o) const {
         return tile_n_max == o.tile_n_max && stages == o.stages && grid == o.grid &&
-               row_bytes == o.row_bytes;
+               row_bytes == o.row_bytes && pair == o.pair;
     }
 };
 
@@ -124,6 +125,16 @@ struct TcOperand {
 cudaError_t tc_gemm_launch(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
                            cudaStream_t s);
 int tc_max_stages(TcMode mode, int tile_n_max, int row_bytes = 128);
+// CTA-pair form: problems made with make_problem(..., pair = true); `grid` counts CTAs
+// (rounded down to even, capped by the clusters that fit at once).
+cudaError_t tc_gemm_launch_pair(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
+                                cudaStream_t s);
+int tc_pair_max_stages(TcMode mode, int tile_n_max, int row_bytes = 128);
+// Dispatch on cfg.pair.
+inline int tc_stages_for(TcMode mode, const TcConfig& c) {
+    return c.pair ? tc_pair_max_stages(mode, c.tile_n_max, c.row_bytes)
+                  : tc_max_stages(mode, c.tile_n_max, c.row_bytes);
+}
 
 // Encodes a K-major operand map (3-D: cols, rows, batch), box = box_rows x 128 bytes.
 bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t rows, int64_t cols,
@@ -133,7 +144,7 @@ bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t r
 int choose_tile_n(int64_t N, int tile_n_max);
 // Fills operand maps and tiling fields of a problem: D (M x N) += A B^T over Kred x nbatch.
 bool make_problem(TcProblem& p, TcMode mode, const TcOperand& A, const TcOperand& B,
-                  int tile_n_max, int k_splits, int row_bytes = 128);
+                  int tile_n_max, int k_splits, int row_bytes = 128, bool pair = false);
 // Scatter for a plain row-major (rows x cols, leading dimension ld) destination.
 TcScatter scatter_rowmajor(int64_t ld);
 

@@ -93,7 +93,8 @@ extern "C" DMRG_API dmrg_status dmrg_rotate_ops_noalloc(const double* U, int64_t
     dmrg::TcConfig cfg;
     cfg.tile_n_max = 256;
     cfg.row_bytes = 128;
-    cfg.stages = dmrg::tc_max_stages(mode, 256, cfg.row_bytes);
+    cfg.pair = 1;
+    cfg.stages = dmrg::tc_stages_for(mode, cfg);
     return dmrg::dense_tc_forward(h, U, m, d, mp, O, in_is_fp64, K, Oout, precision, c->ws, cfg,
                                   cfg, s);
 }

@@ -1,0 +1,175 @@
+// tc_common.cuh -- device helpers shared by the tcgen05 GEMM kernels (one-CTA and
+// CTA-pair forms): tile decoding of the persistent schedule, TF32 rounding and the
+// epilogue's scatter of one 32-column accumulator chunk.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+
+namespace dmrg {
+namespace tcdev {
+
+struct Decoded {
+    const TcProblem* P;
+    int mt, nt, kb_begin, kb_end, kb_per_batch;
+};
+
+__device__ __forceinline__ Decoded decode_tile(const TcLaunch& L, int t, int elems_per_row) {
+    const TcProblem* P = &L.inline_prob[0];
+    if (L.table != nullptr) {
+        int lo = 0, hi = L.nprob - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (L.table[mid].tile_start <= t) lo = mid; else hi = mid - 1;
+        }
+        P = &L.table[lo];
+    } else {
+        for (int i = 1; i < L.nprob; ++i)
+            if (L.inline_prob[i].tile_start <= t) P = &L.inline_prob[i];
+    }
+    Decoded d;
+    d.P = P;
+    const int local = t - P->tile_start;
+    const int per_split = P->m_tiles * P->n_tiles;
+    const int ks = local / per_split;
+    const int rem = local - ks * per_split;
+    d.mt = rem / P->n_tiles;
+    d.nt = rem - d.mt * P->n_tiles;
+    d.mt += P->m_tile0;
+    d.kb_per_batch = (P->Kred + elems_per_row - 1) / elems_per_row;
+    const int kb_total = d.kb_per_batch * P->nbatch;
+    d.kb_begin = ks * P->kb_per_split;
+    d.kb_end = min(kb_total, d.kb_begin + P->kb_per_split);
+    return d;
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Stores one 32-column chunk of a finished accumulator row through scatter map S
+// (row_base already includes the row part of the map).  r[] is indexed with
+// constants only, so it stays in registers.
+template <int EPI>
+__device__ __forceinline__ void store_chunk(const TcLaunch& L, const uint32_t (&r)[32],
+                                        int64_t row_base, int n0, int c, int cmax, int cdiv,
+                                        int64_t sch, int64_t scl, bool tile_atomic) {
+    if (EPI == EPI_SPLIT_BF16) {
+        __nv_bfloat16* hi = static_cast<__nv_bfloat16*>(L.out[0][0]);
+        __nv_bfloat16* lo = static_cast<__nv_bfloat16*>(L.out[0][1]);
+        const bool vec4 = cdiv == 4 && scl == 1 && ((row_base & 3) == 0) &&
+                          ((sch & 3) == 0) && cmax == 32;
+        if (vec4) {
+            // four consecutive columns (b, s = 0..3) -> four consecutive
+            // elements; pairs are split with packed bf16x2 conversions
+            const int64_t base = row_base + int64_t((n0 + c) >> 2) * sch;
+            uint2* ph = reinterpret_cast<uint2*>(hi + base);
+            uint2* pl = reinterpret_cast<uint2*>(lo + base);
+            const int64_t step = sch >> 2;  // in uint2 units
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+                uint32_t hw[2], lw[2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const float2 v = make_float2(__uint_as_float(r[j + 2 * q]),
+                                                 __uint_as_float(r[j + 2 * q + 1]));
+                    const __nv_bfloat162 h2 = __float22bfloat162_rn(v);
+                    const float2 hf = __bfloat1622float2(h2);
+                    const __nv_bfloat162 l2 =
+                        __float22bfloat162_rn(make_float2(v.x - hf.x, v.y - hf.y));
+                    hw[q] = *reinterpret_cast<const uint32_t*>(&h2);
+                    lw[q] = *reinterpret_cast<const uint32_t*>(&l2);
+                }
+                ph[(j >> 2) * step] = make_uint2(hw[0], hw[1]);
+                pl[(j >> 2) * step] = make_uint2(lw[0], lw[1]);
+            }
+        } else {
+            // r[] is indexed with constants only (full unroll), so it stays
+            // in registers
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j < cmax) {
+                    const int n = n0 + c + j;
+                    const int64_t idx = row_base + int64_t(n / cdiv) * sch +
+                                        int64_t(n % cdiv) * scl;
+                    const float v = __uint_as_float(r[j]);
+                    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                    hi[idx] = h;
+                    lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+                }
+            }
+        }
+    } else {
+        float* out = static_cast<float*>(L.out[0][0]);
+        const bool atom = (EPI == EPI_F32_ATOMIC) || tile_atomic;
+        if (!atom && cdiv == 4 && scl == 1 && cmax == 32 && ((row_base & 3) == 0) &&
+            ((sch & 3) == 0)) {
+            // groups of four columns (b, s = 0..3) land on four consecutive words
+            float4* p4 = reinterpret_cast<float4*>(out + row_base +
+                                                   int64_t((n0 + c) >> 2) * sch);
+            const int64_t step = sch >> 2;  // in float4 units
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+                float4 v;
+                v.x = __uint_as_float(r[j]);
+                v.y = __uint_as_float(r[j + 1]);
+                v.z = __uint_as_float(r[j + 2]);
+                v.w = __uint_as_float(r[j + 3]);
+                if (EPI == EPI_TF32) {
+                    v.x = tf32_round(v.x); v.y = tf32_round(v.y);
+                    v.z = tf32_round(v.z); v.w = tf32_round(v.w);
+                }
+                p4[(j >> 2) * step] = v;
+            }
+        } else if (!atom && cdiv == 1 && sch == 1 && cmax == 32 &&
+                   (((row_base + n0 + c) & 3) == 0)) {
+            float4* o4 = reinterpret_cast<float4*>(out + row_base + n0 + c);
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+                float4 v;
+                v.x = __uint_as_float(r[j]);
+                v.y = __uint_as_float(r[j + 1]);
+                v.z = __uint_as_float(r[j + 2]);
+                v.w = __uint_as_float(r[j + 3]);
+                if (EPI == EPI_TF32) {
+                    v.x = tf32_round(v.x); v.y = tf32_round(v.y);
+                    v.z = tf32_round(v.z); v.w = tf32_round(v.w);
+                }
+                o4[j >> 2] = v;
+            }
+        } else if (cdiv == 1) {
+            // one stride per column (the transposed store of the second product):
+            // lanes hold consecutive rows, so each store instruction is coalesced
+            float* p = out + row_base + int64_t(n0 + c) * sch;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j < cmax) {
+                    const float v = __uint_as_float(r[j]);
+                    if (atom) atomicAdd(p + j * sch, v);
+                    else p[j * sch] = (EPI == EPI_TF32) ? tf32_round(v) : v;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (j < cmax) {
+                    const int n = n0 + c + j;
+                    const int64_t idx = row_base + int64_t(n / cdiv) * sch +
+                                        int64_t(n % cdiv) * scl;
+                    const float v = __uint_as_float(r[j]);
+                    if (atom) atomicAdd(out + idx, v);
+                    else if (EPI == EPI_TF32) out[idx] = tf32_round(v);
+                    else out[idx] = v;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace tcdev
+}  // namespace dmrg

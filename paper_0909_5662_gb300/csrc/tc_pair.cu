@@ -1,0 +1,383 @@
+// tc_pair.cu -- tcgen05 GEMM on CTA pairs (cta_group::2), sm_103a.
+//
+// The same persistent pipeline as tc.cu, but two CTAs of a cluster compute one
+// 256 x N tile together: each CTA stages its 128 rows of A and half of the N rows
+// of B in its own shared memory, and one thread of the even ("leader") CTA issues
+// tcgen05.mma.cta_group::2, which reads both CTAs' operands and accumulates each
+// CTA's 128 rows in that CTA's TMEM.  Per SM this halves the shared-memory and L2
+// traffic of the B operand, which bounds the one-CTA kernel.
+//
+// Protocol (every wait bounded, as in the one-CTA kernel):
+//   * both CTAs' TMA loads of a stage complete on the leader's full[s] barrier
+//     (the leader arms it with the bytes of both CTAs);
+//   * the leader's commits multicast to empty[s] and to the accumulator-full
+//     barrier of both CTAs, so each CTA refills and drains its own buffers;
+//   * the epilogue warps of both CTAs arrive on the leader's accumulator-empty
+//     barrier (the peer through its shared::cluster address);
+//   * cluster barriers after set-up and before teardown keep either CTA from
+//     leaving while the other may still reach its barriers or TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "internal.h"
+#include "ptx.cuh"
+#include "tc_common.cuh"
+
+namespace dmrg {
+namespace {
+
+using namespace tcdev;
+
+constexpr int kThreads = 320;         // producer, MMA issuer, 8 epilogue warps (per CTA)
+constexpr int kEpiWarps = 8;
+constexpr int kBM = 128;              // rows per CTA (TMEM lanes)
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kAccStride = 256;
+constexpr uint64_t kDrainTimeoutNs = 2000000000ull;
+
+// MMA width of an N tile with `left` columns remaining: a multiple of 16 (each CTA
+// then holds whole 8-row swizzle atoms of B), at least 32.
+__device__ __forceinline__ int pair_n(int tile_n, int left) {
+    const int n = min(tile_n, left);
+    return max(32, (n + 15) & ~15);
+}
+
+template <int MODE, int EPI, int RB>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_pair_kernel(const __grid_constant__ TcLaunch L, int stages, int bh_smem) {
+    constexpr int kRowBytes = RB;
+    constexpr bool kSplit = (MODE == TC_BF16X3);
+    constexpr int kElem = (MODE == TC_TF32) ? 4 : 2;
+    constexpr int kElemsPerRow = kRowBytes / kElem;
+    constexpr int kUmmaK = 32 / kElem;
+    constexpr int kStepsPerBlock = kElemsPerRow / kUmmaK;
+    constexpr uint32_t kFmt = (MODE == TC_TF32) ? 2u : 1u;
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t a_bytes = kBM * kRowBytes;
+    const uint32_t b_bytes = uint32_t(bh_smem) * kRowBytes;  // half of the N tile
+    const uint32_t stage_bytes = (a_bytes + b_bytes) * (kSplit ? 2 : 1);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + size_t(stages) * stage_bytes);
+    uint64_t* empty = full + stages;
+    uint64_t* tfull = empty + stages;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* drain = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+    int* zero_flag = abort_flag + 1;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    const bool leader = (rank == 0);
+    const int pair = blockIdx.x >> 1;
+    const int npairs = gridDim.x >> 1;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 2 * kEpiWarps);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        *zero_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) tmem_alloc_pair<kTmemCols>(tmem_slot);
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    volatile int* vabort = abort_flag;
+    const uint64_t tmo = L.timeout_ns;
+
+    auto stage_a = [&](int s, int half) -> uint8_t* {
+        return smem + size_t(s) * stage_bytes + size_t(half) * (a_bytes + b_bytes);
+    };
+    auto stage_b = [&](int s, int half) -> uint8_t* { return stage_a(s, half) + a_bytes; };
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer (both CTAs)
+        if (lane == 0) {
+            if (L.table == nullptr) {
+                for (int i = 0; i < L.nprob; ++i) {
+                    tma_prefetch_desc(&L.inline_prob[i].tmA[0]);
+                    tma_prefetch_desc(&L.inline_prob[i].tmB[0]);
+                    if (kSplit) {
+                        tma_prefetch_desc(&L.inline_prob[i].tmA[1]);
+                        tma_prefetch_desc(&L.inline_prob[i].tmB[1]);
+                    }
+                }
+            }
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t armed = 0;
+            uint32_t armed_parity = 0;
+            bool ok = true;
+            for (int t = pair; t < L.total_tiles && ok; t += npairs) {
+                const Decoded dt = decode_tile(L, t, kElemsPerRow);
+                const TcProblem* P = dt.P;
+                // both CTAs' bytes: A (128 rows each) and the B halves (tile_n / 2 rows each)
+                const uint32_t bytes =
+                    2u * (a_bytes + uint32_t(P->tile_n / 2) * kRowBytes) * (kSplit ? 2u : 1u);
+                const int n_eff = pair_n(P->tile_n, P->N - dt.nt * P->tile_n);
+                const int ya = dt.mt * (2 * kBM) + int(rank) * kBM;
+                const int yb = dt.nt * P->tile_n + int(rank) * (n_eff / 2);
+                for (int kb = dt.kb_begin; kb < dt.kb_end; ++kb) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, tmo, L.status, vabort)) {
+                        ok = false;
+                        break;
+                    }
+                    if (leader) mbar_arrive_expect_tx(&full[stage], bytes);
+                    const uint32_t fb = mapa_shared(smem_u32(&full[stage]), 0);
+                    const int z = kb / dt.kb_per_batch;
+                    const int x = (kb - z * dt.kb_per_batch) * kElemsPerRow;
+                    tma_load_3d_pair(stage_a(stage, 0), &P->tmA[0], fb, x, ya, z);
+                    tma_load_3d_pair(stage_b(stage, 0), &P->tmB[0], fb, x, yb, z);
+                    if (kSplit) {
+                        tma_load_3d_pair(stage_a(stage, 1), &P->tmA[1], fb, x, ya, z);
+                        tma_load_3d_pair(stage_b(stage, 1), &P->tmB[1], fb, x, yb, z);
+                    }
+                    armed |= 1u << stage;
+                    armed_parity = (armed_parity & ~(1u << stage)) | (phase << stage);
+                    if (++stage == stages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            // Tail.  The leader's full barriers count both CTAs' copies: once the last
+            // armed phase of each stage completed, no copy of either CTA is in flight.
+            // Each CTA then waits for the release of its last fill of every stage, so
+            // that no commit of the leader still has an arrival on its way to this CTA
+            // when it leaves.  After an abort the release waits give up at once.
+            if (leader)
+                for (int s = 0; s < stages; ++s)
+                    if (armed & (1u << s))
+                        mbar_wait(&full[s], (armed_parity >> s) & 1u, kDrainTimeoutNs, L.status,
+                                  zero_flag);
+            if (ok)
+                for (int s = 0; s < stages; ++s)
+                    if (armed & (1u << s))
+                        mbar_wait(&empty[s], (armed_parity >> s) & 1u, tmo, L.status, vabort);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer (leader)
+        if (lane == 0 && leader) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int it = 0;
+            bool ok = true;
+            for (int t = pair; t < L.total_tiles && ok; t += npairs, ++it) {
+                const Decoded dt = decode_tile(L, t, kElemsPerRow);
+                const TcProblem* P = dt.P;
+                const int acc = it & 1;
+                const uint32_t acc_parity = uint32_t(it >> 1) & 1u;
+                if (!mbar_wait(&tempty[acc], acc_parity ^ 1u, tmo, L.status, vabort)) break;
+                tc_fence_after();
+                const uint32_t tmem_d = tmem_base + uint32_t(acc) * kAccStride;
+                const int n_eff = pair_n(P->tile_n, P->N - dt.nt * P->tile_n);
+                const uint32_t idesc = make_idesc_pair(kFmt, uint32_t(n_eff));
+                for (int kb = dt.kb_begin; kb < dt.kb_end; ++kb) {
+                    if (!mbar_wait(&full[stage], phase, tmo, L.status, vabort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const int rem = P->Kred - (kb % dt.kb_per_batch) * kElemsPerRow;
+                    const int steps = min(kStepsPerBlock, (rem + kUmmaK - 1) / kUmmaK);
+                    const uint64_t ah = smem_desc_kmajor<RB>(smem_u32(stage_a(stage, 0)));
+                    const uint64_t bh = smem_desc_kmajor<RB>(smem_u32(stage_b(stage, 0)));
+                    const uint64_t al = kSplit ? smem_desc_kmajor<RB>(smem_u32(stage_a(stage, 1))) : 0;
+                    const uint64_t bl = kSplit ? smem_desc_kmajor<RB>(smem_u32(stage_b(stage, 1))) : 0;
+                    for (int k = 0; k < steps; ++k) {
+                        const uint64_t off = uint64_t(k) * 2;
+                        const uint32_t accum = (kb > dt.kb_begin || k > 0) ? 1u : 0u;
+                        if (MODE == TC_BF16X3) {
+                            mma_bf16_pair(tmem_d, al + off, bh + off, idesc, accum);
+                            mma_bf16_pair(tmem_d, ah + off, bl + off, idesc, 1u);
+                            mma_bf16_pair(tmem_d, ah + off, bh + off, idesc, 1u);
+                        } else if (MODE == TC_TF32) {
+                            mma_tf32_pair(tmem_d, ah + off, bh + off, idesc, accum);
+                        } else {
+                            mma_bf16_pair(tmem_d, ah + off, bh + off, idesc, accum);
+                        }
+                    }
+                    // Test hook: withhold one release so that both producers' bounded
+                    // waits on this stage expire (a barrier that nothing arrives on).
+                    const bool withhold = L.drop_arrival && pair == 0 && it == 0 &&
+                                          kb == dt.kb_begin;
+                    if (!withhold) mma_commit_pair(&empty[stage], 3);
+                    if (++stage == stages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit_pair(&tfull[acc], 3);
+            }
+            mma_commit_pair(drain, 1);
+            mbar_wait(drain, 0, kDrainTimeoutNs, L.status, zero_flag);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue (both CTAs)
+        const int quad = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const uint32_t tempty_leader0 = mapa_shared(smem_u32(&tempty[0]), 0);
+        const uint32_t tempty_leader1 = mapa_shared(smem_u32(&tempty[1]), 0);
+        int it = 0;
+        for (int t = pair; t < L.total_tiles; t += npairs, ++it) {
+            const Decoded dt = decode_tile(L, t, kElemsPerRow);
+            const TcProblem* P = dt.P;
+            const int acc = it & 1;
+            const uint32_t acc_parity = uint32_t(it >> 1) & 1u;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(&tfull[acc], acc_parity, tmo, L.status, vabort) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            tc_fence_after();
+            const int row = dt.mt * (2 * kBM) + int(rank) * kBM + quad * 32 + lane;
+            const bool row_ok = row < P->M && dt.kb_begin < dt.kb_end;
+            const int n0 = dt.nt * P->tile_n;
+            const int ncols = min(P->tile_n, P->N - n0);
+            const TcScatter& S = P->sc[0];
+            int64_t row_base = 0;
+            if (row_ok) {
+                const int g = row / S.rows_per_op;
+                const int rr = row - g * S.rows_per_op;
+                row_base = S.out_off + (S.op_off ? S.op_off[g] : int64_t(g) * S.s_op) +
+                           int64_t(rr) * S.s_row;
+            }
+            const int cdiv = S.col_div;
+            const int64_t sch = S.s_col_hi, scl = S.s_col_lo;
+            const bool tile_atomic = P->atomic != 0;
+            for (int c = half * 32; c < ncols; c += 64) {
+                uint32_t r[32];
+                tmem_ld_32x32b_x32(tmem_base + uint32_t(acc) * kAccStride +
+                                       (uint32_t(quad * 32) << 16) + uint32_t(c),
+                                   r);
+                tmem_ld_wait();
+                if (!row_ok) continue;
+                const int cmax = min(32, ncols - c);
+                store_chunk<EPI>(L, r, row_base, n0, c, cmax, cdiv, sch, scl, tile_atomic);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                if (leader) mbar_arrive(&tempty[acc]);
+                else mbar_arrive_cluster(acc ? tempty_leader1 : tempty_leader0);
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();
+    if (*vabort) {
+        // After an expired wait copies issued before it may still be landing here.
+        const uint64_t t0 = globaltimer_ns();
+        while (globaltimer_ns() - t0 < 1000000ull) __nanosleep(1000);
+    }
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair<kTmemCols>(tmem_base);
+    }
+}
+
+// Pairs of this kernel that are resident at once (0 if unknown), cached per
+// device, kernel and shared-memory size.
+int clusters_that_fit(const void* kernel, const cudaLaunchConfig_t& cfg) {
+    struct Entry {
+        int dev;
+        const void* k;
+        size_t smem;
+        int fit;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Entry& e : cache)
+        if (e.dev == dev && e.k == kernel && e.smem == cfg.dynamicSmemBytes) return e.fit;
+    int fit = 0;
+    if (cudaOccupancyMaxActiveClusters(&fit, kernel, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        fit = 0;
+    }
+    cache.push_back({dev, kernel, cfg.dynamicSmemBytes, fit});
+    return fit;
+}
+
+template <int MODE, int EPI>
+cudaError_t launch_pair(const TcLaunch& L, int stages, int grid, int bh_smem, size_t smem,
+                        cudaStream_t s) {
+    auto k = L.row_bytes == 64 ? tc_gemm_pair_kernel<MODE, EPI, 64> : tc_gemm_pair_kernel<MODE, EPI, 128>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid), 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // A persistent grid larger than the pairs that fit at once would only queue.
+    const int fit = clusters_that_fit(reinterpret_cast<const void*>(k), cfg);
+    if (fit > 0 && 2 * fit < grid) cfg.gridDim.x = unsigned(2 * fit);
+    return cudaLaunchKernelEx(&cfg, k, L, stages, bh_smem);
+}
+
+size_t pair_smem_bytes(TcMode mode, int stages, int bh, int rb) {
+    const size_t a = size_t(kBM) * rb, b = size_t(bh) * rb;
+    const size_t stage = (a + b) * (mode == TC_BF16X3 ? 2 : 1);
+    return 1024 + stage * stages + 8 * (2 * size_t(stages) + 5) + 32;
+}
+
+}  // namespace
+
+int tc_pair_max_stages(TcMode mode, int tile_n_max, int row_bytes) {
+    int s = 1;
+    while (s < 8 && pair_smem_bytes(mode, s + 1, tile_n_max / 2, row_bytes) <= 232448) ++s;
+    return s;
+}
+
+cudaError_t tc_gemm_launch_pair(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
+                                cudaStream_t s) {
+    if (L.total_tiles <= 0) return cudaSuccess;
+    if (L.table != nullptr || L.nprob < 1 || L.nprob > kMaxInlineProblems) return cudaErrorInvalidValue;
+    int bn = 32;
+    for (int i = 0; i < L.nprob; ++i) bn = std::max(bn, L.inline_prob[i].tile_n);
+    const int bh = bn / 2;
+    const size_t smem = pair_smem_bytes(mode, stages, bh, L.row_bytes);
+    if (smem > 232448) return cudaErrorInvalidConfiguration;
+    grid = std::max(2, std::min(grid, 2 * L.total_tiles)) & ~1;
+#define DMRG_TC_CASE(M, E) \
+    if (mode == M && epi == E) return launch_pair<M, E>(L, stages, grid, bh, smem, s);
+    DMRG_TC_CASE(TC_BF16X3, EPI_SPLIT_BF16)
+    DMRG_TC_CASE(TC_BF16X3, EPI_F32)
+    DMRG_TC_CASE(TC_TF32, EPI_TF32)
+    DMRG_TC_CASE(TC_TF32, EPI_F32)
+#undef DMRG_TC_CASE
+    return cudaErrorNotSupported;
+}
+
+}  // namespace dmrg
