@@ -225,7 +225,7 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     {
         TcOperand A{Op[0], Op[1], K * m, m, D.ld1};
         TcOperand B{B1[0], B1[1], int64_t(d) * mp, m, D.ld1};
-        if (!make_problem(P1, mode, A, B, c1.tile_n_max, 1, c1.row_bytes, c1.pair != 0))
+        if (!make_problem(P1, mode, A, B, c1.tile_n_max, 1, c1.row_bytes, c1.pair))
             return fail(h, DMRG_ERR_CUDA, "cuTensorMapEncodeTiled failed (first product)");
     }
     TcScatter& S1 = P1.sc[0];
@@ -247,7 +247,7 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     const int grid1 = c1.grid > 0 ? c1.grid : h->num_sms;
     e = timed_launch(h, "tc_gemm_first_product", s, [&] {
         const TcEpi epi = split ? EPI_SPLIT_BF16 : EPI_TF32;
-        return c1.pair ? tc_gemm_launch_pair(mode, epi, L1, c1.stages, grid1, s)
+        return c1.pair ? tc_gemm_launch_pair(mode, epi, L1, c1.stages, grid1, s, c1.pair)
                        : tc_gemm_launch(mode, epi, L1, c1.stages, grid1, s);
     });
     if (e != cudaSuccess) return cuda_fail(h, e, "first product");
@@ -258,7 +258,7 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     {
         TcOperand A{Tt[0], Tt[1], K * mp, D.md, D.ld2};
         TcOperand B{B2[0], B2[1], mp, D.md, D.ld2};
-        if (!make_problem(P2, mode, A, B, c2.tile_n_max, 1, c2.row_bytes, c2.pair != 0))
+        if (!make_problem(P2, mode, A, B, c2.tile_n_max, 1, c2.row_bytes, c2.pair))
             return fail(h, DMRG_ERR_CUDA, "cuTensorMapEncodeTiled failed (second product)");
     }
     TcScatter& S2 = P2.sc[0];
@@ -277,7 +277,7 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     // CTA pairs) are whole M tiles whose reduction is split so the last round is short.
     // Their parts accumulate with atomics into outputs cleared first.
     {
-        const int slots = c2.pair ? grid2 / 2 : grid2;
+        const int slots = c2.pair ? grid2 / (2 * c2.pair) : grid2;
         const int bm = c2.pair ? 256 : 128;
         const int tiles = P2.m_tiles * P2.n_tiles;
         const int full_mt = (tiles / slots) * slots / P2.n_tiles;
@@ -307,7 +307,7 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     L2.timeout_ns = timeout_ns(h);
     L2.row_bytes = c2.row_bytes;
     e = timed_launch(h, "tc_gemm_second_product", s, [&] {
-        return c2.pair ? tc_gemm_launch_pair(mode, EPI_F32, L2, c2.stages, grid2, s)
+        return c2.pair ? tc_gemm_launch_pair(mode, EPI_F32, L2, c2.stages, grid2, s, c2.pair)
                        : tc_gemm_launch(mode, EPI_F32, L2, c2.stages, grid2, s);
     });
     if (e != cudaSuccess) return cuda_fail(h, e, "second product");

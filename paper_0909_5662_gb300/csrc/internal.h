@@ -91,7 +91,8 @@ struct TcConfig {
     int stages = 3;
     int grid = 0;           // 0 = number of SMs
     int row_bytes = 128;    // 128: 128-byte swizzle; 64: 64-byte swizzle, half-depth k-blocks
-    int pair = 0;           // 1: CTA-pair kernel (256-row tiles on two SMs, cta_group::2)
+    int pair = 0;           // 1: CTA-pair kernel (256-row tiles on two SMs, cta_group::2);
+                            // 2: clusters of two pairs on neighbouring N tiles sharing A
     bool operator==(const TcConfig& o) const {
         return tile_n_max == o.tile_n_max && stages == o.stages && grid == o.grid &&
                row_bytes == o.row_bytes && pair == o.pair;
@@ -125,10 +126,10 @@ struct TcOperand {
 cudaError_t tc_gemm_launch(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
                            cudaStream_t s);
 int tc_max_stages(TcMode mode, int tile_n_max, int row_bytes = 128);
-// CTA-pair form: problems made with make_problem(..., pair = true); `grid` counts CTAs
-// (rounded down to even, capped by the clusters that fit at once).
+// CTA-pair form: problems made with make_problem(..., pairs_per_cluster); `grid` counts
+// CTAs (rounded down to whole clusters, capped by the clusters that fit at once).
 cudaError_t tc_gemm_launch_pair(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
-                                cudaStream_t s);
+                                cudaStream_t s, int pairs_per_cluster);
 int tc_pair_max_stages(TcMode mode, int tile_n_max, int row_bytes = 128);
 // Dispatch on cfg.pair.
 inline int tc_stages_for(TcMode mode, const TcConfig& c) {
@@ -143,8 +144,10 @@ bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t r
 // Chooses an N tile (multiple of 16, <= tile_n_max) that splits N evenly.
 int choose_tile_n(int64_t N, int tile_n_max);
 // Fills operand maps and tiling fields of a problem: D (M x N) += A B^T over Kred x nbatch.
+// pairs_per_cluster: 0 for the one-CTA kernel, 1 or 2 for the CTA-pair kernel (with 2,
+// n_tiles counts tiles of the cluster: two neighbouring N tiles).
 bool make_problem(TcProblem& p, TcMode mode, const TcOperand& A, const TcOperand& B,
-                  int tile_n_max, int k_splits, int row_bytes = 128, bool pair = false);
+                  int tile_n_max, int k_splits, int row_bytes = 128, int pairs_per_cluster = 0);
 // Scatter for a plain row-major (rows x cols, leading dimension ld) destination.
 TcScatter scatter_rowmajor(int64_t ld);
 

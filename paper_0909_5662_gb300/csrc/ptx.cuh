@@ -231,6 +231,20 @@ __device__ __forceinline__ void tma_load_3d_pair(void* smem_dst, const void* tma
         : "memory");
 }
 
+// The same, multicast: the tile lands at the same offset in every CTA of cta_mask,
+// and each destination's bytes are counted on the barrier at bar's offset in the
+// even CTA of that destination's pair.
+__device__ __forceinline__ void tma_load_3d_pair_mc(void* smem_dst, const void* tmap,
+                                                    uint32_t bar_cluster, int32_t x, int32_t y,
+                                                    int32_t z, uint16_t cta_mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        ".multicast::cluster [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(bar_cluster),
+        "h"(cta_mask)
+        : "memory");
+}
+
 template <uint32_t NCOLS>
 __device__ __forceinline__ void tmem_alloc_pair(uint32_t* dst_smem) {
     asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(

@@ -660,20 +660,23 @@ int choose_tile_n(int64_t N, int tile_n_max) {
 }
 
 bool make_problem(TcProblem& p, TcMode mode, const TcOperand& A, const TcOperand& B,
-                  int tile_n_max, int k_splits, int row_bytes, bool pair) {
+                  int tile_n_max, int k_splits, int row_bytes, int pairs_per_cluster) {
     const bool f32 = (mode == TC_TF32);
     const bool split = (mode == TC_BF16X3);
     if (row_bytes != 64) row_bytes = 128;
     const int elems = row_bytes / (f32 ? 4 : 2);
     if (A.cols != B.cols || A.nbatch != B.nbatch) return false;
-    // CTA pairs: 256-row M tiles, each CTA stages half of the N tile (at least 16 rows)
+    // CTA pairs: 256-row M tiles, each CTA stages half of the N tile (at least 16 rows);
+    // with two pairs per cluster each CTA loads half of its A rows (multicast)
+    const bool pair = pairs_per_cluster > 0;
     const int tile_n = pair ? std::max(32, choose_tile_n(B.rows, tile_n_max)) : choose_tile_n(B.rows, tile_n_max);
     const int b_box = pair ? tile_n / 2 : tile_n;
+    const int a_box = pairs_per_cluster == 2 ? kBM / 2 : kBM;
     const int bm = pair ? 2 * kBM : kBM;
     for (int i = 0; i < (split ? 2 : 1); ++i) {
         const void* a = i ? A.lo : A.hi;
         const void* b = i ? B.lo : B.hi;
-        if (!encode_operand_map(&p.tmA[i], a, f32, A.rows, A.cols, A.ld, 128, A.nbatch, A.batch_stride,
+        if (!encode_operand_map(&p.tmA[i], a, f32, A.rows, A.cols, A.ld, a_box, A.nbatch, A.batch_stride,
                                 row_bytes) ||
             !encode_operand_map(&p.tmB[i], b, f32, B.rows, B.cols, B.ld, b_box, B.nbatch,
                                 B.batch_stride, row_bytes))
@@ -690,6 +693,7 @@ bool make_problem(TcProblem& p, TcMode mode, const TcOperand& A, const TcOperand
     p.tile_n = tile_n;
     p.m_tiles = int32_t((A.rows + bm - 1) / bm);
     p.n_tiles = int32_t((B.rows + tile_n - 1) / tile_n);
+    if (pairs_per_cluster == 2) p.n_tiles = (p.n_tiles + 1) / 2;
     const int kb_total = int((A.cols + elems - 1) / elems) * int(A.nbatch);
     if (k_splits < 1) k_splits = 1;
     if (k_splits > kb_total) k_splits = kb_total;

@@ -1,21 +1,28 @@
 // tc_pair.cu -- tcgen05 GEMM on CTA pairs (cta_group::2), sm_103a.
 //
-// The same persistent pipeline as tc.cu, but two CTAs of a cluster compute one
+// The same persistent pipeline as tc.cu, but two CTAs (a pair) compute one
 // 256 x N tile together: each CTA stages its 128 rows of A and half of the N rows
 // of B in its own shared memory, and one thread of the even ("leader") CTA issues
 // tcgen05.mma.cta_group::2, which reads both CTAs' operands and accumulates each
 // CTA's 128 rows in that CTA's TMEM.  Per SM this halves the shared-memory and L2
 // traffic of the B operand, which bounds the one-CTA kernel.
 //
+// With NP = 2 a cluster holds two pairs working on neighbouring N tiles of the
+// same M tile.  They need the same rows of A, so each CTA loads half of its
+// 128 rows and the TMA multicasts them to the CTA of the same rank in the other
+// pair: the L2-to-SM operand traffic drops by another quarter.
+//
 // Protocol (every wait bounded, as in the one-CTA kernel):
-//   * both CTAs' TMA loads of a stage complete on the leader's full[s] barrier
+//   * all TMA loads landing in a pair complete on its leader's full[s] barrier
 //     (the leader arms it with the bytes of both CTAs);
-//   * the leader's commits multicast to empty[s] and to the accumulator-full
-//     barrier of both CTAs, so each CTA refills and drains its own buffers;
-//   * the epilogue warps of both CTAs arrive on the leader's accumulator-empty
+//   * every leader's commit multicasts to empty[s] of all CTAs of the cluster
+//     (empty[s] expects one arrival per pair: a stage is refilled only when every
+//     pair that reads it is done), and to the accumulator-full barrier of both
+//     CTAs of its own pair;
+//   * the epilogue warps of both CTAs arrive on their leader's accumulator-empty
 //     barrier (the peer through its shared::cluster address);
-//   * cluster barriers after set-up and before teardown keep either CTA from
-//     leaving while the other may still reach its barriers or TMEM.
+//   * cluster barriers after set-up and before teardown keep any CTA from leaving
+//     while another may still reach its barriers, its shared memory or TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -48,7 +55,7 @@ __device__ __forceinline__ int pair_n(int tile_n, int left) {
     return max(32, (n + 15) & ~15);
 }
 
-template <int MODE, int EPI, int RB>
+template <int MODE, int EPI, int RB, int NP>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_pair_kernel(const __grid_constant__ TcLaunch L, int stages, int bh_smem) {
     constexpr int kRowBytes = RB;
@@ -76,15 +83,25 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const uint32_t rank = cluster_ctarank();
+    const uint32_t crank = cluster_ctarank();  // 0 .. 2*NP-1
+    const uint32_t rank = crank & 1u;           // within the pair
+    const int pq = int(crank >> 1);             // pair within the cluster
+    const uint32_t lead = crank & ~1u;          // cluster rank of this pair's leader
     const bool leader = (rank == 0);
-    const int pair = blockIdx.x >> 1;
-    const int npairs = gridDim.x >> 1;
+    const int pair = blockIdx.x / (2 * NP);     // cluster index (tile schedule)
+    const int npairs = gridDim.x / (2 * NP);
+    constexpr uint16_t kAllCtas = (1u << (2 * NP)) - 1u;
+    const uint16_t pair_mask = uint16_t(3u << lead);
+    // A rows: this CTA loads kBM / NP of them and multicasts them to the CTA of the
+    // same rank in every pair of the cluster
+    constexpr int kARows = kBM / NP;
+    uint16_t a_mask = 0;
+    for (int q = 0; q < NP; ++q) a_mask |= uint16_t(1u << (2 * q + int(rank)));
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], NP);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
@@ -133,23 +150,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // both CTAs' bytes: A (128 rows each) and the B halves (tile_n / 2 rows each)
                 const uint32_t bytes =
                     2u * (a_bytes + uint32_t(P->tile_n / 2) * kRowBytes) * (kSplit ? 2u : 1u);
-                const int n_eff = pair_n(P->tile_n, P->N - dt.nt * P->tile_n);
-                const int ya = dt.mt * (2 * kBM) + int(rank) * kBM;
-                const int yb = dt.nt * P->tile_n + int(rank) * (n_eff / 2);
+                const int nt = NP * dt.nt + pq;
+                const int n_eff = pair_n(P->tile_n, P->N - nt * P->tile_n);
+                const int ya = dt.mt * (2 * kBM) + int(rank) * kBM + pq * kARows;
+                const int yb = nt * P->tile_n + int(rank) * (n_eff / 2);
                 for (int kb = dt.kb_begin; kb < dt.kb_end; ++kb) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, tmo, L.status, vabort)) {
                         ok = false;
                         break;
                     }
                     if (leader) mbar_arrive_expect_tx(&full[stage], bytes);
-                    const uint32_t fb = mapa_shared(smem_u32(&full[stage]), 0);
+                    const uint32_t fb = mapa_shared(smem_u32(&full[stage]), lead);
                     const int z = kb / dt.kb_per_batch;
                     const int x = (kb - z * dt.kb_per_batch) * kElemsPerRow;
-                    tma_load_3d_pair(stage_a(stage, 0), &P->tmA[0], fb, x, ya, z);
-                    tma_load_3d_pair(stage_b(stage, 0), &P->tmB[0], fb, x, yb, z);
-                    if (kSplit) {
-                        tma_load_3d_pair(stage_a(stage, 1), &P->tmA[1], fb, x, ya, z);
-                        tma_load_3d_pair(stage_b(stage, 1), &P->tmB[1], fb, x, yb, z);
+                    const uint32_t a_off = uint32_t(pq * kARows * kRowBytes);
+                    for (int h = 0; h < (kSplit ? 2 : 1); ++h) {
+                        if (NP == 1)
+                            tma_load_3d_pair(stage_a(stage, h), &P->tmA[h], fb, x, ya, z);
+                        else
+                            tma_load_3d_pair_mc(stage_a(stage, h) + a_off, &P->tmA[h], fb, x, ya, z,
+                                                a_mask);
+                        tma_load_3d_pair(stage_b(stage, h), &P->tmB[h], fb, x, yb, z);
                     }
                     armed |= 1u << stage;
                     armed_parity = (armed_parity & ~(1u << stage)) | (phase << stage);
@@ -189,7 +210,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!mbar_wait(&tempty[acc], acc_parity ^ 1u, tmo, L.status, vabort)) break;
                 tc_fence_after();
                 const uint32_t tmem_d = tmem_base + uint32_t(acc) * kAccStride;
-                const int n_eff = pair_n(P->tile_n, P->N - dt.nt * P->tile_n);
+                const int n_eff = pair_n(P->tile_n, P->N - (NP * dt.nt + pq) * P->tile_n);
                 const uint32_t idesc = make_idesc_pair(kFmt, uint32_t(n_eff));
                 for (int kb = dt.kb_begin; kb < dt.kb_end; ++kb) {
                     if (!mbar_wait(&full[stage], phase, tmo, L.status, vabort)) {
@@ -220,24 +241,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // waits on this stage expire (a barrier that nothing arrives on).
                     const bool withhold = L.drop_arrival && pair == 0 && it == 0 &&
                                           kb == dt.kb_begin;
-                    if (!withhold) mma_commit_pair(&empty[stage], 3);
+                    if (!withhold) mma_commit_pair(&empty[stage], kAllCtas);
                     if (++stage == stages) {
                         stage = 0;
                         phase ^= 1u;
                     }
                 }
                 if (!ok) break;
-                mma_commit_pair(&tfull[acc], 3);
+                mma_commit_pair(&tfull[acc], pair_mask);
             }
-            mma_commit_pair(drain, 1);
+            mma_commit_pair(drain, uint16_t(1u << lead));
             mbar_wait(drain, 0, kDrainTimeoutNs, L.status, zero_flag);
         }
     } else {
         // ------------------------------------------------------------ epilogue (both CTAs)
         const int quad = warp & 3;
         const int half = (warp - 2) >> 2;
-        const uint32_t tempty_leader0 = mapa_shared(smem_u32(&tempty[0]), 0);
-        const uint32_t tempty_leader1 = mapa_shared(smem_u32(&tempty[1]), 0);
+        const uint32_t tempty_leader0 = mapa_shared(smem_u32(&tempty[0]), lead);
+        const uint32_t tempty_leader1 = mapa_shared(smem_u32(&tempty[1]), lead);
         int it = 0;
         for (int t = pair; t < L.total_tiles; t += npairs, ++it) {
             const Decoded dt = decode_tile(L, t, kElemsPerRow);
@@ -251,8 +272,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const int row = dt.mt * (2 * kBM) + int(rank) * kBM + quad * 32 + lane;
             const bool row_ok = row < P->M && dt.kb_begin < dt.kb_end;
-            const int n0 = dt.nt * P->tile_n;
-            const int ncols = min(P->tile_n, P->N - n0);
+            const int n0 = (NP * dt.nt + pq) * P->tile_n;
+            const int ncols = min(P->tile_n, P->N - n0);  // <= 0: a padding tile of the cluster
             const TcScatter& S = P->sc[0];
             int64_t row_base = 0;
             if (row_ok) {
@@ -322,10 +343,11 @@ int clusters_that_fit(const void* kernel, const cudaLaunchConfig_t& cfg) {
     return fit;
 }
 
-template <int MODE, int EPI>
+template <int MODE, int EPI, int NP>
 cudaError_t launch_pair(const TcLaunch& L, int stages, int grid, int bh_smem, size_t smem,
                         cudaStream_t s) {
-    auto k = L.row_bytes == 64 ? tc_gemm_pair_kernel<MODE, EPI, 64> : tc_gemm_pair_kernel<MODE, EPI, 128>;
+    auto k = L.row_bytes == 64 ? tc_gemm_pair_kernel<MODE, EPI, 64, NP>
+                               : tc_gemm_pair_kernel<MODE, EPI, 128, NP>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -335,14 +357,14 @@ cudaError_t launch_pair(const TcLaunch& L, int stages, int grid, int bh_smem, si
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.x = 2 * NP;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    // A persistent grid larger than the pairs that fit at once would only queue.
+    // A persistent grid larger than the clusters that fit at once would only queue.
     const int fit = clusters_that_fit(reinterpret_cast<const void*>(k), cfg);
-    if (fit > 0 && 2 * fit < grid) cfg.gridDim.x = unsigned(2 * fit);
+    if (fit > 0 && 2 * NP * fit < grid) cfg.gridDim.x = unsigned(2 * NP * fit);
     return cudaLaunchKernelEx(&cfg, k, L, stages, bh_smem);
 }
 
@@ -361,17 +383,21 @@ int tc_pair_max_stages(TcMode mode, int tile_n_max, int row_bytes) {
 }
 
 cudaError_t tc_gemm_launch_pair(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
-                                cudaStream_t s) {
+                                cudaStream_t s, int pairs_per_cluster) {
     if (L.total_tiles <= 0) return cudaSuccess;
     if (L.table != nullptr || L.nprob < 1 || L.nprob > kMaxInlineProblems) return cudaErrorInvalidValue;
+    if (pairs_per_cluster != 1 && pairs_per_cluster != 2) return cudaErrorInvalidValue;
     int bn = 32;
     for (int i = 0; i < L.nprob; ++i) bn = std::max(bn, L.inline_prob[i].tile_n);
     const int bh = bn / 2;
     const size_t smem = pair_smem_bytes(mode, stages, bh, L.row_bytes);
     if (smem > 232448) return cudaErrorInvalidConfiguration;
-    grid = std::max(2, std::min(grid, 2 * L.total_tiles)) & ~1;
-#define DMRG_TC_CASE(M, E) \
-    if (mode == M && epi == E) return launch_pair<M, E>(L, stages, grid, bh, smem, s);
+    const int csize = 2 * pairs_per_cluster;
+    grid = std::max(csize, std::min(grid, csize * L.total_tiles)) / csize * csize;
+#define DMRG_TC_CASE(M, E)                                                          \
+    if (mode == M && epi == E)                                                      \
+        return pairs_per_cluster == 2 ? launch_pair<M, E, 2>(L, stages, grid, bh, smem, s) \
+                                      : launch_pair<M, E, 1>(L, stages, grid, bh, smem, s);
     DMRG_TC_CASE(TC_BF16X3, EPI_SPLIT_BF16)
     DMRG_TC_CASE(TC_BF16X3, EPI_F32)
     DMRG_TC_CASE(TC_TF32, EPI_TF32)

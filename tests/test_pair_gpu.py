@@ -1,10 +1,12 @@
 """GPU parity of the CTA-pair (cta_group::2) tensor-core kernels against the FP64
 oracle: the dense rotation O'_k = U^T (O_k (x) I_d) U (Sec. 2 step 5) with both
-products forced onto the pair kernel through the tiling cache file.
+products forced onto the pair kernel through the tiling cache file, with one pair
+per cluster and with two pairs per cluster sharing the A rows (TMA multicast).
 
 Shapes cover a pair tile whose second CTA is wholly past the last row, N tiles
-whose second half is wholly past the last column, ragged reductions, both swizzle
-widths and the split tail wave of the second product.
+whose second half is wholly past the last column, an odd number of N tiles (the
+second pair of the last cluster tile has no columns), ragged reductions, both
+swizzle widths and the split tail wave of the second product.
 """
 import json
 import os
@@ -33,13 +35,13 @@ def rel_err(got, ref):
     return num / np.linalg.norm(ref.reshape(len(ref), -1), axis=1)
 
 
-def run_pair(P, tmp_path, U, O, d, prec, tn1, tn2, rb, stages=None, deterministic=False):
+def run_pair(P, tmp_path, U, O, d, prec, tn1, tn2, rb, npc, stages=None, deterministic=False):
     K, m = O.shape[0], O.shape[1]
     mp = U.shape[1]
     key = lambda g: "%s:K%d:m%d:d%d:mp%d:p%d" % (g, K, m, d, mp, PCODE[prec])
     st = stages or 8   # reduced to the deepest pipeline that fits
     path = tmp_path / "tune.json"
-    path.write_text(json.dumps({key("g1"): [tn1, st, 0, rb, 1], key("g2"): [tn2, st, 0, rb, 1]}))
+    path.write_text(json.dumps({key("g1"): [tn1, st, 0, rb, npc], key("g2"): [tn2, st, 0, rb, npc]}))
     os.environ["DMRG_AUTOTUNE_CACHE"] = str(path)
     try:
         h = P.Handle()
@@ -68,33 +70,36 @@ SHAPES = [
 ]
 
 
+@pytest.mark.parametrize("npc", [1, 2])
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
-def test_pair_ragged(P, tmp_path, shape, prec):
+def test_pair_ragged(P, tmp_path, shape, prec, npc):
     m, d, mp, K = shape
     rng = np.random.default_rng(7000 + m + 3 * mp + K)
     U = orthonormal_columns(rng, m * d, mp)
     O = rng.standard_normal((K, m, m))
     ref = oracle.rotate_dense(U, O, d)
-    got = run_pair(P, tmp_path, U, O, d, prec, 256, 256, 128)
+    got = run_pair(P, tmp_path, U, O, d, prec, 256, 256, 128, npc)
     assert rel_err(got, ref).max() <= TOL[prec]
 
 
-@pytest.mark.parametrize("tiles", [(96, 64), (160, 208), (256, 128)])
+@pytest.mark.parametrize("npc", [1, 2])
+@pytest.mark.parametrize("tiles", [(96, 64), (160, 208), (256, 128), (224, 48)])
 @pytest.mark.parametrize("rb", [128, 64])
-def test_pair_tilings(P, tmp_path, tiles, rb):
+def test_pair_tilings(P, tmp_path, tiles, rb, npc):
     m, d, mp, K = 120, 4, 150, 9
     rng = np.random.default_rng(7100 + tiles[0] + rb)
     U = orthonormal_columns(rng, m * d, mp)
     O = rng.standard_normal((K, m, m))
     ref = oracle.rotate_dense(U, O, d)
     for prec in ("bf16x3", "tf32"):
-        got = run_pair(P, tmp_path, U, O, d, prec, tiles[0], tiles[1], rb)
-        assert rel_err(got, ref).max() <= TOL[prec], (prec, tiles, rb)
+        got = run_pair(P, tmp_path, U, O, d, prec, tiles[0], tiles[1], rb, npc)
+        assert rel_err(got, ref).max() <= TOL[prec], (prec, tiles, rb, npc)
 
 
+@pytest.mark.parametrize("npc", [1, 2])
 @pytest.mark.parametrize("deterministic", [False, True])
-def test_pair_full_size_m400_sampled(P, tmp_path, deterministic):
+def test_pair_full_size_m400_sampled(P, tmp_path, deterministic, npc):
     # Full size of the benchmark workload (d=4, m=m'=400, K=150); the second product
     # has more 256-row tiles than one wave of pairs, so its tail wave is split
     # (unless the deterministic option is set).  A seeded sample of operators is
@@ -104,5 +109,5 @@ def test_pair_full_size_m400_sampled(P, tmp_path, deterministic):
     sample = np.unique(np.concatenate([[0, 1, 2, w.K - 1], np.random.default_rng(5).choice(w.K, 8, replace=False)]))
     ref = oracle.rotate_dense(w.U, O32[sample].astype(np.float64), 4)
     for prec in ("bf16x3", "tf32"):
-        got = run_pair(P, tmp_path, w.U, O32, 4, prec, 160, 208, 128, deterministic=deterministic)
+        got = run_pair(P, tmp_path, w.U, O32, 4, prec, 240, 208, 128, npc, deterministic=deterministic)
         assert rel_err(got[sample], ref).max() <= TOL[prec], prec
