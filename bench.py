@@ -70,7 +70,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -80,7 +80,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def mark(self, which):
+        """Brackets the timed region: samples outside it are dropped."""
+        setattr(self, which, time.monotonic())
 
     def stop(self):
         if self.proc is None:
@@ -95,7 +99,10 @@ class ClockSampler:
             self.thread.join(timeout=2)
         sm, smax, reasons, power = [], [], set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        t0 = getattr(self, "t_begin", -1e30)
+        t1 = getattr(self, "t_end", 1e30)
+        inside = [ln for t, ln in self.lines if t0 <= t <= t1]
+        for ln in inside:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -108,10 +115,11 @@ class ClockSampler:
             for nm, val in zip(names, parts[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
-        loaded = [s for s, p in zip(sm, power) if p > 300] or sm
-        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+        return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm),
+                "window": "samples taken during the timed BF16x3 steps",
+                "power_w_median": statistics.median(power) if power else None,
                 "power_w_max": max(power) if power else None}
 
 
@@ -170,7 +178,7 @@ def run_reference(args):
     w = dense_config(WORKLOAD)
     for _ in range(args.warmup):
         pass  # the oracle has no warm-up state; keep the arm's shape
-    res = cpu_oracle_sample(w, budget_s=max(10.0, 3.0 * args.steps), max_ops=K_PER_GPU)
+    res = cpu_oracle_sample(w, budget_s=min(60.0, max(10.0, 3.0 * args.steps)), max_ops=K_PER_GPU)
     v = res["value"]
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": K_PER_GPU / v * 1e3, "higher_is_better": True,
@@ -265,8 +273,8 @@ def run_chained(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="dense", choices=["dense", "chained"],
@@ -314,11 +322,13 @@ def main():
             pg.barrier()
         torch.cuda.synchronize()
 
-    def time_steps(prec, O, steps, warmup, timing=False):
+    def time_steps(prec, O, steps, warmup, timing=False, sampler=None):
         out = P.dmrg_rotate_ops(U, O, D, prec)
         for _ in range(warmup):
             P.dmrg_rotate_ops(U, O, D, prec, out=out)
         barrier()
+        if sampler is not None:
+            sampler.mark("t_begin")
         if timing:
             P.dmrg_kernel_timing(reset=True)
             P.dmrg_set_option("kernel_timing", 1)
@@ -332,6 +342,8 @@ def main():
             b.record()
             evs.append((a, b))
         barrier()
+        if sampler is not None:
+            sampler.mark("t_end")
         if timing:
             P.dmrg_set_option("kernel_timing", 0)
         ms = sum(a.elapsed_time(b) for a, b in evs)
@@ -360,7 +372,8 @@ def main():
     P.dmrg_rotate_ops(U, O32, D, "bf16x3")
     torch.cuda.synchronize()
     sampler.start()
-    ms_total, kt, out_bf = time_steps("bf16x3", O32, args.steps, args.warmup, timing=True)
+    ms_total, kt, out_bf = time_steps("bf16x3", O32, args.steps, args.warmup, timing=True,
+                                      sampler=sampler)
     clocks = sampler.stop()
     ms_step = max_over_ranks(ms_total / args.steps)
     value = K_total / (ms_step * 1e-3)

@@ -274,8 +274,10 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     L2.out[0][0] = Oout;
     const int grid2 = c2.grid > 0 ? c2.grid : h->num_sms;
     // Tail wave: the tiles left after the last full wave over the persistent CTAs (or
-    // CTA pairs) are whole M tiles whose reduction is split so the last round is short.
-    // Their parts accumulate with atomics into outputs cleared first.
+    // CTA pairs) are whole M tiles whose reduction is split so the last round is short;
+    // a problem smaller than one wave is split as a whole.  The parts accumulate with
+    // atomics into outputs cleared first (so the summation order of those outputs may
+    // differ between runs; DMRG_OPT_DETERMINISTIC turns the split off).
     {
         const int slots = c2.pair ? grid2 / (2 * c2.pair) : grid2;
         const int bm = c2.pair ? 256 : 128;
@@ -285,7 +287,7 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
         const int64_t epr = c2.row_bytes / (split ? 2 : 4);   // reduction elements per k-block
         const int kb = int((D.md + epr - 1) / epr);
         const int parts = tail_mt > 0 ? std::min(kb, slots / (tail_mt * P2.n_tiles)) : 0;
-        if (!h->deterministic && full_mt > 0 && tail_mt > 0 && parts >= 2) {
+        if (!h->deterministic && tail_mt > 0 && parts >= 2) {
             TcProblem& T2 = L2.inline_prob[1];
             T2 = P2;
             P2.m_tiles = full_mt;

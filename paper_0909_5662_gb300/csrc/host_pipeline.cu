@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "api_common.h"
 
@@ -18,8 +19,35 @@ using namespace dmrg;
 
 namespace {
 
+// Chunk boundaries.  chunk > 0: equal chunks of that many operators.  chunk == 0:
+// about five equal chunks, but the first and the last are cut to a third, so that
+// the copy-in before the first rotation and the copy-out after the last one, which
+// nothing overlaps, are short.
+std::vector<int64_t> chunk_starts(int64_t K, int64_t chunk) {
+    std::vector<int64_t> st;
+    if (K <= 0) return st;
+    if (chunk > 0) {
+        for (int64_t k = 0; k < K; k += chunk) st.push_back(k);
+    } else {
+        const int64_t base = std::max<int64_t>(1, (K + 4) / 5);
+        const int64_t edge = std::max<int64_t>(1, (base + 2) / 3);
+        if (K <= 2 * edge) {
+            for (int64_t k = 0; k < K; k += edge) st.push_back(k);
+        } else {
+            // first and last chunks of `edge`, the middle split evenly into chunks <= base
+            const int64_t mid = K - 2 * edge, n = (mid + base - 1) / base;
+            st.push_back(0);
+            for (int64_t i = 0; i < n; ++i) st.push_back(edge + mid * i / n);
+            st.push_back(K - edge);
+        }
+    }
+    st.push_back(K);
+    return st;
+}
+
 struct HostDims {
-    int64_t chunk, nchunks;
+    int64_t chunk, nchunks;   // largest chunk, number of chunks
+    std::vector<int64_t> starts;
     size_t es_in, es_out;
     WsLayout ws;   // U, O[2], Oout[2], rotation workspace for one chunk
 };
@@ -27,9 +55,10 @@ struct HostDims {
 HostDims host_dims(int64_t K, int64_t m, int d, int64_t mp, dmrg_precision p, int in_is_fp64,
                    int64_t chunk) {
     HostDims H;
-    if (chunk <= 0) chunk = std::max<int64_t>(1, (K + 4) / 5);
-    H.chunk = std::min<int64_t>(chunk, std::max<int64_t>(K, 1));
-    H.nchunks = K > 0 ? (K + H.chunk - 1) / H.chunk : 0;
+    H.starts = chunk_starts(K, chunk);
+    H.nchunks = H.starts.empty() ? 0 : int64_t(H.starts.size()) - 1;
+    H.chunk = 1;
+    for (int64_t c = 0; c < H.nchunks; ++c) H.chunk = std::max(H.chunk, H.starts[c + 1] - H.starts[c]);
     H.es_in = in_is_fp64 ? 8 : 4;
     H.es_out = p == DMRG_PREC_FP64 ? 8 : 4;
     H.ws.add("U", size_t(m) * d * mp * 8);
@@ -94,8 +123,6 @@ dmrg_status dmrg_rotate_ops_host(dmrg_handle h, const double* U, int64_t m, int 
     cudaStream_t cs[2] = {s, h->compute2};
     const size_t op_in = size_t(m) * m * H.es_in, op_out = size_t(mp) * mp * H.es_out;
     const TcMode mode = (p == DMRG_PREC_BF16X3) ? TC_BF16X3 : TC_TF32;
-    const TcConfig c1 = tuned_config(h, shape_key("g1", H.chunk, m, d, mp, p), mode);
-    const TcConfig c2 = tuned_config(h, shape_key("g2", H.chunk, m, d, mp, p), mode);
 
     // everything the caller queued before this call happens first
     if ((e = cudaEventRecord(h->ev_start, s)) != cudaSuccess ||
@@ -110,7 +137,7 @@ dmrg_status dmrg_rotate_ops_host(dmrg_handle h, const double* U, int64_t m, int 
     if (e != cudaSuccess) return cuda_fail(h, e, "copy U");
     for (int64_t c = 0; c < H.nchunks; ++c) {
         const int b = int(c & 1);
-        const int64_t k0 = c * H.chunk, kc = std::min(H.chunk, K - k0);
+        const int64_t k0 = H.starts[c], kc = H.starts[c + 1] - k0;
         // copy in: the buffer is free once the rotation of chunk c-2 has read it
         if (c >= 2 && (e = cudaStreamWaitEvent(h->copy_in, h->ev_comp[b], 0)) != cudaSuccess)
             return cuda_fail(h, e, "ordering");
@@ -124,6 +151,8 @@ dmrg_status dmrg_rotate_ops_host(dmrg_handle h, const double* U, int64_t m, int 
         if ((e = cudaStreamWaitEvent(x, h->ev_in[b], 0)) != cudaSuccess) return cuda_fail(h, e, "ordering");
         if (c >= 2 && (e = cudaStreamWaitEvent(x, h->ev_out[b], 0)) != cudaSuccess)
             return cuda_fail(h, e, "ordering");
+        const TcConfig c1 = tc ? tuned_config(h, shape_key("g1", kc, m, d, mp, p), mode) : TcConfig();
+        const TcConfig c2 = tc ? tuned_config(h, shape_key("g2", kc, m, d, mp, p), mode) : TcConfig();
         st = tc ? dense_tc_forward(h, Ud, m, d, mp, Od[b], in_is_fp64, kc, Rd[b], p, rot[b], c1, c2, x,
                                    c < 2)
                 : dense_simt_forward(h, Ud, m, d, mp, Od[b], in_is_fp64, kc, Rd[b], p, rot[b], x, c < 2);

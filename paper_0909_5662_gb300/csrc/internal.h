@@ -175,7 +175,8 @@ struct PackJob {
     // srcs[src_sel] of the launch and dst0 / dst1 hold byte offsets from its
     // workspace base (rel = 1); rel = 0 means absolute pointers.
     int32_t rel, src_sel;
-    int32_t vec8, pad;     // set by the launcher: contiguous rows, 8 elements per thread
+    int32_t vec8;          // set by the launcher: contiguous rows, 8 elements per thread
+    int32_t tiled;         // set by the launcher: transposing gather through 32 x 32 tiles
 };
 cudaError_t pack_launch(const PackJob* jobs_host, int njobs, PackJob* jobs_dev_or_null,
                         cudaStream_t s);

@@ -349,72 +349,16 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constan
     }
 }
 
-// Contiguous fast path: source rows of `cols` elements at stride s_r_hi, 8
-// elements per thread with 16/32-byte loads and 16-byte stores (BF16 hi and lo)
-// or 2 x 16-byte stores (TF32 / FP32).
+// Contiguous fast path: one 8-element unit v of a job whose source rows are
+// contiguous (16/32-byte loads, 16-byte stores of the BF16 hi and lo halves or
+// 2 x 16-byte stores of TF32 / FP32), in two halves so that a thread can issue the
+// loads of several units before converting.
 template <typename S>
-__global__ void __launch_bounds__(kPackThreads) pack_rows_vec8_kernel(const __grid_constant__ PackJob j) {
-    const int64_t per_row = j.cols >> 3;
-    const int64_t total = j.rows * per_row;
-    const S* src = static_cast<const S*>(j.src) + j.src_off;
-    for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < total;
-         v += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t r = v / per_row;
-        const int64_t c = (v - r * per_row) << 3;
-        const S* sp = src + r * j.s_r_hi + c;
-        S x[8];
-        if (sizeof(S) == 4) {
-            const float4 a = reinterpret_cast<const float4*>(sp)[0];
-            const float4 b = reinterpret_cast<const float4*>(sp)[1];
-            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-            x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const double2 a = reinterpret_cast<const double2*>(sp)[q];
-                x[2 * q] = S(a.x);
-                x[2 * q + 1] = S(a.y);
-            }
-        }
-        const int64_t dst = r * j.ld + c;
-        if (j.mode == 0) {
-            uint32_t hw[4], lw[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                uint32_t hh[2], ll[2];
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    __nv_bfloat16 h, l;
-                    split_bf16(x[2 * q + e], h, l);
-                    hh[e] = __bfloat16_as_ushort(h);
-                    ll[e] = __bfloat16_as_ushort(l);
-                }
-                hw[q] = hh[0] | (hh[1] << 16);
-                lw[q] = ll[0] | (ll[1] << 16);
-            }
-            *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(j.dst0) + dst) =
-                make_uint4(hw[0], hw[1], hw[2], hw[3]);
-            *reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(j.dst1) + dst) =
-                make_uint4(lw[0], lw[1], lw[2], lw[3]);
-        } else {
-            float y[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) y[e] = (j.mode == 1) ? tf32_round(float(x[e])) : float(x[e]);
-            float4* d4 = reinterpret_cast<float4*>(static_cast<float*>(j.dst0) + dst);
-            d4[0] = make_float4(y[0], y[1], y[2], y[3]);
-            d4[1] = make_float4(y[4], y[5], y[6], y[7]);
-        }
-    }
-}
-
-// One 8-element unit v of a contiguous job (see pack_rows_vec8_kernel).
-template <typename S>
-__device__ __forceinline__ void pack_vec8_unit(const PackJob& j, int64_t v) {
+__device__ __forceinline__ void pack_vec8_load(const PackJob& j, int64_t v, S (&x)[8]) {
     const int64_t per_row = j.cols >> 3;
     const int64_t r = v / per_row;
     const int64_t c = (v - r * per_row) << 3;
     const S* sp = static_cast<const S*>(j.src) + j.src_off + r * j.s_r_hi + c;
-    S x[8];
     if (sizeof(S) == 4) {
         const float4 a = reinterpret_cast<const float4*>(sp)[0];
         const float4 b = reinterpret_cast<const float4*>(sp)[1];
@@ -428,6 +372,13 @@ __device__ __forceinline__ void pack_vec8_unit(const PackJob& j, int64_t v) {
             x[2 * q + 1] = S(a.y);
         }
     }
+}
+
+template <typename S>
+__device__ __forceinline__ void pack_vec8_store(const PackJob& j, int64_t v, const S (&x)[8]) {
+    const int64_t per_row = j.cols >> 3;
+    const int64_t r = v / per_row;
+    const int64_t c = (v - r * per_row) << 3;
     const int64_t dst = r * j.ld + c;
     if (j.mode == 0) {
         uint32_t hw[4], lw[4];
@@ -458,20 +409,83 @@ __device__ __forceinline__ void pack_vec8_unit(const PackJob& j, int64_t v) {
     }
 }
 
+// kVec8Units units per thread, block-strided, all loads issued before the stores.
+constexpr int kVec8Units = 2;
+
+template <typename S>
+__device__ __forceinline__ void pack_vec8_block(const PackJob& j, int64_t blk) {
+    const int64_t total = j.rows * (j.cols >> 3);
+    const int64_t v0 = blk * (int64_t(kPackThreads) * kVec8Units) + threadIdx.x;
+    S x[kVec8Units][8];
+#pragma unroll
+    for (int u = 0; u < kVec8Units; ++u) {
+        const int64_t v = v0 + int64_t(u) * kPackThreads;
+        if (v < total) pack_vec8_load<S>(j, v, x[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kVec8Units; ++u) {
+        const int64_t v = v0 + int64_t(u) * kPackThreads;
+        if (v < total) pack_vec8_store<S>(j, v, x[u]);
+    }
+}
+
+// Transposing gathers (source contiguous along the row index, strided along the
+// column index, e.g. U -> U^T) go through shared memory in 32 x 32 tiles so that both
+// the reads and the writes are coalesced.  Tile t of a job covers, for one residue
+// rem = r mod rdiv, the rows r = (h0 + 0..31) * rdiv + rem and columns c0 + 0..31.
+__device__ __forceinline__ int64_t pack_tiles_for(const PackJob& j) {
+    const int64_t hrows = j.rows / j.rdiv;
+    return int64_t(j.rdiv) * ((hrows + 31) / 32) * ((j.cols + 31) / 32);
+}
+
+__device__ __forceinline__ void pack_tile(const PackJob& j, int64_t t, double (*tile)[33]) {
+    const int64_t hrows = j.rows / j.rdiv;
+    const int64_t ht = (hrows + 31) / 32, ct = (j.cols + 31) / 32;
+    const int64_t rem = t / (ht * ct);
+    const int64_t u = t - rem * ht * ct;
+    const int64_t h0 = (u / ct) * 32, c0 = (u % ct) * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 warps
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t c = c0 + ty + 8 * q, hr = h0 + tx;
+        double v = 0.0;
+        if (c < j.cols && hr < hrows) {
+            const int64_t src = j.src_off + hr + rem * j.s_r_lo + c * j.s_c;
+            v = j.src_f64 ? static_cast<const double*>(j.src)[src]
+                          : double(static_cast<const float*>(j.src)[src]);
+        }
+        tile[ty + 8 * q][tx] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t hr = h0 + ty + 8 * q, c = c0 + tx;
+        if (c < j.cols && hr < hrows) {
+            const int64_t r = hr * j.rdiv + rem;
+            if (j.src_f64) pack_store(j, r * j.ld + c, tile[tx][ty + 8 * q]);
+            else pack_store(j, r * j.ld + c, float(tile[tx][ty + 8 * q]));
+        }
+    }
+}
+
 // Several jobs in one launch: block ranges per job; contiguous jobs take the 8-wide
-// path, the others the general gather.  Small gathers placed first run alongside
-// the bandwidth-bound contiguous job instead of after it.
+// path, transposing gathers the tiled path, the others the general gather.  Small
+// gathers placed first run alongside the bandwidth-bound contiguous job instead of
+// after it.
 __global__ void __launch_bounds__(kPackThreads) pack_mixed_kernel(const __grid_constant__ PackLaunch L) {
+    __shared__ double tile[32][33];
     const int b = blockIdx.x;
     int k = 0;
     for (int i = 1; i < L.njobs; ++i)
         if (L.inline_jobs[i].block_start <= b) k = i;
     const PackJob& j = L.inline_jobs[k];
+    if (j.tiled) {
+        pack_tile(j, int64_t(b - j.block_start), tile);
+        return;
+    }
     if (j.vec8) {
-        const int64_t v = int64_t(b - j.block_start) * kPackThreads + threadIdx.x;
-        if (v >= j.rows * (j.cols >> 3)) return;
-        if (j.src_f64) pack_vec8_unit<double>(j, v);
-        else pack_vec8_unit<float>(j, v);
+        if (j.src_f64) pack_vec8_block<double>(j, int64_t(b - j.block_start));
+        else pack_vec8_block<float>(j, int64_t(b - j.block_start));
         return;
     }
     const int64_t total = j.rows * j.cols;
@@ -491,6 +505,17 @@ __global__ void __launch_bounds__(kPackThreads) pack_mixed_kernel(const __grid_c
         else
             pack_store(j, r * j.ld + c, static_cast<const float*>(j.src)[src]);
     }
+}
+
+bool pack_tiled_ok(const PackJob& j) {
+    const bool single_group = (j.rows_per_op >= j.rows) && j.op_off == nullptr;
+    return single_group && j.s_r_hi == 1 && j.s_c != 1 && j.rdiv >= 1 && (j.rows % j.rdiv) == 0 &&
+           j.cols >= 8;
+}
+
+int64_t pack_tiles_host(const PackJob& j) {
+    const int64_t hrows = j.rows / j.rdiv;
+    return int64_t(j.rdiv) * ((hrows + 31) / 32) * ((j.cols + 31) / 32);
 }
 
 bool pack_vec8_ok(const PackJob& j) {
@@ -587,11 +612,14 @@ cudaError_t pack_launch(const PackJob* jobs, int njobs, PackJob* /*unused*/, cud
             if (jobs[i].rows * jobs[i].cols == 0) continue;
             const bool v8 = pack_vec8_ok(jobs[i]);
             if (v8 != (pass == 1)) continue;
+            const bool tl = !v8 && pack_tiled_ok(jobs[i]);
             PackJob& j = L.inline_jobs[n++];
             j = jobs[i];
             j.vec8 = v8 ? 1 : 0;
+            j.tiled = tl ? 1 : 0;
             j.block_start = blocks;
-            blocks += v8 ? (j.rows * (j.cols / 8) + kPackThreads - 1) / kPackThreads : pack_blocks_for(j);
+            blocks += v8 ? (j.rows * (j.cols / 8) + kPackThreads * kVec8Units - 1) / (kPackThreads * kVec8Units)
+                    : tl ? pack_tiles_host(j) : pack_blocks_for(j);
         }
     if (n == 0 || blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
