@@ -193,6 +193,112 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------- GPU leg
+# ---------------------------------------------------------------------------- blocked and adjoint reports
+def _timed(fn, steps, warmup, flush):
+    """Mean CUDA-event time (ms) of fn over `steps` calls after `warmup`, L2 flushed
+    between calls (the flush itself is outside the timed intervals)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+
+def run_blocked(args):
+    """The U(1)xU(1) block-sparse rotation (grouped launches over the realised sector
+    problems) on both synthetic sector laws: time per call for every precision,
+    logical TFLOP/s over the realised problems, and the error of each reduced path
+    against the FP64 GPU path on the same inputs."""
+    import torch
+    import paper_0909_5662_gb300 as P
+    from workloads import blocked_config
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    steps = max(1, min(args.steps, 200))
+    res = {}
+    for name in ("blocked_m1000_k200_s4", "blocked_m1000_k200_s1.2"):
+        w = blocked_config(name)
+        plan = P.dmrg_blocked_plan_create(w.block_sectors, w.site_shifts, w.kept_sectors, w.op_shifts)
+        n1, n2, flops = plan.stats()
+        Ub = torch.from_numpy(w.U_blocks).to(dev)
+        O64 = torch.from_numpy(w.O_blocks).to(dev)
+        O32 = O64.float()
+        ref = P.dmrg_rotate_ops_blocked(plan, Ub, O64, "fp64")
+        row = {"problems_first": n1, "problems_second": n2, "flops_per_call": flops,
+               "sectors": len(w.block_sectors), "operators": w.K,
+               "block_rows_max": max(s[2] for s in w.block_sectors)}
+        for prec in ("bf16x3", "tf32", "fp32", "fp64"):
+            O = O64 if prec == "fp64" else O32
+            out = P.dmrg_rotate_ops_blocked(plan, Ub, O, prec)
+            ms = _timed(lambda: P.dmrg_rotate_ops_blocked(plan, Ub, O, prec, out=out),
+                        steps if prec != "fp64" else max(1, steps // 10), 3, flush)
+            P.dmrg_sync_status()
+            err = float((torch.linalg.vector_norm(out.double() - ref) / torch.linalg.vector_norm(ref)).item())
+            row[prec] = {"ms_per_call": ms, "ops_per_s": w.K / (ms * 1e-3),
+                         "tflops_logical": flops / (ms * 1e-3) / 1e12, "rel_fro_err_vs_fp64": err}
+        res[name] = row
+        plan.close()
+    line = {"workload": "blocked U(1)xU(1), m=1000, d=4, K=200 (two sector laws)",
+            "metric": "block-sparse rotation: ms per call, logical TFLOP/s over the realised problems",
+            "steps": steps, "l2": "flushed between timed calls", "results": res, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_backward(args):
+    """The adjoint at the benchmark shape (d = 4, m = m' = 400, K = 150, FP32 operators,
+    upstream G ~ N(0,1)): dO and dU per call for each precision, in forward-product
+    equivalents (one forward product = 0.512 GFLOP logical per operator), with the
+    error of the reduced paths against the FP32-input FP64 path."""
+    import numpy as np
+    import torch
+    import paper_0909_5662_gb300 as P
+    from workloads import dense_config, backward_upstream, SEED_BASE
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    steps = max(1, min(args.steps, 200))
+    w = dense_config(WORKLOAD)
+    U = torch.from_numpy(w.U).to(dev)
+    O32 = torch.from_numpy(w.O).to(dev, torch.float32)
+    G32 = torch.from_numpy(backward_upstream(SEED_BASE + 4, w.K, w.mp)).to(dev, torch.float32)
+    dO_ref, dU_ref = P.dmrg_rotate_ops_backward(U, O32.double(), G32.double(), w.d, "fp64")
+    fwd_product = 2.0 * w.K * w.m * (w.d * w.mp) * w.m
+    res = {}
+    for prec in ("bf16x3", "tf32", "fp32"):
+        dO, dU = P.dmrg_rotate_ops_backward(U, O32, G32, w.d, prec)
+        ms = _timed(lambda: P.dmrg_rotate_ops_backward(U, O32, G32, w.d, prec), steps, 3, flush)
+        P.dmrg_sync_status()
+        num = torch.linalg.vector_norm((dO.double() - dO_ref).reshape(w.K, -1), dim=1)
+        den = torch.linalg.vector_norm(dO_ref.reshape(w.K, -1), dim=1)
+        res[prec] = {"ms_per_call": ms, "ops_per_s": w.K / (ms * 1e-3),
+                     "forward_products_per_ms": 1.0 / ms,
+                     "tflops_at_5_products": 5 * fwd_product / (ms * 1e-3) / 1e12,
+                     "dO_max_rel_fro_err": float((num / den).max()),
+                     "dU_rel_fro_err": float((torch.linalg.vector_norm(dU - dU_ref) /
+                                              torch.linalg.vector_norm(dU_ref)).item())}
+    t64 = _timed(lambda: P.dmrg_rotate_ops_backward(U, O32.double(), G32.double(), w.d, "fp64"), 1, 1, flush)
+    res["fp64"] = {"ms_per_call": t64, "ops_per_s": w.K / (t64 * 1e-3)}
+    line = {"workload": "backward dense_m400_k150 (d=4, m=m'=400, K=150, upstream N(0,1))",
+            "metric": "adjoint: ms per call (dO and dU), rotated operators/s",
+            "steps": steps, "l2": "flushed between timed calls", "results": res, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------------------- chained sweep
 def run_chained(args):
     """50 consecutive block-growth steps at d = 4, m = m' = 1200, K = 300: the rotated
@@ -277,8 +383,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="dense", choices=["dense", "chained"],
-                    help="dense: the benchmark line; chained: the 50-step sweep report")
+    ap.add_argument("--workload", default="dense", choices=["dense", "chained", "blocked", "backward"],
+                    help="dense: the benchmark line; chained: the 50-step sweep report; "
+                         "blocked / backward: reports of the block-sparse and adjoint paths")
     ap.add_argument("--sweep-steps", type=int, default=50)
     ap.add_argument("--profile", action="store_true",
                     help="only the BF16x3 step: warm-up then --steps steps (for ncu captures)")
@@ -289,6 +396,10 @@ def main():
         return run_reference(args)
     if args.workload == "chained":
         return run_chained(args)
+    if args.workload == "blocked":
+        return run_blocked(args)
+    if args.workload == "backward":
+        return run_backward(args)
 
     import numpy as np
     import torch

@@ -158,11 +158,13 @@ TcConfig tuned_config(dmrg_handle h, const std::string& key, TcMode mode) {
         return c;
     }
     // Untuned default: 128-byte rows, N tiles up to 256, the deepest pipeline that
-    // fits; the two dense products run on CTA pairs (half of B staged per SM).
+    // fits; the dense products and the adjoint's products run on CTA pairs (half of B
+    // staged per SM).
     TcConfig c;
     c.tile_n_max = 256;
     c.row_bytes = 128;
-    c.pair = (key.compare(0, 3, "g1:") == 0 || key.compare(0, 3, "g2:") == 0) ? 1 : 0;
+    c.pair = (key.compare(0, 3, "g1:") == 0 || key.compare(0, 3, "g2:") == 0 ||
+              key.compare(0, 4, "bwd:") == 0) ? 1 : 0;
     c.stages = tc_stages_for(mode, c);
     c.grid = 0;
     return c;

@@ -177,9 +177,9 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
     };
     auto lo = [&](int idx) -> void* { return split ? sec(idx, 1) : sec(idx, 0); };
     cudaError_t e;
-    // ---- packs
+    // ---- packs: U, U_r, G, G^T and (for dU) O, O^T in one launch
     {
-        PackJob jobs[4] = {};
+        PackJob jobs[6] = {};
         PackJob& ju = jobs[0];   // U: rows r, cols a
         ju.src = U; ju.src_f64 = 1; ju.mode = pmode; ju.rows = md; ju.cols = mp; ju.rows_per_op = md;
         ju.rdiv = 1; ju.s_r_hi = mp; ju.s_c = 1; ju.dst0 = sec(B.i_U, 0); ju.dst1 = lo(B.i_U); ju.ld = B.ld_u;
@@ -194,25 +194,21 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
         jt.src = G; jt.src_f64 = in_is_fp64; jt.mode = pmode; jt.rows = K * mp; jt.cols = mp;
         jt.rows_per_op = mp; jt.s_op = mp * mp; jt.rdiv = 1; jt.s_r_hi = 1; jt.s_c = mp;
         jt.dst0 = sec(B.i_GT, 0); jt.dst1 = lo(B.i_GT); jt.ld = B.ld_u;
-        e = timed_launch(h, "bwd_pack_UG", s, [&] { return pack_launch(jobs, 4, nullptr, s); });
-        if (e != cudaSuccess) return cuda_fail(h, e, "pack U/G");
+        int nj = 4;
+        if (dU) {
+            PackJob& jo = jobs[nj++];   // O: rows (k, i), cols j
+            jo.src = O; jo.src_f64 = in_is_fp64; jo.mode = pmode; jo.rows = K * m; jo.cols = m;
+            jo.rows_per_op = K * m; jo.rdiv = 1; jo.s_r_hi = m; jo.s_c = 1;
+            jo.dst0 = sec(B.i_O, 0); jo.dst1 = lo(B.i_O); jo.ld = B.ld_j;
+            PackJob& jq = jobs[nj++];   // O^T: rows (k, i), cols j = O_k[j][i]
+            jq.src = O; jq.src_f64 = in_is_fp64; jq.mode = pmode; jq.rows = K * m; jq.cols = m;
+            jq.rows_per_op = m; jq.s_op = m * m; jq.rdiv = 1; jq.s_r_hi = 1; jq.s_c = m;
+            jq.dst0 = sec(B.i_OT, 0); jq.dst1 = lo(B.i_OT); jq.ld = B.ld_j;
+        }
+        e = timed_launch(h, "bwd_pack", s, [&] { return pack_launch(jobs, nj, nullptr, s); });
+        if (e != cudaSuccess) return cuda_fail(h, e, "pack");
     }
-    if (dU) {
-        PackJob jobs[2] = {};
-        PackJob& jo = jobs[0];   // O: rows (k, i), cols j
-        jo.src = O; jo.src_f64 = in_is_fp64; jo.mode = pmode; jo.rows = K * m; jo.cols = m;
-        jo.rows_per_op = K * m; jo.rdiv = 1; jo.s_r_hi = m; jo.s_c = 1;
-        jo.dst0 = sec(B.i_O, 0); jo.dst1 = lo(B.i_O); jo.ld = B.ld_j;
-        PackJob& jt = jobs[1];   // O^T: rows (k, i), cols j = O_k[j][i]
-        jt.src = O; jt.src_f64 = in_is_fp64; jt.mode = pmode; jt.rows = K * m; jt.cols = m;
-        jt.rows_per_op = m; jt.s_op = m * m; jt.rdiv = 1; jt.s_r_hi = 1; jt.s_c = m;
-        jt.dst0 = sec(B.i_OT, 0); jt.dst1 = lo(B.i_OT); jt.ld = B.ld_j;
-        e = timed_launch(h, "bwd_pack_O", s, [&] { return pack_launch(jobs, 2, nullptr, s); });
-        if (e != cudaSuccess) return cuda_fail(h, e, "pack O");
-    }
-    TcConfig cfg = tuned_config(h, shape_key("bwd", K, m, d, mp, p), mode);
-    cfg.pair = 0;  // the adjoint's grouped products run on the one-CTA kernel
-    cfg.stages = std::min(cfg.stages, tc_max_stages(mode, cfg.tile_n_max, cfg.row_bytes));
+    const TcConfig cfg = tuned_config(h, shape_key("bwd", K, m, d, mp, p), mode);
     const int grid = cfg.grid > 0 ? cfg.grid : h->num_sms;
     auto launch = [&](const char* name, TcLaunch& L, TcEpi epi) -> dmrg_status {
         L.table = nullptr;
@@ -226,7 +222,8 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
         L.timeout_ns = timeout_ns(h);
         L.row_bytes = cfg.row_bytes;
         cudaError_t ee = timed_launch(h, name, s, [&] {
-            return tc_gemm_launch(mode, epi, L, cfg.stages, grid, s);
+            return cfg.pair ? tc_gemm_launch_pair(mode, epi, L, cfg.stages, grid, s, cfg.pair)
+                            : tc_gemm_launch(mode, epi, L, cfg.stages, grid, s);
         });
         return cuda_fail(h, ee, name);
     };
@@ -237,7 +234,7 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
         TcProblem& P = L.inline_prob[0];
         TcOperand A{sec(B.i_G, 0), lo(B.i_G), K * mp, mp, B.ld_u};
         TcOperand Bo{sec(B.i_U, 0), lo(B.i_U), md, mp, B.ld_u};
-        if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, 1, cfg.row_bytes)) return fail(h, DMRG_ERR_CUDA, "tensor map");
+        if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, 1, cfg.row_bytes, cfg.pair)) return fail(h, DMRG_ERR_CUDA, "tensor map");
         TcScatter& S = P.sc[0];
         S.rows_per_op = int32_t(mp); S.s_op = m * B.ld_n; S.s_row = 1;
         S.col_div = d; S.s_col_hi = B.ld_n; S.s_col_lo = mp;
@@ -250,7 +247,7 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
         TcProblem& P2 = L2.inline_prob[0];
         TcOperand A2{sec(B.i_Wp, 0), lo(B.i_Wp), K * m, dmp, B.ld_n};
         TcOperand B2{sec(B.i_Ur, 0), lo(B.i_Ur), m, dmp, B.ld_n};
-        if (!make_problem(P2, mode, A2, B2, cfg.tile_n_max, 1, cfg.row_bytes)) return fail(h, DMRG_ERR_CUDA, "tensor map");
+        if (!make_problem(P2, mode, A2, B2, cfg.tile_n_max, 1, cfg.row_bytes, cfg.pair)) return fail(h, DMRG_ERR_CUDA, "tensor map");
         TcScatter& S2 = P2.sc[0];
         S2.rows_per_op = int32_t(m); S2.s_op = m * m; S2.s_row = 1;
         S2.col_div = 1; S2.s_col_hi = m; S2.s_col_lo = 0;
@@ -275,7 +272,7 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
                                 static_cast<char*>(lo(B.i_U)) + size_t(sidx) * B.ld_u * esz,
                                 m, mp, int64_t(d) * B.ld_u};
                     TcOperand Bo{sec(gsec, 0), lo(gsec), K * mp, mp, B.ld_u};
-                    if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, 1, cfg.row_bytes))
+                    if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, 1, cfg.row_bytes, cfg.pair))
                         return fail(h, DMRG_ERR_CUDA, "tensor map");
                     TcScatter& S = P.sc[0];
                     S.rows_per_op = 1 << 30; S.s_op = 0; S.s_row = 1;
@@ -306,7 +303,7 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
             const int bsec = q == 0 ? B.i_WTp : B.i_WT;
             TcOperand A{sec(asec, 0), lo(asec), m, m, B.ld_j, K, m * B.ld_j};
             TcOperand Bo{sec(bsec, 0), lo(bsec), dmp, m, B.ld_j, K, dmp * B.ld_j};
-            if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, ksplit, cfg.row_bytes))
+            if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, ksplit, cfg.row_bytes, cfg.pair))
                 return fail(h, DMRG_ERR_CUDA, "tensor map");
             P.sc[0] = scatter_rowmajor(dmp);
         }

@@ -268,8 +268,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ---------------------------------------------------------------- packer
+constexpr int kMaxPackJobs = 8;
+
 struct PackLaunch {
-    PackJob inline_jobs[4];
+    PackJob inline_jobs[kMaxPackJobs];
     const PackJob* table;
     int njobs;
     const void* srcs[2];
@@ -429,42 +431,64 @@ __device__ __forceinline__ void pack_vec8_block(const PackJob& j, int64_t blk) {
     }
 }
 
-// Transposing gathers (source contiguous along the row index, strided along the
-// column index, e.g. U -> U^T) go through shared memory in 32 x 32 tiles so that both
-// the reads and the writes are coalesced.  Tile t of a job covers, for one residue
-// rem = r mod rdiv, the rows r = (h0 + 0..31) * rdiv + rem and columns c0 + 0..31.
-__device__ __forceinline__ int64_t pack_tiles_for(const PackJob& j) {
-    const int64_t hrows = j.rows / j.rdiv;
-    return int64_t(j.rdiv) * ((hrows + 31) / 32) * ((j.cols + 31) / 32);
+// Transposing gathers of FP32 sources (contiguous along the row index, strided along
+// the column index, e.g. O_k -> O_k^T) go through shared memory in 64 x 64 tiles, so
+// that both the reads and the writes are coalesced: each thread has 16 loads in flight
+// and writes column pairs (packed BF16 pairs, or FP32 pairs).  Tile t of a job covers,
+// in operator group g and for one residue rem = rr mod rdiv, the rows
+// rr = (h0 + 0..63) * rdiv + rem of the group and the columns c0 + 0..63.
+constexpr int kTile = 64;
+
+__device__ __forceinline__ void pack_store2(const PackJob& j, int64_t dst, float x0, float x1) {
+    if (j.mode == 0) {
+        __nv_bfloat16 h0, l0, h1, l1;
+        split_bf16(x0, h0, l0);
+        split_bf16(x1, h1, l1);
+        *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(j.dst0) + dst) =
+            uint32_t(__bfloat16_as_ushort(h0)) | (uint32_t(__bfloat16_as_ushort(h1)) << 16);
+        *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(j.dst1) + dst) =
+            uint32_t(__bfloat16_as_ushort(l0)) | (uint32_t(__bfloat16_as_ushort(l1)) << 16);
+    } else {
+        const bool t = (j.mode == 1);
+        *reinterpret_cast<float2*>(static_cast<float*>(j.dst0) + dst) =
+            make_float2(t ? tf32_round(x0) : x0, t ? tf32_round(x1) : x1);
+    }
 }
 
-__device__ __forceinline__ void pack_tile(const PackJob& j, int64_t t, double (*tile)[33]) {
-    const int64_t hrows = j.rows / j.rdiv;
-    const int64_t ht = (hrows + 31) / 32, ct = (j.cols + 31) / 32;
-    const int64_t rem = t / (ht * ct);
-    const int64_t u = t - rem * ht * ct;
-    const int64_t h0 = (u / ct) * 32, c0 = (u % ct) * 32;
+__device__ __forceinline__ void pack_tile(const PackJob& j, int64_t t, float (*tile)[kTile + 1]) {
+    const int64_t rpo = j.rows_per_op < j.rows ? j.rows_per_op : j.rows;
+    const int64_t hrows = rpo / j.rdiv;
+    const int64_t ht = (hrows + kTile - 1) / kTile, ct = (j.cols + kTile - 1) / kTile;
+    const int64_t per_group = int64_t(j.rdiv) * ht * ct;
+    const int64_t g = t / per_group;
+    const int64_t u0 = t - g * per_group;
+    const int64_t rem = u0 / (ht * ct);
+    const int64_t u = u0 - rem * ht * ct;
+    const int64_t h0 = (u / ct) * kTile, c0 = (u % ct) * kTile;
+    const float* src = static_cast<const float*>(j.src) + j.src_off + g * j.s_op + rem * j.s_r_lo;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 warps
+    float v[16];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int64_t c = c0 + ty + 8 * q, hr = h0 + tx;
-        double v = 0.0;
-        if (c < j.cols && hr < hrows) {
-            const int64_t src = j.src_off + hr + rem * j.s_r_lo + c * j.s_c;
-            v = j.src_f64 ? static_cast<const double*>(j.src)[src]
-                          : double(static_cast<const float*>(j.src)[src]);
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int64_t c = c0 + ty + 8 * q, hr = h0 + tx + 32 * hh;
+            v[2 * q + hh] = (c < j.cols && hr < hrows) ? src[hr + c * j.s_c] : 0.f;
         }
-        tile[ty + 8 * q][tx] = v;
-    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) tile[ty + 8 * q][tx + 32 * hh] = v[2 * q + hh];
     __syncthreads();
+    const int64_t c = c0 + 2 * tx;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int64_t hr = h0 + ty + 8 * q, c = c0 + tx;
-        if (c < j.cols && hr < hrows) {
-            const int64_t r = hr * j.rdiv + rem;
-            if (j.src_f64) pack_store(j, r * j.ld + c, tile[tx][ty + 8 * q]);
-            else pack_store(j, r * j.ld + c, float(tile[tx][ty + 8 * q]));
-        }
+    for (int q = 0; q < 8; ++q) {
+        const int64_t hr = h0 + ty + 8 * q;
+        if (hr >= hrows || c >= j.cols) continue;
+        const int64_t dst = (g * rpo + hr * j.rdiv + rem) * j.ld + c;
+        const float x0 = tile[2 * tx][ty + 8 * q];
+        if (c + 1 < j.cols) pack_store2(j, dst, x0, tile[2 * tx + 1][ty + 8 * q]);
+        else pack_store(j, dst, x0);
     }
 }
 
@@ -473,7 +497,7 @@ __device__ __forceinline__ void pack_tile(const PackJob& j, int64_t t, double (*
 // gathers placed first run alongside the bandwidth-bound contiguous job instead of
 // after it.
 __global__ void __launch_bounds__(kPackThreads) pack_mixed_kernel(const __grid_constant__ PackLaunch L) {
-    __shared__ double tile[32][33];
+    __shared__ float tile[kTile][kTile + 1];
     const int b = blockIdx.x;
     int k = 0;
     for (int i = 1; i < L.njobs; ++i)
@@ -507,15 +531,21 @@ __global__ void __launch_bounds__(kPackThreads) pack_mixed_kernel(const __grid_c
     }
 }
 
+// FP32 sources in groups of rows_per_op rows at source stride s_op (no offset table),
+// whole groups only; even destination strides (pair stores).
 bool pack_tiled_ok(const PackJob& j) {
-    const bool single_group = (j.rows_per_op >= j.rows) && j.op_off == nullptr;
-    return single_group && j.s_r_hi == 1 && j.s_c != 1 && j.rdiv >= 1 && (j.rows % j.rdiv) == 0 &&
-           j.cols >= 8;
+    const int64_t rpo = j.rows_per_op < j.rows ? j.rows_per_op : j.rows;
+    const bool aligned = (j.ld % 2) == 0 && (reinterpret_cast<uintptr_t>(j.dst0) % 8) == 0 &&
+                         (j.dst1 == nullptr || (reinterpret_cast<uintptr_t>(j.dst1) % 4) == 0);
+    return !j.src_f64 && j.op_off == nullptr && rpo > 0 && (j.rows % rpo) == 0 && j.s_r_hi == 1 &&
+           j.s_c != 1 && j.rdiv >= 1 && (rpo % j.rdiv) == 0 && j.cols >= 8 && aligned;
 }
 
 int64_t pack_tiles_host(const PackJob& j) {
-    const int64_t hrows = j.rows / j.rdiv;
-    return int64_t(j.rdiv) * ((hrows + 31) / 32) * ((j.cols + 31) / 32);
+    const int64_t rpo = j.rows_per_op < j.rows ? j.rows_per_op : j.rows;
+    const int64_t hrows = rpo / j.rdiv;
+    return (j.rows / rpo) * int64_t(j.rdiv) * ((hrows + kTile - 1) / kTile) *
+           ((j.cols + kTile - 1) / kTile);
 }
 
 bool pack_vec8_ok(const PackJob& j) {
@@ -602,7 +632,7 @@ int64_t pack_blocks_for(const PackJob& j) {
 
 cudaError_t pack_launch(const PackJob* jobs, int njobs, PackJob* /*unused*/, cudaStream_t s) {
     if (njobs <= 0) return cudaSuccess;
-    if (njobs > 4) return cudaErrorInvalidValue;
+    if (njobs > kMaxPackJobs) return cudaErrorInvalidValue;
     PackLaunch L{};
     int64_t blocks = 0;
     int n = 0;

@@ -52,6 +52,13 @@ __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float(r);
 }
 
+// out[0..3] += v0..v3 as one relaxed, GPU-scope vector reduction (16-byte aligned).
+__device__ __forceinline__ void red_add_v4(float* out, float v0, float v1, float v2, float v3) {
+    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(out), "f"(v0),
+                 "f"(v1), "f"(v2), "f"(v3)
+                 : "memory");
+}
+
 // Stores one 32-column chunk of a finished accumulator row through scatter map S
 // (row_base already includes the row part of the map).  r[] is indexed with
 // constants only, so it stays in registers.
@@ -89,18 +96,26 @@ __device__ __forceinline__ void store_chunk(const TcLaunch& L, const uint32_t (&
                 pl[(j >> 2) * step] = make_uint2(lw[0], lw[1]);
             }
         } else {
-            // r[] is indexed with constants only (full unroll), so it stays
-            // in registers
+            // r[] is indexed with constants only (full unroll), so it stays in
+            // registers; the scatter index advances column by column (one division
+            // per chunk)
+            const int n = n0 + c;
+            int rem = n % cdiv;
+            int64_t idx = row_base + int64_t(n / cdiv) * sch + int64_t(rem) * scl;
+            const int64_t wrap = sch - int64_t(cdiv - 1) * scl;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 if (j < cmax) {
-                    const int n = n0 + c + j;
-                    const int64_t idx = row_base + int64_t(n / cdiv) * sch +
-                                        int64_t(n % cdiv) * scl;
                     const float v = __uint_as_float(r[j]);
                     const __nv_bfloat16 h = __float2bfloat16_rn(v);
                     hi[idx] = h;
                     lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+                }
+                if (++rem == cdiv) {
+                    rem = 0;
+                    idx += wrap;
+                } else {
+                    idx += scl;
                 }
             }
         }
@@ -142,6 +157,14 @@ __device__ __forceinline__ void store_chunk(const TcLaunch& L, const uint32_t (&
                 }
                 o4[j >> 2] = v;
             }
+        } else if (atom && cdiv == 1 && sch == 1 && cmax == 32 &&
+                   ((reinterpret_cast<uintptr_t>(out + row_base + n0 + c) & 15) == 0)) {
+            // a contiguous row segment accumulated with 16-byte vector reductions
+            float* p = out + row_base + n0 + c;
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+                red_add_v4(p + j, __uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                           __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
         } else if (cdiv == 1) {
             // one stride per column (the transposed store of the second product):
             // lanes hold consecutive rows, so each store instruction is coalesced
@@ -155,16 +178,23 @@ __device__ __forceinline__ void store_chunk(const TcLaunch& L, const uint32_t (&
                 }
             }
         } else {
+            const int n = n0 + c;
+            int rem = n % cdiv;
+            int64_t idx = row_base + int64_t(n / cdiv) * sch + int64_t(rem) * scl;
+            const int64_t wrap = sch - int64_t(cdiv - 1) * scl;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 if (j < cmax) {
-                    const int n = n0 + c + j;
-                    const int64_t idx = row_base + int64_t(n / cdiv) * sch +
-                                        int64_t(n % cdiv) * scl;
                     const float v = __uint_as_float(r[j]);
                     if (atom) atomicAdd(out + idx, v);
                     else if (EPI == EPI_TF32) out[idx] = tf32_round(v);
                     else out[idx] = v;
+                }
+                if (++rem == cdiv) {
+                    rem = 0;
+                    idx += wrap;
+                } else {
+                    idx += scl;
                 }
             }
         }

@@ -400,8 +400,10 @@ cudaError_t tc_gemm_launch_pair(TcMode mode, TcEpi epi, const TcLaunch& L, int s
                                       : launch_pair<M, E, 1>(L, stages, grid, bh, smem, s);
     DMRG_TC_CASE(TC_BF16X3, EPI_SPLIT_BF16)
     DMRG_TC_CASE(TC_BF16X3, EPI_F32)
+    DMRG_TC_CASE(TC_BF16X3, EPI_F32_ATOMIC)
     DMRG_TC_CASE(TC_TF32, EPI_TF32)
     DMRG_TC_CASE(TC_TF32, EPI_F32)
+    DMRG_TC_CASE(TC_TF32, EPI_F32_ATOMIC)
 #undef DMRG_TC_CASE
     return cudaErrorNotSupported;
 }
