@@ -257,6 +257,19 @@ dmrg_status build_plan(dmrg_blocked_plan_s& pl) {
     return DMRG_OK;
 }
 
+// Tiling of one grouped plain-FMA problem: blocks of small outputs go one warp per
+// operator (8 operators per CTA), the others 64 x 64 tiles per operator.
+void set_simt_tiles(SimtGemm& g) {
+    g.small = (g.M <= kSimtSmall && g.N <= kSimtSmall && !g.reduce_batch) ? 1 : 0;
+    g.tiles_m = int((g.M + simt_tile_m() - 1) / simt_tile_m());
+    g.tiles_n = int((g.N + simt_tile_n() - 1) / simt_tile_n());
+}
+
+int simt_tile_count(const SimtGemm& g) {
+    if (g.small) return (g.batch + kSimtSmallPerBlock - 1) / kSimtSmallPerBlock;
+    return g.tiles_m * g.tiles_n * g.batch;
+}
+
 // Device arena: class offset arrays, grouped plain-FMA problem tables and the pack-job
 // table (all element offsets, independent of the caller's pointers).
 dmrg_status upload_static(dmrg_blocked_plan_s& pl) {
@@ -274,10 +287,9 @@ dmrg_status upload_static(dmrg_blocked_plan_s& pl) {
         g.C = reinterpret_cast<void*>(intptr_t(pl.simt_T_off[f.p2] + pl.segoff[size_t(f.Q2) * d + f.s] * pl.km[f.Q]));
         g.c_sel = 2; g.sCb = pl.D[f.Q2] * pl.km[f.Q]; g.sCi = pl.km[f.Q]; g.sCj = 1;
         g.batch = int32_t(cl.ops.size());
-        g.tiles_m = int((g.M + simt_tile_m() - 1) / simt_tile_m());
-        g.tiles_n = int((g.N + simt_tile_n() - 1) / simt_tile_n());
+        set_simt_tiles(g);
         g.tile_start = tiles;
-        tiles += g.tiles_m * g.tiles_n * g.batch;
+        tiles += simt_tile_count(g);
         pl.simt_first_h.push_back(g);
     }
     pl.simt_tiles_first = tiles;
@@ -294,10 +306,9 @@ dmrg_status upload_static(dmrg_blocked_plan_s& pl) {
         g.C = reinterpret_cast<void*>(intptr_t(cl.out_local[p.Q]));
         g.c_sel = 3; g.sCi = pl.km[p.Q]; g.sCj = 1;
         g.batch = int32_t(cl.ops.size());
-        g.tiles_m = int((g.M + simt_tile_m() - 1) / simt_tile_m());
-        g.tiles_n = int((g.N + simt_tile_n() - 1) / simt_tile_n());
+        set_simt_tiles(g);
         g.tile_start = tiles;
-        tiles += g.tiles_m * g.tiles_n * g.batch;
+        tiles += simt_tile_count(g);
         pl.simt_second_h.push_back(g);
     }
     pl.simt_tiles_second = tiles;

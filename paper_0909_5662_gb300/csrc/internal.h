@@ -31,7 +31,8 @@ struct SimtGemm {
     // Grouped launches: A, B and C hold element offsets from bases[a_sel / b_sel / c_sel]
     // of the launch (sel < 0: absolute pointers); a_boff / c_boff, when set, give the
     // element offset of each batch entry instead of b * sAb / b * sCb.
-    int32_t a_sel, b_sel, c_sel, pad;
+    int32_t a_sel, b_sel, c_sel;
+    int32_t small;        // grouped launches: M, N <= 32, one warp per batch entry, 8 per block
     const int64_t* a_boff;
     const int64_t* c_boff;
 };
@@ -42,6 +43,10 @@ enum class Real { F64, F32 };
 cudaError_t simt_gemm_launch(Real t, const SimtGemm& g, cudaStream_t s);
 cudaError_t simt_gemm_grouped_launch(Real t, const SimtGemm* d_problems, int nprob,
                                      int total_tiles, const void* const bases[4], cudaStream_t s);
+// Grouped problems with M, N <= kSimtSmall and no batch reduction take the small path
+// (set SimtGemm::small and count ceil(batch / kSimtSmallPerBlock) tiles).
+constexpr int kSimtSmall = 32;
+constexpr int kSimtSmallPerBlock = 8;
 int simt_tile_m();
 int simt_tile_n();
 

@@ -142,6 +142,27 @@ __global__ void __launch_bounds__(NT) simt_gemm_grouped_kernel(const SimtGemm* _
     g.B = rebase(g.B, g.b_sel);
     g.C = const_cast<void*>(rebase(g.C, g.c_sel));
     const int64_t local = t - g.tile_start;
+    if (g.small) {
+        // one warp per batch entry: lanes stride over the (at most 32 x 32) outputs,
+        // operands read through L1 (tiny blocks, no shared-memory staging)
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int64_t b = local * kSimtSmallPerBlock + warp;
+        if (b >= g.batch) return;
+        const T* A = static_cast<const T*>(g.A) + (g.a_boff ? g.a_boff[b] : b * g.sAb);
+        const T* B = static_cast<const T*>(g.B) + b * g.sBb;
+        T* C = static_cast<T*>(g.C) + (g.c_boff ? g.c_boff[b] : b * g.sCb);
+        const int n = int(g.N);
+        for (int e = lane; e < int(g.M) * n; e += 32) {
+            const int i = e / n, j = e - (e / n) * n;
+            const T* a = A + i * g.sAi;
+            const T* bp = B + j * g.sBj;
+            T acc = T(0);
+            for (int64_t k = 0; k < g.K; ++k) acc = fma(a[k * g.sAk], bp[k * g.sBk], acc);
+            T* dst = C + i * g.sCi + j * g.sCj;
+            *dst = g.accumulate ? (*dst + acc) : acc;
+        }
+        return;
+    }
     const int64_t per_b = int64_t(g.tiles_m) * g.tiles_n;
     const int64_t b = local / per_b;
     const int64_t r = local % per_b;
