@@ -24,6 +24,8 @@ from .oracle import (  # noqa: F401
     num_threads,
     rotate_dense,
     rotate_dense_kron,
+    rotate_site,
+    rotate_site_kron,
     orthonormality_error,
     correlations,
     rotate_backward,

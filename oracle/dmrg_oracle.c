@@ -119,6 +119,68 @@ int oracle_rotate_dense(const double* U, const double* O, double* Oout,
     return fail;
 }
 
+/* Blocked site and cross operators, then rotated (Sec. 2, the blocking that follows
+ * step 5 -- operators acting on the added site, and products of a block operator
+ * with a site operator, are written in the [B a] basis before R Z R^+ -- and the
+ * "blocking" task (ii) of Sec. 3.2):
+ *
+ *   Z_k = (A_k P^{f_k}) (x) S_{c(k)},   O'_k = U^T Z_k U,
+ *
+ * where P = diag(parity) is the block's fermion parity (-1)^{N_B}: with the
+ * Jordan-Wigner order block modes before the site's, a fermion operator of the
+ * added site carries the string P on the block, and f = 1 for operators that are
+ * odd on the site.  The operators come in n_class consecutive classes: class c
+ * has counts[c] operators, site matrix S + c*d*d (d x d, row-major) and parity
+ * flag flags[c].  A: K x m x m, U: (m*d) x mp, parity: m entries (+1/-1; unused
+ * when every flag is 0).  Literal loops in the paper's order: T = Z U, then
+ * O' = U^T T.  Returns 0 on success. */
+int oracle_rotate_site(const double* U, const double* A, const double* S, const int64_t* counts,
+                       const int32_t* flags, int n_class, const double* parity, double* Oout,
+                       int64_t m, int d, int64_t mp, int64_t K) {
+    if (m <= 0 || d <= 0 || mp <= 0 || K < 0 || n_class < 0) return 1;
+    const int64_t md = m * d;
+    double* T = (double*)malloc(sizeof(double) * (size_t)(md * mp));
+    if (!T) return 1;
+    int64_t k = 0;
+    for (int c = 0; c < n_class; ++c) {
+        const double* Sc = S + (int64_t)c * d * d;
+        for (int64_t q = 0; q < counts[c]; ++q, ++k) {
+            if (k >= K) { free(T); return 1; }
+            const double* Ak = A + k * m * m;
+            /* T[(i,s)][b] = sum_{j,t} A[i][j] P[j]^f S[s][t] U[(j,t)][b] */
+            for (int64_t i = 0; i < m; ++i)
+                for (int s = 0; s < d; ++s) {
+                    double* Trow = T + (i * d + s) * mp;
+                    for (int64_t b = 0; b < mp; ++b) Trow[b] = 0.0;
+                    for (int64_t j = 0; j < m; ++j) {
+                        const double a = Ak[i * m + j] * (flags[c] ? parity[j] : 1.0);
+                        if (a == 0.0) continue;
+                        for (int t = 0; t < d; ++t) {
+                            const double z = a * Sc[s * d + t];
+                            if (z == 0.0) continue;
+                            const double* Urow = U + (j * d + t) * mp;
+                            for (int64_t b = 0; b < mp; ++b) Trow[b] += z * Urow[b];
+                        }
+                    }
+                }
+            /* O'[a][b] = sum_r U[r][a] T[r][b] */
+            double* Ok = Oout + k * mp * mp;
+            for (int64_t x = 0; x < mp * mp; ++x) Ok[x] = 0.0;
+            for (int64_t r = 0; r < md; ++r) {
+                const double* Trow = T + r * mp;
+                for (int64_t a = 0; a < mp; ++a) {
+                    const double u = U[r * mp + a];
+                    if (u == 0.0) continue;
+                    double* orow = Ok + a * mp;
+                    for (int64_t b = 0; b < mp; ++b) orow[b] += u * Trow[b];
+                }
+            }
+        }
+    }
+    free(T);
+    return k == K ? 0 : 1;
+}
+
 /* ||U^T U - I||_F in FP64 (U needs orthonormal columns: B is only
  * approximately complete, Sec. 2; the kept |w_alpha> are orthonormal). */
 double oracle_orthonormality_error(const double* U, int64_t rows, int64_t mp) {

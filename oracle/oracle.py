@@ -72,6 +72,10 @@ def _load():
             ctypes.c_int, _i32p, _i32p, _i64p, ctypes.c_int64, _i32p, _i32p,
             _f64p, _f64p, _f64p]
         lib.oracle_rotate_blocked.restype = ctypes.c_int
+        lib.oracle_rotate_site.argtypes = [_f64p, _f64p, _f64p, _i64p, _i32p, ctypes.c_int, _f64p,
+                                           _f64p, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
+                                           ctypes.c_int64]
+        lib.oracle_rotate_site.restype = ctypes.c_int
         lib.oracle_num_threads.argtypes = []
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
@@ -123,6 +127,47 @@ def rotate_dense_kron(U, O, d: int) -> np.ndarray:
     out = np.stack([U.T @ (np.kron(Ok, eye) @ U) for Ok in O]) if len(O) else \
         np.zeros((0, U.shape[1], U.shape[1]))
     return out[0] if squeeze else out
+
+
+def rotate_site(U, A, d: int, S, counts, flags, parity=None) -> np.ndarray:
+    """Blocked site and cross operators, rotated (Sec. 2, blocking after step 5):
+    O'_k = U^T ((A_k P^{f_c}) (x) S_c) U for the operators of class c.
+
+    A: K x m x m; S: n_class x d x d; counts: operators per class (in order, summing
+    to K); flags: 1 where the class carries the block parity P = diag(parity)."""
+    U = _c(U, np.float64)
+    A = _c(A, np.float64)
+    S = _c(np.asarray(S, dtype=np.float64).reshape(-1, d, d), np.float64)
+    counts = _c(np.asarray(counts, dtype=np.int64).reshape(-1), np.int64)
+    flags = _c(np.asarray(flags, dtype=np.int32).reshape(-1), np.int32)
+    K, m, m2 = A.shape
+    assert m == m2 and U.shape[0] == m * d and len(counts) == len(flags) == len(S)
+    par = _c(np.ones(m) if parity is None else np.asarray(parity, dtype=np.float64), np.float64)
+    mp = U.shape[1]
+    out = np.empty((K, mp, mp), dtype=np.float64)
+    rc = _load().oracle_rotate_site(_p(U, _f64p), _p(A, _f64p), _p(S, _f64p), _p(counts, _i64p),
+                                    _p(flags, _i32p), len(counts), _p(par, _f64p), _p(out, _f64p),
+                                    m, d, mp, K)
+    if rc:
+        raise RuntimeError("oracle_rotate_site failed")
+    return out
+
+
+def rotate_site_kron(U, A, d: int, S, counts, flags, parity=None) -> np.ndarray:
+    """Second route: build kron(A_k P^f, S_c) explicitly and form U^T Z U with
+    library matmuls.  Small sizes only."""
+    U = np.asarray(U, dtype=np.float64)
+    A = np.asarray(A, dtype=np.float64)
+    S = np.asarray(S, dtype=np.float64).reshape(-1, d, d)
+    m = A.shape[1]
+    P = np.diag(np.ones(m) if parity is None else np.asarray(parity, dtype=np.float64))
+    out, k = [], 0
+    for c, n in enumerate(counts):
+        for _ in range(int(n)):
+            Ak = A[k] @ P if flags[c] else A[k]
+            out.append(U.T @ np.kron(Ak, S[c]) @ U)
+            k += 1
+    return np.stack(out) if out else np.zeros((0, U.shape[1], U.shape[1]))
 
 
 def orthonormality_error(U) -> float:

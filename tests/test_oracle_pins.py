@@ -374,3 +374,70 @@ def test_sector_split_histograms():
     assert sum(n for *_, n in s4) == 1000 and sum(n for *_, n in s12) == 1000
     assert len(s4) == 311 and min(n for *_, n in s4) == 1 and max(n for *_, n in s4) == 10
     assert len(s12) == 45 and min(n for *_, n in s12) == 1 and max(n for *_, n in s12) == 111
+
+
+# ---------------------------------------------------------------- blocked site operators
+def _site_4chain(mp):
+    """4-site Hubbard chain (t = 1, U/t = 8, open): block = sites 1-3, added site 4.
+    Returns U (lowest mp eigenvectors), block annihilators, local annihilators, the
+    block parity (-1)^{N_B} and the full-space annihilators."""
+    cb = jw.annihilators(3)
+    cl = jw.annihilators(1)                       # d = 4 local operators, local signs
+    cf = jw.annihilators(4)
+    H = jw.hubbard_hamiltonian(4, 1.0, 8.0, cf)
+    _, V = np.linalg.eigh(H)
+    nb = sum(cb[p].T @ cb[p] for p in range(6))
+    parity = np.where(np.round(np.diag(nb)).astype(int) % 2 == 0, 1.0, -1.0)
+    return np.ascontiguousarray(V[:, :mp]), cb, cl, parity, cf
+
+
+@pytest.mark.parametrize("mp", [64, 256])
+def test_site_operators_bruteforce(oracle_lib, mp):
+    # Operators of the added site and block x site products, blocked with the
+    # Jordan-Wigner string on the block (block modes first), must equal the
+    # full-space matrix elements <u_a| O_full |u_b> -- built independently on all
+    # 8 modes, exact even with truncation.
+    U, cb, cl, parity, cf = _site_4chain(mp)
+    I64 = np.eye(64)
+    classes = []   # (S, flag, [(A, full operator)])
+    for s in range(2):
+        # c_4s = P_B (x) c_s;  c+_is c_4s = (c+_is P_B) (x) c_s
+        classes.append((cl[s], 1, [(I64, cf[6 + s]),
+                                   (cb[s].T, cf[s].T @ cf[6 + s]),
+                                   (cb[4 + s].T, cf[4 + s].T @ cf[6 + s])]))
+        # c+_4s = P_B (x) c_s^T;  c+_4s c_2s = (P_B c_2s) (x) c_s^T = (-c_2s P_B) (x) c_s^T
+        classes.append((cl[s].T, 1, [(I64, cf[6 + s].T),
+                                     (-cb[2 + s], cf[6 + s].T @ cf[2 + s])]))
+    n_loc = cl[0].T @ cl[0] + cl[1].T @ cl[1]
+    classes.append((n_loc, 0, [(I64, cf[6].T @ cf[6] + cf[7].T @ cf[7]),              # n_4
+                               (cb[0].T @ cb[0], (cf[0].T @ cf[0]) @ (cf[6].T @ cf[6] + cf[7].T @ cf[7]))]))
+    A = np.stack([a for _, _, ops in classes for a, _ in ops])
+    S = np.stack([c[0] for c in classes])
+    counts = [len(c[2]) for c in classes]
+    flags = [c[1] for c in classes]
+    out = oracle_lib.rotate_site(U, A, 4, S, counts, flags, parity)
+    full = [f for _, _, ops in classes for _, f in ops]
+    for k in range(len(full)):
+        assert np.abs(out[k] - U.T @ full[k] @ U).max() < 1e-12, k
+
+
+def test_site_operators_reduce_and_second_route(oracle_lib):
+    rng = np.random.default_rng(31)
+    m, d, mp, K = 7, 3, 12, 5
+    U = orthonormal_columns(rng, m * d, mp)
+    A = rng.standard_normal((K, m, m))
+    # S = I without parity is the plain block rotation
+    got = oracle_lib.rotate_site(U, A, d, np.eye(d)[None], [K], [0])
+    assert np.abs(got - oracle_lib.rotate_dense(U, A, d)).max() < 1e-12
+    # random classes against the explicit kron route
+    S = rng.standard_normal((3, d, d))
+    par = rng.choice([-1.0, 1.0], m)
+    counts, flags = [2, 0, 3], [1, 0, 0]
+    a = oracle_lib.rotate_site(U, A, d, S, counts, flags, par)
+    b = oracle_lib.rotate_site_kron(U, A, d, S, counts, flags, par)
+    assert np.abs(a - b).max() < 1e-12
+    # parity flag: (A P) (x) S = (A (x) S)(P (x) I)
+    a1 = oracle_lib.rotate_site(U, A[:1], d, S[:1], [1], [1], par)
+    ref = U.T @ np.kron(A[0], S[0]) @ np.kron(np.diag(par), np.eye(d)) @ U
+    assert np.abs(a1[0] - ref).max() < 1e-12
+
