@@ -271,6 +271,44 @@ DMRG_API dmrg_status dmrg_rotate_ops_blocked(dmrg_handle handle, dmrg_blocked_pl
                                     size_t ws_bytes, dmrg_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Blocked site and cross operators (Sec. 2, the blocking of operators into the
+ * [B a] basis that follows step 5; task ii of the rotation step in Sec. 3.2).
+ *
+ * Operators acting on the added site, and products of a block operator with a
+ * site operator, are written in [B a] as Z_k = (A_k P^f) (x) S, where S is a
+ * d x d site matrix and P = diag(parity) the block's fermion parity (-1)^{N_B}:
+ * with the Jordan-Wigner order block modes before the site's, a fermion operator
+ * of the added site carries that string on the block.  This call rotates them:
+ *
+ *     O'_k = U^T ((A_k P^{f_c}) (x) S_c) U
+ *
+ * The K operators come in n_class consecutive classes: class c has counts[c]
+ * operators, site matrix S + c*d*d and parity flag flags[c] (0 or 1).
+ *
+ *   U       device, (m*d) x mp FP64, row-major, orthonormal columns.
+ *   A       device, K x m x m, FP64 (in_is_fp64 = 1) or FP32, row-major.
+ *   S       HOST, n_class x d x d FP64 (copied into kernel arguments; d <= 8).
+ *   counts  HOST, n_class entries >= 0 summing to K.
+ *   flags   HOST, n_class entries in {0, 1}.
+ *   parity  device, m entries of +1 / -1 (signed char); may be NULL when every
+ *           flag is 0.
+ *   Oout    device, K x mp x mp: FP64 for DMRG_PREC_FP64, else FP32.
+ * Errors: DMRG_ERR_INVALID_ARG for NULL pointers, counts not summing to K, a flag
+ * outside {0, 1} or a set flag without parity; DMRG_ERR_SHAPE as for
+ * dmrg_rotate_ops or d > 8; DMRG_ERR_WORKSPACE when ws_bytes is too small.  With
+ * every S = I and every flag 0 the result equals dmrg_rotate_ops.  Not captured
+ * into CUDA graphs (S, counts and flags are host data of the call).
+ * ------------------------------------------------------------------------ */
+DMRG_API dmrg_status dmrg_rotate_site_ops_workspace(dmrg_handle handle, int64_t K, int64_t m, int d,
+                                           int64_t mp, dmrg_precision precision, size_t* bytes);
+DMRG_API dmrg_status dmrg_rotate_site_ops(dmrg_handle handle, const double* U, int64_t m, int d,
+                                 int64_t mp, const void* A, int in_is_fp64, int64_t K,
+                                 int n_class, const double* S, const int64_t* counts,
+                                 const int32_t* flags, const signed char* parity, void* Oout,
+                                 dmrg_precision precision, void* ws, size_t ws_bytes,
+                                 dmrg_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Dense rotation without any allocation (the paper has no counterpart; this
  * entry point exists for callers of the library, not for the method).
  *

@@ -16,6 +16,7 @@ from .api import (  # noqa: F401
     dmrg_rotate_ops_host,
     dmrg_autotune_rotate_ops,
     dmrg_rotate_ops_backward,
+    dmrg_rotate_site_ops,
     dmrg_orthonormality_error,
     dmrg_correlations,
     dmrg_set_option,

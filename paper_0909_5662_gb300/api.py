@@ -5,6 +5,7 @@ import ctypes
 import json
 from typing import Optional, Sequence, Tuple
 
+import numpy as np
 import torch
 
 from . import _capi
@@ -226,6 +227,39 @@ def dmrg_rotate_ops_backward(U: torch.Tensor, O: torch.Tensor, G: torch.Tensor, 
         h.h, _ptr(U), m, d, mp, _ptr(O), _ptr(G), int(O.dtype == torch.float64), K, _ptr(dO),
         _ptr(dU), p, _ptr(ws), ws.numel(), _stream(stream)), h.h, "dmrg_rotate_ops_backward")
     return dO, dU
+
+
+def dmrg_rotate_site_ops(U: torch.Tensor, A: torch.Tensor, d: int, S, counts, flags,
+                         parity: Optional[torch.Tensor] = None, precision="bf16x3",
+                         out: Optional[torch.Tensor] = None, handle: Optional[Handle] = None,
+                         stream=None) -> torch.Tensor:
+    """Blocked site and cross operators: O'_k = U^T ((A_k P^f_c) (x) S_c) U.
+
+    A: K x m x m on the device (operators ordered by class); S: n_class x d x d site
+    matrices (host data, any array-like); counts / flags: per class, host; parity:
+    m entries of +-1 (int8) on the device, needed when a flag is set."""
+    h = handle or default_handle()
+    K, m, mp, p = _dense_args(U, A, d, precision)
+    S_np = np.ascontiguousarray(np.asarray(S, dtype=np.float64).reshape(-1, d, d))
+    counts_np = np.ascontiguousarray(np.asarray(counts, dtype=np.int64).reshape(-1))
+    flags_np = np.ascontiguousarray(np.asarray(flags, dtype=np.int32).reshape(-1))
+    if not (len(S_np) == len(counts_np) == len(flags_np)):
+        raise ValueError("S, counts and flags need one entry per class")
+    if parity is not None:
+        _need(parity, "parity", (torch.int8,), 1)
+    odt = torch.float64 if p == 0 else torch.float32
+    if out is None:
+        out = torch.empty((K, mp, mp), dtype=odt, device=A.device)
+    n = ctypes.c_size_t()
+    _capi.check(h.lib.dmrg_rotate_site_ops_workspace(h.h, K, m, d, mp, p, ctypes.byref(n)),
+                h.h, "dmrg_rotate_site_ops_workspace")
+    ws = h.workspace(n.value)
+    _capi.check(h.lib.dmrg_rotate_site_ops(
+        h.h, _ptr(U), m, d, mp, _ptr(A), int(A.dtype == torch.float64), K, len(counts_np),
+        S_np.ctypes.data_as(ctypes.c_void_p), counts_np.ctypes.data_as(ctypes.c_void_p),
+        flags_np.ctypes.data_as(ctypes.c_void_p), _ptr(parity) if parity is not None else None,
+        _ptr(out), p, _ptr(ws), ws.numel(), _stream(stream)), h.h, "dmrg_rotate_site_ops")
+    return out
 
 
 def dmrg_orthonormality_error(U: torch.Tensor, handle: Optional[Handle] = None, stream=None

@@ -181,7 +181,7 @@ std::string shape_key(const char* tag, int64_t K, int64_t m, int d, int64_t mp, 
 dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
                              const void* O, int in_is_fp64, int64_t K, void* Oout,
                              dmrg_precision p, void* ws, const TcConfig& c1, const TcConfig& c2,
-                             cudaStream_t s, bool pack_u) {
+                             cudaStream_t s, bool pack_u, const double* U1) {
     const DenseDims D = dense_dims(K, m, d, mp, p);
     const bool split = (p == DMRG_PREC_BF16X3);
     const TcMode mode = split ? TC_BF16X3 : TC_TF32;
@@ -206,7 +206,7 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     jo.rdiv = 1; jo.s_r_hi = m; jo.s_r_lo = 0; jo.s_c = 1;
     jo.dst0 = Op[0]; jo.dst1 = Op[1]; jo.ld = D.ld1;
     PackJob& j1 = jobs[1];
-    j1.src = U; j1.src_f64 = 1; j1.mode = pmode;
+    j1.src = U1 ? U1 : U; j1.src_f64 = 1; j1.mode = pmode;
     j1.rows = int64_t(d) * mp; j1.cols = m; j1.rows_per_op = j1.rows;
     j1.rdiv = d; j1.s_r_hi = 1; j1.s_r_lo = mp; j1.s_c = int64_t(d) * mp;
     j1.dst0 = B1[0]; j1.dst1 = B1[1]; j1.ld = D.ld1;
@@ -320,12 +320,14 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
 
 dmrg_status dense_simt_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
                                const void* O, int in_is_fp64, int64_t K, void* Oout,
-                               dmrg_precision p, void* ws, cudaStream_t s, bool pack_u) {
+                               dmrg_precision p, void* ws, cudaStream_t s, bool pack_u,
+                               const double* U1, float* U1_32) {
     const DenseDims D = dense_dims(K, m, d, mp, p);
     char* base = static_cast<char*>(ws);
     const bool f64 = (p == DMRG_PREC_FP64);
     const void* Ouse = O;
     const void* Uuse = U;
+    const void* U1use = U1 ? U1 : U;
     void* T = nullptr;
     cudaError_t e = cudaSuccess;
     if (f64) {
@@ -334,7 +336,8 @@ dmrg_status dense_simt_forward(dmrg_handle h, const double* U, int64_t m, int d,
         float* U32 = reinterpret_cast<float*>(base + D.ws.offsets[0]);
         float* O32 = reinterpret_cast<float*>(base + D.ws.offsets[1]);
         T = base + D.ws.offsets[2];
-        PackJob jobs[2] = {};
+        if (U1 && !U1_32) return fail(h, DMRG_ERR_INVALID_ARG, "FP32 path needs a scratch for U1");
+        PackJob jobs[3] = {};
         int nj = 0;
         if (in_is_fp64) {
             PackJob& j = jobs[nj++];
@@ -348,6 +351,13 @@ dmrg_status dense_simt_forward(dmrg_handle h, const double* U, int64_t m, int d,
             j.rdiv = 1; j.s_r_hi = mp; j.s_c = 1; j.dst0 = U32; j.ld = mp;
         }
         Uuse = U32;
+        U1use = U32;
+        if (U1) {
+            PackJob& j = jobs[nj++];
+            j.src = U1; j.src_f64 = 1; j.mode = 2; j.rows = D.md; j.cols = mp; j.rows_per_op = D.md;
+            j.rdiv = 1; j.s_r_hi = mp; j.s_c = 1; j.dst0 = U1_32; j.ld = mp;
+            U1use = U1_32;
+        }
         if (nj > 0) {
             e = timed_launch(h, "convert_fp32", s, [&] { return pack_launch(jobs, nj, nullptr, s); });
             if (e != cudaSuccess) return cuda_fail(h, e, "convert");
@@ -356,7 +366,7 @@ dmrg_status dense_simt_forward(dmrg_handle h, const double* U, int64_t m, int d,
     const Real rt = f64 ? Real::F64 : Real::F32;
     // First product: T_k (m x d*mp) = O_k (m x m) * U_r (m x d*mp).
     SimtGemm g1{};
-    g1.A = Ouse; g1.B = Uuse; g1.C = T;
+    g1.A = Ouse; g1.B = U1use; g1.C = T;
     g1.M = m; g1.N = int64_t(d) * mp; g1.K = m;
     g1.sAb = m * m; g1.sAi = m; g1.sAk = 1;
     g1.sBb = 0; g1.sBk = int64_t(d) * mp; g1.sBj = 1;

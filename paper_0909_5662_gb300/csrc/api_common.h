@@ -39,14 +39,19 @@ TcConfig tuned_config(dmrg_handle h, const std::string& key, TcMode mode);
 void load_tune_file(dmrg_handle h);
 void save_tune_file(dmrg_handle h);
 std::string shape_key(const char* tag, int64_t K, int64_t m, int d, int64_t mp, dmrg_precision p);
+// The dense rotation O'_k = U^T (O_k (x) I_d) U.  With U1 != nullptr the first
+// product uses U1 in place of U, i.e. O'_k = U^T (O_k (x) I_d) U1 (the blocked site
+// operators pass U1 = (P (x) S) U); the FP32 plain-FMA path then needs U1_32, an
+// (m*d) x mp FP32 scratch for U1's conversion.
 dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
                              const void* O, int in_is_fp64, int64_t K, void* Oout,
                              dmrg_precision p, void* ws, const TcConfig& c1, const TcConfig& c2,
-                             cudaStream_t s, bool pack_u = true);
+                             cudaStream_t s, bool pack_u = true, const double* U1 = nullptr);
 
 dmrg_status dense_simt_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
                                const void* O, int in_is_fp64, int64_t K, void* Oout,
-                               dmrg_precision p, void* ws, cudaStream_t s, bool pack_u = true);
+                               dmrg_precision p, void* ws, cudaStream_t s, bool pack_u = true,
+                               const double* U1 = nullptr, float* U1_32 = nullptr);
 
 cudaError_t tc_gemm_launch_grouped(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
                                    int bn_smem, cudaStream_t s);
