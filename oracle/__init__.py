@@ -28,6 +28,9 @@ from .oracle import (  # noqa: F401
     rotate_site_kron,
     orthonormality_error,
     correlations,
+    expectation,
+    cross_correlations,
+    structure_factor,
     rotate_backward,
     rotate_blocked,
     rotate_blocked_assembled,

@@ -181,6 +181,107 @@ int oracle_rotate_site(const double* U, const double* A, const double* S, const 
     return k == K ? 0 : 1;
 }
 
+/* Measurement stage (Sec. 3.2, one- and two-point functions <psi0|Z_i|psi0>,
+ * <psi0|Z_i Z_j|psi0>; Sec. 2, the structure factors).  The superblock ground state
+ * is psi0 = sum_{a,e} Psi[a][e] |a>|e>, system basis a (rows), environment basis e
+ * (cols), Psi row-major.
+ *
+ * oracle_expectation: <Z_k> = <psi0| Z_k (x) I |psi0> (side 0, Z_k rows x rows) or
+ * <psi0| I (x) Z_k |psi0> (side 1, cols x cols), written out over every index.
+ * Returns 0 on success. */
+int oracle_expectation(const double* Z, int64_t K, const double* Psi, int64_t rows, int64_t cols,
+                       int side, double* out) {
+    if (K < 0 || rows <= 0 || cols <= 0 || (side != 0 && side != 1)) return 1;
+    const int64_t n = side == 0 ? rows : cols;
+    for (int64_t k = 0; k < K; ++k) {
+        const double* Zk = Z + k * n * n;
+        double acc = 0.0;
+        if (side == 0) {
+            /* sum_{a,b,e} Psi[a][e] Z[a][b] Psi[b][e] */
+            for (int64_t a = 0; a < rows; ++a)
+                for (int64_t b = 0; b < rows; ++b) {
+                    const double z = Zk[a * rows + b];
+                    if (z == 0.0) continue;
+                    double t = 0.0;
+                    for (int64_t e = 0; e < cols; ++e) t += Psi[a * cols + e] * Psi[b * cols + e];
+                    acc += z * t;
+                }
+        } else {
+            /* sum_{a,e,f} Psi[a][e] Z[e][f] Psi[a][f] */
+            for (int64_t e = 0; e < cols; ++e)
+                for (int64_t f = 0; f < cols; ++f) {
+                    const double z = Zk[e * cols + f];
+                    if (z == 0.0) continue;
+                    double t = 0.0;
+                    for (int64_t a = 0; a < rows; ++a) t += Psi[a * cols + e] * Psi[a * cols + f];
+                    acc += z * t;
+                }
+        }
+        out[k] = acc;
+    }
+    return 0;
+}
+
+/* oracle_cross_correlations: C[i][j] = <psi0| Z_i (x) W_j |psi0>
+ *   = sum_{a,b,e,f} Psi[a][e] Z_i[a][b] W_j[e][f] Psi[b][f],
+ * Z: Ks x rows x rows (system), W: Ke x cols x cols (environment).  The inner sum
+ * over (b, f) is formed once per (i, a, e) as (Z_i Psi W_j^T)[a][e]. */
+int oracle_cross_correlations(const double* Z, int64_t Ks, const double* W, int64_t Ke,
+                              const double* Psi, int64_t rows, int64_t cols, double* C) {
+    if (Ks < 0 || Ke < 0 || rows <= 0 || cols <= 0) return 1;
+    double* Y = (double*)malloc(sizeof(double) * (size_t)(rows * cols));
+    if (!Y) return 1;
+    for (int64_t i = 0; i < Ks; ++i) {
+        const double* Zi = Z + i * rows * rows;
+        /* Y = Z_i Psi */
+        for (int64_t a = 0; a < rows; ++a)
+            for (int64_t f = 0; f < cols; ++f) {
+                double t = 0.0;
+                for (int64_t b = 0; b < rows; ++b) t += Zi[a * rows + b] * Psi[b * cols + f];
+                Y[a * cols + f] = t;
+            }
+        for (int64_t j = 0; j < Ke; ++j) {
+            const double* Wj = W + j * cols * cols;
+            double acc = 0.0;
+            for (int64_t a = 0; a < rows; ++a)
+                for (int64_t e = 0; e < cols; ++e) {
+                    double t = 0.0;
+                    for (int64_t f = 0; f < cols; ++f) t += Wj[e * cols + f] * Y[a * cols + f];
+                    acc += Psi[a * cols + e] * t;
+                }
+            C[i * Ke + j] = acc;
+        }
+    }
+    free(Y);
+    return 0;
+}
+
+/* oracle_structure_factor (Sec. 2, N(q) and S^z(q)):
+ *   F(q_p) = (1/L) sum_{k,j} e^{i q_p (k - j)} <(X_k - c)(X_j - c)>,   q_p = 2 pi p / L,
+ * with G[k][j] = <X_k X_j> and v[k] = <X_k> (v may be NULL when c = 0), so that
+ * <(X_k - c)(X_j - c)> = G[k][j] - c v[k] - c v[j] + c^2.  Writes the real part
+ * Fre[p] and the imaginary part Fim[p] for p = 0 .. L-1. */
+int oracle_structure_factor(const double* G, const double* v, double c, int64_t L, double* Fre,
+                            double* Fim) {
+    if (L <= 0) return 1;
+    const double pi = 3.14159265358979323846;
+    for (int64_t p = 0; p < L; ++p) {
+        const double q = 2.0 * pi * (double)p / (double)L;
+        double re = 0.0, im = 0.0;
+        for (int64_t k = 0; k < L; ++k)
+            for (int64_t j = 0; j < L; ++j) {
+                double x = G[k * L + j];
+                if (v) x += -c * v[k] - c * v[j] + c * c;
+                else x += c * c;
+                re += cos(q * (double)(k - j)) * x;
+                im += sin(q * (double)(k - j)) * x;
+            }
+        Fre[p] = re / (double)L;
+        Fim[p] = im / (double)L;
+    }
+    return 0;
+}
+
 /* ||U^T U - I||_F in FP64 (U needs orthonormal columns: B is only
  * approximately complete, Sec. 2; the kept |w_alpha> are orthonormal). */
 double oracle_orthonormality_error(const double* U, int64_t rows, int64_t mp) {

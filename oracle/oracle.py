@@ -76,6 +76,15 @@ def _load():
                                            _f64p, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
                                            ctypes.c_int64]
         lib.oracle_rotate_site.restype = ctypes.c_int
+        lib.oracle_expectation.argtypes = [_f64p, ctypes.c_int64, _f64p, ctypes.c_int64, ctypes.c_int64,
+                                           ctypes.c_int, _f64p]
+        lib.oracle_expectation.restype = ctypes.c_int
+        lib.oracle_cross_correlations.argtypes = [_f64p, ctypes.c_int64, _f64p, ctypes.c_int64, _f64p,
+                                                  ctypes.c_int64, ctypes.c_int64, _f64p]
+        lib.oracle_cross_correlations.restype = ctypes.c_int
+        lib.oracle_structure_factor.argtypes = [_f64p, _f64p, ctypes.c_double, ctypes.c_int64, _f64p,
+                                                _f64p]
+        lib.oracle_structure_factor.restype = ctypes.c_int
         lib.oracle_num_threads.argtypes = []
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
@@ -168,6 +177,47 @@ def rotate_site_kron(U, A, d: int, S, counts, flags, parity=None) -> np.ndarray:
             out.append(U.T @ np.kron(Ak, S[c]) @ U)
             k += 1
     return np.stack(out) if out else np.zeros((0, U.shape[1], U.shape[1]))
+
+
+def expectation(Z, Psi, side: int = 0) -> np.ndarray:
+    """<psi0| Z_k (x) I |psi0> (side 0) or <psi0| I (x) Z_k |psi0> (side 1) for the
+    superblock state psi0 = sum Psi[a][e] |a>|e> (Sec. 3.2)."""
+    Z = _c(Z, np.float64)
+    Psi = _c(Psi, np.float64)
+    if Z.ndim == 2:
+        Z = Z[None]
+    rows, cols = Psi.shape
+    out = np.empty(len(Z))
+    if _load().oracle_expectation(_p(Z, _f64p), len(Z), _p(Psi, _f64p), rows, cols, int(side),
+                                  _p(out, _f64p)):
+        raise RuntimeError("oracle_expectation failed")
+    return out
+
+
+def cross_correlations(Z, W, Psi) -> np.ndarray:
+    """C[i][j] = <psi0| Z_i (x) W_j |psi0>, Z on the system, W on the environment."""
+    Z = _c(Z, np.float64)
+    W = _c(W, np.float64)
+    Psi = _c(Psi, np.float64)
+    rows, cols = Psi.shape
+    C = np.empty((len(Z), len(W)))
+    if _load().oracle_cross_correlations(_p(Z, _f64p), len(Z), _p(W, _f64p), len(W), _p(Psi, _f64p),
+                                         rows, cols, _p(C, _f64p)):
+        raise RuntimeError("oracle_cross_correlations failed")
+    return C
+
+
+def structure_factor(G, v=None, c: float = 0.0):
+    """F(q_p) = (1/L) sum_{k,j} e^{i q_p (k-j)} <(X_k - c)(X_j - c)>, q_p = 2 pi p / L
+    (Sec. 2, N(q) and S^z(q)); returns (real part, imaginary part)."""
+    G = _c(G, np.float64)
+    L = G.shape[0]
+    vv = None if v is None else _c(v, np.float64)
+    re, im = np.empty(L), np.empty(L)
+    if _load().oracle_structure_factor(_p(G, _f64p), None if vv is None else _p(vv, _f64p), float(c), L,
+                                       _p(re, _f64p), _p(im, _f64p)):
+        raise RuntimeError("oracle_structure_factor failed")
+    return re, im
 
 
 def orthonormality_error(U) -> float:

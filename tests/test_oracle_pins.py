@@ -441,3 +441,74 @@ def test_site_operators_reduce_and_second_route(oracle_lib):
     ref = U.T @ np.kron(A[0], S[0]) @ np.kron(np.diag(par), np.eye(d)) @ U
     assert np.abs(a1[0] - ref).max() < 1e-12
 
+
+
+# ---------------------------------------------------------------- measurement stage
+def _chain_split():
+    """Ground state of the 4-site Hubbard chain (t = 1, U/t = 8) as a 16 x 16 matrix:
+    system = sites 1-2 (rows), environment = sites 3-4 (cols); full-space operators."""
+    cf = jw.annihilators(4)
+    H = jw.hubbard_hamiltonian(4, 1.0, 8.0, cf)
+    w, V = np.linalg.eigh(H)
+    psi = V[:, 0]
+    c2 = jw.annihilators(2)          # the local 2-site operators of either half
+    return psi, psi.reshape(16, 16), cf, c2
+
+
+def _n(c, i):
+    return c[2 * i].T @ c[2 * i] + c[2 * i + 1].T @ c[2 * i + 1]
+
+
+def _sz(c, i):
+    return 0.5 * (c[2 * i].T @ c[2 * i] - c[2 * i + 1].T @ c[2 * i + 1])
+
+
+def test_measurement_bruteforce_hubbard(oracle_lib):
+    # <n_i>, <S^z_i> on both halves and the cross two-point functions <n_i n_j>,
+    # <S^z_i S^z_j> (i in the system, j in the environment) against the full-space
+    # expectation values in the exact ground state.  Number and spin operators are
+    # even, so the environment's operators carry no string from the system.
+    psi, Psi, cf, c2 = _chain_split()
+    sys_ops = [_n(c2, 0), _n(c2, 1), _sz(c2, 0), _sz(c2, 1)]
+    env_ops = sys_ops
+    full_sys = [_n(cf, 0), _n(cf, 1), _sz(cf, 0), _sz(cf, 1)]
+    full_env = [_n(cf, 2), _n(cf, 3), _sz(cf, 2), _sz(cf, 3)]
+    e_sys = oracle_lib.expectation(np.stack(sys_ops), Psi, 0)
+    e_env = oracle_lib.expectation(np.stack(env_ops), Psi, 1)
+    for k in range(4):
+        assert abs(e_sys[k] - psi @ full_sys[k] @ psi) < 1e-12
+        assert abs(e_env[k] - psi @ full_env[k] @ psi) < 1e-12
+    C = oracle_lib.cross_correlations(np.stack(sys_ops), np.stack(env_ops), Psi)
+    for i in range(4):
+        for j in range(4):
+            assert abs(C[i, j] - psi @ full_sys[i] @ full_env[j] @ psi) < 1e-12
+    # the nondegenerate ground state has a definite particle number (2 here) and the
+    # open chain's reflection symmetry: <n_1> = <n_4>, <n_2> = <n_3>
+    total = e_sys[0] + e_sys[1] + e_env[0] + e_env[1]
+    assert abs(total - round(total)) < 1e-10 and round(total) == 2
+    assert abs(e_sys[0] - e_env[1]) < 1e-10 and abs(e_sys[1] - e_env[0]) < 1e-10
+
+
+def test_structure_factor_closed_forms(oracle_lib):
+    L = 12
+    rng = np.random.default_rng(41)
+    X = rng.standard_normal((L, L))
+    G = X + X.T
+    v = rng.standard_normal(L)
+    re, im = oracle_lib.structure_factor(G, v, 0.7)
+    Gc = G - 0.7 * v[:, None] - 0.7 * v[None, :] + 0.49
+    assert abs(re.sum() - np.trace(Gc)) < 1e-10               # sum rule over q
+    assert abs(re[0] - Gc.sum() / L) < 1e-10                   # q = 0: total
+    assert np.abs(im).max() < 1e-10                            # symmetric G: real
+    re0, _ = oracle_lib.structure_factor(np.full((L, L), 0.25), np.full(L, 0.5), 0.5)
+    assert np.abs(re0).max() < 1e-12                           # uncorrelated: zero
+    re1, _ = oracle_lib.structure_factor(np.eye(L))
+    assert np.abs(re1 - 1.0).max() < 1e-12                    # delta correlation: flat
+    p0 = 3
+    k = np.arange(L)
+    Gcos = np.cos(2 * np.pi * p0 * (k[:, None] - k[None, :]) / L)
+    re2, _ = oracle_lib.structure_factor(Gcos)
+    expect = np.zeros(L)
+    expect[p0] += L / 2
+    expect[L - p0] += L / 2
+    assert np.abs(re2 - expect).max() < 1e-10                  # a single wave vector
