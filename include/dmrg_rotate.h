@@ -271,6 +271,53 @@ DMRG_API dmrg_status dmrg_rotate_ops_blocked(dmrg_handle handle, dmrg_blocked_pl
                                     size_t ws_bytes, dmrg_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Measurement stage (Sec. 3.2: one- and two-point functions <psi0|Z_i|psi0>,
+ * <psi0|Z_i Z_j|psi0>; Sec. 2: the structure factors N(q), S^z(q)).
+ *
+ * The superblock ground state psi0 = sum_{a,e} Psi[a][e] |a>|e> is a rows x cols
+ * FP64 matrix on the device: system basis a (rows), environment basis e (cols).
+ * All results are FP64.
+ * ------------------------------------------------------------------------ */
+
+/* <Z_k> = <psi0| Z_k (x) I |psi0> (side 0: Z_k rows x rows, system) or
+ * <psi0| I (x) Z_k |psi0> (side 1: cols x cols, environment), for K operators Z
+ * (device, K x n x n, FP64 or FP32, row-major) -- single-site operators and the
+ * stored products Z_i Z_j of one block alike.  Computed as Tr(rho Z_k) with the
+ * reduced density matrix rho = Psi Psi^T (side 0) or Psi^T Psi (side 1), formed in
+ * the workspace.  out: device, K doubles.  Errors: DMRG_ERR_INVALID_ARG for NULL
+ * pointers or side not in {0, 1}; DMRG_ERR_SHAPE for K < 0 or empty Psi. */
+DMRG_API dmrg_status dmrg_expectation_workspace(dmrg_handle handle, int64_t K, int64_t rows,
+                                       int64_t cols, int side, size_t* bytes);
+DMRG_API dmrg_status dmrg_expectation(dmrg_handle handle, const void* Z, int in_is_fp64, int64_t K,
+                             const double* Psi, int64_t rows, int64_t cols, int side,
+                             double* out, void* ws, size_t ws_bytes, dmrg_stream_t stream);
+
+/* Two-point functions across the two blocks:
+ *   C[i][j] = <psi0| Z_i (x) W_j |psi0> = <Psi^T Z_i Psi, W_j>_F,
+ * Z: device, Ks x rows x rows (system operators), W: device, Ke x cols x cols
+ * (environment operators), each FP64 or FP32; C: device, Ks x Ke FP64 row-major.
+ * Operators that are odd under fermion parity need the string of the block in
+ * front of them folded into W by the caller (number and spin operators need none). */
+DMRG_API dmrg_status dmrg_cross_correlations_workspace(dmrg_handle handle, int64_t Ks, int64_t Ke,
+                                              int64_t rows, int64_t cols, int z_is_fp64,
+                                              int w_is_fp64, size_t* bytes);
+DMRG_API dmrg_status dmrg_cross_correlations(dmrg_handle handle, const void* Z, int z_is_fp64,
+                                    int64_t Ks, const void* W, int w_is_fp64, int64_t Ke,
+                                    const double* Psi, int64_t rows, int64_t cols, double* C,
+                                    void* ws, size_t ws_bytes, dmrg_stream_t stream);
+
+/* Structure factor (Sec. 2):
+ *   F(q_p) = (1/L) sum_{k,j} e^{i q_p (k - j)} (G[k][j] - c v[k] - c v[j] + c^2),
+ *   q_p = 2 pi p / L, p = 0 .. L-1,
+ * from G[k][j] = <X_k X_j> (device, L x L FP64) and v[k] = <X_k> (device, L FP64, or
+ * NULL for v = 0): N(q) with X = n and c = n, the mean charge; S^z(q) with X = S^z
+ * and c = 0.  Fre, Fim: device, L doubles each (real and imaginary parts; the
+ * imaginary part vanishes for symmetric G). */
+DMRG_API dmrg_status dmrg_structure_factor(dmrg_handle handle, const double* G, const double* v,
+                                  double c, int64_t L, double* Fre, double* Fim,
+                                  dmrg_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Blocked site and cross operators (Sec. 2, the blocking of operators into the
  * [B a] basis that follows step 5; task ii of the rotation step in Sec. 3.2).
  *

@@ -19,6 +19,9 @@ from .api import (  # noqa: F401
     dmrg_rotate_site_ops,
     dmrg_orthonormality_error,
     dmrg_correlations,
+    dmrg_expectation,
+    dmrg_cross_correlations,
+    dmrg_structure_factor,
     dmrg_set_option,
     dmrg_kernel_timing,
     dmrg_sync_status,

@@ -262,6 +262,65 @@ def dmrg_rotate_site_ops(U: torch.Tensor, A: torch.Tensor, d: int, S, counts, fl
     return out
 
 
+def dmrg_expectation(Z: torch.Tensor, Psi: torch.Tensor, side: int = 0,
+                     handle: Optional[Handle] = None, stream=None) -> torch.Tensor:
+    """<psi0| Z_k (x) I |psi0> (side 0) or <psi0| I (x) Z_k |psi0> (side 1) for the
+    superblock state psi0 = sum Psi[a][e] |a>|e>; K FP64 values."""
+    h = handle or default_handle()
+    _need(Z, "Z", (torch.float64, torch.float32), 3)
+    _need(Psi, "Psi", (torch.float64,), 2)
+    rows, cols = Psi.shape
+    K = Z.shape[0]
+    out = torch.empty(K, dtype=torch.float64, device=Z.device)
+    n = ctypes.c_size_t()
+    _capi.check(h.lib.dmrg_expectation_workspace(h.h, K, rows, cols, int(side), ctypes.byref(n)),
+                h.h, "dmrg_expectation_workspace")
+    ws = h.workspace(n.value)
+    _capi.check(h.lib.dmrg_expectation(h.h, _ptr(Z), int(Z.dtype == torch.float64), K, _ptr(Psi), rows,
+                                       cols, int(side), _ptr(out), _ptr(ws), ws.numel(), _stream(stream)),
+                h.h, "dmrg_expectation")
+    return out
+
+
+def dmrg_cross_correlations(Z: torch.Tensor, W: torch.Tensor, Psi: torch.Tensor,
+                            handle: Optional[Handle] = None, stream=None) -> torch.Tensor:
+    """C[i][j] = <psi0| Z_i (x) W_j |psi0>: Z on the system, W on the environment."""
+    h = handle or default_handle()
+    _need(Z, "Z", (torch.float64, torch.float32), 3)
+    _need(W, "W", (torch.float64, torch.float32), 3)
+    _need(Psi, "Psi", (torch.float64,), 2)
+    rows, cols = Psi.shape
+    Ks, Ke = Z.shape[0], W.shape[0]
+    C = torch.empty((Ks, Ke), dtype=torch.float64, device=Z.device)
+    z64, w64 = int(Z.dtype == torch.float64), int(W.dtype == torch.float64)
+    n = ctypes.c_size_t()
+    _capi.check(h.lib.dmrg_cross_correlations_workspace(h.h, Ks, Ke, rows, cols, z64, w64,
+                                                        ctypes.byref(n)),
+                h.h, "dmrg_cross_correlations_workspace")
+    ws = h.workspace(n.value)
+    _capi.check(h.lib.dmrg_cross_correlations(h.h, _ptr(Z), z64, Ks, _ptr(W), w64, Ke, _ptr(Psi), rows,
+                                              cols, _ptr(C), _ptr(ws), ws.numel(), _stream(stream)),
+                h.h, "dmrg_cross_correlations")
+    return C
+
+
+def dmrg_structure_factor(G: torch.Tensor, v: Optional[torch.Tensor] = None, c: float = 0.0,
+                          handle: Optional[Handle] = None, stream=None):
+    """F(q_p) = (1/L) sum_{k,j} e^{i q_p (k-j)} <(X_k - c)(X_j - c)> for q_p = 2 pi p / L,
+    from G = <X_k X_j> (L x L) and v = <X_k>; returns (real part, imaginary part)."""
+    h = handle or default_handle()
+    _need(G, "G", (torch.float64,), 2)
+    L = G.shape[0]
+    if v is not None:
+        _need(v, "v", (torch.float64,), 1)
+    re = torch.empty(L, dtype=torch.float64, device=G.device)
+    im = torch.empty(L, dtype=torch.float64, device=G.device)
+    _capi.check(h.lib.dmrg_structure_factor(h.h, _ptr(G), _ptr(v) if v is not None else None, float(c), L,
+                                            _ptr(re), _ptr(im), _stream(stream)),
+                h.h, "dmrg_structure_factor")
+    return re, im
+
+
 def dmrg_orthonormality_error(U: torch.Tensor, handle: Optional[Handle] = None, stream=None
                               ) -> torch.Tensor:
     """||U^T U - I||_F in FP64 as a 1-element device tensor."""
