@@ -31,6 +31,7 @@ from .oracle import (  # noqa: F401
     expectation,
     cross_correlations,
     structure_factor,
+    truncation,
     rotate_backward,
     rotate_blocked,
     rotate_blocked_assembled,

@@ -220,6 +220,30 @@ def structure_factor(G, v=None, c: float = 0.0):
     return re, im
 
 
+def truncation(Psi, mp: int):
+    """Truncation matrix (Sec. 2, steps 3-4, Eq. rho and Eq. error): the reduced
+    density matrix rho[i][i'] = sum_j Psi[i][j] Psi[i'][j] of the system, its
+    eigenvalues w_alpha in decreasing order, U = the mp eigenvectors |w_alpha> with
+    the largest eigenvalues (columns; each with its largest-magnitude component
+    positive, the first such index on ties) and the discarded weight
+    eps_rho = sum_{alpha > mp} w_alpha (= 1 - sum of the kept ones for a normalized
+    psi).  The eigen-decomposition is the library routine numpy.linalg.eigh.
+    Returns (U, w, eps)."""
+    Psi = np.asarray(Psi, dtype=np.float64)
+    n, nc = Psi.shape
+    rho = np.zeros((n, n))
+    for i in range(n):                      # rho by its definition, row by row
+        rho[i] = Psi @ Psi[i]
+    w, V = np.linalg.eigh(rho)
+    order = np.argsort(-w, kind="stable")
+    w, V = w[order], V[:, order]
+    for a in range(V.shape[1]):
+        j = int(np.argmax(np.abs(V[:, a])))
+        if V[j, a] < 0:
+            V[:, a] = -V[:, a]
+    return np.ascontiguousarray(V[:, :mp]), w, float(w[mp:].sum())
+
+
 def orthonormality_error(U) -> float:
     """||U^T U - I||_F in FP64."""
     U = _c(U, np.float64)

@@ -512,3 +512,41 @@ def test_structure_factor_closed_forms(oracle_lib):
     expect[p0] += L / 2
     expect[L - p0] += L / 2
     assert np.abs(re2 - expect).max() < 1e-10                  # a single wave vector
+
+
+# ---------------------------------------------------------------- truncation matrix
+def schmidt_state(rng, n, nc, weights):
+    """Psi = sum_k sqrt(w_k) u_k v_k^T with orthonormal u (n) and v (nc): the reduced
+    density matrix Psi Psi^T has exactly the eigenpairs (w_k, u_k)."""
+    r = len(weights)
+    u = orthonormal_columns(rng, n, r)
+    v = orthonormal_columns(rng, nc, r)
+    return (u * np.sqrt(weights)) @ v.T, u
+
+
+def test_truncation_schmidt_spectrum(oracle_lib):
+    rng = np.random.default_rng(71)
+    n, nc, mp = 40, 30, 12
+    w = np.sort(rng.uniform(0.1, 1.0, 20))[::-1] * np.exp(-0.3 * np.arange(20))
+    w /= w.sum()                               # normalized psi: weights sum to 1
+    Psi, u = schmidt_state(rng, n, nc, w)
+    U, lam, eps = oracle_lib.truncation(Psi, mp)
+    assert np.abs(lam[:20] - w).max() < 1e-14                     # the Schmidt weights
+    assert np.abs(lam[20:]).max() < 1e-14                          # rank 20
+    assert abs(eps - w[mp:].sum()) < 1e-14
+    assert abs(eps - (1.0 - lam[:mp].sum())) < 1e-13               # Eq. error, normalized psi
+    assert np.abs(np.abs(U.T @ u[:, :mp]) - np.eye(mp)).max() < 1e-12   # kept |w_alpha>
+    assert np.abs(U.T @ U - np.eye(mp)).max() < 1e-13
+    for a in range(mp):                                            # sign convention
+        j = np.argmax(np.abs(U[:, a]))
+        assert U[j, a] > 0
+
+
+def test_truncation_product_state(oracle_lib):
+    # A product state (rank-1 Psi) keeps everything with one state: eps = 0.
+    rng = np.random.default_rng(72)
+    a, b = rng.standard_normal(9), rng.standard_normal(5)
+    Psi = np.outer(a, b) / (np.linalg.norm(a) * np.linalg.norm(b))
+    U, lam, eps = oracle_lib.truncation(Psi, 1)
+    assert abs(lam[0] - 1.0) < 1e-14 and abs(eps) < 1e-14
+    assert np.abs(np.abs(U[:, 0]) - np.abs(a) / np.linalg.norm(a)).max() < 1e-14
