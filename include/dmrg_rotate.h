@@ -318,6 +318,32 @@ DMRG_API dmrg_status dmrg_structure_factor(dmrg_handle handle, const double* G, 
                                   dmrg_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Truncation matrix (Sec. 2, steps 3-4; Eq. rho and Eq. error).
+ *
+ * From the superblock ground state Psi (device, rows x cols FP64: system states i,
+ * environment states j), forms the system's reduced density matrix
+ * rho[i][i'] = sum_j Psi[i][j] Psi[i'][j], diagonalises it by cyclic Jacobi
+ * rotations in FP64, and returns
+ *   U       device, rows x mp FP64 row-major: the mp eigenvectors with the largest
+ *           eigenvalues as columns, in decreasing eigenvalue order, each with its
+ *           largest-magnitude component positive (U = R^+ of the rotation);
+ *   lambda  device, rows FP64: all eigenvalues in decreasing order;
+ *   eps     device, 1 FP64: the discarded weight sum_{a >= mp} lambda[a]
+ *           (= 1 - sum of the kept eigenvalues for a normalized state);
+ *   sweeps  host (may be NULL): sweeps done; -max_sweeps if the off-diagonal part
+ *           did not fall below tol * ||rho||_F (the outputs then hold the last
+ *           iterate).
+ * The call waits for the stream once per sweep (the convergence test), so it is not
+ * graph-capturable.  Errors: DMRG_ERR_SHAPE unless 1 <= mp <= rows;
+ * DMRG_ERR_INVALID_ARG for NULL outputs, tol <= 0 or max_sweeps < 1. */
+DMRG_API dmrg_status dmrg_truncation_workspace(dmrg_handle handle, int64_t rows, int64_t cols,
+                                      size_t* bytes);
+DMRG_API dmrg_status dmrg_truncation(dmrg_handle handle, const double* Psi, int64_t rows,
+                            int64_t cols, int64_t mp, double* U, double* lambda, double* eps,
+                            double tol, int max_sweeps, int* sweeps, void* ws, size_t ws_bytes,
+                            dmrg_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Blocked site and cross operators (Sec. 2, the blocking of operators into the
  * [B a] basis that follows step 5; task ii of the rotation step in Sec. 3.2).
  *

@@ -22,6 +22,7 @@ from .api import (  # noqa: F401
     dmrg_expectation,
     dmrg_cross_correlations,
     dmrg_structure_factor,
+    dmrg_truncation,
     dmrg_set_option,
     dmrg_kernel_timing,
     dmrg_sync_status,

@@ -72,6 +72,9 @@ SIGNATURES = {
     "dmrg_cross_correlations_workspace": [_p, _i64, _i64, _i64, _i64, _int, _int, ctypes.POINTER(_sz)],
     "dmrg_cross_correlations": [_p, _p, _int, _i64, _p, _int, _i64, _p, _i64, _i64, _p, _p, _sz, _p],
     "dmrg_structure_factor": [_p, _p, _p, ctypes.c_double, _i64, _p, _p, _p],
+    "dmrg_truncation_workspace": [_p, _i64, _i64, ctypes.POINTER(_sz)],
+    "dmrg_truncation": [_p, _p, _i64, _i64, _i64, _p, _p, _p, ctypes.c_double, _int,
+                        ctypes.POINTER(_int), _p, _sz, _p],
     "dmrg_rotate_site_ops_workspace": [_p, _i64, _i64, _int, _i64, _int, ctypes.POINTER(_sz)],
     "dmrg_rotate_site_ops": [_p, _p, _i64, _int, _i64, _p, _int, _i64, _int, _p, _p, _p, _p, _p, _int,
                              _p, _sz, _p],

@@ -321,6 +321,28 @@ def dmrg_structure_factor(G: torch.Tensor, v: Optional[torch.Tensor] = None, c: 
     return re, im
 
 
+def dmrg_truncation(Psi: torch.Tensor, mp: int, tol: float = 1e-14, max_sweeps: int = 30,
+                    handle: Optional[Handle] = None, stream=None):
+    """Truncation matrix from the superblock state Psi (rows x cols, FP64): returns
+    (U rows x mp, all eigenvalues of rho = Psi Psi^T in decreasing order, the discarded
+    weight eps as a 1-element tensor, sweeps done)."""
+    h = handle or default_handle()
+    _need(Psi, "Psi", (torch.float64,), 2)
+    rows, cols = Psi.shape
+    U = torch.empty((rows, mp), dtype=torch.float64, device=Psi.device)
+    lam = torch.empty(rows, dtype=torch.float64, device=Psi.device)
+    eps = torch.empty(1, dtype=torch.float64, device=Psi.device)
+    n = ctypes.c_size_t()
+    _capi.check(h.lib.dmrg_truncation_workspace(h.h, rows, cols, ctypes.byref(n)), h.h,
+                "dmrg_truncation_workspace")
+    ws = h.workspace(n.value)
+    sweeps = ctypes.c_int()
+    _capi.check(h.lib.dmrg_truncation(h.h, _ptr(Psi), rows, cols, int(mp), _ptr(U), _ptr(lam), _ptr(eps),
+                                      float(tol), int(max_sweeps), ctypes.byref(sweeps), _ptr(ws),
+                                      ws.numel(), _stream(stream)), h.h, "dmrg_truncation")
+    return U, lam, eps, sweeps.value
+
+
 def dmrg_orthonormality_error(U: torch.Tensor, handle: Optional[Handle] = None, stream=None
                               ) -> torch.Tensor:
     """||U^T U - I||_F in FP64 as a 1-element device tensor."""

@@ -59,6 +59,10 @@ cudaError_t corr_matvec_launch(const void* Op, bool f64, const double* psi, int6
                                double* x, double* y, cudaStream_t s);
 // dO-style partial trace helper etc. live in the api translation unit.
 cudaError_t convert_f32_to_f64_launch(const float* src, double* dst, int64_t n, cudaStream_t s);
+// Reduced density matrix of the superblock state Psi (rows x cols, FP64):
+// rho = Psi Psi^T (side 0, rows x rows) or Psi^T Psi (side 1, cols x cols).
+cudaError_t rho_launch(const double* Psi, int64_t rows, int64_t cols, int side, double* rho,
+                       cudaStream_t s);
 cudaError_t fill_zero_launch(void* p, size_t bytes, cudaStream_t s);
 
 // ---------------------------------------------------------------- tensor-core GEMM

@@ -79,6 +79,10 @@ __global__ void structure_factor_kernel(const double* __restrict__ G, const doub
     }
 }
 
+}  // namespace
+
+namespace dmrg {
+
 // rho = Psi Psi^T (side 0, rows x rows) or Psi^T Psi (side 1, cols x cols).
 cudaError_t rho_launch(const double* Psi, int64_t rows, int64_t cols, int side, double* rho,
                        cudaStream_t s) {
@@ -97,6 +101,10 @@ cudaError_t rho_launch(const double* Psi, int64_t rows, int64_t cols, int side, 
     }
     return simt_gemm_launch(Real::F64, g, s);
 }
+
+}  // namespace dmrg
+
+namespace {
 
 WsLayout cross_layout(int64_t Ks, int64_t Ke, int64_t rows, int64_t cols, int z64, int w64) {
     WsLayout W;

@@ -1,0 +1,78 @@
+"""GPU parity of the truncation matrix (Sec. 2, steps 3-4: rho = Psi Psi^T, its kept
+eigenvectors and the discarded weight) against the FP64 oracle, and its use as the
+rotation U of the next step.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from workloads import orthonormal_columns
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_0909_5662_gb300 as lib
+    return lib
+
+
+def schmidt(rng, n, nc, w):
+    u = orthonormal_columns(rng, n, len(w))
+    v = orthonormal_columns(rng, nc, len(w))
+    return (u * np.sqrt(w)) @ v.T
+
+
+def run(P, Psi, mp):
+    U, lam, eps, sweeps = P.dmrg_truncation(torch.from_numpy(Psi).cuda(), mp)
+    torch.cuda.synchronize()
+    P.dmrg_sync_status()
+    return U.cpu().numpy(), lam.cpu().numpy(), float(eps.item()), sweeps
+
+
+@pytest.mark.parametrize("n,nc,rank,mp", [(40, 30, 20, 12), (37, 64, 37, 10), (64, 16, 16, 16), (2, 3, 2, 1)])
+def test_truncation_matches_oracle_schmidt(P, n, nc, rank, mp):
+    # distinct Schmidt weights: every kept eigenvector is unique up to sign
+    rng = np.random.default_rng(n * 100 + nc)
+    w = np.exp(-0.25 * np.arange(rank)) * (1.0 + 0.05 * rng.random(rank))
+    w = np.sort(w)[::-1] / w.sum()
+    Psi = schmidt(rng, n, nc, w)
+    U_ref, lam_ref, eps_ref = oracle.truncation(Psi, mp)
+    U, lam, eps, sweeps = run(P, Psi, mp)
+    assert sweeps > 0
+    assert np.abs(lam - lam_ref).max() < 1e-13
+    assert abs(eps - eps_ref) < 1e-13
+    assert np.abs(U - U_ref).max() < 1e-10
+    assert np.abs(U.T @ U - np.eye(mp)).max() < 1e-12
+
+
+@pytest.mark.parametrize("n,nc,mp", [(64, 50, 20), (129, 200, 40), (400, 400, 100)])
+def test_truncation_random_state(P, n, nc, mp):
+    rng = np.random.default_rng(n + nc)
+    Psi = rng.standard_normal((n, nc))
+    Psi /= np.linalg.norm(Psi)
+    U_ref, lam_ref, eps_ref = oracle.truncation(Psi, mp)
+    U, lam, eps, sweeps = run(P, Psi, mp)
+    assert sweeps > 0
+    assert np.abs(lam - lam_ref).max() < 1e-13 * max(1.0, lam_ref[0])
+    assert abs(eps - eps_ref) < 1e-12
+    # the kept subspace (projector), unique when lambda[mp-1] > lambda[mp]
+    assert np.abs(U @ U.T - U_ref @ U_ref.T).max() < 1e-9
+    assert abs(lam.sum() - 1.0) < 1e-12                     # Tr rho = |psi|^2 = 1
+
+
+def test_truncation_feeds_the_rotation(P):
+    # The U of one step is the rotation of the next: orthonormal to FP64 rounding and
+    # consumed by dmrg_rotate_ops (compare with the oracle's U and rotation).
+    rng = np.random.default_rng(5)
+    m, d, mp = 24, 4, 30
+    Psi = rng.standard_normal((m * d, 50))
+    Psi /= np.linalg.norm(Psi)
+    U, _, _, _ = run(P, Psi, mp)
+    U_ref, _, _ = oracle.truncation(Psi, mp)
+    assert oracle.orthonormality_error(U) < 1e-12   # rounding of ~10 sweeps of rotations
+    O = rng.standard_normal((6, m, m))
+    got = P.dmrg_rotate_ops(torch.from_numpy(U).cuda(), torch.from_numpy(O).cuda(), d, "fp64").cpu().numpy()
+    ref = oracle.rotate_dense(U_ref, O, d)
+    assert np.abs(got - ref).max() < 1e-10 * np.abs(ref).max()
