@@ -198,26 +198,89 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     for (int i = 0; i < ns; ++i) Op[i] = base + D.ws.offsets[si++];
     for (int i = 0; i < ns; ++i) Tt[i] = base + D.ws.offsets[si++];
 
-    // ---- operand packing: O (stacked K*m x m), U_r' (rows b*d + s, cols j), U^T.
-    PackJob jobs[3] = {};
-    PackJob& jo = jobs[0];
+    // ---- second product's problem first: its split tail decides which outputs the
+    //      packing launch clears.  O'_k^T rows = T_all rows (k*mp + b), columns a.
+    TcLaunch L2{};
+    TcProblem& P2 = L2.inline_prob[0];
+    {
+        TcOperand A{Tt[0], Tt[1], K * mp, D.md, D.ld2};
+        TcOperand B{B2[0], B2[1], mp, D.md, D.ld2};
+        if (!make_problem(P2, mode, A, B, c2.tile_n_max, 1, c2.row_bytes, c2.pair))
+            return fail(h, DMRG_ERR_CUDA, "cuTensorMapEncodeTiled failed (second product)");
+    }
+    TcScatter& S2 = P2.sc[0];
+    S2.rows_per_op = int32_t(mp);
+    S2.s_op = mp * mp;
+    S2.s_row = 1;
+    S2.col_div = 1;
+    S2.s_col_hi = mp;
+    S2.s_col_lo = 0;
+    L2.table = nullptr;
+    L2.nprob = 1;
+    L2.total_tiles = P2.m_tiles * P2.n_tiles * P2.k_splits;
+    L2.out[0][0] = Oout;
+    const int grid2 = c2.grid > 0 ? c2.grid : h->num_sms;
+    int64_t k_clear = K;   // outputs k >= k_clear are accumulated atomically: cleared first
+    // Tail wave: the tiles left after the last full wave over the persistent CTAs (or
+    // CTA pairs) are whole M tiles whose reduction is split so the last round is short;
+    // a problem smaller than one wave is split as a whole.  The parts accumulate with
+    // atomics into outputs cleared first (so the summation order of those outputs may
+    // differ between runs; DMRG_OPT_DETERMINISTIC turns the split off).
+    {
+        const int slots = c2.pair ? grid2 / (2 * c2.pair) : grid2;
+        const int bm = c2.pair ? 256 : 128;
+        const int tiles = P2.m_tiles * P2.n_tiles;
+        const int full_mt = (tiles / slots) * slots / P2.n_tiles;
+        const int tail_mt = P2.m_tiles - full_mt;
+        const int64_t epr = c2.row_bytes / (split ? 2 : 4);   // reduction elements per k-block
+        const int kb = int((D.md + epr - 1) / epr);
+        const int parts = tail_mt > 0 ? std::min(kb, slots / (tail_mt * P2.n_tiles)) : 0;
+        if (!h->deterministic && tail_mt > 0 && parts >= 2) {
+            TcProblem& T2 = L2.inline_prob[1];
+            T2 = P2;
+            P2.m_tiles = full_mt;
+            T2.m_tile0 = full_mt;
+            T2.m_tiles = tail_mt;
+            T2.kb_per_split = (kb + parts - 1) / parts;
+            T2.k_splits = (kb + T2.kb_per_split - 1) / T2.kb_per_split;
+            T2.atomic = 1;
+            T2.tile_start = P2.m_tiles * P2.n_tiles;
+            L2.nprob = 2;
+            L2.total_tiles = T2.tile_start + T2.m_tiles * T2.n_tiles * T2.k_splits;
+            k_clear = int64_t(full_mt) * bm / mp;
+        }
+    }
+
+    // ---- operand packing: O (stacked K*m x m), U_r' (rows b*d + s, cols j), U^T, and
+    //      the clearing of the split tail's outputs, in one launch (the two small U
+    //      gathers run alongside the bandwidth-bound O stream).
+    PackJob jobs[4] = {};
+    int nj = 0;
+    PackJob& jo = jobs[nj++];
     jo.src = O; jo.src_f64 = in_is_fp64; jo.mode = pmode;
     jo.rows = K * m; jo.cols = m; jo.rows_per_op = K * m; jo.s_op = 0; jo.op_off = nullptr;
     jo.rdiv = 1; jo.s_r_hi = m; jo.s_r_lo = 0; jo.s_c = 1;
     jo.dst0 = Op[0]; jo.dst1 = Op[1]; jo.ld = D.ld1;
-    PackJob& j1 = jobs[1];
-    j1.src = U1 ? U1 : U; j1.src_f64 = 1; j1.mode = pmode;
-    j1.rows = int64_t(d) * mp; j1.cols = m; j1.rows_per_op = j1.rows;
-    j1.rdiv = d; j1.s_r_hi = 1; j1.s_r_lo = mp; j1.s_c = int64_t(d) * mp;
-    j1.dst0 = B1[0]; j1.dst1 = B1[1]; j1.ld = D.ld1;
-    PackJob& j2 = jobs[2];
-    j2.src = U; j2.src_f64 = 1; j2.mode = pmode;
-    j2.rows = mp; j2.cols = D.md; j2.rows_per_op = mp;
-    j2.rdiv = 1; j2.s_r_hi = 1; j2.s_r_lo = 0; j2.s_c = mp;
-    j2.dst0 = B2[0]; j2.dst1 = B2[1]; j2.ld = D.ld2;
-    // one launch: the two small U gathers run alongside the bandwidth-bound O stream
+    if (pack_u) {
+        PackJob& j1 = jobs[nj++];
+        j1.src = U1 ? U1 : U; j1.src_f64 = 1; j1.mode = pmode;
+        j1.rows = int64_t(d) * mp; j1.cols = m; j1.rows_per_op = j1.rows;
+        j1.rdiv = d; j1.s_r_hi = 1; j1.s_r_lo = mp; j1.s_c = int64_t(d) * mp;
+        j1.dst0 = B1[0]; j1.dst1 = B1[1]; j1.ld = D.ld1;
+        PackJob& j2 = jobs[nj++];
+        j2.src = U; j2.src_f64 = 1; j2.mode = pmode;
+        j2.rows = mp; j2.cols = D.md; j2.rows_per_op = mp;
+        j2.rdiv = 1; j2.s_r_hi = 1; j2.s_r_lo = 0; j2.s_c = mp;
+        j2.dst0 = B2[0]; j2.dst1 = B2[1]; j2.ld = D.ld2;
+    }
+    if (k_clear < K) {
+        PackJob& jz = jobs[nj++];
+        jz.mode = kPackZero;
+        jz.rows = 1; jz.cols = (K - k_clear) * mp * mp; jz.rows_per_op = 1; jz.rdiv = 1;
+        jz.dst0 = static_cast<float*>(Oout) + k_clear * mp * mp; jz.ld = jz.cols;
+    }
     cudaError_t e = timed_launch(h, "pack_operands", s,
-                                 [&] { return pack_launch(jobs, pack_u ? 3 : 1, nullptr, s); });
+                                 [&] { return pack_launch(jobs, nj, nullptr, s); });
     if (e != cudaSuccess) return cuda_fail(h, e, "pack");
 
     // ---- first product: T = O U_r, written straight into the second product's
@@ -254,59 +317,6 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     });
     if (e != cudaSuccess) return cuda_fail(h, e, "first product");
 
-    // ---- second product: O'_k^T rows = T_all rows (k*mp + b), columns a: O'_k[a][b].
-    TcLaunch L2{};
-    TcProblem& P2 = L2.inline_prob[0];
-    {
-        TcOperand A{Tt[0], Tt[1], K * mp, D.md, D.ld2};
-        TcOperand B{B2[0], B2[1], mp, D.md, D.ld2};
-        if (!make_problem(P2, mode, A, B, c2.tile_n_max, 1, c2.row_bytes, c2.pair))
-            return fail(h, DMRG_ERR_CUDA, "cuTensorMapEncodeTiled failed (second product)");
-    }
-    TcScatter& S2 = P2.sc[0];
-    S2.rows_per_op = int32_t(mp);
-    S2.s_op = mp * mp;
-    S2.s_row = 1;
-    S2.col_div = 1;
-    S2.s_col_hi = mp;
-    S2.s_col_lo = 0;
-    L2.table = nullptr;
-    L2.nprob = 1;
-    L2.total_tiles = P2.m_tiles * P2.n_tiles * P2.k_splits;
-    L2.out[0][0] = Oout;
-    const int grid2 = c2.grid > 0 ? c2.grid : h->num_sms;
-    // Tail wave: the tiles left after the last full wave over the persistent CTAs (or
-    // CTA pairs) are whole M tiles whose reduction is split so the last round is short;
-    // a problem smaller than one wave is split as a whole.  The parts accumulate with
-    // atomics into outputs cleared first (so the summation order of those outputs may
-    // differ between runs; DMRG_OPT_DETERMINISTIC turns the split off).
-    {
-        const int slots = c2.pair ? grid2 / (2 * c2.pair) : grid2;
-        const int bm = c2.pair ? 256 : 128;
-        const int tiles = P2.m_tiles * P2.n_tiles;
-        const int full_mt = (tiles / slots) * slots / P2.n_tiles;
-        const int tail_mt = P2.m_tiles - full_mt;
-        const int64_t epr = c2.row_bytes / (split ? 2 : 4);   // reduction elements per k-block
-        const int kb = int((D.md + epr - 1) / epr);
-        const int parts = tail_mt > 0 ? std::min(kb, slots / (tail_mt * P2.n_tiles)) : 0;
-        if (!h->deterministic && tail_mt > 0 && parts >= 2) {
-            TcProblem& T2 = L2.inline_prob[1];
-            T2 = P2;
-            P2.m_tiles = full_mt;
-            T2.m_tile0 = full_mt;
-            T2.m_tiles = tail_mt;
-            T2.kb_per_split = (kb + parts - 1) / parts;
-            T2.k_splits = (kb + T2.kb_per_split - 1) / T2.kb_per_split;
-            T2.atomic = 1;
-            T2.tile_start = P2.m_tiles * P2.n_tiles;
-            L2.nprob = 2;
-            L2.total_tiles = T2.tile_start + T2.m_tiles * T2.n_tiles * T2.k_splits;
-            const int64_t k_first = int64_t(full_mt) * bm / mp;
-            e = cudaMemsetAsync(static_cast<float*>(Oout) + k_first * mp * mp, 0,
-                                size_t(K - k_first) * mp * mp * sizeof(float), s);
-            if (e != cudaSuccess) return cuda_fail(h, e, "clear tail outputs");
-        }
-    }
     L2.status = h->d_status;
     L2.timeout_ns = timeout_ns(h);
     L2.row_bytes = c2.row_bytes;

@@ -166,10 +166,12 @@ TcScatter scatter_rowmajor(int64_t ld);
 // For row r: g = r / rows_per_op (operand group), rr = r % rows_per_op;
 //   src index = src_off + (op_off ? op_off[g] : g * s_op) + (rr / rdiv) * s_r_hi
 //               + (rr % rdiv) * s_r_lo + c * s_c.
+constexpr int32_t kPackZero = 3;   // PackJob::mode: clear rows x cols FP32 values at dst0
+
 struct PackJob {
     const void* src;
     int32_t src_f64;
-    int32_t mode;          // 0: BF16 hi/lo pair, 1: FP32 rounded to TF32
+    int32_t mode;          // 0: BF16 hi/lo pair, 1: FP32 rounded to TF32, 2: FP32, 3: zero fill
     int64_t rows, cols;
     int64_t src_off;
     int64_t rows_per_op;

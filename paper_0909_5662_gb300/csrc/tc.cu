@@ -91,6 +91,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem_base = *tmem_slot;
     volatile int* vabort = abort_flag;
     const uint64_t tmo = L.timeout_ns;
+    // The set-up above may overlap the previous kernel's tail; nothing in global
+    // memory is touched before that kernel has completed.
+    griddep_wait();
+    griddep_launch_dependents();
 
     auto stage_a = [&](int s, int half) -> uint8_t* {
         return smem + size_t(s) * stage_bytes + size_t(half) * (a_bytes + b_bytes);
@@ -498,11 +502,27 @@ __device__ __forceinline__ void pack_tile(const PackJob& j, int64_t t, float (*t
 // after it.
 __global__ void __launch_bounds__(kPackThreads) pack_mixed_kernel(const __grid_constant__ PackLaunch L) {
     __shared__ float tile[kTile][kTile + 1];
+    griddep_wait();   // launched as a programmatic dependent of the previous kernel
     const int b = blockIdx.x;
     int k = 0;
     for (int i = 1; i < L.njobs; ++i)
         if (L.inline_jobs[i].block_start <= b) k = i;
     const PackJob& j = L.inline_jobs[k];
+    if (j.mode == kPackZero) {
+        // rows x cols FP32 zeros at row stride ld; 8 values per thread, coalesced
+        float* d = static_cast<float*>(j.dst0);
+        const int64_t total = j.rows * j.cols;
+        const int64_t e0 = int64_t(b - j.block_start) * kPackThreads * 8 + threadIdx.x;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int64_t e = e0 + int64_t(q) * kPackThreads;
+            if (e < total) {
+                const int64_t r = e / j.cols;
+                d[r * j.ld + (e - r * j.cols)] = 0.f;
+            }
+        }
+        return;
+    }
     if (j.tiled) {
         pack_tile(j, int64_t(b - j.block_start), tile);
         return;
@@ -534,6 +554,7 @@ __global__ void __launch_bounds__(kPackThreads) pack_mixed_kernel(const __grid_c
 // FP32 sources in groups of rows_per_op rows at source stride s_op (no offset table),
 // whole groups only; even destination strides (pair stores).
 bool pack_tiled_ok(const PackJob& j) {
+    if (j.mode == kPackZero) return false;
     const int64_t rpo = j.rows_per_op < j.rows ? j.rows_per_op : j.rows;
     const bool aligned = (j.ld % 2) == 0 && (reinterpret_cast<uintptr_t>(j.dst0) % 8) == 0 &&
                          (j.dst1 == nullptr || (reinterpret_cast<uintptr_t>(j.dst1) % 4) == 0);
@@ -549,6 +570,7 @@ int64_t pack_tiles_host(const PackJob& j) {
 }
 
 bool pack_vec8_ok(const PackJob& j) {
+    if (j.mode == kPackZero) return false;
     const size_t es = j.src_f64 ? 8 : 4;
     const bool single_group = (j.rows_per_op >= j.rows) && j.op_off == nullptr;
     return single_group && j.rdiv == 1 && j.s_c == 1 && (j.cols % 8) == 0 && (j.s_r_hi % 8) == 0 &&
@@ -564,8 +586,17 @@ cudaError_t launch_one(const TcLaunch& L, int stages, int grid, int bn_smem, siz
     auto k = L.row_bytes == 64 ? tc_gemm_kernel<MODE, EPI, 64> : tc_gemm_kernel<MODE, EPI, 128>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    k<<<grid, kThreads, smem, s>>>(L, stages, bn_smem);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid), 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, L, stages, bn_smem);
 }
 
 size_t tc_smem_bytes(TcMode mode, int stages, int bn, int rb) {
@@ -649,14 +680,24 @@ cudaError_t pack_launch(const PackJob* jobs, int njobs, PackJob* /*unused*/, cud
             j.tiled = tl ? 1 : 0;
             j.block_start = blocks;
             blocks += v8 ? (j.rows * (j.cols / 8) + kPackThreads * kVec8Units - 1) / (kPackThreads * kVec8Units)
-                    : tl ? pack_tiles_host(j) : pack_blocks_for(j);
+                    : tl ? pack_tiles_host(j)
+                    : j.mode == kPackZero ? (j.rows * j.cols + kPackThreads * 8 - 1) / (kPackThreads * 8)
+                                          : pack_blocks_for(j);
         }
     if (n == 0 || blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     L.table = nullptr;
     L.njobs = n;
-    pack_mixed_kernel<<<unsigned(blocks), kPackThreads, 0, s>>>(L);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(blocks), 1, 1);
+    cfg.blockDim = dim3(kPackThreads, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, pack_mixed_kernel, L);
 }
 
 cudaError_t pack_grouped_launch(const PackJob* jobs_dev, int njobs, int64_t total_blocks,

@@ -120,6 +120,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem_base = *tmem_slot;
     volatile int* vabort = abort_flag;
     const uint64_t tmo = L.timeout_ns;
+    // The set-up above may overlap the previous kernel's tail; nothing in global
+    // memory is touched before that kernel has completed.
+    griddep_wait();
+    griddep_launch_dependents();
 
     auto stage_a = [&](int s, int half) -> uint8_t* {
         return smem + size_t(s) * stage_bytes + size_t(half) * (a_bytes + b_bytes);
@@ -355,13 +359,15 @@ cudaError_t launch_pair(const TcLaunch& L, int stages, int grid, int bh_smem, si
     cfg.blockDim = dim3(kThreads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 2 * NP;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     // A persistent grid larger than the clusters that fit at once would only queue.
     const int fit = clusters_that_fit(reinterpret_cast<const void*>(k), cfg);
     if (fit > 0 && 2 * NP * fit < grid) cfg.gridDim.x = unsigned(2 * NP * fit);
