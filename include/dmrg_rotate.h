@@ -102,6 +102,13 @@ DMRG_API dmrg_status dmrg_sync_status(dmrg_handle handle, dmrg_stream_t stream);
  *                              accumulated with FP32 atomics, so the last few
  *                              operators' rounding order may differ between runs
  *                              (within the precision's tolerance).
+ *   DMRG_OPT_ACCUM_CHAIN     : longest reduction (in elements) that one tensor-core
+ *                              FP32 accumulator sums in the BF16x3 dense products
+ *                              (default 1024).  A longer reduction (and longer than
+ *                              512) is cut into chains of this length whose results
+ *                              are added in FP32 with round to nearest; the tensor
+ *                              core's own accumulation error grows with the chain
+ *                              length.  0 = one chain.
  *   DMRG_OPT_TEST_WITHHOLD_ARRIVAL : test hook for failure detection.  1 makes
  *                              the next dense tensor-core launch withhold one
  *                              shared-memory stage release in its first CTA, so
@@ -115,7 +122,8 @@ typedef enum {
     DMRG_OPT_WAIT_TIMEOUT_MS = 3,
     DMRG_OPT_CHECK_ORTHO = 4,
     DMRG_OPT_TEST_WITHHOLD_ARRIVAL = 5,
-    DMRG_OPT_DETERMINISTIC = 6
+    DMRG_OPT_DETERMINISTIC = 6,
+    DMRG_OPT_ACCUM_CHAIN = 7
 } dmrg_option;
 DMRG_API dmrg_status dmrg_set_option(dmrg_handle handle, dmrg_option option, double value);
 

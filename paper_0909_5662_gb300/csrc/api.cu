@@ -129,6 +129,8 @@ DenseDims dense_dims(int64_t K, int64_t m, int d, int64_t mp, dmrg_precision p) 
         for (int s = 0; s < nsplit; ++s) W.add("B2", size_t(mp) * D.ld2 * es);
         for (int s = 0; s < nsplit; ++s) W.add("Op", size_t(K) * m * D.ld1 * es);
         for (int s = 0; s < nsplit; ++s) W.add("T", size_t(K) * mp * D.ld2 * es);
+        // running sums of chained accumulation (BF16x3 reductions longer than 512)
+        W.add("chain", (p == DMRG_PREC_BF16X3 && D.md > kChainMinRed) ? kChainScratchBytes : 0);
     }
     return D;
 }
@@ -197,6 +199,17 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     for (int i = 0; i < ns; ++i) B2[i] = base + D.ws.offsets[si++];
     for (int i = 0; i < ns; ++i) Op[i] = base + D.ws.offsets[si++];
     for (int i = 0; i < ns; ++i) Tt[i] = base + D.ws.offsets[si++];
+    // Chained accumulation (CTA-pair kernel, BF16x3): reductions longer than the handle's
+    // chain length are cut into chains summed in FP32 through a per-CTA scratch.
+    float* chain_scr =
+        (split && D.md > kChainMinRed) ? reinterpret_cast<float*>(base + D.ws.offsets[si]) : nullptr;
+    auto chain_kb = [&](const TcConfig& c, int64_t red, int grid) -> int {
+        if (!chain_scr || !c.pair || h->accum_chain <= 0 || red <= h->accum_chain ||
+            grid > kChainScratchCtas)
+            return 0;
+        const int64_t epr = c.row_bytes / 2;   // BF16 elements per k-block
+        return int(std::max<int64_t>(1, h->accum_chain / epr));
+    };
 
     // ---- second product's problem first: its split tail decides which outputs the
     //      packing launch clears.  O'_k^T rows = T_all rows (k*mp + b), columns a.
@@ -220,6 +233,8 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     L2.total_tiles = P2.m_tiles * P2.n_tiles * P2.k_splits;
     L2.out[0][0] = Oout;
     const int grid2 = c2.grid > 0 ? c2.grid : h->num_sms;
+    P2.kb_chunk = chain_kb(c2, D.md, grid2);
+    L2.chunk_scratch = P2.kb_chunk ? chain_scr : nullptr;
     int64_t k_clear = K;   // outputs k >= k_clear are accumulated atomically: cleared first
     // Tail wave: the tiles left after the last full wave over the persistent CTAs (or
     // CTA pairs) are whole M tiles whose reduction is split so the last round is short;
@@ -310,6 +325,8 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     L1.drop_arrival = take_drop_arrival(h);
     L1.row_bytes = c1.row_bytes;
     const int grid1 = c1.grid > 0 ? c1.grid : h->num_sms;
+    P1.kb_chunk = chain_kb(c1, m, grid1);
+    L1.chunk_scratch = P1.kb_chunk ? chain_scr : nullptr;
     e = timed_launch(h, "tc_gemm_first_product", s, [&] {
         const TcEpi epi = split ? EPI_SPLIT_BF16 : EPI_TF32;
         return c1.pair ? tc_gemm_launch_pair(mode, epi, L1, c1.stages, grid1, s, c1.pair)
@@ -485,6 +502,10 @@ dmrg_status dmrg_set_option(dmrg_handle h, dmrg_option o, double v) {
             return DMRG_OK;
         case DMRG_OPT_DETERMINISTIC:
             h->deterministic = v != 0;
+            return DMRG_OK;
+        case DMRG_OPT_ACCUM_CHAIN:
+            if (v < 0 || v > 1e9) return fail(h, DMRG_ERR_INVALID_ARG, "accum_chain must be >= 0");
+            h->accum_chain = int(v);
             return DMRG_OK;
         case DMRG_OPT_TEST_WITHHOLD_ARRIVAL:
             h->drop_arrival_next = v != 0;

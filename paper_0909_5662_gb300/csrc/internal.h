@@ -89,6 +89,8 @@ struct TcProblem {  // 64-byte aligned through its CUtensorMap members
     int32_t tile_start;  // first global tile of this problem
     int32_t m_tile0;     // first M tile (the problem covers M tiles m_tile0 .. m_tile0 + m_tiles - 1)
     int32_t atomic;      // FP32 epilogues: accumulate with atomics (split-K parts of a tile)
+    int32_t kb_chunk;    // CTA-pair kernel: k-blocks per tensor-core accumulation chain; the
+                         // chains of a tile are summed in FP32 registers (0: one chain)
     TcScatter sc[1];
 };
 
@@ -109,6 +111,12 @@ struct TcConfig {
 };
 
 constexpr int kMaxInlineProblems = 4;
+// Running-sum scratch of the CTA-pair kernel's chained accumulation: kChainScratchCtas
+// CTAs x 128 rows x 256 FP32 columns.
+constexpr int kChainScratchCtas = 160;
+constexpr size_t kChainScratchBytes = size_t(kChainScratchCtas) * 128 * 256 * 4;
+// Reductions up to this length always run as one chain (no scratch is reserved for them).
+constexpr int64_t kChainMinRed = 512;
 
 struct TcLaunch {
     TcProblem inline_prob[kMaxInlineProblems];  // used when table == nullptr
@@ -120,6 +128,8 @@ struct TcLaunch {
     uint64_t timeout_ns;
     int32_t drop_arrival;   // test hook: CTA 0 withholds its first stage release
     int32_t row_bytes;      // 128 or 64: must match the problems' tensor maps
+    float* chunk_scratch;   // CTA-pair kernel with kb_chunk: gridDim.x x 128 x 256 FP32 running
+                            // sums (nullptr: every tile is one accumulation chain)
 };
 
 // One operand seen by the kernel: `nbatch` slices of rows x cols (cols = the
@@ -215,6 +225,8 @@ struct dmrg_handle_s {
     double check_ortho_tol = 0.0;
     int drop_arrival_next = 0;      // test hook, consumed by the next tensor-core launch
     bool deterministic = false;     // no atomically accumulated split tiles
+    int accum_chain = 1024;         // BF16x3 dense products: reduction elements per accumulator
+                                    // chain (0 = one chain per tile)
 
     struct Timed {
         std::string name;

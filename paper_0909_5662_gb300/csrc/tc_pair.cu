@@ -204,55 +204,65 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0 && leader) {
             int stage = 0;
             uint32_t phase = 0;
-            int it = 0;
+            int it = 0;   // accumulation chains issued (one TMEM accumulator each, alternating)
             bool ok = true;
-            for (int t = pair; t < L.total_tiles && ok; t += npairs, ++it) {
+            for (int t = pair; t < L.total_tiles && ok; t += npairs) {
                 const Decoded dt = decode_tile(L, t, kElemsPerRow);
                 const TcProblem* P = dt.P;
-                const int acc = it & 1;
-                const uint32_t acc_parity = uint32_t(it >> 1) & 1u;
-                if (!mbar_wait(&tempty[acc], acc_parity ^ 1u, tmo, L.status, vabort)) break;
-                tc_fence_after();
-                const uint32_t tmem_d = tmem_base + uint32_t(acc) * kAccStride;
                 const int n_eff = pair_n(P->tile_n, P->N - (NP * dt.nt + pq) * P->tile_n);
                 const uint32_t idesc = make_idesc_pair(kFmt, uint32_t(n_eff));
-                for (int kb = dt.kb_begin; kb < dt.kb_end; ++kb) {
-                    if (!mbar_wait(&full[stage], phase, tmo, L.status, vabort)) {
+                const int chunk = (P->kb_chunk > 0 && L.chunk_scratch) ? P->kb_chunk
+                                                                        : (dt.kb_end - dt.kb_begin);
+                int kb0 = dt.kb_begin;
+                do {   // one chain per chunk of k-blocks (at least one, even for an empty tile)
+                    const int kb1 = (dt.kb_end - kb0 > chunk) ? kb0 + chunk : dt.kb_end;
+                    const int acc = it & 1;
+                    const uint32_t acc_parity = uint32_t(it >> 1) & 1u;
+                    if (!mbar_wait(&tempty[acc], acc_parity ^ 1u, tmo, L.status, vabort)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const int rem = P->Kred - (kb % dt.kb_per_batch) * kElemsPerRow;
-                    const int steps = min(kStepsPerBlock, (rem + kUmmaK - 1) / kUmmaK);
-                    const uint64_t ah = smem_desc_kmajor<RB>(smem_u32(stage_a(stage, 0)));
-                    const uint64_t bh = smem_desc_kmajor<RB>(smem_u32(stage_b(stage, 0)));
-                    const uint64_t al = kSplit ? smem_desc_kmajor<RB>(smem_u32(stage_a(stage, 1))) : 0;
-                    const uint64_t bl = kSplit ? smem_desc_kmajor<RB>(smem_u32(stage_b(stage, 1))) : 0;
-                    for (int k = 0; k < steps; ++k) {
-                        const uint64_t off = uint64_t(k) * 2;
-                        const uint32_t accum = (kb > dt.kb_begin || k > 0) ? 1u : 0u;
-                        if (MODE == TC_BF16X3) {
-                            mma_bf16_pair(tmem_d, al + off, bh + off, idesc, accum);
-                            mma_bf16_pair(tmem_d, ah + off, bl + off, idesc, 1u);
-                            mma_bf16_pair(tmem_d, ah + off, bh + off, idesc, 1u);
-                        } else if (MODE == TC_TF32) {
-                            mma_tf32_pair(tmem_d, ah + off, bh + off, idesc, accum);
-                        } else {
-                            mma_bf16_pair(tmem_d, ah + off, bh + off, idesc, accum);
+                    const uint32_t tmem_d = tmem_base + uint32_t(acc) * kAccStride;
+                    for (int kb = kb0; kb < kb1; ++kb) {
+                        if (!mbar_wait(&full[stage], phase, tmo, L.status, vabort)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const int rem = P->Kred - (kb % dt.kb_per_batch) * kElemsPerRow;
+                        const int steps = min(kStepsPerBlock, (rem + kUmmaK - 1) / kUmmaK);
+                        const uint64_t ah = smem_desc_kmajor<RB>(smem_u32(stage_a(stage, 0)));
+                        const uint64_t bh = smem_desc_kmajor<RB>(smem_u32(stage_b(stage, 0)));
+                        const uint64_t al = kSplit ? smem_desc_kmajor<RB>(smem_u32(stage_a(stage, 1))) : 0;
+                        const uint64_t bl = kSplit ? smem_desc_kmajor<RB>(smem_u32(stage_b(stage, 1))) : 0;
+                        for (int k = 0; k < steps; ++k) {
+                            const uint64_t off = uint64_t(k) * 2;
+                            const uint32_t accum = (kb > kb0 || k > 0) ? 1u : 0u;
+                            if (MODE == TC_BF16X3) {
+                                mma_bf16_pair(tmem_d, al + off, bh + off, idesc, accum);
+                                mma_bf16_pair(tmem_d, ah + off, bl + off, idesc, 1u);
+                                mma_bf16_pair(tmem_d, ah + off, bh + off, idesc, 1u);
+                            } else if (MODE == TC_TF32) {
+                                mma_tf32_pair(tmem_d, ah + off, bh + off, idesc, accum);
+                            } else {
+                                mma_bf16_pair(tmem_d, ah + off, bh + off, idesc, accum);
+                            }
+                        }
+                        // Test hook: withhold one release so that both producers' bounded
+                        // waits on this stage expire (a barrier that nothing arrives on).
+                        const bool withhold = L.drop_arrival && pair == 0 && it == 0 && kb == kb0;
+                        if (!withhold) mma_commit_pair(&empty[stage], kAllCtas);
+                        if (++stage == stages) {
+                            stage = 0;
+                            phase ^= 1u;
                         }
                     }
-                    // Test hook: withhold one release so that both producers' bounded
-                    // waits on this stage expire (a barrier that nothing arrives on).
-                    const bool withhold = L.drop_arrival && pair == 0 && it == 0 &&
-                                          kb == dt.kb_begin;
-                    if (!withhold) mma_commit_pair(&empty[stage], kAllCtas);
-                    if (++stage == stages) {
-                        stage = 0;
-                        phase ^= 1u;
-                    }
-                }
-                if (!ok) break;
-                mma_commit_pair(&tfull[acc], pair_mask);
+                    if (!ok) break;
+                    mma_commit_pair(&tfull[acc], pair_mask);
+                    ++it;
+                    kb0 = kb1;
+                } while (kb0 < dt.kb_end);
             }
             mma_commit_pair(drain, uint16_t(1u << lead));
             mbar_wait(drain, 0, kDrainTimeoutNs, L.status, zero_flag);
@@ -263,17 +273,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int half = (warp - 2) >> 2;
         const uint32_t tempty_leader0 = mapa_shared(smem_u32(&tempty[0]), lead);
         const uint32_t tempty_leader1 = mapa_shared(smem_u32(&tempty[1]), lead);
-        int it = 0;
-        for (int t = pair; t < L.total_tiles; t += npairs, ++it) {
+        int it = 0;   // accumulation chains consumed, in the MMA issuer's order
+        bool ok = true;
+        // Running sums of a tile's chains, added to in FP32 with round to nearest: this
+        // CTA's 128 x 256 block of the scratch, stored lane-interleaved so that a warp's
+        // 16-byte accesses are contiguous: the float4 j of 32-column chunk ci of lane l of
+        // TMEM lane quadrant q sits at float4 index ((q * 8 + ci) * 8 + j) * 32 + l.
+        float4* scr = L.chunk_scratch
+                          ? reinterpret_cast<float4*>(L.chunk_scratch) +
+                                (int64_t(blockIdx.x) * 4 + quad) * (8 * 8 * 32) + lane
+                          : nullptr;
+        for (int t = pair; t < L.total_tiles && ok; t += npairs) {
             const Decoded dt = decode_tile(L, t, kElemsPerRow);
             const TcProblem* P = dt.P;
-            const int acc = it & 1;
-            const uint32_t acc_parity = uint32_t(it >> 1) & 1u;
-            int ok = 1;
-            if (lane == 0) ok = mbar_wait(&tfull[acc], acc_parity, tmo, L.status, vabort) ? 1 : 0;
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) break;
-            tc_fence_after();
             const int row = dt.mt * (2 * kBM) + int(rank) * kBM + quad * 32 + lane;
             const bool row_ok = row < P->M && dt.kb_begin < dt.kb_end;
             const int n0 = (NP * dt.nt + pq) * P->tile_n;
@@ -289,22 +301,60 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int cdiv = S.col_div;
             const int64_t sch = S.s_col_hi, scl = S.s_col_lo;
             const bool tile_atomic = P->atomic != 0;
-            for (int c = half * 32; c < ncols; c += 64) {
-                uint32_t r[32];
-                tmem_ld_32x32b_x32(tmem_base + uint32_t(acc) * kAccStride +
-                                       (uint32_t(quad * 32) << 16) + uint32_t(c),
-                                   r);
-                tmem_ld_wait();
-                if (!row_ok) continue;
-                const int cmax = min(32, ncols - c);
-                store_chunk<EPI>(L, r, row_base, n0, c, cmax, cdiv, sch, scl, tile_atomic);
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) {
-                if (leader) mbar_arrive(&tempty[acc]);
-                else mbar_arrive_cluster(acc ? tempty_leader1 : tempty_leader0);
-            }
+            const int chunk = (P->kb_chunk > 0 && scr) ? P->kb_chunk : (dt.kb_end - dt.kb_begin);
+            int kb0 = dt.kb_begin;
+            bool first = true;
+            do {
+                const int kb1 = (dt.kb_end - kb0 > chunk) ? kb0 + chunk : dt.kb_end;
+                const bool last = kb1 >= dt.kb_end;
+                const int acc = it & 1;
+                const uint32_t acc_parity = uint32_t(it >> 1) & 1u;
+                int got = 1;
+                if (lane == 0) got = mbar_wait(&tfull[acc], acc_parity, tmo, L.status, vabort) ? 1 : 0;
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                for (int c = half * 32; c < ncols; c += 64) {
+                    uint32_t r[32];
+                    tmem_ld_32x32b_x32(tmem_base + uint32_t(acc) * kAccStride +
+                                           (uint32_t(quad * 32) << 16) + uint32_t(c),
+                                       r);
+                    tmem_ld_wait();
+                    if (!row_ok) continue;
+                    float4* s4 = scr ? scr + (c >> 5) * (8 * 32) : nullptr;
+                    if (!first) {   // add the chains before this one
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const float4 v = s4[j * 32];
+                            r[4 * j] = __float_as_uint(__uint_as_float(r[4 * j]) + v.x);
+                            r[4 * j + 1] = __float_as_uint(__uint_as_float(r[4 * j + 1]) + v.y);
+                            r[4 * j + 2] = __float_as_uint(__uint_as_float(r[4 * j + 2]) + v.z);
+                            r[4 * j + 3] = __float_as_uint(__uint_as_float(r[4 * j + 3]) + v.w);
+                        }
+                    }
+                    if (!last) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            s4[j * 32] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                                __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+                        continue;
+                    }
+                    const int cmax = min(32, ncols - c);
+                    store_chunk<EPI>(L, r, row_base, n0, c, cmax, cdiv, sch, scl, tile_atomic);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    if (leader) mbar_arrive(&tempty[acc]);
+                    else mbar_arrive_cluster(acc ? tempty_leader1 : tempty_leader0);
+                }
+                first = false;
+                ++it;
+                kb0 = kb1;
+            } while (kb0 < dt.kb_end);
         }
     }
 

@@ -111,3 +111,30 @@ def test_pair_full_size_m400_sampled(P, tmp_path, deterministic, npc):
     for prec in ("bf16x3", "tf32"):
         got = run_pair(P, tmp_path, w.U, O32, 4, prec, 240, 208, 128, npc, deterministic=deterministic)
         assert rel_err(got[sample], ref).max() <= TOL[prec], prec
+
+
+@pytest.mark.parametrize("chain", [None, 0, 256])
+def test_long_reduction_chained_accumulation(P, chain):
+    # m = 800, d = 4: the second product reduces over m*d = 3200 elements.  With the
+    # default chain length (1024) the tensor core sums at most 1024 of them per FP32
+    # accumulator and the chains are added in FP32 registers-to-scratch with round to
+    # nearest: BF16x3 stays within 1e-5 of the oracle.  chain = 0 (one chain) is
+    # checked against its own, looser bound.
+    m, d, mp, K = 800, 4, 800, 6
+    rng = np.random.default_rng(4242)
+    U = orthonormal_columns(rng, m * d, mp)
+    O = rng.standard_normal((K, m, m)).astype(np.float32)
+    sample = [0, 3, 5]
+    ref = oracle.rotate_dense(U, O[sample].astype(np.float64), d)
+    h = P.Handle()
+    try:
+        if chain is not None:
+            P.dmrg_set_option("accum_chain", chain, handle=h)
+        out = P.dmrg_rotate_ops(torch.from_numpy(U).cuda(), torch.from_numpy(O).cuda(), d, "bf16x3",
+                                handle=h)
+        torch.cuda.synchronize()
+        P.dmrg_sync_status(handle=h)
+        err = rel_err(out[sample].double().cpu().numpy(), ref).max()
+        assert err <= (3e-5 if chain == 0 else 1e-5), (chain, err)
+    finally:
+        h.close()
