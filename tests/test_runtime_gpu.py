@@ -193,3 +193,43 @@ def test_deterministic_option_and_tail_split(P):
         assert torch.equal(a[:140], b[:140])   # tiles outside the last wave are untouched
     finally:
         h.close()
+
+
+def test_graph_replay_blocked_and_backward(P):
+    # The block-sparse rotation (grouped launches) and the adjoint are captured into
+    # CUDA graphs like the dense rotation: replays equal the eager results (the
+    # block-sparse path bit for bit; the adjoint's dU sums split parts with atomics,
+    # so to rounding).
+    from workloads import blocked_config
+    w = blocked_config("blocked_m1000_k200_s1.2")
+    dev = torch.device("cuda")
+    Ub = torch.from_numpy(w.U_blocks).to(dev)
+    Ob = torch.from_numpy(w.O_blocks).to(dev, torch.float32)
+    h = P.Handle()
+    try:
+        plan = P.dmrg_blocked_plan_create(w.block_sectors, w.site_shifts, w.kept_sectors, w.op_shifts,
+                                          handle=h)
+        eager = P.dmrg_rotate_ops_blocked(plan, Ub, Ob, "bf16x3").clone()
+        P.dmrg_set_option("graph", 1, handle=h)
+        out = torch.empty_like(eager)
+        for _ in range(3):
+            out.zero_()
+            P.dmrg_rotate_ops_blocked(plan, Ub, Ob, "bf16x3", out=out)
+            torch.cuda.synchronize()
+            assert torch.equal(out, eager)
+        plan.close()
+        # adjoint
+        wd, U, O = _inputs(m=96, mp=80, K=9)
+        G = torch.randn(9, 80, 80, device=dev)
+        P.dmrg_set_option("graph", 0, handle=h)
+        dO0, dU0 = P.dmrg_rotate_ops_backward(U, O, G, 4, "bf16x3", handle=h)
+        dO0, dU0 = dO0.clone(), dU0.clone()
+        P.dmrg_set_option("graph", 1, handle=h)
+        for _ in range(2):
+            dO, dU = P.dmrg_rotate_ops_backward(U, O, G, 4, "bf16x3", handle=h)
+            torch.cuda.synchronize()
+            assert torch.allclose(dO, dO0, rtol=0, atol=1e-6 * dO0.abs().max().item())
+            assert torch.allclose(dU, dU0, rtol=0, atol=1e-6 * dU0.abs().max().item())
+        P.dmrg_sync_status(handle=h)
+    finally:
+        h.close()
