@@ -72,11 +72,14 @@ def test_ragged_shapes(lib, shape, prec):
     assert rel_err(got, ref).max() <= TOL[prec]
 
 
-def test_fp32_input_for_tensor_core_paths(lib):
-    w = dense_workload("t", 77, 4, 96, 80, 6)
-    ref = oracle.rotate_dense(w.U, w.O.astype(np.float32).astype(np.float64), 4)
+@pytest.mark.parametrize("m", [77, 96])
+def test_fp32_input_for_tensor_core_paths(lib, m):
+    # FP32 operators: packed (m = 77), or read in place by the TF32 first product when
+    # their rows are 16-byte aligned (m = 96)
+    w = dense_workload("t", 77, 3, m, 80, 6)
+    ref = oracle.rotate_dense(w.U, w.O.astype(np.float32).astype(np.float64), 3)
     for prec in ("bf16x3", "tf32"):
-        got = run(lib, w.U, w.O, 4, prec, torch.float32)
+        got = run(lib, w.U, w.O, 3, prec, torch.float32)
         assert rel_err(got, ref).max() <= TOL[prec]
 
 
