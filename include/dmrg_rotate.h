@@ -340,10 +340,14 @@ DMRG_API dmrg_status dmrg_structure_factor(dmrg_handle handle, const double* G, 
  *           (= 1 - sum of the kept eigenvalues for a normalized state);
  *   sweeps  host (may be NULL): sweeps done; -max_sweeps if the off-diagonal part
  *           did not fall below tol * ||rho||_F (the outputs then hold the last
- *           iterate).
- * The call waits for the stream once per sweep (the convergence test), so it is not
- * graph-capturable.  Errors: DMRG_ERR_SHAPE unless 1 <= mp <= rows;
- * DMRG_ERR_INVALID_ARG for NULL outputs, tol <= 0 or max_sweeps < 1. */
+ *           iterate).  A sweep that rotates no pair (every |rho_ab| at or below
+ *           DBL_EPSILON * sqrt(|rho_aa rho_bb|)) also ends the iteration.
+ * Each sweep is one cooperative launch whose rounds meet at a grid-wide barrier with
+ * a bounded wait.  The call waits for the stream once per sweep (the convergence
+ * test), so it is not graph-capturable.  Errors: DMRG_ERR_SHAPE unless
+ * 1 <= mp <= rows; DMRG_ERR_INVALID_ARG for NULL outputs, tol <= 0 or
+ * max_sweeps < 1; DMRG_ERR_TIMEOUT if a barrier wait expired (the outputs are then
+ * undefined); DMRG_ERR_CUDA if the device cannot run cooperative launches. */
 DMRG_API dmrg_status dmrg_truncation_workspace(dmrg_handle handle, int64_t rows, int64_t cols,
                                       size_t* bytes);
 DMRG_API dmrg_status dmrg_truncation(dmrg_handle handle, const double* Psi, int64_t rows,

@@ -4,32 +4,47 @@
 // discarded weight eps_rho (Eq. error).
 //
 // The eigen-decomposition is the cyclic Jacobi method in FP64.  A sweep visits every
-// pair (p, q) once, in N - 1 rounds of N / 2 disjoint pairs (the round-robin "circle"
-// schedule, N = n rounded up to even; pairs with the padding index are skipped).  In a
-// round every pair's rotation J (the stable 2 x 2 symmetric Schur step: the angle that
-// zeroes a_pq) is computed from the current matrix, then applied as A <- J^T A (a pass
-// over row pairs), A <- A J and V <- V J (a pass over column pairs).  The sweeps stop
-// when the off-diagonal part is below tol * ||A||_F.  Eigenvalues are ranked on the
-// device, and U's columns are V's columns in decreasing eigenvalue order, each with its
-// largest-magnitude component positive (the first such index on ties).
+// pair of indices once, in N - 1 rounds of N / 2 disjoint pairs (the round-robin
+// "circle" schedule, N = n rounded up to even; the padding index pairs with nobody).
+// In a round every pair's rotation J (the stable 2 x 2 symmetric Schur step: the angle
+// that zeroes a_ab) is computed from the current matrix, and the whole round is applied
+// at once, A <- J^T A J and V <- V J.  A pair whose a_ab is below the rounding level of
+// its diagonal, a_ab^2 <= eps^2 |a_aa a_bb|, is not rotated.  The sweeps stop when
+// the off-diagonal part is below tol * ||A||_F, or when a sweep rotated no pair.
+// Eigenvalues are ranked on the device, and U's columns are V's columns in decreasing
+// eigenvalue order, each with its largest-magnitude component positive (the first such
+// index on ties).
+//
+// One sweep is one cooperative launch.  The rounds are separated by a grid-wide barrier
+// (bounded wait), and A is double-buffered: a round reads A_in and writes A_out, so
+// every block can compute the rotations it needs from A_in without waiting for anyone.
+// Within a round, the pairs are cut into tiles of kPT pairs; an A work item is a tile
+// pair (I <= K) and transforms its 2 x 2 blocks J_i^T A[{a_i,b_i},{a_k,b_k}] J_k, writing
+// both triangles; a V work item is 64 rows of V times one tile of pairs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 
 #include "api_common.h"
+#include "ptx.cuh"
 
 using namespace dmrg;
 
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kPT = 16;          // pairs per tile side (kPT * kPT = kThreads)
+constexpr int kVRows = 64;       // rows of V per work item
+constexpr int kMaxBlocksPerSm = 3;
 
-// Pair i of round r in the circle schedule on N (even) indices: index N - 1 is fixed,
-// the others turn.  Every pair of indices meets exactly once in rounds 0 .. N - 2.
-__device__ __forceinline__ void round_pair(int64_t N, int64_t r, int64_t i, int64_t& p, int64_t& q) {
-    const int64_t M = N - 1;
-    int64_t a, b;
+// Slot i of round r on N (even) indices: index N - 1 stays, the others turn, and every
+// pair of indices meets exactly once in rounds 0 .. N - 2.  For i >= 1 the first index
+// (r + i) mod (N - 1) ascends with i and the second (r - i) mod (N - 1) descends, so a
+// tile of consecutive slots reads two runs of neighbouring columns.
+__device__ __forceinline__ void slot_indices(int N, int r, int i, int& a, int& b) {
+    const int M = N - 1;
     if (i == 0) {
         a = M;
         b = r;
@@ -37,107 +52,262 @@ __device__ __forceinline__ void round_pair(int64_t N, int64_t r, int64_t i, int6
         a = (r + i) % M;
         b = (r - i + M) % M;
     }
-    p = a < b ? a : b;
-    q = a < b ? b : a;
+}
+
+struct Rot {
+    double c, s, t;   // J = [[c, s], [-s, c]], t = s / c
+    int a, b;         // -1 for the padding index
+};
+
+__device__ Rot slot_rotation(const double* __restrict__ A, int n, int N, int npair, int r, int slot) {
+    Rot R{1.0, 0.0, 0.0, -1, -1};
+    if (slot >= npair) return R;
+    int a, b;
+    slot_indices(N, r, slot, a, b);
+    R.a = a < n ? a : -1;
+    R.b = b < n ? b : -1;
+    if (R.a < 0 || R.b < 0) return R;
+    const double g = __ldcg(A + size_t(a) * n + b);
+    const double al = __ldcg(A + size_t(a) * n + a);
+    const double be = __ldcg(A + size_t(b) * n + b);
+    if (!(g * g > (DBL_EPSILON * DBL_EPSILON) * fabs(al * be))) return R;
+    const double tau = (be - al) / (2.0 * g);
+    double t;
+    if (fabs(tau) > 1e150) {
+        t = 0.5 / tau;
+    } else {
+        t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+    }
+    R.c = 1.0 / sqrt(1.0 + t * t);
+    R.s = t * R.c;
+    R.t = t;
+    return R;
+}
+
+// A rotation written by another block in this launch: read through L2.
+__device__ __forceinline__ Rot ld_rot(const Rot* p) {
+    Rot R;
+    R.c = __ldcg(&p->c);
+    R.s = __ldcg(&p->s);
+    R.t = __ldcg(&p->t);
+    R.a = __ldcg(&p->a);
+    R.b = __ldcg(&p->b);
+    return R;
+}
+
+// Barrier state of one sweep, zeroed before the launch; the sweep's results follow it.
+struct SweepSync {
+    unsigned count, gen;
+    int abort, pad;
+    double off2, all2;              // sum of squares off the diagonal, and in total
+    unsigned long long rotations;   // pairs rotated in the sweep
+};
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier of a cooperative launch.  The wait is bounded: on expiry it records
+// the timeout in *status, raises the sweep's abort flag, and every block returns false
+// (blocks still on their way see the flag at the barrier and return too).
+__device__ bool grid_barrier(SweepSync* sy, unsigned& gen_seen, uint64_t timeout_ns, unsigned* status) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        const unsigned g = gen_seen;
+        __threadfence();
+        if (atomicAdd(&sy->count, 1u) == gridDim.x - 1) {
+            atomicExch(&sy->count, 0u);
+            __threadfence();
+            atomicAdd(&sy->gen, 1u);
+        } else {
+            const uint64_t t0 = globaltimer_ns();
+            uint32_t spins = 0;
+            while (ld_acquire_gpu(&sy->gen) == g) {
+                if ((++spins & 31u) == 0) {
+                    if (*reinterpret_cast<volatile int*>(&sy->abort)) {
+                        ok = 0;
+                        break;
+                    }
+                    if (globaltimer_ns() - t0 > timeout_ns) {
+                        atomicOr(status, DMRG_DEV_ERR_TIMEOUT);
+                        atomicExch(&sy->abort, 1);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        gen_seen = g + 1;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+struct SweepArgs {
+    double* A[2];       // the sweep reads A[cur] first; round r writes A[(cur + r + 1) & 1]
+    double* V;
+    double* partials;   // 3 per block: off2, all2 of its last-round entries, rotations
+    Rot* rots;          // the round's rotations, npair of them
+    SweepSync* sync;
+    unsigned* status;
+    uint64_t timeout_ns;
+    int n, N, npair, npt, n_atiles, n_vtiles, cur;
+};
+
+// Tile pair (I, K), I <= K, of linear index x over the upper triangle.
+__device__ __forceinline__ void tri_index(int x, int& I, int& K) {
+    int k = int((sqrtf(8.0f * float(x) + 1.0f) - 1.0f) * 0.5f);   // FP32 guess, fixed below
+    while (k * (k + 1) / 2 > x) --k;
+    while ((k + 1) * (k + 2) / 2 <= x) ++k;
+    K = k;
+    I = x - k * (k + 1) / 2;
+}
+
+__global__ void __launch_bounds__(kThreads) jacobi_sweep_kernel(SweepArgs P) {
+    __shared__ Rot rot[2 * kPT];
+    __shared__ double red[3][kThreads / 32];
+    const int n = P.n;
+    const int tid = threadIdx.x;
+    unsigned gen_seen = 0;
+    double off2 = 0.0, all2 = 0.0, nrot = 0.0;
+    const int items = P.n_atiles + P.n_vtiles;
+    for (int r = 0; r < P.N - 1; ++r) {
+        const bool odd = ((P.cur + r) & 1) != 0;
+        const double* __restrict__ Ain = odd ? P.A[1] : P.A[0];
+        double* __restrict__ Aout = odd ? P.A[0] : P.A[1];
+        const bool last = r == P.N - 2;
+        // phase 1: every pair's rotation, once
+        // (slot-major over blocks, so that every SM takes a few of the FP64 divide chains)
+        for (int slot = tid * gridDim.x + blockIdx.x; slot < P.npair; slot += gridDim.x * kThreads) {
+            const Rot R = slot_rotation(Ain, n, P.N, P.npair, r, slot);
+            if (R.s != 0.0) nrot += 1.0;
+            P.rots[slot] = R;
+        }
+        if (!grid_barrier(P.sync, gen_seen, P.timeout_ns, P.status)) return;
+        // phase 2: A <- J^T A J and V <- V J
+        for (int item = blockIdx.x; item < items; item += gridDim.x) {
+            if (item < P.n_atiles) {
+                int I, K;
+                tri_index(item, I, K);
+                if (tid < 2 * kPT) {
+                    const int slot = (tid < kPT ? I : K) * kPT + (tid & (kPT - 1));
+                    if (slot < P.npair) rot[tid] = ld_rot(P.rots + slot);
+                }
+                __syncthreads();
+                const int i = tid / kPT, k = tid % kPT;
+                const int si = I * kPT + i, sk = K * kPT + k;
+                if (si < P.npair && sk < P.npair && !(I == K && i > k)) {
+                    const Rot Ri = rot[i], Rk = rot[kPT + k];
+                    auto ld = [=](int x, int y) {
+                        return (x >= 0 && y >= 0) ? __ldcg(Ain + size_t(x) * n + y) : 0.0;
+                    };
+                    auto st = [=](int x, int y, double v) {
+                        if (x >= 0 && y >= 0) __stcg(Aout + size_t(x) * n + y, v);
+                    };
+                    if (si == sk) {
+                        double x00 = ld(Ri.a, Ri.a), x11 = ld(Ri.b, Ri.b), x01 = ld(Ri.a, Ri.b);
+                        if (Ri.s != 0.0) {
+                            x00 -= Ri.t * x01;
+                            x11 += Ri.t * x01;
+                            x01 = 0.0;
+                        }
+                        st(Ri.a, Ri.a, x00);
+                        st(Ri.b, Ri.b, x11);
+                        st(Ri.a, Ri.b, x01);
+                        st(Ri.b, Ri.a, x01);
+                        if (last) {
+                            const double o = (Ri.a >= 0 && Ri.b >= 0) ? 2.0 * x01 * x01 : 0.0;
+                            off2 += o;
+                            all2 += o + (Ri.a >= 0 ? x00 * x00 : 0.0) + (Ri.b >= 0 ? x11 * x11 : 0.0);
+                        }
+                    } else {
+                        const double x00 = ld(Ri.a, Rk.a), x01 = ld(Ri.a, Rk.b);
+                        const double x10 = ld(Ri.b, Rk.a), x11 = ld(Ri.b, Rk.b);
+                        // right factor J_k on the two rows, then left factor J_i^T
+                        const double y00 = Rk.c * x00 - Rk.s * x01, y01 = Rk.s * x00 + Rk.c * x01;
+                        const double y10 = Rk.c * x10 - Rk.s * x11, y11 = Rk.s * x10 + Rk.c * x11;
+                        const double z00 = Ri.c * y00 - Ri.s * y10, z01 = Ri.c * y01 - Ri.s * y11;
+                        const double z10 = Ri.s * y00 + Ri.c * y10, z11 = Ri.s * y01 + Ri.c * y11;
+                        st(Ri.a, Rk.a, z00);
+                        st(Ri.a, Rk.b, z01);
+                        st(Ri.b, Rk.a, z10);
+                        st(Ri.b, Rk.b, z11);
+                        st(Rk.a, Ri.a, z00);
+                        st(Rk.b, Ri.a, z01);
+                        st(Rk.a, Ri.b, z10);
+                        st(Rk.b, Ri.b, z11);
+                        if (last) {
+                            // padding entries were loaded as 0 and stay 0
+                            const double o = 2.0 * (z00 * z00 + z01 * z01 + z10 * z10 + z11 * z11);
+                            off2 += o;
+                            all2 += o;
+                        }
+                    }
+                }
+                __syncthreads();
+            } else {
+                const int v = item - P.n_atiles;
+                const int R = v / P.npt, K = v % P.npt;
+                if (tid < kPT && K * kPT + tid < P.npair) rot[tid] = ld_rot(P.rots + K * kPT + tid);
+                __syncthreads();
+                const int sk = K * kPT + tid % kPT;
+                const Rot Rk = rot[tid % kPT];
+                if (sk < P.npair && Rk.s != 0.0) {
+                    for (int j = 0; j < kVRows / (kThreads / kPT); ++j) {
+                        const int row = R * kVRows + tid / kPT + j * (kThreads / kPT);
+                        if (row >= n) break;
+                        double* va = P.V + size_t(row) * n + Rk.a;
+                        double* vb = P.V + size_t(row) * n + Rk.b;
+                        const double x = __ldcg(va), y = __ldcg(vb);
+                        __stcg(va, Rk.c * x - Rk.s * y);
+                        __stcg(vb, Rk.s * x + Rk.c * y);
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (last) {
+            // per-block partial sums of the final matrix, combined in block order below
+            for (int o = 16; o > 0; o >>= 1) {
+                off2 += __shfl_xor_sync(0xffffffffu, off2, o);
+                all2 += __shfl_xor_sync(0xffffffffu, all2, o);
+                nrot += __shfl_xor_sync(0xffffffffu, nrot, o);
+            }
+            if ((tid & 31) == 0) {
+                red[0][tid >> 5] = off2;
+                red[1][tid >> 5] = all2;
+                red[2][tid >> 5] = nrot;
+            }
+            __syncthreads();
+            if (tid < 3) {
+                double acc = 0.0;
+                for (int w = 0; w < kThreads / 32; ++w) acc += red[tid][w];
+                P.partials[3 * blockIdx.x + tid] = acc;
+            }
+        }
+        if (!grid_barrier(P.sync, gen_seen, P.timeout_ns, P.status)) return;
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+        double o = 0.0, a = 0.0, q = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) {
+            o += __ldcg(P.partials + 3 * b);
+            a += __ldcg(P.partials + 3 * b + 1);
+            q += __ldcg(P.partials + 3 * b + 2);
+        }
+        P.sync->off2 = o;
+        P.sync->all2 = a;
+        P.sync->rotations = static_cast<unsigned long long>(q);
+    }
 }
 
 __global__ void identity_kernel(double* V, int64_t n) {
     const int64_t x = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (x < n * n) V[x] = (x / n == x % n) ? 1.0 : 0.0;
-}
-
-// Rotation of every pair of round r: cs[2i] = c, cs[2i+1] = s, pq[2i] = p, pq[2i+1] = q
-// (p = q = -1 for a skipped pair).
-__global__ void angles_kernel(const double* __restrict__ A, int64_t n, int64_t N, int64_t r,
-                              double* __restrict__ cs, int64_t* __restrict__ pq) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= N / 2) return;
-    int64_t p, q;
-    round_pair(N, r, i, p, q);
-    double c = 1.0, s = 0.0;
-    if (q < n) {
-        const double apq = A[p * n + q];
-        if (apq != 0.0) {
-            const double tau = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
-            double t;
-            if (fabs(tau) > 1e150) {
-                t = 0.5 / tau;
-            } else {
-                t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            }
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
-        }
-    } else {
-        p = q = -1;
-    }
-    cs[2 * i] = c;
-    cs[2 * i + 1] = s;
-    pq[2 * i] = p;
-    pq[2 * i + 1] = q;
-}
-
-// A <- J^T A on the rows of every pair: thread per (pair, column), columns fastest.
-__global__ void row_pass_kernel(double* __restrict__ A, int64_t n, int64_t npair,
-                                const double* __restrict__ cs, const int64_t* __restrict__ pq) {
-    const int64_t x = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (x >= npair * n) return;
-    const int64_t i = x / n, j = x - (x / n) * n;
-    const int64_t p = pq[2 * i], q = pq[2 * i + 1];
-    if (p < 0) return;
-    const double c = cs[2 * i], s = cs[2 * i + 1];
-    const double a = A[p * n + j], b = A[q * n + j];
-    A[p * n + j] = c * a - s * b;
-    A[q * n + j] = s * a + c * b;
-}
-
-// A <- A J and V <- V J on the columns of every pair: thread per (row, pair), pairs
-// fastest (one row per warp stays in L1).
-__global__ void col_pass_kernel(double* __restrict__ A, double* __restrict__ V, int64_t n,
-                                int64_t npair, const double* __restrict__ cs,
-                                const int64_t* __restrict__ pq) {
-    const int64_t x = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (x >= npair * n) return;
-    const int64_t row = x / npair, i = x - (x / npair) * npair;
-    const int64_t p = pq[2 * i], q = pq[2 * i + 1];
-    if (p < 0) return;
-    const double c = cs[2 * i], s = cs[2 * i + 1];
-    double a = A[row * n + p], b = A[row * n + q];
-    A[row * n + p] = c * a - s * b;
-    A[row * n + q] = s * a + c * b;
-    a = V[row * n + p];
-    b = V[row * n + q];
-    V[row * n + p] = c * a - s * b;
-    V[row * n + q] = s * a + c * b;
-}
-
-// out[0] = sum_{i != j} A_ij^2, out[1] = sum A_ij^2 (one block).
-__global__ void off_norm_kernel(const double* __restrict__ A, int64_t n, double* __restrict__ out) {
-    double off = 0.0, all = 0.0;
-    for (int64_t x = threadIdx.x; x < n * n; x += blockDim.x) {
-        const double v = A[x] * A[x];
-        all += v;
-        if (x / n != x % n) off += v;
-    }
-    __shared__ double red[2][kThreads / 32];
-    for (int o = 16; o > 0; o >>= 1) {
-        off += __shfl_xor_sync(0xffffffffu, off, o);
-        all += __shfl_xor_sync(0xffffffffu, all, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        red[0][threadIdx.x >> 5] = off;
-        red[1][threadIdx.x >> 5] = all;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) {
-            a += red[0][w];
-            b += red[1][w];
-        }
-        out[0] = a;
-        out[1] = b;
-    }
 }
 
 // Rank of every eigenvalue in decreasing order (ties by index): lambda[rank] = d_i,
@@ -215,25 +385,45 @@ __global__ void discarded_kernel(const double* __restrict__ lambda, int64_t n, i
     }
 }
 
+constexpr int kMaxSweepBlocks = 4096;
+
 struct TruncDims {
-    int64_t N, npair;
+    int N, npair, npt, n_atiles, n_vtiles;
     WsLayout ws;
 };
 
 TruncDims trunc_dims(int64_t rows) {
     TruncDims D;
-    D.N = rows + (rows & 1);
+    D.N = int(rows + (rows & 1));
     D.npair = D.N / 2;
-    D.ws.add("A", size_t(rows) * rows * 8);
+    D.npt = (D.npair + kPT - 1) / kPT;
+    D.n_atiles = D.npt * (D.npt + 1) / 2;
+    D.n_vtiles = int((rows + kVRows - 1) / kVRows) * D.npt;
+    D.ws.add("A0", size_t(rows) * rows * 8);
+    D.ws.add("A1", size_t(rows) * rows * 8);
     D.ws.add("V", size_t(rows) * rows * 8);
-    D.ws.add("cs", size_t(D.npair) * 2 * 8);
-    D.ws.add("pq", size_t(D.npair) * 2 * 8);
-    D.ws.add("norms", 2 * 8);
+    D.ws.add("sync", sizeof(SweepSync));
+    D.ws.add("partials", size_t(kMaxSweepBlocks) * 3 * 8);
     D.ws.add("col", size_t(rows) * 8);
+    D.ws.add("rots", size_t(D.npair) * sizeof(Rot));
     return D;
 }
 
 unsigned blocks_for(int64_t n) { return unsigned((n + kThreads - 1) / kThreads); }
+
+// Blocks of one sweep launch: every block must be resident at once (cooperative launch).
+cudaError_t sweep_grid(int items, int* grid) {
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_sweep_kernel, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (!coop || per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    *grid = std::min({items, sms * std::min(per_sm, kMaxBlocksPerSm), kMaxSweepBlocks});
+    return cudaSuccess;
+}
 
 }  // namespace
 
@@ -261,35 +451,59 @@ dmrg_status dmrg_truncation(dmrg_handle h, const double* Psi, int64_t rows, int6
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const TruncDims D = trunc_dims(rows);
     char* base = static_cast<char*>(ws);
-    double* A = reinterpret_cast<double*>(base + D.ws.offsets[0]);
-    double* V = reinterpret_cast<double*>(base + D.ws.offsets[1]);
-    double* cs = reinterpret_cast<double*>(base + D.ws.offsets[2]);
-    int64_t* pq = reinterpret_cast<int64_t*>(base + D.ws.offsets[3]);
-    double* norms = reinterpret_cast<double*>(base + D.ws.offsets[4]);
+    double* A0 = reinterpret_cast<double*>(base + D.ws.offsets[0]);
+    double* A1 = reinterpret_cast<double*>(base + D.ws.offsets[1]);
+    double* V = reinterpret_cast<double*>(base + D.ws.offsets[2]);
+    SweepSync* sync = reinterpret_cast<SweepSync*>(base + D.ws.offsets[3]);
+    double* partials = reinterpret_cast<double*>(base + D.ws.offsets[4]);
     int64_t* col = reinterpret_cast<int64_t*>(base + D.ws.offsets[5]);
+    Rot* rots = reinterpret_cast<Rot*>(base + D.ws.offsets[6]);
     const int64_t n = rows;
-    cudaError_t e = timed_launch(h, "trunc_rho", s, [&] { return rho_launch(Psi, rows, cols, 0, A, s); });
+    cudaError_t e = timed_launch(h, "trunc_rho", s, [&] { return rho_launch(Psi, rows, cols, 0, A0, s); });
     if (e != cudaSuccess) return cuda_fail(h, e, "reduced density matrix");
     identity_kernel<<<blocks_for(n * n), kThreads, 0, s>>>(V, n);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "identity");
+    int grid = 0;
+    if (n > 1 && (e = sweep_grid(D.n_atiles + D.n_vtiles, &grid)) != cudaSuccess)
+        return cuda_fail(h, e, "cooperative launch size");
+    SweepArgs P{};
+    P.A[0] = A0;
+    P.A[1] = A1;
+    P.V = V;
+    P.partials = partials;
+    P.rots = rots;
+    P.sync = sync;
+    P.status = h->d_status;
+    P.timeout_ns = timeout_ns(h);
+    P.n = int(n);
+    P.N = D.N;
+    P.npair = D.npair;
+    P.npt = D.npt;
+    P.n_atiles = D.n_atiles;
+    P.n_vtiles = D.n_vtiles;
+    P.cur = 0;
     int done = -max_sweeps;
-    double host_norms[2] = {0.0, 0.0};
+    SweepSync host{};
     for (int sweep = 0; sweep < max_sweeps && n > 1; ++sweep) {
-        for (int64_t r = 0; r < D.N - 1; ++r) {
-            angles_kernel<<<blocks_for(D.npair), kThreads, 0, s>>>(A, n, D.N, r, cs, pq);
-            row_pass_kernel<<<blocks_for(D.npair * n), kThreads, 0, s>>>(A, n, D.npair, cs, pq);
-            col_pass_kernel<<<blocks_for(D.npair * n), kThreads, 0, s>>>(A, V, n, D.npair, cs, pq);
-        }
-        off_norm_kernel<<<1, kThreads, 0, s>>>(A, n, norms);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "Jacobi sweep");
-        e = cudaMemcpyAsync(host_norms, norms, sizeof host_norms, cudaMemcpyDeviceToHost, s);
+        e = cudaMemsetAsync(sync, 0, sizeof(SweepSync), s);
+        if (e == cudaSuccess)
+            e = timed_launch(h, "trunc_sweep", s, [&] {
+                void* args[] = {&P};
+                return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(jacobi_sweep_kernel),
+                                                   dim3(unsigned(grid)), dim3(kThreads), args, 0, s);
+            });
+        if (e != cudaSuccess) return cuda_fail(h, e, "Jacobi sweep");
+        P.cur = (P.cur + D.N - 1) & 1;
+        e = cudaMemcpyAsync(&host, sync, sizeof host, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(h, e, "convergence test");
-        if (host_norms[0] <= tol * tol * host_norms[1]) {
+        if (host.abort) return fail(h, DMRG_ERR_TIMEOUT, "a Jacobi sweep's grid barrier timed out");
+        if (host.off2 <= tol * tol * host.all2 || host.rotations == 0) {
             done = sweep + 1;
             break;
         }
     }
+    const double* A = P.A[P.cur];
     if (n == 1) done = 0;
     rank_kernel<<<blocks_for(n), kThreads, 0, s>>>(A, n, lambda, col);
     gather_kernel<<<unsigned(mp), kThreads, 0, s>>>(V, n, col, mp, U);
