@@ -239,7 +239,7 @@ def run_blocked(args):
         row = {"problems_first": n1, "problems_second": n2, "flops_per_call": flops,
                "sectors": len(w.block_sectors), "operators": w.K,
                "block_rows_max": max(s[2] for s in w.block_sectors)}
-        for prec in ("bf16x3", "tf32", "fp32", "fp64"):
+        for prec in ([args.precision] if args.precision else ("bf16x3", "tf32", "fp32", "fp64")):
             O = O64 if prec == "fp64" else O32
             out = P.dmrg_rotate_ops_blocked(plan, Ub, O, prec)
             ms = _timed(lambda: P.dmrg_rotate_ops_blocked(plan, Ub, O, prec, out=out),
@@ -278,7 +278,8 @@ def run_backward(args):
     dO_ref, dU_ref = P.dmrg_rotate_ops_backward(U, O32.double(), G32.double(), w.d, "fp64")
     fwd_product = 2.0 * w.K * w.m * (w.d * w.mp) * w.m
     res = {}
-    for prec in ("bf16x3", "tf32", "fp32"):
+    precs = [args.precision] if args.precision else ["bf16x3", "tf32", "fp32", "fp64"]
+    for prec in [p for p in precs if p != "fp64"]:
         dO, dU = P.dmrg_rotate_ops_backward(U, O32, G32, w.d, prec)
         ms = _timed(lambda: P.dmrg_rotate_ops_backward(U, O32, G32, w.d, prec), steps, 3, flush)
         P.dmrg_sync_status()
@@ -290,11 +291,253 @@ def run_backward(args):
                      "dO_max_rel_fro_err": float((num / den).max()),
                      "dU_rel_fro_err": float((torch.linalg.vector_norm(dU - dU_ref) /
                                               torch.linalg.vector_norm(dU_ref)).item())}
-    t64 = _timed(lambda: P.dmrg_rotate_ops_backward(U, O32.double(), G32.double(), w.d, "fp64"), 1, 1, flush)
-    res["fp64"] = {"ms_per_call": t64, "ops_per_s": w.K / (t64 * 1e-3)}
+    if "fp64" in precs:
+        t64 = _timed(lambda: P.dmrg_rotate_ops_backward(U, O32.double(), G32.double(), w.d, "fp64"),
+                     1, 1, flush)
+        res["fp64"] = {"ms_per_call": t64, "ops_per_s": w.K / (t64 * 1e-3)}
     line = {"workload": "backward dense_m400_k150 (d=4, m=m'=400, K=150, upstream N(0,1))",
             "metric": "adjoint: ms per call (dO and dU), rotated operators/s",
             "steps": steps, "l2": "flushed between timed calls", "results": res, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _kernel_report(timed_calls):
+    """Per-kernel CUDA-event totals (ms per call and launches per call) over
+    `timed_calls` calls, from the handle's kernel timing."""
+    import paper_0909_5662_gb300 as P
+    kt = P.dmrg_kernel_timing(reset=True)
+    return {k["kernel"]: {"ms_per_call": k["total_ms"] / timed_calls,
+                          "launches_per_call": k["launches"] / timed_calls,
+                          "ms_per_launch": k["total_ms"] / k["launches"]} for k in kt}
+
+
+def _with_kernel_timing(fn, calls, flush):
+    """Runs fn `calls` times with per-kernel events on (L2 flushed before each call)."""
+    import torch
+    import paper_0909_5662_gb300 as P
+    P.dmrg_kernel_timing(reset=True)
+    P.dmrg_set_option("kernel_timing", 1)
+    for _ in range(calls):
+        flush.zero_()
+        fn()
+    torch.cuda.synchronize()
+    P.dmrg_set_option("kernel_timing", 0)
+    return _kernel_report(calls)
+
+
+# FP64 arithmetic has no measured peak on this part: the denominator of FP64-bound
+# kernels is the nominal GB300 rate (1.25 TFLOP/s, an FMA counted as 2 flops).
+FP64_NOMINAL_GFLOPS = 1250.0
+
+
+def run_truncation(args):
+    """The truncation matrix (Sec. 2, steps 3-4): rho = Psi Psi^T of a superblock
+    state with a ground-state-like Schmidt spectrum, its Jacobi eigen-decomposition
+    in FP64, the kept m' eigenvectors and the discarded weight.  Time per call, the
+    sweep kernel's FP64 rate against the nominal FP64 peak, and the FP64 CPU oracle
+    (the library eigh on the host cores) on the same state."""
+    import numpy as np
+    import torch
+    import paper_0909_5662_gb300 as P
+    import oracle
+    from workloads import schmidt_state, SEED_BASE
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    steps = max(1, min(args.steps, 5))
+    res = {}
+    for n, mp in ((400, 100), (1600, 400)):
+        name = "truncation_n%d_mp%d" % (n, mp)
+        Psi_np = schmidt_state(SEED_BASE + 8, n, n)
+        Psi = torch.from_numpy(Psi_np).to(dev)
+        U, lam, eps, sweeps = P.dmrg_truncation(Psi, mp)
+        ms = _timed(lambda: P.dmrg_truncation(Psi, mp), steps, 1, flush)
+        kt = _with_kernel_timing(lambda: P.dmrg_truncation(Psi, mp), 1, flush)
+        P.dmrg_sync_status()
+        N = n + (n & 1)
+        npair = N // 2
+        # a rotation applied to a pair of entries is 6 flops: 4 per 2 x 2 block of A on
+        # the upper triangle of pairs (both triangles are written from it), 1 per
+        # (row, pair) of V; N - 1 rounds per sweep
+        flops_sweep = (N - 1) * (24.0 * npair * (npair + 1) / 2 + 6.0 * n * npair)
+        sw = kt.get("trunc_sweep", {})
+        achieved = flops_sweep / (sw["ms_per_launch"] * 1e-3) / 1e9 if sw else None
+        if args.no_cpu_baseline:
+            lam_ref, eps_ref, t_cpu = lam.cpu().numpy(), float(eps.item()), float("nan")
+        else:
+            t0 = time.perf_counter()
+            U_ref, lam_ref, eps_ref = oracle.truncation(Psi_np, mp)
+            t_cpu = time.perf_counter() - t0
+        rho = Psi @ Psi.T
+        Uk = U
+        resid = float(torch.linalg.vector_norm(rho @ Uk - Uk * lam[:mp][None, :], dim=0).max())
+        res[name] = {
+            "ms_per_call": ms, "sweeps": sweeps, "kernels": kt,
+            "max_abs_eig_err_vs_oracle": float(np.abs(lam.cpu().numpy() - lam_ref).max()),
+            "eps": float(eps.item()), "eps_abs_err_vs_oracle": abs(float(eps.item()) - eps_ref),
+            "max_residual_rhoU_minus_Ulambda": resid,
+            "orthonormality_err": float(torch.linalg.matrix_norm(
+                Uk.T @ Uk - torch.eye(mp, dtype=torch.float64, device=dev)).item()),
+            "roofline": {"bound": "alu", "kernel": "trunc_sweep", "achieved": achieved,
+                         "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s (FP64)",
+                         "frac": achieved / FP64_NOMINAL_GFLOPS if achieved else None,
+                         "flops_per_launch": flops_sweep, "traffic": None,
+                         "peak_source": "nominal FP64 rate (no measured FP64 peak)"},
+            "cpu_baseline": None if args.no_cpu_baseline else {
+                "value": t_cpu * 1e3, "unit": "ms per call", "kind": "oracle",
+                "cores": oracle.num_threads(),
+                "sample": "the whole call: rho by rows, numpy.linalg.eigh, ranking"}}
+    line = {"workload": "truncation of Schmidt-spectrum states (w_k ~ exp(-k/20)), "
+                        "n = m d = 400 and 1600 rows, square Psi",
+            "metric": "truncation matrix: ms per call (rho, Jacobi sweeps, ranking, U, eps)",
+            "steps": steps, "l2": "flushed between timed calls", "results": res, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_site(args):
+    """Blocked site and cross operators O'_k = U^T ((A_k P^f) (x) S_c) U at d = 4,
+    m = m' = 400, K = 150 (six Hubbard site-operator classes of 25): time per call
+    for each precision, error against the FP64 GPU path, and the FP64 CPU oracle on
+    a bounded sample (two operators per class)."""
+    import numpy as np
+    import torch
+    import paper_0909_5662_gb300 as P
+    import oracle
+    from workloads import site_workload
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    steps = max(1, min(args.steps, 200))
+    w = site_workload()
+    U = torch.from_numpy(w.U).to(dev)
+    A64 = torch.from_numpy(w.A).to(dev)
+    A32 = A64.float()
+    par = torch.from_numpy(w.parity).to(dev)
+    call = lambda A, prec, out=None: P.dmrg_rotate_site_ops(U, A, w.d, w.S, w.counts, w.flags, par,
+                                                            prec, out=out)
+    ref = call(A32.double(), "fp64")
+    flops = 2.0 * w.K * w.d * w.m * w.mp * (w.m + w.mp)
+    res = {}
+    precs = [args.precision] if args.precision else ["bf16x3", "tf32", "fp64"]
+    for prec in precs:
+        A = A32.double() if prec == "fp64" else A32
+        out = call(A, prec)
+        n = steps if prec != "fp64" else max(1, min(steps, 2))
+        ms = _timed(lambda: call(A, prec, out), n, 3 if prec != "fp64" else 1, flush)
+        kt = _with_kernel_timing(lambda: call(A, prec, out), min(n, 20), flush)
+        P.dmrg_sync_status()
+        num = torch.linalg.vector_norm((out.double() - ref).reshape(w.K, -1), dim=1)
+        den = torch.linalg.vector_norm(ref.reshape(w.K, -1), dim=1)
+        res[prec] = {"ms_per_call": ms, "ops_per_s": w.K / (ms * 1e-3),
+                     "eff_tflops": flops / (ms * 1e-3) / 1e12,
+                     "max_rel_fro_err_vs_fp64": float((num / den).max()), "kernels": kt}
+    if args.no_cpu_baseline:
+        print(json.dumps({"workload": "site_m400_k150", "results": res}), flush=True)
+        return 0
+    # the oracle on two operators of every class
+    take = np.concatenate([np.arange(c * 25, c * 25 + 2) for c in range(len(w.counts))])
+    t0 = time.perf_counter()
+    o_ref = oracle.rotate_site(w.U, A32.double().cpu().numpy()[take], w.d, w.S,
+                               np.full(len(w.counts), 2), w.flags, w.parity.astype(np.float64))
+    t_cpu = time.perf_counter() - t0
+    g = ref[torch.from_numpy(take).to(dev)].cpu().numpy()
+    gpu_vs_oracle = float((np.linalg.norm((g - o_ref).reshape(len(take), -1), axis=1) /
+                           np.linalg.norm(o_ref.reshape(len(take), -1), axis=1)).max())
+    line = {"workload": "site_m400_k150 (d=4, m=m'=400, K=150: c_up, c_dn, c+_up, c+_dn with the "
+                        "block parity, n_up, n_dn; 25 block operators each)",
+            "metric": "blocked site/cross operators: ms per call, rotated operators/s",
+            "steps": steps, "l2": "flushed between timed calls", "results": res,
+            "fp64_gpu_vs_oracle_max_rel_fro": gpu_vs_oracle,
+            "cpu_baseline": {"value": len(take) / t_cpu, "unit": "rotated operators/s",
+                             "kind": "oracle", "cores": oracle.num_threads(),
+                             "sample": "%d operators (2 per class), FP64 loops" % len(take)},
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_measure(args):
+    """The measurement stage on the superblock state of the m = 400, d = 4 step
+    (Psi 1600 x 1600): <Z_k> for 150 system operators (rho = Psi Psi^T, then
+    Tr(rho Z_k)), the 50 x 50 system-environment correlations, and N(q) at L = 128.
+    Time per call, per-kernel times, and the FP64 CPU oracle on a bounded sample."""
+    import numpy as np
+    import torch
+    import paper_0909_5662_gb300 as P
+    import oracle
+    from workloads import measure_workload
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    steps = max(1, min(args.steps, 20))
+    w = measure_workload()
+    Psi = torch.from_numpy(w.Psi).to(dev)
+    Z = torch.from_numpy(w.Z).to(dev)
+    W = torch.from_numpy(w.W).to(dev)
+    G = torch.from_numpy(w.G).to(dev)
+    v = torch.from_numpy(w.v).to(dev)
+    n = w.Psi.shape[0]
+    Ks, Ke = Z.shape[0], W.shape[0]
+    Zc = Z[:Ke].contiguous()          # correlations: the first Ke system operators
+    res = {}
+    calls = {
+        "expectation": lambda: P.dmrg_expectation(Z, Psi, 0),
+        "cross_correlations": lambda: P.dmrg_cross_correlations(Zc, W, Psi),
+        "structure_factor": lambda: P.dmrg_structure_factor(G, v, 0.5),
+    }
+    for name, fn in calls.items():
+        got = fn()
+        ms = _timed(fn, steps, 2, flush)
+        kt = _with_kernel_timing(fn, min(steps, 5), flush)
+        P.dmrg_sync_status()
+        res[name] = {"ms_per_call": ms, "kernels": kt}
+    peaks, peak_src = measured_peaks()
+    tr = res["expectation"]["kernels"].get("measure_trace")
+    if tr:
+        gbs = (Ks * n * n * 4 + n * n * 8) / (tr["ms_per_launch"] * 1e-3) / 1e9
+        res["expectation"]["roofline_trace"] = {
+            "bound": "hbm", "kernel": "measure_trace", "achieved": gbs, "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+            "bytes_per_launch": Ks * n * n * 4 + n * n * 8, "peak_source": "%s hbm_gbs" % peak_src}
+    rh = res["expectation"]["kernels"].get("measure_rho")
+    if rh:
+        gf = 2.0 * n * n * n / (rh["ms_per_launch"] * 1e-3) / 1e9
+        res["expectation"]["roofline_rho"] = {
+            "bound": "alu", "kernel": "measure_rho", "achieved": gf, "peak": FP64_NOMINAL_GFLOPS,
+            "unit": "GFLOP/s (FP64)", "frac": gf / FP64_NOMINAL_GFLOPS, "traffic": None,
+            "peak_source": "nominal FP64 rate (no measured FP64 peak)"}
+    if args.no_cpu_baseline:
+        print(json.dumps({"workload": "measure_m400", "results": res}), flush=True)
+        return 0
+    # accuracy and the oracle on a bounded sample
+    take = 4
+    t0 = time.perf_counter()
+    e_ref = oracle.expectation(w.Z[:take].astype(np.float64), w.Psi, 0)
+    t_cpu = time.perf_counter() - t0
+    e_gpu = P.dmrg_expectation(Z[:take].contiguous(), Psi, 0).cpu().numpy()
+    c_ref = oracle.cross_correlations(w.Z[:2].astype(np.float64), w.W[:2].astype(np.float64), w.Psi)
+    c_gpu = P.dmrg_cross_correlations(Z[:2].contiguous(), W[:2].contiguous(), Psi).cpu().numpy()
+    f_ref = oracle.structure_factor(w.G, w.v, 0.5)
+    f_gpu = [x.cpu().numpy() for x in P.dmrg_structure_factor(G, v, 0.5)]
+    line = {"workload": "measure_m400 (Psi 1600 x 1600 with w_k ~ exp(-k/20); 150 system "
+                        "operators for <Z>, 50 x 50 for the correlations, FP32; L = 128 "
+                        "structure factor)",
+            "metric": "measurement stage: ms per call",
+            "steps": steps, "l2": "flushed between timed calls", "results": res,
+            "max_abs_err_vs_oracle": {
+                "expectation": float(np.abs(e_gpu - e_ref).max()),
+                "cross_correlations": float(np.abs(c_gpu - c_ref).max()),
+                "structure_factor": float(max(np.abs(f_gpu[0] - f_ref[0]).max(),
+                                              np.abs(f_gpu[1] - f_ref[1]).max()))},
+            "cpu_baseline": {"value": take / t_cpu, "unit": "expectation values/s", "kind": "oracle",
+                             "cores": oracle.num_threads(),
+                             "sample": "%d of the 150 system operators: rho and Tr(rho Z), FP64 loops" % take},
+            "data": "synthetic"}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -383,9 +626,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="dense", choices=["dense", "chained", "blocked", "backward"],
+    ap.add_argument("--workload", default="dense",
+                    choices=["dense", "chained", "blocked", "backward", "site", "measure", "truncation"],
                     help="dense: the benchmark line; chained: the 50-step sweep report; "
-                         "blocked / backward: reports of the block-sparse and adjoint paths")
+                         "blocked / backward / site / measure / truncation: reports of the "
+                         "block-sparse, adjoint, site-operator, measurement and truncation paths")
+    ap.add_argument("--precision", default=None, choices=["bf16x3", "tf32", "fp32", "fp64"],
+                    help="blocked / backward / site reports: time this precision only")
     ap.add_argument("--sweep-steps", type=int, default=50)
     ap.add_argument("--profile", action="store_true",
                     help="only the BF16x3 step: warm-up then --steps steps (for ncu captures)")
@@ -400,6 +647,12 @@ def main():
         return run_blocked(args)
     if args.workload == "backward":
         return run_backward(args)
+    if args.workload == "site":
+        return run_site(args)
+    if args.workload == "measure":
+        return run_measure(args)
+    if args.workload == "truncation":
+        return run_truncation(args)
 
     import numpy as np
     import torch

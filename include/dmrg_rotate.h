@@ -340,8 +340,10 @@ DMRG_API dmrg_status dmrg_structure_factor(dmrg_handle handle, const double* G, 
  *           (= 1 - sum of the kept eigenvalues for a normalized state);
  *   sweeps  host (may be NULL): sweeps done; -max_sweeps if the off-diagonal part
  *           did not fall below tol * ||rho||_F (the outputs then hold the last
- *           iterate).  A sweep that rotates no pair (every |rho_ab| at or below
- *           DBL_EPSILON * sqrt(|rho_aa rho_bb|)) also ends the iteration.
+ *           iterate).  A pair is rotated only if |rho_ab| exceeds both
+ *           DBL_EPSILON * sqrt(|rho_aa rho_bb|) and (from the second sweep on)
+ *           DBL_EPSILON * ||rho||_F / sqrt(rows); a sweep that rotates no pair also
+ *           ends the iteration.
  * Each sweep is one cooperative launch whose rounds meet at a grid-wide barrier with
  * a bounded wait.  The call waits for the stream once per sweep (the convergence
  * test), so it is not graph-capturable.  Errors: DMRG_ERR_SHAPE unless

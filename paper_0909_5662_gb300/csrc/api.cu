@@ -183,8 +183,11 @@ std::string shape_key(const char* tag, int64_t K, int64_t m, int d, int64_t mp, 
 dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
                              const void* O, int in_is_fp64, int64_t K, void* Oout,
                              dmrg_precision p, void* ws, const TcConfig& c1, const TcConfig& c2,
-                             cudaStream_t s, bool pack_u, const double* U1) {
+                             cudaStream_t s, bool pack_u, const double* U1,
+                             const FirstClasses* cls) {
     const DenseDims D = dense_dims(K, m, d, mp, p);
+    if (cls && (cls->n < 1 || cls->n > kMaxInlineProblems || !cls->U1 || !pack_u))
+        return fail(h, DMRG_ERR_INVALID_ARG, "bad operator classes");
     const bool split = (p == DMRG_PREC_BF16X3);
     const TcMode mode = split ? TC_BF16X3 : TC_TF32;
     const int pmode = split ? 0 : 1;
@@ -282,6 +285,12 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
         j1.rows = int64_t(d) * mp; j1.cols = m; j1.rows_per_op = j1.rows;
         j1.rdiv = d; j1.s_r_hi = 1; j1.s_r_lo = mp; j1.s_c = int64_t(d) * mp;
         j1.dst0 = B1[0]; j1.dst1 = B1[1]; j1.ld = D.ld1;
+        if (cls) {   // the classes' U1_c, stacked
+            j1.src = cls->U1;
+            j1.rows = int64_t(cls->n) * d * mp;
+            j1.s_op = m * d * mp;
+            j1.dst0 = cls->b1[0]; j1.dst1 = cls->b1[1];
+        }
         PackJob& j2 = jobs[nj++];
         j2.src = U; j2.src_f64 = 1; j2.mode = pmode;
         j2.rows = mp; j2.cols = D.md; j2.rows_per_op = mp;
@@ -301,32 +310,43 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     // ---- first product: T = O U_r, written straight into the second product's
     //      K-major operand layout: T_all[k*mp + b][i*d + s].
     TcLaunch L1{};
-    TcProblem& P1 = L1.inline_prob[0];
-    {
-        TcOperand A{Op[0], Op[1], K * m, m, D.ld1};
-        TcOperand B{B1[0], B1[1], int64_t(d) * mp, m, D.ld1};
+    const int nprob1 = cls ? cls->n : 1;
+    const size_t es = split ? 2 : 4;
+    const int grid1 = c1.grid > 0 ? c1.grid : h->num_sms;
+    L1.total_tiles = 0;
+    for (int c = 0; c < nprob1; ++c) {
+        TcProblem& P1 = L1.inline_prob[c];
+        const int64_t k0 = cls ? cls->k0[c] : 0, kc = cls ? cls->kc[c] : K;
+        const size_t a_off = size_t(k0) * m * D.ld1 * es;
+        const size_t b_off = cls ? size_t(c) * d * mp * D.ld1 * es : 0;
+        void* const* bsrc = cls ? cls->b1 : B1;
+        TcOperand A{static_cast<char*>(Op[0]) + a_off, Op[1] ? static_cast<char*>(Op[1]) + a_off : nullptr,
+                    kc * m, m, D.ld1};
+        TcOperand B{static_cast<char*>(bsrc[0]) + b_off,
+                    bsrc[1] ? static_cast<char*>(bsrc[1]) + b_off : nullptr, int64_t(d) * mp, m, D.ld1};
         if (!make_problem(P1, mode, A, B, c1.tile_n_max, 1, c1.row_bytes, c1.pair))
             return fail(h, DMRG_ERR_CUDA, "cuTensorMapEncodeTiled failed (first product)");
+        TcScatter& S1 = P1.sc[0];
+        S1.out_off = k0 * mp * D.ld2;
+        S1.rows_per_op = int32_t(m);
+        S1.s_op = mp * D.ld2;
+        S1.s_row = d;
+        S1.col_div = d;
+        S1.s_col_hi = D.ld2;
+        S1.s_col_lo = 1;
+        P1.tile_start = L1.total_tiles;
+        P1.kb_chunk = chain_kb(c1, m, grid1);
+        L1.total_tiles += P1.m_tiles * P1.n_tiles * P1.k_splits;
     }
-    TcScatter& S1 = P1.sc[0];
-    S1.rows_per_op = int32_t(m);
-    S1.s_op = mp * D.ld2;
-    S1.s_row = d;
-    S1.col_div = d;
-    S1.s_col_hi = D.ld2;
-    S1.s_col_lo = 1;
     L1.table = nullptr;
-    L1.nprob = 1;
-    L1.total_tiles = P1.m_tiles * P1.n_tiles * P1.k_splits;
+    L1.nprob = nprob1;
     L1.out[0][0] = Tt[0];
     L1.out[0][1] = Tt[1];
     L1.status = h->d_status;
     L1.timeout_ns = timeout_ns(h);
     L1.drop_arrival = take_drop_arrival(h);
     L1.row_bytes = c1.row_bytes;
-    const int grid1 = c1.grid > 0 ? c1.grid : h->num_sms;
-    P1.kb_chunk = chain_kb(c1, m, grid1);
-    L1.chunk_scratch = P1.kb_chunk ? chain_scr : nullptr;
+    L1.chunk_scratch = L1.inline_prob[0].kb_chunk ? chain_scr : nullptr;
     e = timed_launch(h, "tc_gemm_first_product", s, [&] {
         const TcEpi epi = split ? EPI_SPLIT_BF16 : EPI_TF32;
         return c1.pair ? tc_gemm_launch_pair(mode, epi, L1, c1.stages, grid1, s, c1.pair)

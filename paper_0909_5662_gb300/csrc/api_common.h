@@ -39,14 +39,28 @@ TcConfig tuned_config(dmrg_handle h, const std::string& key, TcMode mode);
 void load_tune_file(dmrg_handle h);
 void save_tune_file(dmrg_handle h);
 std::string shape_key(const char* tag, int64_t K, int64_t m, int d, int64_t mp, dmrg_precision p);
+// Operator classes of the first product (blocked site operators): class c holds the
+// operators k0[c] .. k0[c] + kc[c] - 1 of the call (consecutive, covering all K) and
+// uses its own U1_c = U1 + c * (m d mp) in place of U.  The packed U1_c go to b1
+// (hi, lo; class c at c * d * mp * ld1 elements), a caller scratch for n classes.
+struct FirstClasses {
+    int n = 0;   // 1 .. kMaxInlineProblems
+    int64_t k0[kMaxInlineProblems] = {};
+    int64_t kc[kMaxInlineProblems] = {};
+    const double* U1 = nullptr;
+    void* b1[2] = {nullptr, nullptr};
+};
+
 // The dense rotation O'_k = U^T (O_k (x) I_d) U.  With U1 != nullptr the first
 // product uses U1 in place of U, i.e. O'_k = U^T (O_k (x) I_d) U1 (the blocked site
 // operators pass U1 = (P (x) S) U); the FP32 plain-FMA path then needs U1_32, an
-// (m*d) x mp FP32 scratch for U1's conversion.
+// (m*d) x mp FP32 scratch for U1's conversion.  With cls != nullptr (tensor-core
+// paths) the first product runs one problem per class in one launch.
 dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
                              const void* O, int in_is_fp64, int64_t K, void* Oout,
                              dmrg_precision p, void* ws, const TcConfig& c1, const TcConfig& c2,
-                             cudaStream_t s, bool pack_u = true, const double* U1 = nullptr);
+                             cudaStream_t s, bool pack_u = true, const double* U1 = nullptr,
+                             const FirstClasses* cls = nullptr);
 
 dmrg_status dense_simt_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
                                const void* O, int in_is_fp64, int64_t K, void* Oout,

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 
 #include "api_common.h"
 
@@ -17,23 +18,119 @@ using namespace dmrg;
 
 namespace {
 
-// out[k] = sum_{a,b} Z_k[a][b] rho[a][b]  (rho symmetric: Tr(rho Z_k)), one block per k.
-template <typename T>
-__global__ void trace_kernel(const T* __restrict__ Z, const double* __restrict__ rho, int64_t n,
-                             double* __restrict__ out) {
-    const int64_t k = blockIdx.x;
-    const T* Zk = Z + k * n * n;
-    double acc = 0.0;
-    for (int64_t x = threadIdx.x; x < n * n; x += blockDim.x) acc += double(Zk[x]) * rho[x];
+// Tr(rho Z_k) = sum_{a,b} Z_k[a][b] rho[a][b] (rho symmetric), in two passes so that
+// every operator is read by many blocks at once: block (c, k) sums chunk c of Z_k into
+// part[k * chunks + c], then trace_finish_kernel adds the chunks in order.
+constexpr int kTraceThreads = 256;
+
+__device__ __forceinline__ double block_sum(double acc) {
     __shared__ double red[32];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __syncthreads();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
+    double s = 0.0;
     if (threadIdx.x < 32) {
-        double s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (threadIdx.x == 0) out[k] = s;
     }
+    return s;   // valid in thread 0
+}
+
+// FP32 -> FP64 on the integer pipe (exponent rebias, mantissa shift): the FP64 pipe of
+// this part is slow, and a hardware conversion there would cost as much as the FMA it
+// feeds.  Zero keeps its sign; subnormals, infinities and NaN take the hardware path.
+__device__ __forceinline__ double widen(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    const bool zero = (u << 1) == 0u;
+    if (!zero && (e == 0u || e == 0xffu)) return double(f);
+    const unsigned hi = zero ? (u & 0x80000000u)
+                             : ((u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu));
+    const unsigned lo = zero ? 0u : (u << 29);
+    return __hiloint2double(int(hi), int(lo));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTraceThreads)
+trace_partial_kernel(const T* __restrict__ Z, const double* __restrict__ rho, int64_t nn,
+                     int64_t per, int chunks, double* __restrict__ part) {
+    const int64_t k = blockIdx.y;
+    const int64_t lo = int64_t(blockIdx.x) * per;
+    const int64_t hi = lo + per < nn ? lo + per : nn;
+    const T* Zk = Z + k * nn;
+    double acc = 0.0;
+    if (sizeof(T) == 4 && (nn & 3) == 0 && (per & 3) == 0 &&
+        (reinterpret_cast<uintptr_t>(Z) & 15) == 0 && (reinterpret_cast<uintptr_t>(rho) & 15) == 0) {
+        // four FP32 entries and the matching rho entries per step
+        const float4* z4 = reinterpret_cast<const float4*>(Zk);
+        const double2* r2 = reinterpret_cast<const double2*>(rho);
+        for (int64_t q = lo / 4 + threadIdx.x; q < hi / 4; q += blockDim.x) {
+            const float4 z = __ldcs(z4 + q);
+            const double2 ra = r2[2 * q], rb = r2[2 * q + 1];
+            acc = fma(widen(z.x), ra.x, acc);
+            acc = fma(widen(z.y), ra.y, acc);
+            acc = fma(widen(z.z), rb.x, acc);
+            acc = fma(widen(z.w), rb.y, acc);
+        }
+    } else {
+        for (int64_t x = lo + threadIdx.x; x < hi; x += blockDim.x) acc += double(Zk[x]) * rho[x];
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) part[k * chunks + blockIdx.x] = s;
+}
+
+__global__ void trace_finish_kernel(const double* __restrict__ part, int chunks, int64_t K,
+                                    double* __restrict__ out) {
+    const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    double s = 0.0;
+    for (int c = 0; c < chunks; ++c) s += part[k * chunks + c];
+    out[k] = s;
+}
+
+// C[i][j] = sum_s part[s][i][j], the split reduction of the cross correlations in order.
+__global__ void split_sum_kernel(const double* __restrict__ part, int nsplit, int64_t nout,
+                                 double* __restrict__ C) {
+    const int64_t x = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (x >= nout) return;
+    double s = 0.0;
+    for (int p = 0; p < nsplit; ++p) s += part[int64_t(p) * nout + x];
+    C[x] = s;
+}
+
+// Chunking of Tr(rho Z_k): about 2048 blocks over all operators, chunks of at least
+// 8192 entries, chunk length a multiple of 4 (vector loads).
+struct TraceSplit {
+    int chunks;
+    int64_t per;
+};
+TraceSplit trace_split(int64_t K, int64_t nn) {
+    TraceSplit t;
+    int64_t c = std::max<int64_t>(1, (2048 + K - 1) / std::max<int64_t>(K, 1));
+    c = std::min<int64_t>(c, std::max<int64_t>(1, (nn + 8191) / 8192));
+    int64_t per = (nn + c - 1) / c;
+    per = (per + 3) / 4 * 4;
+    t.per = per;
+    t.chunks = int((nn + per - 1) / per);
+    return t;
+}
+
+// Split of the reduction of length Lx = cols^2 in the cross correlations into about 608
+// pieces (four per SM) of a multiple of 16 entries.
+struct CrossSplit {
+    int64_t kc, full, tail;
+    int nsplit;
+};
+CrossSplit cross_split(int64_t Lx) {
+    CrossSplit c;
+    int64_t kc = std::max<int64_t>(1024, (Lx + 607) / 608);
+    kc = (kc + 15) / 16 * 16;
+    c.kc = kc;
+    c.full = Lx / kc;
+    c.tail = Lx - c.full * kc;
+    c.nsplit = int(c.full + (c.tail ? 1 : 0));
+    return c;
 }
 
 // F(q_p) = (1/L) sum_{k,j} e^{i q_p (k-j)} (G[k][j] - c v[k] - c v[j] + c^2),
@@ -112,6 +209,7 @@ WsLayout cross_layout(int64_t Ks, int64_t Ke, int64_t rows, int64_t cols, int z6
     W.add("W64", w64 ? 0 : size_t(Ke) * cols * cols * 8);
     W.add("Y", size_t(Ks) * rows * cols * 8);
     W.add("M", size_t(Ks) * cols * cols * 8);
+    W.add("part", size_t(cross_split(cols * cols).nsplit) * Ks * Ke * 8);
     return W;
 }
 
@@ -125,7 +223,8 @@ dmrg_status dmrg_expectation_workspace(dmrg_handle h, int64_t K, int64_t rows, i
     if (K < 0 || rows < 1 || cols < 1) return fail(h, DMRG_ERR_SHAPE, "need K >= 0, rows, cols >= 1");
     if (side != 0 && side != 1) return fail(h, DMRG_ERR_INVALID_ARG, "side must be 0 or 1");
     const int64_t n = side == 0 ? rows : cols;
-    *bytes = size_t(n) * n * 8;
+    const TraceSplit t = trace_split(K, n * n);
+    *bytes = align_up(size_t(n) * n * 8, 256) + size_t(K) * t.chunks * 8;
     return DMRG_OK;
 }
 
@@ -144,11 +243,18 @@ dmrg_status dmrg_expectation(dmrg_handle h, const void* Z, int in_is_fp64, int64
     const int64_t n = side == 0 ? rows : cols;
     cudaError_t e = timed_launch(h, "measure_rho", s, [&] { return rho_launch(Psi, rows, cols, side, rho, s); });
     if (e != cudaSuccess) return cuda_fail(h, e, "reduced density matrix");
+    const TraceSplit t = trace_split(K, n * n);
+    double* part = reinterpret_cast<double*>(static_cast<char*>(ws) + align_up(size_t(n) * n * 8, 256));
+    if (K > 65535) return fail(h, DMRG_ERR_SHAPE, "K too large");
     e = timed_launch(h, "measure_trace", s, [&] {
+        const dim3 grid(unsigned(t.chunks), unsigned(K));
         if (in_is_fp64)
-            trace_kernel<double><<<unsigned(K), 256, 0, s>>>(static_cast<const double*>(Z), rho, n, out);
+            trace_partial_kernel<double><<<grid, kTraceThreads, 0, s>>>(
+                static_cast<const double*>(Z), rho, n * n, t.per, t.chunks, part);
         else
-            trace_kernel<float><<<unsigned(K), 256, 0, s>>>(static_cast<const float*>(Z), rho, n, out);
+            trace_partial_kernel<float><<<grid, kTraceThreads, 0, s>>>(
+                static_cast<const float*>(Z), rho, n * n, t.per, t.chunks, part);
+        trace_finish_kernel<<<unsigned((K + 255) / 256), 256, 0, s>>>(part, t.chunks, K, out);
         return cudaGetLastError();
     });
     return cuda_fail(h, e, "expectation values");
@@ -212,14 +318,32 @@ dmrg_status dmrg_cross_correlations(dmrg_handle h, const void* Z, int z_is_fp64,
     g2.sCb = cols * cols; g2.sCi = cols; g2.sCj = 1;
     e = timed_launch(h, "measure_psiT_Y", s, [&] { return simt_gemm_launch(Real::F64, g2, s); });
     if (e != cudaSuccess) return cuda_fail(h, e, "Psi^T Y");
-    // C[i][j] = <M_i, W_j>_F
-    SimtGemm g3{};
-    g3.A = M; g3.B = W64; g3.C = C; g3.batch = 1;
-    g3.M = Ks; g3.N = Ke; g3.K = cols * cols;
-    g3.sAi = cols * cols; g3.sAk = 1;
-    g3.sBk = 1; g3.sBj = cols * cols;
-    g3.sCi = Ke; g3.sCj = 1;
-    e = timed_launch(h, "measure_cross", s, [&] { return simt_gemm_launch(Real::F64, g3, s); });
+    // C[i][j] = <M_i, W_j>_F: the reduction over cols^2 entries is split into pieces
+    // (one batch entry each, partial C per piece), then the pieces are added in order.
+    double* part = reinterpret_cast<double*>(base + L.offsets[4]);
+    const int64_t Lx = cols * cols;
+    const CrossSplit cs = cross_split(Lx);
+    e = timed_launch(h, "measure_cross", s, [&] {
+        SimtGemm g3{};
+        g3.A = M; g3.B = W64; g3.C = part;
+        g3.M = Ks; g3.N = Ke; g3.K = cs.kc; g3.batch = int32_t(cs.full);
+        g3.sAb = cs.kc; g3.sAi = Lx; g3.sAk = 1;
+        g3.sBb = cs.kc; g3.sBk = 1; g3.sBj = Lx;
+        g3.sCb = Ks * Ke; g3.sCi = Ke; g3.sCj = 1;
+        cudaError_t r = simt_gemm_launch(Real::F64, g3, s);
+        if (r == cudaSuccess && cs.tail) {
+            SimtGemm t3 = g3;
+            t3.A = M + cs.full * cs.kc;
+            t3.B = W64 + cs.full * cs.kc;
+            t3.C = part + cs.full * Ks * Ke;
+            t3.K = cs.tail;
+            t3.batch = 1;
+            r = simt_gemm_launch(Real::F64, t3, s);
+        }
+        if (r != cudaSuccess) return r;
+        split_sum_kernel<<<unsigned((Ks * Ke + 255) / 256), 256, 0, s>>>(part, cs.nsplit, Ks * Ke, C);
+        return cudaGetLastError();
+    });
     return cuda_fail(h, e, "cross correlations");
 }
 

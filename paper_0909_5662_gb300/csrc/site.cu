@@ -7,9 +7,10 @@
 //
 //     O'_k = U^T (A_k (x) I_d) U_c,     U_c = (P^{f_c} (x) S_c) U,
 //
-// i.e. the plain block rotation of A_k with U_c in the first product.  Each class
-// of operators sharing (S_c, f_c) gets U_c from one small FP64 kernel and then runs
-// the dense rotation (pack, first product, second product) on its operators.
+// i.e. the plain block rotation of A_k with U_c in the first product.  On the
+// tensor-core paths the classes go in groups of up to four: one kernel forms the
+// group's U_c, and one dense rotation packs them and runs the first product as one
+// problem per class (each with its own U_c) and the second product over the group.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,42 +23,72 @@ namespace {
 
 constexpr int kMaxSiteDim = 8;
 
-struct SiteMatrix {
-    double s[kMaxSiteDim * kMaxSiteDim];
+constexpr int kGroup = kMaxInlineProblems;   // classes per first-product launch
+
+struct SiteMatrices {
+    double s[kGroup][kMaxSiteDim * kMaxSiteDim];
+    unsigned long long nz[kGroup];   // bit s * d + t set where S_c[s][t] != 0
+    int odd[kGroup];                 // 1: the class carries the block parity
 };
 
-// Uc[(j, s)][b] = p_j * sum_t S[s][t] U[(j, t)][b], one thread per (j, b).
+// Uc_c[(j, s)][b] = p_j^{f_c} * sum_t S_c[s][t] U[(j, t)][b] for class c = blockIdx.z of
+// the group (Uc_c at c * m * d * mp), one thread per (j, b): b from blockIdx.x, rows j
+// from blockIdx.y onwards in steps of gridDim.y.
 __global__ void site_u_kernel(const double* __restrict__ U, double* __restrict__ Uc, int64_t m,
-                              int d, int64_t mp, const __grid_constant__ SiteMatrix S,
+                              int d, int64_t mp, const __grid_constant__ SiteMatrices S,
                               const signed char* __restrict__ parity) {
-    const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (idx >= m * mp) return;
-    const int64_t j = idx / mp, b = idx - j * mp;
-    double u[kMaxSiteDim];
+    const int c = blockIdx.z;
+    const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (b >= mp) return;
+    double* out = Uc + int64_t(c) * m * d * mp;
+    for (int64_t j = blockIdx.y; j < m; j += gridDim.y) {
+        double u[kMaxSiteDim];
 #pragma unroll
-    for (int t = 0; t < kMaxSiteDim; ++t) u[t] = t < d ? U[(j * d + t) * mp + b] : 0.0;
-    const double pj = parity ? double(parity[j]) : 1.0;
+        for (int t = 0; t < kMaxSiteDim; ++t) u[t] = t < d ? U[(j * d + t) * mp + b] : 0.0;
+        // the parity is a sign: applied to the bits, off the (slow) FP64 pipe
+        const long long flip = (S.odd[c] && parity && parity[j] < 0) ? (1ll << 63) : 0ll;
 #pragma unroll
-    for (int s = 0; s < kMaxSiteDim; ++s) {
-        if (s >= d) break;
-        double v = 0.0;
+        for (int s = 0; s < kMaxSiteDim; ++s) {
+            if (s >= d) break;
+            double v = 0.0;
 #pragma unroll
-        for (int t = 0; t < kMaxSiteDim; ++t)
-            if (t < d) v = fma(S.s[s * d + t], u[t], v);
-        Uc[(j * d + s) * mp + b] = pj * v;
+            for (int t = 0; t < kMaxSiteDim; ++t) {
+                // site operators are sparse (one entry per row for c, c+): the zero test is
+                // an integer mask, uniform over the grid
+                if (t < d && ((S.nz[c] >> (s * d + t)) & 1ull)) v = fma(S.s[c][s * d + t], u[t], v);
+            }
+            out[(j * d + s) * mp + b] = __longlong_as_double(__double_as_longlong(v) ^ flip);
+        }
     }
 }
 
 struct SiteDims {
-    WsLayout ws;   // Uc (FP64), Uc in FP32 (plain-FMA FP32 path), dense rotation workspace
+    // Uc (FP64, one group of classes), Uc in FP32 (plain-FMA FP32 path), the group's
+    // packed U_c (tensor-core paths), dense rotation workspace
+    WsLayout ws;
 };
 
 SiteDims site_dims(int64_t K, int64_t m, int d, int64_t mp, dmrg_precision p) {
     SiteDims D;
-    D.ws.add("Uc", size_t(m) * d * mp * 8);
+    const bool tc = (p == DMRG_PREC_TF32 || p == DMRG_PREC_BF16X3);
+    const DenseDims dd = dense_dims(std::max<int64_t>(K, 1), m, d, mp, p);
+    const size_t es = (p == DMRG_PREC_TF32) ? 4 : 2;
+    D.ws.add("Uc", size_t(tc ? kGroup : 1) * m * d * mp * 8);
     D.ws.add("Uc32", p == DMRG_PREC_FP32 ? size_t(m) * d * mp * 4 : 0);
-    D.ws.add("dense", dense_dims(std::max<int64_t>(K, 1), m, d, mp, p).ws.total);
+    for (int i = 0; i < 2; ++i)
+        D.ws.add("B1", (tc && (i == 0 || p == DMRG_PREC_BF16X3)) ? size_t(kGroup) * d * mp * dd.ld1 * es : 0);
+    D.ws.add("dense", dd.ws.total);
     return D;
+}
+
+cudaError_t site_u_launch(dmrg_handle h, const double* U, double* Uc, int64_t m, int d, int64_t mp,
+                          const SiteMatrices& S, int nclass, const signed char* parity,
+                          cudaStream_t s) {
+    const dim3 grid(unsigned((mp + 127) / 128), unsigned(std::min<int64_t>(m, 65535)), unsigned(nclass));
+    return timed_launch(h, "site_u_transform", s, [&] {
+        site_u_kernel<<<grid, 128, 0, s>>>(U, Uc, m, d, mp, S, parity);
+        return cudaGetLastError();
+    });
 }
 
 }  // namespace
@@ -104,33 +135,68 @@ dmrg_status dmrg_rotate_site_ops(dmrg_handle h, const double* U, int64_t m, int 
     char* base = static_cast<char*>(ws);
     double* Uc = reinterpret_cast<double*>(base + D.ws.offsets[0]);
     float* Uc32 = p == DMRG_PREC_FP32 ? reinterpret_cast<float*>(base + D.ws.offsets[1]) : nullptr;
-    void* wsd = base + D.ws.offsets[2];
+    void* b1[2] = {base + D.ws.offsets[2], p == DMRG_PREC_BF16X3 ? base + D.ws.offsets[3] : nullptr};
+    void* wsd = base + D.ws.offsets[4];
     const size_t es_in = in_is_fp64 ? 8 : 4, es_out = p == DMRG_PREC_FP64 ? 8 : 4;
     const TcMode mode = (p == DMRG_PREC_BF16X3) ? TC_BF16X3 : TC_TF32;
-    int64_t k0 = 0;
-    for (int c = 0; c < n_class; ++c) {
-        const int64_t kc = counts[c];
-        if (kc == 0) continue;
-        SiteMatrix Sm{};
-        for (int x = 0; x < d * d; ++x) Sm.s[x] = S[int64_t(c) * d * d + x];
-        const int64_t n = m * mp;
-        cudaError_t e = timed_launch(h, "site_u_transform", s, [&] {
-            site_u_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(U, Uc, m, d, mp, Sm,
-                                                                    flags[c] ? parity : nullptr);
-            return cudaGetLastError();
-        });
-        if (e != cudaSuccess) return cuda_fail(h, e, "site transform");
-        const void* Ac = static_cast<const char*>(A) + size_t(k0) * m * m * es_in;
-        void* Oc = static_cast<char*>(Oout) + size_t(k0) * mp * mp * es_out;
-        if (tc) {
-            const TcConfig c1 = tuned_config(h, shape_key("g1", kc, m, d, mp, p), mode);
-            const TcConfig c2 = tuned_config(h, shape_key("g2", kc, m, d, mp, p), mode);
-            st = dense_tc_forward(h, U, m, d, mp, Ac, in_is_fp64, kc, Oc, p, wsd, c1, c2, s, true, Uc);
-        } else {
-            st = dense_simt_forward(h, U, m, d, mp, Ac, in_is_fp64, kc, Oc, p, wsd, s, true, Uc, Uc32);
+    auto site_matrix = [&](SiteMatrices& Sm, int slot, int c) {
+        Sm.nz[slot] = 0;
+        for (int x = 0; x < d * d; ++x) {
+            Sm.s[slot][x] = S[int64_t(c) * d * d + x];
+            if (Sm.s[slot][x] != 0.0) Sm.nz[slot] |= 1ull << x;
         }
+        Sm.odd[slot] = flags[c];
+    };
+    int64_t k0 = 0;
+    if (!tc) {
+        // plain-FMA paths: one class at a time
+        for (int c = 0; c < n_class; ++c) {
+            const int64_t kc = counts[c];
+            if (kc == 0) continue;
+            SiteMatrices Sm{};
+            site_matrix(Sm, 0, c);
+            cudaError_t e = site_u_launch(h, U, Uc, m, d, mp, Sm, 1, parity, s);
+            if (e != cudaSuccess) return cuda_fail(h, e, "site transform");
+            const void* Ac = static_cast<const char*>(A) + size_t(k0) * m * m * es_in;
+            void* Oc = static_cast<char*>(Oout) + size_t(k0) * mp * mp * es_out;
+            st = dense_simt_forward(h, U, m, d, mp, Ac, in_is_fp64, kc, Oc, p, wsd, s, true, Uc, Uc32);
+            if (st != DMRG_OK) return st;
+            k0 += kc;
+        }
+        return DMRG_OK;
+    }
+    // tensor-core paths: the classes with operators in groups of at most kGroup, the
+    // groups as even as possible
+    int live = 0;
+    for (int x = 0; x < n_class; ++x) live += counts[x] > 0 ? 1 : 0;
+    const int ngroups = (live + kGroup - 1) / kGroup;
+    const int per_group = ngroups ? (live + ngroups - 1) / ngroups : 1;
+    int c = 0;
+    while (c < n_class) {
+        SiteMatrices Sm{};
+        FirstClasses cls;
+        cls.U1 = Uc;
+        cls.b1[0] = b1[0];
+        cls.b1[1] = b1[1];
+        const int64_t g0 = k0;
+        for (; c < n_class && cls.n < per_group; ++c) {
+            if (counts[c] == 0) continue;
+            site_matrix(Sm, cls.n, c);
+            cls.k0[cls.n] = k0 - g0;
+            cls.kc[cls.n] = counts[c];
+            k0 += counts[c];
+            ++cls.n;
+        }
+        if (cls.n == 0) break;
+        cudaError_t e = site_u_launch(h, U, Uc, m, d, mp, Sm, cls.n, parity, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "site transform");
+        const int64_t kg = k0 - g0;
+        const void* Ag = static_cast<const char*>(A) + size_t(g0) * m * m * es_in;
+        void* Og = static_cast<char*>(Oout) + size_t(g0) * mp * mp * es_out;
+        const TcConfig c1 = tuned_config(h, shape_key("g1", kg, m, d, mp, p), mode);
+        const TcConfig c2 = tuned_config(h, shape_key("g2", kg, m, d, mp, p), mode);
+        st = dense_tc_forward(h, U, m, d, mp, Ag, in_is_fp64, kg, Og, p, wsd, c1, c2, s, true, nullptr, &cls);
         if (st != DMRG_OK) return st;
-        k0 += kc;
     }
     return DMRG_OK;
 }

@@ -9,7 +9,11 @@
 // In a round every pair's rotation J (the stable 2 x 2 symmetric Schur step: the angle
 // that zeroes a_ab) is computed from the current matrix, and the whole round is applied
 // at once, A <- J^T A J and V <- V J.  A pair whose a_ab is below the rounding level of
-// its diagonal, a_ab^2 <= eps^2 |a_aa a_bb|, is not rotated.  The sweeps stop when
+// its diagonal, a_ab^2 <= eps^2 |a_aa a_bb|, is not rotated, nor (from the second sweep
+// on) one at the rounding level of the whole matrix, |a_ab| <= eps ||A||_F / sqrt(n):
+// the entries among eigenvectors of eigenvalues below rounding are noise of rho itself,
+// and rotating them only spends sweeps (all skipped entries together perturb the
+// eigenvalues by at most eps ||A||_F sqrt(n)).  The sweeps stop when
 // the off-diagonal part is below tol * ||A||_F, or when a sweep rotated no pair.
 // Eigenvalues are ranked on the device, and U's columns are V's columns in decreasing
 // eigenvalue order, each with its largest-magnitude component positive (the first such
@@ -59,7 +63,8 @@ struct Rot {
     int a, b;         // -1 for the padding index
 };
 
-__device__ Rot slot_rotation(const double* __restrict__ A, int n, int N, int npair, int r, int slot) {
+__device__ Rot slot_rotation(const double* __restrict__ A, int n, int N, int npair, int r, int slot,
+                             double abs2) {
     Rot R{1.0, 0.0, 0.0, -1, -1};
     if (slot >= npair) return R;
     int a, b;
@@ -70,7 +75,7 @@ __device__ Rot slot_rotation(const double* __restrict__ A, int n, int N, int npa
     const double g = __ldcg(A + size_t(a) * n + b);
     const double al = __ldcg(A + size_t(a) * n + a);
     const double be = __ldcg(A + size_t(b) * n + b);
-    if (!(g * g > (DBL_EPSILON * DBL_EPSILON) * fabs(al * be))) return R;
+    if (!(g * g > (DBL_EPSILON * DBL_EPSILON) * fabs(al * be)) || !(g * g > abs2)) return R;
     const double tau = (be - al) / (2.0 * g);
     double t;
     if (fabs(tau) > 1e150) {
@@ -156,6 +161,7 @@ struct SweepArgs {
     SweepSync* sync;
     unsigned* status;
     uint64_t timeout_ns;
+    double abs2;        // square of the absolute rotation threshold
     int n, N, npair, npt, n_atiles, n_vtiles, cur;
 };
 
@@ -184,7 +190,7 @@ __global__ void __launch_bounds__(kThreads) jacobi_sweep_kernel(SweepArgs P) {
         // phase 1: every pair's rotation, once
         // (slot-major over blocks, so that every SM takes a few of the FP64 divide chains)
         for (int slot = tid * gridDim.x + blockIdx.x; slot < P.npair; slot += gridDim.x * kThreads) {
-            const Rot R = slot_rotation(Ain, n, P.N, P.npair, r, slot);
+            const Rot R = slot_rotation(Ain, n, P.N, P.npair, r, slot, P.abs2);
             if (R.s != 0.0) nrot += 1.0;
             P.rots[slot] = R;
         }
@@ -502,6 +508,9 @@ dmrg_status dmrg_truncation(dmrg_handle h, const double* Psi, int64_t rows, int6
             done = sweep + 1;
             break;
         }
+        // From the second sweep on, entries at or below DBL_EPSILON ||A||_F / sqrt(n) are
+        // rounding noise of rho itself and are not rotated.
+        P.abs2 = DBL_EPSILON * DBL_EPSILON * host.all2 / double(n);
     }
     const double* A = P.A[P.cur];
     if (n == 1) done = 0;

@@ -44,6 +44,8 @@ CASES = [
     (130, 2, 200, [3, 2], [0, 1]),
     (64, 4, 96, [1, 1, 1, 1, 1], [1, 1, 0, 0, 1]),
     (129, 4, 130, [4], [1]),
+    # nine classes: first products in groups of four, four and one
+    (100, 4, 100, [3, 1, 2, 2, 1, 3, 2, 1, 2], [1, 0, 1, 0, 1, 0, 1, 0, 1]),
 ]
 
 

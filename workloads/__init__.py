@@ -23,4 +23,10 @@ from .synthetic import (  # noqa: F401
     HUBBARD_SITE_SHIFTS,
     backward_upstream,
     chained_inputs,
+    schmidt_state,
+    HUBBARD_SITE_OPS,
+    SiteWorkload,
+    site_workload,
+    MeasureWorkload,
+    measure_workload,
 )

@@ -208,3 +208,91 @@ def chained_inputs(step: int, md: int, mp: int, device, seed: int = SEED_BASE + 
     sgn[sgn == 0] = 1.0
     return (Q * sgn[None, :]).contiguous()
 
+
+
+# ----------------------------------------------------------------------------
+# Inputs of the stages around the rotation: the truncation matrix, the blocked
+# site operators and the measurement stage.
+# ----------------------------------------------------------------------------
+
+def schmidt_state(seed: int, rows: int, cols: int, xi: float = 20.0) -> np.ndarray:
+    """Unit-norm superblock state Psi (rows x cols) with a ground-state-like
+    Schmidt spectrum: Psi = L diag(sqrt(w)) R^T with seeded orthonormal L and R
+    and weights w_k proportional to exp(-k / xi), k = 0 .. min(rows, cols) - 1."""
+    rng = np.random.default_rng(seed)
+    r = min(rows, cols)
+    w = np.exp(-np.arange(r) / xi)
+    w /= w.sum()
+    Lm = orthonormal_columns(rng, rows, r)
+    Rm = orthonormal_columns(rng, cols, r)
+    return np.ascontiguousarray((Lm * np.sqrt(w)[None, :]) @ Rm.T)
+
+
+# Hubbard site operators in the local basis (0, up, down, up-down), with the up mode
+# before the down mode inside the site: c_up, c_dn, their adjoints, n_up, n_dn.
+_C_UP = np.array([[0, 1, 0, 0], [0, 0, 0, 0], [0, 0, 0, 1], [0, 0, 0, 0]], dtype=np.float64)
+_C_DN = np.array([[0, 0, 1, 0], [0, 0, 0, -1], [0, 0, 0, 0], [0, 0, 0, 0]], dtype=np.float64)
+HUBBARD_SITE_OPS = {
+    "c_up": (_C_UP, 1), "c_dn": (_C_DN, 1), "cdag_up": (_C_UP.T.copy(), 1),
+    "cdag_dn": (_C_DN.T.copy(), 1), "n_up": (_C_UP.T @ _C_UP, 0), "n_dn": (_C_DN.T @ _C_DN, 0),
+}
+
+
+@dataclasses.dataclass
+class SiteWorkload:
+    name: str
+    d: int
+    m: int
+    mp: int
+    U: np.ndarray        # (m*d) x mp, FP64
+    A: np.ndarray        # K x m x m, FP64, ordered by class
+    S: np.ndarray        # n_class x d x d, FP64
+    counts: np.ndarray   # n_class, int64
+    flags: np.ndarray    # n_class, int64 (1: the class carries the block parity)
+    parity: np.ndarray   # m, int8 (+1 / -1)
+
+    @property
+    def K(self) -> int:
+        return int(self.A.shape[0])
+
+
+def site_workload(seed: int = SEED_BASE + 6, m: int = 400, mp: int = 400, per_class: int = 25) -> SiteWorkload:
+    """``site_m400_k150``: d = 4, m = m' = 400, the six Hubbard site operators as
+    classes of 25 block operators each (K = 150); block operators N(0,1), block
+    parity of every block state Bernoulli(1/2) in {+1, -1}."""
+    rng = np.random.default_rng(seed)
+    d = 4
+    U = orthonormal_columns(rng, m * d, mp)
+    names = list(HUBBARD_SITE_OPS)
+    S = np.stack([HUBBARD_SITE_OPS[k][0] for k in names])
+    flags = np.array([HUBBARD_SITE_OPS[k][1] for k in names], dtype=np.int64)
+    counts = np.full(len(names), per_class, dtype=np.int64)
+    A = rng.standard_normal((per_class * len(names), m, m))
+    parity = np.where(rng.integers(0, 2, size=m) == 1, 1, -1).astype(np.int8)
+    return SiteWorkload("site_m400_k150", d, m, mp, U, A, S, counts, flags, parity)
+
+
+@dataclasses.dataclass
+class MeasureWorkload:
+    name: str
+    Psi: np.ndarray      # rows x cols, FP64, unit norm
+    Z: np.ndarray        # Ks x rows x rows (system operators), FP32
+    W: np.ndarray        # Ke x cols x cols (environment operators), FP32
+    G: np.ndarray        # L x L two-point matrix, FP64, symmetric
+    v: np.ndarray        # L one-point values
+
+
+def measure_workload(seed: int = SEED_BASE + 7, n: int = 1600, Ks: int = 150, Ke: int = 50,
+                     L: int = 128) -> MeasureWorkload:
+    """``measure_m400``: the superblock state of the d = 4, m = 400 step as an
+    n x n (n = m d = 1600) matrix with a ground-state-like Schmidt spectrum, Ks
+    system operators and Ke environment operators on the [B a] bases (N(0,1), drawn
+    in FP32, the operators' storage precision),
+    and an L = 128 two-point matrix (symmetric N(0,1)) with one-point values
+    for the structure factor."""
+    Psi = schmidt_state(seed, n, n)
+    rng = np.random.default_rng(seed + 1)
+    Z = rng.standard_normal((Ks, n, n), dtype=np.float32)
+    W = rng.standard_normal((Ke, n, n), dtype=np.float32)
+    X = rng.standard_normal((L, L))
+    return MeasureWorkload("measure_m400", Psi, Z, W, X + X.T, rng.standard_normal(L))
