@@ -236,18 +236,24 @@ def run_blocked(args):
         O64 = torch.from_numpy(w.O_blocks).to(dev)
         O32 = O64.float()
         ref = P.dmrg_rotate_ops_blocked(plan, Ub, O64, "fp64")
-        row = {"problems_first": n1, "problems_second": n2, "flops_per_call": flops,
+        small = max(max(s[2] for s in w.block_sectors), max(s[2] for s in w.kept_sectors)) <= 32
+        row = {"path": "fused small-sector kernel (FP32; FP64 for fp64)" if small else
+                       "grouped GEMMs (tcgen05 for bf16x3/tf32, plain FMA for fp32/fp64)",
+               "problems_first": n1, "problems_second": n2, "flops_per_call": flops,
                "sectors": len(w.block_sectors), "operators": w.K,
                "block_rows_max": max(s[2] for s in w.block_sectors)}
         for prec in ([args.precision] if args.precision else ("bf16x3", "tf32", "fp32", "fp64")):
             O = O64 if prec == "fp64" else O32
             out = P.dmrg_rotate_ops_blocked(plan, Ub, O, prec)
-            ms = _timed(lambda: P.dmrg_rotate_ops_blocked(plan, Ub, O, prec, out=out),
-                        steps if prec != "fp64" else max(1, steps // 10), 3, flush)
+            n = steps if prec != "fp64" else max(1, steps // 10)
+            ms = _timed(lambda: P.dmrg_rotate_ops_blocked(plan, Ub, O, prec, out=out), n, 3, flush)
+            kt = _with_kernel_timing(lambda: P.dmrg_rotate_ops_blocked(plan, Ub, O, prec, out=out),
+                                     min(n, 20), flush)
             P.dmrg_sync_status()
             err = float((torch.linalg.vector_norm(out.double() - ref) / torch.linalg.vector_norm(ref)).item())
             row[prec] = {"ms_per_call": ms, "ops_per_s": w.K / (ms * 1e-3),
-                         "tflops_logical": flops / (ms * 1e-3) / 1e12, "rel_fro_err_vs_fp64": err}
+                         "tflops_logical": flops / (ms * 1e-3) / 1e12, "rel_fro_err_vs_fp64": err,
+                         "kernels": kt}
         res[name] = row
         plan.close()
     line = {"workload": "blocked U(1)xU(1), m=1000, d=4, K=200 (two sector laws)",

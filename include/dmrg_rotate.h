@@ -109,6 +109,11 @@ DMRG_API dmrg_status dmrg_sync_status(dmrg_handle handle, dmrg_stream_t stream);
  *                              are added in FP32 with round to nearest; the tensor
  *                              core's own accumulation error grows with the chain
  *                              length.  0 = one chain.
+ *   DMRG_OPT_BLOCKED_SMALL   : 1 (default) = blocked plans whose sectors all hold at
+ *                              most 32 states (site dimension <= 8) run one fused
+ *                              kernel, one warp per (operator, output block), in FP32
+ *                              for the reduced precisions (more accurate than they
+ *                              ask) and FP64 for DMRG_PREC_FP64; 0 = the grouped GEMMs.
  *   DMRG_OPT_TEST_WITHHOLD_ARRIVAL : test hook for failure detection.  1 makes
  *                              the next dense tensor-core launch withhold one
  *                              shared-memory stage release in its first CTA, so
@@ -123,7 +128,8 @@ typedef enum {
     DMRG_OPT_CHECK_ORTHO = 4,
     DMRG_OPT_TEST_WITHHOLD_ARRIVAL = 5,
     DMRG_OPT_DETERMINISTIC = 6,
-    DMRG_OPT_ACCUM_CHAIN = 7
+    DMRG_OPT_ACCUM_CHAIN = 7,
+    DMRG_OPT_BLOCKED_SMALL = 8
 } dmrg_option;
 DMRG_API dmrg_status dmrg_set_option(dmrg_handle handle, dmrg_option option, double value);
 

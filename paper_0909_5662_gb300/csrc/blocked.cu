@@ -17,6 +17,11 @@
 // second, O'_k[Q2, Q] = U_Q2^T T_k.  FP64 / FP32 run the problems as grouped
 // plain-FMA GEMMs; BF16x3 / TF32 pack the stacked operands into K-major tensor-core
 // layouts and run two grouped tcgen05 launches.
+//
+// Plans whose sectors all hold at most 32 states have nothing for a tensor-core tile:
+// there one warp per (operator, output block) computes sum_s U_Q2[seg s]^T O_k U_Q[seg s]
+// through shared memory in a single launch, in FP64 for the FP64 precision and in FP32
+// (more accurate than BF16x3 and TF32 asked for) otherwise.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,6 +61,69 @@ struct TcTables {
     int tiles_first = 0, tiles_second = 0;
     int bn_first = 16, bn_second = 16;
 };
+
+// ---- fused small-sector path
+constexpr int kSmallMax = 32;    // largest sector (states) of the fused path
+constexpr int kSmallSegs = 8;    // largest site dimension of the fused path
+constexpr int kSmallWarps = 8;   // warps (work items) per block
+
+struct SmallProb {   // one output block (class, Q2 = Q + delta, Q)
+    const int64_t* in_base;    // the class's per-operator input offsets (device)
+    const int64_t* out_base;   // the class's per-operator output offsets (device)
+    int64_t out_local;         // O'_k[Q2, Q] within an operator's output
+    int64_t uQ, uQ2;           // element offsets of U_Q and U_Q2
+    int64_t in_local[kSmallSegs];   // per site state: block (q2, q) in an operator's input, -1: none
+    int32_t bq[kSmallSegs], bq2[kSmallSegs];      // rows of the block sectors q and q2
+    int32_t segQ[kSmallSegs], segQ2[kSmallSegs];  // first rows of segment s in U_Q and U_Q2
+    int32_t kQ, kQ2, nseg;
+};
+
+// Work item x = (problem, operator of its class) goes to warp x % kSmallWarps of block
+// x / kSmallWarps.  A lane owns output entries o = lane + 32 i of the kQ2 x kQ block:
+//   T_s[x][j] = sum_y O_k[q2, q][x][y] U_Q[seg s + y][j]        (shared memory)
+//   A[e][j]  += sum_x U_Q2[seg s + x][e] T_s[x][j]                (shared memory, own entries)
+// Dynamic shared memory: per warp, T_s and A of cap = (largest sector)^2 entries each.
+template <typename T>
+__global__ void __launch_bounds__(kSmallWarps * 32)
+blocked_small_kernel(const SmallProb* __restrict__ probs, const int2* __restrict__ items,
+                     int64_t nitems, const T* __restrict__ U, const T* __restrict__ O,
+                     T* __restrict__ Oout, int cap) {
+    extern __shared__ __align__(16) unsigned char small_smem[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = int64_t(blockIdx.x) * kSmallWarps + w;
+    if (item >= nitems) return;   // whole warps only; no block-wide barrier below
+    const int2 it = items[item];
+    const SmallProb& P = probs[it.x];
+    const int kQ = P.kQ, kQ2 = P.kQ2, nout = kQ2 * kQ;
+    const int64_t ib = P.in_base[it.y];
+    T* Tw = reinterpret_cast<T*>(small_smem) + int64_t(w) * 2 * cap;
+    T* Aw = Tw + cap;
+    for (int o = lane; o < nout; o += 32) Aw[o] = T(0);
+    for (int s = 0; s < P.nseg; ++s) {
+        const int64_t il = P.in_local[s];
+        if (il < 0) continue;
+        const int bq = P.bq[s], bq2 = P.bq2[s];
+        const T* Ob = O + ib + il;
+        const T* Us = U + P.uQ + int64_t(P.segQ[s]) * kQ;
+        __syncwarp();
+        for (int o = lane; o < bq2 * kQ; o += 32) {
+            const int x = o / kQ, j = o - x * kQ;
+            T t = T(0);
+            for (int y = 0; y < bq; ++y) t = fma(Ob[x * bq + y], Us[y * kQ + j], t);
+            Tw[o] = t;
+        }
+        __syncwarp();
+        const T* U2 = U + P.uQ2 + int64_t(P.segQ2[s]) * kQ2;
+        for (int o = lane; o < nout; o += 32) {
+            const int e = o / kQ, j = o - e * kQ;
+            T a = Aw[o];
+            for (int x = 0; x < bq2; ++x) a = fma(U2[x * kQ2 + e], Tw[x * kQ + j], a);
+            Aw[o] = a;
+        }
+    }
+    T* out = Oout + P.out_base[it.y] + P.out_local;
+    for (int o = lane; o < nout; o += 32) out[o] = Aw[o];
+}
 
 int64_t ld_for(int64_t x, int64_t align) { return (x + align - 1) / align * align; }
 size_t a128(size_t x) { return (x + 127) / 128 * 128; }
@@ -100,6 +168,12 @@ struct dmrg_blocked_plan_s {
         int64_t half_elems = 0;                // elements of one half (hi or lo)
     };
     TcLayout tl[2];                          // [0] BF16 (ld multiple of 8), [1] TF32 (of 4)
+    // fused small-sector path (every sector <= kSmallMax states, d <= kSmallSegs)
+    bool small_ok = false;
+    int small_cap = 0;                 // (largest sector)^2
+    SmallProb* d_small = nullptr;
+    int2* d_small_items = nullptr;
+    int64_t n_small_items = 0;
     std::map<std::pair<const void*, int>, TcTables> tc_cache;
     std::vector<void*> device_allocs;
 };
@@ -272,6 +346,61 @@ int simt_tile_count(const SimtGemm& g) {
 
 // Device arena: class offset arrays, grouped plain-FMA problem tables and the pack-job
 // table (all element offsets, independent of the caller's pointers).
+// Tables of the fused small-sector path: one problem per second-product problem and one
+// work item per (problem, operator of its class).  Needs the class arrays on the device.
+dmrg_status upload_small(dmrg_blocked_plan_s& pl) {
+    const int d = pl.d;
+    pl.small_ok = d <= kSmallSegs;
+    for (int64_t m : pl.bm) pl.small_ok = pl.small_ok && m <= kSmallMax;
+    for (int64_t m : pl.km) pl.small_ok = pl.small_ok && m <= kSmallMax;
+    if (!pl.small_ok || pl.second.empty()) return DMRG_OK;
+    int64_t kmax = 1;
+    for (int64_t m : pl.bm) kmax = std::max(kmax, m);
+    for (int64_t m : pl.km) kmax = std::max(kmax, m);
+    pl.small_cap = int(kmax * kmax);
+    std::vector<SmallProb> probs(pl.second.size());
+    std::vector<int2> items;
+    for (size_t i = 0; i < pl.second.size(); ++i) {
+        const Second& p = pl.second[i];
+        const ShiftClass& cl = pl.classes[p.c];
+        SmallProb& sp = probs[i];
+        sp = SmallProb{};
+        sp.in_base = cl.d_in_base;
+        sp.out_base = cl.d_out_base;
+        sp.out_local = cl.out_local[p.Q];
+        sp.uQ = pl.uoff[p.Q];
+        sp.uQ2 = pl.uoff[p.Q2];
+        sp.kQ = int32_t(pl.km[p.Q]);
+        sp.kQ2 = int32_t(pl.km[p.Q2]);
+        sp.nseg = d;
+        for (int s = 0; s < d; ++s) {
+            const int q = pl.segq[size_t(p.Q) * d + s];
+            const int q2 = pl.segq[size_t(p.Q2) * d + s];
+            sp.in_local[s] = (q >= 0 && q2 >= 0) ? cl.in_local[q] : -1;
+            sp.bq[s] = q >= 0 ? int32_t(pl.bm[q]) : 0;
+            sp.bq2[s] = q2 >= 0 ? int32_t(pl.bm[q2]) : 0;
+            sp.segQ[s] = int32_t(pl.segoff[size_t(p.Q) * d + s]);
+            sp.segQ2[s] = int32_t(pl.segoff[size_t(p.Q2) * d + s]);
+        }
+        for (size_t k = 0; k < cl.ops.size(); ++k) items.push_back(make_int2(int(i), int(k)));
+    }
+    pl.n_small_items = int64_t(items.size());
+    if ((pl.n_small_items + kSmallWarps - 1) / kSmallWarps > 0x7fffffffLL) {
+        pl.small_ok = false;
+        return DMRG_OK;
+    }
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&pl.d_small), probs.size() * sizeof(SmallProb));
+    if (e != cudaSuccess) return DMRG_ERR_CUDA;
+    pl.device_allocs.push_back(pl.d_small);
+    e = cudaMalloc(reinterpret_cast<void**>(&pl.d_small_items), std::max<size_t>(items.size(), 1) * sizeof(int2));
+    if (e != cudaSuccess) return DMRG_ERR_CUDA;
+    pl.device_allocs.push_back(pl.d_small_items);
+    e = cudaMemcpy(pl.d_small, probs.data(), probs.size() * sizeof(SmallProb), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(pl.d_small_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? DMRG_OK : DMRG_ERR_CUDA;
+}
+
 dmrg_status upload_static(dmrg_blocked_plan_s& pl) {
     const int S = pl.S, d = pl.d;
     // plain-FMA problems
@@ -426,7 +555,8 @@ dmrg_status upload_static(dmrg_blocked_plan_s& pl) {
         pl.n_pack = int(jobs.size());
     }
     e = cudaMemcpy(pl.d_arena, host.data(), host.size(), cudaMemcpyHostToDevice);
-    return e == cudaSuccess ? DMRG_OK : DMRG_ERR_CUDA;
+    if (e != cudaSuccess) return DMRG_ERR_CUDA;
+    return upload_small(pl);
 }
 
 PackJob* pack_table(dmrg_blocked_plan_s& pl, bool tf32) {
@@ -529,9 +659,18 @@ size_t simt_ws_bytes(const dmrg_blocked_plan_s& pl, dmrg_precision p) {
     return W.total;
 }
 
+// The fused small-sector path in FP32: U and (FP64 inputs) O converted first.
+WsLayout small_layout(const dmrg_blocked_plan_s& pl) {
+    WsLayout W;
+    W.add("U32", size_t(pl.u_elems) * 4);
+    W.add("O32", size_t(pl.in_elems) * 4);
+    return W;
+}
+
 size_t ws_bytes(const dmrg_blocked_plan_s& pl, dmrg_precision p) {
-    if (p == DMRG_PREC_FP64 || p == DMRG_PREC_FP32) return simt_ws_bytes(pl, p);
-    return std::max<size_t>(256, p == DMRG_PREC_BF16X3 ? pl.tc_bytes_split : pl.tc_bytes_tf32);
+    const size_t small = (pl.small_ok && p != DMRG_PREC_FP64) ? small_layout(pl).total : 0;
+    if (p == DMRG_PREC_FP64 || p == DMRG_PREC_FP32) return std::max(small, simt_ws_bytes(pl, p));
+    return std::max<size_t>({256, small, p == DMRG_PREC_BF16X3 ? pl.tc_bytes_split : pl.tc_bytes_tf32});
 }
 
 }  // namespace
@@ -621,6 +760,54 @@ dmrg_status dmrg_rotate_ops_blocked(dmrg_handle h, dmrg_blocked_plan pl, const d
     dmrg_status st = check_ws(h, ws, ws_len, ws_bytes(*pl, p));
     if (st != DMRG_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (pl->small_ok && h->blocked_small) {
+        char key[200];
+        snprintf(key, sizeof key, "blks:%p:%p:%p:%p:%p:%p:%d:%d", (void*)pl, (const void*)U, O, Oout, ws,
+                 (void*)s, int(p), in_is_fp64);
+        return run_maybe_graph(h, key, s, [&](cudaStream_t cs) -> dmrg_status {
+            const unsigned blocks = unsigned((pl->n_small_items + kSmallWarps - 1) / kSmallWarps);
+            const size_t smem = size_t(kSmallWarps) * 2 * pl->small_cap * (p == DMRG_PREC_FP64 ? 8 : 4);
+            cudaError_t e;
+            if (p == DMRG_PREC_FP64) {
+                e = cudaFuncSetAttribute(blocked_small_kernel<double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+                if (e == cudaSuccess)
+                    e = timed_launch(h, "blk_small", cs, [&] {
+                        blocked_small_kernel<double><<<blocks, kSmallWarps * 32, smem, cs>>>(
+                            pl->d_small, pl->d_small_items, pl->n_small_items, U,
+                            static_cast<const double*>(O), static_cast<double*>(Oout), pl->small_cap);
+                        return cudaGetLastError();
+                    });
+                return cuda_fail(h, e, "small-sector rotation");
+            }
+            const WsLayout W = small_layout(*pl);
+            char* base = static_cast<char*>(ws);
+            float* U32 = reinterpret_cast<float*>(base + W.offsets[0]);
+            float* O32 = in_is_fp64 ? reinterpret_cast<float*>(base + W.offsets[1])
+                                    : static_cast<float*>(const_cast<void*>(O));
+            PackJob jobs[2] = {};
+            int nj = 0;
+            auto conv = [&](const void* src, float* dst, int64_t n) {
+                PackJob& j = jobs[nj++];
+                j.src = src; j.src_f64 = 1; j.mode = 2; j.rows = 1; j.cols = n; j.rows_per_op = 1;
+                j.rdiv = 1; j.s_r_hi = n; j.s_c = 1; j.dst0 = dst; j.ld = n;
+            };
+            conv(U, U32, pl->u_elems);
+            if (in_is_fp64) conv(O, O32, pl->in_elems);
+            e = timed_launch(h, "blk_convert_fp32", cs, [&] { return pack_launch(jobs, nj, nullptr, cs); });
+            if (e != cudaSuccess) return cuda_fail(h, e, "convert");
+            e = cudaFuncSetAttribute(blocked_small_kernel<float>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            if (e == cudaSuccess)
+                e = timed_launch(h, "blk_small", cs, [&] {
+                    blocked_small_kernel<float><<<blocks, kSmallWarps * 32, smem, cs>>>(
+                        pl->d_small, pl->d_small_items, pl->n_small_items, U32, O32,
+                        static_cast<float*>(Oout), pl->small_cap);
+                    return cudaGetLastError();
+                });
+            return cuda_fail(h, e, "small-sector rotation");
+        });
+    }
     const bool tc = (p == DMRG_PREC_TF32 || p == DMRG_PREC_BF16X3);
     if (tc && !tc_supported(h)) return fail(h, DMRG_ERR_UNSUPPORTED, "tensor cores need sm_103");
     TcTables* T = nullptr;

@@ -33,8 +33,19 @@ def per_op_slices(in_shapes, out_shapes):
     return ins, outs
 
 
-def run_gpu(P, w, prec, plan=None):
-    plan = plan or P.dmrg_blocked_plan_create(w.block_sectors, w.site_shifts, w.kept_sectors, w.op_shifts)
+@pytest.fixture(scope="module")
+def grouped_handle(P):
+    """A handle on which every plan takes the grouped GEMM paths (the fused
+    small-sector kernel switched off)."""
+    h = P.Handle()
+    P.dmrg_set_option("blocked_small", 0, handle=h)
+    yield h
+    h.close()
+
+
+def run_gpu(P, w, prec, plan=None, handle=None):
+    plan = plan or P.dmrg_blocked_plan_create(w.block_sectors, w.site_shifts, w.kept_sectors, w.op_shifts,
+                                              handle=handle)
     dev = torch.device("cuda")
     U = torch.from_numpy(w.U_blocks).to(dev)
     O = torch.from_numpy(w.O_blocks).to(dev, torch.float64 if prec != "fp32" else torch.float32)
@@ -76,15 +87,34 @@ def random_structure(seed, nu=4, nd=3, maxdim=9, K=6, keep_frac=1.0):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "tf32"])
-@pytest.mark.parametrize("seed,maxdim,keep", [(1, 5, 1.0), (2, 40, 0.7), (3, 130, 0.5)])
-def test_random_sectors(P, prec, seed, maxdim, keep):
+@pytest.mark.parametrize("seed,maxdim,keep", [(1, 5, 1.0), (5, 32, 1.0), (2, 40, 0.7), (3, 130, 0.5)])
+@pytest.mark.parametrize("grouped", [False, True])
+def test_random_sectors(P, grouped_handle, prec, seed, maxdim, keep, grouped):
+    # maxdim <= 32: the fused small-sector kernel by default, the grouped GEMMs when
+    # switched off; larger sectors always take the grouped GEMMs
     w, osh = random_structure(seed, maxdim=maxdim, keep_frac=keep, K=7)
     ref = oracle.rotate_blocked(w.block_sectors, w.site_shifts, w.kept_sectors, w.op_shifts,
                                 w.U_blocks, w.O_blocks if prec != "fp32" else
                                 w.O_blocks.astype(np.float32).astype(np.float64), w.out_size)
-    got, plan = run_gpu(P, w, prec)
+    got, plan = run_gpu(P, w, prec, handle=grouped_handle if grouped else None)
     assert got.shape == ref.shape
     assert rel_blocks(got, ref, osh) <= TOL[prec]
+
+
+def test_small_sector_kernel_is_fp32_accurate(P):
+    # The fused small-sector kernel computes the reduced precisions in FP32: all of
+    # them agree with the oracle to FP32 rounding, well inside their own bars.
+    w, osh = random_structure(6, maxdim=20, K=9)
+    ref = oracle.rotate_blocked(w.block_sectors, w.site_shifts, w.kept_sectors, w.op_shifts,
+                                w.U_blocks, w.O_blocks.astype(np.float32).astype(np.float64), w.out_size)
+    for prec in ("bf16x3", "tf32"):
+        plan = P.dmrg_blocked_plan_create(w.block_sectors, w.site_shifts, w.kept_sectors, w.op_shifts)
+        dev = torch.device("cuda")
+        U = torch.from_numpy(w.U_blocks).to(dev)
+        O = torch.from_numpy(w.O_blocks).to(dev, torch.float32)
+        got = P.dmrg_rotate_ops_blocked(plan, U, O, prec).double().cpu().numpy()
+        P.dmrg_sync_status()
+        assert rel_blocks(got, ref, osh) <= 1e-6, prec
 
 
 def test_plan_sizes_and_stats(P):
@@ -105,7 +135,7 @@ def test_plan_errors(P):
 
 
 @pytest.mark.parametrize("name", ["blocked_m1000_k200_s4", "blocked_m1000_k200_s1.2"])
-def test_full_size_sampled(P, name):
+def test_full_size_sampled(P, grouped_handle, name):
     # The full-size workloads in the launch configuration of the benchmark; the
     # oracle recomputes a sample of operators (each operator's output depends only on
     # its own blocks).
@@ -115,9 +145,12 @@ def test_full_size_sampled(P, name):
     sample = [0, 1, 2, 3, 4, 5, 6, 7, w.K - 1]
     for prec in ("bf16x3", "fp32", "fp64", "tf32"):
         got, _ = run_gpu(P, w, prec)
+        # sigma = 4 (sectors of at most 10 states) also through the grouped GEMMs
+        got_g = run_gpu(P, w, prec, handle=grouped_handle)[0] if name.endswith("s4") else got
         for k in sample:
             (a, b), (c, e) = ins[k], outs[k]
             Ok = w.O_blocks[a:b] if prec != "fp32" else w.O_blocks[a:b].astype(np.float32).astype(np.float64)
             ref = oracle.rotate_blocked(w.block_sectors, w.site_shifts, w.kept_sectors,
                                         [w.op_shifts[k]], w.U_blocks, Ok, e - c)
             assert rel_blocks(got[c:e], ref, [osh[k]]) <= TOL[prec], (name, prec, k)
+            assert rel_blocks(got_g[c:e], ref, [osh[k]]) <= TOL[prec], (name, prec, k)
