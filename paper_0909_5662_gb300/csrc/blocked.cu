@@ -545,6 +545,7 @@ dmrg_status upload_static(dmrg_blocked_plan_s& pl) {
             j.dst0 = reinterpret_cast<void*>(intptr_t(eo * int64_t(es)));
             j.dst1 = li == 0 ? reinterpret_cast<void*>(intptr_t(half_bytes + eo * int64_t(es))) : nullptr;
             j.block_start = blocks;
+            pack_prepare(j);
             blocks += pack_blocks_for(j);
         }
         if (li == 0) pl.pack_blocks = blocks;

@@ -198,7 +198,13 @@ struct PackJob {
     int32_t rel, src_sel;
     int32_t vec8;          // set by the launcher: contiguous rows, 8 elements per thread
     int32_t tiled;         // set by the launcher: transposing gather through 32 x 32 tiles
+    // Set by pack_prepare: n / d == (n * m) >> s for 0 <= n < 2^31 (Granlund-Montgomery
+    // round-up multipliers) for d = cols, rows_per_op, rdiv, when the job fits 31 bits.
+    int32_t fastdiv;
+    int32_t s_cols, s_rpo, s_rdiv;
+    uint64_t m_cols, m_rpo, m_rdiv;
 };
+void pack_prepare(PackJob& j);
 cudaError_t pack_launch(const PackJob* jobs_host, int njobs, PackJob* jobs_dev_or_null,
                         cudaStream_t s);
 int64_t pack_blocks_for(const PackJob& j);

@@ -312,47 +312,83 @@ __device__ __forceinline__ void pack_store(const PackJob& j, int64_t dst, S x) {
     }
 }
 
-__global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constant__ PackLaunch L) {
-    const int b = blockIdx.x;
-    const PackJob* J = nullptr;
-    if (L.table == nullptr) {
-        int k = 0;
-        for (int i = 1; i < L.njobs; ++i)
-            if (L.inline_jobs[i].block_start <= b) k = i;
-        J = &L.inline_jobs[k];
-    } else {
-        int lo = 0, hi = L.njobs - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (L.table[mid].block_start <= b) lo = mid; else hi = mid - 1;
-        }
-        J = &L.table[lo];
-    }
-    PackJob j = *J;
-    if (j.rel) {
-        if (j.src_sel == 1) j.src_f64 = L.src1_f64;
-        const size_t es = j.src_f64 ? 8 : 4;
-        j.src = static_cast<const char*>(L.srcs[j.src_sel]) + reinterpret_cast<intptr_t>(j.src) * es;
-        j.dst0 = L.ws_base + reinterpret_cast<intptr_t>(j.dst0);
-        j.dst1 = j.dst1 ? L.ws_base + reinterpret_cast<intptr_t>(j.dst1) : nullptr;
-    }
+// General gather of one block's kPackThreads * kPackElems elements, thread-strided so
+// that neighbouring threads take neighbouring elements (coalesced stores, and loads where
+// source rows are contiguous).  The row / group / sub-row split uses the host's
+// multiply-shift divisors when the job fits 31 bits (a division is a long instruction
+// sequence, and this path is instruction-bound).
+__device__ __forceinline__ void pack_general(const PackJob& j, int64_t blk) {
     const int64_t total = j.rows * j.cols;
-    const int64_t e0 = (int64_t(b - j.block_start) * kPackThreads + threadIdx.x) * kPackElems;
+    const int64_t base = blk * (int64_t(kPackThreads) * kPackElems) + threadIdx.x;
 #pragma unroll
     for (int q = 0; q < kPackElems; ++q) {
-        const int64_t e = e0 + q;
+        const int64_t e = base + int64_t(q) * kPackThreads;
         if (e >= total) break;
-        const int64_t r = e / j.cols;
-        const int64_t c = e - r * j.cols;
-        const int64_t g = r / j.rows_per_op;
-        const int64_t rr = r - g * j.rows_per_op;
-        const int64_t src = j.src_off + (j.op_off ? j.op_off[g] : g * j.s_op) +
-                            (rr / j.rdiv) * j.s_r_hi + (rr % j.rdiv) * j.s_r_lo + c * j.s_c;
+        int64_t r, c, g, hi, lo;
+        if (j.fastdiv) {
+            const uint32_t eu = uint32_t(e), cu = uint32_t(j.cols);
+            const uint32_t ru = uint32_t((uint64_t(eu) * j.m_cols) >> j.s_cols);
+            const uint32_t rpo = uint32_t(j.rows_per_op), rd = uint32_t(j.rdiv);
+            const uint32_t gu = uint32_t((uint64_t(ru) * j.m_rpo) >> j.s_rpo);
+            const uint32_t rr = ru - gu * rpo;
+            const uint32_t h = uint32_t((uint64_t(rr) * j.m_rdiv) >> j.s_rdiv);
+            r = ru;
+            c = eu - ru * cu;
+            g = gu;
+            hi = h;
+            lo = rr - h * rd;
+        } else {
+            r = e / j.cols;
+            c = e - r * j.cols;
+            g = r / j.rows_per_op;
+            const int64_t rr = r - g * j.rows_per_op;
+            hi = rr / j.rdiv;
+            lo = rr - hi * j.rdiv;
+        }
+        const int64_t src = j.src_off + (j.op_off ? j.op_off[g] : g * j.s_op) + hi * j.s_r_hi +
+                            lo * j.s_r_lo + c * j.s_c;
         if (j.src_f64)
             pack_store(j, r * j.ld + c, static_cast<const double*>(j.src)[src]);
         else
             pack_store(j, r * j.ld + c, static_cast<const float*>(j.src)[src]);
     }
+}
+
+// The block's job is found once (thread 0), copied word by word into shared memory by
+// the block, resolved (relative addresses) by thread 0, and read from there.
+__global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constant__ PackLaunch L) {
+    __shared__ __align__(16) PackJob sj;
+    __shared__ int sk;
+    const int b = blockIdx.x;
+    if (threadIdx.x == 0) {
+        int lo = 0;
+        if (L.table == nullptr) {
+            for (int i = 1; i < L.njobs; ++i)
+                if (L.inline_jobs[i].block_start <= b) lo = i;
+        } else {
+            int hi = L.njobs - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (L.table[mid].block_start <= b) lo = mid; else hi = mid - 1;
+            }
+        }
+        sk = lo;
+    }
+    __syncthreads();
+    const PackJob* J = L.table ? &L.table[sk] : &L.inline_jobs[sk];
+    static_assert(sizeof(PackJob) % 4 == 0, "PackJob is copied in 32-bit words");
+    for (int w = threadIdx.x; w < int(sizeof(PackJob) / 4); w += blockDim.x)
+        reinterpret_cast<uint32_t*>(&sj)[w] = reinterpret_cast<const uint32_t*>(J)[w];
+    __syncthreads();
+    if (threadIdx.x == 0 && sj.rel) {
+        if (sj.src_sel == 1) sj.src_f64 = L.src1_f64;
+        const size_t es = sj.src_f64 ? 8 : 4;
+        sj.src = static_cast<const char*>(L.srcs[sj.src_sel]) + reinterpret_cast<intptr_t>(sj.src) * es;
+        sj.dst0 = L.ws_base + reinterpret_cast<intptr_t>(sj.dst0);
+        sj.dst1 = sj.dst1 ? L.ws_base + reinterpret_cast<intptr_t>(sj.dst1) : nullptr;
+    }
+    __syncthreads();
+    pack_general(sj, int64_t(b - sj.block_start));
 }
 
 // Contiguous fast path: one 8-element unit v of a job whose source rows are
@@ -532,23 +568,7 @@ __global__ void __launch_bounds__(kPackThreads) pack_mixed_kernel(const __grid_c
         else pack_vec8_block<float>(j, int64_t(b - j.block_start));
         return;
     }
-    const int64_t total = j.rows * j.cols;
-    const int64_t e0 = (int64_t(b - j.block_start) * kPackThreads + threadIdx.x) * kPackElems;
-#pragma unroll
-    for (int q = 0; q < kPackElems; ++q) {
-        const int64_t e = e0 + q;
-        if (e >= total) break;
-        const int64_t r = e / j.cols;
-        const int64_t c = e - r * j.cols;
-        const int64_t g = r / j.rows_per_op;
-        const int64_t rr = r - g * j.rows_per_op;
-        const int64_t src = j.src_off + (j.op_off ? j.op_off[g] : g * j.s_op) +
-                            (rr / j.rdiv) * j.s_r_hi + (rr % j.rdiv) * j.s_r_lo + c * j.s_c;
-        if (j.src_f64)
-            pack_store(j, r * j.ld + c, static_cast<const double*>(j.src)[src]);
-        else
-            pack_store(j, r * j.ld + c, static_cast<const float*>(j.src)[src]);
-    }
+    pack_general(j, int64_t(b - j.block_start));
 }
 
 // FP32 sources in groups of rows_per_op rows at source stride s_op (no offset table),
@@ -656,6 +676,29 @@ cudaError_t tc_gemm_launch_grouped(TcMode mode, TcEpi epi, const TcLaunch& L, in
     return cudaErrorNotSupported;
 }
 
+namespace {
+// Round-up multiplier for n / d with 0 <= n < 2^31, 1 <= d < 2^31 (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", Thm. 4.2):
+// l = ceil(log2 d), s = 31 + l, m = ceil(2^s / d); then n / d == (n * m) >> s and
+// n * m < 2^64.
+void div_magic(int64_t d, uint64_t& m, int32_t& s) {
+    int l = 0;
+    while ((int64_t(1) << l) < d) ++l;
+    s = 31 + l;
+    m = ((uint64_t(1) << s) + uint64_t(d) - 1) / uint64_t(d);
+}
+}  // namespace
+
+void pack_prepare(PackJob& j) {
+    const int64_t lim = int64_t(1) << 31;
+    j.fastdiv = j.cols >= 1 && j.rows_per_op >= 1 && j.rdiv >= 1 && j.rows * j.cols < lim &&
+                j.cols < lim && j.rows_per_op < lim && j.rdiv < lim;
+    if (!j.fastdiv) return;
+    div_magic(j.cols, j.m_cols, j.s_cols);
+    div_magic(j.rows_per_op, j.m_rpo, j.s_rpo);
+    div_magic(j.rdiv, j.m_rdiv, j.s_rdiv);
+}
+
 int64_t pack_blocks_for(const PackJob& j) {
     const int64_t per = int64_t(kPackThreads) * kPackElems;
     return (j.rows * j.cols + per - 1) / per;
@@ -676,6 +719,7 @@ cudaError_t pack_launch(const PackJob* jobs, int njobs, PackJob* /*unused*/, cud
             const bool tl = !v8 && pack_tiled_ok(jobs[i]);
             PackJob& j = L.inline_jobs[n++];
             j = jobs[i];
+            pack_prepare(j);
             j.vec8 = v8 ? 1 : 0;
             j.tiled = tl ? 1 : 0;
             j.block_start = blocks;
