@@ -20,8 +20,8 @@
 //
 // Plans whose sectors all hold at most 32 states have nothing for a tensor-core tile:
 // there one warp per (operator, output block) computes sum_s U_Q2[seg s]^T O_k U_Q[seg s]
-// through shared memory in a single launch, in FP64 for the FP64 precision and in FP32
-// (more accurate than BF16x3 and TF32 asked for) otherwise.
+// through shared memory in one launch, in FP64 for the FP64 precision and in FP32 (more
+// accurate than BF16x3 and TF32 ask for) otherwise.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -63,7 +63,7 @@ struct TcTables {
 };
 
 // ---- fused small-sector path
-constexpr int kSmallMax = 32;    // largest sector (states) of the fused path
+constexpr int kSmallMax = 32;    // largest sector (states) of the fused kernel
 constexpr int kSmallSegs = 8;    // largest site dimension of the fused path
 constexpr int kSmallWarps = 8;   // warps (work items) per block
 
@@ -169,8 +169,11 @@ struct dmrg_blocked_plan_s {
     };
     TcLayout tl[2];                          // [0] BF16 (ld multiple of 8), [1] TF32 (of 4)
     // fused small-sector path (every sector <= kSmallMax states, d <= kSmallSegs)
-    bool small_ok = false;
-    int small_cap = 0;                 // (largest sector)^2
+    bool route_small = true;           // the handle's DMRG_OPT_BLOCKED_SMALL at plan creation
+    std::vector<Second> small_second;  // output blocks of the fused kernel (all sectors <= 32)
+    int64_t n_first_all = 0, n_second_all = 0;   // problems of both routes (statistics)
+    bool small_ok = false;             // small_second is non-empty and its tables are uploaded
+    int small_cap = 0;                 // (largest sector of the fused problems)^2
     SmallProb* d_small = nullptr;
     int2* d_small_items = nullptr;
     int64_t n_small_items = 0;
@@ -196,12 +199,19 @@ void build_tc_layout(dmrg_blocked_plan_s& pl, dmrg_blocked_plan_s::TcLayout& L, 
         return o;
     };
     const int C = int(pl.classes.size());
+    // only the operands of the grouped problems (the fused kernel reads its own)
+    std::vector<char> need_a(size_t(C) * S, 0), need_b1(size_t(P) * d, 0), need_b2(P, 0);
+    for (const First& f : pl.first) {
+        need_a[size_t(f.c) * S + f.q] = 1;
+        need_b1[size_t(f.Q) * d + f.s] = 1;
+    }
+    for (const Second& p : pl.second) need_b2[p.Q2] = 1;
     L.a_off.assign(size_t(C) * S, -1);
     L.a_ld.assign(size_t(C) * S, 0);
     for (int c = 0; c < C; ++c) {
         const ShiftClass& cl = pl.classes[c];
         for (int q = 0; q < S; ++q) {
-            if (cl.in_local[q] < 0) continue;
+            if (cl.in_local[q] < 0 || !need_a[size_t(c) * S + q]) continue;
             const int q2 = find_label(pl.bu, pl.bd, pl.bu[q] + cl.du, pl.bd[q] + cl.dd);
             const int64_t ld = ld_for(pl.bm[q], al);
             L.a_ld[size_t(c) * S + q] = ld;
@@ -212,12 +222,13 @@ void build_tc_layout(dmrg_blocked_plan_s& pl, dmrg_blocked_plan_s::TcLayout& L, 
     for (int Q = 0; Q < P; ++Q)
         for (int s = 0; s < d; ++s) {
             const int q = pl.segq[size_t(Q) * d + s];
-            if (q < 0) continue;
+            if (q < 0 || !need_b1[size_t(Q) * d + s]) continue;
             L.b1_off[size_t(Q) * d + s] = take(pl.km[Q] * ld_for(pl.bm[q], al));
         }
     L.b2_off.assign(P, -1);
     L.b2_ld.assign(P, 0);
     for (int Q = 0; Q < P; ++Q) {
+        if (!need_b2[Q]) continue;
         L.b2_ld[Q] = ld_for(pl.D[Q], al);
         L.b2_off[Q] = take(pl.km[Q] * L.b2_ld[Q]);
     }
@@ -292,16 +303,34 @@ dmrg_status build_plan(dmrg_blocked_plan_s& pl) {
     }
     pl.in_elems = in_off;
     pl.out_elems = out_off;
-    // problems
+    // problems: all to the fused kernel when every sector holds at most kSmallMax states
+    // (mixing both routes measured slower: the grouped launch's time is set by its
+    // largest blocks, and the fused kernel's work grows as the cube of the sector size)
+    bool all_small = pl.route_small && d <= kSmallSegs;
+    for (int64_t m : pl.bm) all_small = all_small && m <= kSmallMax;
+    for (int64_t m : pl.km) all_small = all_small && m <= kSmallMax;
     for (int c = 0; c < int(pl.classes.size()); ++c) {
         const ShiftClass& cl = pl.classes[c];
         const double nc = double(cl.ops.size());
         for (int Q = 0; Q < P; ++Q) {
             if (cl.out_local[Q] < 0) continue;
             const int Q2 = find_label(pl.ku, pl.kd, pl.ku[Q] + cl.du, pl.kd[Q] + cl.dd);
+            pl.flops += 2.0 * nc * pl.km[Q2] * pl.D[Q2] * pl.km[Q];
+            ++pl.n_second_all;
+            // output blocks whose sectors all hold at most kSmallMax states: fused kernel
+            if (all_small) {
+                pl.small_second.push_back({c, Q2, Q});
+                for (int s = 0; s < d; ++s) {
+                    const int q = pl.segq[size_t(Q) * d + s];
+                    const int q2 = pl.segq[size_t(Q2) * d + s];
+                    if (q < 0 || q2 < 0) continue;
+                    ++pl.n_first_all;
+                    pl.flops += 2.0 * nc * pl.bm[q2] * pl.bm[q] * pl.km[Q];
+                }
+                continue;
+            }
             const int p2 = int(pl.second.size());
             pl.second.push_back({c, Q2, Q});
-            pl.flops += 2.0 * nc * pl.km[Q2] * pl.D[Q2] * pl.km[Q];
             for (int s = 0; s < d; ++s) {
                 const int q = pl.segq[size_t(Q) * d + s];
                 const int q2 = pl.segq[size_t(Q2) * d + s];
@@ -311,6 +340,7 @@ dmrg_status build_plan(dmrg_blocked_plan_s& pl) {
                     continue;
                 }
                 pl.first.push_back({c, Q2, Q, s, q, q2, p2});
+                ++pl.n_first_all;
                 pl.flops += 2.0 * nc * pl.bm[q2] * pl.bm[q] * pl.km[Q];
             }
         }
@@ -346,22 +376,17 @@ int simt_tile_count(const SimtGemm& g) {
 
 // Device arena: class offset arrays, grouped plain-FMA problem tables and the pack-job
 // table (all element offsets, independent of the caller's pointers).
-// Tables of the fused small-sector path: one problem per second-product problem and one
+// Tables of the fused small-sector path: one problem per routed output block and one
 // work item per (problem, operator of its class).  Needs the class arrays on the device.
 dmrg_status upload_small(dmrg_blocked_plan_s& pl) {
     const int d = pl.d;
-    pl.small_ok = d <= kSmallSegs;
-    for (int64_t m : pl.bm) pl.small_ok = pl.small_ok && m <= kSmallMax;
-    for (int64_t m : pl.km) pl.small_ok = pl.small_ok && m <= kSmallMax;
-    if (!pl.small_ok || pl.second.empty()) return DMRG_OK;
+    pl.small_ok = false;
+    if (pl.small_second.empty()) return DMRG_OK;
     int64_t kmax = 1;
-    for (int64_t m : pl.bm) kmax = std::max(kmax, m);
-    for (int64_t m : pl.km) kmax = std::max(kmax, m);
-    pl.small_cap = int(kmax * kmax);
-    std::vector<SmallProb> probs(pl.second.size());
+    std::vector<SmallProb> probs(pl.small_second.size());
     std::vector<int2> items;
-    for (size_t i = 0; i < pl.second.size(); ++i) {
-        const Second& p = pl.second[i];
+    for (size_t i = 0; i < pl.small_second.size(); ++i) {
+        const Second& p = pl.small_second[i];
         const ShiftClass& cl = pl.classes[p.c];
         SmallProb& sp = probs[i];
         sp = SmallProb{};
@@ -373,6 +398,7 @@ dmrg_status upload_small(dmrg_blocked_plan_s& pl) {
         sp.kQ = int32_t(pl.km[p.Q]);
         sp.kQ2 = int32_t(pl.km[p.Q2]);
         sp.nseg = d;
+        kmax = std::max({kmax, pl.km[p.Q], pl.km[p.Q2]});
         for (int s = 0; s < d; ++s) {
             const int q = pl.segq[size_t(p.Q) * d + s];
             const int q2 = pl.segq[size_t(p.Q2) * d + s];
@@ -381,24 +407,26 @@ dmrg_status upload_small(dmrg_blocked_plan_s& pl) {
             sp.bq2[s] = q2 >= 0 ? int32_t(pl.bm[q2]) : 0;
             sp.segQ[s] = int32_t(pl.segoff[size_t(p.Q) * d + s]);
             sp.segQ2[s] = int32_t(pl.segoff[size_t(p.Q2) * d + s]);
+            kmax = std::max<int64_t>({kmax, sp.bq[s], sp.bq2[s]});
         }
         for (size_t k = 0; k < cl.ops.size(); ++k) items.push_back(make_int2(int(i), int(k)));
     }
+    pl.small_cap = int(kmax * kmax);
     pl.n_small_items = int64_t(items.size());
-    if ((pl.n_small_items + kSmallWarps - 1) / kSmallWarps > 0x7fffffffLL) {
-        pl.small_ok = false;
-        return DMRG_OK;
-    }
+    if (pl.n_small_items == 0) return DMRG_OK;
+    if ((pl.n_small_items + kSmallWarps - 1) / kSmallWarps > 0x7fffffffLL) return DMRG_ERR_SHAPE;
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&pl.d_small), probs.size() * sizeof(SmallProb));
     if (e != cudaSuccess) return DMRG_ERR_CUDA;
     pl.device_allocs.push_back(pl.d_small);
-    e = cudaMalloc(reinterpret_cast<void**>(&pl.d_small_items), std::max<size_t>(items.size(), 1) * sizeof(int2));
+    e = cudaMalloc(reinterpret_cast<void**>(&pl.d_small_items), items.size() * sizeof(int2));
     if (e != cudaSuccess) return DMRG_ERR_CUDA;
     pl.device_allocs.push_back(pl.d_small_items);
     e = cudaMemcpy(pl.d_small, probs.data(), probs.size() * sizeof(SmallProb), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(pl.d_small_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice);
-    return e == cudaSuccess ? DMRG_OK : DMRG_ERR_CUDA;
+    if (e != cudaSuccess) return DMRG_ERR_CUDA;
+    pl.small_ok = true;
+    return DMRG_OK;
 }
 
 dmrg_status upload_static(dmrg_blocked_plan_s& pl) {
@@ -489,6 +517,7 @@ dmrg_status upload_static(dmrg_blocked_plan_s& pl) {
                 jobs.push_back(j);
             }
         for (int Q = 0; Q < pl.P; ++Q) {
+            if (L.b2_off[Q] < 0) continue;
             PackJob j{};
             j.rel = 1; j.src_sel = 0; j.src_f64 = 1; j.mode = li == 0 ? 0 : 1;
             j.src_off = pl.uoff[Q];
@@ -674,6 +703,52 @@ size_t ws_bytes(const dmrg_blocked_plan_s& pl, dmrg_precision p) {
     return std::max<size_t>({256, small, p == DMRG_PREC_BF16X3 ? pl.tc_bytes_split : pl.tc_bytes_tf32});
 }
 
+// The fused small-sector kernel over the plan's routed output blocks.
+dmrg_status run_small(dmrg_handle h, const dmrg_blocked_plan_s* pl, const double* U, const void* O,
+                      int in_is_fp64, void* Oout, dmrg_precision p, void* ws, cudaStream_t cs) {
+    const unsigned blocks = unsigned((pl->n_small_items + kSmallWarps - 1) / kSmallWarps);
+    const size_t smem = size_t(kSmallWarps) * 2 * pl->small_cap * (p == DMRG_PREC_FP64 ? 8 : 4);
+    cudaError_t e;
+    if (p == DMRG_PREC_FP64) {
+        e = cudaFuncSetAttribute(blocked_small_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(smem));
+        if (e == cudaSuccess)
+            e = timed_launch(h, "blk_small", cs, [&] {
+                blocked_small_kernel<double><<<blocks, kSmallWarps * 32, smem, cs>>>(
+                    pl->d_small, pl->d_small_items, pl->n_small_items, U, static_cast<const double*>(O),
+                    static_cast<double*>(Oout), pl->small_cap);
+                return cudaGetLastError();
+            });
+        return cuda_fail(h, e, "small-sector rotation");
+    }
+    const WsLayout W = small_layout(*pl);
+    char* base = static_cast<char*>(ws);
+    float* U32 = reinterpret_cast<float*>(base + W.offsets[0]);
+    const float* O32 = in_is_fp64 ? reinterpret_cast<const float*>(base + W.offsets[1])
+                                  : static_cast<const float*>(O);
+    PackJob jobs[2] = {};
+    int nj = 0;
+    auto conv = [&](const void* src, float* dst, int64_t n) {
+        PackJob& j = jobs[nj++];
+        j.src = src; j.src_f64 = 1; j.mode = 2; j.rows = 1; j.cols = n; j.rows_per_op = 1;
+        j.rdiv = 1; j.s_r_hi = n; j.s_c = 1; j.dst0 = dst; j.ld = n;
+    };
+    conv(U, U32, pl->u_elems);
+    if (in_is_fp64) conv(O, reinterpret_cast<float*>(base + W.offsets[1]), pl->in_elems);
+    e = timed_launch(h, "blk_convert_fp32", cs, [&] { return pack_launch(jobs, nj, nullptr, cs); });
+    if (e != cudaSuccess) return cuda_fail(h, e, "convert");
+    e = cudaFuncSetAttribute(blocked_small_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(smem));
+    if (e == cudaSuccess)
+        e = timed_launch(h, "blk_small", cs, [&] {
+            blocked_small_kernel<float><<<blocks, kSmallWarps * 32, smem, cs>>>(
+                pl->d_small, pl->d_small_items, pl->n_small_items, U32, O32, static_cast<float*>(Oout),
+                pl->small_cap);
+            return cudaGetLastError();
+        });
+    return cuda_fail(h, e, "small-sector rotation");
+}
+
 }  // namespace
 
 extern "C" {
@@ -688,6 +763,7 @@ dmrg_status dmrg_blocked_plan_create(dmrg_handle h, const dmrg_qn_sector* bs, in
     if (!bs || !ss || !ks || (K > 0 && !os)) return fail(h, DMRG_ERR_INVALID_ARG, "null array");
     auto* pl = new dmrg_blocked_plan_s();
     pl->h = h;
+    pl->route_small = h->blocked_small;
     pl->S = nb; pl->d = d; pl->P = nk; pl->K = K;
     for (int i = 0; i < nb; ++i) {
         if (bs[i].dim < 1) { delete pl; return fail(h, DMRG_ERR_SHAPE, "block sector of size < 1"); }
@@ -742,8 +818,8 @@ dmrg_status dmrg_blocked_plan_sizes(dmrg_blocked_plan pl, dmrg_precision p, int6
 
 dmrg_status dmrg_blocked_plan_stats(dmrg_blocked_plan pl, int64_t* n1, int64_t* n2, double* flops) {
     if (!pl) return DMRG_ERR_INVALID_ARG;
-    if (n1) *n1 = int64_t(pl->first.size());
-    if (n2) *n2 = int64_t(pl->second.size());
+    if (n1) *n1 = pl->n_first_all;
+    if (n2) *n2 = pl->n_second_all;
     if (flops) *flops = pl->flops;
     return DMRG_OK;
 }
@@ -761,64 +837,21 @@ dmrg_status dmrg_rotate_ops_blocked(dmrg_handle h, dmrg_blocked_plan pl, const d
     dmrg_status st = check_ws(h, ws, ws_len, ws_bytes(*pl, p));
     if (st != DMRG_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (pl->small_ok && h->blocked_small) {
-        char key[200];
-        snprintf(key, sizeof key, "blks:%p:%p:%p:%p:%p:%p:%d:%d", (void*)pl, (const void*)U, O, Oout, ws,
-                 (void*)s, int(p), in_is_fp64);
-        return run_maybe_graph(h, key, s, [&](cudaStream_t cs) -> dmrg_status {
-            const unsigned blocks = unsigned((pl->n_small_items + kSmallWarps - 1) / kSmallWarps);
-            const size_t smem = size_t(kSmallWarps) * 2 * pl->small_cap * (p == DMRG_PREC_FP64 ? 8 : 4);
-            cudaError_t e;
-            if (p == DMRG_PREC_FP64) {
-                e = cudaFuncSetAttribute(blocked_small_kernel<double>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-                if (e == cudaSuccess)
-                    e = timed_launch(h, "blk_small", cs, [&] {
-                        blocked_small_kernel<double><<<blocks, kSmallWarps * 32, smem, cs>>>(
-                            pl->d_small, pl->d_small_items, pl->n_small_items, U,
-                            static_cast<const double*>(O), static_cast<double*>(Oout), pl->small_cap);
-                        return cudaGetLastError();
-                    });
-                return cuda_fail(h, e, "small-sector rotation");
-            }
-            const WsLayout W = small_layout(*pl);
-            char* base = static_cast<char*>(ws);
-            float* U32 = reinterpret_cast<float*>(base + W.offsets[0]);
-            float* O32 = in_is_fp64 ? reinterpret_cast<float*>(base + W.offsets[1])
-                                    : static_cast<float*>(const_cast<void*>(O));
-            PackJob jobs[2] = {};
-            int nj = 0;
-            auto conv = [&](const void* src, float* dst, int64_t n) {
-                PackJob& j = jobs[nj++];
-                j.src = src; j.src_f64 = 1; j.mode = 2; j.rows = 1; j.cols = n; j.rows_per_op = 1;
-                j.rdiv = 1; j.s_r_hi = n; j.s_c = 1; j.dst0 = dst; j.ld = n;
-            };
-            conv(U, U32, pl->u_elems);
-            if (in_is_fp64) conv(O, O32, pl->in_elems);
-            e = timed_launch(h, "blk_convert_fp32", cs, [&] { return pack_launch(jobs, nj, nullptr, cs); });
-            if (e != cudaSuccess) return cuda_fail(h, e, "convert");
-            e = cudaFuncSetAttribute(blocked_small_kernel<float>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-            if (e == cudaSuccess)
-                e = timed_launch(h, "blk_small", cs, [&] {
-                    blocked_small_kernel<float><<<blocks, kSmallWarps * 32, smem, cs>>>(
-                        pl->d_small, pl->d_small_items, pl->n_small_items, U32, O32,
-                        static_cast<float*>(Oout), pl->small_cap);
-                    return cudaGetLastError();
-                });
-            return cuda_fail(h, e, "small-sector rotation");
-        });
-    }
     const bool tc = (p == DMRG_PREC_TF32 || p == DMRG_PREC_BF16X3);
     if (tc && !tc_supported(h)) return fail(h, DMRG_ERR_UNSUPPORTED, "tensor cores need sm_103");
     TcTables* T = nullptr;
-    if (tc && (st = tc_tables(*pl, ws, p == DMRG_PREC_TF32, T)) != DMRG_OK)
+    if (tc && !pl->second.empty() && (st = tc_tables(*pl, ws, p == DMRG_PREC_TF32, T)) != DMRG_OK)
         return fail(h, st, "tensor-core tables");
     char key[200];
     snprintf(key, sizeof key, "blk:%p:%p:%p:%p:%p:%p:%d:%d", (void*)pl, (const void*)U, O, Oout, ws,
              (void*)s, int(p), in_is_fp64);
     return run_maybe_graph(h, key, s, [&](cudaStream_t cs) -> dmrg_status {
         cudaError_t e;
+        if (pl->small_ok) {
+            const dmrg_status rs = run_small(h, pl, U, O, in_is_fp64, Oout, p, ws, cs);
+            if (rs != DMRG_OK) return rs;
+        }
+        if (pl->second.empty()) return DMRG_OK;
         if (!tc) {
             const bool f64 = (p == DMRG_PREC_FP64);
             const Real rt = f64 ? Real::F64 : Real::F32;

@@ -90,8 +90,9 @@ def random_structure(seed, nu=4, nd=3, maxdim=9, K=6, keep_frac=1.0):
 @pytest.mark.parametrize("seed,maxdim,keep", [(1, 5, 1.0), (5, 32, 1.0), (2, 40, 0.7), (3, 130, 0.5)])
 @pytest.mark.parametrize("grouped", [False, True])
 def test_random_sectors(P, grouped_handle, prec, seed, maxdim, keep, grouped):
-    # maxdim <= 32: the fused small-sector kernel by default, the grouped GEMMs when
-    # switched off; larger sectors always take the grouped GEMMs
+    # by default plans whose sectors all hold <= 32 states take the fused kernel (maxdim
+    # 5 and 32), the others the grouped GEMMs; with the fused kernel switched off,
+    # everything takes the grouped GEMMs
     w, osh = random_structure(seed, maxdim=maxdim, keep_frac=keep, K=7)
     ref = oracle.rotate_blocked(w.block_sectors, w.site_shifts, w.kept_sectors, w.op_shifts,
                                 w.U_blocks, w.O_blocks if prec != "fp32" else
@@ -104,7 +105,7 @@ def test_random_sectors(P, grouped_handle, prec, seed, maxdim, keep, grouped):
 def test_small_sector_kernel_is_fp32_accurate(P):
     # The fused small-sector kernel computes the reduced precisions in FP32: all of
     # them agree with the oracle to FP32 rounding, well inside their own bars.
-    w, osh = random_structure(6, maxdim=20, K=9)
+    w, osh = random_structure(6, maxdim=16, K=9)
     ref = oracle.rotate_blocked(w.block_sectors, w.site_shifts, w.kept_sectors, w.op_shifts,
                                 w.U_blocks, w.O_blocks.astype(np.float32).astype(np.float64), w.out_size)
     for prec in ("bf16x3", "tf32"):
@@ -145,8 +146,9 @@ def test_full_size_sampled(P, grouped_handle, name):
     sample = [0, 1, 2, 3, 4, 5, 6, 7, w.K - 1]
     for prec in ("bf16x3", "fp32", "fp64", "tf32"):
         got, _ = run_gpu(P, w, prec)
-        # sigma = 4 (sectors of at most 10 states) also through the grouped GEMMs
-        got_g = run_gpu(P, w, prec, handle=grouped_handle)[0] if name.endswith("s4") else got
+        # by default sigma = 4 (sectors of at most 10 states) takes the fused kernel;
+        # the grouped GEMMs alone on a second handle
+        got_g = run_gpu(P, w, prec, handle=grouped_handle)[0]
         for k in sample:
             (a, b), (c, e) = ins[k], outs[k]
             Ok = w.O_blocks[a:b] if prec != "fp32" else w.O_blocks[a:b].astype(np.float32).astype(np.float64)
