@@ -339,10 +339,11 @@ FP64_NOMINAL_GFLOPS = 1250.0
 
 def run_truncation(args):
     """The truncation matrix (Sec. 2, steps 3-4): rho = Psi Psi^T of a superblock
-    state with a ground-state-like Schmidt spectrum, its Jacobi eigen-decomposition
-    in FP64, the kept m' eigenvectors and the discarded weight.  Time per call, the
-    sweep kernel's FP64 rate against the nominal FP64 peak, and the FP64 CPU oracle
-    (the library eigh on the host cores) on the same state."""
+    state with a ground-state-like Schmidt spectrum, its eigen-decomposition in FP64, the
+    kept m' eigenvectors and the discarded weight.  Both solvers of the library (the
+    default tridiagonal one and the cyclic Jacobi sweeps): time per call, per-kernel
+    times, accuracy against the FP64 CPU oracle (the library eigh on the host cores),
+    and the oracle's own time on the same state."""
     import numpy as np
     import torch
     import paper_0909_5662_gb300 as P
@@ -358,46 +359,66 @@ def run_truncation(args):
         name = "truncation_n%d_mp%d" % (n, mp)
         Psi_np = schmidt_state(SEED_BASE + 8, n, n)
         Psi = torch.from_numpy(Psi_np).to(dev)
-        U, lam, eps, sweeps = P.dmrg_truncation(Psi, mp)
-        ms = _timed(lambda: P.dmrg_truncation(Psi, mp), steps, 1, flush)
-        kt = _with_kernel_timing(lambda: P.dmrg_truncation(Psi, mp), 1, flush)
-        P.dmrg_sync_status()
-        N = n + (n & 1)
-        npair = N // 2
-        # a rotation applied to a pair of entries is 6 flops: 4 per 2 x 2 block of A on
-        # the upper triangle of pairs (both triangles are written from it), 1 per
-        # (row, pair) of V; N - 1 rounds per sweep
-        flops_sweep = (N - 1) * (24.0 * npair * (npair + 1) / 2 + 6.0 * n * npair)
-        sw = kt.get("trunc_sweep", {})
-        achieved = flops_sweep / (sw["ms_per_launch"] * 1e-3) / 1e9 if sw else None
+        rho = Psi @ Psi.T
         if args.no_cpu_baseline:
-            lam_ref, eps_ref, t_cpu = lam.cpu().numpy(), float(eps.item()), float("nan")
+            lam_ref, eps_ref, t_cpu = None, None, float("nan")
         else:
             t0 = time.perf_counter()
             U_ref, lam_ref, eps_ref = oracle.truncation(Psi_np, mp)
             t_cpu = time.perf_counter() - t0
-        rho = Psi @ Psi.T
-        Uk = U
-        resid = float(torch.linalg.vector_norm(rho @ Uk - Uk * lam[:mp][None, :], dim=0).max())
-        res[name] = {
-            "ms_per_call": ms, "sweeps": sweeps, "kernels": kt,
-            "max_abs_eig_err_vs_oracle": float(np.abs(lam.cpu().numpy() - lam_ref).max()),
-            "eps": float(eps.item()), "eps_abs_err_vs_oracle": abs(float(eps.item()) - eps_ref),
-            "max_residual_rhoU_minus_Ulambda": resid,
-            "orthonormality_err": float(torch.linalg.matrix_norm(
-                Uk.T @ Uk - torch.eye(mp, dtype=torch.float64, device=dev)).item()),
-            "roofline": {"bound": "alu", "kernel": "trunc_sweep", "achieved": achieved,
-                         "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s (FP64)",
-                         "frac": achieved / FP64_NOMINAL_GFLOPS if achieved else None,
-                         "flops_per_launch": flops_sweep, "traffic": None,
-                         "peak_source": "nominal FP64 rate (no measured FP64 peak)"},
-            "cpu_baseline": None if args.no_cpu_baseline else {
-                "value": t_cpu * 1e3, "unit": "ms per call", "kind": "oracle",
-                "cores": oracle.num_threads(),
-                "sample": "the whole call: rho by rows, numpy.linalg.eigh, ranking"}}
+        row = {"cpu_baseline": None if args.no_cpu_baseline else {
+            "value": t_cpu * 1e3, "unit": "ms per call", "kind": "oracle", "cores": oracle.num_threads(),
+            "sample": "the whole call: rho by rows, numpy.linalg.eigh, ranking"}}
+        for method in ("tridiagonal", "jacobi"):
+            h = P.Handle()
+            P.dmrg_set_option("truncation_jacobi", 1 if method == "jacobi" else 0, handle=h)
+            call = lambda: P.dmrg_truncation(Psi, mp, handle=h)
+            U, lam, eps, sweeps = call()
+            ms = _timed(call, steps, 1, flush)
+            P.dmrg_kernel_timing(reset=True, handle=h)
+            P.dmrg_set_option("kernel_timing", 1, handle=h)
+            flush.zero_()
+            call()
+            torch.cuda.synchronize()
+            P.dmrg_set_option("kernel_timing", 0, handle=h)
+            kt = {k["kernel"]: {"ms_per_call": k["total_ms"], "launches_per_call": k["launches"]}
+                  for k in P.dmrg_kernel_timing(reset=True, handle=h)}
+            P.dmrg_sync_status(handle=h)
+            resid = float(torch.linalg.vector_norm(rho @ U - U * lam[:mp][None, :], dim=0).max())
+            ent = {"ms_per_call": ms, "sweeps": sweeps, "kernels": kt,
+                   "max_residual_rhoU_minus_Ulambda": resid,
+                   "orthonormality_err": float(torch.linalg.matrix_norm(
+                       U.T @ U - torch.eye(mp, dtype=torch.float64, device=dev)).item()),
+                   "eps": float(eps.item())}
+            if lam_ref is not None:
+                ent["max_abs_eig_err_vs_oracle"] = float(np.abs(lam.cpu().numpy() - lam_ref).max())
+                ent["eps_abs_err_vs_oracle"] = abs(float(eps.item()) - eps_ref)
+            if method == "jacobi" and "trunc_sweep" in kt:
+                N = n + (n & 1)
+                npair = N // 2
+                # a rotation of a pair of entries is 6 flops: 4 per 2 x 2 block of A on the
+                # upper triangle of pairs, 1 per (row, pair) of V; N - 1 rounds per sweep
+                flops_sweep = (N - 1) * (24.0 * npair * (npair + 1) / 2 + 6.0 * n * npair)
+                per = kt["trunc_sweep"]["ms_per_call"] / kt["trunc_sweep"]["launches_per_call"]
+                gf = flops_sweep / (per * 1e-3) / 1e9
+                ent["roofline"] = {"bound": "alu", "kernel": "trunc_sweep", "achieved": gf,
+                                   "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s (FP64)",
+                                   "frac": gf / FP64_NOMINAL_GFLOPS, "flops_per_launch": flops_sweep,
+                                   "traffic": None, "peak_source": "nominal FP64 rate"}
+            if method == "tridiagonal" and "trunc_tridiag" in kt:
+                # Householder tridiagonalisation: 4 n^3 / 3 flops (multiply-adds counted as 2)
+                gf = (4.0 * n ** 3 / 3.0) / (kt["trunc_tridiag"]["ms_per_call"] * 1e-3) / 1e9
+                ent["roofline"] = {"bound": "alu", "kernel": "trunc_tridiag", "achieved": gf,
+                                   "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s (FP64)",
+                                   "frac": gf / FP64_NOMINAL_GFLOPS,
+                                   "flops_per_launch": 4.0 * n ** 3 / 3.0, "traffic": None,
+                                   "peak_source": "nominal FP64 rate"}
+            row[method] = ent
+            h.close()
+        res[name] = row
     line = {"workload": "truncation of Schmidt-spectrum states (w_k ~ exp(-k/20)), "
                         "n = m d = 400 and 1600 rows, square Psi",
-            "metric": "truncation matrix: ms per call (rho, Jacobi sweeps, ranking, U, eps)",
+            "metric": "truncation matrix: ms per call (rho, eigen-decomposition, U, eps)",
             "steps": steps, "l2": "flushed between timed calls", "results": res, "data": "synthetic"}
     print(json.dumps(line), flush=True)
     return 0

@@ -114,6 +114,10 @@ DMRG_API dmrg_status dmrg_sync_status(dmrg_handle handle, dmrg_stream_t stream);
  *                              kernel, one warp per (operator, output block), in FP32
  *                              for the reduced precisions (more accurate than they
  *                              ask) and FP64 for DMRG_PREC_FP64; 0 = the grouped GEMMs.
+ *   DMRG_OPT_TRUNCATION_JACOBI : 1 = dmrg_truncation diagonalises rho by cyclic Jacobi
+ *                              sweeps; 0 (default) = Householder tridiagonalisation,
+ *                              bisection and inverse iteration (rows <= 6144; larger
+ *                              matrices take the Jacobi sweeps).
  *   DMRG_OPT_TEST_WITHHOLD_ARRIVAL : test hook for failure detection.  1 makes
  *                              the next dense tensor-core launch withhold one
  *                              shared-memory stage release in its first CTA, so
@@ -129,7 +133,8 @@ typedef enum {
     DMRG_OPT_TEST_WITHHOLD_ARRIVAL = 5,
     DMRG_OPT_DETERMINISTIC = 6,
     DMRG_OPT_ACCUM_CHAIN = 7,
-    DMRG_OPT_BLOCKED_SMALL = 8
+    DMRG_OPT_BLOCKED_SMALL = 8,
+    DMRG_OPT_TRUNCATION_JACOBI = 9
 } dmrg_option;
 DMRG_API dmrg_status dmrg_set_option(dmrg_handle handle, dmrg_option option, double value);
 
@@ -344,7 +349,9 @@ DMRG_API dmrg_status dmrg_structure_factor(dmrg_handle handle, const double* G, 
  *   lambda  device, rows FP64: all eigenvalues in decreasing order;
  *   eps     device, 1 FP64: the discarded weight sum_{a >= mp} lambda[a]
  *           (= 1 - sum of the kept eigenvalues for a normalized state);
- *   sweeps  host (may be NULL): sweeps done; -max_sweeps if the off-diagonal part
+ *   sweeps  host (may be NULL): 0 for the tridiagonal solver (the default, see
+ *           DMRG_OPT_TRUNCATION_JACOBI); for the Jacobi sweeps, the sweeps done;
+ *           -max_sweeps if the off-diagonal part
  *           did not fall below tol * ||rho||_F (the outputs then hold the last
  *           iterate).  A pair is rotated only if |rho_ab| exceeds both
  *           DBL_EPSILON * sqrt(|rho_aa rho_bb|) and (from the second sweep on)

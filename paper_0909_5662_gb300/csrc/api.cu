@@ -527,6 +527,9 @@ dmrg_status dmrg_set_option(dmrg_handle h, dmrg_option o, double v) {
             if (v < 0 || v > 1e9) return fail(h, DMRG_ERR_INVALID_ARG, "accum_chain must be >= 0");
             h->accum_chain = int(v);
             return DMRG_OK;
+        case DMRG_OPT_TRUNCATION_JACOBI:
+            h->trunc_jacobi = v != 0;
+            return DMRG_OK;
         case DMRG_OPT_BLOCKED_SMALL:
             h->blocked_small = v != 0;
             return DMRG_OK;

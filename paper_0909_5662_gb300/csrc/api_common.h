@@ -67,6 +67,13 @@ dmrg_status dense_simt_forward(dmrg_handle h, const double* U, int64_t m, int d,
                                dmrg_precision p, void* ws, cudaStream_t s, bool pack_u = true,
                                const double* U1 = nullptr, float* U1_32 = nullptr);
 
+// The truncation's eigen-decomposition by tridiagonalisation (tridiag.cu): workspace
+// layout for n rows and mp kept vectors (rho goes into its first section), and the
+// solver: U (n x mp), lambda (n, decreasing).
+WsLayout tridiag_layout(int64_t n, int64_t mp);
+dmrg_status tridiag_eigen(dmrg_handle h, int64_t n, int64_t mp, char* ws, double* U, double* lambda,
+                          double* eps, cudaStream_t s);
+
 cudaError_t tc_gemm_launch_grouped(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
                                    int bn_smem, cudaStream_t s);
 

@@ -231,6 +231,7 @@ struct dmrg_handle_s {
     double check_ortho_tol = 0.0;
     int drop_arrival_next = 0;      // test hook, consumed by the next tensor-core launch
     bool deterministic = false;     // no atomically accumulated split tiles
+    bool trunc_jacobi = false;      // truncation: cyclic Jacobi instead of the tridiagonal solver
     bool blocked_small = true;      // plans with sectors <= 32 states: fused small-sector kernel
     int accum_chain = 1024;         // BF16x3 dense products: reduction elements per accumulator
                                     // chain (0 = one chain per tile)

@@ -1,0 +1,749 @@
+// tridiag.cu -- eigen-decomposition of the reduced density matrix for the truncation
+// (Sec. 2, steps 3-4) by Householder tridiagonalisation, bisection and inverse iteration,
+// all in FP64.
+//
+// FP64 runs at a small fraction of the FP32 and tensor rates on this part, so the solver
+// spends as few FP64 operations as the problem allows: rho = Q T Q^T costs about 4n^3/3
+// multiply-adds once (a cyclic Jacobi sweep costs 4n^3 and ~20 sweeps are needed), and
+// only the m' kept eigenvectors are formed.
+//   1. Tridiagonalisation (one cooperative launch, one grid barrier per column): for
+//      column k, the reflector H_k = I - tau v v^T (v_0 = 1) with H_k x = beta e_1 for
+//      x = A[k+1:, k]; then A22 <- H_k A22 H_k as A22 - v w^T - w v^T with
+//      p = tau A22 v and w = p - (tau/2)(p^T v) v.  v is kept in row k of A.
+//   2. All eigenvalues of T by multisection on Sturm counts (four threads per
+//      eigenvalue), to an interval of max(2 eps max(|lo|, |hi|), eps ||T||) + pivmin.
+//   3. The m' largest: inverse iteration with T - lambda I factored once (Gaussian
+//      elimination with partial pivoting on the tridiagonal), four solves from a hashed
+//      signed start vector, one thread per eigenvector.
+//   4. Modified Gram-Schmidt over the m' vectors in decreasing eigenvalue order, twice
+//      (one cooperative launch): eigenvectors of close or equal eigenvalues come out of
+//      step 3 independent but not orthogonal.
+//   5. Back-transformation x = H_0 H_1 ... H_{n-3} z, and the sign convention of U
+//      (largest-magnitude component positive, the first such index on ties).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+
+#include "api_common.h"
+#include "grid_sync.cuh"
+#include "ptx.cuh"
+
+namespace {
+
+using dmrg::GridBarrier;
+using dmrg::block_sum_all;
+using dmrg::grid_barrier;
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kInvitIters = 4;
+constexpr int kBackVecs = 2;   // eigenvectors per block in the back-transformation
+
+// ---------------------------------------------------------------- 1. tridiagonalisation
+struct TriArgs {
+    double* A;          // n x n symmetric, both triangles; row k receives v_k
+    double* P;          // 2 x n: p of the current column, by column parity
+    int* ready;         // n flags, zeroed: row k is final for column k
+    double* d;          // n: diagonal of T
+    double* e;          // n: e[k] = T[k+1][k]
+    double* tau;        // n
+    GridBarrier* bar;
+    unsigned* status;
+    uint64_t timeout_ns;
+    int n;
+};
+
+__device__ __forceinline__ int ld_acquire_int(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Thread 0 waits (bounded) until *flag is set; the block learns the outcome.
+__device__ bool wait_flag(const int* flag, GridBarrier* b, uint64_t timeout_ns, unsigned* status) {
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        ok = 1;
+        if (ld_acquire_int(flag) == 0) {
+            const uint64_t t0 = dmrg::globaltimer_ns();
+            uint32_t spins = 0;
+            while (ld_acquire_int(flag) == 0) {
+                if ((++spins & 31u) == 0) {
+                    if (*reinterpret_cast<volatile int*>(&b->abort)) {
+                        ok = 0;
+                        break;
+                    }
+                    if (dmrg::globaltimer_ns() - t0 > timeout_ns) {
+                        atomicOr(status, DMRG_DEV_ERR_TIMEOUT);
+                        atomicExch(&b->abort, 1);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Warp-wide sum over j < L of x[j] * y[j] (x read through L2), eight loads in flight per
+// lane: a row is a chain of L2 round trips, the critical path of every column.
+constexpr int kUnroll = 8;
+
+__device__ __forceinline__ double warp_dot_l2(const double* __restrict__ x, const double* __restrict__ y,
+                                              int L, int lane) {
+    double a[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) a[u] = 0.0;
+    int j = lane;
+    for (; j + 32 * (kUnroll - 1) < L; j += 32 * kUnroll) {
+        double xv[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) xv[u] = __ldcg(x + j + 32 * u);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) a[u] = fma(xv[u], y[j + 32 * u], a[u]);
+    }
+    for (; j < L; j += 32) a[0] = fma(__ldcg(x + j), y[j], a[0]);
+    double acc = 0.0;
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) acc += a[u];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+// Row r belongs to warp r mod (warps of the grid) for the whole launch, so a warp's
+// matrix-vector rows are the rows it updated itself one column earlier.  Per column:
+// wait for the pivot row's flag, form v, p = tau A22 v on own rows, one grid barrier
+// (all of p), then the rank-2 update of own rows; the owner of the next pivot row
+// updates it first and raises its flag.
+// First row >= lo of the rows r = b + g * (w + kWarps * t) owned by warp w of block b.
+__device__ __forceinline__ int first_own_row(int lo, int b, int w, int g) {
+    const int base = b + g * w, step = g * kWarps;
+    if (base >= lo) return base;
+    return base + ((lo - base + step - 1) / step) * step;
+}
+
+__global__ void __launch_bounds__(kThreads) tridiag_kernel(TriArgs T) {
+    extern __shared__ double vs[];   // v (n entries), then w of the current column (n)
+    double* ws = vs + T.n;
+    const int n = T.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nstep = gridDim.x * kWarps;   // rows are dealt to blocks first, then warps
+    unsigned gen = 0;
+    for (int k = 0; k + 2 < n; ++k) {
+        const int L = n - k - 1;
+        double* P = T.P + (k & 1) * n;
+        if (k > 0) {
+            if (!wait_flag(T.ready + k, T.bar, T.timeout_ns, T.status)) return;
+        } else {
+            __syncthreads();
+        }
+        const double* row = T.A + size_t(k) * n + (k + 1);   // x = A[k][k+1:] = A[k+1:][k]
+        double ss = 0.0;
+        for (int j = 1 + tid; j < L; j += kThreads) {
+            const double x = __ldcg(row + j);
+            ss = fma(x, x, ss);
+        }
+        ss = block_sum_all(ss);
+        const double alpha = __ldcg(row);
+        double tau = 0.0, beta = alpha, scale = 0.0;
+        if (ss > 0.0) {
+            beta = -copysign(sqrt(fma(alpha, alpha, ss)), alpha);
+            tau = (beta - alpha) / beta;
+            scale = 1.0 / (alpha - beta);
+        }
+        for (int j = tid; j < L; j += kThreads) vs[j] = j == 0 ? 1.0 : __ldcg(row + j) * scale;
+        if (blockIdx.x == 0 && tid == 0) {
+            T.d[k] = __ldcg(T.A + size_t(k) * n + k);
+            T.e[k] = beta;
+            T.tau[k] = tau;
+        }
+        __syncthreads();
+        // p = tau A22 v on own rows (row r = k + 1 + i)
+        const int r0 = first_own_row(k + 1, blockIdx.x, warp, gridDim.x);
+        for (int r = r0; r < n; r += nstep) {
+            const double acc = warp_dot_l2(T.A + size_t(r) * n + (k + 1), vs, L, lane);
+            if (lane == 0) __stcg(P + (r - (k + 1)), tau * acc);
+        }
+        if (!grid_barrier(T.bar, gen, T.timeout_ns, T.status)) return;
+        // row k is no longer read: it keeps v for the back-transformation
+        if (blockIdx.x == 0)
+            for (int j = tid; j < L; j += kThreads) __stcg(T.A + size_t(k) * n + (k + 1) + j, vs[j]);
+        double pv = 0.0;
+        for (int j = tid; j < L; j += kThreads) {
+            const double pj = __ldcg(P + j);
+            ws[j] = pj;
+            pv = fma(pj, vs[j], pv);
+        }
+        const double half = 0.5 * tau * block_sum_all(pv);
+        for (int j = tid; j < L; j += kThreads) ws[j] = fma(-half, vs[j], ws[j]);   // w = p - half v
+        __syncthreads();
+        // A22 -= v w^T + w v^T (two FMAs an entry), own rows in increasing order
+        for (int r = r0; r < n; r += nstep) {
+            const int i = r - (k + 1);
+            double* ri = T.A + size_t(r) * n + (k + 1);
+            const double vi = vs[i], wi = ws[i];
+            int j = lane;
+            for (; j + 32 * (kUnroll - 1) < L; j += 32 * kUnroll) {   // kUnroll entries in flight
+                double a[kUnroll];
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) a[u] = __ldcg(ri + j + 32 * u);
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u)
+                    __stcg(ri + j + 32 * u, fma(-vi, ws[j + 32 * u], fma(-wi, vs[j + 32 * u], a[u])));
+            }
+            for (; j < L; j += 32) __stcg(ri + j, fma(-vi, ws[j], fma(-wi, vs[j], __ldcg(ri + j))));
+            if (r == k + 1) {   // the next pivot row is final
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence();
+                    atomicExch(T.ready + (k + 1), 1);
+                }
+            }
+        }
+    }
+    if (!grid_barrier(T.bar, gen, T.timeout_ns, T.status)) return;
+    if (blockIdx.x == 0 && tid == 0) {
+        if (n >= 2) {
+            T.d[n - 2] = __ldcg(T.A + size_t(n - 2) * n + (n - 2));
+            T.e[n - 2] = __ldcg(T.A + size_t(n - 2) * n + (n - 1));
+            T.tau[n - 2] = 0.0;
+        }
+        T.d[n - 1] = __ldcg(T.A + size_t(n - 1) * n + (n - 1));
+        T.tau[n - 1] = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------- 2. eigenvalues
+// stats: [0] Gershgorin lower bound, [1] upper bound, [2] max(|lo|, |hi|) = ||T|| bound,
+// [3] pivmin (smallest pivot magnitude of a Sturm count)
+__global__ void tri_stats_kernel(const double* __restrict__ d, const double* __restrict__ e, int n,
+                                 double* __restrict__ stats) {
+    __shared__ double lo_s[kThreads], hi_s[kThreads], e2_s[kThreads];
+    double lo = DBL_MAX, hi = -DBL_MAX, e2 = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double r = 0.0;
+        if (i > 0) r += fabs(e[i - 1]);
+        if (i + 1 < n) r += fabs(e[i]);
+        lo = fmin(lo, d[i] - r);
+        hi = fmax(hi, d[i] + r);
+        if (i + 1 < n) e2 = fmax(e2, e[i] * e[i]);
+    }
+    lo_s[threadIdx.x] = lo;
+    hi_s[threadIdx.x] = hi;
+    e2_s[threadIdx.x] = e2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int t = 1; t < blockDim.x; ++t) {
+            lo = fmin(lo, lo_s[t]);
+            hi = fmax(hi, hi_s[t]);
+            e2 = fmax(e2, e2_s[t]);
+        }
+        const double tn = fmax(fabs(lo), fabs(hi));
+        const double pivmin = DBL_MIN * fmax(1.0, e2);
+        const double pad = 2.0 * DBL_EPSILON * tn * n + 2.0 * pivmin;
+        stats[0] = lo - pad;
+        stats[1] = hi + pad;
+        stats[2] = tn;
+        stats[3] = pivmin;
+    }
+}
+
+// 1/q: the hardware's approximate reciprocal refined by two Newton steps
+// r <- r + r (1 - q r), each of which doubles the correct bits (|q| >= pivmin keeps q
+// normal, so the flush-to-zero form is exact here).
+__device__ __forceinline__ double recip(double q) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(q));
+    r = fma(r, fma(-q, r, 1.0), r);
+    r = fma(r, fma(-q, r, 1.0), r);
+    return r;
+}
+
+// Number of eigenvalues of T below x (Sturm sequence of the LDL^T pivots).
+__device__ __forceinline__ int sturm_count(const double* d, const double* e2, int n, double x,
+                                           double pivmin) {
+    double q = d[0] - x;
+    int c = q < 0.0 ? 1 : 0;
+    for (int i = 1; i < n; ++i) {
+        if (fabs(q) < pivmin) q = -pivmin;
+        q = fma(-e2[i - 1], recip(q), d[i] - x);
+        c += q < 0.0 ? 1 : 0;
+    }
+    return c;
+}
+
+// Multisection: kSect neighbouring threads share eigenvalue j (the j-th smallest) and
+// count at kSect interior points of its interval at once, so each round shrinks it
+// kSect + 1 times.  Stops at width 2 eps max(|lo|, |hi|), or eps ||T|| (the absolute
+// accuracy a backward-stable dense solver gives), plus pivmin.  The eigenvalue is
+// stored as lambda[n - 1 - j] (decreasing order).  d and e^2 are staged in shared
+// memory when they fit.
+constexpr int kSect = 4;
+constexpr int kBisectThreads = 64;
+
+__global__ void __launch_bounds__(kBisectThreads) bisect_kernel(const double* __restrict__ d,
+                                                                const double* __restrict__ e, int n,
+                                                                const double* __restrict__ stats,
+                                                                double* __restrict__ e2g, int staged,
+                                                                double* __restrict__ lambda) {
+    extern __shared__ double sm[];
+    const double* dd = d;
+    const double* ee = e2g;
+    if (staged) {
+        double* ds = sm;
+        double* es = sm + n;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            ds[i] = d[i];
+            if (i + 1 < n) es[i] = e[i] * e[i];
+        }
+        __syncthreads();
+        dd = ds;
+        ee = es;
+    }
+    const int t = threadIdx.x % kSect;
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) / kSect;
+    const bool live = j < n;
+    double lo = stats[0], hi = stats[1];
+    const double atol = DBL_EPSILON * stats[2], pivmin = stats[3];
+    bool done = !live;
+    for (int round = 0; round < 128; ++round) {
+        // every group runs the same number of rounds of the warp's loop; finished or
+        // absent groups keep their interval
+        const double w = hi - lo;
+        if (!done && (w <= fmax(2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)), atol) + pivmin)) done = true;
+        if (__all_sync(0xffffffffu, done)) break;
+        const double x = lo + w * double(t + 1) / double(kSect + 1);
+        const int c = done ? 0 : sturm_count(dd, ee, n, x, pivmin);
+        // the new interval: from the first point whose count exceeds j back to the point
+        // before it (so a count that is not monotone in rounding cannot cross the bounds)
+        double nlo = lo, nhi = hi;
+        bool hit = false;
+#pragma unroll
+        for (int u = 0; u < kSect; ++u) {
+            const int src = ((threadIdx.x & 31) & ~(kSect - 1)) + u;
+            const int cu = __shfl_sync(0xffffffffu, c, src);
+            const double xu = __shfl_sync(0xffffffffu, x, src);
+            if (!hit) {
+                if (cu <= j) {
+                    nlo = xu;
+                } else {
+                    nhi = xu;
+                    hit = true;
+                }
+            }
+        }
+        if (!done) {
+            const bool stuck = !(nlo > lo || nhi < hi);
+            lo = nlo;
+            hi = nhi;
+            if (stuck) done = true;
+        }
+    }
+    if (live && t == 0) lambda[n - 1 - j] = 0.5 * (lo + hi);
+}
+
+__global__ void square_kernel(const double* __restrict__ e, int n, double* __restrict__ e2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i + 1 < n) e2[i] = e[i] * e[i];
+}
+
+// ---------------------------------------------------------------- 3. inverse iteration
+// Signed start entry in [-1, 1) from a multiply-xorshift hash of (i, j).
+__device__ __forceinline__ double start_entry(int i, int j) {
+    uint32_t h = uint32_t(i) * 2654435761u + uint32_t(j) * 40503u + 12345u;
+    h = (h ^ (h >> 15)) * 2246822519u;
+    h ^= h >> 13;
+    return double(h) * (1.0 / 2147483648.0) - 1.0;
+}
+
+// Thread j: the eigenvector of lambda[j] (j < mp, decreasing order).  Scratch arrays are
+// interleaved, entry i of vector j at i * mp + j, so a warp's accesses are contiguous.
+__global__ void __launch_bounds__(32) invit_kernel(const double* __restrict__ d,
+                                                    const double* __restrict__ e, int n, int mp,
+                                                    const double* __restrict__ lambda,
+                                                    const double* __restrict__ stats,
+                                                    double* __restrict__ u1, double* __restrict__ u2,
+                                                    double* __restrict__ u3, double* __restrict__ lm,
+                                                    unsigned char* __restrict__ sw,
+                                                    double* __restrict__ z, double* __restrict__ Zt) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= mp) return;
+    const double lam = lambda[j];
+    const double small = DBL_EPSILON * fmax(stats[2], DBL_MIN);
+    auto at = [&](int i) { return size_t(i) * mp + j; };
+    // factor T - lam I with partial pivoting: U has diagonals u1, u2 (super), u3 (second super)
+    for (int i = 0; i < n; ++i) {
+        u1[at(i)] = d[i] - lam;
+        if (i + 1 < n) u2[at(i)] = e[i];
+    }
+    for (int i = 0; i + 1 < n; ++i) {
+        const double c = e[i];
+        double a = u1[at(i)];
+        if (fabs(a) >= fabs(c)) {
+            if (a == 0.0) {
+                a = small;
+                u1[at(i)] = a;
+            }
+            const double l = c / a;
+            lm[at(i)] = l;
+            sw[at(i)] = 0;
+            u1[at(i + 1)] -= l * u2[at(i)];
+            if (i + 2 < n) u3[at(i)] = 0.0;
+        } else {
+            const double l = a / c;
+            lm[at(i)] = l;
+            sw[at(i)] = 1;
+            const double a_next = u1[at(i + 1)], s_old = u2[at(i)];
+            u1[at(i)] = c;
+            u2[at(i)] = a_next;
+            u1[at(i + 1)] = s_old - l * a_next;
+            if (i + 2 < n) {
+                const double s_next = u2[at(i + 1)];
+                u3[at(i)] = s_next;
+                u2[at(i + 1)] = -l * s_next;
+            }
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        const double a = u1[at(i)];
+        if (fabs(a) < small) u1[at(i)] = a >= 0.0 ? small : -small;
+    }
+    for (int i = 0; i < n; ++i) z[at(i)] = start_entry(i, j);
+    for (int it = 0; it < kInvitIters; ++it) {
+        double zmax = 0.0;
+        for (int i = 0; i < n; ++i) zmax = fmax(zmax, fabs(z[at(i)]));
+        const double inv = zmax > 0.0 ? 1.0 / zmax : 1.0;
+        // forward: the row interchanges and multipliers of the factorisation
+        double prev = z[at(0)] * inv;
+        for (int i = 0; i + 1 < n; ++i) {
+            double cur = z[at(i + 1)] * inv;
+            if (sw[at(i)]) {
+                const double t = prev;
+                prev = cur;
+                cur = t;
+            }
+            z[at(i)] = prev;
+            prev = cur - lm[at(i)] * prev;
+        }
+        z[at(n - 1)] = prev;
+        // backward substitution
+        double x2 = 0.0, x1 = z[at(n - 1)] / u1[at(n - 1)];
+        z[at(n - 1)] = x1;
+        for (int i = n - 2; i >= 0; --i) {
+            const double t3 = (i + 2 < n) ? u3[at(i)] * x2 : 0.0;
+            const double x = (z[at(i)] - u2[at(i)] * x1 - t3) / u1[at(i)];
+            z[at(i)] = x;
+            x2 = x1;
+            x1 = x;
+        }
+    }
+    for (int i = 0; i < n; ++i) Zt[size_t(j) * n + i] = z[at(i)];
+}
+
+// ---------------------------------------------------------------- 4. Gram-Schmidt
+// Warp-wide sum over i < n of x[i] * y[i], both read through L2, four of each in flight.
+__device__ __forceinline__ double warp_dot_l2_both(const double* __restrict__ x,
+                                                   const double* __restrict__ y, int n, int lane) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int i = lane;
+    for (; i + 96 < n; i += 128) {
+        const double x0 = __ldcg(x + i), x1 = __ldcg(x + i + 32), x2 = __ldcg(x + i + 64),
+                     x3 = __ldcg(x + i + 96);
+        const double y0 = __ldcg(y + i), y1 = __ldcg(y + i + 32), y2 = __ldcg(y + i + 64),
+                     y3 = __ldcg(y + i + 96);
+        a0 = fma(x0, y0, a0);
+        a1 = fma(x1, y1, a1);
+        a2 = fma(x2, y2, a2);
+        a3 = fma(x3, y3, a3);
+    }
+    for (; i < n; i += 32) a0 = fma(__ldcg(x + i), __ldcg(y + i), a0);
+    double acc = (a0 + a1) + (a2 + a3);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+struct MgsArgs {
+    double* Zt;   // mp x n, row j = eigenvector j
+    GridBarrier* bar;
+    unsigned* status;
+    uint64_t timeout_ns;
+    int n, mp;
+};
+
+// Two passes of modified Gram-Schmidt in row order; each step projects row j out of the
+// later rows (one row per warp), then every row is normalised.
+__global__ void __launch_bounds__(kThreads) mgs_kernel(MgsArgs M) {
+    const int n = M.n, mp = M.mp, tid = threadIdx.x, lane = tid & 31;
+    const int gwarp = blockIdx.x * kWarps + (tid >> 5), nwarps = gridDim.x * kWarps;
+    unsigned gen = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int j = 0; j + 1 < mp; ++j) {
+            const double* zj = M.Zt + size_t(j) * n;
+            double ss = 0.0;
+            for (int i = tid; i < n; i += kThreads) {
+                const double x = __ldcg(zj + i);
+                ss = fma(x, x, ss);
+            }
+            const double nn = block_sum_all(ss);
+            const double inv2 = nn > 0.0 ? 1.0 / nn : 0.0;
+            for (int r = first_own_row(j + 1, blockIdx.x, tid >> 5, gridDim.x); r < mp; r += nwarps) {
+                double* zr = M.Zt + size_t(r) * n;
+                const double c = warp_dot_l2_both(zj, zr, n, lane) * inv2;
+                int i = lane;
+                for (; i + 96 < n; i += 128) {
+                    double a[4], b[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        a[u] = __ldcg(zr + i + 32 * u);
+                        b[u] = __ldcg(zj + i + 32 * u);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) __stcg(zr + i + 32 * u, fma(-c, b[u], a[u]));
+                }
+                for (; i < n; i += 32) __stcg(zr + i, fma(-c, __ldcg(zj + i), __ldcg(zr + i)));
+            }
+            if (!grid_barrier(M.bar, gen, M.timeout_ns, M.status)) return;
+        }
+        for (int r = gwarp; r < mp; r += nwarps) {
+            double* zr = M.Zt + size_t(r) * n;
+            double ss = 0.0;
+            for (int i = lane; i < n; i += 32) {
+                const double x = __ldcg(zr + i);
+                ss = fma(x, x, ss);
+            }
+            for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            const double inv = ss > 0.0 ? 1.0 / sqrt(ss) : 0.0;
+            for (int i = lane; i < n; i += 32) __stcg(zr + i, __ldcg(zr + i) * inv);
+        }
+        if (!grid_barrier(M.bar, gen, M.timeout_ns, M.status)) return;
+    }
+}
+
+// ---------------------------------------------------------------- 5. back-transformation
+// Block b: eigenvectors kBackVecs * b .. + kBackVecs - 1, staged in shared memory; the
+// reflectors are applied from the last to the first; then each column gets its sign and
+// is written into U (n x mp, row-major).
+__global__ void __launch_bounds__(kThreads) back_kernel(const double* __restrict__ A,
+                                                        const double* __restrict__ tau,
+                                                        const double* __restrict__ Zt, int n,
+                                                        int mp, double* __restrict__ U) {
+    extern __shared__ double zs[];   // kBackVecs x n
+    const int tid = threadIdx.x;
+    const int j0 = blockIdx.x * kBackVecs;
+    const int nv = min(kBackVecs, mp - j0);
+    for (int q = 0; q < nv; ++q)
+        for (int i = tid; i < n; i += kThreads) zs[q * n + i] = Zt[size_t(j0 + q) * n + i];
+    __syncthreads();
+    __shared__ double part[kBackVecs][kWarps];
+    for (int k = n - 3; k >= 0; --k) {
+        const double t = tau[k];
+        if (t == 0.0) continue;   // uniform over the block
+        const double* v = A + size_t(k) * n + (k + 1);
+        const int L = n - k - 1;
+        double acc[kBackVecs];
+#pragma unroll
+        for (int q = 0; q < kBackVecs; ++q) acc[q] = 0.0;
+        for (int i = tid; i < L; i += kThreads) {
+            const double vi = v[i];
+#pragma unroll
+            for (int q = 0; q < kBackVecs; ++q)
+                if (q < nv) acc[q] = fma(vi, zs[q * n + k + 1 + i], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < kBackVecs; ++q) {
+            double a = acc[q];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if ((tid & 31) == 0) part[q][tid >> 5] = a;
+        }
+        __syncthreads();
+        double coef[kBackVecs];
+#pragma unroll
+        for (int q = 0; q < kBackVecs; ++q) {
+            double s = 0.0;
+            for (int w = 0; w < kWarps; ++w) s += part[q][w];
+            coef[q] = t * s;
+        }
+        for (int i = tid; i < L; i += kThreads) {
+            const double vi = v[i];
+#pragma unroll
+            for (int q = 0; q < kBackVecs; ++q)
+                if (q < nv) zs[q * n + k + 1 + i] -= coef[q] * vi;
+        }
+        __syncthreads();
+    }
+    // sign: the largest-magnitude component positive (first index on ties)
+    __shared__ double bv[kWarps];
+    __shared__ int bi[kWarps];
+    __shared__ double sgn;
+    for (int q = 0; q < nv; ++q) {
+        double best = -1.0;
+        int idx = 0;
+        for (int i = tid; i < n; i += kThreads) {
+            const double a = fabs(zs[q * n + i]);
+            if (a > best) {
+                best = a;
+                idx = i;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+            if (ob > best || (ob == best && oi < idx)) {
+                best = ob;
+                idx = oi;
+            }
+        }
+        if ((tid & 31) == 0) {
+            bv[tid >> 5] = best;
+            bi[tid >> 5] = idx;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            best = bv[0];
+            idx = bi[0];
+            for (int w = 1; w < kWarps; ++w)
+                if (bv[w] > best || (bv[w] == best && bi[w] < idx)) {
+                    best = bv[w];
+                    idx = bi[w];
+                }
+            sgn = zs[q * n + idx] < 0.0 ? -1.0 : 1.0;
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += kThreads) U[size_t(i) * mp + j0 + q] = sgn * zs[q * n + i];
+        __syncthreads();
+    }
+}
+
+// Blocks of a cooperative launch of `kernel` with `smem` dynamic bytes, at most `cap`.
+// (one block per SM at most when per_sm_cap = 1: FP64 work is bound per SM)
+cudaError_t coop_grid(const void* kernel, size_t smem, int cap, int* grid, int per_sm_cap = 2) {
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (!coop || per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    *grid = std::max(1, std::min(cap, sms * std::min(per_sm, per_sm_cap)));
+    return cudaSuccess;
+}
+
+}  // namespace
+
+namespace dmrg {
+
+WsLayout tridiag_layout(int64_t n, int64_t mp) {
+    WsLayout W;
+    W.add("A", size_t(n) * n * 8);
+    W.add("P", size_t(n) * 2 * 8);
+    W.add("ready", size_t(n) * 4);
+    W.add("d", size_t(n) * 8);
+    W.add("e", size_t(n) * 8);
+    W.add("e2", size_t(n) * 8);
+    W.add("tau", size_t(n) * 8);
+    W.add("stats", 4 * 8);
+    W.add("bar", sizeof(GridBarrier));
+    W.add("Zt", size_t(mp) * n * 8);
+    for (int a = 0; a < 5; ++a) W.add("lu", size_t(mp) * n * 8);   // u1, u2, u3, l, z
+    W.add("sw", size_t(mp) * n);
+    return W;
+}
+
+// rho (n x n, in the layout's A section) -> U (n x mp), lambda (n, decreasing), eps.
+dmrg_status tridiag_eigen(dmrg_handle h, int64_t n64, int64_t mp64, char* ws, double* U,
+                          double* lambda, double* eps, cudaStream_t s) {
+    const int n = int(n64), mp = int(mp64);
+    const WsLayout W = tridiag_layout(n, mp);
+    double* A = reinterpret_cast<double*>(ws + W.offsets[0]);
+    double* P = reinterpret_cast<double*>(ws + W.offsets[1]);
+    int* ready = reinterpret_cast<int*>(ws + W.offsets[2]);
+    double* d = reinterpret_cast<double*>(ws + W.offsets[3]);
+    double* e = reinterpret_cast<double*>(ws + W.offsets[4]);
+    double* e2 = reinterpret_cast<double*>(ws + W.offsets[5]);
+    double* tau = reinterpret_cast<double*>(ws + W.offsets[6]);
+    double* stats = reinterpret_cast<double*>(ws + W.offsets[7]);
+    GridBarrier* bar = reinterpret_cast<GridBarrier*>(ws + W.offsets[8]);
+    double* Zt = reinterpret_cast<double*>(ws + W.offsets[9]);
+    double* lu[5];
+    for (int a = 0; a < 5; ++a) lu[a] = reinterpret_cast<double*>(ws + W.offsets[10 + a]);
+    unsigned char* sw = reinterpret_cast<unsigned char*>(ws + W.offsets[15]);
+    cudaError_t err;
+    // 1. tridiagonalisation
+    {
+        const size_t smem = size_t(n) * 16;
+        if (smem > 200 * 1024) return fail(h, DMRG_ERR_SHAPE, "rows too large for the tridiagonal solver");
+        err = cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        int grid = 1;
+        if (err == cudaSuccess)
+            err = coop_grid(reinterpret_cast<const void*>(tridiag_kernel), smem, std::max(1, (n + kWarps - 1) / kWarps),
+                            &grid, 1);
+        if (err == cudaSuccess) err = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
+        if (err == cudaSuccess) err = cudaMemsetAsync(ready, 0, size_t(n) * 4, s);
+        if (err != cudaSuccess) return cuda_fail(h, err, "tridiagonalisation set-up");
+        TriArgs T{A, P, ready, d, e, tau, bar, h->d_status, timeout_ns(h), n};
+        err = timed_launch(h, "trunc_tridiag", s, [&] {
+            void* args[] = {&T};
+            return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(tridiag_kernel), dim3(unsigned(grid)),
+                                               dim3(kThreads), args, smem, s);
+        });
+        if (err != cudaSuccess) return cuda_fail(h, err, "tridiagonalisation");
+    }
+    // 2. eigenvalues
+    {
+        const bool staged = size_t(n) * 16 <= 96 * 1024;
+        const size_t smem = staged ? size_t(n) * 16 : 0;
+        err = timed_launch(h, "trunc_bisect", s, [&] {
+            tri_stats_kernel<<<1, kThreads, 0, s>>>(d, e, n, stats);
+            if (!staged) square_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(e, n, e2);
+            cudaError_t r = cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 int(std::max<size_t>(smem, 1)));
+            if (r != cudaSuccess) return r;
+            const int64_t threads = int64_t(n) * kSect;
+            bisect_kernel<<<unsigned((threads + kBisectThreads - 1) / kBisectThreads), kBisectThreads, smem, s>>>(
+                d, e, n, stats, e2, staged ? 1 : 0, lambda);
+            return cudaGetLastError();
+        });
+        if (err != cudaSuccess) return cuda_fail(h, err, "bisection");
+    }
+    // 3. inverse iteration
+    err = timed_launch(h, "trunc_invit", s, [&] {
+        // one warp per block: each SM's FP64 pipes serve as few sequential chains as possible
+        invit_kernel<<<unsigned((mp + 31) / 32), 32, 0, s>>>(d, e, n, mp, lambda, stats, lu[0], lu[1], lu[2],
+                                                             lu[3], sw, lu[4], Zt);
+        return cudaGetLastError();
+    });
+    if (err != cudaSuccess) return cuda_fail(h, err, "inverse iteration");
+    // 4. Gram-Schmidt
+    {
+        int grid = 1;
+        err = coop_grid(reinterpret_cast<const void*>(mgs_kernel), 0, std::max(1, mp), &grid, 1);
+        if (err == cudaSuccess) err = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
+        if (err != cudaSuccess) return cuda_fail(h, err, "orthogonalisation set-up");
+        MgsArgs M{Zt, bar, h->d_status, timeout_ns(h), n, mp};
+        err = timed_launch(h, "trunc_orthogonalise", s, [&] {
+            void* args[] = {&M};
+            return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(mgs_kernel), dim3(unsigned(grid)),
+                                               dim3(kThreads), args, 0, s);
+        });
+        if (err != cudaSuccess) return cuda_fail(h, err, "orthogonalisation");
+    }
+    // 5. back-transformation and the sign convention
+    {
+        const size_t smem = size_t(kBackVecs) * n * 8;
+        if (smem > 200 * 1024) return fail(h, DMRG_ERR_SHAPE, "rows too large for the tridiagonal solver");
+        err = cudaFuncSetAttribute(back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (err == cudaSuccess)
+            err = timed_launch(h, "trunc_back", s, [&] {
+                back_kernel<<<unsigned((mp + kBackVecs - 1) / kBackVecs), kThreads, smem, s>>>(A, tau, Zt, n, mp, U);
+                return cudaGetLastError();
+            });
+        if (err != cudaSuccess) return cuda_fail(h, err, "back-transformation");
+    }
+    (void)eps;
+    return DMRG_OK;
+}
+
+}  // namespace dmrg

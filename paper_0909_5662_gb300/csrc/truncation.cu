@@ -3,7 +3,8 @@
 // eigenvectors with the largest eigenvalues as the columns of U = R^+, and the
 // discarded weight eps_rho (Eq. error).
 //
-// The eigen-decomposition is the cyclic Jacobi method in FP64.  A sweep visits every
+// By default the eigen-decomposition is the tridiagonal solver of tridiag.cu; with
+// DMRG_OPT_TRUNCATION_JACOBI it is the cyclic Jacobi method in FP64 below.  A sweep visits every
 // pair of indices once, in N - 1 rounds of N / 2 disjoint pairs (the round-robin
 // "circle" schedule, N = n rounded up to even; the padding index pairs with nobody).
 // In a round every pair's rotation J (the stable 2 x 2 symmetric Schur step: the angle
@@ -32,6 +33,7 @@
 #include <cmath>
 
 #include "api_common.h"
+#include "grid_sync.cuh"
 #include "ptx.cuh"
 
 using namespace dmrg;
@@ -42,6 +44,7 @@ constexpr int kThreads = 256;
 constexpr int kPT = 16;          // pairs per tile side (kPT * kPT = kThreads)
 constexpr int kVRows = 64;       // rows of V per work item
 constexpr int kMaxBlocksPerSm = 3;
+constexpr int64_t kTridiagMaxRows = 6144;   // the tridiagonal solver's shared-memory staging
 
 // Slot i of round r on N (even) indices: index N - 1 stays, the others turn, and every
 // pair of indices meets exactly once in rounds 0 .. N - 2.  For i >= 1 the first index
@@ -102,56 +105,10 @@ __device__ __forceinline__ Rot ld_rot(const Rot* p) {
 
 // Barrier state of one sweep, zeroed before the launch; the sweep's results follow it.
 struct SweepSync {
-    unsigned count, gen;
-    int abort, pad;
+    GridBarrier bar;
     double off2, all2;              // sum of squares off the diagonal, and in total
     unsigned long long rotations;   // pairs rotated in the sweep
 };
-
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Grid-wide barrier of a cooperative launch.  The wait is bounded: on expiry it records
-// the timeout in *status, raises the sweep's abort flag, and every block returns false
-// (blocks still on their way see the flag at the barrier and return too).
-__device__ bool grid_barrier(SweepSync* sy, unsigned& gen_seen, uint64_t timeout_ns, unsigned* status) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        const unsigned g = gen_seen;
-        __threadfence();
-        if (atomicAdd(&sy->count, 1u) == gridDim.x - 1) {
-            atomicExch(&sy->count, 0u);
-            __threadfence();
-            atomicAdd(&sy->gen, 1u);
-        } else {
-            const uint64_t t0 = globaltimer_ns();
-            uint32_t spins = 0;
-            while (ld_acquire_gpu(&sy->gen) == g) {
-                if ((++spins & 31u) == 0) {
-                    if (*reinterpret_cast<volatile int*>(&sy->abort)) {
-                        ok = 0;
-                        break;
-                    }
-                    if (globaltimer_ns() - t0 > timeout_ns) {
-                        atomicOr(status, DMRG_DEV_ERR_TIMEOUT);
-                        atomicExch(&sy->abort, 1);
-                        ok = 0;
-                        break;
-                    }
-                }
-            }
-        }
-        __threadfence();
-        gen_seen = g + 1;
-    }
-    __syncthreads();
-    return ok != 0;
-}
 
 struct SweepArgs {
     double* A[2];       // the sweep reads A[cur] first; round r writes A[(cur + r + 1) & 1]
@@ -194,7 +151,7 @@ __global__ void __launch_bounds__(kThreads) jacobi_sweep_kernel(SweepArgs P) {
             if (R.s != 0.0) nrot += 1.0;
             P.rots[slot] = R;
         }
-        if (!grid_barrier(P.sync, gen_seen, P.timeout_ns, P.status)) return;
+        if (!grid_barrier(&P.sync->bar, gen_seen, P.timeout_ns, P.status)) return;
         // phase 2: A <- J^T A J and V <- V J
         for (int item = blockIdx.x; item < items; item += gridDim.x) {
             if (item < P.n_atiles) {
@@ -296,7 +253,7 @@ __global__ void __launch_bounds__(kThreads) jacobi_sweep_kernel(SweepArgs P) {
                 P.partials[3 * blockIdx.x + tid] = acc;
             }
         }
-        if (!grid_barrier(P.sync, gen_seen, P.timeout_ns, P.status)) return;
+        if (!grid_barrier(&P.sync->bar, gen_seen, P.timeout_ns, P.status)) return;
     }
     if (blockIdx.x == 0 && tid == 0) {
         double o = 0.0, a = 0.0, q = 0.0;
@@ -438,7 +395,8 @@ extern "C" {
 dmrg_status dmrg_truncation_workspace(dmrg_handle h, int64_t rows, int64_t cols, size_t* bytes) {
     if (!h || !bytes) return DMRG_ERR_INVALID_ARG;
     if (rows < 1 || cols < 1) return fail(h, DMRG_ERR_SHAPE, "need rows, cols >= 1");
-    *bytes = trunc_dims(rows).ws.total;
+    // either solver (the option may change after the query); mp <= rows
+    *bytes = std::max(trunc_dims(rows).ws.total, tridiag_layout(rows, rows).total);
     return DMRG_OK;
 }
 
@@ -455,6 +413,18 @@ dmrg_status dmrg_truncation(dmrg_handle h, const double* Psi, int64_t rows, int6
     st = check_ws(h, ws, ws_bytes, need);
     if (st != DMRG_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!h->trunc_jacobi && rows <= kTridiagMaxRows) {
+        char* base = static_cast<char*>(ws);
+        double* rho = reinterpret_cast<double*>(base + tridiag_layout(rows, mp).offsets[0]);
+        cudaError_t e = timed_launch(h, "trunc_rho", s, [&] { return rho_launch(Psi, rows, cols, 0, rho, s); });
+        if (e != cudaSuccess) return cuda_fail(h, e, "reduced density matrix");
+        st = tridiag_eigen(h, rows, mp, base, U, lambda, eps, s);
+        if (st != DMRG_OK) return st;
+        discarded_kernel<<<1, kThreads, 0, s>>>(lambda, rows, mp, eps);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(h, e, "discarded weight");
+        if (sweeps) *sweeps = 0;
+        return DMRG_OK;
+    }
     const TruncDims D = trunc_dims(rows);
     char* base = static_cast<char*>(ws);
     double* A0 = reinterpret_cast<double*>(base + D.ws.offsets[0]);
@@ -503,7 +473,7 @@ dmrg_status dmrg_truncation(dmrg_handle h, const double* Psi, int64_t rows, int6
         e = cudaMemcpyAsync(&host, sync, sizeof host, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(h, e, "convergence test");
-        if (host.abort) return fail(h, DMRG_ERR_TIMEOUT, "a Jacobi sweep's grid barrier timed out");
+        if (host.bar.abort) return fail(h, DMRG_ERR_TIMEOUT, "a Jacobi sweep's grid barrier timed out");
         if (host.off2 <= tol * tol * host.all2 || host.rotations == 0) {
             done = sweep + 1;
             break;

@@ -24,23 +24,34 @@ def schmidt(rng, n, nc, w):
     return (u * np.sqrt(w)) @ v.T
 
 
-def run(P, Psi, mp):
-    U, lam, eps, sweeps = P.dmrg_truncation(torch.from_numpy(Psi).cuda(), mp)
+@pytest.fixture(scope="module", params=["tridiagonal", "jacobi"])
+def method(request, P):
+    """The default solver (tridiagonalisation, bisection, inverse iteration) and the
+    cyclic Jacobi sweeps, each on its own handle."""
+    h = P.Handle()
+    P.dmrg_set_option("truncation_jacobi", 1 if request.param == "jacobi" else 0, handle=h)
+    yield request.param, h
+    h.close()
+
+
+def run(P, Psi, mp, method=None):
+    name, h = method if method else ("tridiagonal", None)
+    U, lam, eps, sweeps = P.dmrg_truncation(torch.from_numpy(Psi).cuda(), mp, handle=h)
     torch.cuda.synchronize()
-    P.dmrg_sync_status()
+    P.dmrg_sync_status(handle=h)
+    assert (sweeps >= 0) if name == "jacobi" else (sweeps == 0)   # Jacobi: 0 sweeps for one row
     return U.cpu().numpy(), lam.cpu().numpy(), float(eps.item()), sweeps
 
 
 @pytest.mark.parametrize("n,nc,rank,mp", [(40, 30, 20, 12), (37, 64, 37, 10), (64, 16, 16, 16), (2, 3, 2, 1)])
-def test_truncation_matches_oracle_schmidt(P, n, nc, rank, mp):
+def test_truncation_matches_oracle_schmidt(P, method, n, nc, rank, mp):
     # distinct Schmidt weights: every kept eigenvector is unique up to sign
     rng = np.random.default_rng(n * 100 + nc)
     w = np.exp(-0.25 * np.arange(rank)) * (1.0 + 0.05 * rng.random(rank))
     w = np.sort(w)[::-1] / w.sum()
     Psi = schmidt(rng, n, nc, w)
     U_ref, lam_ref, eps_ref = oracle.truncation(Psi, mp)
-    U, lam, eps, sweeps = run(P, Psi, mp)
-    assert sweeps > 0
+    U, lam, eps, sweeps = run(P, Psi, mp, method)
     assert np.abs(lam - lam_ref).max() < 1e-13
     assert abs(eps - eps_ref) < 1e-13
     assert np.abs(U - U_ref).max() < 1e-10
@@ -48,13 +59,12 @@ def test_truncation_matches_oracle_schmidt(P, n, nc, rank, mp):
 
 
 @pytest.mark.parametrize("n,nc,mp", [(64, 50, 20), (129, 200, 40), (400, 400, 100)])
-def test_truncation_random_state(P, n, nc, mp):
+def test_truncation_random_state(P, method, n, nc, mp):
     rng = np.random.default_rng(n + nc)
     Psi = rng.standard_normal((n, nc))
     Psi /= np.linalg.norm(Psi)
     U_ref, lam_ref, eps_ref = oracle.truncation(Psi, mp)
-    U, lam, eps, sweeps = run(P, Psi, mp)
-    assert sweeps > 0
+    U, lam, eps, sweeps = run(P, Psi, mp, method)
     assert np.abs(lam - lam_ref).max() < 1e-13 * max(1.0, lam_ref[0])
     assert abs(eps - eps_ref) < 1e-12
     # the kept subspace (projector), unique when lambda[mp-1] > lambda[mp]
@@ -76,3 +86,34 @@ def test_truncation_feeds_the_rotation(P):
     got = P.dmrg_rotate_ops(torch.from_numpy(U).cuda(), torch.from_numpy(O).cuda(), d, "fp64").cpu().numpy()
     ref = oracle.rotate_dense(U_ref, O, d)
     assert np.abs(got - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("pairs,mp", [(30, 30), (30, 31)])
+def test_truncation_degenerate_pairs(P, method, pairs, mp):
+    # Exactly repeated Schmidt weights: each kept pair spans an eigenspace whose basis is
+    # not unique; the kept subspace (when the cut does not split a pair), the spectrum,
+    # orthonormality and the residual rho U - U Lambda are what is fixed.
+    rng = np.random.default_rng(pairs + mp)
+    w = np.repeat(np.exp(-0.3 * np.arange(pairs)), 2)
+    w /= w.sum()
+    Psi = schmidt(rng, 80, 70, w)
+    U_ref, lam_ref, eps_ref = oracle.truncation(Psi, mp)
+    U, lam, eps, _ = run(P, Psi, mp, method)
+    rho = Psi @ Psi.T
+    assert np.abs(lam - lam_ref).max() < 1e-13
+    assert abs(eps - eps_ref) < 1e-13
+    assert np.abs(U.T @ U - np.eye(mp)).max() < 1e-12
+    assert np.abs(rho @ U - U * lam[:mp]).max() < 1e-13
+    if mp % 2 == 0:
+        assert np.abs(U @ U.T - U_ref @ U_ref.T).max() < 1e-10
+
+
+def test_truncation_tiny_sizes(P, method):
+    # one and two rows (no reflector), mp = rows
+    for rows in (1, 2, 3):
+        Psi = np.arange(1.0, 1.0 + rows * 4).reshape(rows, 4)
+        Psi /= np.linalg.norm(Psi)
+        U_ref, lam_ref, eps_ref = oracle.truncation(Psi, rows)
+        U, lam, eps, _ = run(P, Psi, rows, method)
+        assert np.abs(lam - lam_ref).max() < 1e-14
+        assert np.abs(U - U_ref).max() < 1e-12
