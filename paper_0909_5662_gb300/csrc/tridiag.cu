@@ -361,83 +361,114 @@ __device__ __forceinline__ double start_entry(int i, int j) {
 
 // Thread j: the eigenvector of lambda[j] (j < mp, decreasing order).  Scratch arrays are
 // interleaved, entry i of vector j at i * mp + j, so a warp's accesses are contiguous.
+// The factorisation keeps its running row in registers (d and e are read by every thread
+// of the warp at once); the solves read their operands kChunk at a time, so that the
+// loads of a chunk are in flight together and only the arithmetic is sequential.
+constexpr int kChunk = 8;
+
 __global__ void __launch_bounds__(32) invit_kernel(const double* __restrict__ d,
-                                                    const double* __restrict__ e, int n, int mp,
-                                                    const double* __restrict__ lambda,
-                                                    const double* __restrict__ stats,
-                                                    double* __restrict__ u1, double* __restrict__ u2,
-                                                    double* __restrict__ u3, double* __restrict__ lm,
-                                                    unsigned char* __restrict__ sw,
-                                                    double* __restrict__ z, double* __restrict__ Zt) {
+                                                   const double* __restrict__ e, int n, int mp,
+                                                   const double* __restrict__ lambda,
+                                                   const double* __restrict__ stats,
+                                                   double* __restrict__ u1, double* __restrict__ u2,
+                                                   double* __restrict__ u3, double* __restrict__ lm,
+                                                   unsigned char* __restrict__ sw,
+                                                   double* __restrict__ z, double* __restrict__ Zt) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= mp) return;
     const double lam = lambda[j];
     const double small = DBL_EPSILON * fmax(stats[2], DBL_MIN);
     auto at = [&](int i) { return size_t(i) * mp + j; };
-    // factor T - lam I with partial pivoting: U has diagonals u1, u2 (super), u3 (second super)
-    for (int i = 0; i < n; ++i) {
-        u1[at(i)] = d[i] - lam;
-        if (i + 1 < n) u2[at(i)] = e[i];
-    }
+    auto guard = [&](double a) { return fabs(a) < small ? (a >= 0.0 ? small : -small) : a; };
+    // T - lam I = P L U with partial pivoting; U has diagonals u1, u2 (super), u3
+    double a = d[0] - lam, s_cur = n > 1 ? e[0] : 0.0;
     for (int i = 0; i + 1 < n; ++i) {
-        const double c = e[i];
-        double a = u1[at(i)];
+        const double c = e[i], a_next = d[i + 1] - lam, s_next = (i + 2 < n) ? e[i + 1] : 0.0;
         if (fabs(a) >= fabs(c)) {
-            if (a == 0.0) {
-                a = small;
-                u1[at(i)] = a;
-            }
+            if (a == 0.0) a = small;
             const double l = c / a;
+            u1[at(i)] = guard(a);
+            u2[at(i)] = s_cur;
+            u3[at(i)] = 0.0;
             lm[at(i)] = l;
             sw[at(i)] = 0;
-            u1[at(i + 1)] -= l * u2[at(i)];
-            if (i + 2 < n) u3[at(i)] = 0.0;
+            a = a_next - l * s_cur;
+            s_cur = s_next;
         } else {
             const double l = a / c;
+            u1[at(i)] = guard(c);
+            u2[at(i)] = a_next;
+            u3[at(i)] = s_next;
             lm[at(i)] = l;
             sw[at(i)] = 1;
-            const double a_next = u1[at(i + 1)], s_old = u2[at(i)];
-            u1[at(i)] = c;
-            u2[at(i)] = a_next;
-            u1[at(i + 1)] = s_old - l * a_next;
-            if (i + 2 < n) {
-                const double s_next = u2[at(i + 1)];
-                u3[at(i)] = s_next;
-                u2[at(i + 1)] = -l * s_next;
-            }
+            a = s_cur - l * a_next;
+            s_cur = -l * s_next;
         }
     }
-    for (int i = 0; i < n; ++i) {
-        const double a = u1[at(i)];
-        if (fabs(a) < small) u1[at(i)] = a >= 0.0 ? small : -small;
-    }
+    u1[at(n - 1)] = guard(a);
     for (int i = 0; i < n; ++i) z[at(i)] = start_entry(i, j);
     for (int it = 0; it < kInvitIters; ++it) {
         double zmax = 0.0;
-        for (int i = 0; i < n; ++i) zmax = fmax(zmax, fabs(z[at(i)]));
+        for (int i0 = 0; i0 < n; i0 += kChunk) {
+            double v[kChunk];
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q) v[q] = (i0 + q < n) ? z[at(i0 + q)] : 0.0;
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q) zmax = fmax(zmax, fabs(v[q]));
+        }
         const double inv = zmax > 0.0 ? 1.0 / zmax : 1.0;
         // forward: the row interchanges and multipliers of the factorisation
         double prev = z[at(0)] * inv;
-        for (int i = 0; i + 1 < n; ++i) {
-            double cur = z[at(i + 1)] * inv;
-            if (sw[at(i)]) {
-                const double t = prev;
-                prev = cur;
-                cur = t;
+        for (int i0 = 0; i0 + 1 < n; i0 += kChunk) {
+            double zc[kChunk], lc[kChunk];
+            unsigned char sc[kChunk];
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q) {
+                const int i = i0 + q;
+                const bool ok = i + 1 < n;
+                zc[q] = ok ? z[at(i + 1)] : 0.0;
+                lc[q] = ok ? lm[at(i)] : 0.0;
+                sc[q] = ok ? sw[at(i)] : 0;
             }
-            z[at(i)] = prev;
-            prev = cur - lm[at(i)] * prev;
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q) {
+                const int i = i0 + q;
+                if (i + 1 < n) {
+                    double cur = zc[q] * inv;
+                    if (sc[q]) {
+                        const double t = prev;
+                        prev = cur;
+                        cur = t;
+                    }
+                    z[at(i)] = prev;
+                    prev = cur - lc[q] * prev;
+                }
+            }
         }
         z[at(n - 1)] = prev;
         // backward substitution
-        double x2 = 0.0, x1 = z[at(n - 1)] / u1[at(n - 1)];
-        z[at(n - 1)] = x1;
-        for (int i = n - 2; i >= 0; --i) {
-            const double t3 = (i + 2 < n) ? u3[at(i)] * x2 : 0.0;
-            const double x = (z[at(i)] - u2[at(i)] * x1 - t3) / u1[at(i)];
-            z[at(i)] = x;
-            x2 = x1;
-            x1 = x;
+        double x1 = 0.0, x2 = 0.0;
+        for (int i0 = n - 1; i0 >= 0; i0 -= kChunk) {
+            double yc[kChunk], a1[kChunk], a2[kChunk], a3[kChunk];
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q) {
+                const int i = i0 - q;
+                const bool ok = i >= 0;
+                yc[q] = ok ? z[at(i)] : 0.0;
+                a1[q] = ok ? u1[at(i)] : 1.0;
+                a2[q] = (ok && i + 1 < n) ? u2[at(i)] : 0.0;
+                a3[q] = (ok && i + 2 < n) ? u3[at(i)] : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q) {
+                const int i = i0 - q;
+                if (i >= 0) {
+                    const double x = (yc[q] - a2[q] * x1 - a3[q] * x2) / a1[q];
+                    z[at(i)] = x;
+                    x2 = x1;
+                    x1 = x;
+                }
+            }
         }
     }
     for (int i = 0; i < n; ++i) Zt[size_t(j) * n + i] = z[at(i)];
@@ -524,55 +555,69 @@ __global__ void __launch_bounds__(kThreads) mgs_kernel(MgsArgs M) {
 
 // ---------------------------------------------------------------- 5. back-transformation
 // Block b: eigenvectors kBackVecs * b .. + kBackVecs - 1, staged in shared memory; the
-// reflectors are applied from the last to the first; then each column gets its sign and
-// is written into U (n x mp, row-major).
+// reflectors are applied from the last to the first, each staged in shared memory while
+// the previous one is applied; then each column gets its sign and is written into U
+// (n x mp, row-major).
 __global__ void __launch_bounds__(kThreads) back_kernel(const double* __restrict__ A,
                                                         const double* __restrict__ tau,
                                                         const double* __restrict__ Zt, int n,
                                                         int mp, double* __restrict__ U) {
-    extern __shared__ double zs[];   // kBackVecs x n
+    extern __shared__ double zs[];   // kBackVecs x n, then two reflector buffers of n
+    double* const vb0 = zs + size_t(kBackVecs) * n;
+    double* const vb1 = zs + size_t(kBackVecs + 1) * n;
     const int tid = threadIdx.x;
     const int j0 = blockIdx.x * kBackVecs;
     const int nv = min(kBackVecs, mp - j0);
     for (int q = 0; q < nv; ++q)
         for (int i = tid; i < n; i += kThreads) zs[q * n + i] = Zt[size_t(j0 + q) * n + i];
+    if (n >= 3)   // the last reflector, v_{n-3} (two entries)
+        for (int i = tid; i < 2; i += kThreads) vb0[i] = A[size_t(n - 3) * n + (n - 2) + i];
     __syncthreads();
     __shared__ double part[kBackVecs][kWarps];
+    int cur = 0;
     for (int k = n - 3; k >= 0; --k) {
-        const double t = tau[k];
-        if (t == 0.0) continue;   // uniform over the block
-        const double* v = A + size_t(k) * n + (k + 1);
         const int L = n - k - 1;
-        double acc[kBackVecs];
-#pragma unroll
-        for (int q = 0; q < kBackVecs; ++q) acc[q] = 0.0;
-        for (int i = tid; i < L; i += kThreads) {
-            const double vi = v[i];
-#pragma unroll
-            for (int q = 0; q < kBackVecs; ++q)
-                if (q < nv) acc[q] = fma(vi, zs[q * n + k + 1 + i], acc[q]);
+        const double* v = cur ? vb1 : vb0;
+        // stage the next reflector (k - 1, length L + 1) while this one is applied
+        if (k >= 1) {
+            double* nxt = cur ? vb0 : vb1;
+            const double* src = A + size_t(k - 1) * n + k;
+            for (int i = tid; i < L + 1; i += kThreads) nxt[i] = src[i];
         }
+        const double t = tau[k];
+        if (t != 0.0) {   // uniform over the block
+            double acc[kBackVecs];
 #pragma unroll
-        for (int q = 0; q < kBackVecs; ++q) {
-            double a = acc[q];
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            if ((tid & 31) == 0) part[q][tid >> 5] = a;
+            for (int q = 0; q < kBackVecs; ++q) acc[q] = 0.0;
+            for (int i = tid; i < L; i += kThreads) {
+                const double vi = v[i];
+#pragma unroll
+                for (int q = 0; q < kBackVecs; ++q)
+                    if (q < nv) acc[q] = fma(vi, zs[q * n + k + 1 + i], acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < kBackVecs; ++q) {
+                double a = acc[q];
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                if ((tid & 31) == 0) part[q][tid >> 5] = a;
+            }
+            __syncthreads();
+            double coef[kBackVecs];
+#pragma unroll
+            for (int q = 0; q < kBackVecs; ++q) {
+                double sum = 0.0;
+                for (int w = 0; w < kWarps; ++w) sum += part[q][w];
+                coef[q] = t * sum;
+            }
+            for (int i = tid; i < L; i += kThreads) {
+                const double vi = v[i];
+#pragma unroll
+                for (int q = 0; q < kBackVecs; ++q)
+                    if (q < nv) zs[q * n + k + 1 + i] -= coef[q] * vi;
+            }
         }
         __syncthreads();
-        double coef[kBackVecs];
-#pragma unroll
-        for (int q = 0; q < kBackVecs; ++q) {
-            double s = 0.0;
-            for (int w = 0; w < kWarps; ++w) s += part[q][w];
-            coef[q] = t * s;
-        }
-        for (int i = tid; i < L; i += kThreads) {
-            const double vi = v[i];
-#pragma unroll
-            for (int q = 0; q < kBackVecs; ++q)
-                if (q < nv) zs[q * n + k + 1 + i] -= coef[q] * vi;
-        }
-        __syncthreads();
+        cur ^= 1;
     }
     // sign: the largest-magnitude component positive (first index on ties)
     __shared__ double bv[kWarps];
@@ -732,7 +777,7 @@ dmrg_status tridiag_eigen(dmrg_handle h, int64_t n64, int64_t mp64, char* ws, do
     }
     // 5. back-transformation and the sign convention
     {
-        const size_t smem = size_t(kBackVecs) * n * 8;
+        const size_t smem = size_t(kBackVecs + 2) * n * 8;
         if (smem > 200 * 1024) return fail(h, DMRG_ERR_SHAPE, "rows too large for the tridiagonal solver");
         err = cudaFuncSetAttribute(back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (err == cudaSuccess)
