@@ -58,6 +58,8 @@ struct Second {  // second-product problem
 struct TcTables {
     TcProblem* d_first = nullptr;
     TcProblem* d_second = nullptr;
+    int32_t* d_map_first = nullptr;    // problem of every tile (one load per tile to decode)
+    int32_t* d_map_second = nullptr;
     int tiles_first = 0, tiles_second = 0;
     int bn_first = 16, bn_second = 16;
 };
@@ -662,18 +664,36 @@ dmrg_status tc_tables(dmrg_blocked_plan_s& pl, void* ws, bool tf32, TcTables*& o
         T.bn_second = std::max(T.bn_second, P.tile_n);
     }
     T.tiles_second = tiles;
+    std::vector<int32_t> map1(size_t(T.tiles_first)), map2(size_t(T.tiles_second));
+    for (size_t i = 0; i < first.size(); ++i) {
+        const TcProblem& P = first[i];
+        std::fill(map1.begin() + P.tile_start, map1.begin() + P.tile_start + P.m_tiles * P.n_tiles * P.k_splits,
+                  int32_t(i));
+    }
+    for (size_t i = 0; i < second.size(); ++i) {
+        const TcProblem& P = second[i];
+        std::fill(map2.begin() + P.tile_start, map2.begin() + P.tile_start + P.m_tiles * P.n_tiles * P.k_splits,
+                  int32_t(i));
+    }
     const size_t b1 = a128(first.size() * sizeof(TcProblem)), b2 = a128(second.size() * sizeof(TcProblem));
+    const size_t m1 = a128(map1.size() * 4), m2 = a128(map2.size() * 4);
     char* dev = nullptr;
-    if (cudaMalloc(reinterpret_cast<void**>(&dev), std::max<size_t>(b1 + b2, 256)) != cudaSuccess)
+    if (cudaMalloc(reinterpret_cast<void**>(&dev), std::max<size_t>(b1 + b2 + m1 + m2, 256)) != cudaSuccess)
         return DMRG_ERR_CUDA;
     pl.device_allocs.push_back(dev);
     if ((!first.empty() && cudaMemcpy(dev, first.data(), first.size() * sizeof(TcProblem),
                                       cudaMemcpyHostToDevice) != cudaSuccess) ||
         (!second.empty() && cudaMemcpy(dev + b1, second.data(), second.size() * sizeof(TcProblem),
-                                       cudaMemcpyHostToDevice) != cudaSuccess))
+                                       cudaMemcpyHostToDevice) != cudaSuccess) ||
+        (!map1.empty() && cudaMemcpy(dev + b1 + b2, map1.data(), map1.size() * 4, cudaMemcpyHostToDevice) !=
+                              cudaSuccess) ||
+        (!map2.empty() && cudaMemcpy(dev + b1 + b2 + m1, map2.data(), map2.size() * 4,
+                                     cudaMemcpyHostToDevice) != cudaSuccess))
         return DMRG_ERR_CUDA;
     T.d_first = reinterpret_cast<TcProblem*>(dev);
     T.d_second = reinterpret_cast<TcProblem*>(dev + b1);
+    T.d_map_first = reinterpret_cast<int32_t*>(dev + b1 + b2);
+    T.d_map_second = reinterpret_cast<int32_t*>(dev + b1 + b2 + m1);
     out = &pl.tc_cache.emplace(key, T).first->second;
     return DMRG_OK;
 }
@@ -920,6 +940,7 @@ dmrg_status dmrg_rotate_ops_blocked(dmrg_handle h, dmrg_blocked_plan pl, const d
         }
         TcLaunch L1{};
         L1.table = T->d_first;
+        L1.tile_problem = T->d_map_first;
         L1.nprob = int(pl->first.size());
         L1.total_tiles = T->tiles_first;
         L1.out[0][0] = hi;
@@ -935,6 +956,7 @@ dmrg_status dmrg_rotate_ops_blocked(dmrg_handle h, dmrg_blocked_plan pl, const d
         if (e != cudaSuccess) return cuda_fail(h, e, "first product");
         TcLaunch L2{};
         L2.table = T->d_second;
+        L2.tile_problem = T->d_map_second;
         L2.nprob = int(pl->second.size());
         L2.total_tiles = T->tiles_second;
         L2.out[0][0] = Oout;

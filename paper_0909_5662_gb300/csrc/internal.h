@@ -121,6 +121,7 @@ constexpr int64_t kChainMinRed = 512;
 struct TcLaunch {
     TcProblem inline_prob[kMaxInlineProblems];  // used when table == nullptr
     const TcProblem* table;       // grouped problems in device memory
+    const int32_t* tile_problem;  // with a table: problem index of every tile (nullptr: search)
     int32_t nprob;
     int32_t total_tiles;
     void* out[1][2];              // [scatter][hi, lo]: FP32/TF32 output in [0][0]

@@ -20,10 +20,15 @@ struct Decoded {
 __device__ __forceinline__ Decoded decode_tile(const TcLaunch& L, int t, int elems_per_row) {
     const TcProblem* P = &L.inline_prob[0];
     if (L.table != nullptr) {
-        int lo = 0, hi = L.nprob - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (L.table[mid].tile_start <= t) lo = mid; else hi = mid - 1;
+        int lo = 0;
+        if (L.tile_problem != nullptr) {
+            lo = __ldg(L.tile_problem + t);
+        } else {
+            int hi = L.nprob - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (L.table[mid].tile_start <= t) lo = mid; else hi = mid - 1;
+            }
         }
         P = &L.table[lo];
     } else {
