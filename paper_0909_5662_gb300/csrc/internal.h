@@ -110,7 +110,7 @@ struct TcConfig {
     }
 };
 
-constexpr int kMaxInlineProblems = 4;
+constexpr int kMaxInlineProblems = 6;   // keeps TcLaunch (the kernel parameters) under 4 KB
 // Running-sum scratch of the CTA-pair kernel's chained accumulation: kChainScratchCtas
 // CTAs x 128 rows x 256 FP32 columns.
 constexpr int kChainScratchCtas = 160;

@@ -8,7 +8,7 @@
 //     O'_k = U^T (A_k (x) I_d) U_c,     U_c = (P^{f_c} (x) S_c) U,
 //
 // i.e. the plain block rotation of A_k with U_c in the first product.  On the
-// tensor-core paths the classes go in groups of up to four: one kernel forms the
+// tensor-core paths the classes go in groups of up to six: one kernel forms the
 // group's U_c, and one dense rotation packs them and runs the first product as one
 // problem per class (each with its own U_c) and the second product over the group.
 #include <cuda_runtime.h>
