@@ -186,7 +186,7 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
                              cudaStream_t s, bool pack_u, const double* U1,
                              const FirstClasses* cls) {
     const DenseDims D = dense_dims(K, m, d, mp, p);
-    if (cls && (cls->n < 1 || cls->n > kMaxInlineProblems || !cls->U1 || !pack_u))
+    if (cls && (cls->n < 1 || cls->n > kMaxInlineProblems || (!cls->U1 && !cls->b1_ready) || !pack_u))
         return fail(h, DMRG_ERR_INVALID_ARG, "bad operator classes");
     const bool split = (p == DMRG_PREC_BF16X3);
     const TcMode mode = split ? TC_BF16X3 : TC_TF32;
@@ -280,16 +280,18 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     jo.rdiv = 1; jo.s_r_hi = m; jo.s_r_lo = 0; jo.s_c = 1;
     jo.dst0 = Op[0]; jo.dst1 = Op[1]; jo.ld = D.ld1;
     if (pack_u) {
-        PackJob& j1 = jobs[nj++];
-        j1.src = U1 ? U1 : U; j1.src_f64 = 1; j1.mode = pmode;
-        j1.rows = int64_t(d) * mp; j1.cols = m; j1.rows_per_op = j1.rows;
-        j1.rdiv = d; j1.s_r_hi = 1; j1.s_r_lo = mp; j1.s_c = int64_t(d) * mp;
-        j1.dst0 = B1[0]; j1.dst1 = B1[1]; j1.ld = D.ld1;
-        if (cls) {   // the classes' U1_c, stacked
-            j1.src = cls->U1;
-            j1.rows = int64_t(cls->n) * d * mp;
-            j1.s_op = m * d * mp;
-            j1.dst0 = cls->b1[0]; j1.dst1 = cls->b1[1];
+        if (!(cls && cls->b1_ready)) {
+            PackJob& j1 = jobs[nj++];
+            j1.src = U1 ? U1 : U; j1.src_f64 = 1; j1.mode = pmode;
+            j1.rows = int64_t(d) * mp; j1.cols = m; j1.rows_per_op = j1.rows;
+            j1.rdiv = d; j1.s_r_hi = 1; j1.s_r_lo = mp; j1.s_c = int64_t(d) * mp;
+            j1.dst0 = B1[0]; j1.dst1 = B1[1]; j1.ld = D.ld1;
+            if (cls) {   // the classes' U1_c, stacked
+                j1.src = cls->U1;
+                j1.rows = int64_t(cls->n) * d * mp;
+                j1.s_op = m * d * mp;
+                j1.dst0 = cls->b1[0]; j1.dst1 = cls->b1[1];
+            }
         }
         PackJob& j2 = jobs[nj++];
         j2.src = U; j2.src_f64 = 1; j2.mode = pmode;

@@ -49,6 +49,7 @@ struct FirstClasses {
     int64_t kc[kMaxInlineProblems] = {};
     const double* U1 = nullptr;
     void* b1[2] = {nullptr, nullptr};
+    bool b1_ready = false;   // b1 already holds the packed U1_c (U1 is then not read)
 };
 
 // The dense rotation O'_k = U^T (O_k (x) I_d) U.  With U1 != nullptr the first

@@ -9,13 +9,15 @@
 //
 // i.e. the plain block rotation of A_k with U_c in the first product.  On the
 // tensor-core paths the classes go in groups of up to six: one kernel forms the
-// group's U_c, and one dense rotation packs them and runs the first product as one
-// problem per class (each with its own U_c) and the second product over the group.
+// group's U_c straight into the first product's packed operand, and one dense rotation
+// packs the operators and runs the first product as one problem per class (each with
+// its own U_c) and the second product over the group.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
 #include "api_common.h"
+#include "tc_common.cuh"
 
 using namespace dmrg;
 
@@ -62,9 +64,64 @@ __global__ void site_u_kernel(const double* __restrict__ U, double* __restrict__
     }
 }
 
+// Tensor-core paths: U_c formed and written straight into the first product's packed
+// operand.  Packed row b * d + s, column j of class c holds
+//   U_c[(j, s)][b] = p_j^{f_c} * sum_t S_c[s][t] U[(j, t)][b]
+// as a BF16 hi/lo pair (split) or TF32-rounded FP32 (tf32), row stride ld.  A block
+// takes 16 columns j and 32 rows b of one class (blockIdx.z): it reads U along b,
+// forms the d values per (j, b) in FP64 and writes them along j through shared memory.
+constexpr int kSpJ = 16, kSpB = 32;
+
+__global__ void __launch_bounds__(256) site_pack_kernel(const double* __restrict__ U, int64_t m, int d,
+                                                        int64_t mp, const __grid_constant__ SiteMatrices S,
+                                                        const signed char* __restrict__ parity, int split,
+                                                        void* __restrict__ dst0, void* __restrict__ dst1,
+                                                        int64_t ld) {
+    __shared__ double tile[kMaxSiteDim][kSpJ][kSpB + 1];
+    const int c = blockIdx.z;
+    const int64_t j0 = int64_t(blockIdx.x) * kSpJ, b0 = int64_t(blockIdx.y) * kSpB;
+    const int tb = threadIdx.x % kSpB, tj = threadIdx.x / kSpB;   // 8 column rows per pass
+    for (int jj = tj; jj < kSpJ; jj += 256 / kSpB) {
+        const int64_t j = j0 + jj, b = b0 + tb;
+        if (j >= m || b >= mp) continue;
+        double u[kMaxSiteDim];
+#pragma unroll
+        for (int t = 0; t < kMaxSiteDim; ++t) u[t] = t < d ? U[(j * d + t) * mp + b] : 0.0;
+        const long long flip = (S.odd[c] && parity && parity[j] < 0) ? (1ll << 63) : 0ll;
+#pragma unroll
+        for (int s = 0; s < kMaxSiteDim; ++s) {
+            if (s >= d) break;
+            double v = 0.0;
+#pragma unroll
+            for (int t = 0; t < kMaxSiteDim; ++t)
+                if (t < d && ((S.nz[c] >> (s * d + t)) & 1ull)) v = fma(S.s[c][s * d + t], u[t], v);
+            tile[s][jj][tb] = __longlong_as_double(__double_as_longlong(v) ^ flip);
+        }
+    }
+    __syncthreads();
+    // write: packed row (b, s), columns j0 .. j0 + 15
+    const size_t cls_off = size_t(c) * d * mp * ld;
+    for (int x = threadIdx.x; x < kSpB * d * kSpJ; x += 256) {
+        const int jj = x % kSpJ, rs = x / kSpJ;
+        const int tbb = rs / d, s = rs % d;
+        const int64_t j = j0 + jj, b = b0 + tbb;
+        if (j >= m || b >= mp) continue;
+        const size_t at = cls_off + size_t(b * d + s) * ld + j;
+        const double v = tile[s][jj][tbb];
+        if (split) {
+            __nv_bfloat16 h, l;
+            tcdev::split_bf16(v, h, l);
+            static_cast<__nv_bfloat16*>(dst0)[at] = h;
+            static_cast<__nv_bfloat16*>(dst1)[at] = l;
+        } else {
+            static_cast<float*>(dst0)[at] = tcdev::tf32_round(float(v));
+        }
+    }
+}
+
 struct SiteDims {
-    // Uc (FP64, one group of classes), Uc in FP32 (plain-FMA FP32 path), the group's
-    // packed U_c (tensor-core paths), dense rotation workspace
+    // Uc (FP64, plain-FMA paths), Uc in FP32 (plain-FMA FP32 path), the group's packed
+    // U_c (tensor-core paths), dense rotation workspace
     WsLayout ws;
 };
 
@@ -73,7 +130,7 @@ SiteDims site_dims(int64_t K, int64_t m, int d, int64_t mp, dmrg_precision p) {
     const bool tc = (p == DMRG_PREC_TF32 || p == DMRG_PREC_BF16X3);
     const DenseDims dd = dense_dims(std::max<int64_t>(K, 1), m, d, mp, p);
     const size_t es = (p == DMRG_PREC_TF32) ? 4 : 2;
-    D.ws.add("Uc", size_t(tc ? kGroup : 1) * m * d * mp * 8);
+    D.ws.add("Uc", tc ? 0 : size_t(m) * d * mp * 8);
     D.ws.add("Uc32", p == DMRG_PREC_FP32 ? size_t(m) * d * mp * 4 : 0);
     for (int i = 0; i < 2; ++i)
         D.ws.add("B1", (tc && (i == 0 || p == DMRG_PREC_BF16X3)) ? size_t(kGroup) * d * mp * dd.ld1 * es : 0);
@@ -174,8 +231,7 @@ dmrg_status dmrg_rotate_site_ops(dmrg_handle h, const double* U, int64_t m, int 
     int c = 0;
     while (c < n_class) {
         SiteMatrices Sm{};
-        FirstClasses cls;
-        cls.U1 = Uc;
+        FirstClasses cls;   // U1_c are formed straight into b1 by site_pack_kernel
         cls.b1[0] = b1[0];
         cls.b1[1] = b1[1];
         const int64_t g0 = k0;
@@ -188,8 +244,15 @@ dmrg_status dmrg_rotate_site_ops(dmrg_handle h, const double* U, int64_t m, int 
             ++cls.n;
         }
         if (cls.n == 0) break;
-        cudaError_t e = site_u_launch(h, U, Uc, m, d, mp, Sm, cls.n, parity, s);
+        const int64_t ld1 = dense_dims(1, m, d, mp, p).ld1;
+        cudaError_t e = timed_launch(h, "site_pack", s, [&] {
+            const dim3 grid(unsigned((m + kSpJ - 1) / kSpJ), unsigned((mp + kSpB - 1) / kSpB), unsigned(cls.n));
+            site_pack_kernel<<<grid, 256, 0, s>>>(U, m, d, mp, Sm, parity, p == DMRG_PREC_BF16X3 ? 1 : 0, b1[0],
+                                                  b1[1], ld1);
+            return cudaGetLastError();
+        });
         if (e != cudaSuccess) return cuda_fail(h, e, "site transform");
+        cls.b1_ready = true;
         const int64_t kg = k0 - g0;
         const void* Ag = static_cast<const char*>(A) + size_t(g0) * m * m * es_in;
         void* Og = static_cast<char*>(Oout) + size_t(g0) * mp * mp * es_out;

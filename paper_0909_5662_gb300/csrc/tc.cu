@@ -286,17 +286,6 @@ struct PackLaunch {
 constexpr int kPackThreads = 256;
 constexpr int kPackElems = 4;  // elements per thread
 
-// BF16 pair of x: hi = bf16(x), lo = bf16(x - hi).  For an FP32 source the residual
-// x - hi is exact in FP32; for an FP64 source it is formed in FP64 (one subtraction)
-// and then rounded, so FP64 arithmetic stays off the per-element path otherwise.
-__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& h, __nv_bfloat16& l) {
-    h = __float2bfloat16_rn(x);
-    l = __float2bfloat16_rn(x - __bfloat162float(h));
-}
-__device__ __forceinline__ void split_bf16(double x, __nv_bfloat16& h, __nv_bfloat16& l) {
-    h = __float2bfloat16_rn(__double2float_rn(x));
-    l = __float2bfloat16_rn(__double2float_rn(x - double(__bfloat162float(h))));
-}
 
 template <typename S>
 __device__ __forceinline__ void pack_store(const PackJob& j, int64_t dst, S x) {

@@ -1,6 +1,7 @@
 // tc_common.cuh -- device helpers shared by the tcgen05 GEMM kernels (one-CTA and
-// CTA-pair forms): tile decoding of the persistent schedule, TF32 rounding and the
-// epilogue's scatter of one 32-column accumulator chunk.
+// CTA-pair forms) and the operand packers: tile decoding of the persistent schedule,
+// BF16 hi/lo splitting, TF32 rounding and the epilogue's scatter of one 32-column
+// accumulator chunk.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -49,6 +50,18 @@ __device__ __forceinline__ Decoded decode_tile(const TcLaunch& L, int t, int ele
     d.kb_begin = ks * P->kb_per_split;
     d.kb_end = min(kb_total, d.kb_begin + P->kb_per_split);
     return d;
+}
+
+// BF16 pair of x: hi = bf16(x), lo = bf16(x - hi).  For an FP32 source the residual
+// x - hi is exact in FP32; for an FP64 source it is formed in FP64 (one subtraction)
+// and then rounded, so FP64 arithmetic stays off the per-element path otherwise.
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& h, __nv_bfloat16& l) {
+    h = __float2bfloat16_rn(x);
+    l = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+__device__ __forceinline__ void split_bf16(double x, __nv_bfloat16& h, __nv_bfloat16& l) {
+    h = __float2bfloat16_rn(__double2float_rn(x));
+    l = __float2bfloat16_rn(__double2float_rn(x - double(__bfloat162float(h))));
 }
 
 __device__ __forceinline__ float tf32_round(float x) {
