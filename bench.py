@@ -533,10 +533,13 @@ def run_measure(args):
             "bytes_per_launch": Ks * n * n * 4 + n * n * 8, "peak_source": "%s hbm_gbs" % peak_src}
     rh = res["expectation"]["kernels"].get("measure_rho")
     if rh:
-        gf = 2.0 * n * n * n / (rh["ms_per_launch"] * 1e-3) / 1e9
+        # rho is symmetric: n(n+1)/2 distinct entries, 2n flops each
+        flops = float(n) * (n + 1) * n
+        gf = flops / (rh["ms_per_launch"] * 1e-3) / 1e9
         res["expectation"]["roofline_rho"] = {
             "bound": "alu", "kernel": "measure_rho", "achieved": gf, "peak": FP64_NOMINAL_GFLOPS,
             "unit": "GFLOP/s (FP64)", "frac": gf / FP64_NOMINAL_GFLOPS, "traffic": None,
+            "flops_per_launch": flops,
             "peak_source": "nominal FP64 rate (no measured FP64 peak)"}
     if args.no_cpu_baseline:
         print(json.dumps({"workload": "measure_m400", "results": res}), flush=True)

@@ -33,6 +33,7 @@ struct SimtGemm {
     // element offset of each batch entry instead of b * sAb / b * sCb.
     int32_t a_sel, b_sel, c_sel;
     int32_t small;        // grouped launches: M, N <= 32, one warp per batch entry, 8 per block
+    int32_t lower;        // symmetric C: only tiles on and below the diagonal (the caller mirrors)
     const int64_t* a_boff;
     const int64_t* c_boff;
 };

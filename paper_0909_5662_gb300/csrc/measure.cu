@@ -180,11 +180,13 @@ __global__ void structure_factor_kernel(const double* __restrict__ G, const doub
 
 namespace dmrg {
 
-// rho = Psi Psi^T (side 0, rows x rows) or Psi^T Psi (side 1, cols x cols).
+// rho = Psi Psi^T (side 0, rows x rows) or Psi^T Psi (side 1, cols x cols).  rho is
+// symmetric: the tiles on and below the diagonal are computed and mirrored (the mirror
+// is exact, C[i][j] and C[j][i] being the same products summed in the same order).
 cudaError_t rho_launch(const double* Psi, int64_t rows, int64_t cols, int side, double* rho,
                        cudaStream_t s) {
     SimtGemm g{};
-    g.A = Psi; g.B = Psi; g.C = rho; g.batch = 1;
+    g.A = Psi; g.B = Psi; g.C = rho; g.batch = 1; g.lower = 1;
     if (side == 0) {
         g.M = rows; g.N = rows; g.K = cols;
         g.sAi = cols; g.sAk = 1;          // A(a, e) = Psi[a][e]

@@ -117,7 +117,26 @@ __global__ void __launch_bounds__(NT) simt_gemm_kernel(const SimtGemm g, double*
     const int64_t per_b = int64_t(g.tiles_m) * g.tiles_n;
     const int64_t b = t / per_b;
     const int64_t r = t % per_b;
-    simt_gemm_tile<T, EPI>(g, b, int(r / g.tiles_n), int(r % g.tiles_n), ortho_acc);
+    const int tm = int(r / g.tiles_n), tn = int(r % g.tiles_n);
+    if (g.lower && tn > tm) return;
+    simt_gemm_tile<T, EPI>(g, b, tm, tn, ortho_acc);
+}
+
+// C[i][j] = C[j][i] for the entries of the tiles a `lower` launch skipped (the tile of j
+// after the tile of i), through a 32 x 32 shared-memory transpose.
+__global__ void mirror_lower_kernel(double* __restrict__ C, int64_t n, int64_t ldc) {
+    __shared__ double t[32][33];
+    const int64_t i0 = int64_t(blockIdx.y) * 32, j0 = int64_t(blockIdx.x) * 32;
+    if ((j0 + 31) / BN <= i0 / BM) return;   // every entry of this block was computed
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t j = j0 + r, i = i0 + threadIdx.x;   // read C[j][i] along i
+        if (j < n && i < n) t[r][threadIdx.x] = C[j * ldc + i];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t i = i0 + r, j = j0 + threadIdx.x;   // write C[i][j] along j
+        if (i < n && j < n && j / BN > i / BM) C[i * ldc + j] = t[threadIdx.x][r];
+    }
 }
 
 struct SimtBases {
@@ -218,10 +237,16 @@ cudaError_t simt_gemm_launch(Real t, const SimtGemm& g0, cudaStream_t s) {
     g.tiles_n = int((g.N + BN - 1) / BN);
     const int64_t blocks = int64_t(g.tiles_m) * g.tiles_n * (g.reduce_batch ? 1 : g.batch);
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    if (g.lower && (t != Real::F64 || g.M != g.N || g.batch != 1 || g.sCj != 1 || g.accumulate))
+        return cudaErrorInvalidValue;
     if (t == Real::F64)
         simt_gemm_kernel<double, SE_STORE><<<unsigned(blocks), NT, 0, s>>>(g, nullptr);
     else
         simt_gemm_kernel<float, SE_STORE><<<unsigned(blocks), NT, 0, s>>>(g, nullptr);
+    if (g.lower) {
+        const unsigned nb = unsigned((g.M + 31) / 32);
+        mirror_lower_kernel<<<dim3(nb, nb), dim3(32, 8), 0, s>>>(static_cast<double*>(g.C), g.M, g.sCi);
+    }
     return cudaGetLastError();
 }
 
