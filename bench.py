@@ -487,6 +487,70 @@ def run_site(args):
     return 0
 
 
+def run_fused(args):
+    """The fused rotation (both products of Sec. 3.2 in one kernel, the intermediate
+    (O_k (x) I_d) U kept in tensor memory and shared memory) against the two-product
+    path: BF16x3, d = 4, m = 400, K = 150, m' = 64, 128, 256 (the fused kernel holds
+    at most 256 output columns).  Time per call, kernel times, the fused kernel's
+    issued tensor-core rate, and the error of both against the FP64 oracle on sampled
+    operators."""
+    import numpy as np
+    import torch
+    import paper_0909_5662_gb300 as P
+    import oracle
+    from workloads import dense_workload, SEED_BASE
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    steps = max(1, min(args.steps, 200))
+    peaks, peak_src = measured_peaks()
+    m, d, K = 400, 4, 150
+    sample = [0, 74, 149]
+    res = {}
+    t_cpu = 0.0
+    for mp in (64, 128, 256):
+        w = dense_workload("fused", SEED_BASE + 20 + mp, d, m, mp, K)
+        U = torch.from_numpy(w.U).to(dev)
+        O32 = torch.from_numpy(w.O).to(dev, torch.float32)
+        t0 = time.perf_counter()
+        ref = oracle.rotate_dense(w.U, w.O.astype(np.float32).astype(np.float64)[sample], d)
+        t_cpu += time.perf_counter() - t0
+        entry = {}
+        for name, fused in (("two_products", 0), ("fused", 1)):
+            P.dmrg_set_option("fused_rotation", fused)
+            out = P.dmrg_rotate_ops(U, O32, d, "bf16x3")
+            ms = _timed(lambda: P.dmrg_rotate_ops(U, O32, d, "bf16x3", out=out), steps, 3, flush)
+            kt = _with_kernel_timing(lambda: P.dmrg_rotate_ops(U, O32, d, "bf16x3", out=out),
+                                     min(steps, 20), flush)
+            P.dmrg_sync_status()
+            got = out[sample].double().cpu().numpy()
+            err = np.linalg.norm((got - ref).reshape(len(sample), -1), axis=1) / \
+                np.linalg.norm(ref.reshape(len(sample), -1), axis=1)
+            entry[name] = {"ms_per_call": ms, "ops_per_s": K / (ms * 1e-3), "kernels": kt,
+                           "max_rel_fro_err_vs_oracle": float(err.max())}
+        P.dmrg_set_option("fused_rotation", 0)
+        fk = entry["fused"]["kernels"].get("tc_fused_rotation")
+        if fk:
+            issued = 3.0 * 2.0 * K * d * m * mp * (m + mp)
+            ach = issued / (fk["ms_per_launch"] * 1e-3) / 1e12
+            entry["fused"]["roofline"] = {
+                "bound": "tensor", "kernel": "tc_fused_rotation", "achieved": ach,
+                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops"],
+                "traffic": None, "flops_per_launch": issued,
+                "peak_source": "%s bf16_tflops (burst)" % peak_src}
+        res["mp%d" % mp] = entry
+    line = {"workload": "fused_m400_k150 (d=4, m=400, K=150, m'=64/128/256, BF16x3, FP32 operators)",
+            "metric": "dense rotation: ms per call, fused kernel vs the two products",
+            "steps": steps, "l2": "flushed between timed calls", "results": res,
+            "cpu_baseline": {"value": 3 * len(sample) / t_cpu, "unit": "rotated operators/s",
+                             "kind": "oracle", "cores": oracle.num_threads(),
+                             "sample": "%d operators at each m', FP64" % len(sample)},
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_measure(args):
     """The measurement stage on the superblock state of the m = 400, d = 4 step
     (Psi 1600 x 1600): <Z_k> for 150 system operators (rho = Psi Psi^T, then
@@ -657,10 +721,12 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="dense",
-                    choices=["dense", "chained", "blocked", "backward", "site", "measure", "truncation"],
+                    choices=["dense", "chained", "blocked", "backward", "site", "measure", "truncation",
+                             "fused"],
                     help="dense: the benchmark line; chained: the 50-step sweep report; "
-                         "blocked / backward / site / measure / truncation: reports of the "
-                         "block-sparse, adjoint, site-operator, measurement and truncation paths")
+                         "blocked / backward / site / measure / truncation / fused: reports of "
+                         "the block-sparse, adjoint, site-operator, measurement, truncation and "
+                         "fused-rotation paths")
     ap.add_argument("--precision", default=None, choices=["bf16x3", "tf32", "fp32", "fp64"],
                     help="blocked / backward / site reports: time this precision only")
     ap.add_argument("--sweep-steps", type=int, default=50)
@@ -683,6 +749,8 @@ def main():
         return run_measure(args)
     if args.workload == "truncation":
         return run_truncation(args)
+    if args.workload == "fused":
+        return run_fused(args)
 
     import numpy as np
     import torch

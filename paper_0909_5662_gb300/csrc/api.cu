@@ -367,6 +367,44 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     return DMRG_OK;
 }
 
+// Both products in one kernel (BF16x3, mp <= kFusedMaxMp).  It uses the dense
+// workspace's sections for the packed U_r (whose size fits the packed Pu) and O.
+dmrg_status dense_fused_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
+                                const void* O, int in_is_fp64, int64_t K, void* Oout, void* ws,
+                                cudaStream_t s) {
+    const DenseDims D = dense_dims(K, m, d, mp, DMRG_PREC_BF16X3);
+    char* base = static_cast<char*>(ws);
+    void* Pu[2] = {base + D.ws.offsets[0], base + D.ws.offsets[1]};   // "B1" sections
+    void* Op[2] = {base + D.ws.offsets[4], base + D.ws.offsets[5]};   // "Op" sections
+    PackJob jobs[2] = {};
+    PackJob& jo = jobs[0];
+    jo.src = O; jo.src_f64 = in_is_fp64; jo.mode = 0;
+    jo.rows = K * m; jo.cols = m; jo.rows_per_op = K * m; jo.s_op = 0; jo.op_off = nullptr;
+    jo.rdiv = 1; jo.s_r_hi = m; jo.s_r_lo = 0; jo.s_c = 1;
+    jo.dst0 = Op[0]; jo.dst1 = Op[1]; jo.ld = D.ld1;
+    // Pu row s*mp + x, column j  <-  U[(j d + s) mp + x]
+    PackJob& ju = jobs[1];
+    ju.src = U; ju.src_f64 = 1; ju.mode = 0;
+    ju.rows = int64_t(d) * mp; ju.cols = m; ju.rows_per_op = mp; ju.s_op = mp; ju.op_off = nullptr;
+    ju.rdiv = 1; ju.s_r_hi = 1; ju.s_r_lo = 0; ju.s_c = int64_t(d) * mp;
+    ju.dst0 = Pu[0]; ju.dst1 = Pu[1]; ju.ld = D.ld1;
+    cudaError_t e = timed_launch(h, "pack_operands", s,
+                                 [&] { return pack_launch(jobs, 2, nullptr, s); });
+    if (e != cudaSuccess) return cuda_fail(h, e, "pack");
+    FusedArgs a{};
+    a.Op[0] = Op[0]; a.Op[1] = Op[1];
+    a.Pu[0] = Pu[0]; a.Pu[1] = Pu[1];
+    a.out = static_cast<float*>(Oout);
+    a.K = K; a.m = m; a.mp = mp; a.ld = D.ld1; a.d = d;
+    a.grid = h->num_sms;
+    a.accum_chain = h->accum_chain;
+    a.status = h->d_status;
+    a.timeout_ns = timeout_ns(h);
+    e = timed_launch(h, "tc_fused_rotation", s, [&] { return fused_rotate_launch(a, s); });
+    if (e != cudaSuccess) return cuda_fail(h, e, "fused rotation");
+    return DMRG_OK;
+}
+
 dmrg_status dense_simt_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
                                const void* O, int in_is_fp64, int64_t K, void* Oout,
                                dmrg_precision p, void* ws, cudaStream_t s, bool pack_u,
@@ -535,6 +573,9 @@ dmrg_status dmrg_set_option(dmrg_handle h, dmrg_option o, double v) {
         case DMRG_OPT_BLOCKED_SMALL:
             h->blocked_small = v != 0;
             return DMRG_OK;
+        case DMRG_OPT_FUSED_ROTATION:
+            h->fused_rotation = v != 0;
+            return DMRG_OK;
         case DMRG_OPT_TEST_WITHHOLD_ARRIVAL:
             h->drop_arrival_next = v != 0;
             return DMRG_OK;
@@ -628,6 +669,8 @@ dmrg_status dmrg_rotate_ops(dmrg_handle h, const double* U, int64_t m, int d, in
              Oout, ws, (void*)s, (long long)K, (long long)m, d, (long long)mp, int(p), in_is_fp64);
     return run_maybe_graph(h, key, s, [&](cudaStream_t cs) -> dmrg_status {
         if (!tc) return dense_simt_forward(h, U, m, d, mp, O, in_is_fp64, K, Oout, p, ws, cs, true);
+        if (h->fused_rotation && p == DMRG_PREC_BF16X3 && mp <= kFusedMaxMp)
+            return dense_fused_forward(h, U, m, d, mp, O, in_is_fp64, K, Oout, ws, cs);
         const TcMode mode = (p == DMRG_PREC_BF16X3) ? TC_BF16X3 : TC_TF32;
         const TcConfig c1 = tuned_config(h, shape_key("g1", K, m, d, mp, p), mode);
         const TcConfig c2 = tuned_config(h, shape_key("g2", K, m, d, mp, p), mode);

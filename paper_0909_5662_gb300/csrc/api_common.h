@@ -63,6 +63,9 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
                              cudaStream_t s, bool pack_u = true, const double* U1 = nullptr,
                              const FirstClasses* cls = nullptr);
 
+dmrg_status dense_fused_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
+                                const void* O, int in_is_fp64, int64_t K, void* Oout, void* ws,
+                                cudaStream_t s);
 dmrg_status dense_simt_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
                                const void* O, int in_is_fp64, int64_t K, void* Oout,
                                dmrg_precision p, void* ws, cudaStream_t s, bool pack_u = true,

@@ -214,6 +214,20 @@ cudaError_t pack_grouped_launch(const PackJob* jobs_dev, int njobs, int64_t tota
                                 const void* const srcs[2], void* ws_base, int src1_f64,
                                 cudaStream_t s);
 
+// ---------------------------------------------------------------- fused rotation (fused.cu)
+// Both products in one kernel, the intermediate kept in TMEM and shared memory (BF16x3).
+constexpr int kFusedMaxMp = 256;
+struct FusedArgs {
+    const void* Op[2];   // O hi/lo (BF16): K*m rows of m, row stride ld
+    const void* Pu[2];   // U hi/lo (BF16): Pu[s][x][j] = U[j d + s][x], d*mp rows of m, stride ld
+    float* out;          // K x mp x mp
+    int64_t K, m, mp, ld;
+    int d, grid, accum_chain;
+    unsigned* status;
+    uint64_t timeout_ns;
+};
+cudaError_t fused_rotate_launch(const FusedArgs& a, cudaStream_t s);
+
 // ---------------------------------------------------------------- backward helpers
 cudaError_t f32_to_f64_strided_launch(const float* src, double* dst, int64_t n, cudaStream_t s);
 
@@ -235,6 +249,7 @@ struct dmrg_handle_s {
     bool deterministic = false;     // no atomically accumulated split tiles
     bool trunc_jacobi = false;      // truncation: cyclic Jacobi instead of the tridiagonal solver
     bool blocked_small = true;      // plans with sectors <= 32 states: fused small-sector kernel
+    bool fused_rotation = false;    // dense BF16x3, mp <= 256: both products in one kernel
     int accum_chain = 1024;         // BF16x3 dense products: reduction elements per accumulator
                                     // chain (0 = one chain per tile)
 
