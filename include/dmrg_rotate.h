@@ -118,13 +118,14 @@ DMRG_API dmrg_status dmrg_sync_status(dmrg_handle handle, dmrg_stream_t stream);
  *                              sweeps; 0 (default) = Householder tridiagonalisation,
  *                              bisection and inverse iteration (rows <= 6144; larger
  *                              matrices take the Jacobi sweeps).
- *   DMRG_OPT_FUSED_ROTATION  : 1 = dmrg_rotate_ops runs DMRG_PREC_BF16X3 with
- *                              mp <= 256 as one kernel per call that keeps the
+ *   DMRG_OPT_FUSED_ROTATION  : 1, 2 or 4 = dmrg_rotate_ops runs DMRG_PREC_BF16X3
+ *                              with mp <= 256 as one kernel per call that keeps the
  *                              intermediate (O_k (x) I_d) U on chip (tensor memory and
  *                              shared memory) instead of writing it to global memory;
- *                              same precision and workspace as the two-product path.
- *                              0 (default) = the two products (faster at mp = 400,
- *                              where the intermediate does not fit on chip).
+ *                              the value is the number of CTAs (one per operator) that
+ *                              share each tile of U through cluster multicast.  Same
+ *                              precision and workspace as the two-product path.
+ *                              0 (default) = the two products (mp > 256 always).
  *   DMRG_OPT_TEST_WITHHOLD_ARRIVAL : test hook for failure detection.  1 makes
  *                              the next dense tensor-core launch withhold one
  *                              shared-memory stage release in its first CTA, so

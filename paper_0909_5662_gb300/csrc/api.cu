@@ -398,6 +398,7 @@ dmrg_status dense_fused_forward(dmrg_handle h, const double* U, int64_t m, int d
     a.K = K; a.m = m; a.mp = mp; a.ld = D.ld1; a.d = d;
     a.grid = h->num_sms;
     a.accum_chain = h->accum_chain;
+    a.cluster = h->fused_rotation > 0 ? h->fused_rotation : 1;
     a.status = h->d_status;
     a.timeout_ns = timeout_ns(h);
     e = timed_launch(h, "tc_fused_rotation", s, [&] { return fused_rotate_launch(a, s); });
@@ -574,7 +575,9 @@ dmrg_status dmrg_set_option(dmrg_handle h, dmrg_option o, double v) {
             h->blocked_small = v != 0;
             return DMRG_OK;
         case DMRG_OPT_FUSED_ROTATION:
-            h->fused_rotation = v != 0;
+            if (!(v == 0 || v == 1 || v == 2 || v == 4))
+                return fail(h, DMRG_ERR_INVALID_ARG, "fused_rotation must be 0, 1, 2 or 4");
+            h->fused_rotation = int(v);
             return DMRG_OK;
         case DMRG_OPT_TEST_WITHHOLD_ARRIVAL:
             h->drop_arrival_next = v != 0;

@@ -223,6 +223,7 @@ struct FusedArgs {
     float* out;          // K x mp x mp
     int64_t K, m, mp, ld;
     int d, grid, accum_chain;
+    int cluster;         // CTAs sharing the U tiles: 1, 2 or 4
     unsigned* status;
     uint64_t timeout_ns;
 };
@@ -249,7 +250,8 @@ struct dmrg_handle_s {
     bool deterministic = false;     // no atomically accumulated split tiles
     bool trunc_jacobi = false;      // truncation: cyclic Jacobi instead of the tridiagonal solver
     bool blocked_small = true;      // plans with sectors <= 32 states: fused small-sector kernel
-    bool fused_rotation = false;    // dense BF16x3, mp <= 256: both products in one kernel
+    int fused_rotation = 0;         // dense BF16x3, mp <= 256: both products in one kernel,
+                                    // in clusters of this many CTAs (0 = off)
     int accum_chain = 1024;         // BF16x3 dense products: reduction elements per accumulator
                                     // chain (0 = one chain per tile)
 

@@ -22,10 +22,11 @@ def lib():
     return P
 
 
-@pytest.fixture()
-def fused(lib):
+@pytest.fixture(params=[1, 2, 4], ids=["cta", "cluster2", "cluster4"])
+def fused(lib, request):
+    # the option's value is the number of CTAs sharing each U tile by cluster multicast
     h = lib.Handle()
-    lib.dmrg_set_option("fused_rotation", 1, handle=h)
+    lib.dmrg_set_option("fused_rotation", request.param, handle=h)
     yield h
     h.close()
 
@@ -139,6 +140,18 @@ def test_full_size_sampled(lib, fused):
     idx = [0, 1, 74, 148, 149]
     ref = oracle.rotate_dense(U, O32[idx], d)
     assert rel_err(got[idx], ref).max() <= TOL
+
+
+def test_option_values(lib):
+    h = lib.Handle()
+    try:
+        for v in (0, 1, 2, 4):
+            lib.dmrg_set_option("fused_rotation", v, handle=h)
+        from paper_0909_5662_gb300._capi import DmrgError
+        with pytest.raises(DmrgError):
+            lib.dmrg_set_option("fused_rotation", 3, handle=h)
+    finally:
+        h.close()
 
 
 def test_empty_batch(lib, fused):
