@@ -44,8 +44,8 @@ constexpr int kBackVecs = 2;   // eigenvectors per block in the back-transformat
 // ---------------------------------------------------------------- 1. tridiagonalisation
 struct TriArgs {
     double* A;          // n x n symmetric, both triangles; row k receives v_k
-    double* P;          // 2 x n: p of the current column, by column parity
-    int* ready;         // n flags, zeroed: row k is final for column k
+    double* P;          // 2 x n: p of a column, by column parity
+    double* R;          // 2 x n: the next-but-one pivot row, by row parity
     double* d;          // n: diagonal of T
     double* e;          // n: e[k] = T[k+1][k]
     double* tau;        // n
@@ -55,42 +55,8 @@ struct TriArgs {
     int n;
 };
 
-__device__ __forceinline__ int ld_acquire_int(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Thread 0 waits (bounded) until *flag is set; the block learns the outcome.
-__device__ bool wait_flag(const int* flag, GridBarrier* b, uint64_t timeout_ns, unsigned* status) {
-    __shared__ int ok;
-    if (threadIdx.x == 0) {
-        ok = 1;
-        if (ld_acquire_int(flag) == 0) {
-            const uint64_t t0 = dmrg::globaltimer_ns();
-            uint32_t spins = 0;
-            while (ld_acquire_int(flag) == 0) {
-                if ((++spins & 31u) == 0) {
-                    if (*reinterpret_cast<volatile int*>(&b->abort)) {
-                        ok = 0;
-                        break;
-                    }
-                    if (dmrg::globaltimer_ns() - t0 > timeout_ns) {
-                        atomicOr(status, DMRG_DEV_ERR_TIMEOUT);
-                        atomicExch(&b->abort, 1);
-                        ok = 0;
-                        break;
-                    }
-                }
-            }
-        }
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
 // Warp-wide sum over j < L of x[j] * y[j] (x read through L2), eight loads in flight per
-// lane: a row is a chain of L2 round trips, the critical path of every column.
+// lane: a row is a chain of L2 round trips.
 constexpr int kUnroll = 8;
 
 __device__ __forceinline__ double warp_dot_l2(const double* __restrict__ x, const double* __restrict__ y,
@@ -114,105 +80,157 @@ __device__ __forceinline__ double warp_dot_l2(const double* __restrict__ x, cons
     return acc;
 }
 
-// Row r belongs to warp r mod (warps of the grid) for the whole launch, so a warp's
-// matrix-vector rows are the rows it updated itself one column earlier.  Per column:
-// wait for the pivot row's flag, form v, p = tau A22 v on own rows, one grid barrier
-// (all of p), then the rank-2 update of own rows; the owner of the next pivot row
-// updates it first and raises its flag.
-// First row >= lo of the rows r = b + g * (w + kWarps * t) owned by warp w of block b.
+// Rows are dealt to blocks first, then to warps: row r = b + g * (w + kWarps * t) belongs
+// to warp w of block b for the whole launch.  First such row >= lo:
 __device__ __forceinline__ int first_own_row(int lo, int b, int w, int g) {
     const int base = b + g * w, step = g * kWarps;
     if (base >= lo) return base;
     return base + ((lo - base + step - 1) / step) * step;
 }
 
+// The reflector H = I - tau v v^T with H x = beta e_1, for x = xs[0..Lx) in shared memory
+// (v[0] = 1).  Every thread of the block returns tau and beta; v is complete on return.
+__device__ void reflector(const double* xs, int Lx, double* v, double& tau, double& beta) {
+    double ss = 0.0;
+    for (int j = 1 + int(threadIdx.x); j < Lx; j += kThreads) ss = fma(xs[j], xs[j], ss);
+    ss = block_sum_all(ss);
+    const double alpha = xs[0];
+    tau = 0.0;
+    beta = alpha;
+    double scale = 0.0;
+    if (ss > 0.0) {
+        beta = -copysign(sqrt(fma(alpha, alpha, ss)), alpha);
+        tau = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+    }
+    for (int j = threadIdx.x; j < Lx; j += kThreads) v[j] = j == 0 ? 1.0 : xs[j] * scale;
+    __syncthreads();
+}
+
+// One grid barrier per column.  After the barrier of column k (p_k = tau_k A22 v_k
+// complete) every block forms w_k = p_k - (tau_k / 2)(p_k^T v_k) v_k, and brings the
+// next pivot row k+1 up to date itself (from the copy its owner published one column
+// earlier, with the owner's arithmetic), so it has v_{k+1} without waiting for anyone.
+// Then one pass over its own rows r >= k+2 applies A22 -= v_k w_k^T + w_k v_k^T and
+// accumulates p_{k+1} = tau_{k+1} A v_{k+1} from the updated entries; the owner of row
+// k+2 also publishes that row for the next column.
 __global__ void __launch_bounds__(kThreads) tridiag_kernel(TriArgs T) {
-    extern __shared__ double vs[];   // v (n entries), then w of the current column (n)
-    double* ws = vs + T.n;
+    extern __shared__ double sm[];
     const int n = T.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nstep = gridDim.x * kWarps;   // rows are dealt to blocks first, then warps
-    unsigned gen = 0;
-    for (int k = 0; k + 2 < n; ++k) {
-        const int L = n - k - 1;
-        double* P = T.P + (k & 1) * n;
-        if (k > 0) {
-            if (!wait_flag(T.ready + k, T.bar, T.timeout_ns, T.status)) return;
-        } else {
-            __syncthreads();
-        }
-        const double* row = T.A + size_t(k) * n + (k + 1);   // x = A[k][k+1:] = A[k+1:][k]
-        double ss = 0.0;
-        for (int j = 1 + tid; j < L; j += kThreads) {
-            const double x = __ldcg(row + j);
-            ss = fma(x, x, ss);
-        }
-        ss = block_sum_all(ss);
-        const double alpha = __ldcg(row);
-        double tau = 0.0, beta = alpha, scale = 0.0;
-        if (ss > 0.0) {
-            beta = -copysign(sqrt(fma(alpha, alpha, ss)), alpha);
-            tau = (beta - alpha) / beta;
-            scale = 1.0 / (alpha - beta);
-        }
-        for (int j = tid; j < L; j += kThreads) vs[j] = j == 0 ? 1.0 : __ldcg(row + j) * scale;
+    const int nstep = gridDim.x * kWarps;
+    if (n < 3) {   // already tridiagonal
         if (blockIdx.x == 0 && tid == 0) {
-            T.d[k] = __ldcg(T.A + size_t(k) * n + k);
-            T.e[k] = beta;
-            T.tau[k] = tau;
+            T.d[0] = T.A[0];
+            T.tau[0] = 0.0;
+            if (n == 2) {
+                T.e[0] = T.A[1];
+                T.d[1] = T.A[3];
+                T.tau[1] = 0.0;
+            }
         }
-        __syncthreads();
-        // p = tau A22 v on own rows (row r = k + 1 + i)
-        const int r0 = first_own_row(k + 1, blockIdx.x, warp, gridDim.x);
-        for (int r = r0; r < n; r += nstep) {
-            const double acc = warp_dot_l2(T.A + size_t(r) * n + (k + 1), vs, L, lane);
-            if (lane == 0) __stcg(P + (r - (k + 1)), tau * acc);
-        }
+        return;
+    }
+    double* vs = sm;            // v_k
+    double* ws = sm + n;        // w_k
+    double* xs = sm + 2 * n;    // row k+1 (columns k+1 ..) after column k
+    double* vn = sm + 3 * n;    // v_{k+1}
+    unsigned gen = 0;
+    double tau_k, beta;
+    // column 0: the reflector of row 0 and p_0 on own rows
+    for (int j = tid; j < n - 1; j += kThreads) xs[j] = __ldcg(T.A + 1 + j);
+    __syncthreads();
+    reflector(xs, n - 1, vs, tau_k, beta);
+    if (blockIdx.x == 0 && tid == 0) {
+        T.d[0] = __ldcg(T.A);
+        T.e[0] = beta;
+        T.tau[0] = tau_k;
+    }
+    for (int r = first_own_row(1, blockIdx.x, warp, gridDim.x); r < n; r += nstep) {
+        const double acc = warp_dot_l2(T.A + size_t(r) * n + 1, vs, n - 1, lane);
+        if (lane == 0) __stcg(T.P + (r - 1), tau_k * acc);
+    }
+    for (int k = 0; k + 2 < n; ++k) {
+        const int L = n - k - 1;   // trailing size of column k
         if (!grid_barrier(T.bar, gen, T.timeout_ns, T.status)) return;
-        // row k is no longer read: it keeps v for the back-transformation
+        // row k is read by no one any more: it keeps v_k for the back-transformation
         if (blockIdx.x == 0)
             for (int j = tid; j < L; j += kThreads) __stcg(T.A + size_t(k) * n + (k + 1) + j, vs[j]);
+        const double* P = T.P + (k & 1) * n;
         double pv = 0.0;
         for (int j = tid; j < L; j += kThreads) {
             const double pj = __ldcg(P + j);
             ws[j] = pj;
             pv = fma(pj, vs[j], pv);
         }
-        const double half = 0.5 * tau * block_sum_all(pv);
+        const double half = 0.5 * tau_k * block_sum_all(pv);
         for (int j = tid; j < L; j += kThreads) ws[j] = fma(-half, vs[j], ws[j]);   // w = p - half v
         __syncthreads();
-        // A22 -= v w^T + w v^T (two FMAs an entry), own rows in increasing order
-        for (int r = r0; r < n; r += nstep) {
+        // row k+1 after column k: its owner would compute a - v_0 w - w_0 v with v_0 = 1
+        const double* xold = (k == 0) ? T.A + size_t(n) + 1 : T.R + ((k + 1) & 1) * n;
+        const double w0 = ws[0];
+        for (int j = tid; j < L; j += kThreads) xs[j] = fma(-1.0, ws[j], fma(-w0, vs[j], __ldcg(xold + j)));
+        __syncthreads();
+        const bool next = k + 3 < n;   // column k+1 has a reflector
+        double tau_n = 0.0;
+        if (next) {
+            double beta_n;
+            reflector(xs + 1, L - 1, vn, tau_n, beta_n);
+            if (blockIdx.x == 0 && tid == 0) {
+                T.d[k + 1] = xs[0];
+                T.e[k + 1] = beta_n;
+                T.tau[k + 1] = tau_n;
+            }
+        } else if (blockIdx.x == 0 && tid == 0) {   // k = n-3: rows n-2 and n-1 remain
+            T.d[n - 2] = xs[0];
+            T.e[n - 2] = xs[1];
+            T.tau[n - 2] = 0.0;
+            T.tau[n - 1] = 0.0;
+        }
+        // own rows r >= k+2: update for column k, p for column k+1 (columns k+2 .. only;
+        // column k+1 of these rows is the pivot row's, already eliminated)
+        double* Pn = T.P + ((k + 1) & 1) * n;
+        double* Rn = T.R + (k & 1) * n;   // row k+2, columns k+2 ..
+        for (int r = first_own_row(k + 2, blockIdx.x, warp, gridDim.x); r < n; r += nstep) {
             const int i = r - (k + 1);
             double* ri = T.A + size_t(r) * n + (k + 1);
             const double vi = vs[i], wi = ws[i];
-            int j = lane;
-            for (; j + 32 * (kUnroll - 1) < L; j += 32 * kUnroll) {   // kUnroll entries in flight
+            const bool pub = (r == k + 2) && next;
+            double acc[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) acc[u] = 0.0;
+            int j = 1 + lane;
+            for (; j + 32 * (kUnroll - 1) < L; j += 32 * kUnroll) {
                 double a[kUnroll];
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u) a[u] = __ldcg(ri + j + 32 * u);
 #pragma unroll
-                for (int u = 0; u < kUnroll; ++u)
-                    __stcg(ri + j + 32 * u, fma(-vi, ws[j + 32 * u], fma(-wi, vs[j + 32 * u], a[u])));
-            }
-            for (; j < L; j += 32) __stcg(ri + j, fma(-vi, ws[j], fma(-wi, vs[j], __ldcg(ri + j))));
-            if (r == k + 1) {   // the next pivot row is final
-                __syncwarp();
-                if (lane == 0) {
-                    __threadfence();
-                    atomicExch(T.ready + (k + 1), 1);
+                for (int u = 0; u < kUnroll; ++u) {
+                    const int jj = j + 32 * u;
+                    const double an = fma(-vi, ws[jj], fma(-wi, vs[jj], a[u]));
+                    __stcg(ri + jj, an);
+                    if (pub) __stcg(Rn + (jj - 1), an);
+                    acc[u] = fma(an, vn[jj - 1], acc[u]);
                 }
             }
+            for (; j < L; j += 32) {
+                const double an = fma(-vi, ws[j], fma(-wi, vs[j], __ldcg(ri + j)));
+                __stcg(ri + j, an);
+                if (pub) __stcg(Rn + (j - 1), an);
+                acc[0] = fma(an, vn[j - 1], acc[0]);
+                if (!next && r == n - 1) T.d[n - 1] = an;   // k = n-3: the last diagonal entry
+            }
+            if (next) {
+                double p = 0.0;
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) p += acc[u];
+                for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+                if (lane == 0) __stcg(Pn + (r - (k + 2)), tau_n * p);
+            }
         }
-    }
-    if (!grid_barrier(T.bar, gen, T.timeout_ns, T.status)) return;
-    if (blockIdx.x == 0 && tid == 0) {
-        if (n >= 2) {
-            T.d[n - 2] = __ldcg(T.A + size_t(n - 2) * n + (n - 2));
-            T.e[n - 2] = __ldcg(T.A + size_t(n - 2) * n + (n - 1));
-            T.tau[n - 2] = 0.0;
-        }
-        T.d[n - 1] = __ldcg(T.A + size_t(n - 1) * n + (n - 1));
-        T.tau[n - 1] = 0.0;
+        double* t = vs;
+        vs = vn;
+        vn = t;
+        tau_k = tau_n;
     }
 }
 
@@ -684,7 +702,7 @@ WsLayout tridiag_layout(int64_t n, int64_t mp) {
     WsLayout W;
     W.add("A", size_t(n) * n * 8);
     W.add("P", size_t(n) * 2 * 8);
-    W.add("ready", size_t(n) * 4);
+    W.add("R", size_t(n) * 2 * 8);
     W.add("d", size_t(n) * 8);
     W.add("e", size_t(n) * 8);
     W.add("e2", size_t(n) * 8);
@@ -704,7 +722,7 @@ dmrg_status tridiag_eigen(dmrg_handle h, int64_t n64, int64_t mp64, char* ws, do
     const WsLayout W = tridiag_layout(n, mp);
     double* A = reinterpret_cast<double*>(ws + W.offsets[0]);
     double* P = reinterpret_cast<double*>(ws + W.offsets[1]);
-    int* ready = reinterpret_cast<int*>(ws + W.offsets[2]);
+    double* R = reinterpret_cast<double*>(ws + W.offsets[2]);
     double* d = reinterpret_cast<double*>(ws + W.offsets[3]);
     double* e = reinterpret_cast<double*>(ws + W.offsets[4]);
     double* e2 = reinterpret_cast<double*>(ws + W.offsets[5]);
@@ -718,7 +736,7 @@ dmrg_status tridiag_eigen(dmrg_handle h, int64_t n64, int64_t mp64, char* ws, do
     cudaError_t err;
     // 1. tridiagonalisation
     {
-        const size_t smem = size_t(n) * 16;
+        const size_t smem = size_t(n) * 32;
         if (smem > 200 * 1024) return fail(h, DMRG_ERR_SHAPE, "rows too large for the tridiagonal solver");
         err = cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         int grid = 1;
@@ -726,9 +744,8 @@ dmrg_status tridiag_eigen(dmrg_handle h, int64_t n64, int64_t mp64, char* ws, do
             err = coop_grid(reinterpret_cast<const void*>(tridiag_kernel), smem, std::max(1, (n + kWarps - 1) / kWarps),
                             &grid, 1);
         if (err == cudaSuccess) err = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
-        if (err == cudaSuccess) err = cudaMemsetAsync(ready, 0, size_t(n) * 4, s);
         if (err != cudaSuccess) return cuda_fail(h, err, "tridiagonalisation set-up");
-        TriArgs T{A, P, ready, d, e, tau, bar, h->d_status, timeout_ns(h), n};
+        TriArgs T{A, P, R, d, e, tau, bar, h->d_status, timeout_ns(h), n};
         err = timed_launch(h, "trunc_tridiag", s, [&] {
             void* args[] = {&T};
             return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(tridiag_kernel), dim3(unsigned(grid)),
