@@ -10,7 +10,7 @@
 //      column k, the reflector H_k = I - tau v v^T (v_0 = 1) with H_k x = beta e_1 for
 //      x = A[k+1:, k]; then A22 <- H_k A22 H_k as A22 - v w^T - w v^T with
 //      p = tau A22 v and w = p - (tau/2)(p^T v) v.  v is kept in row k of A.
-//   2. All eigenvalues of T by multisection on Sturm counts (four threads per
+//   2. All eigenvalues of T by multisection on Sturm counts (4, 8 or 16 threads per
 //      eigenvalue), to an interval of max(2 eps max(|lo|, |hi|), eps ||T||) + pivmin.
 //   3. The m' largest: inverse iteration with T - lambda I factored once (Gaussian
 //      elimination with partial pivoting on the tridiagonal), four solves from a hashed
@@ -298,10 +298,12 @@ __device__ __forceinline__ int sturm_count(const double* d, const double* e2, in
 // kSect + 1 times.  Stops at width 2 eps max(|lo|, |hi|), or eps ||T|| (the absolute
 // accuracy a backward-stable dense solver gives), plus pivmin.  The eigenvalue is
 // stored as lambda[n - 1 - j] (decreasing order).  d and e^2 are staged in shared
-// memory when they fit.
-constexpr int kSect = 4;
+// memory when they fit.  A Sturm count is a chain of dependent FP64 operations, so the
+// host picks kSect (4, 8 or 16) to give every SM at least two warps: more points per
+// round cost more counts in all but fewer rounds on the critical path.
 constexpr int kBisectThreads = 64;
 
+template <int kSect>
 __global__ void __launch_bounds__(kBisectThreads) bisect_kernel(const double* __restrict__ d,
                                                                 const double* __restrict__ e, int n,
                                                                 const double* __restrict__ stats,
@@ -760,12 +762,17 @@ dmrg_status tridiag_eigen(dmrg_handle h, int64_t n64, int64_t mp64, char* ws, do
         err = timed_launch(h, "trunc_bisect", s, [&] {
             tri_stats_kernel<<<1, kThreads, 0, s>>>(d, e, n, stats);
             if (!staged) square_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(e, n, e2);
-            cudaError_t r = cudaFuncSetAttribute(bisect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            // at least two warps per SM where n allows it (measured at n = 1600: 4 points
+            // 11.2 ms, 8 points 8.4 ms, 16 points 9.1 ms)
+            const int64_t want = int64_t(h->num_sms) * 2 * 32;
+            const int sect = int64_t(n) * 4 >= want ? 4 : int64_t(n) * 8 >= want ? 8 : 16;
+            const int64_t threads = int64_t(n) * sect;
+            const unsigned blocks = unsigned((threads + kBisectThreads - 1) / kBisectThreads);
+            auto kern = sect == 4 ? bisect_kernel<4> : sect == 8 ? bisect_kernel<8> : bisect_kernel<16>;
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  int(std::max<size_t>(smem, 1)));
             if (r != cudaSuccess) return r;
-            const int64_t threads = int64_t(n) * kSect;
-            bisect_kernel<<<unsigned((threads + kBisectThreads - 1) / kBisectThreads), kBisectThreads, smem, s>>>(
-                d, e, n, stats, e2, staged ? 1 : 0, lambda);
+            kern<<<blocks, kBisectThreads, smem, s>>>(d, e, n, stats, e2, staged ? 1 : 0, lambda);
             return cudaGetLastError();
         });
         if (err != cudaSuccess) return cuda_fail(h, err, "bisection");
