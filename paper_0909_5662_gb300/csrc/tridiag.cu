@@ -39,7 +39,6 @@ using dmrg::grid_barrier;
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kInvitIters = 4;
-constexpr int kBackVecs = 2;   // eigenvectors per block in the back-transformation
 
 // ---------------------------------------------------------------- 1. tridiagonalisation
 struct TriArgs {
@@ -574,112 +573,110 @@ __global__ void __launch_bounds__(kThreads) mgs_kernel(MgsArgs M) {
 }
 
 // ---------------------------------------------------------------- 5. back-transformation
-// Block b: eigenvectors kBackVecs * b .. + kBackVecs - 1, staged in shared memory; the
-// reflectors are applied from the last to the first, each staged in shared memory while
-// the previous one is applied; then each column gets its sign and is written into U
-// (n x mp, row-major).
-__global__ void __launch_bounds__(kThreads) back_kernel(const double* __restrict__ A,
-                                                        const double* __restrict__ tau,
-                                                        const double* __restrict__ Zt, int n,
-                                                        int mp, double* __restrict__ U) {
-    extern __shared__ double zs[];   // kBackVecs x n, then two reflector buffers of n
-    double* const vb0 = zs + size_t(kBackVecs) * n;
-    double* const vb1 = zs + size_t(kBackVecs + 1) * n;
-    const int tid = threadIdx.x;
-    const int j0 = blockIdx.x * kBackVecs;
-    const int nv = min(kBackVecs, mp - j0);
-    for (int q = 0; q < nv; ++q)
-        for (int i = tid; i < n; i += kThreads) zs[q * n + i] = Zt[size_t(j0 + q) * n + i];
-    if (n >= 3)   // the last reflector, v_{n-3} (two entries)
-        for (int i = tid; i < 2; i += kThreads) vb0[i] = A[size_t(n - 3) * n + (n - 2) + i];
+// One block of kBackSplit warps per eigenvector.  The vector lives in shared memory and
+// each warp owns a fixed set of its entries (alternate 32-entry blocks), so the warps
+// meet once per reflector, to add their halves of v^T z.  The reflectors are applied from
+// the last to the first; each is fetched with cp.async into one of three rotating
+// shared-memory buffers while the one before it is applied.  FP64 issues per SM
+// sub-partition, so the vectors are split over warps to occupy all four of them.
+// Then the vector gets its sign (the largest-magnitude component positive, the first
+// index on ties) and is written into U (n x mp, row-major).
+constexpr int kBackSplit = 4;   // warps per eigenvector
+constexpr int kBackThreads = 32 * kBackSplit;
+
+__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dmrg::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__global__ void __launch_bounds__(kBackThreads) back_kernel(const double* __restrict__ A,
+                                                            const double* __restrict__ tau,
+                                                            const double* __restrict__ Zt, int n,
+                                                            int mp, double* __restrict__ U) {
+    extern __shared__ double bsm[];   // the vector (n), three reflector buffers (n each)
+    __shared__ double part[2][kBackSplit];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int j = blockIdx.x;
+    double* z = bsm;
+    for (int i = tid; i < n; i += kBackThreads) z[i] = Zt[size_t(j) * n + i];
+    auto buf = [&](int slot) { return bsm + size_t(1 + slot) * n; };
+    auto fetch = [&](int k, double* dst) {   // v_k: A[k][k+1 .. n-1], one group (maybe empty)
+        if (k >= 0) {
+            const double* src = A + size_t(k) * n + (k + 1);
+            for (int i = tid; i < n - k - 1; i += kBackThreads) cp_async8(dst + i, src + i);
+        }
+        cp_async_commit();
+    };
+    fetch(n - 3, buf(0));
+    fetch(n - 4, buf(1));
+    cp_async_wait_all();
     __syncthreads();
-    __shared__ double part[kBackVecs][kWarps];
-    int cur = 0;
+    // this warp's entries: i = 32 (kBackSplit q + w) + lane, q = 0, 1, ...
+    int slot = 0;
     for (int k = n - 3; k >= 0; --k) {
-        const int L = n - k - 1;
-        const double* v = cur ? vb1 : vb0;
-        // stage the next reflector (k - 1, length L + 1) while this one is applied
-        if (k >= 1) {
-            double* nxt = cur ? vb0 : vb1;
-            const double* src = A + size_t(k - 1) * n + k;
-            for (int i = tid; i < L + 1; i += kThreads) nxt[i] = src[i];
+        const double t = tau[k];   // uniform over the block
+        const double* v = buf(slot);
+        // first of this warp's 32-entry blocks that reaches past k
+        const int b0 = (k + 1) >> 5;
+        const int i0 = 32 * (b0 + (w - b0 % kBackSplit + kBackSplit) % kBackSplit) + lane;
+        double a0 = 0.0, a1 = 0.0;
+        for (int i = i0; i < n; i += 64 * kBackSplit) {
+            if (i > k) a0 = fma(v[i - (k + 1)], z[i], a0);
+            const int i2 = i + 32 * kBackSplit;
+            if (i2 < n) a1 = fma(v[i2 - (k + 1)], z[i2], a1);
         }
-        const double t = tau[k];
-        if (t != 0.0) {   // uniform over the block
-            double acc[kBackVecs];
+        double sdot = a0 + a1;
+        for (int o = 16; o > 0; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
+        if (lane == 0) part[k & 1][w] = sdot;
+        cp_async_wait_all();   // v_{k-1}, fetched one reflector ago
+        __syncthreads();       // both halves of v^T z; v_{k-1} complete; every read of v_{k+1} done
+        fetch(k - 2, buf(slot == 0 ? 2 : slot - 1));   // into the buffer of v_{k+1}
+        if (t != 0.0) {
+            double sum = 0.0;
 #pragma unroll
-            for (int q = 0; q < kBackVecs; ++q) acc[q] = 0.0;
-            for (int i = tid; i < L; i += kThreads) {
-                const double vi = v[i];
-#pragma unroll
-                for (int q = 0; q < kBackVecs; ++q)
-                    if (q < nv) acc[q] = fma(vi, zs[q * n + k + 1 + i], acc[q]);
-            }
-#pragma unroll
-            for (int q = 0; q < kBackVecs; ++q) {
-                double a = acc[q];
-                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-                if ((tid & 31) == 0) part[q][tid >> 5] = a;
-            }
-            __syncthreads();
-            double coef[kBackVecs];
-#pragma unroll
-            for (int q = 0; q < kBackVecs; ++q) {
-                double sum = 0.0;
-                for (int w = 0; w < kWarps; ++w) sum += part[q][w];
-                coef[q] = t * sum;
-            }
-            for (int i = tid; i < L; i += kThreads) {
-                const double vi = v[i];
-#pragma unroll
-                for (int q = 0; q < kBackVecs; ++q)
-                    if (q < nv) zs[q * n + k + 1 + i] -= coef[q] * vi;
-            }
+            for (int u = 0; u < kBackSplit; ++u) sum += part[k & 1][u];
+            const double c = t * sum;
+            for (int i = i0; i < n; i += 32 * kBackSplit)
+                if (i > k) z[i] = fma(-c, v[i - (k + 1)], z[i]);
         }
-        __syncthreads();
-        cur ^= 1;
+        slot = slot == 2 ? 0 : slot + 1;
     }
-    // sign: the largest-magnitude component positive (first index on ties)
-    __shared__ double bv[kWarps];
-    __shared__ int bi[kWarps];
-    __shared__ double sgn;
-    for (int q = 0; q < nv; ++q) {
-        double best = -1.0;
-        int idx = 0;
-        for (int i = tid; i < n; i += kThreads) {
-            const double a = fabs(zs[q * n + i]);
-            if (a > best) {
-                best = a;
-                idx = i;
-            }
+    cp_async_wait_all();
+    __syncthreads();
+    __shared__ double bv[kBackSplit];
+    __shared__ int bi[kBackSplit];
+    double best = -1.0;
+    int idx = 0;
+    for (int i = tid; i < n; i += kBackThreads) {
+        const double a = fabs(z[i]);
+        if (a > best) {
+            best = a;
+            idx = i;
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-            if (ob > best || (ob == best && oi < idx)) {
-                best = ob;
-                idx = oi;
-            }
-        }
-        if ((tid & 31) == 0) {
-            bv[tid >> 5] = best;
-            bi[tid >> 5] = idx;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            best = bv[0];
-            idx = bi[0];
-            for (int w = 1; w < kWarps; ++w)
-                if (bv[w] > best || (bv[w] == best && bi[w] < idx)) {
-                    best = bv[w];
-                    idx = bi[w];
-                }
-            sgn = zs[q * n + idx] < 0.0 ? -1.0 : 1.0;
-        }
-        __syncthreads();
-        for (int i = tid; i < n; i += kThreads) U[size_t(i) * mp + j0 + q] = sgn * zs[q * n + i];
-        __syncthreads();
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ob > best || (ob == best && oi < idx)) {
+            best = ob;
+            idx = oi;
+        }
+    }
+    if (lane == 0) {
+        bv[w] = best;
+        bi[w] = idx;
+    }
+    __syncthreads();
+    best = bv[0];
+    idx = bi[0];
+    for (int u = 1; u < kBackSplit; ++u)
+        if (bv[u] > best || (bv[u] == best && bi[u] < idx)) {
+            best = bv[u];
+            idx = bi[u];
+        }
+    const double sgn = z[idx] < 0.0 ? -1.0 : 1.0;
+    for (int i = tid; i < n; i += kBackThreads) U[size_t(i) * mp + j] = sgn * z[i];
 }
 
 // Blocks of a cooperative launch of `kernel` with `smem` dynamic bytes, at most `cap`.
@@ -801,12 +798,12 @@ dmrg_status tridiag_eigen(dmrg_handle h, int64_t n64, int64_t mp64, char* ws, do
     }
     // 5. back-transformation and the sign convention
     {
-        const size_t smem = size_t(kBackVecs + 2) * n * 8;
+        const size_t smem = size_t(4) * n * 8;
         if (smem > 200 * 1024) return fail(h, DMRG_ERR_SHAPE, "rows too large for the tridiagonal solver");
         err = cudaFuncSetAttribute(back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (err == cudaSuccess)
             err = timed_launch(h, "trunc_back", s, [&] {
-                back_kernel<<<unsigned((mp + kBackVecs - 1) / kBackVecs), kThreads, smem, s>>>(A, tau, Zt, n, mp, U);
+                back_kernel<<<unsigned(mp), kBackThreads, smem, s>>>(A, tau, Zt, n, mp, U);
                 return cudaGetLastError();
             });
         if (err != cudaSuccess) return cuda_fail(h, err, "back-transformation");
