@@ -399,14 +399,16 @@ __global__ void __launch_bounds__(32) invit_kernel(const double* __restrict__ d,
     const double small = DBL_EPSILON * fmax(stats[2], DBL_MIN);
     auto at = [&](int i) { return size_t(i) * mp + j; };
     auto guard = [&](double a) { return fabs(a) < small ? (a >= 0.0 ? small : -small) : a; };
-    // T - lam I = P L U with partial pivoting; U has diagonals u1, u2 (super), u3
+    // T - lam I = P L U with partial pivoting; U has diagonals u1, u2 (super), u3.  u1 is
+    // stored inverted: the one division per row here replaces one per row in each of the
+    // solves below (a division is a long FP64 sequence, and FP64 is this kernel's bound).
     double a = d[0] - lam, s_cur = n > 1 ? e[0] : 0.0;
     for (int i = 0; i + 1 < n; ++i) {
         const double c = e[i], a_next = d[i + 1] - lam, s_next = (i + 2 < n) ? e[i + 1] : 0.0;
         if (fabs(a) >= fabs(c)) {
-            if (a == 0.0) a = small;
-            const double l = c / a;
-            u1[at(i)] = guard(a);
+            const double inv = 1.0 / guard(a);
+            const double l = c * inv;
+            u1[at(i)] = inv;
             u2[at(i)] = s_cur;
             u3[at(i)] = 0.0;
             lm[at(i)] = l;
@@ -414,8 +416,9 @@ __global__ void __launch_bounds__(32) invit_kernel(const double* __restrict__ d,
             a = a_next - l * s_cur;
             s_cur = s_next;
         } else {
-            const double l = a / c;
-            u1[at(i)] = guard(c);
+            const double inv = 1.0 / guard(c);
+            const double l = a * inv;
+            u1[at(i)] = inv;
             u2[at(i)] = a_next;
             u3[at(i)] = s_next;
             lm[at(i)] = l;
@@ -424,7 +427,7 @@ __global__ void __launch_bounds__(32) invit_kernel(const double* __restrict__ d,
             s_cur = -l * s_next;
         }
     }
-    u1[at(n - 1)] = guard(a);
+    u1[at(n - 1)] = 1.0 / guard(a);
     for (int i = 0; i < n; ++i) z[at(i)] = start_entry(i, j);
     for (int it = 0; it < kInvitIters; ++it) {
         double zmax = 0.0;
@@ -482,7 +485,7 @@ __global__ void __launch_bounds__(32) invit_kernel(const double* __restrict__ d,
             for (int q = 0; q < kChunk; ++q) {
                 const int i = i0 - q;
                 if (i >= 0) {
-                    const double x = (yc[q] - a2[q] * x1 - a3[q] * x2) / a1[q];
+                    const double x = (yc[q] - a2[q] * x1 - a3[q] * x2) * a1[q];
                     z[at(i)] = x;
                     x2 = x1;
                     x1 = x;
@@ -776,8 +779,8 @@ dmrg_status tridiag_eigen(dmrg_handle h, int64_t n64, int64_t mp64, char* ws, do
     }
     // 3. inverse iteration
     err = timed_launch(h, "trunc_invit", s, [&] {
-        // one warp per block: each SM's FP64 pipes serve as few sequential chains as possible
-        invit_kernel<<<unsigned((mp + 31) / 32), 32, 0, s>>>(d, e, n, mp, lambda, stats, lu[0], lu[1], lu[2],
+        // four threads per block: the vectors spread over many SM sub-partitions
+        invit_kernel<<<unsigned((mp + 3) / 4), 4, 0, s>>>(d, e, n, mp, lambda, stats, lu[0], lu[1], lu[2],
                                                              lu[3], sw, lu[4], Zt);
         return cudaGetLastError();
     });
