@@ -24,6 +24,11 @@
 // block: the U tiles (the same for every operator) are loaded once per cluster, each
 // CTA fetching 1/C of the rows and multicasting them; every CTA's MMA issuer releases a
 // stage in all CTAs of the cluster, so a stage is refilled only when all have read it.
+//
+// Opt-in (DMRG_OPT_FUSED_ROTATION): at m = 400, d = 4 it is slower than the two products
+// for every m' it supports.  A unit re-streams O_k once per site state and the U panel
+// once per chunk, and a 32 KB stage feeds only 400 cycles of MMAs, so the tensor pipe
+// waits on the operand ring (26 % active); the two-product kernels keep deeper stages.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -56,7 +61,8 @@ struct FusedLaunch {
     CUtensorMap tmUa[2];   // Pu hi/lo: (j, x, s), box 32 x slice_a (first product's A)
     CUtensorMap tmUb[2];   // Pu hi/lo: (i, x, s), box 32 x slice_b (second product's B)
     float* out;            // K x m' x m' (row-major O'_k[alpha][beta])
-    int K, m, d, mp, mpp, nb, units, chain_chunks;
+    int K, m, d, mp, mpp, nb, chain_chunks;
+    int units;                 // (group of C operators, output block) pairs
     int C, slice_a, slice_b;   // cluster size; rows of the U tiles each CTA fetches
     unsigned* status;
     uint64_t timeout_ns;
