@@ -27,8 +27,9 @@
 //
 // Opt-in (DMRG_OPT_FUSED_ROTATION): at m = 400, d = 4 it is slower than the two products
 // for every m' it supports.  A unit re-streams O_k once per site state and the U panel
-// once per chunk, and a 32 KB stage feeds only 400 cycles of MMAs, so the tensor pipe
-// waits on the operand ring (26 % active); the two-product kernels keep deeper stages.
+// once per chunk, a 32 KB stage feeds only 400 cycles of MMAs, and the tensor pipe is
+// 26 % active with no other unit near its limit (latency along the chain from the first
+// product through the epilogue warps to the second).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
