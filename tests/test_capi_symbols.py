@@ -76,3 +76,18 @@ def test_umd_partition():
             assert max(sizes) - min(sizes) <= 1
             # the first L mod p ranks hold the extra operator
             assert sizes == sorted(sizes, reverse=True)
+
+
+def _header_enum(name):
+    text = open(HEADER).read()
+    body = re.search(r"typedef enum \{([^}]*)\}\s*" + name + r";", text).group(1)
+    return {k: int(v) for k, v in re.findall(r"(DMRG_\w+)\s*=\s*(\d+)", body)}
+
+
+def test_binding_enums_match_header():
+    # the Python names of options and precisions carry the header's values
+    from paper_0909_5662_gb300 import _capi
+    opts = _header_enum("dmrg_option")
+    assert {("DMRG_OPT_" + k.upper()): v for k, v in _capi.OPTION.items()} == opts
+    precs = _header_enum("dmrg_precision")
+    assert {("DMRG_PREC_" + k.upper()): v for k, v in _capi.PRECISION.items()} == precs
