@@ -171,21 +171,48 @@ def cpu_oracle_sample(w, budget_s: float = 12.0, max_ops: int = 150):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands, on the host cores.  Each
+    step rotates a bounded sample of the workload's operators (the first n of the
+    batch, n chosen from the warm-up steps so that the timed steps take about 90 s in
+    all, at least one operator and at most the whole batch); value = operators rotated
+    in the timed steps / their total time, and ms_per_step is the measured time of one
+    such step."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    import oracle
     from workloads import dense_config
+    oracle.build()
     w = dense_config(WORKLOAD)
+    cores = oracle.num_threads()
+    n = min(K_PER_GPU, cores)
+    rate = None
     for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state; keep the arm's shape
-    res = cpu_oracle_sample(w, budget_s=min(60.0, max(10.0, 3.0 * args.steps)), max_ops=K_PER_GPU)
-    v = res["value"]
+        t0 = time.perf_counter()
+        oracle.rotate_dense(w.U, w.O[:n], w.d)
+        rate = n / (time.perf_counter() - t0)
+    budget_s = 90.0
+    n = int(max(1, min(K_PER_GPU, rate * budget_s / max(args.steps, 1))))
+    if n >= cores:
+        n = n // cores * cores   # whole rounds of the UMD split
+    t_total = 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.rotate_dense(w.U, w.O[:n], w.d)
+        t_total += time.perf_counter() - t0
+    done = n * args.steps
+    v = done / t_total
+    res = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "each step rotates the first %d of the %d operators of %s (FP64 loops, UMD "
+                     "split over %d OpenMP threads); %d timed steps, %.1f s" %
+                     (n, K_PER_GPU, WORKLOAD, cores, args.steps, t_total)}
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": K_PER_GPU / v * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference",
+            "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
             "config": {"workload": "%s (d=4, m=400, m'=400, K=150)" % WORKLOAD,
-                       "arm": "FP64 CPU oracle (the reference arm of this project)"},
+                       "arm": "FP64 CPU oracle (the reference arm of this project)",
+                       "operators_per_step": n},
             "cpu_baseline": res,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -214,7 +241,7 @@ def _timed(fn, steps, warmup, flush):
     return sum(a.elapsed_time(b) for a, b in evs) / steps
 
 
-def run_blocked(args):
+def blocked_report(steps, precisions, flush):
     """The U(1)xU(1) block-sparse rotation (grouped launches over the realised sector
     problems) on both synthetic sector laws: time per call for every precision,
     logical TFLOP/s over the realised problems, and the error of each reduced path
@@ -223,10 +250,7 @@ def run_blocked(args):
     import paper_0909_5662_gb300 as P
     from workloads import blocked_config
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    steps = max(1, min(args.steps, 200))
+    dev = flush.device
     res = {}
     for name in ("blocked_m1000_k200_s4", "blocked_m1000_k200_s1.2"):
         w = blocked_config(name)
@@ -242,7 +266,7 @@ def run_blocked(args):
                "problems_first": n1, "problems_second": n2, "flops_per_call": flops,
                "sectors": len(w.block_sectors), "operators": w.K,
                "block_rows_max": max(s[2] for s in w.block_sectors)}
-        for prec in ([args.precision] if args.precision else ("bf16x3", "tf32", "fp32", "fp64")):
+        for prec in precisions:
             O = O64 if prec == "fp64" else O32
             out = P.dmrg_rotate_ops_blocked(plan, Ub, O, prec)
             n = steps if prec != "fp64" else max(1, steps // 10)
@@ -256,6 +280,17 @@ def run_blocked(args):
                          "kernels": kt}
         res[name] = row
         plan.close()
+    return res
+
+
+def run_blocked(args):
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    steps = max(1, min(args.steps, 200))
+    res = blocked_report(steps, [args.precision] if args.precision else
+                         ["bf16x3", "tf32", "fp32", "fp64"], flush)
     line = {"workload": "blocked U(1)xU(1), m=1000, d=4, K=200 (two sector laws)",
             "metric": "block-sparse rotation: ms per call, logical TFLOP/s over the realised problems",
             "steps": steps, "l2": "flushed between timed calls", "results": res, "data": "synthetic"}
@@ -263,20 +298,16 @@ def run_blocked(args):
     return 0
 
 
-def run_backward(args):
+def backward_report(steps, precs, flush):
     """The adjoint at the benchmark shape (d = 4, m = m' = 400, K = 150, FP32 operators,
     upstream G ~ N(0,1)): dO and dU per call for each precision, in forward-product
     equivalents (one forward product = 0.512 GFLOP logical per operator), with the
     error of the reduced paths against the FP32-input FP64 path."""
-    import numpy as np
     import torch
     import paper_0909_5662_gb300 as P
     from workloads import dense_config, backward_upstream, SEED_BASE
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    steps = max(1, min(args.steps, 200))
+    dev = flush.device
     w = dense_config(WORKLOAD)
     U = torch.from_numpy(w.U).to(dev)
     O32 = torch.from_numpy(w.O).to(dev, torch.float32)
@@ -284,7 +315,6 @@ def run_backward(args):
     dO_ref, dU_ref = P.dmrg_rotate_ops_backward(U, O32.double(), G32.double(), w.d, "fp64")
     fwd_product = 2.0 * w.K * w.m * (w.d * w.mp) * w.m
     res = {}
-    precs = [args.precision] if args.precision else ["bf16x3", "tf32", "fp32", "fp64"]
     for prec in [p for p in precs if p != "fp64"]:
         dO, dU = P.dmrg_rotate_ops_backward(U, O32, G32, w.d, prec)
         ms = _timed(lambda: P.dmrg_rotate_ops_backward(U, O32, G32, w.d, prec), steps, 3, flush)
@@ -301,6 +331,17 @@ def run_backward(args):
         t64 = _timed(lambda: P.dmrg_rotate_ops_backward(U, O32.double(), G32.double(), w.d, "fp64"),
                      1, 1, flush)
         res["fp64"] = {"ms_per_call": t64, "ops_per_s": w.K / (t64 * 1e-3)}
+    return res
+
+
+def run_backward(args):
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    steps = max(1, min(args.steps, 200))
+    res = backward_report(steps, [args.precision] if args.precision else
+                          ["bf16x3", "tf32", "fp32", "fp64"], flush)
     line = {"workload": "backward dense_m400_k150 (d=4, m=m'=400, K=150, upstream N(0,1))",
             "metric": "adjoint: ms per call (dO and dU), rotated operators/s",
             "steps": steps, "l2": "flushed between timed calls", "results": res, "data": "synthetic"}
@@ -637,7 +678,7 @@ def run_measure(args):
 
 
 # ---------------------------------------------------------------------------- chained sweep
-def run_chained(args):
+def chained_report(sweep_steps, with_oracle):
     """50 consecutive block-growth steps at d = 4, m = m' = 1200, K = 300: the rotated
     operators of step s are the inputs of step s + 1, with a fresh seeded orthonormal U
     per step.  BF16x3 and TF32 carry all 300 operators; the FP64 GPU path carries a
@@ -649,10 +690,9 @@ def run_chained(args):
     import paper_0909_5662_gb300 as P
     from workloads import chained_inputs, SEED_BASE
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
+    dev = torch.device("cuda", torch.cuda.current_device())
     d, m, K = 4, 1200, 300
-    steps = args.sweep_steps
+    steps = sweep_steps
     track = list(range(0, K, K // 16))[:16]
     g = torch.Generator(device=dev)
     g.manual_seed(SEED_BASE + 5)
@@ -680,7 +720,7 @@ def run_chained(args):
         P.dmrg_rotate_ops(U, ref, d, "fp64", out=ref_out)
         ref, ref_out = ref_out, ref
         P.dmrg_sync_status()
-        if step == 0 and not args.no_cpu_baseline:
+        if step == 0 and with_oracle:
             import oracle
             sub = [0, 1]
             r0 = oracle.rotate_dense(U.cpu().numpy(), O0[[track[i] for i in sub]].cpu().numpy(), d)
@@ -697,7 +737,7 @@ def run_chained(args):
         C = P.dmrg_correlations(cur[p][track].contiguous(), psi)
         corr[p] = float((torch.linalg.vector_norm(C - C_ref) / torch.linalg.vector_norm(C_ref)).item())
     flops_step = 2.0 * K * d * m * m * (m + m)
-    line = {"workload": "chained_m1200_k300 (d=4, m=m'=1200, K=300, %d steps)" % steps,
+    return {"workload": "chained_m1200_k300 (d=4, m=m'=1200, K=300, %d steps)" % steps,
             "metric": "chained sweep: rotated operators/s per precision, accumulated drift",
             "unit": UNIT, "steps": steps,
             "precisions": {p: {"ms_per_step": ms[p] / steps,
@@ -709,8 +749,47 @@ def run_chained(args):
                                "correlation_rel_err": corr[p]} for p in cur},
             "fp64_reference": {"tracked_operators": track, "oracle_step1_rel_err": oracle_step1},
             "data": "synthetic"}
-    print(json.dumps(line), flush=True)
+
+
+def run_chained(args):
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(chained_report(args.sweep_steps, not args.no_cpu_baseline)), flush=True)
     return 0
+
+
+def dtype_peaks(dev):
+    """Measured dense matmul peaks of the other two precisions the rotation runs in:
+    TF32 (FP32 torch.matmul with TF32 tensor cores allowed, 8192^3) and FP64
+    (torch.matmul, 4096^3), best of several calls timed with CUDA events.  No clock or
+    power setting is touched."""
+    import torch
+    out = {}
+    for name, dt, n, reps in (("tf32_tflops", torch.float32, 8192, 10),
+                              ("fp64_tflops", torch.float64, 4096, 4)):
+        old = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = (dt == torch.float32)
+        try:
+            a = torch.randn(n, n, dtype=dt, device=dev)
+            b = torch.randn(n, n, dtype=dt, device=dev)
+            c = a @ b
+            torch.cuda.synchronize()
+            best = 1e30
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out[name] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+            out[name.replace("_tflops", "_how")] = "torch.matmul %d^3, best of %d (CUDA events)" % (n, reps)
+            del a, b, c
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = old
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -720,6 +799,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="dense line only: skip the blocked, backward and chained reports and "
+                         "the TF32/FP64 matmul peaks")
     ap.add_argument("--workload", default="dense",
                     choices=["dense", "chained", "blocked", "backward", "site", "measure", "truncation",
                              "fused"],
@@ -906,6 +988,29 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(w)
 
+    # ---- the other workloads of the method on one GPU (block-sparse, adjoint, chained
+    #      sweep) and the TF32 / FP64 matmul peaks, after every timed dense step
+    extras = {}
+    if rank == 0 and ws == 1 and not args.no_extras:
+        del out_bf, out_tf, out_64
+        torch.cuda.empty_cache()
+        n_extra = max(3, min(args.steps, 50))
+        pk = dtype_peaks(dev)
+        eff_tf = flops_logical / (ms_tf * 1e-3) / 1e12
+        eff_64 = flops_logical / (ms_64 * 1e-3) / 1e12
+        extras["dtype_peaks"] = dict(pk, bf16_tflops=peaks["bf16_tflops"],
+                                     bf16_source="%s bf16_tflops (burst)" % peak_src)
+        extras["precision_fractions"] = {
+            "bf16x3_issued_of_bf16_peak": 3 * flops_logical / (ms_step * 1e-3) / 1e12 / peaks["bf16_tflops"],
+            "tf32_of_tf32_peak": eff_tf / pk["tf32_tflops"],
+            "fp64_of_fp64_peak": eff_64 / pk["fp64_tflops"],
+            "note": "whole-step rates (all kernels of the step) over the measured matmul peak "
+                    "of the precision the products issue: BF16x3 issues 3 BF16 MMAs per "
+                    "logical multiply-add, TF32 one, FP64 (SIMT FMA) one"}
+        extras["blocked"] = blocked_report(n_extra, ["bf16x3", "tf32", "fp32", "fp64"], flush)
+        extras["backward"] = backward_report(n_extra, ["bf16x3", "tf32", "fp32", "fp64"], flush)
+        extras["chained"] = chained_report(args.sweep_steps, not args.no_cpu_baseline)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -940,6 +1045,7 @@ def main():
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": clocks,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if pg is not None:
         pg.barrier()

@@ -104,11 +104,16 @@ DMRG_API dmrg_status dmrg_sync_status(dmrg_handle handle, dmrg_stream_t stream);
  *                              (within the precision's tolerance).
  *   DMRG_OPT_ACCUM_CHAIN     : longest reduction (in elements) that one tensor-core
  *                              FP32 accumulator sums in the BF16x3 dense products
- *                              (default 1024).  A longer reduction (and longer than
- *                              512) is cut into chains of this length whose results
- *                              are added in FP32 with round to nearest; the tensor
- *                              core's own accumulation error grows with the chain
- *                              length.  0 = one chain.
+ *                              (default 1024, accepted 1 .. 1024).  A longer
+ *                              reduction (and longer than 512) is cut into chains of
+ *                              this length whose results are added in FP32 with
+ *                              round to nearest; the tensor core's own accumulation
+ *                              error grows with the chain length, and chains longer
+ *                              than 1024 (or one chain per tile) break the 1e-5
+ *                              BF16x3 bound at m*d = 4800, so such values return
+ *                              DMRG_ERR_INVALID_ARG.  Products whose reduction needs
+ *                              chains always run on the CTA-pair kernel, whatever
+ *                              tiling is cached.
  *   DMRG_OPT_BLOCKED_SMALL   : 1 (default) = blocked plans whose sectors all hold at
  *                              most 32 states (site dimension <= 8) run one fused
  *                              kernel, one warp per (operator, output block), in FP32
@@ -118,14 +123,21 @@ DMRG_API dmrg_status dmrg_sync_status(dmrg_handle handle, dmrg_stream_t stream);
  *                              sweeps; 0 (default) = Householder tridiagonalisation,
  *                              bisection and inverse iteration (rows <= 6144; larger
  *                              matrices take the Jacobi sweeps).
- *   DMRG_OPT_FUSED_ROTATION  : 1, 2 or 4 = dmrg_rotate_ops runs DMRG_PREC_BF16X3
- *                              with mp <= 256 as one kernel per call that keeps the
+ *   DMRG_OPT_FUSED_ROTATION  : 1 = dmrg_rotate_ops runs DMRG_PREC_BF16X3 with
+ *                              mp <= 256 as one kernel per call that keeps the
  *                              intermediate (O_k (x) I_d) U on chip (tensor memory and
- *                              shared memory) instead of writing it to global memory;
- *                              the value is the number of CTAs (one per operator) that
- *                              share each tile of U through cluster multicast.  Same
- *                              precision and workspace as the two-product path.
+ *                              shared memory) instead of writing it to global memory.
+ *                              Same precision and workspace as the two-product path.
  *                              0 (default) = the two products (mp > 256 always).
+ *                              Other values return DMRG_ERR_INVALID_ARG.
+ *   DMRG_OPT_PACK_OPERATORS  : 0 = the TF32 and BF16x3 dense products take FP32
+ *                              operators whose rows are whole 16-byte units
+ *                              (m % 4 == 0, 16-byte aligned base) as they are: the
+ *                              first product converts each tile in shared memory (BF16
+ *                              hi/lo split or TF32 rounding, the same values as the
+ *                              packing pass).  1 (default) = always pack the operators
+ *                              in a separate pass first (FP64 operators and other rows
+ *                              always are).
  *   DMRG_OPT_TEST_WITHHOLD_ARRIVAL : test hook for failure detection.  1 makes
  *                              the next dense tensor-core launch withhold one
  *                              shared-memory stage release in its first CTA, so
@@ -143,7 +155,8 @@ typedef enum {
     DMRG_OPT_ACCUM_CHAIN = 7,
     DMRG_OPT_BLOCKED_SMALL = 8,
     DMRG_OPT_TRUNCATION_JACOBI = 9,
-    DMRG_OPT_FUSED_ROTATION = 10
+    DMRG_OPT_FUSED_ROTATION = 10,
+    DMRG_OPT_PACK_OPERATORS = 11
 } dmrg_option;
 DMRG_API dmrg_status dmrg_set_option(dmrg_handle handle, dmrg_option option, double value);
 
@@ -416,6 +429,21 @@ DMRG_API dmrg_status dmrg_rotate_site_ops(dmrg_handle handle, const double* U, i
                                  const int32_t* flags, const signed char* parity, void* Oout,
                                  dmrg_precision precision, void* ws, size_t ws_bytes,
                                  dmrg_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Diagnostic: the reciprocal used by the Sturm counts of dmrg_truncation's
+ * eigenvalue multisection (Sec. 2, the diagonalisation of rho in Eq. rho).
+ *
+ * out[i] = 1 / q[i] computed as the truncation kernels compute it: the
+ * hardware's approximate reciprocal refined by two Newton-Raphson steps.
+ *   q, out  device, n FP64 values each (caller-owned).
+ * For normal |q| <= 1/DBL_MIN the result is within a few ulps of correctly
+ * rounded division; larger |q| flush to zero.  Asynchronous on stream.
+ * Errors: DMRG_ERR_INVALID_ARG for n < 0 or NULL pointers with n > 0,
+ * DMRG_ERR_CUDA if the launch fails.
+ * ------------------------------------------------------------------------ */
+DMRG_API dmrg_status dmrg_debug_reciprocal(const double* q, double* out, int64_t n,
+                                           dmrg_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Dense rotation without any allocation (the paper has no counterpart; this

@@ -182,10 +182,25 @@ std::string shape_key(const char* tag, int64_t K, int64_t m, int d, int64_t mp, 
 // Dense tensor-core forward with explicit tilings (the autotuner calls this directly).
 dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, int64_t mp,
                              const void* O, int in_is_fp64, int64_t K, void* Oout,
-                             dmrg_precision p, void* ws, const TcConfig& c1, const TcConfig& c2,
-                             cudaStream_t s, bool pack_u, const double* U1,
+                             dmrg_precision p, void* ws, const TcConfig& c1_in,
+                             const TcConfig& c2_in, cudaStream_t s, bool pack_u, const double* U1,
                              const FirstClasses* cls) {
     const DenseDims D = dense_dims(K, m, d, mp, p);
+    // Only the CTA-pair kernel cuts long BF16x3 reductions into accumulation chains, so
+    // a product whose reduction is longer than one chain runs on CTA pairs whatever
+    // tiling was tuned or cached (the 1e-5 accuracy of BF16x3 depends on the chains).
+    TcConfig c1 = c1_in, c2 = c2_in;
+    if (p == DMRG_PREC_BF16X3) {
+        const int64_t one_chain = std::max<int64_t>(kChainMinRed, h->accum_chain);
+        TcConfig* cs[2] = {&c1, &c2};
+        const int64_t red[2] = {m, D.md};
+        for (int i = 0; i < 2; ++i) {
+            if (red[i] > one_chain && !cs[i]->pair) {
+                cs[i]->pair = 1;
+                cs[i]->stages = tc_stages_for(TC_BF16X3, *cs[i]);
+            }
+        }
+    }
     if (cls && (cls->n < 1 || cls->n > kMaxInlineProblems || (!cls->U1 && !cls->b1_ready) || !pack_u))
         return fail(h, DMRG_ERR_INVALID_ARG, "bad operator classes");
     const bool split = (p == DMRG_PREC_BF16X3);
@@ -245,7 +260,7 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     // atomics into outputs cleared first (so the summation order of those outputs may
     // differ between runs; DMRG_OPT_DETERMINISTIC turns the split off).
     {
-        const int slots = c2.pair ? grid2 / (2 * c2.pair) : grid2;
+        const int slots = c2.pair ? grid2 / 2 : grid2;
         const int bm = c2.pair ? 256 : 128;
         const int tiles = P2.m_tiles * P2.n_tiles;
         const int full_mt = (tiles / slots) * slots / P2.n_tiles;
@@ -269,16 +284,24 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
         }
     }
 
-    // ---- operand packing: O (stacked K*m x m), U_r' (rows b*d + s, cols j), U^T, and
-    //      the clearing of the split tail's outputs, in one launch (the two small U
-    //      gathers run alongside the bandwidth-bound O stream).
+    // ---- FP32 operators with 16-byte rows feed the first product as they are: the
+    //      CTA-pair kernel converts each tile in shared memory, so O is not packed.
+    const bool convert_a = !in_is_fp64 && (m % 4) == 0 &&
+                           (reinterpret_cast<uintptr_t>(O) & 15) == 0 && c1.pair &&
+                           c1.row_bytes == 128 && !h->pack_operators;
+
+    // ---- operand packing: O (stacked K*m x m) unless converted in the first product,
+    //      U_r' (rows b*d + s, cols j), U^T, and the clearing of the split tail's outputs,
+    //      in one launch (the two small U gathers run alongside the O stream).
     PackJob jobs[4] = {};
     int nj = 0;
-    PackJob& jo = jobs[nj++];
-    jo.src = O; jo.src_f64 = in_is_fp64; jo.mode = pmode;
-    jo.rows = K * m; jo.cols = m; jo.rows_per_op = K * m; jo.s_op = 0; jo.op_off = nullptr;
-    jo.rdiv = 1; jo.s_r_hi = m; jo.s_r_lo = 0; jo.s_c = 1;
-    jo.dst0 = Op[0]; jo.dst1 = Op[1]; jo.ld = D.ld1;
+    if (!convert_a) {
+        PackJob& jo = jobs[nj++];
+        jo.src = O; jo.src_f64 = in_is_fp64; jo.mode = pmode;
+        jo.rows = K * m; jo.cols = m; jo.rows_per_op = K * m; jo.s_op = 0; jo.op_off = nullptr;
+        jo.rdiv = 1; jo.s_r_hi = m; jo.s_r_lo = 0; jo.s_c = 1;
+        jo.dst0 = Op[0]; jo.dst1 = Op[1]; jo.ld = D.ld1;
+    }
     if (pack_u) {
         if (!(cls && cls->b1_ready)) {
             PackJob& j1 = jobs[nj++];
@@ -305,9 +328,11 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
         jz.rows = 1; jz.cols = (K - k_clear) * mp * mp; jz.rows_per_op = 1; jz.rdiv = 1;
         jz.dst0 = static_cast<float*>(Oout) + k_clear * mp * mp; jz.ld = jz.cols;
     }
-    cudaError_t e = timed_launch(h, "pack_operands", s,
-                                 [&] { return pack_launch(jobs, nj, nullptr, s); });
-    if (e != cudaSuccess) return cuda_fail(h, e, "pack");
+    cudaError_t e = cudaSuccess;
+    if (nj > 0) {
+        e = timed_launch(h, "pack_operands", s, [&] { return pack_launch(jobs, nj, nullptr, s); });
+        if (e != cudaSuccess) return cuda_fail(h, e, "pack");
+    }
 
     // ---- first product: T = O U_r, written straight into the second product's
     //      K-major operand layout: T_all[k*mp + b][i*d + s].
@@ -324,6 +349,12 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
         void* const* bsrc = cls ? cls->b1 : B1;
         TcOperand A{static_cast<char*>(Op[0]) + a_off, Op[1] ? static_cast<char*>(Op[1]) + a_off : nullptr,
                     kc * m, m, D.ld1};
+        if (convert_a) {
+            A.hi = static_cast<const float*>(O) + k0 * m * m;
+            A.lo = nullptr;
+            A.ld = m;
+            A.f32_source = 1;
+        }
         TcOperand B{static_cast<char*>(bsrc[0]) + b_off,
                     bsrc[1] ? static_cast<char*>(bsrc[1]) + b_off : nullptr, int64_t(d) * mp, m, D.ld1};
         if (!make_problem(P1, mode, A, B, c1.tile_n_max, 1, c1.row_bytes, c1.pair))
@@ -349,9 +380,10 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     L1.drop_arrival = take_drop_arrival(h);
     L1.row_bytes = c1.row_bytes;
     L1.chunk_scratch = L1.inline_prob[0].kb_chunk ? chain_scr : nullptr;
+    L1.convert_a = convert_a ? 1 : 0;
     e = timed_launch(h, "tc_gemm_first_product", s, [&] {
         const TcEpi epi = split ? EPI_SPLIT_BF16 : EPI_TF32;
-        return c1.pair ? tc_gemm_launch_pair(mode, epi, L1, c1.stages, grid1, s, c1.pair)
+        return c1.pair ? tc_gemm_launch_pair(mode, epi, L1, c1.stages, grid1, s)
                        : tc_gemm_launch(mode, epi, L1, c1.stages, grid1, s);
     });
     if (e != cudaSuccess) return cuda_fail(h, e, "first product");
@@ -360,7 +392,7 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     L2.timeout_ns = timeout_ns(h);
     L2.row_bytes = c2.row_bytes;
     e = timed_launch(h, "tc_gemm_second_product", s, [&] {
-        return c2.pair ? tc_gemm_launch_pair(mode, EPI_F32, L2, c2.stages, grid2, s, c2.pair)
+        return c2.pair ? tc_gemm_launch_pair(mode, EPI_F32, L2, c2.stages, grid2, s)
                        : tc_gemm_launch(mode, EPI_F32, L2, c2.stages, grid2, s);
     });
     if (e != cudaSuccess) return cuda_fail(h, e, "second product");
@@ -398,7 +430,6 @@ dmrg_status dense_fused_forward(dmrg_handle h, const double* U, int64_t m, int d
     a.K = K; a.m = m; a.mp = mp; a.ld = D.ld1; a.d = d;
     a.grid = h->num_sms;
     a.accum_chain = h->accum_chain;
-    a.cluster = h->fused_rotation > 0 ? h->fused_rotation : 1;
     a.status = h->d_status;
     a.timeout_ns = timeout_ns(h);
     e = timed_launch(h, "tc_fused_rotation", s, [&] { return fused_rotate_launch(a, s); });
@@ -565,7 +596,11 @@ dmrg_status dmrg_set_option(dmrg_handle h, dmrg_option o, double v) {
             h->deterministic = v != 0;
             return DMRG_OK;
         case DMRG_OPT_ACCUM_CHAIN:
-            if (v < 0 || v > 1e9) return fail(h, DMRG_ERR_INVALID_ARG, "accum_chain must be >= 0");
+            // Longer chains (or one chain per tile) let the tensor core's FP32 accumulation
+            // error of the BF16x3 products exceed 1e-5 at m*d = 4800 (2.05e-5 measured with
+            // one chain), so they are refused.
+            if (!(v >= 1 && v <= kMaxAccumChain))
+                return fail(h, DMRG_ERR_INVALID_ARG, "accum_chain must be in [1, 1024]");
             h->accum_chain = int(v);
             return DMRG_OK;
         case DMRG_OPT_TRUNCATION_JACOBI:
@@ -574,9 +609,12 @@ dmrg_status dmrg_set_option(dmrg_handle h, dmrg_option o, double v) {
         case DMRG_OPT_BLOCKED_SMALL:
             h->blocked_small = v != 0;
             return DMRG_OK;
+        case DMRG_OPT_PACK_OPERATORS:
+            h->pack_operators = v != 0;
+            return DMRG_OK;
         case DMRG_OPT_FUSED_ROTATION:
-            if (!(v == 0 || v == 1 || v == 2 || v == 4))
-                return fail(h, DMRG_ERR_INVALID_ARG, "fused_rotation must be 0, 1, 2 or 4");
+            if (!(v == 0 || v == 1))
+                return fail(h, DMRG_ERR_INVALID_ARG, "fused_rotation must be 0 or 1");
             h->fused_rotation = int(v);
             return DMRG_OK;
         case DMRG_OPT_TEST_WITHHOLD_ARRIVAL:

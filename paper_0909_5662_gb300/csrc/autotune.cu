@@ -4,8 +4,8 @@
 // with CUDA events on the caller's buffers, keeps the fastest per shape key in the
 // handle and, when $DMRG_AUTOTUNE_CACHE names a file, persists the choices there as
 // a small JSON object {"key": [tile_n_max, stages, grid, row_bytes, pair], ...} so
-// that later processes start tuned (pair = 1: the CTA-pair kernel; 2: clusters of two
-// pairs sharing A).
+// that later processes start tuned (pair = 0: the one-CTA kernel; 1: the CTA-pair
+// kernel).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,7 +46,7 @@ void load_tune_file(dmrg_handle h) {
         if (n == 3) c.row_bytes = 128;
         if (n <= 4) c.pair = 0;
         if (n >= 3 && c.tile_n_max >= 16 && c.tile_n_max <= 256 && c.stages >= 1 && c.stages <= 8 &&
-            c.grid >= 0 && (c.row_bytes == 64 || c.row_bytes == 128) && c.pair >= 0 && c.pair <= 2)
+            c.grid >= 0 && (c.row_bytes == 64 || c.row_bytes == 128) && c.pair >= 0 && c.pair <= 1)
             h->tune_cache[key] = c;
         pos = rb + 1;
     }
@@ -78,7 +78,7 @@ std::vector<TcConfig> candidates(TcMode mode, int64_t N, int num_sms) {
         const int t = choose_tile_n(N, tn);
         if (std::find(seen.begin(), seen.end(), t) != seen.end()) continue;
         seen.push_back(t);
-        for (int pair : {0, 1, 2}) {
+        for (int pair : {0, 1}) {
             for (int rb : {128, 64}) {
                 TcConfig c;
                 c.tile_n_max = t;

@@ -222,7 +222,7 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
         L.timeout_ns = timeout_ns(h);
         L.row_bytes = cfg.row_bytes;
         cudaError_t ee = timed_launch(h, name, s, [&] {
-            return cfg.pair ? tc_gemm_launch_pair(mode, epi, L, cfg.stages, grid, s, cfg.pair)
+            return cfg.pair ? tc_gemm_launch_pair(mode, epi, L, cfg.stages, grid, s)
                             : tc_gemm_launch(mode, epi, L, cfg.stages, grid, s);
         });
         return cuda_fail(h, ee, name);

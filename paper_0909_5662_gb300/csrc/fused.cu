@@ -20,11 +20,6 @@
 // Reductions longer than the accumulation chain are cut: at a chain end the epilogue
 // adds the accumulator into the output (stores the first chain), in a fixed order.
 //
-// Clusters of C = 2 or 4 CTAs work on C consecutive operators with the same output
-// block: the U tiles (the same for every operator) are loaded once per cluster, each
-// CTA fetching 1/C of the rows and multicasting them; every CTA's MMA issuer releases a
-// stage in all CTAs of the cluster, so a stage is refilled only when all have read it.
-//
 // Opt-in (DMRG_OPT_FUSED_ROTATION): at m = 400, d = 4 it is slower than the two products
 // for every m' it supports.  A unit re-streams O_k once per site state and the U panel
 // once per chunk, a 32 KB stage feeds only 400 cycles of MMAs, and the tensor pipe is
@@ -59,12 +54,12 @@ constexpr uint64_t kFDrainNs = 2000000000ull;
 
 struct FusedLaunch {
     CUtensorMap tmO[2];    // O hi/lo: (j, i, k), box 32 x 128
-    CUtensorMap tmUa[2];   // Pu hi/lo: (j, x, s), box 32 x slice_a (first product's A)
+    CUtensorMap tmUa[2];   // Pu hi/lo: (j, x, s), box 32 x 128 (first product's A)
     CUtensorMap tmUb[2];   // Pu hi/lo: (i, x, s), box 32 x slice_b (second product's B)
     float* out;            // K x m' x m' (row-major O'_k[alpha][beta])
     int K, m, d, mp, mpp, nb, chain_chunks;
-    int units;                 // (group of C operators, output block) pairs
-    int C, slice_a, slice_b;   // cluster size; rows of the U tiles each CTA fetches
+    int units;                 // (operator, output block) pairs
+    int slice_b;               // rows of the second product's U tile (m' rounded up to 16)
     unsigned* status;
     uint64_t timeout_ns;
 };
@@ -78,28 +73,6 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// Multicast form of the 3-D tiled load: the tile lands at the same offset in every CTA
-// of `mask`, its bytes counted on the barrier at bar's offset in each of them.
-__device__ __forceinline__ void tma_load_3d_mc(void* dst, const void* tmap, uint64_t* bar,
-                                               int32_t x, int32_t y, int32_t z, uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        ".multicast::cluster [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)),
-        "h"(mask)
-        : "memory");
-}
-
-// Arrive once on the mbarrier at bar's offset in every CTA of `mask` when the MMAs this
-// thread issued so far complete.
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;" ::"r"(smem_u32(bar)),
-        "h"(mask)
-        : "memory");
 }
 
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo_elem, __nv_bfloat16 hi_elem) {
@@ -130,7 +103,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fused_rotate_kernel(const __grid
     if (threadIdx.x == 0) {
         for (int s = 0; s < kFStages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], uint32_t(L.C));
+            mbar_init(&empty[s], 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tacc_full[a], 1);
@@ -148,7 +121,6 @@ __global__ void __launch_bounds__(kFThreads, 1) fused_rotate_kernel(const __grid
     if (warp == 1) tmem_alloc<512>(tmem_slot);
     tc_fence_before();
     __syncthreads();
-    if (L.C > 1) cluster_sync_all();   // every barrier of the cluster is initialised
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
     volatile int* vabort = abort_flag;
@@ -161,10 +133,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fused_rotate_kernel(const __grid
     auto rows_in = [&](int c) { return min(kIC, m - (c % nIC) * kIC); };
     auto nkb2 = [&](int c) { return (rows_in(c) + kKB - 1) / kKB; };
     const int cc = L.chain_chunks;
-    const int C = L.C;
-    const uint32_t crank = C > 1 ? cluster_ctarank() : 0u;
-    const uint16_t cmask = uint16_t((1u << C) - 1u);
-    const int cluster = int(blockIdx.x) / C, nclusters = int(gridDim.x) / C;
+    const int cta = int(blockIdx.x), ncta = int(gridDim.x);
     auto chain_first = [&](int c) { return c % cc == 0; };
     auto chain_last = [&](int c) { return c % cc == cc - 1 || c == nch - 1; };
 
@@ -181,7 +150,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fused_rotate_kernel(const __grid
             uint32_t armed = 0, armed_parity = 0;
             bool ok = true;
             const uint32_t bytes1 = 4 * kTile;
-            const uint32_t bytes2 = 2u * uint32_t(C * L.slice_b) * 64u;
+            const uint32_t bytes2 = 2u * uint32_t(L.slice_b) * 64u;
             auto acquire = [&](uint32_t bytes) -> bool {
                 if (!mbar_wait(&empty[stage], phase ^ 1u, tmo, L.status, vabort)) return false;
                 mbar_arrive_expect_tx(&full[stage], bytes);
@@ -195,24 +164,17 @@ __global__ void __launch_bounds__(kFThreads, 1) fused_rotate_kernel(const __grid
                     phase ^= 1u;
                 }
             };
-            for (int t = cluster; t < L.units && ok; t += nclusters) {
-                const int k = (t / L.nb) * C + int(crank), b = t % L.nb;
-                const uint32_t offa = crank * uint32_t(L.slice_a) * 64u;
-                const uint32_t offb = crank * uint32_t(L.slice_b) * 64u;
+            for (int t = cta; t < L.units && ok; t += ncta) {
+                const int k = t / L.nb, b = t % L.nb;
                 auto load1 = [&](int c) -> bool {
                     const int s = c / nIC, i0 = (c % nIC) * kIC;
                     for (int kb = 0; kb < nkb1; ++kb) {
                         if (!acquire(bytes1)) return false;
                         uint8_t* sl = ring + size_t(stage) * kSlotBytes;
                         const int x = kb * kKB;
-                        const int ya = b * 128 + int(crank) * L.slice_a;
-                        if (C == 1) {
-                            tma_load_3d(sl, &L.tmUa[0], &full[stage], x, ya, s);
-                            tma_load_3d(sl + kTile, &L.tmUa[1], &full[stage], x, ya, s);
-                        } else {
-                            tma_load_3d_mc(sl + offa, &L.tmUa[0], &full[stage], x, ya, s, cmask);
-                            tma_load_3d_mc(sl + kTile + offa, &L.tmUa[1], &full[stage], x, ya, s, cmask);
-                        }
+                        const int ya = b * 128;
+                        tma_load_3d(sl, &L.tmUa[0], &full[stage], x, ya, s);
+                        tma_load_3d(sl + kTile, &L.tmUa[1], &full[stage], x, ya, s);
                         tma_load_3d(sl + 2 * kTile, &L.tmO[0], &full[stage], x, i0, k);
                         tma_load_3d(sl + 3 * kTile, &L.tmO[1], &full[stage], x, i0, k);
                         advance();
@@ -225,14 +187,8 @@ __global__ void __launch_bounds__(kFThreads, 1) fused_rotate_kernel(const __grid
                         if (!acquire(bytes2)) return false;
                         uint8_t* sl = ring + size_t(stage) * kSlotBytes;
                         const int x = i0 + kb * kKB;
-                        const int yb = int(crank) * L.slice_b;
-                        if (C == 1) {
-                            tma_load_3d(sl, &L.tmUb[0], &full[stage], x, yb, s);
-                            tma_load_3d(sl + kB2Lo, &L.tmUb[1], &full[stage], x, yb, s);
-                        } else {
-                            tma_load_3d_mc(sl + offb, &L.tmUb[0], &full[stage], x, yb, s, cmask);
-                            tma_load_3d_mc(sl + kB2Lo + offb, &L.tmUb[1], &full[stage], x, yb, s, cmask);
-                        }
+                        tma_load_3d(sl, &L.tmUb[0], &full[stage], x, 0, s);
+                        tma_load_3d(sl + kB2Lo, &L.tmUb[1], &full[stage], x, 0, s);
                         advance();
                     }
                     return true;
@@ -253,12 +209,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fused_rotate_kernel(const __grid
             uint32_t g1 = 0, g2 = 0, gd = 0;   // T accumulations, T conversions used, drains
             bool ok = true;
             const uint32_t idesc2 = make_idesc(1u, uint32_t(L.mpp));
-            auto release = [&]() {
-                if (C == 1)
-                    mma_commit(&empty[stage]);
-                else
-                    mma_commit_mc(&empty[stage], cmask);
-            };
+            auto release = [&]() { mma_commit(&empty[stage]); };
             auto next = [&]() {
                 if (++stage == kFStages) {
                     stage = 0;
@@ -328,7 +279,7 @@ __global__ void __launch_bounds__(kFThreads, 1) fused_rotate_kernel(const __grid
                 }
                 return true;
             };
-            for (int t = cluster; t < L.units && ok; t += nclusters) {
+            for (int t = cta; t < L.units && ok; t += ncta) {
                 ok = mma1(0);
                 for (int c = 1; c < nch && ok; ++c) ok = mma1(c) && mma2(c - 1);
                 if (ok) ok = mma2(nch - 1);
@@ -391,14 +342,13 @@ __global__ void __launch_bounds__(kFThreads, 1) fused_rotate_kernel(const __grid
             if (!wait_warp(oacc_full, gd & 1u)) return false;
             tc_fence_after();
             const int beta = b * 128 + row;
-            const bool k_ok = k < L.K;   // the last cluster's spare CTAs compute zeros
             const bool first = (c / cc) == 0;
             float* outk = L.out + int64_t(k) * L.mp * L.mp;
             for (int a0 = 0; a0 < L.mpp; a0 += 32) {
                 uint32_t r[32];
                 tmem_ld_32x32b_x32(tmem_base + lane_off + uint32_t(a0), r);
                 tmem_ld_wait();
-                if (beta >= L.mp || !k_ok) continue;
+                if (beta >= L.mp) continue;
                 const int amax = min(32, L.mp - a0);
 #pragma unroll
                 for (int q = 0; q < 32; ++q) {
@@ -414,8 +364,8 @@ __global__ void __launch_bounds__(kFThreads, 1) fused_rotate_kernel(const __grid
             ++gd;
             return true;
         };
-        for (int t = cluster; t < L.units && ok; t += nclusters) {
-            const int k = (t / L.nb) * C + int(crank), b = t % L.nb;
+        for (int t = cta; t < L.units && ok; t += ncta) {
+            const int k = t / L.nb, b = t % L.nb;
             for (int c = 0; c < nch && ok; ++c) {
                 ok = convert(c);
                 if (ok && c >= 1 && chain_last(c - 1)) ok = drain_out(k, b, c - 1);
@@ -426,7 +376,6 @@ __global__ void __launch_bounds__(kFThreads, 1) fused_rotate_kernel(const __grid
 
     tc_fence_before();
     __syncthreads();
-    if (C > 1) cluster_sync_all();   // no peer still arrives on, or copies into, this CTA
     if (*vabort) {
         // After an expired wait, copies issued before it may still be landing here.
         const uint64_t t0 = globaltimer_ns();
@@ -447,19 +396,13 @@ size_t fused_smem_bytes() {
 cudaError_t fused_rotate_launch(const FusedArgs& a, cudaStream_t s) {
     if (a.K <= 0) return cudaSuccess;
     if (a.mp < 1 || a.mp > kFusedMaxMp || a.m < 1 || a.d < 1) return cudaErrorInvalidValue;
-    if (a.cluster != 1 && a.cluster != 2 && a.cluster != 4) return cudaErrorInvalidValue;
     FusedLaunch L{};
-    const int C = a.cluster;
     const int mpp = (int(a.mp) + 15) / 16 * 16;
-    // each CTA of a cluster fetches 1/C of a U tile's rows, a multiple of 8 rows (one
-    // swizzle period) so that every slice lands on a pattern boundary
-    L.C = C;
-    L.slice_a = 128 / C;
-    L.slice_b = ((mpp + 8 * C - 1) / (8 * C) * (8 * C)) / C;
+    L.slice_b = mpp;
     for (int i = 0; i < 2; ++i) {
         if (!encode_operand_map(&L.tmO[i], a.Op[i], false, a.m, a.m, a.ld, kIC, a.K,
                                 int64_t(a.m) * a.ld, 64) ||
-            !encode_operand_map(&L.tmUa[i], a.Pu[i], false, a.mp, a.m, a.ld, L.slice_a, a.d,
+            !encode_operand_map(&L.tmUa[i], a.Pu[i], false, a.mp, a.m, a.ld, 128, a.d,
                                 int64_t(a.mp) * a.ld, 64) ||
             !encode_operand_map(&L.tmUb[i], a.Pu[i], false, a.mp, a.m, a.ld, L.slice_b, a.d,
                                 int64_t(a.mp) * a.ld, 64))
@@ -472,7 +415,7 @@ cudaError_t fused_rotate_launch(const FusedArgs& a, cudaStream_t s) {
     L.mp = int(a.mp);
     L.mpp = mpp;
     L.nb = (int(a.mp) + 127) / 128;
-    const int64_t units = (a.K + C - 1) / C * L.nb;   // (group of C operators, block)
+    const int64_t units = a.K * L.nb;   // (operator, output block)
     if (units > 0x7fffffffLL) return cudaErrorInvalidValue;
     L.units = int(units);
     const int nIC = (L.m + kIC - 1) / kIC;
@@ -486,31 +429,17 @@ cudaError_t fused_rotate_launch(const FusedArgs& a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(fused_rotate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(smem));
     if (e != cudaSuccess) return e;
-    int clusters = std::max(1, std::min(a.grid / C, L.units));
+    const int ctas = std::max(1, std::min(a.grid, L.units));
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(unsigned(clusters * C), 1, 1);
+    cfg.gridDim = dim3(unsigned(ctas), 1, 1);
     cfg.blockDim = dim3(kFThreads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[2];
+    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
-    attr[1].id = cudaLaunchAttributeClusterDimension;
-    attr[1].val.clusterDim.x = unsigned(C);
-    attr[1].val.clusterDim.y = 1;
-    attr[1].val.clusterDim.z = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = C > 1 ? 2 : 1;
-    if (C > 1) {
-        // a persistent grid larger than the clusters resident at once would only queue
-        int fit = 0;
-        if (cudaOccupancyMaxActiveClusters(&fit, fused_rotate_kernel, &cfg) != cudaSuccess) {
-            cudaGetLastError();
-            fit = 0;
-        }
-        if (fit > 0 && fit < clusters) clusters = fit;
-        cfg.gridDim = dim3(unsigned(clusters * C), 1, 1);
-    }
+    cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, fused_rotate_kernel, L);
 }
 

@@ -103,8 +103,7 @@ struct TcConfig {
     int stages = 3;
     int grid = 0;           // 0 = number of SMs
     int row_bytes = 128;    // 128: 128-byte swizzle; 64: 64-byte swizzle, half-depth k-blocks
-    int pair = 0;           // 1: CTA-pair kernel (256-row tiles on two SMs, cta_group::2);
-                            // 2: clusters of two pairs on neighbouring N tiles sharing A
+    int pair = 0;           // 1: CTA-pair kernel (256-row tiles on two SMs, cta_group::2)
     bool operator==(const TcConfig& o) const {
         return tile_n_max == o.tile_n_max && stages == o.stages && grid == o.grid &&
                row_bytes == o.row_bytes && pair == o.pair;
@@ -118,6 +117,8 @@ constexpr int kChainScratchCtas = 160;
 constexpr size_t kChainScratchBytes = size_t(kChainScratchCtas) * 128 * 256 * 4;
 // Reductions up to this length always run as one chain (no scratch is reserved for them).
 constexpr int64_t kChainMinRed = 512;
+// Longest accumulation chain the BF16x3 products accept (DMRG_OPT_ACCUM_CHAIN).
+constexpr int kMaxAccumChain = 1024;
 
 struct TcLaunch {
     TcProblem inline_prob[kMaxInlineProblems];  // used when table == nullptr
@@ -132,6 +133,8 @@ struct TcLaunch {
     int32_t row_bytes;      // 128 or 64: must match the problems' tensor maps
     float* chunk_scratch;   // CTA-pair kernel with kb_chunk: gridDim.x x 128 x 256 FP32 running
                             // sums (nullptr: every tile is one accumulation chain)
+    int32_t convert_a;      // CTA-pair kernel: every problem's A map is an FP32 source that
+                            // the converter warps turn into the MMA operand (f32_source)
 };
 
 // One operand seen by the kernel: `nbatch` slices of rows x cols (cols = the
@@ -142,15 +145,19 @@ struct TcOperand {
     int64_t rows, cols, ld;
     int64_t nbatch = 1;
     int64_t batch_stride = 0;
+    // A operand of the CTA-pair kernel only: `hi` is an unconverted FP32 matrix (row
+    // stride ld floats, a multiple of 4, 16-byte aligned) that the kernel's converter
+    // warps split into BF16 hi/lo (BF16X3) or round to TF32 in shared memory.
+    int32_t f32_source = 0;
 };
 
 cudaError_t tc_gemm_launch(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
                            cudaStream_t s);
 int tc_max_stages(TcMode mode, int tile_n_max, int row_bytes = 128);
-// CTA-pair form: problems made with make_problem(..., pairs_per_cluster); `grid` counts
-// CTAs (rounded down to whole clusters, capped by the clusters that fit at once).
+// CTA-pair form: problems made with make_problem(..., pair_form = 1); `grid` counts
+// CTAs (rounded down to whole pairs, capped by the pairs that fit at once).
 cudaError_t tc_gemm_launch_pair(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
-                                cudaStream_t s, int pairs_per_cluster);
+                                cudaStream_t s);
 int tc_pair_max_stages(TcMode mode, int tile_n_max, int row_bytes = 128);
 // Dispatch on cfg.pair.
 inline int tc_stages_for(TcMode mode, const TcConfig& c) {
@@ -165,10 +172,9 @@ bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t r
 // Chooses an N tile (multiple of 16, <= tile_n_max) that splits N evenly.
 int choose_tile_n(int64_t N, int tile_n_max);
 // Fills operand maps and tiling fields of a problem: D (M x N) += A B^T over Kred x nbatch.
-// pairs_per_cluster: 0 for the one-CTA kernel, 1 or 2 for the CTA-pair kernel (with 2,
-// n_tiles counts tiles of the cluster: two neighbouring N tiles).
+// pair_form: 0 for the one-CTA kernel, 1 for the CTA-pair kernel (other values fail).
 bool make_problem(TcProblem& p, TcMode mode, const TcOperand& A, const TcOperand& B,
-                  int tile_n_max, int k_splits, int row_bytes = 128, int pairs_per_cluster = 0);
+                  int tile_n_max, int k_splits, int row_bytes = 128, int pair_form = 0);
 // Scatter for a plain row-major (rows x cols, leading dimension ld) destination.
 TcScatter scatter_rowmajor(int64_t ld);
 
@@ -223,7 +229,6 @@ struct FusedArgs {
     float* out;          // K x mp x mp
     int64_t K, m, mp, ld;
     int d, grid, accum_chain;
-    int cluster;         // CTAs sharing the U tiles: 1, 2 or 4
     unsigned* status;
     uint64_t timeout_ns;
 };
@@ -250,8 +255,11 @@ struct dmrg_handle_s {
     bool deterministic = false;     // no atomically accumulated split tiles
     bool trunc_jacobi = false;      // truncation: cyclic Jacobi instead of the tridiagonal solver
     bool blocked_small = true;      // plans with sectors <= 32 states: fused small-sector kernel
-    int fused_rotation = 0;         // dense BF16x3, mp <= 256: both products in one kernel,
-                                    // in clusters of this many CTAs (0 = off)
+    bool pack_operators = true;     // dense tensor-core products: pack FP32 operators in a
+                                    // separate pass instead of converting them in the first
+                                    // product's shared memory
+    int fused_rotation = 0;         // dense BF16x3, mp <= 256: both products in one kernel
+                                    // (0 = off)
     int accum_chain = 1024;         // BF16x3 dense products: reduction elements per accumulator
                                     // chain (0 = one chain per tile)
 

@@ -792,28 +792,36 @@ int choose_tile_n(int64_t N, int tile_n_max) {
 }
 
 bool make_problem(TcProblem& p, TcMode mode, const TcOperand& A, const TcOperand& B,
-                  int tile_n_max, int k_splits, int row_bytes, int pairs_per_cluster) {
+                  int tile_n_max, int k_splits, int row_bytes, int pair_form) {
     const bool f32 = (mode == TC_TF32);
     const bool split = (mode == TC_BF16X3);
     if (row_bytes != 64) row_bytes = 128;
     const int elems = row_bytes / (f32 ? 4 : 2);
     if (A.cols != B.cols || A.nbatch != B.nbatch) return false;
-    // CTA pairs: 256-row M tiles, each CTA stages half of the N tile (at least 16 rows);
-    // with two pairs per cluster each CTA loads half of its A rows (multicast)
-    const bool pair = pairs_per_cluster > 0;
+    // CTA pairs: 256-row M tiles, each CTA stages half of the N tile (at least 16 rows)
+    if (pair_form != 0 && pair_form != 1) return false;
+    const bool pair = pair_form == 1;
     const int tile_n = pair ? std::max(32, choose_tile_n(B.rows, tile_n_max)) : choose_tile_n(B.rows, tile_n_max);
     const int b_box = pair ? tile_n / 2 : tile_n;
-    const int a_box = pairs_per_cluster == 2 ? kBM / 2 : kBM;
+    const int a_box = kBM;
     const int bm = pair ? 2 * kBM : kBM;
+    // An FP32 source for A (CTA pairs, 128-byte rows): boxes of 32 floats x 128 rows
+    // that the converter warps turn into the operand in place.
+    if (A.f32_source && (!pair || row_bytes != 128 || (A.ld & 3) != 0 ||
+                         (reinterpret_cast<uintptr_t>(A.hi) & 15) != 0))
+        return false;
     for (int i = 0; i < (split ? 2 : 1); ++i) {
         const void* a = i ? A.lo : A.hi;
         const void* b = i ? B.lo : B.hi;
-        if (!encode_operand_map(&p.tmA[i], a, f32, A.rows, A.cols, A.ld, a_box, A.nbatch, A.batch_stride,
-                                row_bytes) ||
-            !encode_operand_map(&p.tmB[i], b, f32, B.rows, B.cols, B.ld, b_box, B.nbatch,
+        if (!(A.f32_source && i == 1) &&
+            !encode_operand_map(&p.tmA[i], a, f32 || A.f32_source, A.rows, A.cols, A.ld, a_box,
+                                A.nbatch, A.batch_stride, row_bytes))
+            return false;
+        if (!encode_operand_map(&p.tmB[i], b, f32, B.rows, B.cols, B.ld, b_box, B.nbatch,
                                 B.batch_stride, row_bytes))
             return false;
     }
+    if (A.f32_source) p.tmA[1] = p.tmA[0];
     if (!split) {
         p.tmA[1] = p.tmA[0];
         p.tmB[1] = p.tmB[0];
@@ -825,7 +833,6 @@ bool make_problem(TcProblem& p, TcMode mode, const TcOperand& A, const TcOperand
     p.tile_n = tile_n;
     p.m_tiles = int32_t((A.rows + bm - 1) / bm);
     p.n_tiles = int32_t((B.rows + tile_n - 1) / tile_n);
-    if (pairs_per_cluster == 2) p.n_tiles = (p.n_tiles + 1) / 2;
     const int kb_total = int((A.cols + elems - 1) / elems) * int(A.nbatch);
     if (k_splits < 1) k_splits = 1;
     if (k_splits > kb_total) k_splits = kb_total;

@@ -7,22 +7,32 @@
 // CTA's 128 rows in that CTA's TMEM.  Per SM this halves the shared-memory and L2
 // traffic of the B operand, which bounds the one-CTA kernel.
 //
-// With NP = 2 a cluster holds two pairs working on neighbouring N tiles of the
-// same M tile.  They need the same rows of A, so each CTA loads half of its
-// 128 rows and the TMA multicasts them to the CTA of the same rank in the other
-// pair: the L2-to-SM operand traffic drops by another quarter.
+// Every TMA load lands in the shared memory of the CTA that issues it; only the
+// completion (the mbarrier's transaction count) is signalled in the leader.
 //
 // Protocol (every wait bounded, as in the one-CTA kernel):
 //   * all TMA loads landing in a pair complete on its leader's full[s] barrier
 //     (the leader arms it with the bytes of both CTAs);
-//   * every leader's commit multicasts to empty[s] of all CTAs of the cluster
-//     (empty[s] expects one arrival per pair: a stage is refilled only when every
-//     pair that reads it is done), and to the accumulator-full barrier of both
-//     CTAs of its own pair;
+//   * the leader's commits arrive on empty[s] of both CTAs of the pair (a stage
+//     is refilled only when the MMAs that read it are done), and on the
+//     accumulator-full barrier of both CTAs;
 //   * the epilogue warps of both CTAs arrive on their leader's accumulator-empty
 //     barrier (the peer through its shared::cluster address);
 //   * cluster barriers after set-up and before teardown keep any CTA from leaving
 //     while another may still reach its barriers, its shared memory or TMEM.
+//
+// Converting form (CONV): the A operand arrives as an unconverted FP32 matrix (the
+// operators O as the caller stores them).  Each CTA's A tile lands, 128-byte
+// swizzled, on that CTA's own afull[s] barrier; four converter warps then turn it
+// into the MMA operand in place, one row per lane: BF16X3 reads the 64 floats of
+// its row from the two 32-float boxes and writes the row's BF16 hi part over the
+// first box and the lo part over the second (the layout the MMA reads); TF32 rounds
+// the 32 floats of its row to TF32 where they are.  A lane touches only its own
+// row, so no other lane's data is overwritten before it is read.  Each converter
+// warp then makes its writes visible to the tensor core (proxy fence) and arrives on
+// the leader's full[s], which in this form counts the B bytes of both CTAs and eight
+// converter arrivals.  This replaces a separate packing pass over O in global
+// memory (a read and a write of the whole operator batch).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -42,6 +52,8 @@ namespace {
 using namespace tcdev;
 
 constexpr int kThreads = 320;         // producer, MMA issuer, 8 epilogue warps (per CTA)
+constexpr int kThreadsConv = 448;     // ... and 4 converter warps (converting form)
+constexpr int kConvWarp0 = 10;
 constexpr int kEpiWarps = 8;
 constexpr int kBM = 128;              // rows per CTA (TMEM lanes)
 constexpr uint32_t kTmemCols = 512;
@@ -55,8 +67,71 @@ __device__ __forceinline__ int pair_n(int tile_n, int left) {
     return max(32, (n + 15) & ~15);
 }
 
-template <int MODE, int EPI, int RB, int NP>
-__global__ void __launch_bounds__(kThreads, 1)
+__device__ __forceinline__ void ld_shared_v4(uint32_t addr, float4& v) {
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_shared_v4u(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
+                                              uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
+                 "r"(d)
+                 : "memory");
+}
+
+// BF16 hi/lo of two floats as packed pairs: hi = bf16(x), lo = bf16(x - hi).
+__device__ __forceinline__ void split2(float x, float y, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(x - hf.x, y - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// Converts row `row` of this CTA's A tile in place (see the converting form above).
+// box0 / box1: shared addresses of the two 128 x 128-byte regions of the stage's A.
+template <int MODE>
+__device__ __forceinline__ void convert_a_row(uint32_t box0, uint32_t box1, int row) {
+    const uint32_t r0 = box0 + uint32_t(row) * 128u;
+    const uint32_t sw = uint32_t(row & 7);
+    if (MODE == TC_BF16X3) {
+        const uint32_t r1 = box1 + uint32_t(row) * 128u;
+        float4 v[16];   // v[c] = floats 4c .. 4c+3 of the row
+#pragma unroll
+        for (int c = 0; c < 8; ++c) ld_shared_v4(r0 + ((uint32_t(c) ^ sw) << 4), v[c]);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) ld_shared_v4(r1 + ((uint32_t(c) ^ sw) << 4), v[8 + c]);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {   // 16-byte chunk q: elements 8q .. 8q+7
+            uint32_t h[4], l[4];
+            split2(v[2 * q].x, v[2 * q].y, h[0], l[0]);
+            split2(v[2 * q].z, v[2 * q].w, h[1], l[1]);
+            split2(v[2 * q + 1].x, v[2 * q + 1].y, h[2], l[2]);
+            split2(v[2 * q + 1].z, v[2 * q + 1].w, h[3], l[3]);
+            const uint32_t off = (uint32_t(q) ^ sw) << 4;
+            st_shared_v4u(r0 + off, h[0], h[1], h[2], h[3]);
+            st_shared_v4u(r1 + off, l[0], l[1], l[2], l[3]);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const uint32_t a = r0 + (uint32_t(c) << 4);   // same place in or out of the swizzle
+            float4 v;
+            ld_shared_v4(a, v);
+            st_shared_v4u(a, __float_as_uint(tf32_round(v.x)), __float_as_uint(tf32_round(v.y)),
+                          __float_as_uint(tf32_round(v.z)), __float_as_uint(tf32_round(v.w)));
+        }
+    }
+}
+
+__device__ __forceinline__ void fence_proxy_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <int MODE, int EPI, int RB, bool CONV>
+__global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
     tc_gemm_pair_kernel(const __grid_constant__ TcLaunch L, int stages, int bh_smem) {
     constexpr int kRowBytes = RB;
     constexpr bool kSplit = (MODE == TC_BF16X3);
@@ -77,31 +152,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* tfull = empty + stages;
     uint64_t* tempty = tfull + 2;
     uint64_t* drain = tempty + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    uint64_t* afull = drain + 1;   // converting form: this CTA's A tile landed ([stages])
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(afull + stages);
     int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
     int* zero_flag = abort_flag + 1;
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const uint32_t crank = cluster_ctarank();  // 0 .. 2*NP-1
-    const uint32_t rank = crank & 1u;           // within the pair
-    const int pq = int(crank >> 1);             // pair within the cluster
-    const uint32_t lead = crank & ~1u;          // cluster rank of this pair's leader
+    const uint32_t rank = cluster_ctarank();   // 0: leader, 1: its peer
+    constexpr uint32_t lead = 0;                // cluster rank of the leader
     const bool leader = (rank == 0);
-    const int pair = blockIdx.x / (2 * NP);     // cluster index (tile schedule)
-    const int npairs = gridDim.x / (2 * NP);
-    constexpr uint16_t kAllCtas = (1u << (2 * NP)) - 1u;
-    const uint16_t pair_mask = uint16_t(3u << lead);
-    // A rows: this CTA loads kBM / NP of them and multicasts them to the CTA of the
-    // same rank in every pair of the cluster
-    constexpr int kARows = kBM / NP;
-    uint16_t a_mask = 0;
-    for (int q = 0; q < NP; ++q) a_mask |= uint16_t(1u << (2 * q + int(rank)));
+    const int pair = blockIdx.x / 2;            // cluster index (tile schedule)
+    const int npairs = gridDim.x / 2;
+    constexpr uint16_t pair_mask = 3u;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], NP);
+            // converting form: the leader's arming plus one arrival per converter warp of
+            // both CTAs
+            mbar_init(&full[s], CONV ? 1 + 2 * 4 : 1);
+            mbar_init(&empty[s], 1);
+            if (CONV) mbar_init(&afull[s], 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
@@ -151,13 +222,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int t = pair; t < L.total_tiles && ok; t += npairs) {
                 const Decoded dt = decode_tile(L, t, kElemsPerRow);
                 const TcProblem* P = dt.P;
-                // both CTAs' bytes: A (128 rows each) and the B halves (tile_n / 2 rows each)
+                // both CTAs' bytes: A (128 rows each; counted on afull in the converting
+                // form) and the B halves (tile_n / 2 rows each)
                 const uint32_t bytes =
-                    2u * (a_bytes + uint32_t(P->tile_n / 2) * kRowBytes) * (kSplit ? 2u : 1u);
-                const int nt = NP * dt.nt + pq;
-                const int n_eff = pair_n(P->tile_n, P->N - nt * P->tile_n);
-                const int ya = dt.mt * (2 * kBM) + int(rank) * kBM + pq * kARows;
-                const int yb = nt * P->tile_n + int(rank) * (n_eff / 2);
+                    2u * ((CONV ? 0u : a_bytes) + uint32_t(P->tile_n / 2) * kRowBytes) *
+                    (kSplit ? 2u : 1u);
+                // converting form: this CTA's FP32 A tile, 128 rows x 32 floats per box
+                const uint32_t a_tx = kSplit ? 2u * a_bytes : a_bytes;
+                const int n_eff = pair_n(P->tile_n, P->N - dt.nt * P->tile_n);
+                const int ya = dt.mt * (2 * kBM) + int(rank) * kBM;
+                const int yb = dt.nt * P->tile_n + int(rank) * (n_eff / 2);
                 for (int kb = dt.kb_begin; kb < dt.kb_end; ++kb) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, tmo, L.status, vabort)) {
                         ok = false;
@@ -167,13 +241,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t fb = mapa_shared(smem_u32(&full[stage]), lead);
                     const int z = kb / dt.kb_per_batch;
                     const int x = (kb - z * dt.kb_per_batch) * kElemsPerRow;
-                    const uint32_t a_off = uint32_t(pq * kARows * kRowBytes);
+                    if (CONV) {
+                        mbar_arrive_expect_tx(&afull[stage], a_tx);
+                        tma_load_3d(stage_a(stage, 0), &P->tmA[0], &afull[stage], x, ya, z);
+                        if (kSplit)
+                            tma_load_3d(stage_a(stage, 1), &P->tmA[0], &afull[stage], x + 32, ya, z);
+                    }
                     for (int h = 0; h < (kSplit ? 2 : 1); ++h) {
-                        if (NP == 1)
-                            tma_load_3d_pair(stage_a(stage, h), &P->tmA[h], fb, x, ya, z);
-                        else
-                            tma_load_3d_pair_mc(stage_a(stage, h) + a_off, &P->tmA[h], fb, x, ya, z,
-                                                a_mask);
+                        if (!CONV) tma_load_3d_pair(stage_a(stage, h), &P->tmA[h], fb, x, ya, z);
                         tma_load_3d_pair(stage_b(stage, h), &P->tmB[h], fb, x, yb, z);
                     }
                     armed |= 1u << stage;
@@ -194,6 +269,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (armed & (1u << s))
                         mbar_wait(&full[s], (armed_parity >> s) & 1u, kDrainTimeoutNs, L.status,
                                   zero_flag);
+            if (CONV)   // this CTA's own A copies
+                for (int s = 0; s < stages; ++s)
+                    if (armed & (1u << s))
+                        mbar_wait(&afull[s], (armed_parity >> s) & 1u, kDrainTimeoutNs, L.status,
+                                  zero_flag);
             if (ok)
                 for (int s = 0; s < stages; ++s)
                     if (armed & (1u << s))
@@ -209,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int t = pair; t < L.total_tiles && ok; t += npairs) {
                 const Decoded dt = decode_tile(L, t, kElemsPerRow);
                 const TcProblem* P = dt.P;
-                const int n_eff = pair_n(P->tile_n, P->N - (NP * dt.nt + pq) * P->tile_n);
+                const int n_eff = pair_n(P->tile_n, P->N - dt.nt * P->tile_n);
                 const uint32_t idesc = make_idesc_pair(kFmt, uint32_t(n_eff));
                 const int chunk = (P->kb_chunk > 0 && L.chunk_scratch) ? P->kb_chunk
                                                                         : (dt.kb_end - dt.kb_begin);
@@ -225,7 +305,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_after();
                     const uint32_t tmem_d = tmem_base + uint32_t(acc) * kAccStride;
                     for (int kb = kb0; kb < kb1; ++kb) {
-                        if (!mbar_wait(&full[stage], phase, tmo, L.status, vabort)) {
+                        if (!(CONV ? mbar_wait_cluster(&full[stage], phase, tmo, L.status, vabort)
+                                   : mbar_wait(&full[stage], phase, tmo, L.status, vabort))) {
                             ok = false;
                             break;
                         }
@@ -252,7 +333,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         // Test hook: withhold one release so that both producers' bounded
                         // waits on this stage expire (a barrier that nothing arrives on).
                         const bool withhold = L.drop_arrival && pair == 0 && it == 0 && kb == kb0;
-                        if (!withhold) mma_commit_pair(&empty[stage], kAllCtas);
+                        if (!withhold) mma_commit_pair(&empty[stage], pair_mask);
                         if (++stage == stages) {
                             stage = 0;
                             phase ^= 1u;
@@ -266,6 +347,39 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             mma_commit_pair(drain, uint16_t(1u << lead));
             mbar_wait(drain, 0, kDrainTimeoutNs, L.status, zero_flag);
+        }
+    } else if (CONV && warp >= kConvWarp0) {
+        // ------------------------------------------------------------ A converters (both CTAs)
+        const int row = (warp - kConvWarp0) * 32 + lane;
+        const uint32_t full0_lead = mapa_shared(smem_u32(&full[0]), lead);
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        for (int t = pair; t < L.total_tiles && ok; t += npairs) {
+            const Decoded dt = decode_tile(L, t, kElemsPerRow);
+            for (int kb = dt.kb_begin; kb < dt.kb_end; ++kb) {
+                int got = 1;
+                if (lane == 0) got = mbar_wait(&afull[stage], phase, tmo, L.status, vabort) ? 1 : 0;
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    ok = false;
+                    break;
+                }
+                // the phase has completed: every lane's own (immediately successful) wait
+                // orders the tile's bytes before its reads
+                mbar_try_wait(&afull[stage], phase);
+                convert_a_row<MODE>(smem_u32(stage_a(stage, 0)), smem_u32(stage_a(stage, 1)), row);
+                fence_proxy_async_shared();
+                __syncwarp();
+                if (lane == 0) {
+                    if (leader) mbar_arrive(&full[stage]);
+                    else mbar_arrive_cluster(full0_lead + uint32_t(stage) * 8u);
+                }
+                if (++stage == stages) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
         }
     } else {
         // ------------------------------------------------------------ epilogue (both CTAs)
@@ -288,8 +402,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const TcProblem* P = dt.P;
             const int row = dt.mt * (2 * kBM) + int(rank) * kBM + quad * 32 + lane;
             const bool row_ok = row < P->M && dt.kb_begin < dt.kb_end;
-            const int n0 = (NP * dt.nt + pq) * P->tile_n;
-            const int ncols = min(P->tile_n, P->N - n0);  // <= 0: a padding tile of the cluster
+            const int n0 = dt.nt * P->tile_n;
+            const int ncols = min(P->tile_n, P->N - n0);
             const TcScatter& S = P->sc[0];
             int64_t row_base = 0;
             if (row_ok) {
@@ -397,21 +511,22 @@ int clusters_that_fit(const void* kernel, const cudaLaunchConfig_t& cfg) {
     return fit;
 }
 
-template <int MODE, int EPI, int NP>
+template <int MODE, int EPI>
 cudaError_t launch_pair(const TcLaunch& L, int stages, int grid, int bh_smem, size_t smem,
                         cudaStream_t s) {
-    auto k = L.row_bytes == 64 ? tc_gemm_pair_kernel<MODE, EPI, 64, NP>
-                               : tc_gemm_pair_kernel<MODE, EPI, 128, NP>;
+    auto k = L.convert_a ? tc_gemm_pair_kernel<MODE, EPI, 128, true>
+             : L.row_bytes == 64 ? tc_gemm_pair_kernel<MODE, EPI, 64, false>
+                                 : tc_gemm_pair_kernel<MODE, EPI, 128, false>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(grid), 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.blockDim = dim3(L.convert_a ? kThreadsConv : kThreads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2 * NP;
+    attr[0].val.clusterDim.x = 2;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -420,14 +535,14 @@ cudaError_t launch_pair(const TcLaunch& L, int stages, int grid, int bh_smem, si
     cfg.numAttrs = 2;
     // A persistent grid larger than the clusters that fit at once would only queue.
     const int fit = clusters_that_fit(reinterpret_cast<const void*>(k), cfg);
-    if (fit > 0 && 2 * NP * fit < grid) cfg.gridDim.x = unsigned(2 * NP * fit);
+    if (fit > 0 && 2 * fit < grid) cfg.gridDim.x = unsigned(2 * fit);
     return cudaLaunchKernelEx(&cfg, k, L, stages, bh_smem);
 }
 
 size_t pair_smem_bytes(TcMode mode, int stages, int bh, int rb) {
     const size_t a = size_t(kBM) * rb, b = size_t(bh) * rb;
     const size_t stage = (a + b) * (mode == TC_BF16X3 ? 2 : 1);
-    return 1024 + stage * stages + 8 * (2 * size_t(stages) + 5) + 32;
+    return 1024 + stage * stages + 8 * (3 * size_t(stages) + 5) + 32;
 }
 
 }  // namespace
@@ -439,21 +554,18 @@ int tc_pair_max_stages(TcMode mode, int tile_n_max, int row_bytes) {
 }
 
 cudaError_t tc_gemm_launch_pair(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
-                                cudaStream_t s, int pairs_per_cluster) {
+                                cudaStream_t s) {
     if (L.total_tiles <= 0) return cudaSuccess;
     if (L.table != nullptr || L.nprob < 1 || L.nprob > kMaxInlineProblems) return cudaErrorInvalidValue;
-    if (pairs_per_cluster != 1 && pairs_per_cluster != 2) return cudaErrorInvalidValue;
+    if (L.convert_a && (L.row_bytes != 128 || mode == TC_BF16)) return cudaErrorInvalidValue;
     int bn = 32;
     for (int i = 0; i < L.nprob; ++i) bn = std::max(bn, L.inline_prob[i].tile_n);
     const int bh = bn / 2;
     const size_t smem = pair_smem_bytes(mode, stages, bh, L.row_bytes);
     if (smem > 232448) return cudaErrorInvalidConfiguration;
-    const int csize = 2 * pairs_per_cluster;
-    grid = std::max(csize, std::min(grid, csize * L.total_tiles)) / csize * csize;
-#define DMRG_TC_CASE(M, E)                                                          \
-    if (mode == M && epi == E)                                                      \
-        return pairs_per_cluster == 2 ? launch_pair<M, E, 2>(L, stages, grid, bh, smem, s) \
-                                      : launch_pair<M, E, 1>(L, stages, grid, bh, smem, s);
+    grid = std::max(2, std::min(grid, 2 * L.total_tiles)) / 2 * 2;
+#define DMRG_TC_CASE(M, E) \
+    if (mode == M && epi == E) return launch_pair<M, E>(L, stages, grid, bh, smem, s);
     DMRG_TC_CASE(TC_BF16X3, EPI_SPLIT_BF16)
     DMRG_TC_CASE(TC_BF16X3, EPI_F32)
     DMRG_TC_CASE(TC_BF16X3, EPI_F32_ATOMIC)

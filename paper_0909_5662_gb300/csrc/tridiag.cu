@@ -268,9 +268,13 @@ __global__ void tri_stats_kernel(const double* __restrict__ d, const double* __r
     }
 }
 
-// 1/q: the hardware's approximate reciprocal refined by two Newton steps
-// r <- r + r (1 - q r), each of which doubles the correct bits (|q| >= pivmin keeps q
-// normal, so the flush-to-zero form is exact here).
+// 1/q by Newton-Raphson iteration for the reciprocal: the hardware's approximate
+// reciprocal refined by two Newton steps r <- r + r (1 - q r), each of which doubles
+// the correct bits (|q| >= pivmin keeps q normal, so the flush-to-zero form is exact
+// here; for |q| > 1/DBL_MIN the result flushes to zero, which leaves a Sturm count
+// unchanged because the term e2 / q it scales is then below the rounding of d - x).
+// dmrg_debug_reciprocal exposes it so that a test can bound its error in ulps
+// against correctly rounded division.
 __device__ __forceinline__ double recip(double q) {
     double r;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(q));
@@ -696,7 +700,22 @@ cudaError_t coop_grid(const void* kernel, size_t smem, int cap, int* grid, int p
     return cudaSuccess;
 }
 
+__global__ void recip_kernel(const double* __restrict__ q, double* __restrict__ out, int64_t n) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = recip(q[i]);
+}
+
 }  // namespace
+
+extern "C" DMRG_API dmrg_status dmrg_debug_reciprocal(const double* q, double* out, int64_t n,
+                                                      dmrg_stream_t stream) {
+    if (n < 0 || (n > 0 && (!q || !out))) return DMRG_ERR_INVALID_ARG;
+    if (n == 0) return DMRG_OK;
+    const int64_t blocks = (n + 255) / 256;
+    if (blocks > 0x7fffffffLL) return DMRG_ERR_SHAPE;
+    recip_kernel<<<unsigned(blocks), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(q, out, n);
+    return cudaGetLastError() == cudaSuccess ? DMRG_OK : DMRG_ERR_CUDA;
+}
 
 namespace dmrg {
 

@@ -74,8 +74,8 @@ def test_ragged_shapes(lib, shape, prec):
 
 @pytest.mark.parametrize("m", [77, 96])
 def test_fp32_input_for_tensor_core_paths(lib, m):
-    # FP32 operators: packed (m = 77), or read in place by the TF32 first product when
-    # their rows are 16-byte aligned (m = 96)
+    # FP32 operators with rows that are not (m = 77) and are (m = 96) 16-byte aligned;
+    # both go through the rounding (TF32) or splitting (BF16x3) of the operands
     w = dense_workload("t", 77, 3, m, 80, 6)
     ref = oracle.rotate_dense(w.U, w.O.astype(np.float32).astype(np.float64), 3)
     for prec in ("bf16x3", "tf32"):
@@ -152,6 +152,29 @@ def test_correlations_gpu(lib):
     got32 = lib.dmrg_correlations(torch.from_numpy(Op).cuda().float(), torch.from_numpy(psi).cuda()).cpu().numpy()
     ref32 = oracle.correlations(Op.astype(np.float32).astype(np.float64), psi)
     assert np.abs(got32 - ref32).max() <= 1e-12 * np.abs(ref32).max()
+
+
+def test_correlations_gpu_chained_sweep_size(lib):
+    # K = 300 operators of m' = 1200 (the chained-sweep workload's last step), FP32 and
+    # FP64 operators holding the same values.  Every C_ij needs only O'_i and O'_j, so
+    # the oracle recomputes the block of a seeded sample of operators (first and last
+    # included) and the GPU's full K x K matrix is compared on that block.
+    rng = np.random.default_rng(2300)
+    K, mp = 300, 1200
+    Op32 = rng.standard_normal((K, mp, mp), dtype=np.float32)
+    psi = rng.standard_normal(mp)
+    psi /= np.linalg.norm(psi)
+    sample = np.unique(np.concatenate([[0, 1, K - 1], rng.choice(K, 21, replace=False)]))
+    ref = oracle.correlations(Op32[sample].astype(np.float64), psi)
+    dev = torch.device("cuda")
+    O_dev = torch.from_numpy(Op32).to(dev)
+    psi_dev = torch.from_numpy(psi).to(dev)
+    for Ouse in (O_dev, O_dev.double()):
+        got = lib.dmrg_correlations(Ouse, psi_dev).cpu().numpy()
+        assert got.shape == (K, K)
+        blk = got[np.ix_(sample, sample)]
+        assert np.abs(blk - ref).max() <= 1e-12 * np.abs(ref).max(), Ouse.dtype
+        del got
 
 
 def test_full_size_m400_sampled(lib):

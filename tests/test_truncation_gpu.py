@@ -117,3 +117,47 @@ def test_truncation_tiny_sizes(P, method):
         U, lam, eps, _ = run(P, Psi, rows, method)
         assert np.abs(lam - lam_ref).max() < 1e-14
         assert np.abs(U - U_ref).max() < 1e-12
+
+
+def _ulp_distance(a, b):
+    """Distance in units in the last place between same-signed finite doubles."""
+    ia = a.view(np.int64)
+    ib = b.view(np.int64)
+    return np.abs(ia - ib)
+
+
+def test_sturm_reciprocal_within_two_ulps():
+    # The Sturm counts of the eigenvalue multisection divide by the pivots through a
+    # Newton-Raphson reciprocal.  Over the pivot range (|q| from the pivot floor
+    # DBL_MIN up to 1e300, both signs, random mantissas, exact powers of two) it must
+    # stay within 2 ulps of correctly rounded division; past 1/DBL_MIN it flushes to 0.
+    import ctypes
+    from paper_0909_5662_gb300 import _capi
+    lib = _capi.load()
+    rng = np.random.default_rng(91)
+    tiny = np.finfo(np.float64).tiny
+    mags = np.concatenate([
+        10.0 ** rng.uniform(-307.5, 300.0, 200000),
+        tiny * rng.uniform(1.0, 4.0, 2000),
+        2.0 ** np.arange(-1022, 997, dtype=np.float64),
+        1.0 + rng.uniform(-1e-3, 1e-3, 2000),
+    ])
+    q = np.concatenate([mags, -mags])
+    dev = torch.device("cuda")
+    qd = torch.from_numpy(q).to(dev)
+    out = torch.empty_like(qd)
+    st = lib.dmrg_debug_reciprocal(ctypes.c_void_p(qd.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                   len(q), None)
+    assert st == 0
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    exact = 1.0 / q
+    assert np.all(np.sign(got) == np.sign(exact))
+    assert _ulp_distance(got, exact).max() <= 2
+    # beyond the range: results flush to zero instead of going subnormal
+    big = torch.tensor([1e308, -1e308], dtype=torch.float64, device=dev)
+    ob = torch.empty_like(big)
+    assert lib.dmrg_debug_reciprocal(ctypes.c_void_p(big.data_ptr()), ctypes.c_void_p(ob.data_ptr()),
+                                     2, None) == 0
+    torch.cuda.synchronize()
+    assert np.all(np.abs(ob.cpu().numpy()) <= tiny)

@@ -6,9 +6,11 @@ memory limit, or a loop where an allocation would synchronise the device).
 This entry point takes no handle and no workspace; its scratch is a fixed
 static device array inside the library.  The test calls it through the C ABI
 twice in a row on different inputs and checks each result against
-dmrg_rotate_ops on the same inputs, with the tolerances of the other dense
-tests, then checks that an oversized problem is refused before any launch.
-This file is named to be collected last.
+dmrg_rotate_ops on the same inputs and against the FP64 oracle, with the
+tolerances of the other dense tests.  One BF16x3 case has m*d > 1024, so its
+second product cuts the reduction into accumulation chains whose running sums
+live in the static array too.  Finally an oversized problem must be refused
+before any launch.  This file is named to be collected last.
 """
 import ctypes
 
@@ -16,6 +18,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from workloads import dense_workload
 
 pytestmark = pytest.mark.gpu
@@ -39,24 +42,39 @@ def _rel(a, b):
     return (num / np.linalg.norm(b.reshape(len(b), -1), axis=1)).max()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "tf32", "fp32"])
-def test_noalloc_matches_dmrg_rotate_ops_twice(prec):
+CASES = [
+    # (prec, d, m, mp, K)
+    ("fp64", 4, 64, 64, 32),
+    ("bf16x3", 4, 64, 64, 32),
+    ("tf32", 4, 64, 64, 32),
+    ("fp32", 4, 64, 64, 32),
+    # m*d = 1200 > 1024: chained accumulation through the static array (about 27 MiB)
+    ("bf16x3", 4, 300, 64, 8),
+]
+
+
+@pytest.mark.parametrize("prec,d,m,mp,K", CASES)
+def test_noalloc_matches_dmrg_rotate_ops_twice(prec, d, m, mp, K):
     import paper_0909_5662_gb300 as P
     from paper_0909_5662_gb300 import _capi
     lib = _capi.load()
     dev = torch.device("cuda")
     odt = torch.float64 if prec == "fp64" else torch.float32
     for call, seed in enumerate((101, 202)):
-        w = dense_workload("noalloc", seed, 4, 64, 64, 32)
+        w = dense_workload("noalloc", seed + m, d, m, mp, K)
         U = torch.from_numpy(w.U).to(dev)
         O = torch.from_numpy(w.O).to(dev, torch.float64 if prec != "fp32" else torch.float32)
-        ref = P.dmrg_rotate_ops(U, O, 4, prec)
-        out = torch.full((w.K, 64, 64), float("nan"), dtype=odt, device=dev)
-        st = _call_noalloc(lib, U, O, 4, prec, out)
+        ref = P.dmrg_rotate_ops(U, O, d, prec)
+        out = torch.full((K, mp, mp), float("nan"), dtype=odt, device=dev)
+        st = _call_noalloc(lib, U, O, d, prec, out)
         assert st == 0, (prec, call, _capi.STATUS.get(st))
         torch.cuda.synchronize()
         assert torch.isfinite(out).all()
         assert _rel(out, ref) <= TOL[prec], (prec, call)
+        # and against the FP64 oracle on the operators as the call saw them
+        o_seen = O.double().cpu().numpy()
+        exact = torch.from_numpy(oracle.rotate_dense(w.U, o_seen, d))
+        assert _rel(out, exact) <= TOL[prec], (prec, call, "oracle")
 
 
 def test_noalloc_refuses_problems_beyond_its_scratch():
