@@ -941,7 +941,8 @@ def main():
                 "peak_source": "%s bf16_tflops (burst)" % peak_src,
                 "flops_per_launch": issued[dom], "ms_per_launch": per_kernel[dom]}
     else:
-        byt = {"pack_operands": K * M * M * (4 + 4)}
+        byt = {"pack_operands": K * M * M * (4 + 4),
+               "pack_u": D * M * MP * 8 + 2 * (2 * D * M * MP * 2)}
         achieved = byt.get(dom, 0) / (per_kernel[dom] * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic_for(dom), "kernel": dom}

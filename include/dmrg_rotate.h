@@ -130,14 +130,18 @@ DMRG_API dmrg_status dmrg_sync_status(dmrg_handle handle, dmrg_stream_t stream);
  *                              Same precision and workspace as the two-product path.
  *                              0 (default) = the two products (mp > 256 always).
  *                              Other values return DMRG_ERR_INVALID_ARG.
- *   DMRG_OPT_PACK_OPERATORS  : 0 = the TF32 and BF16x3 dense products take FP32
+ *   DMRG_OPT_PACK_OPERATORS  : how the TF32 and BF16x3 dense products take FP32
  *                              operators whose rows are whole 16-byte units
- *                              (m % 4 == 0, 16-byte aligned base) as they are: the
- *                              first product converts each tile in shared memory (BF16
- *                              hi/lo split or TF32 rounding, the same values as the
- *                              packing pass).  1 (default) = always pack the operators
- *                              in a separate pass first (FP64 operators and other rows
- *                              always are).
+ *                              (m % 4 == 0, 16-byte aligned base).  Either a separate
+ *                              pass packs them (BF16 hi/lo split or TF32 rounding), or
+ *                              the first product reads them as they are and converts
+ *                              each tile in shared memory into the same values (results
+ *                              are bit-identical).  The conversion is repeated for
+ *                              every N tile of the first product, so it pays only for
+ *                              few tiles.  0 (default) = convert for BF16x3 when d*mp
+ *                              fits in two N tiles, else pack; 1 = always pack;
+ *                              2 = convert whenever the layout allows.  FP64 operators
+ *                              and other rows are always packed.
  *   DMRG_OPT_TEST_WITHHOLD_ARRIVAL : test hook for failure detection.  1 makes
  *                              the next dense tensor-core launch withhold one
  *                              shared-memory stage release in its first CTA, so

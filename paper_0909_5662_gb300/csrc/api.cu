@@ -286,9 +286,16 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
 
     // ---- FP32 operators with 16-byte rows feed the first product as they are: the
     //      CTA-pair kernel converts each tile in shared memory, so O is not packed.
-    const bool convert_a = !in_is_fp64 && (m % 4) == 0 &&
-                           (reinterpret_cast<uintptr_t>(O) & 15) == 0 && c1.pair &&
-                           c1.row_bytes == 128 && !h->pack_operators;
+    //      Each A tile is converted once per N tile, so this pays only when the first
+    //      product has few N tiles (measured: BF16x3 wins at d*m' <= 512, loses at 1600;
+    //      TF32, with half as many MMA cycles per converted byte, loses everywhere).
+    const int n1_tile = std::max(32, choose_tile_n(int64_t(d) * mp, c1.tile_n_max));
+    const int64_t n1_tiles = (int64_t(d) * mp + n1_tile - 1) / n1_tile;
+    const bool can_convert = !in_is_fp64 && (m % 4) == 0 &&
+                             (reinterpret_cast<uintptr_t>(O) & 15) == 0 && c1.pair &&
+                             c1.row_bytes == 128;
+    const bool convert_a = can_convert && (h->pack_operators == 2 ||
+                                           (h->pack_operators == 0 && split && n1_tiles <= 2));
 
     // ---- operand packing: O (stacked K*m x m) unless converted in the first product,
     //      U_r' (rows b*d + s, cols j), U^T, and the clearing of the split tail's outputs,
@@ -330,7 +337,8 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     }
     cudaError_t e = cudaSuccess;
     if (nj > 0) {
-        e = timed_launch(h, "pack_operands", s, [&] { return pack_launch(jobs, nj, nullptr, s); });
+        e = timed_launch(h, convert_a ? "pack_u" : "pack_operands", s,
+                         [&] { return pack_launch(jobs, nj, nullptr, s); });
         if (e != cudaSuccess) return cuda_fail(h, e, "pack");
     }
 
@@ -610,7 +618,9 @@ dmrg_status dmrg_set_option(dmrg_handle h, dmrg_option o, double v) {
             h->blocked_small = v != 0;
             return DMRG_OK;
         case DMRG_OPT_PACK_OPERATORS:
-            h->pack_operators = v != 0;
+            if (!(v == 0 || v == 1 || v == 2))
+                return fail(h, DMRG_ERR_INVALID_ARG, "pack_operators must be 0, 1 or 2");
+            h->pack_operators = int(v);
             return DMRG_OK;
         case DMRG_OPT_FUSED_ROTATION:
             if (!(v == 0 || v == 1))

@@ -78,6 +78,8 @@ struct TcScatter {
     int64_t out_off, s_op, s_row, s_col_hi, s_col_lo;
     const int64_t* op_off;
     int32_t rows_per_op, col_div;
+    int64_t s_split;   // CTA-pair kernel: output offset per reduction split (0: the splits
+                       // of a tile add into one output, atomically when the problem says so)
 };
 
 struct TcProblem {  // 64-byte aligned through its CUtensorMap members
@@ -135,6 +137,14 @@ struct TcLaunch {
                             // sums (nullptr: every tile is one accumulation chain)
     int32_t convert_a;      // CTA-pair kernel: every problem's A map is an FP32 source that
                             // the converter warps turn into the MMA operand (f32_source)
+    // CTA-pair kernel, EPI_SPLIT_BF16 / EPI_TF32: a second, site-major copy of the result
+    // (null: none).  Element (row R, column c) also goes to
+    //   out2 + (R / o2_rows_per_op) * o2_s_op + (R % o2_rows_per_op) * o2_s_row
+    //        + (c % o2_d) * o2_s_site + c / o2_d
+    // i.e. for rows (k, a) and columns c = j * d + s: copy_k[s * m' + a][j], j contiguous.
+    void* out2[2];
+    int64_t o2_s_op, o2_s_row, o2_s_site;
+    int32_t o2_rows_per_op, o2_d;
 };
 
 // One operand seen by the kernel: `nbatch` slices of rows x cols (cols = the
@@ -255,9 +265,11 @@ struct dmrg_handle_s {
     bool deterministic = false;     // no atomically accumulated split tiles
     bool trunc_jacobi = false;      // truncation: cyclic Jacobi instead of the tridiagonal solver
     bool blocked_small = true;      // plans with sectors <= 32 states: fused small-sector kernel
-    bool pack_operators = true;     // dense tensor-core products: pack FP32 operators in a
-                                    // separate pass instead of converting them in the first
-                                    // product's shared memory
+    int pack_operators = 0;         // dense tensor-core products, FP32 operators: 0 = convert
+                                    // them in the first product's shared memory where that
+                                    // was measured faster (BF16x3, at most two N tiles),
+                                    // 1 = always pack them in a separate pass, 2 = convert
+                                    // whenever their layout allows
     int fused_rotation = 0;         // dense BF16x3, mp <= 256: both products in one kernel
                                     // (0 = off)
     int accum_chain = 1024;         // BF16x3 dense products: reduction elements per accumulator

@@ -219,5 +219,86 @@ __device__ __forceinline__ void store_chunk(const TcLaunch& L, const uint32_t (&
     }
 }
 
+// Stores one 32-column chunk (first column c0) of accumulator row `row` into the
+// site-major copy described by TcLaunch::out2 (see internal.h).  With d = 4 and aligned
+// rows the four site states' runs of eight consecutive j go out as vector stores.
+template <int EPI>
+__device__ __forceinline__ void store_chunk_site_major(const TcLaunch& L, const uint32_t (&r)[32],
+                                                       int row, int c0, int cmax) {
+    const int g = row / L.o2_rows_per_op;
+    const int rr = row - g * L.o2_rows_per_op;
+    const int d = L.o2_d;
+    const int64_t base = int64_t(g) * L.o2_s_op + int64_t(rr) * L.o2_s_row;
+    const bool fast = d == 4 && cmax == 32 && (c0 & 3) == 0 && ((base + c0 / 4) & 3) == 0 &&
+                      (L.o2_s_site & 3) == 0;
+    if (EPI == EPI_SPLIT_BF16) {
+        __nv_bfloat16* hi = static_cast<__nv_bfloat16*>(L.out2[0]);
+        __nv_bfloat16* lo = static_cast<__nv_bfloat16*>(L.out2[1]);
+        if (fast) {
+            const int64_t j0 = base + c0 / 4;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {   // j = 4q .. 4q + 3 of the chunk: columns 4j + s
+                    uint32_t hw[2], lw[2];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const float2 v = make_float2(__uint_as_float(r[4 * (4 * q + 2 * e) + s]),
+                                                     __uint_as_float(r[4 * (4 * q + 2 * e + 1) + s]));
+                        const __nv_bfloat162 h2 = __float22bfloat162_rn(v);
+                        const float2 hf = __bfloat1622float2(h2);
+                        const __nv_bfloat162 l2 =
+                            __float22bfloat162_rn(make_float2(v.x - hf.x, v.y - hf.y));
+                        hw[e] = *reinterpret_cast<const uint32_t*>(&h2);
+                        lw[e] = *reinterpret_cast<const uint32_t*>(&l2);
+                    }
+                    const int64_t o = j0 + int64_t(s) * L.o2_s_site + 4 * q;
+                    *reinterpret_cast<uint2*>(hi + o) = make_uint2(hw[0], hw[1]);
+                    *reinterpret_cast<uint2*>(lo + o) = make_uint2(lw[0], lw[1]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+                if (jj < cmax) {
+                    const int c = c0 + jj;
+                    const int j = c / d;
+                    const int64_t o = base + int64_t(c - j * d) * L.o2_s_site + j;
+                    const float v = __uint_as_float(r[jj]);
+                    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                    hi[o] = h;
+                    lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+                }
+            }
+        }
+    } else {
+        float* out = static_cast<float*>(L.out2[0]);
+        if (fast) {
+            const int64_t j0 = base + c0 / 4;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    float4 v;
+                    v.x = tf32_round(__uint_as_float(r[4 * (4 * q) + s]));
+                    v.y = tf32_round(__uint_as_float(r[4 * (4 * q + 1) + s]));
+                    v.z = tf32_round(__uint_as_float(r[4 * (4 * q + 2) + s]));
+                    v.w = tf32_round(__uint_as_float(r[4 * (4 * q + 3) + s]));
+                    *reinterpret_cast<float4*>(out + j0 + int64_t(s) * L.o2_s_site + 4 * q) = v;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+                if (jj < cmax) {
+                    const int c = c0 + jj;
+                    const int j = c / d;
+                    out[base + int64_t(c - j * d) * L.o2_s_site + j] = tf32_round(__uint_as_float(r[jj]));
+                }
+            }
+        }
+    }
+}
+
 }  // namespace tcdev
 }  // namespace dmrg

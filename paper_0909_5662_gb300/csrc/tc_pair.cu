@@ -117,7 +117,9 @@ __device__ __forceinline__ void convert_a_row(uint32_t box0, uint32_t box1, int 
     } else {
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const uint32_t a = r0 + (uint32_t(c) << 4);   // same place in or out of the swizzle
+            // chunk c ^ sw: the eight lanes of a quarter warp (eight consecutive rows)
+            // then touch eight different 16-byte bank groups
+            const uint32_t a = r0 + ((uint32_t(c) ^ sw) << 4);
             float4 v;
             ld_shared_v4(a, v);
             st_shared_v4u(a, __float_as_uint(tf32_round(v.x)), __float_as_uint(tf32_round(v.y)),
@@ -411,6 +413,7 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                 const int rr = row - g * S.rows_per_op;
                 row_base = S.out_off + (S.op_off ? S.op_off[g] : int64_t(g) * S.s_op) +
                            int64_t(rr) * S.s_row;
+                if (S.s_split) row_base += int64_t(dt.kb_begin / P->kb_per_split) * S.s_split;
             }
             const int cdiv = S.col_div;
             const int64_t sch = S.s_col_hi, scl = S.s_col_lo;
@@ -458,6 +461,8 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                     }
                     const int cmax = min(32, ncols - c);
                     store_chunk<EPI>(L, r, row_base, n0, c, cmax, cdiv, sch, scl, tile_atomic);
+                    if ((EPI == EPI_SPLIT_BF16 || EPI == EPI_TF32) && L.out2[0] != nullptr)
+                        store_chunk_site_major<EPI>(L, r, row, n0 + c, cmax);
                 }
                 tc_fence_before();
                 __syncwarp();
