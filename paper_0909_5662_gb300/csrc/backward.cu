@@ -6,14 +6,21 @@
 //   dU   = sum_k (O_k (x) I) U G_k^T + (O_k (x) I)^T U G_k.
 // Nothing from the forward pass is kept: only U, O and G are read.
 //
-// Tensor-core schedule (BF16x3 or TF32), with W_k = U G_k and W'_k = U G_k^T:
-//   1. W'_k  = (G_k U^T)^T : M = K*m' rows (k, a), N = m*d, written row-major per op;
-//   2. dO_k[i][j] = sum_(s,a) W'_k[j*d+s][a] U[i*d+s][a] : M = K*m rows (k, j), N = m;
-//   3. W_k and W'_k again, one problem per site state s, rows = block states j, written
-//      transposed (WT_k[s*m'+b][j]) so the next reduction over (k, j) is K-major;
-//   4. dU_r[i][n] = sum_(k,j) O_k[i][j] WT'_k[n][j] + O_k[j][i] WT_k[n][j] : one launch of
-//      two problems over 3-D operand maps, split over (k, j) and accumulated in FP32;
-//   5. dU (FP64) = dU_r (dU and dU_r share the row-major layout).
+// Tensor-core schedule (BF16x3 or TF32, CTA-pair kernel), with W_k = U G_k and
+// W'_k = U G_k^T (md x m' each; W_{k,s} = rows j*d + s):
+//   1. W'_k: M = K*m' rows (k, a), N = d*m columns ordered (s, j) (U packed with rows
+//      s*m + j), reduction m'.  The epilogue writes it twice: row-major (rows (k, j),
+//      columns (s, a): the dO operand) and site-major, WT'_k[s*m' + a][j] (j contiguous:
+//      the dU operand), where a 32-column chunk is a run of 32 consecutive j;
+//   2. W_k the same way from G^T, written site-major only (WT_k);
+//   3. dO_k[i][j] = sum_(s,a) W'_k[j*d+s][a] U[i*d+s][a] : M = K*m rows (k, j), N = m;
+//   4. dU_r^T[(s,n)][i] = sum_(k,j) WT'_k[(s,n)][j] O_k[i][j] + WT_k[(s,n)][j] O_k[j][i]:
+//      one problem whose reduction runs over 2K slices ([WT' | WT] against [O | O^T]),
+//      split into P parts that write their own partial sums;
+//   5. dU[i*d+s][n] = sum_p partial_p[(s,n)][i], summed in FP64 in a fixed order.
+// BF16x3 reductions longer than one accumulation chain (dO: d*m'; dU: 2*K*m) are cut
+// into chains as in the forward products, and nothing is accumulated atomically, so dO
+// and dU are reproducible bit for bit.
 // Plain FMA schedule (FP64, FP32): the same formulas as strided batched GEMMs.
 #include <cuda_runtime.h>
 
@@ -26,13 +33,17 @@ using namespace dmrg;
 
 namespace {
 
+// dU's reduction over 2K*m terms is split into at most this many parts, each written to
+// its own partial sum.
+constexpr int kBwdMaxParts = 16;
+
 struct BwdDims {
     int64_t K, m, mp, md, dmp;
     int d;
     int64_t ld_u, ld_n, ld_j;  // packed leading dimensions (elements)
     WsLayout ws;
     // section indices
-    int i_U, i_Ur, i_G, i_GT, i_O, i_OT, i_Wp, i_WT, i_WTp, i_dU, i_conv;
+    int i_U, i_Ur, i_G, i_GT, i_O, i_Wp, i_WT, i_dU, i_conv;
 };
 
 BwdDims bwd_dims(int64_t K, int64_t m, int d, int64_t mp, dmrg_precision p) {
@@ -68,13 +79,13 @@ BwdDims bwd_dims(int64_t K, int64_t m, int d, int64_t mp, dmrg_precision p) {
     add(B.i_Ur, size_t(m) * B.ld_n);
     add(B.i_G, size_t(K) * mp * B.ld_u);
     add(B.i_GT, size_t(K) * mp * B.ld_u);
-    add(B.i_O, size_t(K) * m * B.ld_j);
-    add(B.i_OT, size_t(K) * m * B.ld_j);
-    add(B.i_Wp, size_t(K) * m * B.ld_n);
-    add(B.i_WT, size_t(K) * B.dmp * B.ld_j);
-    add(B.i_WTp, size_t(K) * B.dmp * B.ld_j);
+    add(B.i_O, size_t(2 * K) * m * B.ld_j);       // [O | O^T], 2K slices of m x ld_j
+    add(B.i_Wp, size_t(K) * m * B.ld_n);          // W' row-major: rows (k, j), cols (s, a)
+    add(B.i_WT, size_t(2 * K) * B.dmp * B.ld_j);  // [WT' | WT], 2K slices of d*m' x ld_j
     B.i_dU = int(W.offsets.size());
-    W.add("dU32", size_t(B.md) * mp * 4);
+    W.add("dUpart", size_t(kBwdMaxParts) * B.md * mp * 4);
+    B.i_conv = int(W.offsets.size());
+    W.add("chain", split ? kChainScratchBytes : 0);
     return B;
 }
 
@@ -162,6 +173,31 @@ dmrg_status bwd_simt(dmrg_handle h, const double* U, const void* O, const void* 
     return DMRG_OK;
 }
 
+// dU[(i d + s) m' + n] = sum_p part[p][(s m' + n) m + i], in FP64, p in order: the
+// partial sums of dU_r^T are transposed back through a shared-memory tile.
+__global__ void __launch_bounds__(256) bwd_du_reduce_kernel(const float* __restrict__ part,
+                                                            int nparts, int64_t dmp, int64_t m,
+                                                            int64_t mp, int d,
+                                                            double* __restrict__ dU) {
+    __shared__ double t[32][33];
+    const int64_t R0 = int64_t(blockIdx.y) * 32, I0 = int64_t(blockIdx.x) * 32;
+    for (int rr = threadIdx.y; rr < 32; rr += 8) {
+        const int64_t R = R0 + rr, I = I0 + threadIdx.x;
+        double acc = 0.0;
+        if (R < dmp && I < m)
+            for (int q = 0; q < nparts; ++q) acc += double(part[(int64_t(q) * dmp + R) * m + I]);
+        t[rr][threadIdx.x] = acc;
+    }
+    __syncthreads();
+    for (int ii = threadIdx.y; ii < 32; ii += 8) {
+        const int64_t I = I0 + ii, R = R0 + threadIdx.x;
+        if (R < dmp && I < m) {
+            const int64_t sidx = R / mp, n = R - sidx * mp;
+            dU[(I * d + sidx) * mp + n] = t[threadIdx.x][ii];
+        }
+    }
+}
+
 dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G, int in_is_fp64,
                    void* dO, double* dU, const BwdDims& B, dmrg_precision p, void* ws,
                    cudaStream_t s) {
@@ -171,31 +207,37 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
     const TcEpi epi_op = split ? EPI_SPLIT_BF16 : EPI_TF32;
     const int64_t K = B.K, m = B.m, mp = B.mp, md = B.md, dmp = B.dmp;
     const int d = B.d;
+    const size_t es = split ? 2 : 4;
     char* base = static_cast<char*>(ws);
-    auto sec = [&](int idx, int half) -> void* {
+    auto sec = [&](int idx, int half) -> char* {
         return base + B.ws.offsets[idx + (split ? half : 0)];
     };
-    auto lo = [&](int idx) -> void* { return split ? sec(idx, 1) : sec(idx, 0); };
+    auto lo = [&](int idx) -> char* { return split ? sec(idx, 1) : sec(idx, 0); };
     cudaError_t e;
-    // ---- packs: U, U_r, G, G^T and (for dU) O, O^T in one launch
+    // ---- packs: U, U_r (dO), G, and for dU G^T, O and O^T, in one launch
     {
         PackJob jobs[6] = {};
-        PackJob& ju = jobs[0];   // U: rows r, cols a
-        ju.src = U; ju.src_f64 = 1; ju.mode = pmode; ju.rows = md; ju.cols = mp; ju.rows_per_op = md;
-        ju.rdiv = 1; ju.s_r_hi = mp; ju.s_c = 1; ju.dst0 = sec(B.i_U, 0); ju.dst1 = lo(B.i_U); ju.ld = B.ld_u;
-        PackJob& jr = jobs[1];   // U_r: rows j, cols (s, a)
-        jr.src = U; jr.src_f64 = 1; jr.mode = pmode; jr.rows = m; jr.cols = dmp; jr.rows_per_op = m;
-        jr.rdiv = 1; jr.s_r_hi = dmp; jr.s_c = 1; jr.dst0 = sec(B.i_Ur, 0); jr.dst1 = lo(B.i_Ur); jr.ld = B.ld_n;
-        PackJob& jg = jobs[2];   // G: rows (k, a), cols b = G_k[a][b]
+        int nj = 0;
+        PackJob& ju = jobs[nj++];   // U site-major: row s*m + j, cols a = U[j*d + s][a]
+        ju.src = U; ju.src_f64 = 1; ju.mode = pmode; ju.rows = md; ju.cols = mp; ju.rows_per_op = m;
+        ju.s_op = mp; ju.rdiv = 1; ju.s_r_hi = int64_t(d) * mp; ju.s_c = 1;
+        ju.dst0 = sec(B.i_U, 0); ju.dst1 = lo(B.i_U); ju.ld = B.ld_u;
+        if (dO) {
+            PackJob& jr = jobs[nj++];   // U_r: rows j, cols (s, a)
+            jr.src = U; jr.src_f64 = 1; jr.mode = pmode; jr.rows = m; jr.cols = dmp; jr.rows_per_op = m;
+            jr.rdiv = 1; jr.s_r_hi = dmp; jr.s_c = 1; jr.dst0 = sec(B.i_Ur, 0); jr.dst1 = lo(B.i_Ur);
+            jr.ld = B.ld_n;
+        }
+        PackJob& jg = jobs[nj++];   // G: rows (k, a), cols b = G_k[a][b]
         jg.src = G; jg.src_f64 = in_is_fp64; jg.mode = pmode; jg.rows = K * mp; jg.cols = mp;
         jg.rows_per_op = K * mp; jg.rdiv = 1; jg.s_r_hi = mp; jg.s_c = 1;
         jg.dst0 = sec(B.i_G, 0); jg.dst1 = lo(B.i_G); jg.ld = B.ld_u;
-        PackJob& jt = jobs[3];   // G^T: rows (k, b), cols a = G_k[a][b]
-        jt.src = G; jt.src_f64 = in_is_fp64; jt.mode = pmode; jt.rows = K * mp; jt.cols = mp;
-        jt.rows_per_op = mp; jt.s_op = mp * mp; jt.rdiv = 1; jt.s_r_hi = 1; jt.s_c = mp;
-        jt.dst0 = sec(B.i_GT, 0); jt.dst1 = lo(B.i_GT); jt.ld = B.ld_u;
-        int nj = 4;
         if (dU) {
+            PackJob& jt = jobs[nj++];   // G^T: rows (k, b), cols a = G_k[a][b]
+            jt.src = G; jt.src_f64 = in_is_fp64; jt.mode = pmode; jt.rows = K * mp; jt.cols = mp;
+            jt.rows_per_op = mp; jt.s_op = mp * mp; jt.rdiv = 1; jt.s_r_hi = 1; jt.s_c = mp;
+            jt.dst0 = sec(B.i_GT, 0); jt.dst1 = lo(B.i_GT); jt.ld = B.ld_u;
+            const size_t oT = size_t(K) * m * B.ld_j * es;   // O^T slices follow the O slices
             PackJob& jo = jobs[nj++];   // O: rows (k, i), cols j
             jo.src = O; jo.src_f64 = in_is_fp64; jo.mode = pmode; jo.rows = K * m; jo.cols = m;
             jo.rows_per_op = K * m; jo.rdiv = 1; jo.s_r_hi = m; jo.s_c = 1;
@@ -203,115 +245,131 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
             PackJob& jq = jobs[nj++];   // O^T: rows (k, i), cols j = O_k[j][i]
             jq.src = O; jq.src_f64 = in_is_fp64; jq.mode = pmode; jq.rows = K * m; jq.cols = m;
             jq.rows_per_op = m; jq.s_op = m * m; jq.rdiv = 1; jq.s_r_hi = 1; jq.s_c = m;
-            jq.dst0 = sec(B.i_OT, 0); jq.dst1 = lo(B.i_OT); jq.ld = B.ld_j;
+            jq.dst0 = sec(B.i_O, 0) + oT; jq.dst1 = lo(B.i_O) + (split ? oT : 0); jq.ld = B.ld_j;
         }
         e = timed_launch(h, "bwd_pack", s, [&] { return pack_launch(jobs, nj, nullptr, s); });
         if (e != cudaSuccess) return cuda_fail(h, e, "pack");
     }
-    const TcConfig cfg = tuned_config(h, shape_key("bwd", K, m, d, mp, p), mode);
-    const int grid = cfg.grid > 0 ? cfg.grid : h->num_sms;
-    auto launch = [&](const char* name, TcLaunch& L, TcEpi epi) -> dmrg_status {
+    // Every product runs on CTA pairs: only that kernel writes the site-major copy, the
+    // per-split partial sums and the chained accumulation.
+    TcConfig cfg = tuned_config(h, shape_key("bwd", K, m, d, mp, p), mode);
+    if (!cfg.pair || cfg.row_bytes != 128) {
+        cfg.pair = 1;
+        cfg.row_bytes = 128;
+        cfg.stages = tc_stages_for(mode, cfg);
+    }
+    const int grid = std::min(cfg.grid > 0 ? cfg.grid : h->num_sms, kChainScratchCtas) / 2 * 2;
+    float* chain_scr = split ? reinterpret_cast<float*>(base + B.ws.offsets[B.i_conv]) : nullptr;
+    const int chain_kb = split ? std::max(1, h->accum_chain / 64) : 0;   // 64 BF16 per k-block
+    auto launch = [&](const char* name, TcLaunch& L, TcEpi epi, int64_t red) -> dmrg_status {
         L.table = nullptr;
         int tiles = 0;
         for (int i = 0; i < L.nprob; ++i) {
-            L.inline_prob[i].tile_start = tiles;
-            tiles += L.inline_prob[i].m_tiles * L.inline_prob[i].n_tiles * L.inline_prob[i].k_splits;
+            TcProblem& P = L.inline_prob[i];
+            P.tile_start = tiles;
+            P.kb_chunk = (chain_scr && red > std::max<int64_t>(kChainMinRed, h->accum_chain)) ? chain_kb : 0;
+            tiles += P.m_tiles * P.n_tiles * P.k_splits;
         }
         L.total_tiles = tiles;
         L.status = h->d_status;
         L.timeout_ns = timeout_ns(h);
         L.row_bytes = cfg.row_bytes;
+        L.chunk_scratch = L.inline_prob[0].kb_chunk ? chain_scr : nullptr;
         cudaError_t ee = timed_launch(h, name, s, [&] {
-            return cfg.pair ? tc_gemm_launch_pair(mode, epi, L, cfg.stages, grid, s)
-                            : tc_gemm_launch(mode, epi, L, cfg.stages, grid, s);
+            return tc_gemm_launch_pair(mode, epi, L, cfg.stages, grid, s);
         });
         return cuda_fail(h, ee, name);
     };
     dmrg_status st;
-    if (dO) {
-        // 1. W'_k[r][a] = sum_b G_k[a][b] U[r][b], rows (k, a), written as W'_k row-major.
+    char* wt_hi = sec(B.i_WT, 0);
+    char* wt_lo = lo(B.i_WT);
+    const size_t wt_second = size_t(K) * dmp * B.ld_j * es;   // WT slices follow the WT' slices
+    // site-major copy of a W product: rows (k, a), columns c = s m + j -> slice k, row
+    // s m' + a, column j
+    auto site_major = [&](TcLaunch& L, char* hi, char* lo_) {
+        L.out2[0] = hi;
+        L.out2[1] = split ? lo_ : nullptr;
+        L.o2_rows_per_op = int32_t(mp);
+        L.o2_s_op = dmp * B.ld_j;
+        L.o2_s_row = B.ld_j;
+        L.o2_s_site = mp * B.ld_j;
+        L.o2_m = int32_t(m);
+    };
+    {
+        // 1. W'_k[j d + s][a] = sum_b G_k[a][b] U[j d + s][b], rows (k, a), columns (s, j):
+        //    row-major into Wp (rows (k, j), cols (s, a)), and site-major into the first K
+        //    slices of WT.
         TcLaunch L{};
         TcProblem& P = L.inline_prob[0];
         TcOperand A{sec(B.i_G, 0), lo(B.i_G), K * mp, mp, B.ld_u};
         TcOperand Bo{sec(B.i_U, 0), lo(B.i_U), md, mp, B.ld_u};
-        if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, 1, cfg.row_bytes, cfg.pair)) return fail(h, DMRG_ERR_CUDA, "tensor map");
+        if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, 1, cfg.row_bytes, 1))
+            return fail(h, DMRG_ERR_CUDA, "tensor map");
         TcScatter& S = P.sc[0];
         S.rows_per_op = int32_t(mp); S.s_op = m * B.ld_n; S.s_row = 1;
-        S.col_div = d; S.s_col_hi = B.ld_n; S.s_col_lo = mp;
+        S.col_div = int32_t(m); S.s_col_hi = mp; S.s_col_lo = B.ld_n;
         L.nprob = 1;
-        L.out[0][0] = sec(B.i_Wp, 0);
-        L.out[0][1] = lo(B.i_Wp);
-        if ((st = launch("bwd_tc_Wp_rows", L, epi_op)) != DMRG_OK) return st;
-        // 2. dO_k[i][j] = sum_(s,a) W'_k[j*d+s][a] U[i*d+s][a], rows (k, j), cols i.
+        L.out[0][0] = dO ? sec(B.i_Wp, 0) : nullptr;
+        L.out[0][1] = dO ? lo(B.i_Wp) : nullptr;
+        if (dU) site_major(L, wt_hi, wt_lo);
+        if ((st = launch("bwd_tc_Wp", L, epi_op, mp)) != DMRG_OK) return st;
+    }
+    if (dO) {
+        // 3. dO_k[i][j] = sum_(s,a) W'_k[j*d+s][a] U[i*d+s][a], rows (k, j), cols i.
         TcLaunch L2{};
         TcProblem& P2 = L2.inline_prob[0];
         TcOperand A2{sec(B.i_Wp, 0), lo(B.i_Wp), K * m, dmp, B.ld_n};
         TcOperand B2{sec(B.i_Ur, 0), lo(B.i_Ur), m, dmp, B.ld_n};
-        if (!make_problem(P2, mode, A2, B2, cfg.tile_n_max, 1, cfg.row_bytes, cfg.pair)) return fail(h, DMRG_ERR_CUDA, "tensor map");
+        if (!make_problem(P2, mode, A2, B2, cfg.tile_n_max, 1, cfg.row_bytes, 1))
+            return fail(h, DMRG_ERR_CUDA, "tensor map");
         TcScatter& S2 = P2.sc[0];
         S2.rows_per_op = int32_t(m); S2.s_op = m * m; S2.s_row = 1;
         S2.col_div = 1; S2.s_col_hi = m; S2.s_col_lo = 0;
         L2.nprob = 1;
         L2.out[0][0] = dO;
-        if ((st = launch("bwd_tc_dO", L2, EPI_F32)) != DMRG_OK) return st;
+        if ((st = launch("bwd_tc_dO", L2, EPI_F32, dmp)) != DMRG_OK) return st;
     }
     if (dU) {
-        // 3. WT_k[s*mp + b][j] = W_k[j*d+s][b] and WT'_k likewise: one problem per s,
-        //    rows j (so stores run along j), columns (k, b).
-        for (int which = 0; which < 2; ++which) {
-            const int gsec = which == 0 ? B.i_GT : B.i_G;   // W = U G (B^T rows = G^T), W' = U G^T
-            const int osec = which == 0 ? B.i_WT : B.i_WTp;
-            for (int s0 = 0; s0 < d; s0 += kMaxInlineProblems) {
-                TcLaunch L{};
-                L.nprob = std::min(kMaxInlineProblems, d - s0);
-                for (int q = 0; q < L.nprob; ++q) {
-                    const int sidx = s0 + q;
-                    TcProblem& P = L.inline_prob[q];
-                    const int esz = split ? 2 : 4;
-                    TcOperand A{static_cast<char*>(sec(B.i_U, 0)) + size_t(sidx) * B.ld_u * esz,
-                                static_cast<char*>(lo(B.i_U)) + size_t(sidx) * B.ld_u * esz,
-                                m, mp, int64_t(d) * B.ld_u};
-                    TcOperand Bo{sec(gsec, 0), lo(gsec), K * mp, mp, B.ld_u};
-                    if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, 1, cfg.row_bytes, cfg.pair))
-                        return fail(h, DMRG_ERR_CUDA, "tensor map");
-                    TcScatter& S = P.sc[0];
-                    S.rows_per_op = 1 << 30; S.s_op = 0; S.s_row = 1;
-                    S.col_div = int32_t(mp); S.s_col_hi = dmp * B.ld_j; S.s_col_lo = B.ld_j;
-                    S.out_off = int64_t(sidx) * mp * B.ld_j;
-                }
-                L.out[0][0] = sec(osec, 0);
-                L.out[0][1] = lo(osec);
-                if ((st = launch(which == 0 ? "bwd_tc_WT" : "bwd_tc_WTp", L, epi_op)) != DMRG_OK)
-                    return st;
-            }
-        }
-        // 4. dU_r[i][n] = sum_(k,j) O_k[i][j] WT'_k[n][j] + O_k[j][i] WT_k[n][j]
-        float* dUr = reinterpret_cast<float*>(base + B.ws.offsets[B.i_dU]);
-        e = cudaMemsetAsync(dUr, 0, size_t(md) * mp * 4, s);
-        if (e != cudaSuccess) return cuda_fail(h, e, "memset");
-        TcLaunch L{};
-        L.nprob = 2;
-        // The reduction runs over K*m terms.  Each split accumulates at most 16 k-blocks
-        // in the tensor core's FP32 accumulator (a chain no longer than the forward
-        // products'); the splits are then summed with FP32 atomics (round to nearest).
-        const int64_t epr = cfg.row_bytes / (split ? 2 : 4);   // reduction elements per k-block
-        const int64_t kb = (m + epr - 1) / epr * K;
-        const int ksplit = int(std::max<int64_t>(1, (kb + 15) / 16));
-        for (int q = 0; q < 2; ++q) {
-            TcProblem& P = L.inline_prob[q];
-            const int asec = q == 0 ? B.i_O : B.i_OT;
-            const int bsec = q == 0 ? B.i_WTp : B.i_WT;
-            TcOperand A{sec(asec, 0), lo(asec), m, m, B.ld_j, K, m * B.ld_j};
-            TcOperand Bo{sec(bsec, 0), lo(bsec), dmp, m, B.ld_j, K, dmp * B.ld_j};
-            if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, ksplit, cfg.row_bytes, cfg.pair))
+        // 2. W_k[r][b] = sum_a G_k[a][b] U[r][a], rows (k, b), site-major into the last K
+        //    slices of WT only.
+        {
+            TcLaunch L{};
+            TcProblem& P = L.inline_prob[0];
+            TcOperand A{sec(B.i_GT, 0), lo(B.i_GT), K * mp, mp, B.ld_u};
+            TcOperand Bo{sec(B.i_U, 0), lo(B.i_U), md, mp, B.ld_u};
+            if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, 1, cfg.row_bytes, 1))
                 return fail(h, DMRG_ERR_CUDA, "tensor map");
-            P.sc[0] = scatter_rowmajor(dmp);
+            L.nprob = 1;
+            L.out[0][0] = nullptr;   // no row-major copy
+            site_major(L, wt_hi + wt_second, split ? wt_lo + wt_second : nullptr);
+            if ((st = launch("bwd_tc_W", L, epi_op, mp)) != DMRG_OK) return st;
         }
-        L.out[0][0] = dUr;
-        if ((st = launch("bwd_tc_dU", L, EPI_F32_ATOMIC)) != DMRG_OK) return st;
-        e = timed_launch(h, "bwd_dU_to_fp64", s,
-                         [&] { return convert_f32_to_f64_launch(dUr, dU, md * mp, s); });
-        if (e != cudaSuccess) return cuda_fail(h, e, "dU convert");
+        // 4. dU_r^T[(s,n)][i] over 2K slices, split into parts with their own partial sums.
+        float* part = reinterpret_cast<float*>(base + B.ws.offsets[B.i_dU]);
+        TcLaunch L{};
+        TcProblem& P = L.inline_prob[0];
+        TcOperand A{wt_hi, split ? wt_lo : nullptr, dmp, m, B.ld_j, 2 * K, dmp * B.ld_j};
+        TcOperand Bo{sec(B.i_O, 0), split ? lo(B.i_O) : nullptr, m, m, B.ld_j, 2 * K, m * B.ld_j};
+        if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, 1, cfg.row_bytes, 1))
+            return fail(h, DMRG_ERR_CUDA, "tensor map");
+        // parts: enough to give every CTA pair a tile, at most kBwdMaxParts
+        const int tiles = P.m_tiles * P.n_tiles;
+        const int parts = std::max(1, std::min(kBwdMaxParts, (grid / 2) / std::max(1, tiles)));
+        if (!make_problem(P, mode, A, Bo, cfg.tile_n_max, parts, cfg.row_bytes, 1))
+            return fail(h, DMRG_ERR_CUDA, "tensor map");
+        P.sc[0] = scatter_rowmajor(m);
+        P.sc[0].s_split = dmp * m;
+        L.nprob = 1;
+        L.out[0][0] = part;
+        if ((st = launch("bwd_tc_dU", L, EPI_F32, int64_t(2) * K * m)) != DMRG_OK) return st;
+        // 5. dU = the sum of the parts, transposed back, in FP64.
+        const int nparts = P.k_splits;
+        e = timed_launch(h, "bwd_dU_reduce", s, [&] {
+            dim3 grd(unsigned((m + 31) / 32), unsigned((dmp + 31) / 32));
+            bwd_du_reduce_kernel<<<grd, dim3(32, 8), 0, s>>>(part, nparts, dmp, m, mp, d, dU);
+            return cudaGetLastError();
+        });
+        if (e != cudaSuccess) return cuda_fail(h, e, "dU reduce");
     }
     return DMRG_OK;
 }

@@ -140,11 +140,11 @@ struct TcLaunch {
     // CTA-pair kernel, EPI_SPLIT_BF16 / EPI_TF32: a second, site-major copy of the result
     // (null: none).  Element (row R, column c) also goes to
     //   out2 + (R / o2_rows_per_op) * o2_s_op + (R % o2_rows_per_op) * o2_s_row
-    //        + (c % o2_d) * o2_s_site + c / o2_d
-    // i.e. for rows (k, a) and columns c = j * d + s: copy_k[s * m' + a][j], j contiguous.
+    //        + (c / o2_m) * o2_s_site + c % o2_m
+    // i.e. for rows (k, a) and columns c = s * m + j: copy_k[s * m' + a][j], j contiguous.
     void* out2[2];
     int64_t o2_s_op, o2_s_row, o2_s_site;
-    int32_t o2_rows_per_op, o2_d;
+    int32_t o2_rows_per_op, o2_m;
 };
 
 // One operand seen by the kernel: `nbatch` slices of rows x cols (cols = the

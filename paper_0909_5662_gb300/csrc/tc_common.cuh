@@ -219,32 +219,104 @@ __device__ __forceinline__ void store_chunk(const TcLaunch& L, const uint32_t (&
     }
 }
 
+// out[0..3] = the 16-byte word x[sel] (sel in 0..3, chosen per lane) of four.
+__device__ __forceinline__ void pick4(const uint32_t (&x)[4][4], int sel, uint32_t (&out)[4]) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const uint32_t a = (sel & 1) ? x[1][e] : x[0][e];
+        const uint32_t b = (sel & 1) ? x[3][e] : x[2][e];
+        out[e] = (sel & 2) ? b : a;
+    }
+}
+
+// Writes the 4 x 16-byte words x[q] (elements 8q .. 8q+7 of this lane's row segment,
+// 64 bytes at rowp) so that the four lanes of each aligned group of four write one
+// row's 64 bytes per store instruction: the words are exchanged in a 4 x 4 transpose
+// within the group (three shuffle rounds), then store i of lane 4g + t writes word t of
+// row 4g + i.  All 32 lanes must take part.
+__device__ __forceinline__ void store_rows64_grouped(uint4* rowp, const uint32_t (&x)[4][4]) {
+    const int t = threadIdx.x & 3;
+    uint32_t y[4][4];   // y[v] = word t of the row of lane (4g + (t ^ v))
+#pragma unroll
+    for (int e = 0; e < 4; ++e) y[0][e] = 0;
+    pick4(x, t, y[0]);
+#pragma unroll
+    for (int v = 1; v < 4; ++v) {
+        uint32_t snd[4];
+        pick4(x, t ^ v, snd);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) y[v][e] = __shfl_xor_sync(0xffffffffu, snd[e], v);
+    }
+    const uint64_t mine = reinterpret_cast<uint64_t>(rowp);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        // row 4g + i: its pointer comes from lane 4g + i; its word t is y[t ^ i]
+        const uint64_t p = __shfl_sync(0xffffffffu, mine, (threadIdx.x & ~3) | i);
+        uint32_t w[4];
+        pick4(y, t ^ i, w);
+        if (p != 0) reinterpret_cast<uint4*>(p)[t] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
 // Stores one 32-column chunk (first column c0) of accumulator row `row` into the
-// site-major copy described by TcLaunch::out2 (see internal.h).  With d = 4 and aligned
-// rows the four site states' runs of eight consecutive j go out as vector stores.
+// site-major copy described by TcLaunch::out2 (see internal.h).  A chunk that lies in
+// one site state's run of columns is 32 consecutive j of one output row; when every
+// lane's segment is 16-byte aligned the warp writes them as whole 64-byte row pieces
+// (BF16: store_rows64_grouped; FP32: 16-byte vectors).  `active`: this lane's row
+// exists (all lanes of the warp call this function).
 template <int EPI>
 __device__ __forceinline__ void store_chunk_site_major(const TcLaunch& L, const uint32_t (&r)[32],
-                                                       int row, int c0, int cmax) {
-    const int g = row / L.o2_rows_per_op;
-    const int rr = row - g * L.o2_rows_per_op;
-    const int d = L.o2_d;
-    const int64_t base = int64_t(g) * L.o2_s_op + int64_t(rr) * L.o2_s_row;
-    const bool fast = d == 4 && cmax == 32 && (c0 & 3) == 0 && ((base + c0 / 4) & 3) == 0 &&
-                      (L.o2_s_site & 3) == 0;
+                                                       int row, int c0, int cmax, bool active) {
+    const int mm = L.o2_m;
+    int64_t base = 0;
+    if (active) {
+        const int g = row / L.o2_rows_per_op;
+        const int rr = row - g * L.o2_rows_per_op;
+        base = int64_t(g) * L.o2_s_op + int64_t(rr) * L.o2_s_row;
+    }
+    const int s0 = c0 / mm;
+    const int j0 = c0 - s0 * mm;
+    const int64_t o0 = base + int64_t(s0) * L.o2_s_site + j0;
+    // c0, cmax and the site-major layout are the same for every lane of the warp
+    const bool one_run = cmax == 32 && j0 + 32 <= mm;
     if (EPI == EPI_SPLIT_BF16) {
         __nv_bfloat16* hi = static_cast<__nv_bfloat16*>(L.out2[0]);
         __nv_bfloat16* lo = static_cast<__nv_bfloat16*>(L.out2[1]);
-        if (fast) {
-            const int64_t j0 = base + c0 / 4;
+        const bool vec = one_run && __all_sync(0xffffffffu, !active || (o0 & 7) == 0);
+        if (vec) {
+            uint32_t hw[4][4], lw[4][4];
 #pragma unroll
-            for (int s = 0; s < 4; ++s) {
+            for (int q = 0; q < 4; ++q) {   // elements 8q .. 8q + 7
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {   // j = 4q .. 4q + 3 of the chunk: columns 4j + s
-                    uint32_t hw[2], lw[2];
+                for (int e = 0; e < 4; ++e) {
+                    const float2 v = make_float2(__uint_as_float(r[8 * q + 2 * e]),
+                                                 __uint_as_float(r[8 * q + 2 * e + 1]));
+                    const __nv_bfloat162 h2 = __float22bfloat162_rn(v);
+                    const float2 hf = __bfloat1622float2(h2);
+                    const __nv_bfloat162 l2 =
+                        __float22bfloat162_rn(make_float2(v.x - hf.x, v.y - hf.y));
+                    hw[q][e] = *reinterpret_cast<const uint32_t*>(&h2);
+                    lw[q][e] = *reinterpret_cast<const uint32_t*>(&l2);
+                }
+            }
+            store_rows64_grouped(active ? reinterpret_cast<uint4*>(hi + o0) : nullptr, hw);
+            store_rows64_grouped(active ? reinterpret_cast<uint4*>(lo + o0) : nullptr, lw);
+        } else if (active) {
+            // groups of eight elements: one 16-byte store each where the group lies in one
+            // run and is aligned (the tail chunk of a tile, a chunk across two runs)
 #pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const float2 v = make_float2(__uint_as_float(r[4 * (4 * q + 2 * e) + s]),
-                                                     __uint_as_float(r[4 * (4 * q + 2 * e + 1) + s]));
+            for (int q = 0; q < 4; ++q) {
+                if (8 * q >= cmax) break;
+                const int c = c0 + 8 * q;
+                const int sidx = c / mm;
+                const int j = c - sidx * mm;
+                const int64_t o = base + int64_t(sidx) * L.o2_s_site + j;
+                if (8 * q + 8 <= cmax && j + 8 <= mm && (o & 7) == 0) {
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float2 v = make_float2(__uint_as_float(r[8 * q + 2 * e]),
+                                                     __uint_as_float(r[8 * q + 2 * e + 1]));
                         const __nv_bfloat162 h2 = __float22bfloat162_rn(v);
                         const float2 hf = __bfloat1622float2(h2);
                         const __nv_bfloat162 l2 =
@@ -252,48 +324,51 @@ __device__ __forceinline__ void store_chunk_site_major(const TcLaunch& L, const 
                         hw[e] = *reinterpret_cast<const uint32_t*>(&h2);
                         lw[e] = *reinterpret_cast<const uint32_t*>(&l2);
                     }
-                    const int64_t o = j0 + int64_t(s) * L.o2_s_site + 4 * q;
-                    *reinterpret_cast<uint2*>(hi + o) = make_uint2(hw[0], hw[1]);
-                    *reinterpret_cast<uint2*>(lo + o) = make_uint2(lw[0], lw[1]);
-                }
-            }
-        } else {
+                    *reinterpret_cast<uint4*>(hi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4*>(lo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                } else {
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj) {
-                if (jj < cmax) {
-                    const int c = c0 + jj;
-                    const int j = c / d;
-                    const int64_t o = base + int64_t(c - j * d) * L.o2_s_site + j;
-                    const float v = __uint_as_float(r[jj]);
-                    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-                    hi[o] = h;
-                    lo[o] = __float2bfloat16_rn(v - __bfloat162float(h));
+                    for (int e = 0; e < 8; ++e) {
+                        if (8 * q + e < cmax) {
+                            const int ce = c + e;
+                            const int se = ce / mm;
+                            const int64_t oe = base + int64_t(se) * L.o2_s_site + (ce - se * mm);
+                            const float v = __uint_as_float(r[8 * q + e]);
+                            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+                            hi[oe] = h;
+                            lo[oe] = __float2bfloat16_rn(v - __bfloat162float(h));
+                        }
+                    }
                 }
             }
         }
-    } else {
+    } else if (active) {
         float* out = static_cast<float*>(L.out2[0]);
-        if (fast) {
-            const int64_t j0 = base + c0 / 4;
+        // groups of four elements: one 16-byte store each where the group lies in one run
+        // and is aligned
 #pragma unroll
-            for (int s = 0; s < 4; ++s) {
+        for (int q = 0; q < 8; ++q) {
+            if (4 * q >= cmax) break;
+            const int c = c0 + 4 * q;
+            const int sidx = c / mm;
+            const int j = c - sidx * mm;
+            const int64_t o = base + int64_t(sidx) * L.o2_s_site + j;
+            if (4 * q + 4 <= cmax && j + 4 <= mm && (o & 3) == 0) {
+                float4 v;
+                v.x = tf32_round(__uint_as_float(r[4 * q]));
+                v.y = tf32_round(__uint_as_float(r[4 * q + 1]));
+                v.z = tf32_round(__uint_as_float(r[4 * q + 2]));
+                v.w = tf32_round(__uint_as_float(r[4 * q + 3]));
+                *reinterpret_cast<float4*>(out + o) = v;
+            } else {
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    float4 v;
-                    v.x = tf32_round(__uint_as_float(r[4 * (4 * q) + s]));
-                    v.y = tf32_round(__uint_as_float(r[4 * (4 * q + 1) + s]));
-                    v.z = tf32_round(__uint_as_float(r[4 * (4 * q + 2) + s]));
-                    v.w = tf32_round(__uint_as_float(r[4 * (4 * q + 3) + s]));
-                    *reinterpret_cast<float4*>(out + j0 + int64_t(s) * L.o2_s_site + 4 * q) = v;
-                }
-            }
-        } else {
-#pragma unroll
-            for (int jj = 0; jj < 32; ++jj) {
-                if (jj < cmax) {
-                    const int c = c0 + jj;
-                    const int j = c / d;
-                    out[base + int64_t(c - j * d) * L.o2_s_site + j] = tf32_round(__uint_as_float(r[jj]));
+                for (int e = 0; e < 4; ++e) {
+                    if (4 * q + e < cmax) {
+                        const int ce = c + e;
+                        const int se = ce / mm;
+                        out[base + int64_t(se) * L.o2_s_site + (ce - se * mm)] =
+                            tf32_round(__uint_as_float(r[4 * q + e]));
+                    }
                 }
             }
         }

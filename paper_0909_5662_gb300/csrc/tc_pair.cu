@@ -440,29 +440,31 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                                            (uint32_t(quad * 32) << 16) + uint32_t(c),
                                        r);
                     tmem_ld_wait();
-                    if (!row_ok) continue;
-                    float4* s4 = scr ? scr + (c >> 5) * (8 * 32) : nullptr;
-                    if (!first) {   // add the chains before this one
+                    const int cmax = min(32, ncols - c);   // the same for the whole warp
+                    if (row_ok) {
+                        float4* s4 = scr ? scr + (c >> 5) * (8 * 32) : nullptr;
+                        if (!first) {   // add the chains before this one
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const float4 v = s4[j * 32];
-                            r[4 * j] = __float_as_uint(__uint_as_float(r[4 * j]) + v.x);
-                            r[4 * j + 1] = __float_as_uint(__uint_as_float(r[4 * j + 1]) + v.y);
-                            r[4 * j + 2] = __float_as_uint(__uint_as_float(r[4 * j + 2]) + v.z);
-                            r[4 * j + 3] = __float_as_uint(__uint_as_float(r[4 * j + 3]) + v.w);
+                            for (int j = 0; j < 8; ++j) {
+                                const float4 v = s4[j * 32];
+                                r[4 * j] = __float_as_uint(__uint_as_float(r[4 * j]) + v.x);
+                                r[4 * j + 1] = __float_as_uint(__uint_as_float(r[4 * j + 1]) + v.y);
+                                r[4 * j + 2] = __float_as_uint(__uint_as_float(r[4 * j + 2]) + v.z);
+                                r[4 * j + 3] = __float_as_uint(__uint_as_float(r[4 * j + 3]) + v.w);
+                            }
+                        }
+                        if (!last) {
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                s4[j * 32] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                                    __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+                        } else if (L.out[0][0] != nullptr) {   // (a launch may want the second copy only)
+                            store_chunk<EPI>(L, r, row_base, n0, c, cmax, cdiv, sch, scl, tile_atomic);
                         }
                     }
-                    if (!last) {
-#pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            s4[j * 32] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                                                __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
-                        continue;
-                    }
-                    const int cmax = min(32, ncols - c);
-                    store_chunk<EPI>(L, r, row_base, n0, c, cmax, cdiv, sch, scl, tile_atomic);
-                    if ((EPI == EPI_SPLIT_BF16 || EPI == EPI_TF32) && L.out2[0] != nullptr)
-                        store_chunk_site_major<EPI>(L, r, row, n0 + c, cmax);
+                    // the site-major copy's stores are warp-collective: every lane comes here
+                    if ((EPI == EPI_SPLIT_BF16 || EPI == EPI_TF32) && last && L.out2[0] != nullptr)
+                        store_chunk_site_major<EPI>(L, r, row, n0 + c, cmax, row_ok);
                 }
                 tc_fence_before();
                 __syncwarp();

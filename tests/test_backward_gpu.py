@@ -144,3 +144,19 @@ def test_backward_full_size(P):
         P.dmrg_sync_status()
         assert rel_per_op(dO.double().cpu().numpy(), dO_ref) <= TOL[prec], (prec, "dO")
         assert rel(dU.cpu().numpy(), dU_ref) <= TOL[prec], (prec, "dU")
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_backward_reproducible_bit_for_bit(P, prec):
+    # dU's reduction over every operator is split into parts with their own partial
+    # sums, added in a fixed order (no atomics): two calls agree bit for bit.
+    rng = np.random.default_rng(43)
+    m, d, mp, K = 96, 4, 80, 24
+    dev = torch.device("cuda")
+    U = torch.from_numpy(orthonormal_columns(rng, m * d, mp)).to(dev)
+    O = torch.from_numpy(rng.standard_normal((K, m, m))).to(dev, torch.float32)
+    G = torch.from_numpy(rng.standard_normal((K, mp, mp))).to(dev, torch.float32)
+    a = P.dmrg_rotate_ops_backward(U, O, G, d, prec)
+    b = P.dmrg_rotate_ops_backward(U, O, G, d, prec)
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
