@@ -579,6 +579,149 @@ __global__ void __launch_bounds__(kThreads) mgs_kernel(MgsArgs M) {
     }
 }
 
+// The same two passes of modified Gram-Schmidt with the rows kept in shared memory and
+// one grid barrier per group of kMgsG rows.  Rows are dealt to blocks in groups of
+// kMgsG consecutive rows (group G to block G mod gridDim); kMgsS warps share each row,
+// every warp owning a contiguous slice of its entries, so a block keeps all four SM
+// sub-partitions busy with FP64 work.  Step J: the block owning group J runs the
+// Gram-Schmidt steps of the group's rows among themselves and publishes them (and their
+// squared norms) to global memory; after the barrier every block stages the published
+// rows in shared memory and projects them, in order, out of its rows of later groups.
+// Each row receives the same projections in the same order as in mgs_kernel, with a
+// barrier every kMgsG rows instead of every row.  Small groups keep the FP64 work of a
+// step per SM, which lies on the critical path, short.
+constexpr int kMgsG = 2;                       // rows per group
+constexpr int kMgsS = 2;                       // warps per row
+constexpr int kMgsThreads = 32 * kMgsG * kMgsS;
+
+// Partial dot over this warp's slice [i0, i1) of two shared-memory rows.
+__device__ __forceinline__ double slice_dot(const double* x, const double* y, int i0, int i1,
+                                            int lane) {
+    double a0 = 0.0, a1 = 0.0;
+    int i = i0 + lane;
+    for (; i + 32 < i1; i += 64) {
+        a0 = fma(x[i], y[i], a0);
+        a1 = fma(x[i + 32], y[i + 32], a1);
+    }
+    for (; i < i1; i += 32) a0 = fma(x[i], y[i], a0);
+    double acc = a0 + a1;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+__global__ void __launch_bounds__(kMgsThreads) mgs_group_kernel(MgsArgs M, double* norms) {
+    extern __shared__ double own[];   // [owned group t][row][n], then pub[kMgsG][n]
+    __shared__ double part[kMgsG][kMgsS];
+    const int n = M.n, mp = M.mp, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = warp / kMgsS;       // row of the group
+    const int q = warp % kMgsS;       // slice of the row
+    const int slice = (n + kMgsS - 1) / kMgsS;
+    const int i0 = min(n, q * slice), i1 = min(n, i0 + slice);
+    const int ngroups = (mp + kMgsG - 1) / kMgsG;
+    const int nown = (ngroups - int(blockIdx.x) + int(gridDim.x) - 1) / int(gridDim.x);
+    double* pub = own + size_t(nown) * kMgsG * n;
+    const int last_own = int(blockIdx.x) + (nown - 1) * int(gridDim.x);
+    // sum of the kMgsS partial dots of row w (every thread of the block calls this)
+    auto row_sum = [&](double v) -> double {
+        if (lane == 0) part[w][q] = v;
+        __syncthreads();
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < kMgsS; ++k) t += part[w][k];
+        __syncthreads();
+        return t;
+    };
+    for (int t = 0; t < nown; ++t) {
+        const int r = (int(blockIdx.x) + t * int(gridDim.x)) * kMgsG + w;
+        if (r < mp)
+            for (int i = i0 + lane; i < i1; i += 32) own[(size_t(t) * kMgsG + w) * n + i] = M.Zt[size_t(r) * n + i];
+    }
+    __syncthreads();
+    unsigned gen = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int J = 0; J < ngroups; ++J) {
+            const int nj = min(kMgsG, mp - J * kMgsG);
+            if (J % int(gridDim.x) == int(blockIdx.x)) {
+                // the group's own Gram-Schmidt steps, then publication
+                double* grow = own + size_t(J / int(gridDim.x)) * kMgsG * n;
+                for (int jj = 0; jj < nj; ++jj) {
+                    const double* zj = grow + size_t(jj) * n;
+                    // |z_jj|^2 from the slices of row jj (all warps take part in the sums)
+                    double nn = 0.0;
+                    {
+                        const double v = (w == jj) ? slice_dot(zj, zj, i0, i1, lane) : 0.0;
+                        if (lane == 0) part[w][q] = v;
+                        __syncthreads();
+                        for (int k = 0; k < kMgsS; ++k) nn += part[jj][k];
+                        __syncthreads();
+                    }
+                    if (threadIdx.x == 0) __stcg(norms + J * kMgsG + jj, nn);
+                    double* zr = grow + size_t(w) * n;
+                    const bool mine = w > jj && w < nj;
+                    const double dsum = row_sum(mine ? slice_dot(zj, zr, i0, i1, lane) : 0.0);
+                    if (mine) {
+                        const double c = nn > 0.0 ? dsum / nn : 0.0;
+                        for (int i = i0 + lane; i < i1; i += 32) zr[i] = fma(-c, zj[i], zr[i]);
+                    }
+                    __syncthreads();
+                }
+                const int r = J * kMgsG + w;
+                if (w < nj)
+                    for (int i = i0 + lane; i < i1; i += 32)
+                        __stcg(M.Zt + size_t(r) * n + i, grow[size_t(w) * n + i]);
+            }
+            if (!grid_barrier(M.bar, gen, M.timeout_ns, M.status)) return;
+            if (last_own <= J) continue;   // no later rows here (block-uniform)
+            // stage the published group J in shared memory (the whole block, many loads in
+            // flight), then project it out of this block's rows of later groups
+            {
+                const double* src = M.Zt + size_t(J) * kMgsG * n;
+                const int total = nj * n;
+                if ((n & 1) == 0) {
+                    const double2* s2 = reinterpret_cast<const double2*>(src);
+                    double2* d2 = reinterpret_cast<double2*>(pub);
+                    for (int i = threadIdx.x; i < total / 2; i += kMgsThreads) d2[i] = __ldcg(s2 + i);
+                } else {
+                    for (int i = threadIdx.x; i < total; i += kMgsThreads) pub[i] = __ldcg(src + i);
+                }
+            }
+            __syncthreads();
+            for (int t = 0; t < nown; ++t) {
+                const int G2 = int(blockIdx.x) + t * int(gridDim.x);
+                if (G2 <= J) continue;   // block-uniform
+                const int r = G2 * kMgsG + w;
+                const bool live = r < mp;
+                double* zr = own + (size_t(t) * kMgsG + w) * n;
+                for (int jj = 0; jj < nj; ++jj) {
+                    const double* zj = pub + size_t(jj) * n;
+                    const double nn = __ldcg(norms + J * kMgsG + jj);
+                    const double dsum = row_sum(live ? slice_dot(zr, zj, i0, i1, lane) : 0.0);
+                    if (live) {
+                        const double c = nn > 0.0 ? dsum / nn : 0.0;
+                        for (int i = i0 + lane; i < i1; i += 32) zr[i] = fma(-c, zj[i], zr[i]);
+                    }
+                }
+            }
+            __syncthreads();   // pub is refilled in the next step
+        }
+        // normalise this block's rows
+        for (int t = 0; t < nown; ++t) {
+            const int r = (int(blockIdx.x) + t * int(gridDim.x)) * kMgsG + w;
+            double* zr = own + (size_t(t) * kMgsG + w) * n;
+            const double ss = row_sum(r < mp ? slice_dot(zr, zr, i0, i1, lane) : 0.0);
+            const double inv = ss > 0.0 ? 1.0 / sqrt(ss) : 0.0;
+            if (r < mp)
+                for (int i = i0 + lane; i < i1; i += 32) zr[i] *= inv;
+        }
+        __syncthreads();
+    }
+    for (int t = 0; t < nown; ++t) {
+        const int r = (int(blockIdx.x) + t * int(gridDim.x)) * kMgsG + w;
+        if (r < mp)
+            for (int i = i0 + lane; i < i1; i += 32) M.Zt[size_t(r) * n + i] = own[(size_t(t) * kMgsG + w) * n + i];
+    }
+}
+
 // ---------------------------------------------------------------- 5. back-transformation
 // One block of kBackSplit warps per eigenvector.  The vector lives in shared memory and
 // each warp owns a fixed set of its entries (alternate 32-entry blocks), so the warps
@@ -804,8 +947,41 @@ dmrg_status tridiag_eigen(dmrg_handle h, int64_t n64, int64_t mp64, char* ws, do
         return cudaGetLastError();
     });
     if (err != cudaSuccess) return cuda_fail(h, err, "inverse iteration");
-    // 4. Gram-Schmidt
+    // 4. Gram-Schmidt: rows in shared memory, one barrier per group of kMgsG rows, when
+    //    every block's rows fit (else the row-per-barrier form through L2)
+    bool grouped_done = false;
     {
+        const int ngroups = (mp + kMgsG - 1) / kMgsG;
+        int dev = 0, sms = 0, coop = 0, per_sm = 0;
+        err = cudaGetDevice(&dev);
+        if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (err == cudaSuccess) err = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        if (err != cudaSuccess) return cuda_fail(h, err, "orthogonalisation set-up");
+        // as many blocks as groups, up to two per SM (a block holds all its groups' rows)
+        const int grid = std::max(1, std::min(ngroups, 2 * sms));
+        const int nown = (ngroups + grid - 1) / grid;
+        const size_t smem = size_t(nown + 1) * kMgsG * n * 8;   // own rows + the published ones
+        if (coop && smem <= 200 * 1024) {
+            err = cudaFuncSetAttribute(mgs_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            if (err == cudaSuccess)
+                err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mgs_group_kernel, kMgsThreads, smem);
+            if (err != cudaSuccess) return cuda_fail(h, err, "orthogonalisation set-up");
+            if (per_sm * sms >= grid) {
+                err = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
+                if (err != cudaSuccess) return cuda_fail(h, err, "orthogonalisation set-up");
+                MgsArgs M{Zt, bar, h->d_status, timeout_ns(h), n, mp};
+                double* norms = lu[0];   // free once the inverse iteration is done
+                err = timed_launch(h, "trunc_orthogonalise_grouped", s, [&] {
+                    void* args[] = {&M, &norms};
+                    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(mgs_group_kernel),
+                                                       dim3(unsigned(grid)), dim3(kMgsThreads), args, smem, s);
+                });
+                if (err != cudaSuccess) return cuda_fail(h, err, "orthogonalisation");
+                grouped_done = true;
+            }
+        }
+    }
+    if (!grouped_done) {
         int grid = 1;
         err = coop_grid(reinterpret_cast<const void*>(mgs_kernel), 0, std::max(1, mp), &grid, 1);
         if (err == cudaSuccess) err = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
