@@ -132,7 +132,9 @@ __device__ __forceinline__ void fence_proxy_async_shared() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-template <int MODE, int EPI, int RB, bool CONV>
+// SITE: the launch also writes the site-major second copy (TcLaunch::out2); a separate
+// instantiation, so that the other launches do not carry its registers.
+template <int MODE, int EPI, int RB, bool CONV, bool SITE>
 __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
     tc_gemm_pair_kernel(const __grid_constant__ TcLaunch L, int stages, int bh_smem) {
     constexpr int kRowBytes = RB;
@@ -463,7 +465,7 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                         }
                     }
                     // the site-major copy's stores are warp-collective: every lane comes here
-                    if ((EPI == EPI_SPLIT_BF16 || EPI == EPI_TF32) && last && L.out2[0] != nullptr)
+                    if (SITE && (EPI == EPI_SPLIT_BF16 || EPI == EPI_TF32) && last)
                         store_chunk_site_major<EPI>(L, r, row, n0 + c, cmax, row_ok);
                 }
                 tc_fence_before();
@@ -521,9 +523,11 @@ int clusters_that_fit(const void* kernel, const cudaLaunchConfig_t& cfg) {
 template <int MODE, int EPI>
 cudaError_t launch_pair(const TcLaunch& L, int stages, int grid, int bh_smem, size_t smem,
                         cudaStream_t s) {
-    auto k = L.convert_a ? tc_gemm_pair_kernel<MODE, EPI, 128, true>
-             : L.row_bytes == 64 ? tc_gemm_pair_kernel<MODE, EPI, 64, false>
-                                 : tc_gemm_pair_kernel<MODE, EPI, 128, false>;
+    constexpr bool kSiteEpi = (EPI == EPI_SPLIT_BF16 || EPI == EPI_TF32);
+    auto k = L.convert_a ? tc_gemm_pair_kernel<MODE, EPI, 128, true, false>
+             : L.row_bytes == 64 ? tc_gemm_pair_kernel<MODE, EPI, 64, false, false>
+                                 : tc_gemm_pair_kernel<MODE, EPI, 128, false, false>;
+    if (kSiteEpi && L.out2[0] != nullptr) k = tc_gemm_pair_kernel<MODE, EPI, 128, false, kSiteEpi>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -565,6 +569,9 @@ cudaError_t tc_gemm_launch_pair(TcMode mode, TcEpi epi, const TcLaunch& L, int s
     if (L.total_tiles <= 0) return cudaSuccess;
     if (L.table != nullptr || L.nprob < 1 || L.nprob > kMaxInlineProblems) return cudaErrorInvalidValue;
     if (L.convert_a && (L.row_bytes != 128 || mode == TC_BF16)) return cudaErrorInvalidValue;
+    if (L.out2[0] != nullptr && (L.row_bytes != 128 || L.convert_a ||
+                                 !(epi == EPI_SPLIT_BF16 || epi == EPI_TF32)))
+        return cudaErrorInvalidValue;
     int bn = 32;
     for (int i = 0; i < L.nprob; ++i) bn = std::max(bn, L.inline_prob[i].tile_n);
     const int bh = bn / 2;
