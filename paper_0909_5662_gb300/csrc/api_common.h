@@ -78,7 +78,9 @@ WsLayout tridiag_layout(int64_t n, int64_t mp);
 dmrg_status tridiag_eigen(dmrg_handle h, int64_t n, int64_t mp, char* ws, double* U, double* lambda,
                           double* eps, cudaStream_t s);
 
+// two_per_sm: the variant with 128-column accumulators and 64-byte rows, two CTAs per
+// SM (grid may then be twice the SM count; needs row_bytes 64 and bn_smem <= 128).
 cudaError_t tc_gemm_launch_grouped(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
-                                   int bn_smem, cudaStream_t s);
+                                   int bn_smem, cudaStream_t s, bool two_per_sm = false);
 
 }  // namespace dmrg

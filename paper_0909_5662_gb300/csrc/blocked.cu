@@ -62,6 +62,12 @@ struct TcTables {
     int32_t* d_map_second = nullptr;
     int tiles_first = 0, tiles_second = 0;
     int bn_first = 16, bn_second = 16;
+    // first product with every N tile <= 128: 64-byte rows and two CTAs per SM (its
+    // reductions are a block sector, at most a few k-blocks, so its tiles are short and
+    // two CTAs overlap each other's per-tile latency; the second product, reducing over
+    // a whole [B a] sector, keeps 128-byte rows and one CTA per SM, which measured faster)
+    bool two_per_sm = false;
+    int row_bytes = 128;   // of the first product
 };
 
 // ---- fused small-sector path
@@ -576,7 +582,7 @@ dmrg_status upload_static(dmrg_blocked_plan_s& pl) {
             j.dst0 = reinterpret_cast<void*>(intptr_t(eo * int64_t(es)));
             j.dst1 = li == 0 ? reinterpret_cast<void*>(intptr_t(half_bytes + eo * int64_t(es))) : nullptr;
             j.block_start = blocks;
-            pack_prepare(j);
+            pack_prepare_grouped(j);
             blocks += pack_blocks_for(j);
         }
         if (li == 0) pl.pack_blocks = blocks;
@@ -614,6 +620,10 @@ dmrg_status tc_tables(dmrg_blocked_plan_s& pl, void* ws, bool tf32, TcTables*& o
     const int S = pl.S, d = pl.d;
     std::vector<TcProblem> first(pl.first.size()), second(pl.second.size());
     TcTables T;
+    int bn_max = 16;
+    for (const First& f : pl.first) bn_max = std::max(bn_max, choose_tile_n(pl.km[f.Q], 256));
+    T.two_per_sm = bn_max <= 128 && tc_stages_two_per_sm(mode, bn_max) >= 2;
+    T.row_bytes = T.two_per_sm ? 64 : 128;
     int tiles = 0;
     for (size_t i = 0; i < pl.first.size(); ++i) {
         const First& f = pl.first[i];
@@ -626,7 +636,7 @@ dmrg_status tc_tables(dmrg_blocked_plan_s& pl, void* ws, bool tf32, TcTables*& o
         TcOperand B{ptr(hi, bo), ptr(lo, bo), pl.km[f.Q], pl.bm[f.q],
                     ld_for(pl.bm[f.q], tf32 ? 4 : 8)};
         TcProblem& P = first[i];
-        if (!make_problem(P, mode, A, B, 256, 1)) return DMRG_ERR_CUDA;
+        if (!make_problem(P, mode, A, B, 256, 1, T.row_bytes)) return DMRG_ERR_CUDA;
         TcScatter& sc = P.sc[0];
         sc.out_off = L.t2_off[f.p2] + pl.segoff[size_t(f.Q2) * d + f.s];
         sc.rows_per_op = int32_t(pl.bm[f.q2]);
@@ -947,11 +957,13 @@ dmrg_status dmrg_rotate_ops_blocked(dmrg_handle h, dmrg_blocked_plan pl, const d
         L1.out[0][1] = lo;
         L1.status = h->d_status;
         L1.timeout_ns = timeout_ns(h);
-        L1.row_bytes = 128;
-        const int st1 = tc_max_stages(mode, T->bn_first);
+        L1.row_bytes = T->row_bytes;
+        const bool two = T->two_per_sm;
+        const int st1 = two ? tc_stages_two_per_sm(mode, T->bn_first)
+                            : std::min(tc_max_stages(mode, T->bn_first), 4);
         e = timed_launch(h, "blk_tc_first_product", cs, [&] {
-            return tc_gemm_launch_grouped(mode, tf32 ? EPI_TF32 : EPI_SPLIT_BF16, L1, std::min(st1, 4),
-                                          h->num_sms, T->bn_first, cs);
+            return tc_gemm_launch_grouped(mode, tf32 ? EPI_TF32 : EPI_SPLIT_BF16, L1, st1,
+                                          (two ? 2 : 1) * h->num_sms, T->bn_first, cs, two);
         });
         if (e != cudaSuccess) return cuda_fail(h, e, "first product");
         TcLaunch L2{};
@@ -963,10 +975,9 @@ dmrg_status dmrg_rotate_ops_blocked(dmrg_handle h, dmrg_blocked_plan pl, const d
         L2.status = h->d_status;
         L2.timeout_ns = timeout_ns(h);
         L2.row_bytes = 128;
-        const int st2 = tc_max_stages(mode, T->bn_second);
+        const int st2 = std::min(tc_max_stages(mode, T->bn_second), 4);
         e = timed_launch(h, "blk_tc_second_product", cs, [&] {
-            return tc_gemm_launch_grouped(mode, EPI_F32, L2, std::min(st2, 4), h->num_sms,
-                                          T->bn_second, cs);
+            return tc_gemm_launch_grouped(mode, EPI_F32, L2, st2, h->num_sms, T->bn_second, cs);
         });
         return cuda_fail(h, e, "second product");
     });

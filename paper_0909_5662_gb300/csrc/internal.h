@@ -164,6 +164,9 @@ struct TcOperand {
 cudaError_t tc_gemm_launch(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
                            cudaStream_t s);
 int tc_max_stages(TcMode mode, int tile_n_max, int row_bytes = 128);
+// One-CTA kernel with two CTAs per SM (N tiles <= 128, 64-byte rows): the deepest
+// pipeline that fits, or 0 if none does.
+int tc_stages_two_per_sm(TcMode mode, int tile_n_max);
 // CTA-pair form: problems made with make_problem(..., pair_form = 1); `grid` counts
 // CTAs (rounded down to whole pairs, capped by the pairs that fit at once).
 cudaError_t tc_gemm_launch_pair(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
@@ -221,8 +224,13 @@ struct PackJob {
     int32_t fastdiv;
     int32_t s_cols, s_rpo, s_rdiv;
     uint64_t m_cols, m_rpo, m_rdiv;
+    // Set by pack_prepare_grouped (grouped launches): the job's rows are contiguous runs
+    // of its source (s_c = 1, rdiv = 1) and are copied one warp per row.
+    int32_t rowwise, pad_;
 };
 void pack_prepare(PackJob& j);
+// pack_prepare, and for grouped launches the row-by-row copy of contiguous rows.
+void pack_prepare_grouped(PackJob& j);
 cudaError_t pack_launch(const PackJob* jobs_host, int njobs, PackJob* jobs_dev_or_null,
                         cudaStream_t s);
 int64_t pack_blocks_for(const PackJob& j);

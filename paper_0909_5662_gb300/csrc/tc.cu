@@ -33,17 +33,20 @@ using namespace tcdev;
 constexpr int kThreads = 320;        // 10 warps: producer, MMA issuer, 8 epilogue warps
 constexpr int kEpiWarps = 8;         // two per TMEM lane quadrant, alternate 32-column chunks
 constexpr int kBM = 128;             // rows per tile (TMEM lanes)
-constexpr uint32_t kTmemCols = 512;  // two accumulators of up to 256 FP32 columns
-constexpr uint32_t kAccStride = 256;
+// ACC (template): FP32 columns per TMEM accumulator; two accumulators.  256 is the
+// default; 128 (N tiles of at most 128) halves the TMEM and, with 64-byte rows, the
+// shared memory, so that two CTAs share an SM and overlap each other's per-tile latency.
 // Winding down after an expired wait: copies and MMAs already issued are waited for
 // with this fixed limit, whatever limit the caller chose for the main waits.
 constexpr uint64_t kDrainTimeoutNs = 2000000000ull;
 
 // RB: bytes of reduction per shared-memory row and k-block (128 -> 128-byte swizzle,
 // 64 -> 64-byte swizzle with half-depth k-blocks and twice the pipeline stages).
-template <int MODE, int EPI, int RB>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int MODE, int EPI, int RB, int ACC>
+__global__ void __launch_bounds__(kThreads, ACC == 128 ? 2 : 1)
     tc_gemm_kernel(const __grid_constant__ TcLaunch L, int stages, int bn_smem) {
+    constexpr uint32_t kTmemCols = 2 * ACC;
+    constexpr uint32_t kAccStride = ACC;
     constexpr int kRowBytes = RB;
     constexpr bool kSplit = (MODE == TC_BF16X3);
     constexpr int kElem = (MODE == TC_TF32) ? 4 : 2;
@@ -343,6 +346,59 @@ __device__ __forceinline__ void pack_general(const PackJob& j, int64_t blk) {
     }
 }
 
+// Rows whose elements are a contiguous run of the source (s_c = 1, rdiv = 1): one warp
+// per row, kPackRowWarps rows per block, lanes along the row, so loads and stores are
+// coalesced and the row split costs one division per row instead of per element.
+constexpr int kPackRows = 32;   // rows per block (four per warp)
+
+__device__ __forceinline__ void pack_rows(const PackJob& j, int64_t blk) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t cols = j.cols;
+    for (int rr = warp; rr < kPackRows; rr += kPackThreads / 32) {
+        const int64_t r = blk * kPackRows + rr;
+        if (r >= j.rows) break;
+        int64_t g, x;
+        if (j.fastdiv) {
+            const uint32_t ru = uint32_t(r);
+            const uint32_t gu = uint32_t((uint64_t(ru) * j.m_rpo) >> j.s_rpo);
+            g = gu;
+            x = ru - gu * uint32_t(j.rows_per_op);
+        } else {
+            g = r / j.rows_per_op;
+            x = r - g * j.rows_per_op;
+        }
+        const int64_t src = j.src_off + (j.op_off ? j.op_off[g] : g * j.s_op) + x * j.s_r_hi;
+        const int64_t dst = r * j.ld;
+        for (int64_t c0 = 0; c0 < cols; c0 += 128) {
+            if (j.src_f64) {
+                double v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t c = c0 + lane + 32 * u;
+                    v[u] = c < cols ? static_cast<const double*>(j.src)[src + c] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t c = c0 + lane + 32 * u;
+                    if (c < cols) pack_store(j, dst + c, v[u]);
+                }
+            } else {
+                float v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t c = c0 + lane + 32 * u;
+                    v[u] = c < cols ? static_cast<const float*>(j.src)[src + c] : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t c = c0 + lane + 32 * u;
+                    if (c < cols) pack_store(j, dst + c, v[u]);
+                }
+            }
+        }
+    }
+}
+
 // The block's job is found once (thread 0), copied word by word into shared memory by
 // the block, resolved (relative addresses) by thread 0, and read from there.
 __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constant__ PackLaunch L) {
@@ -377,7 +433,8 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constan
         sj.dst1 = sj.dst1 ? L.ws_base + reinterpret_cast<intptr_t>(sj.dst1) : nullptr;
     }
     __syncthreads();
-    pack_general(sj, int64_t(b - sj.block_start));
+    if (sj.rowwise) pack_rows(sj, int64_t(b - sj.block_start));
+    else pack_general(sj, int64_t(b - sj.block_start));
 }
 
 // Contiguous fast path: one 8-element unit v of a job whose source rows are
@@ -591,8 +648,10 @@ bool pack_vec8_ok(const PackJob& j) {
 
 template <int MODE, int EPI>
 cudaError_t launch_one(const TcLaunch& L, int stages, int grid, int bn_smem, size_t smem,
-                       cudaStream_t s) {
-    auto k = L.row_bytes == 64 ? tc_gemm_kernel<MODE, EPI, 64> : tc_gemm_kernel<MODE, EPI, 128>;
+                       cudaStream_t s, bool two_per_sm = false) {
+    auto k = two_per_sm ? tc_gemm_kernel<MODE, EPI, 64, 128>
+             : L.row_bytes == 64 ? tc_gemm_kernel<MODE, EPI, 64, 256>
+                                 : tc_gemm_kernel<MODE, EPI, 128, 256>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -622,6 +681,16 @@ int tc_max_stages(TcMode mode, int tile_n_max, int row_bytes) {
     return s;
 }
 
+// Shared memory of one CTA when two share an SM (228 KB per SM, 1 KB reserved per CTA).
+constexpr size_t kTwoPerSmSmem = 112 * 1024;
+
+int tc_stages_two_per_sm(TcMode mode, int tile_n_max) {
+    if (tile_n_max > 128 || tc_smem_bytes(mode, 2, tile_n_max, 64) > kTwoPerSmSmem) return 0;
+    int s = 2;
+    while (s < 8 && tc_smem_bytes(mode, s + 1, tile_n_max, 64) <= kTwoPerSmSmem) ++s;
+    return s;
+}
+
 cudaError_t tc_gemm_launch(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
                            cudaStream_t s) {
     if (L.total_tiles <= 0) return cudaSuccess;
@@ -648,13 +717,15 @@ cudaError_t tc_gemm_launch(TcMode mode, TcEpi epi, const TcLaunch& L, int stages
 }
 
 cudaError_t tc_gemm_launch_grouped(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,
-                                   int bn_smem, cudaStream_t s) {
+                                   int bn_smem, cudaStream_t s, bool two_per_sm) {
     if (L.total_tiles <= 0) return cudaSuccess;
     const size_t smem = tc_smem_bytes(mode, stages, bn_smem, L.row_bytes);
     if (smem > 232448) return cudaErrorInvalidConfiguration;
+    if (two_per_sm && (L.row_bytes != 64 || bn_smem > 128 || smem > kTwoPerSmSmem))
+        return cudaErrorInvalidConfiguration;
     grid = std::max(1, std::min(grid, L.total_tiles));
 #define DMRG_TC_CASE(M, E) \
-    if (mode == M && epi == E) return launch_one<M, E>(L, stages, grid, bn_smem, smem, s);
+    if (mode == M && epi == E) return launch_one<M, E>(L, stages, grid, bn_smem, smem, s, two_per_sm);
     DMRG_TC_CASE(TC_BF16X3, EPI_SPLIT_BF16)
     DMRG_TC_CASE(TC_BF16X3, EPI_F32)
     DMRG_TC_CASE(TC_BF16X3, EPI_F32_ATOMIC)
@@ -688,7 +759,13 @@ void pack_prepare(PackJob& j) {
     div_magic(j.rdiv, j.m_rdiv, j.s_rdiv);
 }
 
+void pack_prepare_grouped(PackJob& j) {
+    pack_prepare(j);
+    j.rowwise = (j.s_c == 1 && j.rdiv == 1 && j.mode != kPackZero && j.cols >= 16) ? 1 : 0;
+}
+
 int64_t pack_blocks_for(const PackJob& j) {
+    if (j.rowwise) return (j.rows + kPackRows - 1) / kPackRows;
     const int64_t per = int64_t(kPackThreads) * kPackElems;
     return (j.rows * j.cols + per - 1) / per;
 }
