@@ -193,7 +193,7 @@ def run_reference(args):
         rate = n / (time.perf_counter() - t0)
     budget_s = 90.0
     n = int(max(1, min(K_PER_GPU, rate * budget_s / max(args.steps, 1))))
-    if n >= cores:
+    if cores <= n < K_PER_GPU:
         n = n // cores * cores   # whole rounds of the UMD split
     t_total = 0.0
     for _ in range(args.steps):
