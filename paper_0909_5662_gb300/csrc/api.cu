@@ -389,6 +389,10 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     L1.row_bytes = c1.row_bytes;
     L1.chunk_scratch = L1.inline_prob[0].kb_chunk ? chain_scr : nullptr;
     L1.convert_a = convert_a ? 1 : 0;
+    // The packing pass wrote the operators in row order and the rows it wrote last are
+    // the ones still in L2: the first product starts from the last M tile.  It then leaves
+    // the first operators' T rows in L2 for the second product, which starts there.
+    L1.reverse_m = convert_a ? 0 : 1;
     e = timed_launch(h, "tc_gemm_first_product", s, [&] {
         const TcEpi epi = split ? EPI_SPLIT_BF16 : EPI_TF32;
         return c1.pair ? tc_gemm_launch_pair(mode, epi, L1, c1.stages, grid1, s)

@@ -137,6 +137,8 @@ struct TcLaunch {
                             // sums (nullptr: every tile is one accumulation chain)
     int32_t convert_a;      // CTA-pair kernel: every problem's A map is an FP32 source that
                             // the converter warps turn into the MMA operand (f32_source)
+    int32_t reverse_m;      // 1: each problem's M tiles run from the last to the first (the
+                            // rows a preceding kernel wrote last are the likeliest in L2)
     // CTA-pair kernel, EPI_SPLIT_BF16 / EPI_TF32: a second, site-major copy of the result
     // (null: none).  Element (row R, column c) also goes to
     //   out2 + (R / o2_rows_per_op) * o2_s_op + (R % o2_rows_per_op) * o2_s_row

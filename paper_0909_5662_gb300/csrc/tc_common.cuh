@@ -44,6 +44,7 @@ __device__ __forceinline__ Decoded decode_tile(const TcLaunch& L, int t, int ele
     const int rem = local - ks * per_split;
     d.mt = rem / P->n_tiles;
     d.nt = rem - d.mt * P->n_tiles;
+    if (L.reverse_m) d.mt = P->m_tiles - 1 - d.mt;
     d.mt += P->m_tile0;
     d.kb_per_batch = (P->Kred + elems_per_row - 1) / elems_per_row;
     const int kb_total = d.kb_per_batch * P->nbatch;
