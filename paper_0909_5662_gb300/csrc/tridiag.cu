@@ -35,6 +35,8 @@ namespace {
 using dmrg::GridBarrier;
 using dmrg::block_sum_all;
 using dmrg::grid_barrier;
+using dmrg::globaltimer_ns;
+using dmrg::ld_acquire_gpu;
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
@@ -580,19 +582,33 @@ __global__ void __launch_bounds__(kThreads) mgs_kernel(MgsArgs M) {
 }
 
 // The same two passes of modified Gram-Schmidt with the rows kept in shared memory and
-// one grid barrier per group of kMgsG rows.  Rows are dealt to blocks in groups of
-// kMgsG consecutive rows (group G to block G mod gridDim); kMgsS warps share each row,
-// every warp owning a contiguous slice of its entries, so a block keeps all four SM
-// sub-partitions busy with FP64 work.  Step J: the block owning group J runs the
-// Gram-Schmidt steps of the group's rows among themselves and publishes them (and their
-// squared norms) to global memory; after the barrier every block stages the published
-// rows in shared memory and projects them, in order, out of its rows of later groups.
-// Each row receives the same projections in the same order as in mgs_kernel, with a
-// barrier every kMgsG rows instead of every row.  Small groups keep the FP64 work of a
-// step per SM, which lies on the critical path, short.
+// no grid-wide barrier.  Rows are dealt to blocks in groups of kMgsG consecutive rows
+// (group G to block G mod gridDim); kMgsS warps share each row, every warp owning a
+// contiguous slice of its entries, so a block keeps all four SM sub-partitions busy with
+// FP64 work.  Each block walks the groups in order: when group J is its own it runs the
+// Gram-Schmidt steps of the group's rows among themselves, publishes them and their
+// squared norms, and raises the group's flag; then, if it holds rows of later groups,
+// it waits for group J's flag, stages the published rows in shared memory and projects
+// them, in order, out of those rows.  Each row receives the same projections in the same
+// order as in mgs_kernel; a block waits only for the group it needs next, so the
+// critical path is one group's hand-on per group instead of a grid barrier per row.
+// Every pass publishes into its own buffer, so a block still reading a group of the first
+// pass never sees the second pass's rows.  Waits are bounded: on expiry a block records
+// the timeout, raises the abort word and returns, and the others return at their next
+// wait.
 constexpr int kMgsG = 2;                       // rows per group
 constexpr int kMgsS = 2;                       // warps per row
 constexpr int kMgsThreads = 32 * kMgsG * kMgsS;
+
+struct MgsFlowArgs {
+    double* Zt;           // mp x n, row j = eigenvector j (input and output)
+    double* pub[2];       // per pass: published rows, mp x n
+    double* norms[2];     // per pass: squared norms of the published rows
+    unsigned* flags;      // [2][ngroups] publication flags, then the abort word; zeroed
+    unsigned* status;
+    uint64_t timeout_ns;
+    int n, mp;
+};
 
 // Partial dot over this warp's slice [i0, i1) of two shared-memory rows.
 __device__ __forceinline__ double slice_dot(const double* x, const double* y, int i0, int i1,
@@ -609,7 +625,42 @@ __device__ __forceinline__ double slice_dot(const double* x, const double* y, in
     return acc;
 }
 
-__global__ void __launch_bounds__(kMgsThreads) mgs_group_kernel(MgsArgs M, double* norms) {
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Thread 0 waits (bounded) until *flag is set; the block follows its verdict.
+__device__ bool wait_flag(unsigned* flag, unsigned* abort_word, uint64_t timeout_ns,
+                          unsigned* status) {
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        ok = 1;
+        if (ld_acquire_gpu(flag) == 0u) {
+            const uint64_t t0 = globaltimer_ns();
+            uint32_t spins = 0;
+            while (ld_acquire_gpu(flag) == 0u) {
+                if ((++spins & 31u) == 0) {
+                    if (ld_acquire_gpu(abort_word) != 0u) {
+                        ok = 0;
+                        break;
+                    }
+                    if (globaltimer_ns() - t0 > timeout_ns) {
+                        atomicOr(status, DMRG_DEV_ERR_TIMEOUT);
+                        atomicExch(abort_word, 1u);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const bool r = ok != 0;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kMgsThreads) mgs_flow_kernel(MgsFlowArgs M) {
     extern __shared__ double own[];   // [owned group t][row][n], then pub[kMgsG][n]
     __shared__ double part[kMgsG][kMgsS];
     const int n = M.n, mp = M.mp, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -619,8 +670,9 @@ __global__ void __launch_bounds__(kMgsThreads) mgs_group_kernel(MgsArgs M, doubl
     const int i0 = min(n, q * slice), i1 = min(n, i0 + slice);
     const int ngroups = (mp + kMgsG - 1) / kMgsG;
     const int nown = (ngroups - int(blockIdx.x) + int(gridDim.x) - 1) / int(gridDim.x);
-    double* pub = own + size_t(nown) * kMgsG * n;
+    double* stage = own + size_t(nown) * kMgsG * n;
     const int last_own = int(blockIdx.x) + (nown - 1) * int(gridDim.x);
+    unsigned* abort_word = M.flags + 2 * ngroups;
     // sum of the kMgsS partial dots of row w (every thread of the block calls this)
     auto row_sum = [&](double v) -> double {
         if (lane == 0) part[w][q] = v;
@@ -637,16 +689,17 @@ __global__ void __launch_bounds__(kMgsThreads) mgs_group_kernel(MgsArgs M, doubl
             for (int i = i0 + lane; i < i1; i += 32) own[(size_t(t) * kMgsG + w) * n + i] = M.Zt[size_t(r) * n + i];
     }
     __syncthreads();
-    unsigned gen = 0;
     for (int pass = 0; pass < 2; ++pass) {
+        double* pubz = M.pub[pass];
+        double* norms = M.norms[pass];
+        unsigned* flags = M.flags + pass * ngroups;
         for (int J = 0; J < ngroups; ++J) {
             const int nj = min(kMgsG, mp - J * kMgsG);
             if (J % int(gridDim.x) == int(blockIdx.x)) {
-                // the group's own Gram-Schmidt steps, then publication
+                // the group's own Gram-Schmidt steps, then publication and the flag
                 double* grow = own + size_t(J / int(gridDim.x)) * kMgsG * n;
                 for (int jj = 0; jj < nj; ++jj) {
                     const double* zj = grow + size_t(jj) * n;
-                    // |z_jj|^2 from the slices of row jj (all warps take part in the sums)
                     double nn = 0.0;
                     {
                         const double v = (w == jj) ? slice_dot(zj, zj, i0, i1, lane) : 0.0;
@@ -665,24 +718,26 @@ __global__ void __launch_bounds__(kMgsThreads) mgs_group_kernel(MgsArgs M, doubl
                     }
                     __syncthreads();
                 }
-                const int r = J * kMgsG + w;
                 if (w < nj)
                     for (int i = i0 + lane; i < i1; i += 32)
-                        __stcg(M.Zt + size_t(r) * n + i, grow[size_t(w) * n + i]);
+                        __stcg(pubz + size_t(J * kMgsG + w) * n + i, grow[size_t(w) * n + i]);
+                __threadfence();
+                __syncthreads();
+                if (threadIdx.x == 0) st_release_gpu(flags + J, 1u);
             }
-            if (!grid_barrier(M.bar, gen, M.timeout_ns, M.status)) return;
             if (last_own <= J) continue;   // no later rows here (block-uniform)
-            // stage the published group J in shared memory (the whole block, many loads in
-            // flight), then project it out of this block's rows of later groups
+            if (!wait_flag(flags + J, abort_word, M.timeout_ns, M.status)) return;
+            // stage the published group J in shared memory, then project it out of this
+            // block's rows of later groups
             {
-                const double* src = M.Zt + size_t(J) * kMgsG * n;
+                const double* src = pubz + size_t(J) * kMgsG * n;
                 const int total = nj * n;
                 if ((n & 1) == 0) {
                     const double2* s2 = reinterpret_cast<const double2*>(src);
-                    double2* d2 = reinterpret_cast<double2*>(pub);
+                    double2* d2 = reinterpret_cast<double2*>(stage);
                     for (int i = threadIdx.x; i < total / 2; i += kMgsThreads) d2[i] = __ldcg(s2 + i);
                 } else {
-                    for (int i = threadIdx.x; i < total; i += kMgsThreads) pub[i] = __ldcg(src + i);
+                    for (int i = threadIdx.x; i < total; i += kMgsThreads) stage[i] = __ldcg(src + i);
                 }
             }
             __syncthreads();
@@ -693,7 +748,7 @@ __global__ void __launch_bounds__(kMgsThreads) mgs_group_kernel(MgsArgs M, doubl
                 const bool live = r < mp;
                 double* zr = own + (size_t(t) * kMgsG + w) * n;
                 for (int jj = 0; jj < nj; ++jj) {
-                    const double* zj = pub + size_t(jj) * n;
+                    const double* zj = stage + size_t(jj) * n;
                     const double nn = __ldcg(norms + J * kMgsG + jj);
                     const double dsum = row_sum(live ? slice_dot(zr, zj, i0, i1, lane) : 0.0);
                     if (live) {
@@ -702,7 +757,7 @@ __global__ void __launch_bounds__(kMgsThreads) mgs_group_kernel(MgsArgs M, doubl
                     }
                 }
             }
-            __syncthreads();   // pub is refilled in the next step
+            __syncthreads();   // the staging buffer is refilled for the next group
         }
         // normalise this block's rows
         for (int t = 0; t < nown; ++t) {
@@ -947,8 +1002,8 @@ dmrg_status tridiag_eigen(dmrg_handle h, int64_t n64, int64_t mp64, char* ws, do
         return cudaGetLastError();
     });
     if (err != cudaSuccess) return cuda_fail(h, err, "inverse iteration");
-    // 4. Gram-Schmidt: rows in shared memory, one barrier per group of kMgsG rows, when
-    //    every block's rows fit (else the row-per-barrier form through L2)
+    // 4. Gram-Schmidt: rows in shared memory, groups handed on by flags, when every
+    //    block's rows fit (else the row-per-barrier form through L2)
     bool grouped_done = false;
     {
         const int ngroups = (mp + kMgsG - 1) / kMgsG;
@@ -957,23 +1012,36 @@ dmrg_status tridiag_eigen(dmrg_handle h, int64_t n64, int64_t mp64, char* ws, do
         if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (err == cudaSuccess) err = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
         if (err != cudaSuccess) return cuda_fail(h, err, "orthogonalisation set-up");
-        // as many blocks as groups, up to two per SM (a block holds all its groups' rows)
+        // as many blocks as groups, up to two per SM (a block holds all its groups' rows);
+        // the flag waits need every block resident: a cooperative launch
         const int grid = std::max(1, std::min(ngroups, 2 * sms));
         const int nown = (ngroups + grid - 1) / grid;
-        const size_t smem = size_t(nown + 1) * kMgsG * n * 8;   // own rows + the published ones
-        if (coop && smem <= 200 * 1024) {
-            err = cudaFuncSetAttribute(mgs_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        const size_t smem = size_t(nown + 1) * kMgsG * n * 8;   // own rows + the staged ones
+        // buffers free once the inverse iteration is done: published rows of the two
+        // passes, their squared norms, the flags
+        const bool fits = size_t(2 * mp + 2 * ngroups + 1) * 8 <= size_t(mp) * n * 8;
+        if (coop && smem <= 200 * 1024 && fits) {
+            err = cudaFuncSetAttribute(mgs_flow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
             if (err == cudaSuccess)
-                err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mgs_group_kernel, kMgsThreads, smem);
+                err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mgs_flow_kernel, kMgsThreads, smem);
             if (err != cudaSuccess) return cuda_fail(h, err, "orthogonalisation set-up");
             if (per_sm * sms >= grid) {
-                err = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
+                MgsFlowArgs M{};
+                M.Zt = Zt;
+                M.pub[0] = lu[0];
+                M.pub[1] = lu[1];
+                M.norms[0] = lu[2];
+                M.norms[1] = lu[2] + mp;
+                M.flags = reinterpret_cast<unsigned*>(lu[3]);
+                M.status = h->d_status;
+                M.timeout_ns = timeout_ns(h);
+                M.n = n;
+                M.mp = mp;
+                err = cudaMemsetAsync(M.flags, 0, size_t(2 * ngroups + 1) * sizeof(unsigned), s);
                 if (err != cudaSuccess) return cuda_fail(h, err, "orthogonalisation set-up");
-                MgsArgs M{Zt, bar, h->d_status, timeout_ns(h), n, mp};
-                double* norms = lu[0];   // free once the inverse iteration is done
-                err = timed_launch(h, "trunc_orthogonalise_grouped", s, [&] {
-                    void* args[] = {&M, &norms};
-                    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(mgs_group_kernel),
+                err = timed_launch(h, "trunc_orthogonalise", s, [&] {
+                    void* args[] = {&M};
+                    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(mgs_flow_kernel),
                                                        dim3(unsigned(grid)), dim3(kMgsThreads), args, smem, s);
                 });
                 if (err != cudaSuccess) return cuda_fail(h, err, "orthogonalisation");
