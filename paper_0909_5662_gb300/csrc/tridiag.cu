@@ -40,6 +40,11 @@ using dmrg::ld_acquire_gpu;
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+// Dynamic shared memory of the resident tridiagonalisation (227 KB per block, less the
+// static shared memory of the barrier and block sums).
+constexpr size_t kTridiagResidentSmem = 226 * 1024;
+constexpr int kResidentPer = 8;                        // column entries per thread at most
+constexpr int kResidentMaxN = kResidentPer * kThreads;
 constexpr int kInvitIters = 4;
 
 // ---------------------------------------------------------------- 1. tridiagonalisation
@@ -224,6 +229,172 @@ __global__ void __launch_bounds__(kThreads) tridiag_kernel(TriArgs T) {
                 double p = 0.0;
 #pragma unroll
                 for (int u = 0; u < kUnroll; ++u) p += acc[u];
+                for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+                if (lane == 0) __stcg(Pn + (r - (k + 2)), tau_n * p);
+            }
+        }
+        double* t = vs;
+        vs = vn;
+        vn = t;
+        tau_k = tau_n;
+    }
+}
+
+// The same column steps with every block's rows of A resident in shared memory for the
+// whole launch (block b owns rows b + G i, G = gridDim.x; rpb rows at most).  Each
+// column's update and product then read and write shared memory instead of making a
+// chain of L2 round trips per row, and the block's eight warps share the entries of
+// each row, so that the FP64 pipe, not memory latency, bounds the column.  Products of
+// a row are summed per warp and then over the warps in a fixed order.
+__global__ void __launch_bounds__(kThreads) tridiag_smem_kernel(TriArgs T, int rpb) {
+    extern __shared__ double sm[];
+    const int n = T.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = gridDim.x, b = blockIdx.x;
+    double* vs = sm;                      // v_k
+    double* ws = sm + n;                  // w_k
+    double* xs = sm + 2 * n;              // row k+1 (columns k+1 ..) after column k
+    double* vn = sm + 3 * n;              // v_{k+1}
+    double* rows = sm + 4 * n;            // rpb x n: this block's rows of A
+    const int nown = b < n ? (n - 1 - b) / G + 1 : 0;
+    __shared__ double p0;                  // p_k[0] of the current column
+    __shared__ double red[kWarps], sc[2];  // per-warp sums; tau and scale of the reflector
+    for (int i = 0; i < nown; ++i)
+        for (int c = tid; c < n; c += kThreads) rows[size_t(i) * n + c] = __ldcg(T.A + size_t(b + G * i) * n + c);
+    unsigned gen = 0;
+    double tau_k, beta;
+    // column 0: the reflector of row 0 and p_0 on own rows
+    for (int j = tid; j < n - 1; j += kThreads) xs[j] = __ldcg(T.A + 1 + j);
+    __syncthreads();
+    reflector(xs, n - 1, vs, tau_k, beta);
+    if (b == 0 && tid == 0) {
+        T.d[0] = __ldcg(T.A);
+        T.e[0] = beta;
+        T.tau[0] = tau_k;
+    }
+    const int i_first0 = (b >= 1) ? 0 : 1;   // own rows r >= 1
+    for (int i = i_first0 + warp; i < nown; i += kWarps) {
+        const double* ri = rows + size_t(i) * n + 1;
+        double acc = 0.0;
+        for (int j = lane; j < n - 1; j += 32) acc = fma(ri[j], vs[j], acc);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) __stcg(T.P + (b + G * i - 1), tau_k * acc);
+    }
+    for (int k = 0; k + 2 < n; ++k) {
+        const int L = n - k - 1;   // trailing size of column k
+        if (!grid_barrier(T.bar, gen, T.timeout_ns, T.status)) return;
+        // row k is read by no one any more: it keeps v_k for the back-transformation
+        if (b == 0)
+            for (int j = tid; j < L; j += kThreads) __stcg(T.A + size_t(k) * n + (k + 1) + j, vs[j]);
+        // p_k (summed by every block over its rows) and row k+1 (published by its owner
+        // one column earlier) are read together, one L2 round trip
+        const double* P = T.P + (k & 1) * n;
+        const double* xold = (k == 0) ? T.A + size_t(n) + 1 : T.R + ((k + 1) & 1) * n;
+        double pv = 0.0;
+        {   // every load in flight before the first use (L <= kResidentMaxN)
+            double pr[kResidentPer], xr[kResidentPer];
+#pragma unroll
+            for (int u = 0; u < kResidentPer; ++u) {
+                const int j = tid + u * kThreads;
+                if (j < L) {
+                    pr[u] = __ldcg(P + j);
+                    xr[u] = __ldcg(xold + j);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kResidentPer; ++u) {
+                const int j = tid + u * kThreads;
+                if (j < L) {
+                    ws[j] = pr[u];
+                    xs[j] = xr[u];
+                    pv = fma(pr[u], vs[j], pv);
+                }
+            }
+            if (tid == 0) p0 = pr[0];   // ws[0] is rewritten below while others still need p_0
+        }
+        const double half = 0.5 * tau_k * block_sum_all(pv);   // (its barriers order p0)
+        // w = p - half v, row k+1 after column k: x - v_0 w - w_0 v with v_0 = 1, and the
+        // squared norm of its entries 2 .. for the next reflector, in one pass
+        const double w0 = fma(-half, vs[0], p0);
+        double ss = 0.0;
+        for (int j = tid; j < L; j += kThreads) {
+            const double wj = fma(-half, vs[j], ws[j]);
+            ws[j] = wj;
+            const double xj = fma(-1.0, wj, fma(-w0, vs[j], xs[j]));
+            xs[j] = xj;
+            if (j >= 2) ss = fma(xj, xj, ss);
+        }
+        const bool next = k + 3 < n;   // column k+1 has a reflector
+        // The sum of ss over the block, and the reflector's scalars from it, in one thread:
+        // an FP64 instruction occupies the SM's FP64 pipe for a whole warp's worth of
+        // lanes, so scalar work repeated by every warp costs as much as vector work.
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (lane == 0) red[warp] = ss;
+        __syncthreads();   // (also completes ws and xs)
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kWarps; ++w) t += red[w];
+            // H x = beta e_1 for x = xs[1 .. L): v[0] = 1, as reflector() forms it
+            const double alpha = xs[1];
+            double beta_n = alpha, tau_r = 0.0, scale = 0.0;
+            if (next && t > 0.0) {
+                beta_n = -copysign(sqrt(fma(alpha, alpha, t)), alpha);
+                tau_r = (beta_n - alpha) / beta_n;
+                scale = 1.0 / (alpha - beta_n);
+            }
+            sc[0] = tau_r;
+            sc[1] = scale;
+            if (b == 0) {
+                if (next) {
+                    T.d[k + 1] = xs[0];
+                    T.e[k + 1] = beta_n;
+                    T.tau[k + 1] = tau_r;
+                } else {   // k = n-3: rows n-2 and n-1 remain
+                    T.d[n - 2] = xs[0];
+                    T.e[n - 2] = xs[1];
+                    T.tau[n - 2] = 0.0;
+                    T.tau[n - 1] = 0.0;
+                }
+            }
+        }
+        __syncthreads();
+        const double tau_n = sc[0];
+        if (next) {
+            const double scale = sc[1];
+            for (int j = tid; j < L - 1; j += kThreads) vn[j] = j == 0 ? 1.0 : xs[j + 1] * scale;
+            __syncthreads();
+        }
+        // own rows r >= k+2: update for column k, p for column k+1 (columns k+2 ..)
+        double* Pn = T.P + ((k + 1) & 1) * n;
+        double* Rn = T.R + (k & 1) * n;   // row k+2, columns k+2 ..
+        // one warp per row (a row's product then takes one warp reduction)
+        const int i0 = (k + 2 > b) ? (k + 2 - b + G - 1) / G : 0;
+        for (int i = i0 + warp; i < nown; i += kWarps) {
+            const int r = b + G * i;
+            const int ii = r - (k + 1);
+            double* ri = rows + size_t(i) * n + (k + 1);
+            const double vi = vs[ii], wi = ws[ii];
+            const bool pub = (r == k + 2) && next;
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            int j = 1 + lane;
+            for (; j + 96 < L; j += 128) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int jj = j + 32 * u;
+                    const double an = fma(-vi, ws[jj], fma(-wi, vs[jj], ri[jj]));
+                    ri[jj] = an;
+                    if (pub) __stcg(Rn + (jj - 1), an);
+                    acc[u] = fma(an, vn[jj - 1], acc[u]);
+                }
+            }
+            for (; j < L; j += 32) {
+                const double an = fma(-vi, ws[j], fma(-wi, vs[j], ri[j]));
+                ri[j] = an;
+                if (pub) __stcg(Rn + (j - 1), an);
+                acc[0] = fma(an, vn[j - 1], acc[0]);
+                if (!next && r == n - 1) T.d[n - 1] = an;   // k = n-3: the last diagonal entry
+            }
+            if (next) {
+                double p = (acc[0] + acc[1]) + (acc[2] + acc[3]);
                 for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
                 if (lane == 0) __stcg(Pn + (r - (k + 2)), tau_n * p);
             }
@@ -953,8 +1124,35 @@ dmrg_status tridiag_eigen(dmrg_handle h, int64_t n64, int64_t mp64, char* ws, do
     for (int a = 0; a < 5; ++a) lu[a] = reinterpret_cast<double*>(ws + W.offsets[10 + a]);
     unsigned char* sw = reinterpret_cast<unsigned char*>(ws + W.offsets[15]);
     cudaError_t err;
-    // 1. tridiagonalisation
-    {
+    // 1. tridiagonalisation: with every block's rows in shared memory when they fit
+    //    (one block per SM), else through L2
+    const int g_res = std::max(1, std::min(h->num_sms, n));
+    const int rpb = (n + g_res - 1) / g_res;
+    const size_t smem_res = (size_t(4) * n + size_t(rpb) * n) * 8;
+    bool resident = n >= 3 && n <= kResidentMaxN && smem_res <= kTridiagResidentSmem;
+    if (resident) {
+        int grid = 0;
+        err = cudaFuncSetAttribute(tridiag_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   int(smem_res));
+        if (err == cudaSuccess)
+            err = coop_grid(reinterpret_cast<const void*>(tridiag_smem_kernel), smem_res, g_res, &grid, 1);
+        if (err != cudaSuccess || grid != g_res) {
+            cudaGetLastError();
+            resident = false;
+        }
+    }
+    if (resident) {
+        err = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
+        if (err != cudaSuccess) return cuda_fail(h, err, "tridiagonalisation set-up");
+        TriArgs T{A, P, R, d, e, tau, bar, h->d_status, timeout_ns(h), n};
+        int rpb_arg = rpb;
+        err = timed_launch(h, "trunc_tridiag", s, [&] {
+            void* args[] = {&T, &rpb_arg};
+            return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(tridiag_smem_kernel),
+                                               dim3(unsigned(g_res)), dim3(kThreads), args, smem_res, s);
+        });
+        if (err != cudaSuccess) return cuda_fail(h, err, "tridiagonalisation");
+    } else {
         const size_t smem = size_t(n) * 32;
         if (smem > 200 * 1024) return fail(h, DMRG_ERR_SHAPE, "rows too large for the tridiagonal solver");
         err = cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
