@@ -229,6 +229,13 @@ struct PackJob {
     // Set by pack_prepare_grouped (grouped launches): the job's rows are contiguous runs
     // of its source (s_c = 1, rdiv = 1) and are copied one warp per row.
     int32_t rowwise, pad_;
+    // Set by the single-launch packer (pack_launch): multiply-shift divisors, in 32-bit
+    // index arithmetic, of the tiled path's geometry (tiles per operator group, per
+    // residue and per row of tiles) and of the 8-wide path's units per row (fast8).
+    uint64_t m_pg, m_hc, m_ct, m_u8;
+    int32_t s_pg, s_hc, s_ct, s_u8;
+    int32_t t_pg, t_hc, t_ct, fast8;
+    int64_t t_hrows;
 };
 void pack_prepare(PackJob& j);
 // pack_prepare, and for grouped launches the row-by-row copy of contiguous rows.

@@ -441,11 +441,24 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const __grid_constan
 // contiguous (16/32-byte loads, 16-byte stores of the BF16 hi and lo halves or
 // 2 x 16-byte stores of TF32 / FP32), in two halves so that a thread can issue the
 // loads of several units before converting.
+// Row and column of 8-element unit v of a contiguous job.
+__device__ __forceinline__ void vec8_rc(const PackJob& j, int64_t v, int64_t& r, int64_t& c) {
+    const int64_t per_row = j.cols >> 3;
+    if (j.fast8) {
+        const uint32_t vu = uint32_t(v);
+        const uint32_t ru = uint32_t((uint64_t(vu) * j.m_u8) >> j.s_u8);
+        r = ru;
+        c = int64_t(vu - ru * uint32_t(per_row)) << 3;
+    } else {
+        r = v / per_row;
+        c = (v - r * per_row) << 3;
+    }
+}
+
 template <typename S>
 __device__ __forceinline__ void pack_vec8_load(const PackJob& j, int64_t v, S (&x)[8]) {
-    const int64_t per_row = j.cols >> 3;
-    const int64_t r = v / per_row;
-    const int64_t c = (v - r * per_row) << 3;
+    int64_t r, c;
+    vec8_rc(j, v, r, c);
     const S* sp = static_cast<const S*>(j.src) + j.src_off + r * j.s_r_hi + c;
     if (sizeof(S) == 4) {
         const float4 a = reinterpret_cast<const float4*>(sp)[0];
@@ -464,9 +477,8 @@ __device__ __forceinline__ void pack_vec8_load(const PackJob& j, int64_t v, S (&
 
 template <typename S>
 __device__ __forceinline__ void pack_vec8_store(const PackJob& j, int64_t v, const S (&x)[8]) {
-    const int64_t per_row = j.cols >> 3;
-    const int64_t r = v / per_row;
-    const int64_t c = (v - r * per_row) << 3;
+    int64_t r, c;
+    vec8_rc(j, v, r, c);
     const int64_t dst = r * j.ld + c;
     if (j.mode == 0) {
         uint32_t hw[4], lw[4];
@@ -541,16 +553,19 @@ __device__ __forceinline__ void pack_store2(const PackJob& j, int64_t dst, float
     }
 }
 
+// The tile's coordinates come from host-computed multiply-shift divisors (32-bit index
+// arithmetic): 64-bit divisions here made the launch instruction-bound.
 __device__ __forceinline__ void pack_tile(const PackJob& j, int64_t t, float (*tile)[kTile + 1]) {
     const int64_t rpo = j.rows_per_op < j.rows ? j.rows_per_op : j.rows;
-    const int64_t hrows = rpo / j.rdiv;
-    const int64_t ht = (hrows + kTile - 1) / kTile, ct = (j.cols + kTile - 1) / kTile;
-    const int64_t per_group = int64_t(j.rdiv) * ht * ct;
-    const int64_t g = t / per_group;
-    const int64_t u0 = t - g * per_group;
-    const int64_t rem = u0 / (ht * ct);
-    const int64_t u = u0 - rem * ht * ct;
-    const int64_t h0 = (u / ct) * kTile, c0 = (u % ct) * kTile;
+    const int64_t hrows = j.t_hrows;
+    const uint32_t tu = uint32_t(t);
+    const uint32_t gu = uint32_t((uint64_t(tu) * j.m_pg) >> j.s_pg);
+    const uint32_t u0 = tu - gu * uint32_t(j.t_pg);
+    const uint32_t remu = uint32_t((uint64_t(u0) * j.m_hc) >> j.s_hc);
+    const uint32_t u = u0 - remu * uint32_t(j.t_hc);
+    const uint32_t hq = uint32_t((uint64_t(u) * j.m_ct) >> j.s_ct);
+    const int64_t g = gu, rem = remu;
+    const int64_t h0 = int64_t(hq) * kTile, c0 = int64_t(u - hq * uint32_t(j.t_ct)) * kTile;
     const float* src = static_cast<const float*>(j.src) + j.src_off + g * j.s_op + rem * j.s_r_lo;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 8 warps
     float v[16];
@@ -788,6 +803,25 @@ cudaError_t pack_launch(const PackJob* jobs, int njobs, PackJob* /*unused*/, cud
             pack_prepare(j);
             j.vec8 = v8 ? 1 : 0;
             j.tiled = tl ? 1 : 0;
+            if (v8) {
+                const int64_t per_row = j.cols / 8;
+                j.fast8 = (j.rows * per_row < (int64_t(1) << 31)) ? 1 : 0;
+                if (j.fast8) div_magic(per_row, j.m_u8, j.s_u8);
+            }
+            if (tl) {
+                const int64_t rpo = j.rows_per_op < j.rows ? j.rows_per_op : j.rows;
+                j.t_hrows = rpo / j.rdiv;
+                const int64_t ht = (j.t_hrows + kTile - 1) / kTile, ct = (j.cols + kTile - 1) / kTile;
+                const int64_t hc = ht * ct, pg = int64_t(j.rdiv) * hc;
+                if (pg >= (int64_t(1) << 31) || pack_tiles_host(j) >= (int64_t(1) << 31))
+                    return cudaErrorInvalidConfiguration;
+                j.t_ct = int32_t(ct);
+                j.t_hc = int32_t(hc);
+                j.t_pg = int32_t(pg);
+                div_magic(ct, j.m_ct, j.s_ct);
+                div_magic(hc, j.m_hc, j.s_hc);
+                div_magic(pg, j.m_pg, j.s_pg);
+            }
             j.block_start = blocks;
             blocks += v8 ? (j.rows * (j.cols / 8) + kPackThreads * kVec8Units - 1) / (kPackThreads * kVec8Units)
                     : tl ? pack_tiles_host(j)
