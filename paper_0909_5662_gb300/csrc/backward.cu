@@ -6,8 +6,8 @@
 //   dU   = sum_k (O_k (x) I) U G_k^T + (O_k (x) I)^T U G_k.
 // Nothing from the forward pass is kept: only U, O and G are read.
 //
-// Tensor-core schedule (BF16x3 or TF32, CTA-pair kernel), with W_k = U G_k and
-// W'_k = U G_k^T (md x m' each; W_{k,s} = rows j*d + s):
+// Tensor-core schedule (TF32; BF16x3 as noted below), CTA-pair kernel, with
+// W_k = U G_k and W'_k = U G_k^T (md x m' each; W_{k,s} = rows j*d + s):
 //   1. W'_k: M = K*m' rows (k, a), N = d*m columns ordered (s, j) (U packed with rows
 //      s*m + j), reduction m'.  The epilogue writes it twice: row-major (rows (k, j),
 //      columns (s, a): the dO operand) and site-major, WT'_k[s*m' + a][j] (j contiguous:
@@ -17,7 +17,11 @@
 //   4. dU_r^T[(s,n)][i] = sum_(k,j) WT'_k[(s,n)][j] O_k[i][j] + WT_k[(s,n)][j] O_k[j][i]:
 //      one problem whose reduction runs over 2K slices ([WT' | WT] against [O | O^T]),
 //      split into P parts that write their own partial sums;
-//   5. dU[i*d+s][n] = sum_p partial_p[(s,n)][i], summed in FP64 in a fixed order.
+//   5. dU[i*d+s][n] = sum_p partial_p[(s,n)][i], summed in a fixed order.
+// BF16x3 reads 16-bit operands in either order (MN-major operands of the pair kernel):
+// W' is written row-major only and dU's first K slices read it MN-major; the last K
+// slices read O MN-major as O^T, so O^T is not packed.  The two halves are separate
+// problems with their own parts.
 // BF16x3 reductions longer than one accumulation chain (dO: d*m'; dU: 2*K*m) are cut
 // into chains as in the forward products, and nothing is accumulated atomically, so dO
 // and dU are reproducible bit for bit.
@@ -173,8 +177,11 @@ dmrg_status bwd_simt(dmrg_handle h, const double* U, const void* O, const void* 
     return DMRG_OK;
 }
 
-// dU[(i d + s) m' + n] = sum_p part[p][(s m' + n) m + i], in FP64, p in order: the
-// partial sums of dU_r^T are transposed back through a shared-memory tile.
+// dU[(i d + s) m' + n] = sum_p part[p][(s m' + n) m + i], p in order: the partial sums
+// of dU_r^T are transposed back through a shared-memory tile.  The sum is compensated
+// (Neumaier's variant of Kahan summation) in FP32: an FP64 addition per part would make
+// the kernel FP64-bound on this part, and the compensated sum's error stays at the final
+// rounding to FP32 for the few parts there are.
 __global__ void __launch_bounds__(256) bwd_du_reduce_kernel(const float* __restrict__ part,
                                                             int nparts, int64_t dmp, int64_t m,
                                                             int64_t mp, int d,
@@ -183,10 +190,21 @@ __global__ void __launch_bounds__(256) bwd_du_reduce_kernel(const float* __restr
     const int64_t R0 = int64_t(blockIdx.y) * 32, I0 = int64_t(blockIdx.x) * 32;
     for (int rr = threadIdx.y; rr < 32; rr += 8) {
         const int64_t R = R0 + rr, I = I0 + threadIdx.x;
-        double acc = 0.0;
-        if (R < dmp && I < m)
-            for (int q = 0; q < nparts; ++q) acc += double(part[(int64_t(q) * dmp + R) * m + I]);
-        t[rr][threadIdx.x] = acc;
+        float sum = 0.f, comp = 0.f;
+        if (R < dmp && I < m) {
+            float x[kBwdMaxParts];   // every part's load in flight before the sum
+#pragma unroll
+            for (int q = 0; q < kBwdMaxParts; ++q)
+                x[q] = q < nparts ? part[(int64_t(q) * dmp + R) * m + I] : 0.f;
+#pragma unroll
+            for (int q = 0; q < kBwdMaxParts; ++q) {
+                if (q >= nparts) break;
+                const float u = sum + x[q];
+                comp += fabsf(sum) >= fabsf(x[q]) ? (sum - u) + x[q] : (x[q] - u) + sum;
+                sum = u;
+            }
+        }
+        t[rr][threadIdx.x] = double(sum) + double(comp);
     }
     __syncthreads();
     for (int ii = threadIdx.y; ii < 32; ii += 8) {
@@ -213,6 +231,10 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
         return base + B.ws.offsets[idx + (split ? half : 0)];
     };
     auto lo = [&](int idx) -> char* { return split ? sec(idx, 1) : sec(idx, 0); };
+    // BF16x3: dU reads W' and W row-major and O^T from O, as MN-major operands of the
+    // CTA-pair kernel (its tensor core takes 16-bit operands in either order), so neither
+    // the transposed pack of O nor site-major copies of W' and W are made.
+    const bool mn = split;
     cudaError_t e;
     // ---- packs: U, U_r (dO), G, and for dU G^T, O and O^T, in one launch
     {
@@ -242,10 +264,12 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
             jo.src = O; jo.src_f64 = in_is_fp64; jo.mode = pmode; jo.rows = K * m; jo.cols = m;
             jo.rows_per_op = K * m; jo.rdiv = 1; jo.s_r_hi = m; jo.s_c = 1;
             jo.dst0 = sec(B.i_O, 0); jo.dst1 = lo(B.i_O); jo.ld = B.ld_j;
-            PackJob& jq = jobs[nj++];   // O^T: rows (k, i), cols j = O_k[j][i]
-            jq.src = O; jq.src_f64 = in_is_fp64; jq.mode = pmode; jq.rows = K * m; jq.cols = m;
-            jq.rows_per_op = m; jq.s_op = m * m; jq.rdiv = 1; jq.s_r_hi = 1; jq.s_c = m;
-            jq.dst0 = sec(B.i_O, 0) + oT; jq.dst1 = lo(B.i_O) + (split ? oT : 0); jq.ld = B.ld_j;
+            if (!mn) {   // (BF16x3 reads O MN-major instead)
+                PackJob& jq = jobs[nj++];   // O^T: rows (k, i), cols j = O_k[j][i]
+                jq.src = O; jq.src_f64 = in_is_fp64; jq.mode = pmode; jq.rows = K * m; jq.cols = m;
+                jq.rows_per_op = m; jq.s_op = m * m; jq.rdiv = 1; jq.s_r_hi = 1; jq.s_c = m;
+                jq.dst0 = sec(B.i_O, 0) + oT; jq.dst1 = lo(B.i_O) + (split ? oT : 0); jq.ld = B.ld_j;
+            }
         }
         e = timed_launch(h, "bwd_pack", s, [&] { return pack_launch(jobs, nj, nullptr, s); });
         if (e != cudaSuccess) return cuda_fail(h, e, "pack");
@@ -309,9 +333,10 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
         S.rows_per_op = int32_t(mp); S.s_op = m * B.ld_n; S.s_row = 1;
         S.col_div = int32_t(m); S.s_col_hi = mp; S.s_col_lo = B.ld_n;
         L.nprob = 1;
-        L.out[0][0] = dO ? sec(B.i_Wp, 0) : nullptr;
-        L.out[0][1] = dO ? lo(B.i_Wp) : nullptr;
-        if (dU) site_major(L, wt_hi, wt_lo);
+        const bool rowmajor = dO || (dU && mn);
+        L.out[0][0] = rowmajor ? sec(B.i_Wp, 0) : nullptr;
+        L.out[0][1] = rowmajor ? lo(B.i_Wp) : nullptr;
+        if (dU && !mn) site_major(L, wt_hi, wt_lo);
         if ((st = launch("bwd_tc_Wp", L, epi_op, mp)) != DMRG_OK) return st;
     }
     if (dO) {
@@ -346,6 +371,55 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
         }
         // 4. dU_r^T[(s,n)][i] over 2K slices, split into parts with their own partial sums.
         float* part = reinterpret_cast<float*>(base + B.ws.offsets[B.i_dU]);
+        if (mn) {
+            // Two problems of K slices each, written to parts [0, pa) and [pa, pa + pb):
+            //   sum_(k,j) W'_k[j*d+s][n] O_k[i][j]  (A: W' row-major read MN-major,
+            //                                        B: O K-major),
+            //   sum_(k,j) WT_k[s*m'+n][j] O_k[j][i] (A: W site-major, K-major,
+            //                                        B: O read MN-major).
+            TcLaunch L{};
+            TcOperand Ap{sec(B.i_Wp, 0), lo(B.i_Wp), dmp, m, B.ld_n, K, m * B.ld_n};
+            Ap.mn_major = 1;
+            TcOperand Aw{wt_hi + wt_second, wt_lo + wt_second, dmp, m, B.ld_j, K, dmp * B.ld_j};
+            TcOperand Bk{sec(B.i_O, 0), lo(B.i_O), m, m, B.ld_j, K, m * B.ld_j};
+            TcOperand Bt = Bk;
+            Bt.mn_major = 1;
+            TcProblem& Pa = L.inline_prob[0];
+            TcProblem& Pb = L.inline_prob[1];
+            if (!make_problem(Pa, mode, Ap, Bk, cfg.tile_n_max, 1, cfg.row_bytes, 1))
+                return fail(h, DMRG_ERR_CUDA, "tensor map");
+            // parts per problem: the fewest waves of tiles per unit of reduction length
+            // (waves over the CTA pairs x reduction per part), fewer parts on ties
+            const int tiles = Pa.m_tiles * Pa.n_tiles;
+            const int pairs = std::max(1, grid / 2);
+            int each = 1;
+            double best = 1e300;
+            for (int e = 1; e <= kBwdMaxParts / 2; ++e) {
+                const double cost = double((2 * e * tiles + pairs - 1) / pairs) / e + 1e-3 * e;
+                if (cost < best) {
+                    best = cost;
+                    each = e;
+                }
+            }
+            if (!make_problem(Pa, mode, Ap, Bk, cfg.tile_n_max, each, cfg.row_bytes, 1) ||
+                !make_problem(Pb, mode, Aw, Bt, cfg.tile_n_max, each, cfg.row_bytes, 1))
+                return fail(h, DMRG_ERR_CUDA, "tensor map");
+            Pa.sc[0] = scatter_rowmajor(m);
+            Pa.sc[0].s_split = dmp * m;
+            Pb.sc[0] = Pa.sc[0];
+            Pb.sc[0].out_off = int64_t(Pa.k_splits) * dmp * m;
+            L.nprob = 2;
+            L.out[0][0] = part;
+            if ((st = launch("bwd_tc_dU", L, EPI_F32, K * m)) != DMRG_OK) return st;
+            const int nparts = Pa.k_splits + Pb.k_splits;
+            e = timed_launch(h, "bwd_dU_reduce", s, [&] {
+                dim3 grd(unsigned((m + 31) / 32), unsigned((dmp + 31) / 32));
+                bwd_du_reduce_kernel<<<grd, dim3(32, 8), 0, s>>>(part, nparts, dmp, m, mp, d, dU);
+                return cudaGetLastError();
+            });
+            if (e != cudaSuccess) return cuda_fail(h, e, "dU reduce");
+            return DMRG_OK;
+        }
         TcLaunch L{};
         TcProblem& P = L.inline_prob[0];
         TcOperand A{wt_hi, split ? wt_lo : nullptr, dmp, m, B.ld_j, 2 * K, dmp * B.ld_j};

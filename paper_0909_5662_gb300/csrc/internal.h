@@ -94,6 +94,8 @@ struct TcProblem {  // 64-byte aligned through its CUtensorMap members
     int32_t atomic;      // FP32 epilogues: accumulate with atomics (split-K parts of a tile)
     int32_t kb_chunk;    // CTA-pair kernel: k-blocks per tensor-core accumulation chain; the
                          // chains of a tile are summed in FP32 registers (0: one chain)
+    int32_t a_mn, b_mn;  // CTA-pair kernel, BF16 operands: A / B stored MN-major (its M / N
+                         // index contiguous in memory), read in 64-column boxes
     TcScatter sc[1];
 };
 
@@ -112,7 +114,10 @@ struct TcConfig {
     }
 };
 
-constexpr int kMaxInlineProblems = 6;   // keeps TcLaunch (the kernel parameters) under 4 KB
+constexpr int kMaxInlineProblems = 6;
+// MN-major operands are loaded in boxes of this many rows (64 BF16: one 128-byte row per
+// reduction index).
+constexpr int kMnBox = 64;   // keeps TcLaunch (the kernel parameters) under 4 KB
 // Running-sum scratch of the CTA-pair kernel's chained accumulation: kChainScratchCtas
 // CTAs x 128 rows x 256 FP32 columns.
 constexpr int kChainScratchCtas = 160;
@@ -161,6 +166,10 @@ struct TcOperand {
     // stride ld floats, a multiple of 4, 16-byte aligned) that the kernel's converter
     // warps split into BF16 hi/lo (BF16X3) or round to TF32 in shared memory.
     int32_t f32_source = 0;
+    // CTA-pair kernel, BF16 operands (BF16X3, 128-byte rows): the operand is stored
+    // MN-major, element (row r, reduction index c) of slice z at z * batch_stride +
+    // c * ld + r (its rows contiguous), ld a multiple of 8.
+    int32_t mn_major = 0;
 };
 
 cudaError_t tc_gemm_launch(TcMode mode, TcEpi epi, const TcLaunch& L, int stages, int grid,

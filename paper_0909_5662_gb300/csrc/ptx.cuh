@@ -235,6 +235,20 @@ __device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t saddr) {
     return d;
 }
 
+// Shared-memory matrix descriptor, MN-major operand, 128-byte swizzle: rows of 64 BF16
+// along M (or N) for one reduction index each, 8-row (1024-byte) swizzle atoms along the
+// reduction (stride byte offset), 64-column blocks `mn_block_bytes` apart (leading byte
+// offset).
+__device__ __forceinline__ uint64_t smem_desc_mn128(uint32_t saddr, uint32_t mn_block_bytes) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);            // start address
+    d |= static_cast<uint64_t>((mn_block_bytes >> 4) & 0x3FFFu) << 16;   // leading byte offset
+    d |= static_cast<uint64_t>(1024 >> 4) << 32;                    // stride byte offset
+    d |= static_cast<uint64_t>(1) << 46;                            // descriptor version
+    d |= static_cast<uint64_t>(2) << 61;                            // 128-byte swizzle
+    return d;
+}
+
 // Instruction descriptor: FP32 accumulator, both operands K-major, M = 128.
 // a_fmt/b_fmt: 1 = BF16 (kind::f16), 2 = TF32 (kind::tf32).
 __host__ __device__ __forceinline__ uint32_t make_idesc(uint32_t fmt, uint32_t n) {

@@ -921,17 +921,31 @@ bool make_problem(TcProblem& p, TcMode mode, const TcOperand& A, const TcOperand
     if (A.f32_source && (!pair || row_bytes != 128 || (A.ld & 3) != 0 ||
                          (reinterpret_cast<uintptr_t>(A.hi) & 15) != 0))
         return false;
+    // MN-major operands (CTA pairs, BF16, 128-byte rows): boxes of 64 rows of the operand
+    // (its contiguous index) by one 64-element k-block, two per CTA's share of the tile.
+    auto mn_ok = [&](const TcOperand& X) {
+        return pair && !f32 && row_bytes == 128 && !X.f32_source && (X.ld & 7) == 0 &&
+               (reinterpret_cast<uintptr_t>(X.hi) & 15) == 0 &&
+               (X.lo == nullptr || (reinterpret_cast<uintptr_t>(X.lo) & 15) == 0);
+    };
+    if ((A.mn_major && !mn_ok(A)) || (B.mn_major && !mn_ok(B))) return false;
+    if (B.mn_major && tile_n / 2 > 2 * kMnBox) return false;
+    auto encode = [&](CUtensorMap* map, const void* base, const TcOperand& X, bool fp32, int box) {
+        if (X.mn_major)   // dimensions (row, reduction, slice): the row index is contiguous
+            return encode_operand_map(map, base, false, X.cols, X.rows, X.ld, kMnBox, X.nbatch,
+                                      X.batch_stride, row_bytes);
+        return encode_operand_map(map, base, fp32, X.rows, X.cols, X.ld, box, X.nbatch,
+                                  X.batch_stride, row_bytes);
+    };
     for (int i = 0; i < (split ? 2 : 1); ++i) {
         const void* a = i ? A.lo : A.hi;
         const void* b = i ? B.lo : B.hi;
-        if (!(A.f32_source && i == 1) &&
-            !encode_operand_map(&p.tmA[i], a, f32 || A.f32_source, A.rows, A.cols, A.ld, a_box,
-                                A.nbatch, A.batch_stride, row_bytes))
+        if (!(A.f32_source && i == 1) && !encode(&p.tmA[i], a, A, f32 || A.f32_source, a_box))
             return false;
-        if (!encode_operand_map(&p.tmB[i], b, f32, B.rows, B.cols, B.ld, b_box, B.nbatch,
-                                B.batch_stride, row_bytes))
-            return false;
+        if (!encode(&p.tmB[i], b, B, f32, b_box)) return false;
     }
+    p.a_mn = A.mn_major ? 1 : 0;
+    p.b_mn = B.mn_major ? 1 : 0;
     if (A.f32_source) p.tmA[1] = p.tmA[0];
     if (!split) {
         p.tmA[1] = p.tmA[0];

@@ -144,6 +144,9 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
     constexpr int kUmmaK = 32 / kElem;
     constexpr int kStepsPerBlock = kElemsPerRow / kUmmaK;
     constexpr uint32_t kFmt = (MODE == TC_TF32) ? 2u : 1u;
+    // MN-major operands: BF16 with 128-byte rows only (the host refuses other forms)
+    constexpr bool kMnOk = (MODE != TC_TF32) && (RB == 128) && !CONV;
+    constexpr uint32_t kMnBoxBytes = uint32_t(kMnBox) * 128u;
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -228,8 +231,10 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                 const TcProblem* P = dt.P;
                 // both CTAs' bytes: A (128 rows each; counted on afull in the converting
                 // form) and the B halves (tile_n / 2 rows each)
+                const bool a_mn = kMnOk && P->a_mn, b_mn = kMnOk && P->b_mn;
                 const uint32_t bytes =
-                    2u * ((CONV ? 0u : a_bytes) + uint32_t(P->tile_n / 2) * kRowBytes) *
+                    2u * ((CONV ? 0u : a_bytes) +
+                          (b_mn ? 2u * kMnBoxBytes : uint32_t(P->tile_n / 2) * kRowBytes)) *
                     (kSplit ? 2u : 1u);
                 // converting form: this CTA's FP32 A tile, 128 rows x 32 floats per box
                 const uint32_t a_tx = kSplit ? 2u * a_bytes : a_bytes;
@@ -252,8 +257,21 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                             tma_load_3d(stage_a(stage, 1), &P->tmA[0], &afull[stage], x + 32, ya, z);
                     }
                     for (int h = 0; h < (kSplit ? 2 : 1); ++h) {
-                        if (!CONV) tma_load_3d_pair(stage_a(stage, h), &P->tmA[h], fb, x, ya, z);
-                        tma_load_3d_pair(stage_b(stage, h), &P->tmB[h], fb, x, yb, z);
+                        // an MN-major operand: two boxes of 64 rows, coordinates (row, k)
+                        if (a_mn) {
+                            tma_load_3d_pair(stage_a(stage, h), &P->tmA[h], fb, ya, x, z);
+                            tma_load_3d_pair(stage_a(stage, h) + kMnBoxBytes, &P->tmA[h], fb,
+                                             ya + kMnBox, x, z);
+                        } else if (!CONV) {
+                            tma_load_3d_pair(stage_a(stage, h), &P->tmA[h], fb, x, ya, z);
+                        }
+                        if (b_mn) {
+                            tma_load_3d_pair(stage_b(stage, h), &P->tmB[h], fb, yb, x, z);
+                            tma_load_3d_pair(stage_b(stage, h) + kMnBoxBytes, &P->tmB[h], fb,
+                                             yb + kMnBox, x, z);
+                        } else {
+                            tma_load_3d_pair(stage_b(stage, h), &P->tmB[h], fb, x, yb, z);
+                        }
                     }
                     armed |= 1u << stage;
                     armed_parity = (armed_parity & ~(1u << stage)) | (phase << stage);
@@ -294,7 +312,19 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                 const Decoded dt = decode_tile(L, t, kElemsPerRow);
                 const TcProblem* P = dt.P;
                 const int n_eff = pair_n(P->tile_n, P->N - dt.nt * P->tile_n);
-                const uint32_t idesc = make_idesc_pair(kFmt, uint32_t(n_eff));
+                const bool a_mn = kMnOk && P->a_mn, b_mn = kMnOk && P->b_mn;
+                // transpose bits: A (bit 15) and B (bit 16) MN-major
+                const uint32_t idesc = make_idesc_pair(kFmt, uint32_t(n_eff)) |
+                                       (a_mn ? 1u << 15 : 0u) | (b_mn ? 1u << 16 : 0u);
+                // descriptor advance per 16-element k-step, in 16-byte units: 32 bytes along
+                // a K-major row, 16 rows of 128 bytes MN-major
+                const uint64_t a_step = a_mn ? 128 : 2, b_step = b_mn ? 128 : 2;
+                // the descriptors' fields other than the start address, per operand order
+                const uint64_t a_bits = a_mn ? smem_desc_mn128(0, kMnBoxBytes) : smem_desc_kmajor<RB>(0);
+                const uint64_t b_bits = b_mn ? smem_desc_mn128(0, kMnBoxBytes) : smem_desc_kmajor<RB>(0);
+                auto desc = [&](uint8_t* base, uint64_t bits) -> uint64_t {
+                    return bits | uint64_t((smem_u32(base) & 0x3FFFFu) >> 4);
+                };
                 const int chunk = (P->kb_chunk > 0 && L.chunk_scratch) ? P->kb_chunk
                                                                         : (dt.kb_end - dt.kb_begin);
                 int kb0 = dt.kb_begin;
@@ -309,29 +339,30 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                     tc_fence_after();
                     const uint32_t tmem_d = tmem_base + uint32_t(acc) * kAccStride;
                     for (int kb = kb0; kb < kb1; ++kb) {
+                        // (formed before the wait, off the path from the barrier to the MMA)
+                        const int rem = P->Kred - (kb % dt.kb_per_batch) * kElemsPerRow;
+                        const int steps = min(kStepsPerBlock, (rem + kUmmaK - 1) / kUmmaK);
+                        const uint64_t ah = desc(stage_a(stage, 0), a_bits);
+                        const uint64_t bh = desc(stage_b(stage, 0), b_bits);
+                        const uint64_t al = kSplit ? desc(stage_a(stage, 1), a_bits) : 0;
+                        const uint64_t bl = kSplit ? desc(stage_b(stage, 1), b_bits) : 0;
                         if (!(CONV ? mbar_wait_cluster(&full[stage], phase, tmo, L.status, vabort)
                                    : mbar_wait(&full[stage], phase, tmo, L.status, vabort))) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const int rem = P->Kred - (kb % dt.kb_per_batch) * kElemsPerRow;
-                        const int steps = min(kStepsPerBlock, (rem + kUmmaK - 1) / kUmmaK);
-                        const uint64_t ah = smem_desc_kmajor<RB>(smem_u32(stage_a(stage, 0)));
-                        const uint64_t bh = smem_desc_kmajor<RB>(smem_u32(stage_b(stage, 0)));
-                        const uint64_t al = kSplit ? smem_desc_kmajor<RB>(smem_u32(stage_a(stage, 1))) : 0;
-                        const uint64_t bl = kSplit ? smem_desc_kmajor<RB>(smem_u32(stage_b(stage, 1))) : 0;
                         for (int k = 0; k < steps; ++k) {
-                            const uint64_t off = uint64_t(k) * 2;
+                            const uint64_t oa = uint64_t(k) * a_step, ob = uint64_t(k) * b_step;
                             const uint32_t accum = (kb > kb0 || k > 0) ? 1u : 0u;
                             if (MODE == TC_BF16X3) {
-                                mma_bf16_pair(tmem_d, al + off, bh + off, idesc, accum);
-                                mma_bf16_pair(tmem_d, ah + off, bl + off, idesc, 1u);
-                                mma_bf16_pair(tmem_d, ah + off, bh + off, idesc, 1u);
+                                mma_bf16_pair(tmem_d, al + oa, bh + ob, idesc, accum);
+                                mma_bf16_pair(tmem_d, ah + oa, bl + ob, idesc, 1u);
+                                mma_bf16_pair(tmem_d, ah + oa, bh + ob, idesc, 1u);
                             } else if (MODE == TC_TF32) {
-                                mma_tf32_pair(tmem_d, ah + off, bh + off, idesc, accum);
+                                mma_tf32_pair(tmem_d, ah + oa, bh + ob, idesc, accum);
                             } else {
-                                mma_bf16_pair(tmem_d, ah + off, bh + off, idesc, accum);
+                                mma_bf16_pair(tmem_d, ah + oa, bh + ob, idesc, accum);
                             }
                         }
                         // Test hook: withhold one release so that both producers' bounded
@@ -573,8 +604,17 @@ cudaError_t tc_gemm_launch_pair(TcMode mode, TcEpi epi, const TcLaunch& L, int s
                                  !(epi == EPI_SPLIT_BF16 || epi == EPI_TF32)))
         return cudaErrorInvalidValue;
     int bn = 32;
-    for (int i = 0; i < L.nprob; ++i) bn = std::max(bn, L.inline_prob[i].tile_n);
-    const int bh = bn / 2;
+    bool any_mn = false, b_mn = false;
+    for (int i = 0; i < L.nprob; ++i) {
+        const TcProblem& P = L.inline_prob[i];
+        bn = std::max(bn, P.tile_n);
+        any_mn = any_mn || P.a_mn || P.b_mn;
+        b_mn = b_mn || P.b_mn;
+        if (P.b_mn && P.tile_n / 2 > 2 * kMnBox) return cudaErrorInvalidValue;
+    }
+    if (any_mn && (mode == TC_TF32 || L.row_bytes != 128 || L.convert_a)) return cudaErrorInvalidValue;
+    // an MN-major B share is two 64-row boxes whatever the tile width
+    const int bh = b_mn ? 2 * kMnBox : bn / 2;
     const size_t smem = pair_smem_bytes(mode, stages, bh, L.row_bytes);
     if (smem > 232448) return cudaErrorInvalidConfiguration;
     grid = std::max(2, std::min(grid, 2 * L.total_tiles)) / 2 * 2;
