@@ -134,7 +134,9 @@ __device__ __forceinline__ void fence_proxy_async_shared() {
 
 // SITE: the launch also writes the site-major second copy (TcLaunch::out2); a separate
 // instantiation, so that the other launches do not carry its registers.
-template <int MODE, int EPI, int RB, bool CONV, bool SITE>
+// MN: the launch has problems with MN-major operands (a separate instantiation, so that
+// the others carry none of their per-k-block choices).
+template <int MODE, int EPI, int RB, bool CONV, bool SITE, bool MN>
 __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
     tc_gemm_pair_kernel(const __grid_constant__ TcLaunch L, int stages, int bh_smem) {
     constexpr int kRowBytes = RB;
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
     constexpr int kStepsPerBlock = kElemsPerRow / kUmmaK;
     constexpr uint32_t kFmt = (MODE == TC_TF32) ? 2u : 1u;
     // MN-major operands: BF16 with 128-byte rows only (the host refuses other forms)
-    constexpr bool kMnOk = (MODE != TC_TF32) && (RB == 128) && !CONV;
+    constexpr bool kMnOk = MN && (MODE != TC_TF32) && (RB == 128) && !CONV;
     constexpr uint32_t kMnBoxBytes = uint32_t(kMnBox) * 128u;
 
     extern __shared__ uint8_t smem_raw[];
@@ -555,10 +557,15 @@ template <int MODE, int EPI>
 cudaError_t launch_pair(const TcLaunch& L, int stages, int grid, int bh_smem, size_t smem,
                         cudaStream_t s) {
     constexpr bool kSiteEpi = (EPI == EPI_SPLIT_BF16 || EPI == EPI_TF32);
-    auto k = L.convert_a ? tc_gemm_pair_kernel<MODE, EPI, 128, true, false>
-             : L.row_bytes == 64 ? tc_gemm_pair_kernel<MODE, EPI, 64, false, false>
-                                 : tc_gemm_pair_kernel<MODE, EPI, 128, false, false>;
-    if (kSiteEpi && L.out2[0] != nullptr) k = tc_gemm_pair_kernel<MODE, EPI, 128, false, kSiteEpi>;
+    auto k = L.convert_a ? tc_gemm_pair_kernel<MODE, EPI, 128, true, false, false>
+             : L.row_bytes == 64 ? tc_gemm_pair_kernel<MODE, EPI, 64, false, false, false>
+                                 : tc_gemm_pair_kernel<MODE, EPI, 128, false, false, false>;
+    if (kSiteEpi && L.out2[0] != nullptr) k = tc_gemm_pair_kernel<MODE, EPI, 128, false, kSiteEpi, false>;
+    if constexpr (MODE == TC_BF16X3) {
+        bool mn = false;
+        for (int i = 0; i < L.nprob; ++i) mn = mn || L.inline_prob[i].a_mn || L.inline_prob[i].b_mn;
+        if (mn) k = tc_gemm_pair_kernel<MODE, EPI, 128, false, false, true>;
+    }
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
