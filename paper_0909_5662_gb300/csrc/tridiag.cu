@@ -469,6 +469,20 @@ __device__ __forceinline__ int sturm_count(const double* d, const double* e2, in
     return c;
 }
 
+// The same count in FP32 (for the coarse phase below, on T / ||T||), 1/q correctly
+// rounded.
+__device__ __forceinline__ int sturm_count32(const float* d, const float* e2, int n, float x,
+                                             float pivmin) {
+    float q = d[0] - x;
+    int c = q < 0.f ? 1 : 0;
+    for (int i = 1; i < n; ++i) {
+        if (fabsf(q) < pivmin) q = -pivmin;
+        q = fmaf(-e2[i - 1], __frcp_rn(q), d[i] - x);
+        c += q < 0.f ? 1 : 0;
+    }
+    return c;
+}
+
 // Multisection: kSect neighbouring threads share eigenvalue j (the j-th smallest) and
 // count at kSect interior points of its interval at once, so each round shrinks it
 // kSect + 1 times.  Stops at width 2 eps max(|lo|, |hi|), or eps ||T|| (the absolute
@@ -488,22 +502,88 @@ __global__ void __launch_bounds__(kBisectThreads) bisect_kernel(const double* __
     extern __shared__ double sm[];
     const double* dd = d;
     const double* ee = e2g;
+    const float* d32 = nullptr;
+    const float* e32 = nullptr;
+    // staged: 0 = d and e^2 read from global memory; 1 = staged in shared memory (FP64);
+    // 2 = also their FP32 copies for the coarse phase
+    const double tn = stats[2];
+    const bool coarse = staged == 2 && tn > 0.0;
     if (staged) {
         double* ds = sm;
         double* es = sm + n;
+        float* fs = reinterpret_cast<float*>(sm + 2 * n);   // T / ||T|| in FP32
+        float* gs = fs + n;
+        const double inv = tn > 0.0 ? 1.0 / tn : 0.0;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             ds[i] = d[i];
-            if (i + 1 < n) es[i] = e[i] * e[i];
+            if (staged == 2) fs[i] = float(d[i] * inv);
+            if (i + 1 < n) {
+                es[i] = e[i] * e[i];
+                const double es_i = e[i] * inv;
+                if (staged == 2) gs[i] = float(es_i * es_i);
+            }
         }
         __syncthreads();
         dd = ds;
         ee = es;
+        d32 = fs;
+        e32 = gs;
     }
     const int t = threadIdx.x % kSect;
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) / kSect;
     const bool live = j < n;
     double lo = stats[0], hi = stats[1];
     const double atol = DBL_EPSILON * stats[2], pivmin = stats[3];
+    const int gbase = (threadIdx.x & 31) & ~(kSect - 1);   // first lane of this group
+    if (coarse) {
+        // Coarse phase: the same multisection with FP32 counts on T / ||T|| (an FP32
+        // operation costs a small fraction of an FP64 one here).  A computed count is the
+        // exact count of a matrix within a few FP32 roundings of T, so the interval, widened
+        // by 16 FP32 epsilons of ||T||, is checked with FP64 counts at its two ends and
+        // used only if they bracket j; otherwise the search starts from the Gershgorin
+        // interval as before.
+        float flo = float(lo / tn), fhi = float(hi / tn);
+        bool fdone = !live;
+        for (int round = 0; round < 64; ++round) {
+            const float w = fhi - flo;
+            if (!fdone && w <= 0x1p-20f) fdone = true;
+            if (__all_sync(0xffffffffu, fdone)) break;
+            const float x = flo + w * float(t + 1) / float(kSect + 1);
+            const int c = fdone ? 0 : sturm_count32(d32, e32, n, x, FLT_MIN);
+            float nlo = flo, nhi = fhi;
+            bool hit = false;
+#pragma unroll
+            for (int u = 0; u < kSect; ++u) {
+                const int cu = __shfl_sync(0xffffffffu, c, gbase + u);
+                const float xu = __shfl_sync(0xffffffffu, x, gbase + u);
+                if (!hit) {
+                    if (cu <= j) {
+                        nlo = xu;
+                    } else {
+                        nhi = xu;
+                        hit = true;
+                    }
+                }
+            }
+            if (!fdone) {
+                const bool stuck = !(nlo > flo || nhi < fhi);
+                flo = nlo;
+                fhi = nhi;
+                if (stuck) fdone = true;
+            }
+        }
+        const double margin = 16.0 * double(FLT_EPSILON) * tn;
+        const double clo = fmax(double(flo) * tn - margin, lo);
+        const double chi = fmin(double(fhi) * tn + margin, hi);
+        int cend = 0;
+        if (live && t < 2) cend = sturm_count(dd, ee, n, t == 0 ? clo : chi, pivmin);
+        const int clo_n = __shfl_sync(0xffffffffu, cend, gbase);
+        const int chi_n = __shfl_sync(0xffffffffu, cend, gbase + 1);
+        if (live && clo < chi && clo_n <= j && j < chi_n) {
+            lo = clo;
+            hi = chi;
+        }
+    }
     bool done = !live;
     for (int round = 0; round < 128; ++round) {
         // every group runs the same number of rounds of the warp's loop; finished or
@@ -519,7 +599,7 @@ __global__ void __launch_bounds__(kBisectThreads) bisect_kernel(const double* __
         bool hit = false;
 #pragma unroll
         for (int u = 0; u < kSect; ++u) {
-            const int src = ((threadIdx.x & 31) & ~(kSect - 1)) + u;
+            const int src = gbase + u;
             const int cu = __shfl_sync(0xffffffffu, c, src);
             const double xu = __shfl_sync(0xffffffffu, x, src);
             if (!hit) {
@@ -1172,8 +1252,10 @@ dmrg_status tridiag_eigen(dmrg_handle h, int64_t n64, int64_t mp64, char* ws, do
     }
     // 2. eigenvalues
     {
-        const bool staged = size_t(n) * 16 <= 96 * 1024;
-        const size_t smem = staged ? size_t(n) * 16 : 0;
+        // d and e^2 in shared memory, with their FP32 copies for the coarse phase when
+        // those fit too
+        const int staged = size_t(n) * 24 <= 96 * 1024 ? 2 : size_t(n) * 16 <= 96 * 1024 ? 1 : 0;
+        const size_t smem = size_t(n) * (staged == 2 ? 24 : staged == 1 ? 16 : 0);
         err = timed_launch(h, "trunc_bisect", s, [&] {
             tri_stats_kernel<<<1, kThreads, 0, s>>>(d, e, n, stats);
             if (!staged) square_kernel<<<unsigned((n + 255) / 256), 256, 0, s>>>(e, n, e2);
@@ -1187,7 +1269,7 @@ dmrg_status tridiag_eigen(dmrg_handle h, int64_t n64, int64_t mp64, char* ws, do
             cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  int(std::max<size_t>(smem, 1)));
             if (r != cudaSuccess) return r;
-            kern<<<blocks, kBisectThreads, smem, s>>>(d, e, n, stats, e2, staged ? 1 : 0, lambda);
+            kern<<<blocks, kBisectThreads, smem, s>>>(d, e, n, stats, e2, staged, lambda);
             return cudaGetLastError();
         });
         if (err != cudaSuccess) return cuda_fail(h, err, "bisection");
