@@ -1051,7 +1051,8 @@ __global__ void __launch_bounds__(kBackThreads) back_kernel(const double* __rest
                                                             const double* __restrict__ Zt, int n,
                                                             int mp, double* __restrict__ U) {
     extern __shared__ double bsm[];   // the vector (n), three reflector buffers (n each)
-    __shared__ double part[2][kBackSplit];
+    __shared__ double lanes[2][kBackThreads];   // every lane's part of v^T z
+    __shared__ double coef[2];                  // tau v^T z
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int j = blockIdx.x;
     double* z = bsm;
@@ -1082,17 +1083,22 @@ __global__ void __launch_bounds__(kBackThreads) back_kernel(const double* __rest
             const int i2 = i + 32 * kBackSplit;
             if (i2 < n) a1 = fma(v[i2 - (k + 1)], z[i2], a1);
         }
-        double sdot = a0 + a1;
-        for (int o = 16; o > 0; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
-        if (lane == 0) part[k & 1][w] = sdot;
+        lanes[k & 1][tid] = a0 + a1;
         cp_async_wait_all();   // v_{k-1}, fetched one reflector ago
-        __syncthreads();       // both halves of v^T z; v_{k-1} complete; every read of v_{k+1} done
+        __syncthreads();       // every lane's part of v^T z; v_{k-1} complete; v_{k+1} read
         fetch(k - 2, buf(slot == 0 ? 2 : slot - 1));   // into the buffer of v_{k+1}
-        if (t != 0.0) {
-            double sum = 0.0;
+        // One warp adds the parts and forms tau v^T z: an FP64 instruction holds the
+        // sub-partition's FP64 pipe for a whole warp, so the sum is not repeated per warp.
+        if (w == 0) {
+            double sdot = 0.0;
 #pragma unroll
-            for (int u = 0; u < kBackSplit; ++u) sum += part[k & 1][u];
-            const double c = t * sum;
+            for (int u = 0; u < kBackSplit; ++u) sdot += lanes[k & 1][32 * u + lane];
+            for (int o = 16; o > 0; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
+            if (lane == 0) coef[k & 1] = t * sdot;
+        }
+        __syncthreads();
+        if (t != 0.0) {
+            const double c = coef[k & 1];
             for (int i = i0; i < n; i += 32 * kBackSplit)
                 if (i > k) z[i] = fma(-c, v[i - (k + 1)], z[i]);
         }
