@@ -854,7 +854,7 @@ constexpr int kMgsThreads = 32 * kMgsG * kMgsS;
 struct MgsFlowArgs {
     double* Zt;           // mp x n, row j = eigenvector j (input and output)
     double* pub[2];       // per pass: published rows, mp x n
-    double* norms[2];     // per pass: squared norms of the published rows
+    double* norms[2];     // per pass: reciprocal squared norms of the published rows (0 for 0)
     unsigned* flags;      // [2][ngroups] publication flags, then the abort word; zeroed
     unsigned* status;
     uint64_t timeout_ns;
@@ -914,6 +914,7 @@ __device__ bool wait_flag(unsigned* flag, unsigned* abort_word, uint64_t timeout
 __global__ void __launch_bounds__(kMgsThreads) mgs_flow_kernel(MgsFlowArgs M) {
     extern __shared__ double own[];   // [owned group t][row][n], then pub[kMgsG][n]
     __shared__ double part[kMgsG][kMgsS];
+    __shared__ double rinv;
     const int n = M.n, mp = M.mp, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int w = warp / kMgsS;       // row of the group
     const int q = warp % kMgsS;       // slice of the row
@@ -959,12 +960,16 @@ __global__ void __launch_bounds__(kMgsThreads) mgs_flow_kernel(MgsFlowArgs M) {
                         for (int k = 0; k < kMgsS; ++k) nn += part[jj][k];
                         __syncthreads();
                     }
-                    if (threadIdx.x == 0) __stcg(norms + J * kMgsG + jj, nn);
+                    // the reciprocal, once: every projection of row jj multiplies by it
+                    if (threadIdx.x == 0) rinv = nn > 0.0 ? 1.0 / nn : 0.0;
+                    __syncthreads();
+                    const double rn = rinv;
+                    if (threadIdx.x == 0) __stcg(norms + J * kMgsG + jj, rn);
                     double* zr = grow + size_t(w) * n;
                     const bool mine = w > jj && w < nj;
                     const double dsum = row_sum(mine ? slice_dot(zj, zr, i0, i1, lane) : 0.0);
                     if (mine) {
-                        const double c = nn > 0.0 ? dsum / nn : 0.0;
+                        const double c = dsum * rn;
                         for (int i = i0 + lane; i < i1; i += 32) zr[i] = fma(-c, zj[i], zr[i]);
                     }
                     __syncthreads();
@@ -1000,10 +1005,10 @@ __global__ void __launch_bounds__(kMgsThreads) mgs_flow_kernel(MgsFlowArgs M) {
                 double* zr = own + (size_t(t) * kMgsG + w) * n;
                 for (int jj = 0; jj < nj; ++jj) {
                     const double* zj = stage + size_t(jj) * n;
-                    const double nn = __ldcg(norms + J * kMgsG + jj);
+                    const double rn = __ldcg(norms + J * kMgsG + jj);   // 1 / ||z_j||^2 (0 for 0)
                     const double dsum = row_sum(live ? slice_dot(zr, zj, i0, i1, lane) : 0.0);
                     if (live) {
-                        const double c = nn > 0.0 ? dsum / nn : 0.0;
+                        const double c = dsum * rn;
                         for (int i = i0 + lane; i < i1; i += 32) zr[i] = fma(-c, zj[i], zr[i]);
                     }
                 }
