@@ -169,24 +169,25 @@ __global__ void __launch_bounds__(kThreads, ACC == 128 ? 2 : 1)
                 const TcProblem* P = dt.P;
                 const int acc = it & 1;
                 const uint32_t acc_parity = uint32_t(it >> 1) & 1u;
-                if (!mbar_wait(&tempty[acc], acc_parity ^ 1u, tmo, L.status, vabort)) break;
-                tc_fence_after();
-                const uint32_t tmem_d = tmem_base + uint32_t(acc) * kAccStride;
+                // (everything that does not depend on a barrier is formed before its wait)
                 int n_eff = min(P->tile_n, P->N - dt.nt * P->tile_n);
                 n_eff = (n_eff + 15) & ~15;
                 const uint32_t idesc = make_idesc(kFmt, uint32_t(n_eff));
+                const uint32_t tmem_d = tmem_base + uint32_t(acc) * kAccStride;
+                if (!mbar_wait(&tempty[acc], acc_parity ^ 1u, tmo, L.status, vabort)) break;
+                tc_fence_after();
                 for (int kb = dt.kb_begin; kb < dt.kb_end; ++kb) {
-                    if (!mbar_wait(&full[stage], phase, tmo, L.status, vabort)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
                     const int rem = P->Kred - (kb % dt.kb_per_batch) * kElemsPerRow;
                     const int steps = min(kStepsPerBlock, (rem + kUmmaK - 1) / kUmmaK);
                     const uint64_t ah = smem_desc_kmajor<RB>(smem_u32(stage_a(stage, 0)));
                     const uint64_t bh = smem_desc_kmajor<RB>(smem_u32(stage_b(stage, 0)));
                     const uint64_t al = kSplit ? smem_desc_kmajor<RB>(smem_u32(stage_a(stage, 1))) : 0;
                     const uint64_t bl = kSplit ? smem_desc_kmajor<RB>(smem_u32(stage_b(stage, 1))) : 0;
+                    if (!mbar_wait(&full[stage], phase, tmo, L.status, vabort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
                     for (int k = 0; k < steps; ++k) {
                         const uint64_t off = uint64_t(k) * 2;  // 32 bytes in 16-byte units
                         const uint32_t accum = (kb > dt.kb_begin || k > 0) ? 1u : 0u;
