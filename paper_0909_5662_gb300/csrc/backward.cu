@@ -83,9 +83,11 @@ BwdDims bwd_dims(int64_t K, int64_t m, int d, int64_t mp, dmrg_precision p) {
     add(B.i_Ur, size_t(m) * B.ld_n);
     add(B.i_G, size_t(K) * mp * B.ld_u);
     add(B.i_GT, size_t(K) * mp * B.ld_u);
-    add(B.i_O, size_t(2 * K) * m * B.ld_j);       // [O | O^T], 2K slices of m x ld_j
-    add(B.i_Wp, size_t(K) * m * B.ld_n);          // W' row-major: rows (k, j), cols (s, a)
-    add(B.i_WT, size_t(2 * K) * B.dmp * B.ld_j);  // [WT' | WT], 2K slices of d*m' x ld_j
+    // BF16x3 reads O^T from O and W' row-major (MN-major operands): only O and WT are kept
+    const int64_t slices = split ? K : 2 * K;
+    add(B.i_O, size_t(slices) * m * B.ld_j);       // [O | O^T], slices of m x ld_j
+    add(B.i_Wp, size_t(K) * m * B.ld_n);           // W' row-major: rows (k, j), cols (s, a)
+    add(B.i_WT, size_t(slices) * B.dmp * B.ld_j);  // [WT' | WT], slices of d*m' x ld_j
     B.i_dU = int(W.offsets.size());
     W.add("dUpart", size_t(kBwdMaxParts) * B.md * mp * 4);
     B.i_conv = int(W.offsets.size());
@@ -307,7 +309,8 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
     dmrg_status st;
     char* wt_hi = sec(B.i_WT, 0);
     char* wt_lo = lo(B.i_WT);
-    const size_t wt_second = size_t(K) * dmp * B.ld_j * es;   // WT slices follow the WT' slices
+    // WT slices follow the WT' slices (BF16x3 keeps WT alone)
+    const size_t wt_second = mn ? 0 : size_t(K) * dmp * B.ld_j * es;
     // site-major copy of a W product: rows (k, a), columns c = s m + j -> slice k, row
     // s m' + a, column j
     auto site_major = [&](TcLaunch& L, char* hi, char* lo_) {
