@@ -142,6 +142,15 @@ DMRG_API dmrg_status dmrg_sync_status(dmrg_handle handle, dmrg_stream_t stream);
  *                              fits in two N tiles, else pack; 1 = always pack;
  *                              2 = convert whenever the layout allows.  FP64 operators
  *                              and other rows are always packed.
+ *   DMRG_OPT_STORE_EPILOGUE  : how the BF16x3 first product (on CTA pairs) writes its
+ *                              result T = O_k U_r.  0 (default) = each epilogue warp
+ *                              stages a 32 x 32 chunk of BF16 hi/lo values in shared
+ *                              memory and one lane sends it out with TMA bulk tensor
+ *                              stores, where d is 2 or 4, m is a multiple of 16 and
+ *                              the shared memory holds the staging (else as 1);
+ *                              1 = every thread stores its own values.  The values
+ *                              written are the same.  Other values return
+ *                              DMRG_ERR_INVALID_ARG.
  *   DMRG_OPT_TEST_WITHHOLD_ARRIVAL : test hook for failure detection.  1 makes
  *                              the next dense tensor-core launch withhold one
  *                              shared-memory stage release in its first CTA, so
@@ -160,7 +169,8 @@ typedef enum {
     DMRG_OPT_BLOCKED_SMALL = 8,
     DMRG_OPT_TRUNCATION_JACOBI = 9,
     DMRG_OPT_FUSED_ROTATION = 10,
-    DMRG_OPT_PACK_OPERATORS = 11
+    DMRG_OPT_PACK_OPERATORS = 11,
+    DMRG_OPT_STORE_EPILOGUE = 12
 } dmrg_option;
 DMRG_API dmrg_status dmrg_set_option(dmrg_handle handle, dmrg_option option, double value);
 

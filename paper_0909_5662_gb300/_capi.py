@@ -20,7 +20,8 @@ STATUS = {0: "DMRG_OK", 1: "DMRG_ERR_INVALID_ARG", 2: "DMRG_ERR_SHAPE",
 PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3}
 OPTION = {"graph": 1, "kernel_timing": 2, "wait_timeout_ms": 3, "check_ortho": 4,
           "test_withhold_arrival": 5, "deterministic": 6, "accum_chain": 7, "blocked_small": 8,
-          "truncation_jacobi": 9, "fused_rotation": 10, "pack_operators": 11}
+          "truncation_jacobi": 9, "fused_rotation": 10, "pack_operators": 11,
+          "store_epilogue": 12}
 
 _p = ctypes.c_void_p
 _i64 = ctypes.c_int64

@@ -389,6 +389,17 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     L1.row_bytes = c1.row_bytes;
     L1.chunk_scratch = L1.inline_prob[0].kb_chunk ? chain_scr : nullptr;
     L1.convert_a = convert_a ? 1 : 0;
+    // BF16x3 on CTA pairs: T leaves through TMA bulk stores (staged per warp in shared
+    // memory) rather than 8-byte stores from registers, where the layout allows it
+    if (split && c1.pair && h->store_epilogue == 0 && (d == 2 || d == 4) && m % 16 == 0) {
+        bool ok = true;
+        for (int c = 0; c < 2 && ok; ++c)
+            ok = encode_store_map(&L1.t_store[c], Tt[c], D.md, mp, K, D.ld2, d);
+        if (ok) {
+            L1.t_store_d = d;
+            for (int c = 0; c < nprob1; ++c) L1.inline_prob[c].store_z0 = int32_t(cls ? cls->k0[c] : 0);
+        }
+    }
     // The packing pass wrote the operators in row order and the rows it wrote last are
     // the ones still in L2: the first product starts from the last M tile.  It then leaves
     // the first operators' T rows in L2 for the second product, which starts there.
@@ -626,6 +637,11 @@ dmrg_status dmrg_set_option(dmrg_handle h, dmrg_option o, double v) {
                 return fail(h, DMRG_ERR_INVALID_ARG, "pack_operators must be 0, 1 or 2");
             h->pack_operators = int(v);
             return DMRG_OK;
+        case DMRG_OPT_STORE_EPILOGUE:
+            if (!(v == 0 || v == 1))
+                return fail(h, DMRG_ERR_INVALID_ARG, "store_epilogue must be 0 or 1");
+            h->store_epilogue = int(v);
+            return DMRG_OK;
         case DMRG_OPT_FUSED_ROTATION:
             if (!(v == 0 || v == 1))
                 return fail(h, DMRG_ERR_INVALID_ARG, "fused_rotation must be 0 or 1");
@@ -719,9 +735,12 @@ dmrg_status dmrg_rotate_ops(dmrg_handle h, const double* U, int64_t m, int d, in
             return fail(h, DMRG_ERR_NOT_ORTHONORMAL, b);
         }
     }
+    // the options that change the launches are part of the key
     char key[256];
-    snprintf(key, sizeof key, "dense:%p:%p:%p:%p:%p:%lld:%lld:%d:%lld:%d:%d", (const void*)U, O,
-             Oout, ws, (void*)s, (long long)K, (long long)m, d, (long long)mp, int(p), in_is_fp64);
+    snprintf(key, sizeof key, "dense:%p:%p:%p:%p:%p:%lld:%lld:%d:%lld:%d:%d:%d%d%d%d:%d", (const void*)U,
+             O, Oout, ws, (void*)s, (long long)K, (long long)m, d, (long long)mp, int(p), in_is_fp64,
+             int(h->deterministic), h->pack_operators, h->fused_rotation, h->store_epilogue,
+             h->accum_chain);
     return run_maybe_graph(h, key, s, [&](cudaStream_t cs) -> dmrg_status {
         if (!tc) return dense_simt_forward(h, U, m, d, mp, O, in_is_fp64, K, Oout, p, ws, cs, true);
         if (h->fused_rotation && p == DMRG_PREC_BF16X3 && mp <= kFusedMaxMp)

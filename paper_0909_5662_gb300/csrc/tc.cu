@@ -866,9 +866,8 @@ namespace {
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 }
 
-bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t rows, int64_t cols,
-                        int64_t ld, int box_rows, int64_t nbatch, int64_t batch_stride,
-                        int row_bytes) {
+// Looks up cuTensorMapEncodeTiled once (through the runtime: no driver library link).
+static bool have_encode() {
     if (g_encode == nullptr) {
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q;
@@ -878,6 +877,13 @@ bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t r
             return false;
         g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
+    return true;
+}
+
+bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t rows, int64_t cols,
+                        int64_t ld, int box_rows, int64_t nbatch, int64_t batch_stride,
+                        int row_bytes) {
+    if (!have_encode()) return false;
     const int esize = fp32 ? 4 : 2;
     if (nbatch < 1) nbatch = 1;
     if (nbatch == 1) batch_stride = rows * ld;
@@ -891,6 +897,21 @@ bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t r
                           CU_TENSOR_MAP_INTERLEAVE_NONE,
                           row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+bool encode_store_map(CUtensorMap* map, void* base, int64_t md, int64_t mp, int64_t K, int64_t ld,
+                      int d) {
+    if (!(d == 2 || d == 4) || (ld % 8) != 0 || md > ld || (reinterpret_cast<uintptr_t>(base) & 15))
+        return false;
+    if (!have_encode()) return false;
+    cuuint64_t gdim[3] = {cuuint64_t(md), cuuint64_t(mp), cuuint64_t(K)};
+    cuuint64_t gstride[2] = {cuuint64_t(ld) * 2, cuuint64_t(mp * ld) * 2};
+    cuuint32_t box[3] = {cuuint32_t(16 * d), cuuint32_t(32 / d), 1};
+    cuuint32_t estride[3] = {1, 1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, gdim, gstride, box, estride,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 

@@ -90,6 +90,64 @@ __device__ __forceinline__ void split2(float x, float y, uint32_t& hi, uint32_t&
     lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
+__device__ __forceinline__ void fence_proxy_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void st_shared_v2u(uint32_t addr, uint32_t a, uint32_t b) {
+    asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
+}
+__device__ __forceinline__ void st_shared_u32(uint32_t addr, uint32_t a) {
+    asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(a) : "memory");
+}
+
+// TMA-store epilogue (TcLaunch::t_store_d = d): one 32-column chunk of this warp's 32
+// rows, split into BF16 hi/lo, staged in the warp's 4 KB of shared memory `stg` and sent
+// out by lane 0 as up to four bulk tensor stores.  The chunk covers 32 / d values of b
+// and the warp's rows are two groups of 16 consecutive rows i (each inside one operator,
+// rows_per_op being a multiple of 16): the staging holds one store box per (group, half):
+// hi at stg + group * 1024, lo 2048 further, each box 32 / d rows b of 16 d elements
+// (i * d + s).  Lane l's values of (b, s = 0..d-1) land in row b of its group's box at
+// element (l % 16) * d.  x[g], z[g]: the box coordinates of group g (valid[g] = 0: the
+// group lies past the last row); y = the chunk's first b.  A lane's r[] need not hold
+// data when its group is not stored.
+__device__ __forceinline__ void store_chunk_tma(const TcLaunch& L, const uint32_t (&r)[32],
+                                                uint32_t stg, int lane, int d, const int (&x)[2],
+                                                int y, const int (&z)[2], const bool (&valid)[2]) {
+    if (lane == 0) bulk_wait_group_read0();   // the previous chunk's stores have read stg
+    __syncwarp();
+    const uint32_t box = stg + uint32_t(lane >> 4) * 1024u + uint32_t(lane & 15) * uint32_t(2 * d);
+    if (d == 4) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {   // row b = j: columns 4j .. 4j+3
+            uint32_t h0, l0, h1, l1;
+            split2(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]), h0, l0);
+            split2(__uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]), h1, l1);
+            st_shared_v2u(box + uint32_t(j) * 128u, h0, h1);
+            st_shared_v2u(box + 2048u + uint32_t(j) * 128u, l0, l1);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {   // d = 2, row b = j: columns 2j, 2j+1
+            uint32_t h0, l0;
+            split2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]), h0, l0);
+            st_shared_u32(box + uint32_t(j) * 64u, h0);
+            st_shared_u32(box + 2048u + uint32_t(j) * 64u, l0);
+        }
+    }
+    fence_proxy_async_shared();   // the staging writes, before the tensor stores read them
+    __syncwarp();
+    if (lane == 0) {
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            if (!valid[g]) continue;
+            tma_store_3d(&L.t_store[0], stg + uint32_t(g) * 1024u, x[g], y, z[g]);
+            tma_store_3d(&L.t_store[1], stg + 2048u + uint32_t(g) * 1024u, x[g], y, z[g]);
+        }
+        bulk_commit_group();
+    }
+}
+
 // Converts row `row` of this CTA's A tile in place (see the converting form above).
 // box0 / box1: shared addresses of the two 128 x 128-byte regions of the stage's A.
 template <int MODE>
@@ -126,10 +184,6 @@ __device__ __forceinline__ void convert_a_row(uint32_t box0, uint32_t box1, int 
                           __float_as_uint(tf32_round(v.z)), __float_as_uint(tf32_round(v.w)));
         }
     }
-}
-
-__device__ __forceinline__ void fence_proxy_async_shared() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // SITE: the launch also writes the site-major second copy (TcLaunch::out2); a separate
@@ -434,6 +488,11 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                           ? reinterpret_cast<float4*>(L.chunk_scratch) +
                                 (int64_t(blockIdx.x) * 4 + quad) * (8 * 8 * 32) + lane
                           : nullptr;
+        // TMA-store epilogue: this warp's 4 KB of staging after the barriers
+        constexpr bool kStoreOk = (EPI == EPI_SPLIT_BF16) && !SITE;
+        const int tsd = kStoreOk ? L.t_store_d : 0;
+        const uint32_t stg = smem_u32(smem + size_t(stages) * stage_bytes + 512) +
+                             uint32_t(warp - 2) * 4096u;
         for (int t = pair; t < L.total_tiles && ok; t += npairs) {
             const Decoded dt = decode_tile(L, t, kElemsPerRow);
             const TcProblem* P = dt.P;
@@ -453,6 +512,19 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
             const int cdiv = S.col_div;
             const int64_t sch = S.s_col_hi, scl = S.s_col_lo;
             const bool tile_atomic = P->atomic != 0;
+            // store boxes of the warp's two 16-row groups (TMA-store epilogue)
+            int bx[2] = {0, 0}, bz[2] = {0, 0};
+            bool bvalid[2] = {false, false};
+            if (tsd) {
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    const int rg = row - lane + 16 * g;
+                    bvalid[g] = rg < P->M && dt.kb_begin < dt.kb_end;
+                    const int op = rg / S.rows_per_op;
+                    bx[g] = (rg - op * S.rows_per_op) * tsd;
+                    bz[g] = P->store_z0 + op;
+                }
+            }
             const int chunk = (P->kb_chunk > 0 && scr) ? P->kb_chunk : (dt.kb_end - dt.kb_begin);
             int kb0 = dt.kb_begin;
             bool first = true;
@@ -476,6 +548,9 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                                        r);
                     tmem_ld_wait();
                     const int cmax = min(32, ncols - c);   // the same for the whole warp
+                    // a chunk goes out by TMA unless it is short inside N (the box would
+                    // spill into the next tile's columns; past N the map clips it)
+                    const bool tma_chunk = tsd && last && (cmax == 32 || n0 + ncols == P->N);
                     if (row_ok) {
                         float4* s4 = scr ? scr + (c >> 5) * (8 * 32) : nullptr;
                         if (!first) {   // add the chains before this one
@@ -493,10 +568,12 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                             for (int j = 0; j < 8; ++j)
                                 s4[j * 32] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
                                                     __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
-                        } else if (L.out[0][0] != nullptr) {   // (a launch may want the second copy only)
+                        } else if (!tma_chunk && L.out[0][0] != nullptr) {   // (a launch may want
+                                                                             // the second copy only)
                             store_chunk<EPI>(L, r, row_base, n0, c, cmax, cdiv, sch, scl, tile_atomic);
                         }
                     }
+                    if (tma_chunk) store_chunk_tma(L, r, stg, lane, tsd, bx, (n0 + c) / tsd, bz, bvalid);
                     // the site-major copy's stores are warp-collective: every lane comes here
                     if (SITE && (EPI == EPI_SPLIT_BF16 || EPI == EPI_TF32) && last)
                         store_chunk_site_major<EPI>(L, r, row, n0 + c, cmax, row_ok);
@@ -512,6 +589,8 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                 kb0 = kb1;
             } while (kb0 < dt.kb_end);
         }
+        // the TMA stores are complete before the CTA (and its shared memory) goes away
+        if (tsd && lane == 0) bulk_wait_group0();
     }
 
     tc_fence_before();
@@ -588,10 +667,12 @@ cudaError_t launch_pair(const TcLaunch& L, int stages, int grid, int bh_smem, si
     return cudaLaunchKernelEx(&cfg, k, L, stages, bh_smem);
 }
 
-size_t pair_smem_bytes(TcMode mode, int stages, int bh, int rb) {
+// Stages, barriers (within 512 bytes) and, for the TMA-store epilogue, the staging.
+size_t pair_smem_bytes(TcMode mode, int stages, int bh, int rb, bool t_store = false) {
     const size_t a = size_t(kBM) * rb, b = size_t(bh) * rb;
     const size_t stage = (a + b) * (mode == TC_BF16X3 ? 2 : 1);
-    return 1024 + stage * stages + 8 * (3 * size_t(stages) + 5) + 32;
+    const size_t bars = 8 * (3 * size_t(stages) + 5) + 32;
+    return 1024 + stage * stages + (t_store ? 512 + kStoreStagingBytes : bars);
 }
 
 }  // namespace
@@ -622,11 +703,32 @@ cudaError_t tc_gemm_launch_pair(TcMode mode, TcEpi epi, const TcLaunch& L, int s
     if (any_mn && (mode == TC_TF32 || L.row_bytes != 128 || L.convert_a)) return cudaErrorInvalidValue;
     // an MN-major B share is two 64-row boxes whatever the tile width
     const int bh = b_mn ? 2 * kMnBox : bn / 2;
-    const size_t smem = pair_smem_bytes(mode, stages, bh, L.row_bytes);
+    size_t smem = pair_smem_bytes(mode, stages, bh, L.row_bytes);
     if (smem > 232448) return cudaErrorInvalidConfiguration;
     grid = std::max(2, std::min(grid, 2 * L.total_tiles)) / 2 * 2;
+    // TMA-store epilogue: only for the BF16 split output without the second copy, and
+    // only where its staging fits; otherwise the same launch stores from registers.
+    const TcLaunch* Lp = &L;
+    TcLaunch plain;
+    if (L.t_store_d != 0) {
+        bool ok = epi == EPI_SPLIT_BF16 && L.out2[0] == nullptr && L.out[0][0] != nullptr &&
+                  (L.t_store_d == 2 || L.t_store_d == 4);
+        for (int i = 0; ok && i < L.nprob; ++i) {
+            const TcProblem& P = L.inline_prob[i];
+            ok = P.k_splits == 1 && P.sc[0].s_split == 0 && P.sc[0].rows_per_op % 16 == 0 &&
+                 P.sc[0].col_div == L.t_store_d;
+        }
+        const size_t with = pair_smem_bytes(mode, stages, bh, L.row_bytes, true);
+        if (ok && with <= 232448) {
+            smem = with;
+        } else {
+            plain = L;
+            plain.t_store_d = 0;
+            Lp = &plain;
+        }
+    }
 #define DMRG_TC_CASE(M, E) \
-    if (mode == M && epi == E) return launch_pair<M, E>(L, stages, grid, bh, smem, s);
+    if (mode == M && epi == E) return launch_pair<M, E>(*Lp, stages, grid, bh, smem, s);
     DMRG_TC_CASE(TC_BF16X3, EPI_SPLIT_BF16)
     DMRG_TC_CASE(TC_BF16X3, EPI_F32)
     DMRG_TC_CASE(TC_BF16X3, EPI_F32_ATOMIC)

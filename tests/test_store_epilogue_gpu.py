@@ -1,0 +1,138 @@
+"""GPU parity of the BF16x3 first product's TMA-store epilogue (T = O_k U_r leaving the
+CTA-pair kernel through bulk tensor stores staged in shared memory) against the same
+kernel storing from registers, and of both against the FP64 oracle of the rotation
+O'_k = U^T (O_k (x) I_d) U (Sec. 2 step 5).
+
+The two epilogues write the same BF16 hi/lo values to the same places, so with the
+deterministic option the rotated operators must agree bit for bit.  The shapes cover
+both site dimensions the store maps take (d = 2, 4), operators that begin in the middle
+of a warp's 32 rows (m = 48, 400), chunks that are short inside N (N tiles of 208 and
+176 columns) and at the end of N (d * m' not a multiple of 32), rows past the last
+operator, accumulation chains (m > 1024), and layouts that fall back to register stores
+(d = 3, m not a multiple of 16).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from workloads import orthonormal_columns
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_0909_5662_gb300 as lib
+    return lib
+
+
+def rel_err(got, ref):
+    num = np.linalg.norm((got - ref).reshape(len(ref), -1), axis=1)
+    return num / np.linalg.norm(ref.reshape(len(ref), -1), axis=1)
+
+
+def rotate(P, U, O, d, store, opts=()):
+    h = P.Handle()
+    try:
+        P.dmrg_set_option("deterministic", 1, handle=h)
+        P.dmrg_set_option("store_epilogue", store, handle=h)
+        for k, v in opts:
+            P.dmrg_set_option(k, v, handle=h)
+        out = P.dmrg_rotate_ops(U, O, d, "bf16x3", handle=h)
+        torch.cuda.synchronize()
+        P.dmrg_sync_status(handle=h)
+        return out.double().cpu().numpy()
+    finally:
+        h.close()
+
+
+SHAPES = [
+    # (m, d, mp, K)
+    (16, 4, 8, 1),        # one 16-row group, one short chunk at the end of N
+    (48, 4, 100, 7),      # operators start inside a warp's rows; rows past the last one
+    (400, 4, 400, 9),     # the benchmark's m, d, m' (N tiles of 256, a short last tile)
+    (64, 2, 104, 5),      # d = 2: N = 208, one 208-column tile (a 16-column chunk at N's end)
+    (96, 4, 130, 3),      # N = 520: tiles of 176 (a short chunk inside N) and 168
+    (1040, 4, 64, 2),     # accumulation chains over the reduction (m > 1024)
+    (160, 2, 333, 4),     # d = 2, odd m': the last chunk partly past N
+    (50, 4, 60, 3),       # m not a multiple of 16: register stores
+    (48, 3, 70, 3),       # d = 3: register stores
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_tma_store_epilogue_matches_register_stores_and_oracle(P, shape):
+    m, d, mp, K = shape
+    rng = np.random.default_rng(9500 + m + 7 * mp + K)
+    U = orthonormal_columns(rng, m * d, mp)
+    O = rng.standard_normal((K, m, m)).astype(np.float32)
+    dev = torch.device("cuda")
+    Ud, Od = torch.from_numpy(U).to(dev), torch.from_numpy(O).to(dev)
+    tma = rotate(P, Ud, Od, d, 0, opts=(("pack_operators", 1),))
+    reg = rotate(P, Ud, Od, d, 1, opts=(("pack_operators", 1),))
+    assert np.array_equal(tma, reg)
+    ref = oracle.rotate_dense(U, O.astype(np.float64), d)
+    assert rel_err(tma, ref).max() <= TOL
+
+
+@pytest.mark.parametrize("shape", [(64, 4, 64, 5), (48, 2, 100, 4)])
+def test_tma_store_epilogue_with_converting_form(P, shape):
+    # the converting first product (FP32 operators split in shared memory) keeps its
+    # stage layout; the staging goes after it when it fits
+    m, d, mp, K = shape
+    rng = np.random.default_rng(9600 + m + mp)
+    U = orthonormal_columns(rng, m * d, mp)
+    O = rng.standard_normal((K, m, m)).astype(np.float32)
+    dev = torch.device("cuda")
+    Ud, Od = torch.from_numpy(U).to(dev), torch.from_numpy(O).to(dev)
+    tma = rotate(P, Ud, Od, d, 0, opts=(("pack_operators", 2),))
+    reg = rotate(P, Ud, Od, d, 1, opts=(("pack_operators", 2),))
+    assert np.array_equal(tma, reg)
+    assert rel_err(tma, oracle.rotate_dense(U, O.astype(np.float64), d)).max() <= TOL
+
+
+def test_tma_store_epilogue_site_classes(P):
+    # site operators: the first product runs as one problem per class of operators, each
+    # writing its own range of T (the store maps' operator index starts at the class's k0)
+    m, d, mp = 64, 4, 96
+    counts, flags = [2, 1, 3, 1, 2], [1, 0, 1, 0, 1]
+    rng = np.random.default_rng(9700)
+    U = orthonormal_columns(rng, m * d, mp)
+    K = sum(counts)
+    A = rng.standard_normal((K, m, m))
+    S = rng.standard_normal((len(counts), d, d))
+    parity = rng.choice([-1.0, 1.0], m)
+    dev = torch.device("cuda")
+    par = torch.from_numpy(parity.astype(np.int8)).to(dev)
+    outs = []
+    for store in (0, 1):
+        h = P.Handle()
+        try:
+            P.dmrg_set_option("deterministic", 1, handle=h)
+            P.dmrg_set_option("store_epilogue", store, handle=h)
+            out = P.dmrg_rotate_site_ops(torch.from_numpy(U).to(dev),
+                                         torch.from_numpy(A).to(dev, torch.float32), d, S,
+                                         counts, flags, par, "bf16x3", handle=h)
+            torch.cuda.synchronize()
+            P.dmrg_sync_status(handle=h)
+            outs.append(out.double().cpu().numpy())
+        finally:
+            h.close()
+    assert np.array_equal(outs[0], outs[1])
+    ref = oracle.rotate_site(U, A.astype(np.float32).astype(np.float64), d, S, counts, flags, parity)
+    assert rel_err(outs[0], ref).max() <= TOL
+
+
+def test_store_epilogue_option_values(P):
+    from paper_0909_5662_gb300._capi import DmrgError
+    h = P.Handle()
+    try:
+        for v in (0, 1):
+            P.dmrg_set_option("store_epilogue", v, handle=h)
+        with pytest.raises(DmrgError):
+            P.dmrg_set_option("store_epilogue", 2, handle=h)
+    finally:
+        h.close()
