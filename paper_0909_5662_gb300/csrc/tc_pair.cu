@@ -203,6 +203,14 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
     // MN-major operands: BF16 with 128-byte rows only (the host refuses other forms)
     constexpr bool kMnOk = MN && (MODE != TC_TF32) && (RB == 128) && !CONV;
     constexpr uint32_t kMnBoxBytes = uint32_t(kMnBox) * 128u;
+    // FP32 output: the chains of a tile are summed in the output itself (the first chain
+    // stores, later ones add with reductions).  Only the MN-major instantiation (the
+    // adjoint's dU products, up to eight chains per tile, for which the reductions
+    // measured slower) carries the scratch code for FP32 and uses it when given one;
+    // elsewhere the unused scratch code alone cost 2-3 % of the second product.
+    constexpr bool kF32Out = (EPI == EPI_F32 || EPI == EPI_F32_ATOMIC);
+    constexpr bool kScratchCode = !kF32Out || MN;
+    const bool sum_in_out = kF32Out && (!MN || L.chunk_scratch == nullptr);
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -381,7 +389,7 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                 auto desc = [&](uint8_t* base, uint64_t bits) -> uint64_t {
                     return bits | uint64_t((smem_u32(base) & 0x3FFFFu) >> 4);
                 };
-                const int chunk = (P->kb_chunk > 0 && L.chunk_scratch) ? P->kb_chunk
+                const int chunk = (P->kb_chunk > 0 && (kF32Out || L.chunk_scratch)) ? P->kb_chunk
                                                                         : (dt.kb_end - dt.kb_begin);
                 int kb0 = dt.kb_begin;
                 do {   // one chain per chunk of k-blocks (at least one, even for an empty tile)
@@ -484,7 +492,8 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
         // CTA's 128 x 256 block of the scratch, stored lane-interleaved so that a warp's
         // 16-byte accesses are contiguous: the float4 j of 32-column chunk ci of lane l of
         // TMEM lane quadrant q sits at float4 index ((q * 8 + ci) * 8 + j) * 32 + l.
-        float4* scr = L.chunk_scratch
+        // FP32 epilogues mostly keep the running sums in the output (sum_in_out).
+        float4* scr = (kScratchCode && L.chunk_scratch)
                           ? reinterpret_cast<float4*>(L.chunk_scratch) +
                                 (int64_t(blockIdx.x) * 4 + quad) * (8 * 8 * 32) + lane
                           : nullptr;
@@ -525,7 +534,8 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                     bz[g] = P->store_z0 + op;
                 }
             }
-            const int chunk = (P->kb_chunk > 0 && scr) ? P->kb_chunk : (dt.kb_end - dt.kb_begin);
+            const int chunk = (P->kb_chunk > 0 && (kF32Out || scr)) ? P->kb_chunk
+                                                                       : (dt.kb_end - dt.kb_begin);
             int kb0 = dt.kb_begin;
             bool first = true;
             do {
@@ -551,29 +561,42 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                     // a chunk goes out by TMA unless it is short inside N (the box would
                     // spill into the next tile's columns; past N the map clips it)
                     const bool tma_chunk = tsd && last && (cmax == 32 || n0 + ncols == P->N);
-                    if (row_ok) {
-                        float4* s4 = scr ? scr + (c >> 5) * (8 * 32) : nullptr;
-                        if (!first) {   // add the chains before this one
+                    if (sum_in_out) {
+                        // the first chain stores, each later one adds into the output
+                        // (the same lane, in program order: the same FP32 additions in
+                        // the same order as through the scratch, subnormal sums aside,
+                        // which the reductions flush to zero)
+                        if (row_ok && L.out[0][0] != nullptr)
+                            store_chunk<EPI>(L, r, row_base, n0, c, cmax, cdiv, sch, scl,
+                                             tile_atomic || !first);
+                    } else if constexpr (kScratchCode) {
+                        if (row_ok) {
+                            float4* s4 = scr ? scr + (c >> 5) * (8 * 32) : nullptr;
+                            if (!first) {   // add the chains before this one
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) {
-                                const float4 v = s4[j * 32];
-                                r[4 * j] = __float_as_uint(__uint_as_float(r[4 * j]) + v.x);
-                                r[4 * j + 1] = __float_as_uint(__uint_as_float(r[4 * j + 1]) + v.y);
-                                r[4 * j + 2] = __float_as_uint(__uint_as_float(r[4 * j + 2]) + v.z);
-                                r[4 * j + 3] = __float_as_uint(__uint_as_float(r[4 * j + 3]) + v.w);
+                                for (int j = 0; j < 8; ++j) {
+                                    const float4 v = s4[j * 32];
+                                    r[4 * j] = __float_as_uint(__uint_as_float(r[4 * j]) + v.x);
+                                    r[4 * j + 1] = __float_as_uint(__uint_as_float(r[4 * j + 1]) + v.y);
+                                    r[4 * j + 2] = __float_as_uint(__uint_as_float(r[4 * j + 2]) + v.z);
+                                    r[4 * j + 3] = __float_as_uint(__uint_as_float(r[4 * j + 3]) + v.w);
+                                }
+                            }
+                            if (!last) {
+#pragma unroll
+                                for (int j = 0; j < 8; ++j)
+                                    s4[j * 32] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                                        __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+                            } else if (!tma_chunk && L.out[0][0] != nullptr) {   // (a launch may want
+                                                                                 // the second copy only)
+                                store_chunk<EPI>(L, r, row_base, n0, c, cmax, cdiv, sch, scl, tile_atomic);
                             }
                         }
-                        if (!last) {
-#pragma unroll
-                            for (int j = 0; j < 8; ++j)
-                                s4[j * 32] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                                                    __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
-                        } else if (!tma_chunk && L.out[0][0] != nullptr) {   // (a launch may want
-                                                                             // the second copy only)
-                            store_chunk<EPI>(L, r, row_base, n0, c, cmax, cdiv, sch, scl, tile_atomic);
-                        }
                     }
-                    if (tma_chunk) store_chunk_tma(L, r, stg, lane, tsd, bx, (n0 + c) / tsd, bz, bvalid);
+                    if constexpr (kStoreOk) {
+                        if (tma_chunk)
+                            store_chunk_tma(L, r, stg, lane, tsd, bx, (n0 + c) / tsd, bz, bvalid);
+                    }
                     // the site-major copy's stores are warp-collective: every lane comes here
                     if (SITE && (EPI == EPI_SPLIT_BF16 || EPI == EPI_TF32) && last)
                         store_chunk_site_major<EPI>(L, r, row, n0 + c, cmax, row_ok);
