@@ -397,8 +397,9 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     if (split && c1.pair && h->store_epilogue == 0 && (d == 2 || d == 4) && m % 16 == 0) {
         bool ok = true;
         for (int c = 0; c < 2 && ok; ++c)
-            ok = encode_store_map(&L1.t_store[c], Tt[c], D.md, mp, K, D.ld2, d);
+            ok = encode_store_map(&L1.t_store_map[c], Tt[c], D.md, mp, K, D.ld2, 16 * d, 32 / d);
         if (ok) {
+            L1.t_store = kStoreSiteInterleaved;
             L1.t_store_d = d;
             for (int c = 0; c < nprob1; ++c) L1.inline_prob[c].store_z0 = int32_t(cls ? cls->k0[c] : 0);
         }

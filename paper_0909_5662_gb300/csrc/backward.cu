@@ -252,10 +252,6 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
             jr.rdiv = 1; jr.s_r_hi = dmp; jr.s_c = 1; jr.dst0 = sec(B.i_Ur, 0); jr.dst1 = lo(B.i_Ur);
             jr.ld = B.ld_n;
         }
-        PackJob& jg = jobs[nj++];   // G: rows (k, a), cols b = G_k[a][b]
-        jg.src = G; jg.src_f64 = in_is_fp64; jg.mode = pmode; jg.rows = K * mp; jg.cols = mp;
-        jg.rows_per_op = K * mp; jg.rdiv = 1; jg.s_r_hi = mp; jg.s_c = 1;
-        jg.dst0 = sec(B.i_G, 0); jg.dst1 = lo(B.i_G); jg.ld = B.ld_u;
         if (dU) {
             PackJob& jt = jobs[nj++];   // G^T: rows (k, b), cols a = G_k[a][b]
             jt.src = G; jt.src_f64 = in_is_fp64; jt.mode = pmode; jt.rows = K * mp; jt.cols = mp;
@@ -273,6 +269,12 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
                 jq.dst0 = sec(B.i_O, 0) + oT; jq.dst1 = lo(B.i_O) + (split ? oT : 0); jq.ld = B.ld_j;
             }
         }
+        // G last: its last rows are still in L2 when the W' product, which runs its M tiles
+        // from the last to the first, starts reading them
+        PackJob& jg = jobs[nj++];   // G: rows (k, a), cols b = G_k[a][b]
+        jg.src = G; jg.src_f64 = in_is_fp64; jg.mode = pmode; jg.rows = K * mp; jg.cols = mp;
+        jg.rows_per_op = K * mp; jg.rdiv = 1; jg.s_r_hi = mp; jg.s_c = 1;
+        jg.dst0 = sec(B.i_G, 0); jg.dst1 = lo(B.i_G); jg.ld = B.ld_u;
         e = timed_launch(h, "bwd_pack", s, [&] { return pack_launch(jobs, nj, nullptr, s); });
         if (e != cudaSuccess) return cuda_fail(h, e, "pack");
     }
@@ -336,10 +338,20 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
         S.rows_per_op = int32_t(mp); S.s_op = m * B.ld_n; S.s_row = 1;
         S.col_div = int32_t(m); S.s_col_hi = mp; S.s_col_lo = B.ld_n;
         L.nprob = 1;
+        // last M tile first (G's last rows are the packer's latest writes); the W' rows of
+        // the first operators, written last, are then in L2 for the dO product
+        L.reverse_m = 1;
         const bool rowmajor = dO || (dU && mn);
         L.out[0][0] = rowmajor ? sec(B.i_Wp, 0) : nullptr;
         L.out[0][1] = rowmajor ? lo(B.i_Wp) : nullptr;
         if (dU && !mn) site_major(L, wt_hi, wt_lo);
+        // BF16x3, row-major only: W' leaves by TMA bulk stores (W'_k rows j, columns
+        // s m' + a; a lane's values run down a column), staged per warp in shared memory
+        if (split && rowmajor && L.out2[0] == nullptr && h->store_epilogue == 0 && m % 16 == 0 &&
+            mp % 16 == 0 &&
+            encode_store_map(&L.t_store_map[0], L.out[0][0], dmp, m, K, B.ld_n, 16, 16) &&
+            encode_store_map(&L.t_store_map[1], L.out[0][1], dmp, m, K, B.ld_n, 16, 16))
+            L.t_store = kStoreRowContiguous;
         if ((st = launch("bwd_tc_Wp", L, epi_op, mp)) != DMRG_OK) return st;
     }
     if (dO) {

@@ -96,7 +96,7 @@ struct TcProblem {  // 64-byte aligned through its CUtensorMap members
                          // chains of a tile are summed in FP32 registers (0: one chain)
     int32_t a_mn, b_mn;  // CTA-pair kernel, BF16 operands: A / B stored MN-major (its M / N
                          // index contiguous in memory), read in 64-column boxes
-    int32_t store_z0;    // with TcLaunch::t_store_d: operator index of this problem's first
+    int32_t store_z0;    // with TcLaunch::t_store: operator index of this problem's first
                          // operator in the store maps
     TcScatter sc[1];
 };
@@ -154,16 +154,24 @@ struct TcLaunch {
     void* out2[2];
     int64_t o2_s_op, o2_s_row, o2_s_site;
     int32_t o2_rows_per_op, o2_m;
-    // CTA-pair kernel, EPI_SPLIT_BF16: t_store_d = d (2 or 4) sends the result out by TMA
-    // bulk stores instead of stores from registers (0: off).  The scatter must then be
-    // the first product's layout T[k][b][i * d + s] (column n = b * d + s of row
-    // R = k_local * rows_per_op + i, rows_per_op a multiple of 16), and t_store[hi, lo]
-    // map it in 3-D: (i * d + s, b, k) with k = store_z0 + k_local, box 16 d x 32 / d x 1.
-    // Each epilogue warp stages one 32-column chunk (hi and lo) in shared memory;
-    // launches whose shared memory cannot hold the staging store from registers.
-    CUtensorMap t_store[2];
+    // CTA-pair kernel, EPI_SPLIT_BF16: the result leaves by TMA bulk stores instead of
+    // stores from registers (t_store = 0: off).  Each epilogue warp stages one 32-column
+    // chunk (hi and lo) of its 32 rows in shared memory; launches whose shared memory
+    // cannot hold the staging store from registers.  Rows R = k_local * rows_per_op + i
+    // (rows_per_op a multiple of 16); t_store_map[hi, lo] are 3-D maps whose third
+    // coordinate is the operator k = store_z0 + k_local.  The scatter must be one of:
+    //   kStoreSiteInterleaved (t_store_d = d, 2 or 4): column n = b * d + s goes to
+    //     T[k][b][i * d + s], as in the first product; map (i * d + s, b, k), box
+    //     16 d x 32 / d x 1;
+    //   kStoreRowContiguous: column n = s * col_div + j goes to
+    //     W[k][j][s * s_col_hi + i] (s_row = 1, col_div a multiple of 16); map
+    //     (s * s_col_hi + i, j, k), box 16 x 16 x 1.
+    CUtensorMap t_store_map[2];
+    int32_t t_store;
     int32_t t_store_d;
 };
+constexpr int32_t kStoreSiteInterleaved = 1;
+constexpr int32_t kStoreRowContiguous = 2;
 // Shared memory of the CTA-pair kernel's store staging: per epilogue warp, the hi and lo
 // halves of a 32-row x 32-column BF16 chunk.
 constexpr size_t kStoreStagingBytes = size_t(8) * 2 * 32 * 32 * 2;
@@ -207,10 +215,10 @@ inline int tc_stages_for(TcMode mode, const TcConfig& c) {
 bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t rows, int64_t cols,
                         int64_t ld, int box_rows, int64_t nbatch = 1, int64_t batch_stride = 0,
                         int row_bytes = 128);
-// Encodes a BF16 store map over T (K slices of mp rows x ld elements, md used) for the
-// CTA-pair kernel's TMA-store epilogue: 3-D (md, mp, K), box 16 d x 32 / d x 1.
-bool encode_store_map(CUtensorMap* map, void* base, int64_t md, int64_t mp, int64_t K, int64_t ld,
-                      int d);
+// Encodes a BF16 store map for the CTA-pair kernel's TMA-store epilogue: nz slices of ny
+// rows x nx elements (row stride ld elements, slice stride ny * ld), box bx x by x 1.
+bool encode_store_map(CUtensorMap* map, void* base, int64_t nx, int64_t ny, int64_t nz, int64_t ld,
+                      int bx, int by);
 // Chooses an N tile (multiple of 16, <= tile_n_max) that splits N evenly.
 int choose_tile_n(int64_t N, int tile_n_max);
 // Fills operand maps and tiling fields of a problem: D (M x N) += A B^T over Kred x nbatch.

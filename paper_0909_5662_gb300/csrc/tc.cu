@@ -900,14 +900,14 @@ bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t r
     return r == CUDA_SUCCESS;
 }
 
-bool encode_store_map(CUtensorMap* map, void* base, int64_t md, int64_t mp, int64_t K, int64_t ld,
-                      int d) {
-    if (!(d == 2 || d == 4) || (ld % 8) != 0 || md > ld || (reinterpret_cast<uintptr_t>(base) & 15))
+bool encode_store_map(CUtensorMap* map, void* base, int64_t nx, int64_t ny, int64_t nz, int64_t ld,
+                      int bx, int by) {
+    if ((ld % 8) != 0 || nx > ld || (reinterpret_cast<uintptr_t>(base) & 15) || (bx * 2) % 16 != 0)
         return false;
     if (!have_encode()) return false;
-    cuuint64_t gdim[3] = {cuuint64_t(md), cuuint64_t(mp), cuuint64_t(K)};
-    cuuint64_t gstride[2] = {cuuint64_t(ld) * 2, cuuint64_t(mp * ld) * 2};
-    cuuint32_t box[3] = {cuuint32_t(16 * d), cuuint32_t(32 / d), 1};
+    cuuint64_t gdim[3] = {cuuint64_t(nx), cuuint64_t(ny), cuuint64_t(nz)};
+    cuuint64_t gstride[2] = {cuuint64_t(ld) * 2, cuuint64_t(ny * ld) * 2};
+    cuuint32_t box[3] = {cuuint32_t(bx), cuuint32_t(by), 1};
     cuuint32_t estride[3] = {1, 1, 1};
     CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, gdim, gstride, box, estride,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

@@ -101,9 +101,14 @@ __device__ __forceinline__ void st_shared_u32(uint32_t addr, uint32_t a) {
     asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(a) : "memory");
 }
 
-// TMA-store epilogue (TcLaunch::t_store_d = d): one 32-column chunk of this warp's 32
-// rows, split into BF16 hi/lo, staged in the warp's 4 KB of shared memory `stg` and sent
-// out by lane 0 as up to four bulk tensor stores.  The chunk covers 32 / d values of b
+__device__ __forceinline__ void st_shared_u16(uint32_t addr, uint16_t a) {
+    asm volatile("st.shared.b16 [%0], %1;" ::"r"(addr), "h"(a) : "memory");
+}
+
+// TMA-store epilogue, site-interleaved layout (TcLaunch::t_store = kStoreSiteInterleaved,
+// t_store_d = d): one 32-column chunk of this warp's 32 rows, split into BF16 hi/lo,
+// staged in the warp's 4 KB of shared memory `stg` and sent out by lane 0 as up to four
+// bulk tensor stores.  The chunk covers 32 / d values of b
 // and the warp's rows are two groups of 16 consecutive rows i (each inside one operator,
 // rows_per_op being a multiple of 16): the staging holds one store box per (group, half):
 // hi at stg + group * 1024, lo 2048 further, each box 32 / d rows b of 16 d elements
@@ -141,8 +146,59 @@ __device__ __forceinline__ void store_chunk_tma(const TcLaunch& L, const uint32_
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
             if (!valid[g]) continue;
-            tma_store_3d(&L.t_store[0], stg + uint32_t(g) * 1024u, x[g], y, z[g]);
-            tma_store_3d(&L.t_store[1], stg + 2048u + uint32_t(g) * 1024u, x[g], y, z[g]);
+            tma_store_3d(&L.t_store_map[0], stg + uint32_t(g) * 1024u, x[g], y, z[g]);
+            tma_store_3d(&L.t_store_map[1], stg + 2048u + uint32_t(g) * 1024u, x[g], y, z[g]);
+        }
+        bulk_commit_group();
+    }
+}
+
+// TMA-store epilogue, row-contiguous layout (TcLaunch::t_store = kStoreRowContiguous):
+// column n = s * cdiv + j of row (k, i) goes to W[k][j][s * sch + i], so a lane's values
+// run down a column of W.  The chunk (columns n .. n + 31, 16-aligned, cmax of them
+// valid, a multiple of 16) is four boxes of 16 j x 16 i per hi/lo: box (g, h) holds
+// row group g and column half h at stg + (2 g + h) * 512 (lo 2048 further), row j of a
+// box at 32 j bytes.  At step j the upper half-warp writes column (j + 1) mod 16, so
+// its row lies 32 bytes along the banks from the lower half's and the two halves never
+// meet in a bank.  x[g] = i of group g's first row, z[g] its operator.
+__device__ __forceinline__ void store_chunk_tma_rows(const TcLaunch& L, const uint32_t (&r)[32],
+                                                     uint32_t stg, int lane, const int (&x)[2],
+                                                     const int (&z)[2], const bool (&valid)[2],
+                                                     int n, int cmax, int cdiv, int64_t sch) {
+    if (lane == 0) bulk_wait_group_read0();   // the previous chunk's stores have read stg
+    __syncwarp();
+    const bool up = lane >= 16;
+    const uint32_t base = stg + (up ? 1024u : 0u) + uint32_t(lane & 15) * 2u;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int ju = (j + 1) & 15;
+            const float v = __uint_as_float(up ? r[16 * h + ju] : r[16 * h + j]);
+            const __nv_bfloat16 hb = __float2bfloat16_rn(v);
+            const __nv_bfloat16 lb = __float2bfloat16_rn(v - __bfloat162float(hb));
+            const uint32_t a = base + uint32_t(h) * 512u + uint32_t(up ? ju : j) * 32u;
+            st_shared_u16(a, __bfloat16_as_ushort(hb));
+            st_shared_u16(a + 2048u, __bfloat16_as_ushort(lb));
+        }
+    }
+    fence_proxy_async_shared();   // the staging writes, before the tensor stores read them
+    __syncwarp();
+    if (lane == 0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (16 * h >= cmax) continue;
+            const int nh = n + 16 * h;
+            const int s = nh / cdiv;
+            const int y = nh - s * cdiv;
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                if (!valid[g]) continue;
+                const int xg = int(int64_t(s) * sch) + x[g];
+                const uint32_t box = stg + uint32_t(2 * g + h) * 512u;
+                tma_store_3d(&L.t_store_map[0], box, xg, y, z[g]);
+                tma_store_3d(&L.t_store_map[1], box + 2048u, xg, y, z[g]);
+            }
         }
         bulk_commit_group();
     }
@@ -499,7 +555,8 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                           : nullptr;
         // TMA-store epilogue: this warp's 4 KB of staging after the barriers
         constexpr bool kStoreOk = (EPI == EPI_SPLIT_BF16) && !SITE;
-        const int tsd = kStoreOk ? L.t_store_d : 0;
+        const int tst = kStoreOk ? L.t_store : 0;
+        const int tsd = L.t_store_d;
         const uint32_t stg = smem_u32(smem + size_t(stages) * stage_bytes + 512) +
                              uint32_t(warp - 2) * 4096u;
         for (int t = pair; t < L.total_tiles && ok; t += npairs) {
@@ -524,13 +581,14 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
             // store boxes of the warp's two 16-row groups (TMA-store epilogue)
             int bx[2] = {0, 0}, bz[2] = {0, 0};
             bool bvalid[2] = {false, false};
-            if (tsd) {
+            if (tst) {
 #pragma unroll
                 for (int g = 0; g < 2; ++g) {
                     const int rg = row - lane + 16 * g;
                     bvalid[g] = rg < P->M && dt.kb_begin < dt.kb_end;
                     const int op = rg / S.rows_per_op;
-                    bx[g] = (rg - op * S.rows_per_op) * tsd;
+                    const int il = rg - op * S.rows_per_op;
+                    bx[g] = tst == kStoreSiteInterleaved ? il * tsd : il;
                     bz[g] = P->store_z0 + op;
                 }
             }
@@ -558,9 +616,12 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                                        r);
                     tmem_ld_wait();
                     const int cmax = min(32, ncols - c);   // the same for the whole warp
-                    // a chunk goes out by TMA unless it is short inside N (the box would
-                    // spill into the next tile's columns; past N the map clips it)
-                    const bool tma_chunk = tsd && last && (cmax == 32 || n0 + ncols == P->N);
+                    // a chunk goes out by TMA unless, site-interleaved, it is short inside
+                    // N (the box would spill into the next tile's columns; past N the map
+                    // clips it); row-contiguous boxes are 16 columns wide, as are tiles
+                    const bool tma_chunk =
+                        tst && last &&
+                        (tst == kStoreRowContiguous || cmax == 32 || n0 + ncols == P->N);
                     if (sum_in_out) {
                         // the first chain stores, each later one adds into the output
                         // (the same lane, in program order: the same FP32 additions in
@@ -594,8 +655,13 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                         }
                     }
                     if constexpr (kStoreOk) {
-                        if (tma_chunk)
-                            store_chunk_tma(L, r, stg, lane, tsd, bx, (n0 + c) / tsd, bz, bvalid);
+                        if (tma_chunk) {
+                            if (tst == kStoreSiteInterleaved)
+                                store_chunk_tma(L, r, stg, lane, tsd, bx, (n0 + c) / tsd, bz, bvalid);
+                            else
+                                store_chunk_tma_rows(L, r, stg, lane, bx, bz, bvalid, n0 + c, cmax,
+                                                     cdiv, sch);
+                        }
                     }
                     // the site-major copy's stores are warp-collective: every lane comes here
                     if (SITE && (EPI == EPI_SPLIT_BF16 || EPI == EPI_TF32) && last)
@@ -613,7 +679,7 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
             } while (kb0 < dt.kb_end);
         }
         // the TMA stores are complete before the CTA (and its shared memory) goes away
-        if (tsd && lane == 0) bulk_wait_group0();
+        if (tst && lane == 0) bulk_wait_group0();
     }
 
     tc_fence_before();
@@ -733,20 +799,23 @@ cudaError_t tc_gemm_launch_pair(TcMode mode, TcEpi epi, const TcLaunch& L, int s
     // only where its staging fits; otherwise the same launch stores from registers.
     const TcLaunch* Lp = &L;
     TcLaunch plain;
-    if (L.t_store_d != 0) {
+    if (L.t_store != 0) {
+        const bool site = L.t_store == kStoreSiteInterleaved;
         bool ok = epi == EPI_SPLIT_BF16 && L.out2[0] == nullptr && L.out[0][0] != nullptr &&
-                  (L.t_store_d == 2 || L.t_store_d == 4);
+                  (site ? (L.t_store_d == 2 || L.t_store_d == 4) : L.t_store == kStoreRowContiguous);
         for (int i = 0; ok && i < L.nprob; ++i) {
-            const TcProblem& P = L.inline_prob[i];
-            ok = P.k_splits == 1 && P.sc[0].s_split == 0 && P.sc[0].rows_per_op % 16 == 0 &&
-                 P.sc[0].col_div == L.t_store_d;
+            const TcScatter& S = L.inline_prob[i].sc[0];
+            ok = L.inline_prob[i].k_splits == 1 && S.s_split == 0 && S.rows_per_op % 16 == 0 &&
+                 (site ? S.col_div == L.t_store_d
+                       : (S.col_div % 16 == 0 && S.s_row == 1 && S.s_col_hi % 8 == 0 &&
+                          L.inline_prob[i].N % 16 == 0));
         }
         const size_t with = pair_smem_bytes(mode, stages, bh, L.row_bytes, true);
         if (ok && with <= 232448) {
             smem = with;
         } else {
             plain = L;
-            plain.t_store_d = 0;
+            plain.t_store = 0;
             Lp = &plain;
         }
     }

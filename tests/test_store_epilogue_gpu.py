@@ -9,7 +9,8 @@ both site dimensions the store maps take (d = 2, 4), operators that begin in the
 of a warp's 32 rows (m = 48, 400), chunks that are short inside N (N tiles of 208 and
 176 columns) and at the end of N (d * m' not a multiple of 32), rows past the last
 operator, accumulation chains (m > 1024), and layouts that fall back to register stores
-(d = 3, m not a multiple of 16).
+(d = 3, m not a multiple of 16).  The adjoint's W' product takes the row-contiguous form
+of the same epilogue and is checked the same way against the oracle's adjoint.
 """
 import numpy as np
 import pytest
@@ -136,3 +137,39 @@ def test_store_epilogue_option_values(P):
             P.dmrg_set_option("store_epilogue", 2, handle=h)
     finally:
         h.close()
+
+
+# The adjoint's W' product (W'_k[j d + s][a] = sum_b G_k[a][b] U[j d + s][b], stored
+# row-major as W'_k[j][s m' + a]) leaves through the row-contiguous TMA-store layout:
+# shapes with operators that begin inside a warp's 32 rows (m' = 48, 112), 32-column
+# chunks whose two 16-column halves fall in different sites s (m = 48), N tiles of 176
+# columns (a chunk with one half), and a shape that stores from registers (m = 37).
+BWD_SHAPES = [(16, 4, 16, 4), (64, 4, 48, 8), (48, 2, 96, 5), (96, 4, 112, 3), (176, 2, 64, 3),
+              (37, 3, 50, 5)]
+
+
+@pytest.mark.parametrize("shape", BWD_SHAPES)
+def test_adjoint_tma_store_matches_register_stores_and_oracle(P, shape):
+    m, d, mp, K = shape
+    rng = np.random.default_rng(9800 + m + 3 * mp + K)
+    U = orthonormal_columns(rng, m * d, mp)
+    O = rng.standard_normal((K, m, m))
+    G = rng.standard_normal((K, mp, mp))
+    dev = torch.device("cuda")
+    outs = []
+    for store in (0, 1):
+        h = P.Handle()
+        try:
+            P.dmrg_set_option("deterministic", 1, handle=h)
+            P.dmrg_set_option("store_epilogue", store, handle=h)
+            dO, dU = P.dmrg_rotate_ops_backward(torch.from_numpy(U).to(dev), torch.from_numpy(O).to(dev),
+                                                torch.from_numpy(G).to(dev), d, "bf16x3", handle=h)
+            torch.cuda.synchronize()
+            P.dmrg_sync_status(handle=h)
+            outs.append((dO.cpu().numpy(), dU.cpu().numpy()))
+        finally:
+            h.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    dO_ref, dU_ref = oracle.rotate_backward(U, O, G, d)
+    assert rel_err(outs[0][0].astype(np.float64), dO_ref).max() <= TOL
+    assert np.linalg.norm(outs[0][1] - dU_ref) / np.linalg.norm(dU_ref) <= TOL
