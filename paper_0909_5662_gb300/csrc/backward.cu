@@ -32,6 +32,7 @@
 #include <cstdio>
 
 #include "api_common.h"
+#include "ptx.cuh"
 
 using namespace dmrg;
 
@@ -218,6 +219,52 @@ __global__ void __launch_bounds__(256) bwd_du_reduce_kernel(const float* __restr
     }
 }
 
+// The same sum with four consecutive i per thread (m % 4 == 0, 16-byte aligned parts):
+// each thread has every part's 16-byte load in flight at once (one round of loads where
+// the one-element form has four).  Per element the parts are added in the same order, so
+// the two forms agree bit for bit.  Launched as a programmatic dependent of the product
+// that writes the parts.
+__global__ void __launch_bounds__(256) bwd_du_reduce4_kernel(const float* __restrict__ part,
+                                                             int nparts, int64_t dmp, int64_t m,
+                                                             int64_t mp, int d,
+                                                             double* __restrict__ dU) {
+    __shared__ double t[32][33];
+    griddep_wait();
+    const int64_t R0 = int64_t(blockIdx.y) * 32, I0 = int64_t(blockIdx.x) * 32;
+    const int rl = threadIdx.x >> 3, i4 = (threadIdx.x & 7) * 4;
+    const int64_t R = R0 + rl, I = I0 + i4;
+    float sum[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
+    if (R < dmp && I < m) {
+        float4 x[kBwdMaxParts];
+#pragma unroll
+        for (int q = 0; q < kBwdMaxParts; ++q)
+            x[q] = q < nparts ? *reinterpret_cast<const float4*>(part + (int64_t(q) * dmp + R) * m + I)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < kBwdMaxParts; ++q) {
+            if (q >= nparts) break;
+            const float xs[4] = {x[q].x, x[q].y, x[q].z, x[q].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float u = sum[e] + xs[e];
+                comp[e] += fabsf(sum[e]) >= fabsf(xs[e]) ? (sum[e] - u) + xs[e] : (xs[e] - u) + sum[e];
+                sum[e] = u;
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) t[rl][i4 + e] = double(sum[e]) + double(comp[e]);
+    __syncthreads();
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int ii = ty; ii < 32; ii += 8) {
+        const int64_t Iw = I0 + ii, Rw = R0 + tx;
+        if (Rw < dmp && Iw < m) {
+            const int64_t sidx = Rw / mp, n = Rw - sidx * mp;
+            dU[(Iw * d + sidx) * mp + n] = t[tx][ii];
+        }
+    }
+}
+
 dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G, int in_is_fp64,
                    void* dO, double* dU, const BwdDims& B, dmrg_precision p, void* ws,
                    cudaStream_t s) {
@@ -270,11 +317,23 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
             }
         }
         // G last: its last rows are still in L2 when the W' product, which runs its M tiles
-        // from the last to the first, starts reading them
-        PackJob& jg = jobs[nj++];   // G: rows (k, a), cols b = G_k[a][b]
-        jg.src = G; jg.src_f64 = in_is_fp64; jg.mode = pmode; jg.rows = K * mp; jg.cols = mp;
-        jg.rows_per_op = K * mp; jg.rdiv = 1; jg.s_r_hi = mp; jg.s_c = 1;
-        jg.dst0 = sec(B.i_G, 0); jg.dst1 = lo(B.i_G); jg.ld = B.ld_u;
+        // from the last to the first, starts reading them.  Where G^T goes through
+        // shared-memory tiles, the same tiles also give G (G is read once).
+        PackJob* jgt = nullptr;
+        for (int i = 0; i < nj; ++i)
+            if (jobs[i].dst0 == sec(B.i_GT, 0)) jgt = &jobs[i];
+        if (jgt != nullptr && pack_job_tiled(*jgt) && (B.ld_u % 2) == 0) {
+            jgt->st0 = sec(B.i_G, 0);
+            jgt->st1 = split ? lo(B.i_G) : nullptr;
+            jgt->st_ld = B.ld_u;
+            jgt->late = 1;
+        } else {
+            PackJob& jg = jobs[nj++];   // G: rows (k, a), cols b = G_k[a][b]
+            jg.src = G; jg.src_f64 = in_is_fp64; jg.mode = pmode; jg.rows = K * mp; jg.cols = mp;
+            jg.rows_per_op = K * mp; jg.rdiv = 1; jg.s_r_hi = mp; jg.s_c = 1;
+            jg.dst0 = sec(B.i_G, 0); jg.dst1 = lo(B.i_G); jg.ld = B.ld_u;
+            jg.late = 1;
+        }
         e = timed_launch(h, "bwd_pack", s, [&] { return pack_launch(jobs, nj, nullptr, s); });
         if (e != cudaSuccess) return cuda_fail(h, e, "pack");
     }
@@ -349,8 +408,10 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
         // s m' + a; a lane's values run down a column), staged per warp in shared memory
         if (split && rowmajor && L.out2[0] == nullptr && h->store_epilogue == 0 && m % 16 == 0 &&
             mp % 16 == 0 &&
-            encode_store_map(&L.t_store_map[0], L.out[0][0], dmp, m, K, B.ld_n, 16, 16) &&
-            encode_store_map(&L.t_store_map[1], L.out[0][1], dmp, m, K, B.ld_n, 16, 16))
+            encode_store_map(&L.t_store_map[0], L.out[0][0], dmp, m, K, B.ld_n, 32, 16) &&
+            encode_store_map(&L.t_store_map[1], L.out[0][1], dmp, m, K, B.ld_n, 32, 16) &&
+            encode_store_map(&L.t_store_map[2], L.out[0][0], dmp, m, K, B.ld_n, 16, 16) &&
+            encode_store_map(&L.t_store_map[3], L.out[0][1], dmp, m, K, B.ld_n, 16, 16))
             L.t_store = kStoreRowContiguous;
         if ((st = launch("bwd_tc_Wp", L, epi_op, mp)) != DMRG_OK) return st;
     }
@@ -382,6 +443,14 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
             L.nprob = 1;
             L.out[0][0] = nullptr;   // no row-major copy
             site_major(L, wt_hi + wt_second, split ? wt_lo + wt_second : nullptr);
+            // BF16x3: the site-major W leaves by TMA bulk stores (a lane's values of a
+            // column half are 32 contiguous bytes of a row of W_k), staged per warp
+            if (split && h->store_epilogue == 0 && m % 16 == 0 && mp % 16 == 0 &&
+                encode_store_map(&L.t_store_map[0], L.out2[0], m, dmp, K, B.ld_j, 32, 16, 64) &&
+                encode_store_map(&L.t_store_map[1], L.out2[1], m, dmp, K, B.ld_j, 32, 16, 64) &&
+                encode_store_map(&L.t_store_map[2], L.out2[0], m, dmp, K, B.ld_j, 16, 16, 32) &&
+                encode_store_map(&L.t_store_map[3], L.out2[1], m, dmp, K, B.ld_j, 16, 16, 32))
+                L.t_store = kStoreSiteMajor;
             if ((st = launch("bwd_tc_W", L, epi_op, mp)) != DMRG_OK) return st;
         }
         // 4. dU_r^T[(s,n)][i] over 2K slices, split into parts with their own partial sums.
@@ -429,8 +498,21 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
             const int nparts = Pa.k_splits + Pb.k_splits;
             e = timed_launch(h, "bwd_dU_reduce", s, [&] {
                 dim3 grd(unsigned((m + 31) / 32), unsigned((dmp + 31) / 32));
-                bwd_du_reduce_kernel<<<grd, dim3(32, 8), 0, s>>>(part, nparts, dmp, m, mp, d, dU);
-                return cudaGetLastError();
+                if (m % 4 != 0 || (reinterpret_cast<uintptr_t>(part) & 15) != 0) {
+                    bwd_du_reduce_kernel<<<grd, dim3(32, 8), 0, s>>>(part, nparts, dmp, m, mp, d, dU);
+                    return cudaGetLastError();
+                }
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = grd;
+                cfg.blockDim = dim3(256, 1, 1);
+                cfg.stream = s;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+                attr[0].val.programmaticStreamSerializationAllowed = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                return cudaLaunchKernelEx(&cfg, bwd_du_reduce4_kernel, (const float*)part, nparts, dmp,
+                                          m, mp, d, dU);
             });
             if (e != cudaSuccess) return cuda_fail(h, e, "dU reduce");
             return DMRG_OK;

@@ -164,14 +164,22 @@ struct TcLaunch {
     //     T[k][b][i * d + s], as in the first product; map (i * d + s, b, k), box
     //     16 d x 32 / d x 1;
     //   kStoreRowContiguous: column n = s * col_div + j goes to
-    //     W[k][j][s * s_col_hi + i] (s_row = 1, col_div a multiple of 16); map
-    //     (s * s_col_hi + i, j, k), box 16 x 16 x 1.
-    CUtensorMap t_store_map[2];
+    //     W[k][j][s * s_col_hi + i] (s_row = 1, col_div a multiple of 16); maps
+    //     (s * s_col_hi + i, j, k), boxes 32 x 16 x 1 ([0], [1]: a warp's 32 rows in one
+    //     operator) and 16 x 16 x 1 ([2], [3]);
+    //   kStoreSiteMajor: the site-major copy alone (out[0] null, out2 set; o2_m and
+    //     o2_rows_per_op multiples of 16): column n = s * o2_m + j goes to
+    //     out2_k[s * o2_rows_per_op + i][j]; maps (j, s * o2_rows_per_op + i, k), boxes
+    //     32 x 16 x 1 with the 64-byte swizzle ([0], [1]: a chunk's 32 columns in one
+    //     site) and 16 x 16 x 1 with the 32-byte swizzle ([2], [3]).
+    // t_store_map[hi, lo, hi narrow, lo narrow].
+    CUtensorMap t_store_map[4];
     int32_t t_store;
     int32_t t_store_d;
 };
 constexpr int32_t kStoreSiteInterleaved = 1;
 constexpr int32_t kStoreRowContiguous = 2;
+constexpr int32_t kStoreSiteMajor = 3;
 // Shared memory of the CTA-pair kernel's store staging: per epilogue warp, the hi and lo
 // halves of a 32-row x 32-column BF16 chunk.
 constexpr size_t kStoreStagingBytes = size_t(8) * 2 * 32 * 32 * 2;
@@ -216,9 +224,10 @@ bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t r
                         int64_t ld, int box_rows, int64_t nbatch = 1, int64_t batch_stride = 0,
                         int row_bytes = 128);
 // Encodes a BF16 store map for the CTA-pair kernel's TMA-store epilogue: nz slices of ny
-// rows x nx elements (row stride ld elements, slice stride ny * ld), box bx x by x 1.
+// rows x nx elements (row stride ld elements, slice stride ny * ld), box bx x by x 1;
+// swizzle: 0, or the shared-memory swizzle span in bytes (bx * 2: 32 or 64).
 bool encode_store_map(CUtensorMap* map, void* base, int64_t nx, int64_t ny, int64_t nz, int64_t ld,
-                      int bx, int by);
+                      int bx, int by, int swizzle = 0);
 // Chooses an N tile (multiple of 16, <= tile_n_max) that splits N evenly.
 int choose_tile_n(int64_t N, int tile_n_max);
 // Fills operand maps and tiling fields of a problem: D (M x N) += A B^T over Kred x nbatch.
@@ -263,7 +272,15 @@ struct PackJob {
     uint64_t m_cols, m_rpo, m_rdiv;
     // Set by pack_prepare_grouped (grouped launches): the job's rows are contiguous runs
     // of its source (s_c = 1, rdiv = 1) and are copied one warp per row.
-    int32_t rowwise, pad_;
+    int32_t rowwise;
+    int32_t late;          // single-launch packer: placed after every other job (its output
+                           // is the likeliest to be in L2 when the launch ends)
+    // Single-launch packer, tiled (transposing) jobs with rdiv = 1: st0 / st1 (null: none)
+    // also receive the untransposed copy, element (row g * cols + c, column r) for the
+    // job's element (row g * rows_per_op + r, column c), row stride st_ld (even).
+    void* st0;
+    void* st1;
+    int64_t st_ld;
     // Set by the single-launch packer (pack_launch): multiply-shift divisors, in 32-bit
     // index arithmetic, of the tiled path's geometry (tiles per operator group, per
     // residue and per row of tiles) and of the 8-wide path's units per row (fast8).
@@ -273,6 +290,8 @@ struct PackJob {
     int64_t t_hrows;
 };
 void pack_prepare(PackJob& j);
+// The single-launch packer takes j through shared-memory tiles (FP32 source, transposing).
+bool pack_job_tiled(const PackJob& j);
 // pack_prepare, and for grouped launches the row-by-row copy of contiguous rows.
 void pack_prepare_grouped(PackJob& j);
 cudaError_t pack_launch(const PackJob* jobs_host, int njobs, PackJob* jobs_dev_or_null,

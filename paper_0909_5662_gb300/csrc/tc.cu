@@ -538,6 +538,34 @@ __device__ __forceinline__ void pack_vec8_block(const PackJob& j, int64_t blk) {
 // rr = (h0 + 0..63) * rdiv + rem of the group and the columns c0 + 0..63.
 constexpr int kTile = 64;
 
+__device__ __forceinline__ void pack_store2_to(int mode, void* d0, void* d1, int64_t dst, float x0,
+                                               float x1) {
+    if (mode == 0) {
+        __nv_bfloat16 h0, l0, h1, l1;
+        split_bf16(x0, h0, l0);
+        split_bf16(x1, h1, l1);
+        *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(d0) + dst) =
+            uint32_t(__bfloat16_as_ushort(h0)) | (uint32_t(__bfloat16_as_ushort(h1)) << 16);
+        *reinterpret_cast<uint32_t*>(static_cast<__nv_bfloat16*>(d1) + dst) =
+            uint32_t(__bfloat16_as_ushort(l0)) | (uint32_t(__bfloat16_as_ushort(l1)) << 16);
+    } else {
+        const bool t = (mode == 1);
+        *reinterpret_cast<float2*>(static_cast<float*>(d0) + dst) =
+            make_float2(t ? tf32_round(x0) : x0, t ? tf32_round(x1) : x1);
+    }
+}
+
+__device__ __forceinline__ void pack_store_to(int mode, void* d0, void* d1, int64_t dst, float x) {
+    if (mode == 0) {
+        __nv_bfloat16 h, l;
+        split_bf16(x, h, l);
+        static_cast<__nv_bfloat16*>(d0)[dst] = h;
+        static_cast<__nv_bfloat16*>(d1)[dst] = l;
+    } else {
+        static_cast<float*>(d0)[dst] = (mode == 1) ? tf32_round(x) : x;
+    }
+}
+
 __device__ __forceinline__ void pack_store2(const PackJob& j, int64_t dst, float x0, float x1) {
     if (j.mode == 0) {
         __nv_bfloat16 h0, l0, h1, l1;
@@ -591,6 +619,20 @@ __device__ __forceinline__ void pack_tile(const PackJob& j, int64_t t, float (*t
         const float x0 = tile[2 * tx][ty + 8 * q];
         if (c + 1 < j.cols) pack_store2(j, dst, x0, tile[2 * tx + 1][ty + 8 * q]);
         else pack_store(j, dst, x0);
+    }
+    if (j.st0 != nullptr) {
+        // the untransposed copy from the same tile: row g * cols + c, columns hs, hs + 1
+        const int64_t hs = h0 + 2 * tx;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int cl = ty + 8 * q;
+            const int64_t cc = c0 + cl;
+            if (cc >= j.cols || hs >= hrows) continue;
+            const int64_t dst = (g * j.cols + cc) * j.st_ld + hs;
+            const float x0 = tile[cl][2 * tx];
+            if (hs + 1 < hrows) pack_store2_to(j.mode, j.st0, j.st1, dst, x0, tile[cl][2 * tx + 1]);
+            else pack_store_to(j.mode, j.st0, j.st1, dst, x0);
+        }
     }
 }
 
@@ -690,6 +732,8 @@ size_t tc_smem_bytes(TcMode mode, int stages, int bn, int rb) {
 }
 
 }  // namespace
+
+bool pack_job_tiled(const PackJob& j) { return !pack_vec8_ok(j) && pack_tiled_ok(j); }
 
 int tc_max_stages(TcMode mode, int tile_n_max, int row_bytes) {
     int s = 1;
@@ -792,13 +836,16 @@ cudaError_t pack_launch(const PackJob* jobs, int njobs, PackJob* /*unused*/, cud
     PackLaunch L{};
     int64_t blocks = 0;
     int n = 0;
-    // general gathers first, contiguous jobs after them
-    for (int pass = 0; pass < 2; ++pass)
+    // general gathers first, contiguous jobs after them, jobs marked late last
+    for (int pass = 0; pass < 3; ++pass)
         for (int i = 0; i < njobs; ++i) {
             if (jobs[i].rows * jobs[i].cols == 0) continue;
             const bool v8 = pack_vec8_ok(jobs[i]);
-            if (v8 != (pass == 1)) continue;
+            if (jobs[i].late ? pass != 2 : (pass == 2 || v8 != (pass == 1))) continue;
             const bool tl = !v8 && pack_tiled_ok(jobs[i]);
+            // the untransposed copy is written by the tiled path only
+            if (jobs[i].st0 != nullptr && (!tl || jobs[i].rdiv != 1 || (jobs[i].st_ld % 2) != 0))
+                return cudaErrorInvalidValue;
             PackJob& j = L.inline_jobs[n++];
             j = jobs[i];
             pack_prepare(j);
@@ -901,8 +948,9 @@ bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t r
 }
 
 bool encode_store_map(CUtensorMap* map, void* base, int64_t nx, int64_t ny, int64_t nz, int64_t ld,
-                      int bx, int by) {
-    if ((ld % 8) != 0 || nx > ld || (reinterpret_cast<uintptr_t>(base) & 15) || (bx * 2) % 16 != 0)
+                      int bx, int by, int swizzle) {
+    if ((ld % 8) != 0 || nx > ld || (reinterpret_cast<uintptr_t>(base) & 15) || (bx * 2) % 16 != 0 ||
+        (swizzle != 0 && swizzle != 2 * bx) || (swizzle != 0 && swizzle != 32 && swizzle != 64))
         return false;
     if (!have_encode()) return false;
     cuuint64_t gdim[3] = {cuuint64_t(nx), cuuint64_t(ny), cuuint64_t(nz)};
@@ -910,7 +958,10 @@ bool encode_store_map(CUtensorMap* map, void* base, int64_t nx, int64_t ny, int6
     cuuint32_t box[3] = {cuuint32_t(bx), cuuint32_t(by), 1};
     cuuint32_t estride[3] = {1, 1, 1};
     CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, gdim, gstride, box, estride,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          swizzle == 64   ? CU_TENSOR_MAP_SWIZZLE_64B
+                          : swizzle == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                          : CU_TENSOR_MAP_SWIZZLE_NONE,
                           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }

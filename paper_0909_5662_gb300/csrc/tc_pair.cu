@@ -155,31 +155,50 @@ __device__ __forceinline__ void store_chunk_tma(const TcLaunch& L, const uint32_
 
 // TMA-store epilogue, row-contiguous layout (TcLaunch::t_store = kStoreRowContiguous):
 // column n = s * cdiv + j of row (k, i) goes to W[k][j][s * sch + i], so a lane's values
-// run down a column of W.  The chunk (columns n .. n + 31, 16-aligned, cmax of them
-// valid, a multiple of 16) is four boxes of 16 j x 16 i per hi/lo: box (g, h) holds
-// row group g and column half h at stg + (2 g + h) * 512 (lo 2048 further), row j of a
-// box at 32 j bytes.  At step j the upper half-warp writes column (j + 1) mod 16, so
-// its row lies 32 bytes along the banks from the lower half's and the two halves never
-// meet in a bank.  x[g] = i of group g's first row, z[g] its operator.
+// run down a column of W.  The chunk is columns n .. n + 31 (16-aligned, cmax of them
+// valid, a multiple of 16), in two halves h of 16 columns, each inside one s.  When the
+// warp's 32 rows lie in one operator, half h is one box of 16 j x 32 i (64-byte rows)
+// at stg + 1024 h (lo 2048 further), row j at 64 j bytes, lane i's element at 2 i.
+// Otherwise each row group g of 16 has its own boxes of 16 j x 16 i at stg + (2 g + h) *
+// 512, and at step j the upper half-warp writes column (j + 1) mod 16, so that its row
+// lies 32 bytes along the banks from the lower half's.  x[g] = i of group g's first row,
+// z[g] its operator.
 __device__ __forceinline__ void store_chunk_tma_rows(const TcLaunch& L, const uint32_t (&r)[32],
                                                      uint32_t stg, int lane, const int (&x)[2],
                                                      const int (&z)[2], const bool (&valid)[2],
                                                      int n, int cmax, int cdiv, int64_t sch) {
     if (lane == 0) bulk_wait_group_read0();   // the previous chunk's stores have read stg
     __syncwarp();
-    const bool up = lane >= 16;
-    const uint32_t base = stg + (up ? 1024u : 0u) + uint32_t(lane & 15) * 2u;
+    const bool wide = valid[0] && valid[1] && z[0] == z[1];   // the same for the whole warp
+    if (wide) {
+        const uint32_t base = stg + uint32_t(lane) * 2u;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < 2; ++h) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int ju = (j + 1) & 15;
-            const float v = __uint_as_float(up ? r[16 * h + ju] : r[16 * h + j]);
-            const __nv_bfloat16 hb = __float2bfloat16_rn(v);
-            const __nv_bfloat16 lb = __float2bfloat16_rn(v - __bfloat162float(hb));
-            const uint32_t a = base + uint32_t(h) * 512u + uint32_t(up ? ju : j) * 32u;
-            st_shared_u16(a, __bfloat16_as_ushort(hb));
-            st_shared_u16(a + 2048u, __bfloat16_as_ushort(lb));
+            for (int j = 0; j < 16; ++j) {
+                const float v = __uint_as_float(r[16 * h + j]);
+                const __nv_bfloat16 hb = __float2bfloat16_rn(v);
+                const __nv_bfloat16 lb = __float2bfloat16_rn(v - __bfloat162float(hb));
+                const uint32_t a = base + uint32_t(h) * 1024u + uint32_t(j) * 64u;
+                st_shared_u16(a, __bfloat16_as_ushort(hb));
+                st_shared_u16(a + 2048u, __bfloat16_as_ushort(lb));
+            }
+        }
+    } else {
+        const bool up = lane >= 16;
+        const uint32_t base = stg + (up ? 1024u : 0u) + uint32_t(lane & 15) * 2u;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int ju = (j + 1) & 15;
+                const float v = __uint_as_float(up ? r[16 * h + ju] : r[16 * h + j]);
+                const __nv_bfloat16 hb = __float2bfloat16_rn(v);
+                const __nv_bfloat16 lb = __float2bfloat16_rn(v - __bfloat162float(hb));
+                const uint32_t a = base + uint32_t(h) * 512u + uint32_t(up ? ju : j) * 32u;
+                st_shared_u16(a, __bfloat16_as_ushort(hb));
+                st_shared_u16(a + 2048u, __bfloat16_as_ushort(lb));
+            }
         }
     }
     fence_proxy_async_shared();   // the staging writes, before the tensor stores read them
@@ -191,13 +210,103 @@ __device__ __forceinline__ void store_chunk_tma_rows(const TcLaunch& L, const ui
             const int nh = n + 16 * h;
             const int s = nh / cdiv;
             const int y = nh - s * cdiv;
+            if (wide) {
+                const int xw = int(int64_t(s) * sch) + x[0];
+                const uint32_t box = stg + uint32_t(h) * 1024u;
+                tma_store_3d(&L.t_store_map[0], box, xw, y, z[0]);
+                tma_store_3d(&L.t_store_map[1], box + 2048u, xw, y, z[0]);
+                continue;
+            }
 #pragma unroll
             for (int g = 0; g < 2; ++g) {
                 if (!valid[g]) continue;
                 const int xg = int(int64_t(s) * sch) + x[g];
                 const uint32_t box = stg + uint32_t(2 * g + h) * 512u;
-                tma_store_3d(&L.t_store_map[0], box, xg, y, z[g]);
-                tma_store_3d(&L.t_store_map[1], box + 2048u, xg, y, z[g]);
+                tma_store_3d(&L.t_store_map[2], box, xg, y, z[g]);
+                tma_store_3d(&L.t_store_map[3], box + 2048u, xg, y, z[g]);
+            }
+        }
+        bulk_commit_group();
+    }
+}
+
+// TMA-store epilogue, site-major layout (TcLaunch::t_store = kStoreSiteMajor): column
+// n = s * o2_m + j of row (k, i) goes to out2_k[s * rps + i][j], so a lane's values of a
+// chunk are contiguous in a row of out2_k.  The chunk is columns n .. n + 31 (16-aligned,
+// cmax of them valid).  When all 32 lie in one site, each row group g of 16 has one box
+// of 16 i x 32 j (64-byte rows, 64-byte swizzle: 16-byte piece q of row i at
+// q ^ ((i >> 1) & 3)) at stg + 1024 g (lo 2048 further).  Otherwise each half h of 16
+// columns has its own boxes of 16 i x 16 j (32-byte rows, 32-byte swizzle: piece q at
+// q ^ ((i >> 2) & 1)) at stg + (2 g + h) * 512.  With either swizzle the 16-byte stores
+// of any eight lanes fall in distinct banks.  x[g] = i of group g's first row, z[g] its
+// operator.
+__device__ __forceinline__ void store_chunk_tma_site(const TcLaunch& L, const uint32_t (&r)[32],
+                                                     uint32_t stg, int lane, const int (&x)[2],
+                                                     const int (&z)[2], const bool (&valid)[2],
+                                                     int n, int cmax, int o2m, int rps) {
+    if (lane == 0) bulk_wait_group_read0();   // the previous chunk's stores have read stg
+    __syncwarp();
+    const int s0 = n / o2m;
+    const int j0 = n - s0 * o2m;
+    const bool wide = cmax == 32 && j0 + 32 <= o2m;   // the same for the whole warp
+    const int li = lane & 15;
+    if (wide) {
+        const uint32_t row = stg + uint32_t(lane >> 4) * 1024u + uint32_t(li) * 64u;
+        const uint32_t flip = uint32_t((li >> 1) & 3);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                split2(__uint_as_float(r[8 * q + 2 * e]), __uint_as_float(r[8 * q + 2 * e + 1]),
+                       hw[e], lw[e]);
+            const uint32_t a = row + ((uint32_t(q) ^ flip) << 4);
+            st_shared_v4u(a, hw[0], hw[1], hw[2], hw[3]);
+            st_shared_v4u(a + 2048u, lw[0], lw[1], lw[2], lw[3]);
+        }
+    } else {
+        const uint32_t row = stg + uint32_t(lane >> 4) * 1024u + uint32_t(li) * 32u;
+        const uint32_t flip = uint32_t((li >> 2) & 1);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    split2(__uint_as_float(r[16 * h + 8 * q + 2 * e]),
+                           __uint_as_float(r[16 * h + 8 * q + 2 * e + 1]), hw[e], lw[e]);
+                const uint32_t a = row + uint32_t(h) * 512u + ((uint32_t(q) ^ flip) << 4);
+                st_shared_v4u(a, hw[0], hw[1], hw[2], hw[3]);
+                st_shared_v4u(a + 2048u, lw[0], lw[1], lw[2], lw[3]);
+            }
+        }
+    }
+    fence_proxy_async_shared();   // the staging writes, before the tensor stores read them
+    __syncwarp();
+    if (lane == 0) {
+        if (wide) {
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                if (!valid[g]) continue;
+                const uint32_t box = stg + uint32_t(g) * 1024u;
+                tma_store_3d(&L.t_store_map[0], box, j0, s0 * rps + x[g], z[g]);
+                tma_store_3d(&L.t_store_map[1], box + 2048u, j0, s0 * rps + x[g], z[g]);
+            }
+        } else {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (16 * h >= cmax) continue;
+                const int nh = n + 16 * h;
+                const int s = nh / o2m;
+                const int j = nh - s * o2m;
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    if (!valid[g]) continue;
+                    const uint32_t box = stg + uint32_t(2 * g + h) * 512u;
+                    tma_store_3d(&L.t_store_map[2], box, j, s * rps + x[g], z[g]);
+                    tma_store_3d(&L.t_store_map[3], box + 2048u, j, s * rps + x[g], z[g]);
+                }
             }
         }
         bulk_commit_group();
@@ -582,12 +691,13 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
             int bx[2] = {0, 0}, bz[2] = {0, 0};
             bool bvalid[2] = {false, false};
             if (tst) {
+                const int rpo = tst == kStoreSiteMajor ? L.o2_rows_per_op : S.rows_per_op;
 #pragma unroll
                 for (int g = 0; g < 2; ++g) {
                     const int rg = row - lane + 16 * g;
                     bvalid[g] = rg < P->M && dt.kb_begin < dt.kb_end;
-                    const int op = rg / S.rows_per_op;
-                    const int il = rg - op * S.rows_per_op;
+                    const int op = rg / rpo;
+                    const int il = rg - op * rpo;
                     bx[g] = tst == kStoreSiteInterleaved ? il * tsd : il;
                     bz[g] = P->store_z0 + op;
                 }
@@ -621,7 +731,7 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                     // clips it); row-contiguous boxes are 16 columns wide, as are tiles
                     const bool tma_chunk =
                         tst && last &&
-                        (tst == kStoreRowContiguous || cmax == 32 || n0 + ncols == P->N);
+                        (tst != kStoreSiteInterleaved || cmax == 32 || n0 + ncols == P->N);
                     if (sum_in_out) {
                         // the first chain stores, each later one adds into the output
                         // (the same lane, in program order: the same FP32 additions in
@@ -658,9 +768,12 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                         if (tma_chunk) {
                             if (tst == kStoreSiteInterleaved)
                                 store_chunk_tma(L, r, stg, lane, tsd, bx, (n0 + c) / tsd, bz, bvalid);
-                            else
+                            else if (tst == kStoreRowContiguous)
                                 store_chunk_tma_rows(L, r, stg, lane, bx, bz, bvalid, n0 + c, cmax,
                                                      cdiv, sch);
+                            else
+                                store_chunk_tma_site(L, r, stg, lane, bx, bz, bvalid, n0 + c, cmax,
+                                                     L.o2_m, L.o2_rows_per_op);
                         }
                     }
                     // the site-major copy's stores are warp-collective: every lane comes here
@@ -728,7 +841,9 @@ cudaError_t launch_pair(const TcLaunch& L, int stages, int grid, int bh_smem, si
     auto k = L.convert_a ? tc_gemm_pair_kernel<MODE, EPI, 128, true, false, false>
              : L.row_bytes == 64 ? tc_gemm_pair_kernel<MODE, EPI, 64, false, false, false>
                                  : tc_gemm_pair_kernel<MODE, EPI, 128, false, false, false>;
-    if (kSiteEpi && L.out2[0] != nullptr) k = tc_gemm_pair_kernel<MODE, EPI, 128, false, kSiteEpi, false>;
+    // (the site-major TMA store writes the second copy itself, without the SITE code)
+    if (kSiteEpi && L.out2[0] != nullptr && L.t_store != kStoreSiteMajor)
+        k = tc_gemm_pair_kernel<MODE, EPI, 128, false, kSiteEpi, false>;
     if constexpr (MODE == TC_BF16X3) {
         bool mn = false;
         for (int i = 0; i < L.nprob; ++i) mn = mn || L.inline_prob[i].a_mn || L.inline_prob[i].b_mn;
@@ -801,14 +916,22 @@ cudaError_t tc_gemm_launch_pair(TcMode mode, TcEpi epi, const TcLaunch& L, int s
     TcLaunch plain;
     if (L.t_store != 0) {
         const bool site = L.t_store == kStoreSiteInterleaved;
-        bool ok = epi == EPI_SPLIT_BF16 && L.out2[0] == nullptr && L.out[0][0] != nullptr &&
-                  (site ? (L.t_store_d == 2 || L.t_store_d == 4) : L.t_store == kStoreRowContiguous);
+        const bool smaj = L.t_store == kStoreSiteMajor;
+        bool ok = epi == EPI_SPLIT_BF16 &&
+                  (smaj ? (L.out2[0] != nullptr && L.out[0][0] == nullptr &&
+                           L.o2_rows_per_op % 16 == 0 && L.o2_m % 16 == 0)
+                        : (L.out2[0] == nullptr && L.out[0][0] != nullptr)) &&
+                  (site ? (L.t_store_d == 2 || L.t_store_d == 4)
+                        : (L.t_store == kStoreRowContiguous || smaj));
         for (int i = 0; ok && i < L.nprob; ++i) {
-            const TcScatter& S = L.inline_prob[i].sc[0];
-            ok = L.inline_prob[i].k_splits == 1 && S.s_split == 0 && S.rows_per_op % 16 == 0 &&
-                 (site ? S.col_div == L.t_store_d
-                       : (S.col_div % 16 == 0 && S.s_row == 1 && S.s_col_hi % 8 == 0 &&
-                          L.inline_prob[i].N % 16 == 0));
+            const TcProblem& P = L.inline_prob[i];
+            const TcScatter& S = P.sc[0];
+            ok = P.k_splits == 1 &&
+                 (smaj ? P.N % 16 == 0
+                       : (S.s_split == 0 && S.rows_per_op % 16 == 0 &&
+                          (site ? S.col_div == L.t_store_d
+                                : (S.col_div % 16 == 0 && S.s_row == 1 && S.s_col_hi % 8 == 0 &&
+                                   P.N % 16 == 0))));
         }
         const size_t with = pair_smem_bytes(mode, stages, bh, L.row_bytes, true);
         if (ok && with <= 232448) {
