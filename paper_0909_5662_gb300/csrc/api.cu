@@ -252,10 +252,16 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     L2.out[0][0] = Oout;
     const int grid2 = c2.grid > 0 ? c2.grid : h->num_sms;
     P2.kb_chunk = chain_kb(c2, D.md, grid2);
-    // a tile's two or three chains are summed in the FP32 output itself (the first chain
-    // stores, the others add with reductions): measured 0.161 -> 0.156 ms against the
-    // scratch at m = m' = 400, d = 4, K = 150
-    L2.chunk_scratch = nullptr;
+    // Up to two chains per tile are summed in the FP32 output itself (the first chain
+    // stores, the second adds with reductions): 0.161 -> 0.156 ms against the scratch at
+    // m = m' = 400, d = 4, K = 150.  More chains go through the scratch: at m = m' = 1200
+    // (five chains) the reductions made the step 3 % slower.
+    {
+        const int64_t epr = c2.row_bytes / (split ? 2 : 4);
+        const int64_t kb = (D.md + epr - 1) / epr;
+        const int64_t chains = P2.kb_chunk > 0 ? (kb + P2.kb_chunk - 1) / P2.kb_chunk : 1;
+        L2.chunk_scratch = chains > 2 ? chain_scr : nullptr;
+    }
     int64_t k_clear = K;   // outputs k >= k_clear are accumulated atomically: cleared first
     // Tail wave: the tiles left after the last full wave over the persistent CTAs (or
     // CTA pairs) are whole M tiles whose reduction is split so the last round is short;

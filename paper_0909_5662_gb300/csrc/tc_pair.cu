@@ -369,10 +369,11 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
     constexpr bool kMnOk = MN && (MODE != TC_TF32) && (RB == 128) && !CONV;
     constexpr uint32_t kMnBoxBytes = uint32_t(kMnBox) * 128u;
     // FP32 output: the chains of a tile are summed in the output itself (the first chain
-    // stores, later ones add with reductions).  Only the MN-major instantiation (the
-    // adjoint's dU products, up to eight chains per tile, for which the reductions
-    // measured slower) carries the scratch code for FP32 and uses it when given one;
-    // elsewhere the unused scratch code alone cost 2-3 % of the second product.
+    // stores, later ones add with reductions).  Only the MN-major instantiation carries the
+    // scratch code for FP32 and uses it when given the scratch (the launcher picks it for
+    // every FP32 launch that is: the adjoint's dU products, up to eight chains per tile,
+    // and second products of more than two chains, for which the reductions measured
+    // slower); elsewhere the unused scratch code alone cost 2-3 % of the second product.
     constexpr bool kF32Out = (EPI == EPI_F32 || EPI == EPI_F32_ATOMIC);
     constexpr bool kScratchCode = !kF32Out || MN;
     const bool sum_in_out = kF32Out && (!MN || L.chunk_scratch == nullptr);
@@ -847,7 +848,11 @@ cudaError_t launch_pair(const TcLaunch& L, int stages, int grid, int bh_smem, si
     if constexpr (MODE == TC_BF16X3) {
         bool mn = false;
         for (int i = 0; i < L.nprob; ++i) mn = mn || L.inline_prob[i].a_mn || L.inline_prob[i].b_mn;
-        if (mn) k = tc_gemm_pair_kernel<MODE, EPI, 128, false, false, true>;
+        // FP32 output with the chain scratch: the MN-major instantiation is the FP32 one that
+        // carries the scratch code (it takes K-major problems as well)
+        const bool f32_scratch = (EPI == EPI_F32 || EPI == EPI_F32_ATOMIC) && L.chunk_scratch != nullptr &&
+                                 L.row_bytes == 128 && !L.convert_a;
+        if (mn || f32_scratch) k = tc_gemm_pair_kernel<MODE, EPI, 128, false, false, true>;
     }
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
