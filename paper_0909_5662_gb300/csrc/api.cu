@@ -398,12 +398,14 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
     L1.row_bytes = c1.row_bytes;
     L1.chunk_scratch = L1.inline_prob[0].kb_chunk ? chain_scr : nullptr;
     L1.convert_a = convert_a ? 1 : 0;
-    // BF16x3 on CTA pairs: T leaves through TMA bulk stores (staged per warp in shared
-    // memory) rather than 8-byte stores from registers, where the layout allows it
-    if (split && c1.pair && h->store_epilogue == 0 && (d == 2 || d == 4) && m % 16 == 0) {
+    // On CTA pairs T leaves through TMA bulk stores (staged per warp in shared memory)
+    // rather than stores from registers, where the layout allows it (BF16 hi and lo, or
+    // the TF32-rounded FP32 T)
+    if (c1.pair && h->store_epilogue == 0 && (d == 2 || d == 4) && m % 16 == 0) {
         bool ok = true;
-        for (int c = 0; c < 2 && ok; ++c)
-            ok = encode_store_map(&L1.t_store_map[c], Tt[c], D.md, mp, K, D.ld2, 16 * d, 32 / d);
+        for (int c = 0; c < (split ? 2 : 1) && ok; ++c)
+            ok = encode_store_map(&L1.t_store_map[c], Tt[c], D.md, mp, K, D.ld2, 16 * d, 32 / d, 0,
+                                  !split);
         if (ok) {
             L1.t_store = kStoreSiteInterleaved;
             L1.t_store_d = d;

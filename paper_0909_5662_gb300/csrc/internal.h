@@ -154,15 +154,15 @@ struct TcLaunch {
     void* out2[2];
     int64_t o2_s_op, o2_s_row, o2_s_site;
     int32_t o2_rows_per_op, o2_m;
-    // CTA-pair kernel, EPI_SPLIT_BF16: the result leaves by TMA bulk stores instead of
-    // stores from registers (t_store = 0: off).  Each epilogue warp stages one 32-column
+    // CTA-pair kernel, EPI_SPLIT_BF16 (and EPI_TF32, site-interleaved layout only): the
+    // result leaves by TMA bulk stores instead of stores from registers (t_store = 0: off).  Each epilogue warp stages one 32-column
     // chunk (hi and lo) of its 32 rows in shared memory; launches whose shared memory
     // cannot hold the staging store from registers.  Rows R = k_local * rows_per_op + i
     // (rows_per_op a multiple of 16); t_store_map[hi, lo] are 3-D maps whose third
     // coordinate is the operator k = store_z0 + k_local.  The scatter must be one of:
     //   kStoreSiteInterleaved (t_store_d = d, 2 or 4): column n = b * d + s goes to
     //     T[k][b][i * d + s], as in the first product; map (i * d + s, b, k), box
-    //     16 d x 32 / d x 1;
+    //     16 d x 32 / d x 1 (EPI_SPLIT_BF16: BF16 hi and lo maps; EPI_TF32: one FP32 map);
     //   kStoreRowContiguous: column n = s * col_div + j goes to
     //     W[k][j][s * s_col_hi + i] (s_row = 1, col_div a multiple of 16); maps
     //     (s * s_col_hi + i, j, k), boxes 32 x 16 x 1 ([0], [1]: a warp's 32 rows in one
@@ -181,7 +181,7 @@ constexpr int32_t kStoreSiteInterleaved = 1;
 constexpr int32_t kStoreRowContiguous = 2;
 constexpr int32_t kStoreSiteMajor = 3;
 // Shared memory of the CTA-pair kernel's store staging: per epilogue warp, the hi and lo
-// halves of a 32-row x 32-column BF16 chunk.
+// halves of a 32-row x 32-column BF16 chunk (or the FP32 chunk).
 constexpr size_t kStoreStagingBytes = size_t(8) * 2 * 32 * 32 * 2;
 
 // One operand seen by the kernel: `nbatch` slices of rows x cols (cols = the
@@ -223,11 +223,12 @@ inline int tc_stages_for(TcMode mode, const TcConfig& c) {
 bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t rows, int64_t cols,
                         int64_t ld, int box_rows, int64_t nbatch = 1, int64_t batch_stride = 0,
                         int row_bytes = 128);
-// Encodes a BF16 store map for the CTA-pair kernel's TMA-store epilogue: nz slices of ny
-// rows x nx elements (row stride ld elements, slice stride ny * ld), box bx x by x 1;
-// swizzle: 0, or the shared-memory swizzle span in bytes (bx * 2: 32 or 64).
+// Encodes a store map (BF16, or FP32 with fp32) for the CTA-pair kernel's TMA-store
+// epilogue: nz slices of ny rows x nx elements (row stride ld elements, slice stride
+// ny * ld), box bx x by x 1; swizzle: 0, or the shared-memory swizzle span in bytes (the
+// box row: 32 or 64).
 bool encode_store_map(CUtensorMap* map, void* base, int64_t nx, int64_t ny, int64_t nz, int64_t ld,
-                      int bx, int by, int swizzle = 0);
+                      int bx, int by, int swizzle = 0, bool fp32 = false);
 // Chooses an N tile (multiple of 16, <= tile_n_max) that splits N evenly.
 int choose_tile_n(int64_t N, int tile_n_max);
 // Fills operand maps and tiling fields of a problem: D (M x N) += A B^T over Kred x nbatch.

@@ -948,16 +948,19 @@ bool encode_operand_map(CUtensorMap* map, const void* base, bool fp32, int64_t r
 }
 
 bool encode_store_map(CUtensorMap* map, void* base, int64_t nx, int64_t ny, int64_t nz, int64_t ld,
-                      int bx, int by, int swizzle) {
-    if ((ld % 8) != 0 || nx > ld || (reinterpret_cast<uintptr_t>(base) & 15) || (bx * 2) % 16 != 0 ||
-        (swizzle != 0 && swizzle != 2 * bx) || (swizzle != 0 && swizzle != 32 && swizzle != 64))
+                      int bx, int by, int swizzle, bool fp32) {
+    const int es = fp32 ? 4 : 2;
+    if ((ld * es) % 16 != 0 || nx > ld || (reinterpret_cast<uintptr_t>(base) & 15) ||
+        (bx * es) % 16 != 0 || (swizzle != 0 && swizzle != es * bx) ||
+        (swizzle != 0 && swizzle != 32 && swizzle != 64))
         return false;
     if (!have_encode()) return false;
     cuuint64_t gdim[3] = {cuuint64_t(nx), cuuint64_t(ny), cuuint64_t(nz)};
-    cuuint64_t gstride[2] = {cuuint64_t(ld) * 2, cuuint64_t(ny * ld) * 2};
+    cuuint64_t gstride[2] = {cuuint64_t(ld) * es, cuuint64_t(ny * ld) * es};
     cuuint32_t box[3] = {cuuint32_t(bx), cuuint32_t(by), 1};
     cuuint32_t estride[3] = {1, 1, 1};
-    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, gdim, gstride, box, estride,
+    CUresult r = g_encode(map, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                          3, base, gdim, gstride, box, estride,
                           CU_TENSOR_MAP_INTERLEAVE_NONE,
                           swizzle == 64   ? CU_TENSOR_MAP_SWIZZLE_64B
                           : swizzle == 32 ? CU_TENSOR_MAP_SWIZZLE_32B

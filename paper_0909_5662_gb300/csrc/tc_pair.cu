@@ -313,6 +313,38 @@ __device__ __forceinline__ void store_chunk_tma_site(const TcLaunch& L, const ui
     }
 }
 
+// The site-interleaved layout for FP32 (TF32-rounded) output: one 4 KB staging buffer, the
+// box of group g (16 d floats x 32 / d rows b) at stg + 2048 g; lane l's values of (b,
+// s = 0..d-1) land in row b at float (l % 16) * d.  One map, t_store_map[0].
+__device__ __forceinline__ void store_chunk_tma_f32(const TcLaunch& L, const uint32_t (&r)[32],
+                                                    uint32_t stg, int lane, int d, const int (&x)[2],
+                                                    int y, const int (&z)[2], const bool (&valid)[2]) {
+    if (lane == 0) bulk_wait_group_read0();   // the previous chunk's stores have read stg
+    __syncwarp();
+    const uint32_t box = stg + uint32_t(lane >> 4) * 2048u + uint32_t(lane & 15) * uint32_t(4 * d);
+    if (d == 4) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)   // row b = j: columns 4j .. 4j+3
+            st_shared_v4u(box + uint32_t(j) * 256u, __float_as_uint(tf32_round(__uint_as_float(r[4 * j]))),
+                          __float_as_uint(tf32_round(__uint_as_float(r[4 * j + 1]))),
+                          __float_as_uint(tf32_round(__uint_as_float(r[4 * j + 2]))),
+                          __float_as_uint(tf32_round(__uint_as_float(r[4 * j + 3]))));
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)   // d = 2, row b = j: columns 2j, 2j+1
+            st_shared_v2u(box + uint32_t(j) * 128u, __float_as_uint(tf32_round(__uint_as_float(r[2 * j]))),
+                          __float_as_uint(tf32_round(__uint_as_float(r[2 * j + 1]))));
+    }
+    fence_proxy_async_shared();   // the staging writes, before the tensor stores read them
+    __syncwarp();
+    if (lane == 0) {
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+            if (valid[g]) tma_store_3d(&L.t_store_map[0], stg + uint32_t(g) * 2048u, x[g], y, z[g]);
+        bulk_commit_group();
+    }
+}
+
 // Converts row `row` of this CTA's A tile in place (see the converting form above).
 // box0 / box1: shared addresses of the two 128 x 128-byte regions of the stage's A.
 template <int MODE>
@@ -664,7 +696,7 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                                 (int64_t(blockIdx.x) * 4 + quad) * (8 * 8 * 32) + lane
                           : nullptr;
         // TMA-store epilogue: this warp's 4 KB of staging after the barriers
-        constexpr bool kStoreOk = (EPI == EPI_SPLIT_BF16) && !SITE;
+        constexpr bool kStoreOk = (EPI == EPI_SPLIT_BF16 || EPI == EPI_TF32) && !SITE;
         const int tst = kStoreOk ? L.t_store : 0;
         const int tsd = L.t_store_d;
         const uint32_t stg = smem_u32(smem + size_t(stages) * stage_bytes + 512) +
@@ -767,14 +799,18 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                     }
                     if constexpr (kStoreOk) {
                         if (tma_chunk) {
-                            if (tst == kStoreSiteInterleaved)
-                                store_chunk_tma(L, r, stg, lane, tsd, bx, (n0 + c) / tsd, bz, bvalid);
-                            else if (tst == kStoreRowContiguous)
-                                store_chunk_tma_rows(L, r, stg, lane, bx, bz, bvalid, n0 + c, cmax,
-                                                     cdiv, sch);
-                            else
-                                store_chunk_tma_site(L, r, stg, lane, bx, bz, bvalid, n0 + c, cmax,
-                                                     L.o2_m, L.o2_rows_per_op);
+                            if constexpr (EPI == EPI_TF32) {   // site-interleaved only
+                                store_chunk_tma_f32(L, r, stg, lane, tsd, bx, (n0 + c) / tsd, bz, bvalid);
+                            } else {
+                                if (tst == kStoreSiteInterleaved)
+                                    store_chunk_tma(L, r, stg, lane, tsd, bx, (n0 + c) / tsd, bz, bvalid);
+                                else if (tst == kStoreRowContiguous)
+                                    store_chunk_tma_rows(L, r, stg, lane, bx, bz, bvalid, n0 + c, cmax,
+                                                         cdiv, sch);
+                                else
+                                    store_chunk_tma_site(L, r, stg, lane, bx, bz, bvalid, n0 + c, cmax,
+                                                         L.o2_m, L.o2_rows_per_op);
+                            }
                         }
                     }
                     // the site-major copy's stores are warp-collective: every lane comes here
@@ -922,7 +958,7 @@ cudaError_t tc_gemm_launch_pair(TcMode mode, TcEpi epi, const TcLaunch& L, int s
     if (L.t_store != 0) {
         const bool site = L.t_store == kStoreSiteInterleaved;
         const bool smaj = L.t_store == kStoreSiteMajor;
-        bool ok = epi == EPI_SPLIT_BF16 &&
+        bool ok = (epi == EPI_SPLIT_BF16 || (epi == EPI_TF32 && site)) &&
                   (smaj ? (L.out2[0] != nullptr && L.out[0][0] == nullptr &&
                            L.o2_rows_per_op % 16 == 0 && L.o2_m % 16 == 0)
                         : (L.out2[0] == nullptr && L.out[0][0] != nullptr)) &&
@@ -938,9 +974,14 @@ cudaError_t tc_gemm_launch_pair(TcMode mode, TcEpi epi, const TcLaunch& L, int s
                                 : (S.col_div % 16 == 0 && S.s_row == 1 && S.s_col_hi % 8 == 0 &&
                                    P.N % 16 == 0))));
         }
-        const size_t with = pair_smem_bytes(mode, stages, bh, L.row_bytes, true);
+        // the staging takes the place of pipeline stages where it must (TF32: 32 KB stages,
+        // seven of which fill the shared memory), down to three
+        int st = stages;
+        while (ok && st > 3 && pair_smem_bytes(mode, st, bh, L.row_bytes, true) > 232448) --st;
+        const size_t with = pair_smem_bytes(mode, st, bh, L.row_bytes, true);
         if (ok && with <= 232448) {
             smem = with;
+            stages = st;
         } else {
             plain = L;
             plain.t_store = 0;

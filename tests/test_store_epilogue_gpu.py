@@ -9,7 +9,7 @@ both site dimensions the store maps take (d = 2, 4), operators that begin in the
 of a warp's 32 rows (m = 48, 400), chunks that are short inside N (N tiles of 208 and
 176 columns) and at the end of N (d * m' not a multiple of 32), rows past the last
 operator, accumulation chains (m > 1024), and layouts that fall back to register stores
-(d = 3, m not a multiple of 16).  The adjoint's W' product takes the row-contiguous form
+(d = 3, m not a multiple of 16); TF32 takes the FP32 form of the first layout.  The adjoint's W' product takes the row-contiguous form
 of the same epilogue and is checked the same way against the oracle's adjoint.
 """
 import numpy as np
@@ -35,14 +35,14 @@ def rel_err(got, ref):
     return num / np.linalg.norm(ref.reshape(len(ref), -1), axis=1)
 
 
-def rotate(P, U, O, d, store, opts=()):
+def rotate(P, U, O, d, store, opts=(), prec="bf16x3"):
     h = P.Handle()
     try:
         P.dmrg_set_option("deterministic", 1, handle=h)
         P.dmrg_set_option("store_epilogue", store, handle=h)
         for k, v in opts:
             P.dmrg_set_option(k, v, handle=h)
-        out = P.dmrg_rotate_ops(U, O, d, "bf16x3", handle=h)
+        out = P.dmrg_rotate_ops(U, O, d, prec, handle=h)
         torch.cuda.synchronize()
         P.dmrg_sync_status(handle=h)
         return out.double().cpu().numpy()
@@ -77,6 +77,23 @@ def test_tma_store_epilogue_matches_register_stores_and_oracle(P, shape):
     assert np.array_equal(tma, reg)
     ref = oracle.rotate_dense(U, O.astype(np.float64), d)
     assert rel_err(tma, ref).max() <= TOL
+
+
+@pytest.mark.parametrize("shape", [(48, 4, 100, 7), (400, 4, 400, 9), (64, 2, 104, 5), (96, 4, 130, 3),
+                                   (50, 4, 60, 3)])
+def test_tma_store_epilogue_tf32(P, shape):
+    # TF32: the first product's T is FP32 (TF32-rounded) and leaves through the same
+    # site-interleaved boxes in FP32, the pipeline giving up a stage for the staging
+    m, d, mp, K = shape
+    rng = np.random.default_rng(9900 + m + 7 * mp + K)
+    U = orthonormal_columns(rng, m * d, mp)
+    O = rng.standard_normal((K, m, m)).astype(np.float32)
+    dev = torch.device("cuda")
+    Ud, Od = torch.from_numpy(U).to(dev), torch.from_numpy(O).to(dev)
+    tma = rotate(P, Ud, Od, d, 0, opts=(("pack_operators", 1),), prec="tf32")
+    reg = rotate(P, Ud, Od, d, 1, opts=(("pack_operators", 1),), prec="tf32")
+    assert np.array_equal(tma, reg)
+    assert rel_err(tma, oracle.rotate_dense(U, O.astype(np.float64), d)).max() <= 3e-3
 
 
 @pytest.mark.parametrize("shape", [(64, 4, 64, 5), (48, 2, 100, 4)])
