@@ -7,9 +7,10 @@ This entry point takes no handle and no workspace; its scratch is a fixed
 static device array inside the library.  The test calls it through the C ABI
 twice in a row on different inputs and checks each result against
 dmrg_rotate_ops on the same inputs and against the FP64 oracle, with the
-tolerances of the other dense tests.  One BF16x3 case has m*d > 1024, so its
-second product cuts the reduction into accumulation chains whose running sums
-live in the static array too.  Finally an oversized problem must be refused
+tolerances of the other dense tests.  Two BF16x3 cases have m*d > 1024, so their
+second product cuts the reduction into accumulation chains: two per tile at
+m*d = 1200, summed in the output itself, and three at m*d = 2400, whose running
+sums live in the static array too.  Finally an oversized problem must be refused
 before any launch.  This file is named to be collected last.
 """
 import ctypes
@@ -48,8 +49,10 @@ CASES = [
     ("bf16x3", 4, 64, 64, 32),
     ("tf32", 4, 64, 64, 32),
     ("fp32", 4, 64, 64, 32),
-    # m*d = 1200 > 1024: chained accumulation through the static array (about 27 MiB)
+    # m*d = 1200 > 1024: two accumulation chains per tile, summed in the output
     ("bf16x3", 4, 300, 64, 8),
+    # m*d = 2400: three chains, summed through the scratch in the static array (about 26 MB)
+    ("bf16x3", 4, 600, 64, 2),
 ]
 
 
