@@ -262,6 +262,11 @@ dmrg_status dense_tc_forward(dmrg_handle h, const double* U, int64_t m, int d, i
         const int64_t chains = P2.kb_chunk > 0 ? (kb + P2.kb_chunk - 1) / P2.kb_chunk : 1;
         L2.chunk_scratch = chains > 2 ? chain_scr : nullptr;
     }
+    // summed in the output: O' leaves by TMA bulk stores, the second chain (and the parts
+    // of split tiles) by TMA reductions, staged per warp in shared memory
+    if (c2.pair && h->store_epilogue == 0 && L2.chunk_scratch == nullptr && mp % 16 == 0 &&
+        encode_store_map(&L2.t_store_map[0], Oout, mp, mp, K, mp, 16, 16, 0, true))
+        L2.t_store = kStoreColumnsF32;
     int64_t k_clear = K;   // outputs k >= k_clear are accumulated atomically: cleared first
     // Tail wave: the tiles left after the last full wave over the persistent CTAs (or
     // CTA pairs) are whole M tiles whose reduction is split so the last round is short;

@@ -361,7 +361,12 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
         L.status = h->d_status;
         L.timeout_ns = timeout_ns(h);
         L.row_bytes = cfg.row_bytes;
-        L.chunk_scratch = L.inline_prob[0].kb_chunk ? chain_scr : nullptr;
+        // FP32 output with at most two chains per tile sums them in the output (the first
+        // chain stores, the second adds), as the forward's second product does
+        const int64_t kbt = (red + cfg.row_bytes / int64_t(es) - 1) / (cfg.row_bytes / int64_t(es));
+        const int64_t chains = chain_kb > 0 ? (kbt + chain_kb - 1) / chain_kb : 1;
+        L.chunk_scratch = (L.inline_prob[0].kb_chunk && !(epi == EPI_F32 && chains <= 2)) ? chain_scr
+                                                                                         : nullptr;
         cudaError_t ee = timed_launch(h, name, s, [&] {
             return tc_gemm_launch_pair(mode, epi, L, cfg.stages, grid, s);
         });
@@ -428,6 +433,11 @@ dmrg_status bwd_tc(dmrg_handle h, const double* U, const void* O, const void* G,
         S2.col_div = 1; S2.s_col_hi = m; S2.s_col_lo = 0;
         L2.nprob = 1;
         L2.out[0][0] = dO;
+        // dO leaves by TMA bulk stores (and its second chain by TMA reductions) where the
+        // launch sums its chains in the output
+        if (split && h->store_epilogue == 0 && m % 16 == 0 &&
+            encode_store_map(&L2.t_store_map[0], dO, m, m, K, m, 16, 16, 0, true))
+            L2.t_store = kStoreColumnsF32;
         if ((st = launch("bwd_tc_dO", L2, EPI_F32, dmp)) != DMRG_OK) return st;
     }
     if (dU) {

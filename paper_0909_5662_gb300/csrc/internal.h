@@ -154,8 +154,9 @@ struct TcLaunch {
     void* out2[2];
     int64_t o2_s_op, o2_s_row, o2_s_site;
     int32_t o2_rows_per_op, o2_m;
-    // CTA-pair kernel, EPI_SPLIT_BF16 (and EPI_TF32, site-interleaved layout only): the
-    // result leaves by TMA bulk stores instead of stores from registers (t_store = 0: off).  Each epilogue warp stages one 32-column
+    // CTA-pair kernel, EPI_SPLIT_BF16 (EPI_TF32: site-interleaved layout only; EPI_F32:
+    // columns layout only): the result leaves by TMA bulk stores instead of stores from
+    // registers (t_store = 0: off).  Each epilogue warp stages one 32-column
     // chunk (hi and lo) of its 32 rows in shared memory; launches whose shared memory
     // cannot hold the staging store from registers.  Rows R = k_local * rows_per_op + i
     // (rows_per_op a multiple of 16); t_store_map[hi, lo] are 3-D maps whose third
@@ -171,8 +172,12 @@ struct TcLaunch {
     //     o2_rows_per_op multiples of 16): column n = s * o2_m + j goes to
     //     out2_k[s * o2_rows_per_op + i][j]; maps (j, s * o2_rows_per_op + i, k), boxes
     //     32 x 16 x 1 with the 64-byte swizzle ([0], [1]: a chunk's 32 columns in one
-    //     site) and 16 x 16 x 1 with the 32-byte swizzle ([2], [3]).
-    // t_store_map[hi, lo, hi narrow, lo narrow].
+    //     site) and 16 x 16 x 1 with the 32-byte swizzle ([2], [3]);
+    //   kStoreColumnsF32 (EPI_F32 / EPI_F32_ATOMIC, chains summed in the output): column
+    //     n of row (k, i) goes to out_k[n][i] (s_row = 1, col_div = 1, s_op = N s_col_hi);
+    //     map (i, n, k), FP32 box 16 x 16 x 1; a tile's later chains and the parts of a
+    //     split tile add with TMA reductions.
+    // t_store_map[hi, lo, hi narrow, lo narrow] (one FP32 map: [0]).
     CUtensorMap t_store_map[4];
     int32_t t_store;
     int32_t t_store_d;
@@ -180,6 +185,7 @@ struct TcLaunch {
 constexpr int32_t kStoreSiteInterleaved = 1;
 constexpr int32_t kStoreRowContiguous = 2;
 constexpr int32_t kStoreSiteMajor = 3;
+constexpr int32_t kStoreColumnsF32 = 4;
 // Shared memory of the CTA-pair kernel's store staging: per epilogue warp, the hi and lo
 // halves of a 32-row x 32-column BF16 chunk (or the FP32 chunk).
 constexpr size_t kStoreStagingBytes = size_t(8) * 2 * 32 * 32 * 2;

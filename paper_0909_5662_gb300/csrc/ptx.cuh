@@ -157,6 +157,15 @@ __device__ __forceinline__ void tma_store_3d(const void* tmap, uint32_t smem_src
                  "r"(x), "r"(y), "r"(z), "r"(smem_src)
                  : "memory");
 }
+// 3-D tiled reduction (add) of a shared-memory box into global memory (bulk-group
+// completion); the element type is the tensor map's.
+__device__ __forceinline__ void tma_reduce_add_3d(const void* tmap, uint32_t smem_src, int32_t x,
+                                                  int32_t y, int32_t z) {
+    asm volatile("cp.reduce.async.bulk.tensor.3d.global.shared::cta.add.bulk_group [%0, {%1, %2, %3}], [%4];" ::
+                     "l"(reinterpret_cast<uint64_t>(tmap)),
+                 "r"(x), "r"(y), "r"(z), "r"(smem_src)
+                 : "memory");
+}
 __device__ __forceinline__ void bulk_commit_group() {
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }

@@ -345,6 +345,52 @@ __device__ __forceinline__ void store_chunk_tma_f32(const TcLaunch& L, const uin
     }
 }
 
+// TMA-store epilogue, columns layout for FP32 output (TcLaunch::t_store =
+// kStoreColumnsF32): column n of row (k, i) goes to out_k[n][i], so a lane's values run
+// down a column of out_k.  The chunk (columns n .. n + 31, cmax of them valid, a multiple
+// of 16) is up to four boxes of 16 n x 16 i: box (g, h) for row group g and column half
+// h at stg + (2 g + h) * 1024, row j (column n + 16 h + j) at 64 j bytes, lane i's value at
+// 4 (i % 16) (the two half-warps' 64-byte rows share banks: two wavefronts per store,
+// which costs less than the registers a rotation of the upper half's columns took).
+// reduce: the boxes are added to the
+// output (a tile's later chains, the parts of a split tile).  drain (the warp's first
+// chunk of a chain that adds): the lane first waits until its earlier bulk operations
+// have completed, so that the chain's additions follow the stores of the chain before it;
+// otherwise it waits only until they have read the staging.  x[g] = i of group g's first
+// row, z[g] its operator.
+__device__ __forceinline__ void store_chunk_tma_cols_f32(const TcLaunch& L, const uint32_t (&r)[32],
+                                                         uint32_t stg, int lane, const int (&x)[2],
+                                                         const int (&z)[2], const bool (&valid)[2],
+                                                         int n, int cmax, bool reduce, bool drain) {
+    if (lane == 0) {
+        if (drain) bulk_wait_group0();
+        else bulk_wait_group_read0();   // the previous chunk's stores have read stg
+    }
+    __syncwarp();
+    const uint32_t base = stg + uint32_t(lane >> 4) * 2048u + uint32_t(lane & 15) * 4u;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) st_shared_u32(base + uint32_t(h * 1024 + j * 64), r[16 * h + j]);
+    }
+    fence_proxy_async_shared();   // the staging writes, before the tensor stores read them
+    __syncwarp();
+    if (lane == 0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (16 * h >= cmax) continue;
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                if (!valid[g]) continue;
+                const uint32_t box = stg + uint32_t(2 * g + h) * 1024u;
+                if (reduce) tma_reduce_add_3d(&L.t_store_map[0], box, x[g], n + 16 * h, z[g]);
+                else tma_store_3d(&L.t_store_map[0], box, x[g], n + 16 * h, z[g]);
+            }
+        }
+        bulk_commit_group();
+    }
+}
+
 // Converts row `row` of this CTA's A tile in place (see the converting form above).
 // box0 / box1: shared addresses of the two 128 x 128-byte regions of the stage's A.
 template <int MODE>
@@ -696,7 +742,7 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                                 (int64_t(blockIdx.x) * 4 + quad) * (8 * 8 * 32) + lane
                           : nullptr;
         // TMA-store epilogue: this warp's 4 KB of staging after the barriers
-        constexpr bool kStoreOk = (EPI == EPI_SPLIT_BF16 || EPI == EPI_TF32) && !SITE;
+        constexpr bool kStoreOk = !SITE;
         const int tst = kStoreOk ? L.t_store : 0;
         const int tsd = L.t_store_d;
         const uint32_t stg = smem_u32(smem + size_t(stages) * stage_bytes + 512) +
@@ -763,16 +809,25 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                     // N (the box would spill into the next tile's columns; past N the map
                     // clips it); row-contiguous boxes are 16 columns wide, as are tiles
                     const bool tma_chunk =
-                        tst && last &&
+                        tst && tst != kStoreColumnsF32 && last &&
                         (tst != kStoreSiteInterleaved || cmax == 32 || n0 + ncols == P->N);
                     if (sum_in_out) {
                         // the first chain stores, each later one adds into the output
                         // (the same lane, in program order: the same FP32 additions in
                         // the same order as through the scratch, subnormal sums aside,
                         // which the reductions flush to zero)
-                        if (row_ok && L.out[0][0] != nullptr)
+                        if constexpr (kF32Out && kStoreOk) {
+                            if (tst == kStoreColumnsF32)   // warp-collective
+                                store_chunk_tma_cols_f32(L, r, stg, lane, bx, bz, bvalid, n0 + c, cmax,
+                                                         tile_atomic || !first,
+                                                         (tile_atomic || !first) && c == half * 32);
+                            else if (row_ok && L.out[0][0] != nullptr)
+                                store_chunk<EPI>(L, r, row_base, n0, c, cmax, cdiv, sch, scl,
+                                                 tile_atomic || !first);
+                        } else if (row_ok && L.out[0][0] != nullptr) {
                             store_chunk<EPI>(L, r, row_base, n0, c, cmax, cdiv, sch, scl,
                                              tile_atomic || !first);
+                        }
                     } else if constexpr (kScratchCode) {
                         if (row_ok) {
                             float4* s4 = scr ? scr + (c >> 5) * (8 * 32) : nullptr;
@@ -797,7 +852,7 @@ __global__ void __launch_bounds__(CONV ? kThreadsConv : kThreads, 1)
                             }
                         }
                     }
-                    if constexpr (kStoreOk) {
+                    if constexpr (kStoreOk && !kF32Out) {
                         if (tma_chunk) {
                             if constexpr (EPI == EPI_TF32) {   // site-interleaved only
                                 store_chunk_tma_f32(L, r, stg, lane, tsd, bx, (n0 + c) / tsd, bz, bvalid);
@@ -875,9 +930,11 @@ template <int MODE, int EPI>
 cudaError_t launch_pair(const TcLaunch& L, int stages, int grid, int bh_smem, size_t smem,
                         cudaStream_t s) {
     constexpr bool kSiteEpi = (EPI == EPI_SPLIT_BF16 || EPI == EPI_TF32);
-    auto k = L.convert_a ? tc_gemm_pair_kernel<MODE, EPI, 128, true, false, false>
-             : L.row_bytes == 64 ? tc_gemm_pair_kernel<MODE, EPI, 64, false, false, false>
-                                 : tc_gemm_pair_kernel<MODE, EPI, 128, false, false, false>;
+    auto k = L.row_bytes == 64 ? tc_gemm_pair_kernel<MODE, EPI, 64, false, false, false>
+                               : tc_gemm_pair_kernel<MODE, EPI, 128, false, false, false>;
+    // (the converting form feeds the first product only: no FP32-output instantiation)
+    if constexpr (EPI == EPI_SPLIT_BF16 || EPI == EPI_TF32)
+        if (L.convert_a) k = tc_gemm_pair_kernel<MODE, EPI, 128, true, false, false>;
     // (the site-major TMA store writes the second copy itself, without the SITE code)
     if (kSiteEpi && L.out2[0] != nullptr && L.t_store != kStoreSiteMajor)
         k = tc_gemm_pair_kernel<MODE, EPI, 128, false, kSiteEpi, false>;
@@ -932,7 +989,9 @@ cudaError_t tc_gemm_launch_pair(TcMode mode, TcEpi epi, const TcLaunch& L, int s
                                 cudaStream_t s) {
     if (L.total_tiles <= 0) return cudaSuccess;
     if (L.table != nullptr || L.nprob < 1 || L.nprob > kMaxInlineProblems) return cudaErrorInvalidValue;
-    if (L.convert_a && (L.row_bytes != 128 || mode == TC_BF16)) return cudaErrorInvalidValue;
+    if (L.convert_a && (L.row_bytes != 128 || mode == TC_BF16 ||
+                        !(epi == EPI_SPLIT_BF16 || epi == EPI_TF32)))
+        return cudaErrorInvalidValue;
     if (L.out2[0] != nullptr && (L.row_bytes != 128 || L.convert_a ||
                                  !(epi == EPI_SPLIT_BF16 || epi == EPI_TF32)))
         return cudaErrorInvalidValue;
@@ -958,13 +1017,21 @@ cudaError_t tc_gemm_launch_pair(TcMode mode, TcEpi epi, const TcLaunch& L, int s
     if (L.t_store != 0) {
         const bool site = L.t_store == kStoreSiteInterleaved;
         const bool smaj = L.t_store == kStoreSiteMajor;
-        bool ok = (epi == EPI_SPLIT_BF16 || (epi == EPI_TF32 && site)) &&
+        const bool cols = L.t_store == kStoreColumnsF32;
+        bool ok = (cols ? ((epi == EPI_F32 || epi == EPI_F32_ATOMIC) && L.out2[0] == nullptr &&
+                           L.out[0][0] != nullptr && L.chunk_scratch == nullptr)
+                        : (epi == EPI_SPLIT_BF16 || (epi == EPI_TF32 && site))) &&
                   (smaj ? (L.out2[0] != nullptr && L.out[0][0] == nullptr &&
                            L.o2_rows_per_op % 16 == 0 && L.o2_m % 16 == 0)
                         : (L.out2[0] == nullptr && L.out[0][0] != nullptr)) &&
                   (site ? (L.t_store_d == 2 || L.t_store_d == 4)
-                        : (L.t_store == kStoreRowContiguous || smaj));
-        for (int i = 0; ok && i < L.nprob; ++i) {
+                        : (L.t_store == kStoreRowContiguous || smaj || cols));
+        for (int i = 0; ok && cols && i < L.nprob; ++i) {
+            const TcScatter& S = L.inline_prob[i].sc[0];
+            ok = S.s_split == 0 && S.rows_per_op % 16 == 0 && S.col_div == 1 && S.s_row == 1 &&
+                 S.op_off == nullptr && S.s_op == int64_t(L.inline_prob[i].N) * S.s_col_hi;
+        }
+        for (int i = 0; ok && !cols && i < L.nprob; ++i) {
             const TcProblem& P = L.inline_prob[i];
             const TcScatter& S = P.sc[0];
             ok = P.k_splits == 1 &&

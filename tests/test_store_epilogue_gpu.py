@@ -9,7 +9,9 @@ both site dimensions the store maps take (d = 2, 4), operators that begin in the
 of a warp's 32 rows (m = 48, 400), chunks that are short inside N (N tiles of 208 and
 176 columns) and at the end of N (d * m' not a multiple of 32), rows past the last
 operator, accumulation chains (m > 1024), and layouts that fall back to register stores
-(d = 3, m not a multiple of 16); TF32 takes the FP32 form of the first layout.  The adjoint's W' product takes the row-contiguous form
+(d = 3, m not a multiple of 16); TF32 takes the FP32 form of the first layout.  The
+second product's FP32 O' leaves through the columns layout, its second accumulation
+chain and the parts of its split tail adding with TMA reductions.  The adjoint's W' product takes the row-contiguous form
 of the same epilogue and is checked the same way against the oracle's adjoint.
 """
 import numpy as np
@@ -94,6 +96,30 @@ def test_tma_store_epilogue_tf32(P, shape):
     reg = rotate(P, Ud, Od, d, 1, opts=(("pack_operators", 1),), prec="tf32")
     assert np.array_equal(tma, reg)
     assert rel_err(tma, oracle.rotate_dense(U, O.astype(np.float64), d)).max() <= 3e-3
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_second_product_tma_reductions_split_tail(P, prec):
+    # the default (non-deterministic) second product splits its last partial wave along
+    # the reduction: the parts add into O' with TMA reductions (the columns layout), as
+    # does the second of its two accumulation chains (BF16x3, m*d = 1600); checked
+    # against the oracle, the summation order of the split tiles being free
+    m, d, mp, K = 400, 4, 400, 23
+    rng = np.random.default_rng(9950)
+    U = orthonormal_columns(rng, m * d, mp)
+    O = rng.standard_normal((K, m, m)).astype(np.float32)
+    dev = torch.device("cuda")
+    h = P.Handle()
+    try:
+        out = P.dmrg_rotate_ops(torch.from_numpy(U).to(dev), torch.from_numpy(O).to(dev), d, prec,
+                                handle=h)
+        torch.cuda.synchronize()
+        P.dmrg_sync_status(handle=h)
+        got = out.double().cpu().numpy()
+    finally:
+        h.close()
+    ref = oracle.rotate_dense(U, O.astype(np.float64), d)
+    assert rel_err(got, ref).max() <= (TOL if prec == "bf16x3" else 3e-3)
 
 
 @pytest.mark.parametrize("shape", [(64, 4, 64, 5), (48, 2, 100, 4)])
