@@ -142,14 +142,19 @@ DMRG_API dmrg_status dmrg_sync_status(dmrg_handle handle, dmrg_stream_t stream);
  *                              fits in two N tiles, else pack; 1 = always pack;
  *                              2 = convert whenever the layout allows.  FP64 operators
  *                              and other rows are always packed.
- *   DMRG_OPT_STORE_EPILOGUE  : how the BF16x3 first product (on CTA pairs) writes its
- *                              result T = O_k U_r.  0 (default) = each epilogue warp
- *                              stages a 32 x 32 chunk of BF16 hi/lo values in shared
- *                              memory and one lane sends it out with TMA bulk tensor
- *                              stores, where d is 2 or 4, m is a multiple of 16 and
- *                              the shared memory holds the staging (else as 1);
+ *   DMRG_OPT_STORE_EPILOGUE  : how the tensor-core products on CTA pairs write their
+ *                              results: the first product's T = O_k U_r (BF16 hi/lo
+ *                              or TF32; d = 2 or 4, m a multiple of 16), the second
+ *                              product's O'_k (FP32, m' a multiple of 16, at most two
+ *                              accumulation chains per tile) and the adjoint's W'_k,
+ *                              W_k and dO_k.  0 (default) = each epilogue warp stages a
+ *                              32 x 32 chunk in shared memory and one lane sends it out
+ *                              with TMA bulk tensor stores (a second accumulation chain,
+ *                              or a part of a split tile, with TMA reductions) where
+ *                              the layout and the shared memory allow (else as 1);
  *                              1 = every thread stores its own values.  The values
- *                              written are the same.  Other values return
+ *                              written are the same (FP32 sums flush subnormal results
+ *                              to zero either way).  Other values return
  *                              DMRG_ERR_INVALID_ARG.
  *   DMRG_OPT_TEST_WITHHOLD_ARRIVAL : test hook for failure detection.  1 makes
  *                              the next dense tensor-core launch withhold one
