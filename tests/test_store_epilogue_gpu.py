@@ -63,6 +63,10 @@ SHAPES = [
     (160, 2, 333, 4),     # d = 2, odd m': the last chunk partly past N
     (50, 4, 60, 3),       # m not a multiple of 16: register stores
     (48, 3, 70, 3),       # d = 3: register stores
+    # the second product's FP32 columns layout (m' a multiple of 16):
+    (64, 4, 48, 7),       # one chain, operators of 48 rows inside a warp's 32
+    (300, 4, 80, 5),      # two chains (m*d = 1200): the second adds by TMA reductions
+    (200, 2, 208, 3),     # one 208-column tile, its last chunk of 16 columns
 ]
 
 
